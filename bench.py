@@ -1,0 +1,416 @@
+#!/usr/bin/env python3
+"""Benchmark: QPE n=28 circuit time and achieved HBM GB/s, partitioned vs per-gate.
+
+One step = one whole QPE circuit on n = 28 qubits (t = 24 counting qubits,
+4 eigenstate qubits, 436 gates, seeded phases) through the C ABI: reset to
+|0...0>, sv_apply_circuit (planning, programme upload, tile passes) and
+sv_argmax of the counting register (FP64 marginal, read back to the host).
+The state (2 GiB complex64) is far larger than the 126 MiB L2, so every pass
+streams from HBM and no L2 flush is needed between steps.
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own
+replica on its own GPU (the workload has no exchange step); ``value`` is the
+circuits/s of all ranks over the slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle instead (the baseline arm),
+each step a bounded prefix of the same circuit, extrapolated by gate count.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QPE n=28 circuit time & achieved HBM GB/s: partitioned/fused vs per-gate"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=28)
+    ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--no-pergate", action="store_true")
+    ap.add_argument("--no-c128", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def traffic_for(kernel_src: str, workload: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if the kernel's
+    source is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        ent = d[workload]
+        with open(os.path.join(ROOT, kernel_src), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        if ent.get("source_sha") != sha:
+            return None
+        return float(ent["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 10:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        loaded = [r for r in rows if (num(r[4]) or 0) >= 50] or rows
+        sm = [num(r[1]) for r in loaded if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": num(rows[0][2]), "samples": len(rows), "samples_loaded": len(loaded),
+                "power_w_max": max((num(r[3]) or 0) for r in rows), "reasons": reasons}
+
+
+def oracle_sample(n: int, gates, seconds: float):
+    """Time the FP64 oracle on a prefix of the circuit; returns (s/circuit, gates, threads)."""
+    from oracle import oracle
+
+    oracle.build()
+    threads = oracle.num_threads()
+    psi = oracle.init(n)
+    done, t0 = 0, time.perf_counter()
+    while done < len(gates):
+        oracle.apply(n, psi, gates[done:done + 1])
+        done += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    del psi
+    return el / done * len(gates), done, threads
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_2605_15098_gb300 import circuits as C
+
+    n = args.n
+    gates, _, _ = C.qpe(n)
+    from oracle import oracle
+
+    oracle.build()
+    threads = oracle.num_threads()
+    psi = oracle.init(n)
+    per = max(1, min(len(gates), 4))
+
+    def step(i):
+        lo = (i * per) % len(gates)
+        sl = gates[lo:lo + per]
+        t0 = time.perf_counter()
+        oracle.apply(n, psi, sl)
+        return time.perf_counter() - t0, len(sl)
+
+    for i in range(args.warmup):
+        step(i)
+    tot, ng = 0.0, 0
+    for i in range(args.steps):
+        dt, g = step(args.warmup + i)
+        tot += dt
+        ng += g
+    circuit_s = tot / ng * len(gates)
+    value = 1.0 / circuit_s
+    sample = (f"{ng} of {len(gates)} gates of the QPE n={n} circuit (FP64 complex128 oracle, "
+              f"{per} gates per step), extrapolated by gate count")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": f"QPE-{n} circuits/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": circuit_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded QPE circuit)",
+        "config": {"workload": f"QPE n={n}, t={n - 4} counting + 4 eigenstate qubits, "
+                               f"{len(gates)} gates", "n": n},
+        "cpu_baseline": {"value": value, "unit": f"QPE-{n} circuits/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": f"QPE-{n} circuits/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2605_15098_gb300 import build as B
+    from paper_2605_15098_gb300 import circuits as C
+
+    torch.cuda.set_device(local)
+    B.build()
+    from paper_2605_15098_gb300 import sv
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n = args.n
+    dt = sv.SV_C64 if args.dtype == "c64" else sv.SV_C128
+    amp_bytes = 8 if dt == sv.SV_C64 else 16
+    gates, expected, info = C.qpe(n)
+    mask = info["mask"]
+    cfg = sv.make_config(sv.SV_MODE_PARTITIONED, tile_qubits=args.tile, chunk_qubits=args.chunk)
+    state_bytes = (1 << n) * amp_bytes
+
+    stream = torch.cuda.Stream()
+    buf = torch.empty(1 << n, dtype=torch.complex64 if dt == sv.SV_C64 else torch.complex128,
+                      device="cuda")
+    h = sv.sv_create_on(n, dt, buf.data_ptr(), state_bytes, stream.cuda_stream)
+
+    def step(c=cfg):
+        sv.sv_reset(h)
+        sv.sv_apply_circuit(h, gates, c)
+        return sv.sv_argmax(h, mask)
+
+    for _ in range(max(args.warmup, 0)):
+        idx, p = step()
+    idx, p = step()
+    ok = idx == info["y"] and abs(p - 1.0) < (1e-4 if dt == sv.SV_C64 else 1e-12)
+    st = sv.sv_last_stats(h)
+
+    # ---- timed region (device time, CUDA events on the library's stream) ----
+    launches0 = sv.sv_launch_count()
+    sv.sv_profile(h, True)
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    launches = sv.sv_launch_count() - launches0
+    recs = sv.sv_profile_read(h)
+    sv.sv_profile(h, False)
+    max_ms = max_over_ranks(elapsed_ms)
+    value = world * args.steps / (max_ms / 1e3)
+
+    tile = [r for r in recs if r["kind"] == sv.SV_KERNEL_TILE]
+    tile_ms = [r["ms"] for r in tile]
+    tile_avg_ms = sum(tile_ms) / len(tile_ms) if tile_ms else float("nan")
+    launch_bytes = 2.0 * state_bytes
+    achieved = launch_bytes / (tile_avg_ms / 1e3) / 1e9 if tile_ms else None
+    peak, peak_kind = peaks()
+    kern_share = sum(tile_ms) / max(max_ms if world == 1 else elapsed_ms, 1e-9)
+    circuit_ms = max_ms / args.steps
+    alg_gbs = st["sweep_bytes"] / (circuit_ms / 1e3) / 1e9
+
+    out = {
+        "metric": METRIC, "value": value, "unit": f"QPE-{n} circuits/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": circuit_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if dt == sv.SV_C64 else "f64",
+        "data": f"synthetic: seeded QPE circuit (splitmix64 seed {C.DEFAULT_SEED}, a_i={info['a']})",
+        "config": {
+            "workload": f"QPE n={n} ({n - 4} counting + 4 eigenstate qubits, {len(gates)} gates), "
+                        f"{'complex64' if dt == sv.SV_C64 else 'complex128'}, partitioned tile passes",
+            "n": n, "gates": len(gates), "mode": "partitioned", "passes": st["passes"],
+            "relabels": st["relabels"], "tile_qubits": args.tile or (13 if dt == sv.SV_C64 else 12),
+            "chunk_qubits": args.chunk or (5 if dt == sv.SV_C64 else 4),
+            "state_bytes": state_bytes,
+            "l2": "state (2^n amplitudes) exceeds the 126 MiB L2; no flush between steps",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "step": "reset + sv_apply_circuit + sv_argmax(counting register)",
+            "outcome_ok": bool(ok),
+        },
+        "hbm_gbs_algorithmic": alg_gbs,
+        "roofline": {
+            "kernel": "k_tile (tile pass)", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic_for("paper_2605_15098_gb300/csrc/tile.cu", f"qpe{n}_{args.dtype}"),
+            "algorithmic_bytes_per_launch": launch_bytes, "launches": len(tile_ms),
+            "avg_launch_ms": tile_avg_ms, "share_of_step_time": kern_share,
+        },
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+
+    # ---- per-gate comparison (same circuit, one HBM sweep per gate) ----
+    if not args.no_pergate:
+        pg = sv.make_config(sv.SV_MODE_PERGATE)
+        step(pg)
+        k = 2
+        e0.record(stream)
+        for _ in range(k):
+            step(pg)
+        e1.record(stream)
+        stream.synchronize()
+        pst = sv.sv_last_stats(h)
+        pms = e0.elapsed_time(e1) / k
+        out["per_gate"] = {
+            "circuit_ms": pms, "passes": pst["passes"],
+            "hbm_gbs_full_sweeps": pst["sweep_bytes"] / (pms / 1e3) / 1e9,
+            "hbm_gbs_touched": pst["touched_bytes"] / (pms / 1e3) / 1e9,
+            "speedup_partitioned_over_pergate": pms / circuit_ms,
+        }
+    sv.sv_destroy(h)
+    del buf
+
+    # ---- complex128 (FP64 arithmetic) at the same n, both paths ----
+    if not args.no_c128 and dt == sv.SV_C64:
+        buf2 = torch.empty(1 << n, dtype=torch.complex128, device="cuda")
+        h2 = sv.sv_create_on(n, sv.SV_C128, buf2.data_ptr(), (1 << n) * 16, stream.cuda_stream)
+        res = {}
+        for name, c2, reps in (("partitioned", sv.make_config(sv.SV_MODE_PARTITIONED), 3),
+                               ("per_gate", sv.make_config(sv.SV_MODE_PERGATE), 1)):
+            if name == "per_gate" and args.no_pergate:
+                continue
+            sv.sv_reset(h2)
+            sv.sv_apply_circuit(h2, gates, c2)
+            e0.record(stream)
+            for _ in range(reps):
+                sv.sv_reset(h2)
+                sv.sv_apply_circuit(h2, gates, c2)
+                i2, p2 = sv.sv_argmax(h2, mask)
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            s2 = sv.sv_last_stats(h2)
+            res[name] = {"circuit_ms": ms, "passes": s2["passes"],
+                         "hbm_gbs_full_sweeps": s2["sweep_bytes"] / (ms / 1e3) / 1e9,
+                         "outcome_ok": bool(i2 == info["y"] and abs(p2 - 1) < 1e-12)}
+        out["c128"] = res
+        sv.sv_destroy(h2)
+        del buf2
+
+    # ---- end to end through the public API with host buffers ----
+    he = sv.sv_create(n, dt)
+    step_e2e = lambda: (sv.sv_reset(he), sv.sv_apply_circuit(he, gates, cfg),
+                        sv.sv_argmax(he, mask))
+    for _ in range(2):
+        step_e2e()
+    ke = max(3, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        step_e2e()
+    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    est = sv.sv_last_stats(he)
+    sv.sv_destroy(he)
+    out["e2e"] = {"value": world * ke / t_e2e, "unit": f"QPE-{n} circuits/s",
+                  "h2d_bytes_per_step": int(est["h2d_bytes"]),
+                  "d2h_bytes_per_step": 16,
+                  "gate_list_bytes": int(gates.nbytes),
+                  "step": "sv_create'd handle: reset + sv_apply_circuit(host gate list) + "
+                          "sv_argmax (host result)"}
+
+    # ---- CPU baseline: the FP64 oracle on the host cores (rank 0, N = 1) ----
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cs, done, threads = oracle_sample(n, gates, args.cpu_seconds)
+        out["cpu_baseline"] = {
+            "value": 1.0 / cs, "unit": f"QPE-{n} circuits/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {done} of {len(gates)} gates of the same QPE n={n} circuit in the "
+                      f"FP64 complex128 oracle, extrapolated by gate count"}
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

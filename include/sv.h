@@ -1,0 +1,266 @@
+/*
+ * sv.h - C ABI of libsv, a GB300 (sm_103a) dense state-vector simulator.
+ *
+ * Method: arxiv 2605.15098, "Accelerating State-Vector Quantum Simulation on
+ * Integrated GPUs via Cache Locality Optimization".  The problem the calls
+ * follow is the paper's: an n-qubit state is an array of 2^n complex
+ * amplitudes that starts in |0...0>, a list of single-qubit and controlled
+ * gates is applied to it (Sec. III-A, Eq. 1, Algorithm 1), and the result is
+ * read out as measured bitstrings (Sec. IV-A).  The partitioned execution
+ * (Sec. III-B: local/global qubits, deferred local gates applied block by
+ * block, global qubits brought local, controls on global qubits decided per
+ * block) is an implementation strategy: it changes the order of work, never
+ * the result beyond floating-point rounding.
+ *
+ * Conventions shared by every call
+ *  - Qubit q is bit q of the amplitude index (the stride 2^t of Algorithm 1).
+ *  - Amplitudes are interleaved complex: SV_C64 = (float re, float im),
+ *    8 bytes; SV_C128 = (double re, double im), 16 bytes.
+ *  - All pointers named host_* are host memory owned by the caller; dev_*
+ *    are device pointers on the handle's device, owned by the caller.  The
+ *    library owns the state buffer unless the handle was made by
+ *    sv_create_on.
+ *  - Every argument is validated on the host before any kernel is launched;
+ *    a call that returns an error has not modified the state.
+ *  - Work is ordered on the handle's CUDA stream.  Calls that return data to
+ *    host memory synchronise that stream before returning; sv_apply_circuit
+ *    returns once its kernels are enqueued.
+ *  - A handle must not be used from two threads at once.  sv_last_error()
+ *    is per thread.
+ *  - Nothing here allocates host memory that the caller must free.
+ */
+#ifndef LIBSV_SV_H_
+#define LIBSV_SV_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sv_state *sv_handle;
+
+typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
+
+typedef enum {
+    SV_OK = 0,
+    SV_ERR_ARG = -1,         /* invalid argument (nothing was run)              */
+    SV_ERR_OOM = -2,         /* device or host allocation failed                */
+    SV_ERR_CUDA = -3,        /* a CUDA runtime call failed (message has the code) */
+    SV_ERR_TIMEOUT = -4,     /* a bounded device wait gave up                    */
+    SV_ERR_STATE = -5,       /* handle in a state that does not allow the call  */
+    SV_ERR_UNSUPPORTED = -6  /* valid request this build cannot serve           */
+} sv_status;
+
+/* Gate kinds.  Matrices (row-major, U11 acts |0> -> |0>):
+ *   SV_X    [[0,1],[1,0]]
+ *   SV_H    [[1,1],[1,-1]]/sqrt(2)
+ *   SV_P    diag(1, e^{i p[0]})                       (Eq. 2's phase gate)
+ *   SV_CP   SV_P on `target` when bit `control` is 1  (control rule, Sec. III-A)
+ *   SV_CZ   diag(1,-1) on `target` when bit `control` is 1
+ *   SV_SWAP exchange qubits `target` and `control`    (the SWAP of Sec. III-B)
+ *   SV_U3   [[cos(a/2), -e^{ic} sin(a/2)], [e^{ib} sin(a/2), e^{i(b+c)} cos(a/2)]]
+ *           with a, b, c = p[0], p[1], p[2]
+ *   SV_U    explicit 2x2: p = {U11.re, U11.im, U12.re, U12.im, U21.re, U21.im,
+ *           U22.re, U22.im}
+ *   SV_CU   SV_U on `target` when bit `control` is 1
+ *   SV_PK   diag(1, e^{2 pi i k / 2^j}) with k = num, j = log2den (0..62); k is
+ *           reduced modulo 2^j as an integer, so the phase is exact (Eq. 3,
+ *           U^a = P(2 pi 2^-n a))
+ *   SV_CPK  SV_PK on `target` when bit `control` is 1
+ */
+enum {
+    SV_X = 0, SV_H = 1, SV_P = 2, SV_CP = 3, SV_CZ = 4, SV_SWAP = 5,
+    SV_U3 = 6, SV_U = 7, SV_CU = 8, SV_PK = 9, SV_CPK = 10
+};
+
+/* One gate, 96 bytes.  `control` is the control qubit of CP/CZ/CU/CPK and
+ * the second qubit of SWAP; it must differ from `target` and is ignored
+ * (set it to -1) for the other kinds.  `reserved` must be 0. */
+typedef struct sv_gate {
+    int32_t kind;
+    int32_t target;
+    int32_t control;
+    int32_t log2den;
+    int64_t num;
+    int64_t reserved;
+    double p[8];
+} sv_gate;
+
+/* Execution strategy for sv_apply_circuit. */
+typedef enum {
+    SV_MODE_AUTO = 0,        /* partitioned when n is larger than a tile      */
+    SV_MODE_PERGATE = 1,     /* one HBM sweep per gate (Algorithm 1 per gate)  */
+    SV_MODE_PARTITIONED = 2, /* tile passes (Sec. III-B), shared-memory tiles  */
+    SV_MODE_FUSED = 3        /* partitioned + 5-qubit blocks on tensor cores   */
+} sv_mode;
+
+/* Flags for sv_config.flags. */
+enum {
+    SV_FLAG_NO_DIAG_MERGE = 1,  /* keep every diagonal gate as its own step  */
+    SV_FLAG_PAPER_SWAP = 2,     /* bring global targets local by explicit
+                                   remap passes with LRU eviction, as the
+                                   paper does, instead of gathering them
+                                   into the tile                               */
+    SV_FLAG_NO_RELABEL = 4      /* execute SWAP gates as data movement        */
+};
+
+/* Planner choice for partitioned modes. */
+typedef enum { SV_PLANNER_GREEDY = 0, SV_PLANNER_LEARNED = 1 } sv_planner;
+
+/* All-zero means "library defaults".  tile_qubits = k, the number of qubits
+ * whose amplitudes one shared-memory tile holds (2^k amplitudes);
+ * chunk_qubits = c, the lowest qubits that every tile contains as one
+ * contiguous run (the unit of a bulk copy). */
+typedef struct sv_config {
+    int32_t mode;          /* sv_mode                                          */
+    int32_t tile_qubits;   /* k; 0 = default for the dtype                     */
+    int32_t chunk_qubits;  /* c; 0 = default                                   */
+    int32_t fuse_qubits;   /* width of a tensor-core fused block; 0 = 5        */
+    int32_t planner;       /* sv_planner                                       */
+    int32_t flags;         /* SV_FLAG_*                                        */
+    int32_t reserved[10];  /* must be 0                                        */
+} sv_config;
+
+/* Counters of the last sv_apply_circuit on a handle. */
+typedef struct sv_stats {
+    int32_t gates;          /* gates in the list                                */
+    int32_t passes;         /* full sweeps over the state: tile passes, per-gate
+                               sweeps and remap passes                          */
+    int32_t remaps;         /* of which explicit remap (permutation) passes     */
+    int32_t kernels;        /* kernel launches enqueued                         */
+    int32_t relabels;       /* SWAP gates absorbed into the qubit map           */
+    int32_t fused_blocks;   /* tensor-core blocks applied                       */
+    double sweep_bytes;     /* 2 * passes * 2^n * sizeof(amplitude)             */
+    double touched_bytes;   /* bytes the kernels had to move (diagonal and SWAP
+                               per-gate sweeps touch part of the state)         */
+    double h2d_bytes;       /* host-to-device bytes copied (the pass programme)  */
+} sv_stats;
+
+/* ---- lifetime --------------------------------------------------------- */
+
+/* Allocate a state of n qubits (1 <= n <= 34) on the current CUDA device and
+ * set it to |0...0>.  The library owns the memory; it uses its own stream.
+ * Errors: SV_ERR_ARG (n, dt, out), SV_ERR_OOM, SV_ERR_CUDA. */
+sv_status sv_create(int n, sv_dtype dt, sv_handle *out);
+
+/* Same, on a caller-owned device buffer of `bytes` >= 2^n * sizeof(amp),
+ * 256-byte aligned, and the caller's stream (NULL = legacy default stream).
+ * The buffer must outlive the handle; sv_destroy does not free it.
+ * The state is set to |0...0>. */
+sv_status sv_create_on(int n, sv_dtype dt, void *dev_buf, size_t bytes,
+                       void *cuda_stream, sv_handle *out);
+
+/* Free the handle (and the state, if owned).  NULL is accepted. */
+sv_status sv_destroy(sv_handle h);
+
+/* Set the state to |0...0> and the qubit map to the identity. */
+sv_status sv_reset(sv_handle h);
+
+/* Number of qubits, dtype, and device address of the state buffer.  The
+ * buffer holds amplitudes in PHYSICAL order; see sv_qubit_map. */
+sv_status sv_info(sv_handle h, int *n, sv_dtype *dt, void **dev_amps);
+
+/* Physical bit position of each logical qubit (array of n ints).  SWAP gates
+ * are absorbed into this map in partitioned modes (Sec. III-B keeps a
+ * logical-to-physical qubit mapping updated after each SWAP). */
+sv_status sv_qubit_map(sv_handle h, int *host_phys_of_logical);
+
+/* ---- applying gates --------------------------------------------------- */
+
+/* Apply gates g[0..m-1] in order.  cfg may be NULL (defaults).
+ * Errors: SV_ERR_ARG with the index of the first bad gate in the message
+ * (qubit out of range, control == target, unknown kind, nonzero reserved,
+ * log2den outside 0..62); nothing is applied in that case. */
+sv_status sv_apply_circuit(sv_handle h, const sv_gate *host_gates, size_t m,
+                           const sv_config *cfg);
+
+/* Counters of the last sv_apply_circuit. */
+sv_status sv_last_stats(sv_handle h, sv_stats *out);
+
+/* ---- reading out (Sec. IV-A: the measured bitstring) ------------------ */
+
+/* Marginal probabilities over the logical qubits in `qubit_mask`, computed
+ * in FP64 from the amplitudes and renormalised by their total.  Output index
+ * bit j is the j-th lowest qubit of the mask; host_out holds
+ * 2^popcount(mask) doubles.  Errors: SV_ERR_ARG (mask empty or beyond n,
+ * popcount > 30), SV_ERR_OOM. */
+sv_status sv_probabilities(sv_handle h, uint64_t qubit_mask, double *host_out);
+
+/* Same, into a caller-owned device buffer of 2^popcount(mask) doubles;
+ * returns without synchronising. */
+sv_status sv_probabilities_device(sv_handle h, uint64_t qubit_mask, double *dev_out);
+
+/* Most probable outcome of the marginal over `qubit_mask` (lowest index
+ * among exact ties) and its probability (p_out may be NULL). */
+sv_status sv_argmax(sv_handle h, uint64_t qubit_mask, uint64_t *host_idx,
+                    double *host_p);
+
+/* Inverse-CDF sampling of the marginal over `qubit_mask`, one outcome per
+ * caller-supplied uniform u[s] in [0,1): the smallest i with C_i > u*C_last,
+ * where C is the inclusive CDF accumulated in blocks of 1024 outcomes
+ * (in-block sums in index order, block totals in block order). */
+sv_status sv_sample(sv_handle h, uint64_t qubit_mask, const double *host_u,
+                    size_t shots, uint64_t *host_out);
+
+/* Copy the amplitudes, in LOGICAL qubit order, to / from host memory of
+ * 2^n * sizeof(amp) bytes.  sv_copy_out may physically reorder the state
+ * to make the qubit map the identity first (results are unchanged). */
+sv_status sv_copy_out(sv_handle h, void *host_amps);
+sv_status sv_copy_in(sv_handle h, const void *host_amps);
+
+/* ---- timing recorder ---------------------------------------------------- */
+
+/* Kernel families named in launch records. */
+enum {
+    SV_KERNEL_PERGATE = 0,  /* one gate, one HBM sweep                       */
+    SV_KERNEL_TILE = 1,     /* one tile pass (shared-memory programme)        */
+    SV_KERNEL_REMAP = 2,    /* explicit qubit-remap permutation pass           */
+    SV_KERNEL_FUSED = 3     /* tile pass with tensor-core fused blocks         */
+};
+
+/* One kernel launch of sv_apply_circuit, timed with CUDA events recorded on
+ * the handle's stream right before and after the launch. */
+typedef struct sv_launch_record {
+    int32_t kind;      /* SV_KERNEL_*                                          */
+    int32_t pass;      /* launch index within its sv_apply_circuit call        */
+    int32_t n;         /* qubits                                              */
+    int32_t k;         /* tile qubits (0 for per-gate)                         */
+    int32_t nops;      /* programme steps of the pass (1 for per-gate)         */
+    int32_t ngates;    /* circuit gates the launch applies                     */
+    int32_t dtype;     /* sv_dtype                                             */
+    int32_t gate_kind; /* per-gate: the gate kind; tile: -1                    */
+    double bytes;      /* algorithmic bytes: 2 * 2^n * sizeof(amp) per sweep,
+                          or the touched share for per-gate diagonal/SWAP      */
+    double ms;         /* measured duration                                    */
+    uint64_t feat;     /* tile: bit mask of the physical qubits in the tile;
+                          per-gate: bit mask of the gate's qubits              */
+} sv_launch_record;
+
+/* Start (enable=1) or stop (0) recording launch records on this handle.
+ * Starting clears earlier records.  Recording adds two event records per
+ * launch and does not change what the kernels compute. */
+sv_status sv_profile(sv_handle h, int enable);
+
+/* Synchronise the handle's stream and copy up to `cap` records (oldest
+ * first) into host_out; *count receives the number available.  Records
+ * that were copied are removed. */
+sv_status sv_profile_read(sv_handle h, sv_launch_record *host_out, size_t cap, size_t *count);
+
+/* Number of kernels this library has launched in the process so far. */
+uint64_t sv_launch_count(void);
+
+/* ---- diagnostics ------------------------------------------------------ */
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *sv_last_error(void);
+
+/* Library version string. */
+const char *sv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBSV_SV_H_ */

@@ -1,0 +1,280 @@
+// C ABI entry points (include/sv.h): handle lifetime, validation, dispatch.
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "common.h"
+
+using namespace sv;
+
+namespace {
+
+constexpr int kMaxQubits = 34;
+
+sv_status make_handle(int n, sv_dtype dt, void *buf, size_t bytes, void *stream, bool own,
+                      sv_handle *out) {
+    clear_error();
+    if (!out) return fail(SV_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > kMaxQubits) return fail(SV_ERR_ARG, "n=%d outside 1..%d", n, kMaxQubits);
+    if (dt != SV_C64 && dt != SV_C128) return fail(SV_ERR_ARG, "unknown dtype %d", (int)dt);
+    const size_t need = ((size_t)1 << n) * (dt == SV_C128 ? 16 : 8);
+    if (!own) {
+        if (!buf) return fail(SV_ERR_ARG, "dev_buf is NULL");
+        if (bytes < need) return fail(SV_ERR_ARG, "buffer of %zu bytes < %zu needed", bytes, need);
+        if ((uintptr_t)buf % 256) return fail(SV_ERR_ARG, "dev_buf not 256-byte aligned");
+    }
+    sv_state *h = new (std::nothrow) sv_state();
+    if (!h) return fail(SV_ERR_OOM, "host allocation failed");
+    h->n = n;
+    h->dt = dt;
+    h->amp_bytes = dt == SV_C128 ? 16 : 8;
+    for (int q = 0; q < 64; q++) h->phys[q] = q;
+    auto bail = [&](sv_status st) {
+        if (h->owned && h->amps) cudaFree(h->amps);
+        if (h->small) cudaFree(h->small);
+        if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+        delete h;
+        return st;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) !=
+            cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        return bail(fail(SV_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e)));
+    }
+    if (own) {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(SV_ERR_CUDA, "cudaStreamCreate failed"));
+        }
+        h->own_stream = true;
+        if (cudaMalloc(&h->amps, need) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(SV_ERR_OOM, "cannot allocate %zu bytes for the state", need));
+        }
+        h->owned = true;
+    } else {
+        h->amps = buf;
+        h->stream = reinterpret_cast<cudaStream_t>(stream);
+    }
+    if (cudaMalloc(&h->small, 65536) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(SV_ERR_OOM, "cannot allocate reduction buffer"));
+    }
+    sv_status st = init_zero_state(h);
+    if (st != SV_OK) return bail(st);
+    *out = h;
+    return SV_OK;
+}
+
+int popcount64(uint64_t x) { return __builtin_popcountll(x); }
+
+sv_status check_mask(sv_state *h, uint64_t mask) {
+    if (!mask) return fail(SV_ERR_ARG, "qubit_mask is empty");
+    if (h->n < 64 && (mask >> h->n)) return fail(SV_ERR_ARG, "qubit_mask has bits beyond n=%d", h->n);
+    if (popcount64(mask) > 30) return fail(SV_ERR_ARG, "qubit_mask selects more than 30 qubits");
+    return SV_OK;
+}
+
+// physical positions of the mask's logical qubits, in increasing logical order
+int mask_positions(const sv_state *h, uint64_t mask, int *pos) {
+    int m = 0;
+    for (int q = 0; q < h->n; q++)
+        if ((mask >> q) & 1) pos[m++] = h->phys[q];
+    return m;
+}
+
+sv_status read_marginal(sv_state *h, uint64_t mask, uint64_t *len) {
+    int pos[64];
+    int m = mask_positions(h, mask, pos);
+    *len = UINT64_C(1) << m;
+    SV_TRY(ensure_probs(h, *len * sizeof(double)));
+    return marginal_device(h, pos, m, h->probs);
+}
+
+// Physically reorder the state so that logical qubit q sits at bit q.
+sv_status normalise_layout(sv_state *h) {
+    for (int q = 0; q < h->n; q++) {
+        if (h->phys[q] == q) continue;
+        int r = -1;
+        for (int k = 0; k < h->n; k++)
+            if (h->phys[k] == q) r = k;
+        const int p = h->phys[q];
+        SV_TRY(pergate_swap_bits(h, p, q));
+        h->phys[q] = q;
+        h->phys[r] = p;
+    }
+    return SV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sv_status sv_create(int n, sv_dtype dt, sv_handle *out) {
+    return make_handle(n, dt, nullptr, 0, nullptr, true, out);
+}
+
+sv_status sv_create_on(int n, sv_dtype dt, void *dev_buf, size_t bytes, void *cuda_stream,
+                       sv_handle *out) {
+    return make_handle(n, dt, dev_buf, bytes, cuda_stream, false, out);
+}
+
+sv_status sv_destroy(sv_handle h) {
+    clear_error();
+    if (!h) return SV_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->owned && h->amps) cudaFree(h->amps);
+    if (h->scratch) cudaFree(h->scratch);
+    if (h->probs) cudaFree(h->probs);
+    if (h->small) cudaFree(h->small);
+    if (h->plan_dev) cudaFree(h->plan_dev);
+    if (h->plan_host) cudaFreeHost(h->plan_host);
+    for (auto &p : h->pending) {
+        cudaEventDestroy(p.e0);
+        cudaEventDestroy(p.e1);
+    }
+    for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return SV_OK;
+}
+
+sv_status sv_reset(sv_handle h) {
+    clear_error();
+    if (!h) return fail(SV_ERR_ARG, "handle is NULL");
+    return init_zero_state(h);
+}
+
+sv_status sv_info(sv_handle h, int *n, sv_dtype *dt, void **dev_amps) {
+    clear_error();
+    if (!h) return fail(SV_ERR_ARG, "handle is NULL");
+    if (n) *n = h->n;
+    if (dt) *dt = h->dt;
+    if (dev_amps) *dev_amps = h->amps;
+    return SV_OK;
+}
+
+sv_status sv_qubit_map(sv_handle h, int *host_phys_of_logical) {
+    clear_error();
+    if (!h || !host_phys_of_logical) return fail(SV_ERR_ARG, "NULL argument");
+    for (int q = 0; q < h->n; q++) host_phys_of_logical[q] = h->phys[q];
+    return SV_OK;
+}
+
+sv_status sv_apply_circuit(sv_handle h, const sv_gate *host_gates, size_t m, const sv_config *cfg) {
+    clear_error();
+    if (!h) return fail(SV_ERR_ARG, "handle is NULL");
+    if (m && !host_gates) return fail(SV_ERR_ARG, "gate list is NULL");
+    sv_config c{};
+    if (cfg) c = *cfg;
+    for (int i = 0; i < 10; i++)
+        if (c.reserved[i]) return fail(SV_ERR_ARG, "sv_config.reserved must be 0");
+    if (c.mode < SV_MODE_AUTO || c.mode > SV_MODE_FUSED)
+        return fail(SV_ERR_ARG, "unknown mode %d", c.mode);
+    if (c.planner < SV_PLANNER_GREEDY || c.planner > SV_PLANNER_LEARNED)
+        return fail(SV_ERR_ARG, "unknown planner %d", c.planner);
+    if (c.tile_qubits < 0 || c.tile_qubits > 14 || c.chunk_qubits < 0 || c.chunk_qubits > 14)
+        return fail(SV_ERR_ARG, "tile_qubits / chunk_qubits outside 0..14");
+    if (c.fuse_qubits != 0 && c.fuse_qubits != 5)
+        return fail(SV_ERR_ARG, "fuse_qubits must be 0 or 5");
+    for (size_t i = 0; i < m; i++) {
+        std::string why = check_gate(h->n, host_gates[i]);
+        if (!why.empty()) return fail(SV_ERR_ARG, "gate %zu: %s", i, why.c_str());
+    }
+    h->stats = sv_stats{};
+    h->stats.gates = (int32_t)m;
+    h->launch_index = 0;
+    int mode = c.mode;
+    if (mode == SV_MODE_AUTO) mode = h->n >= 16 ? SV_MODE_PARTITIONED : SV_MODE_PERGATE;
+    sv_status st = SV_OK;
+    if (mode == SV_MODE_PERGATE) {
+        for (size_t i = 0; i < m && st == SV_OK; i++) {
+            sv_gate g = host_gates[i];
+            g.target = h->phys[g.target];
+            if (is_controlled_kind(g.kind) || g.kind == SV_SWAP) g.control = h->phys[g.control];
+            st = pergate_apply(h, g);
+        }
+    } else {
+        std::vector<sv_gate> gl(host_gates, host_gates + m);
+        c.mode = mode;
+        st = partitioned_apply(h, gl, c);
+    }
+    h->stats.sweep_bytes = 2.0 * h->stats.passes * (double)state_bytes(h);
+    return st;
+}
+
+sv_status sv_last_stats(sv_handle h, sv_stats *out) {
+    clear_error();
+    if (!h || !out) return fail(SV_ERR_ARG, "NULL argument");
+    *out = h->stats;
+    return SV_OK;
+}
+
+sv_status sv_probabilities(sv_handle h, uint64_t qubit_mask, double *host_out) {
+    clear_error();
+    if (!h || !host_out) return fail(SV_ERR_ARG, "NULL argument");
+    SV_TRY(check_mask(h, qubit_mask));
+    uint64_t len;
+    SV_TRY(read_marginal(h, qubit_mask, &len));
+    SV_CUDA(cudaMemcpyAsync(host_out, h->probs, len * sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
+    SV_CUDA(cudaStreamSynchronize(h->stream));
+    return SV_OK;
+}
+
+sv_status sv_probabilities_device(sv_handle h, uint64_t qubit_mask, double *dev_out) {
+    clear_error();
+    if (!h || !dev_out) return fail(SV_ERR_ARG, "NULL argument");
+    SV_TRY(check_mask(h, qubit_mask));
+    int pos[64];
+    int m = mask_positions(h, qubit_mask, pos);
+    return marginal_device(h, pos, m, dev_out);
+}
+
+sv_status sv_argmax(sv_handle h, uint64_t qubit_mask, uint64_t *host_idx, double *host_p) {
+    clear_error();
+    if (!h || !host_idx) return fail(SV_ERR_ARG, "NULL argument");
+    SV_TRY(check_mask(h, qubit_mask));
+    uint64_t len;
+    SV_TRY(read_marginal(h, qubit_mask, &len));
+    return argmax_device(h, h->probs, len, host_idx, host_p);
+}
+
+sv_status sv_sample(sv_handle h, uint64_t qubit_mask, const double *host_u, size_t shots,
+                    uint64_t *host_out) {
+    clear_error();
+    if (!h || (shots && (!host_u || !host_out))) return fail(SV_ERR_ARG, "NULL argument");
+    SV_TRY(check_mask(h, qubit_mask));
+    for (size_t s = 0; s < shots; s++)
+        if (!(host_u[s] >= 0.0 && host_u[s] < 1.0))
+            return fail(SV_ERR_ARG, "u[%zu] = %g is not in [0, 1)", s, host_u[s]);
+    uint64_t len;
+    SV_TRY(read_marginal(h, qubit_mask, &len));
+    return sample_device(h, h->probs, len, host_u, shots, host_out);
+}
+
+sv_status sv_copy_out(sv_handle h, void *host_amps) {
+    clear_error();
+    if (!h || !host_amps) return fail(SV_ERR_ARG, "NULL argument");
+    SV_TRY(normalise_layout(h));
+    SV_CUDA(cudaMemcpyAsync(host_amps, h->amps, state_bytes(h), cudaMemcpyDeviceToHost, h->stream));
+    SV_CUDA(cudaStreamSynchronize(h->stream));
+    return SV_OK;
+}
+
+sv_status sv_copy_in(sv_handle h, const void *host_amps) {
+    clear_error();
+    if (!h || !host_amps) return fail(SV_ERR_ARG, "NULL argument");
+    SV_CUDA(cudaMemcpyAsync(h->amps, host_amps, state_bytes(h), cudaMemcpyHostToDevice, h->stream));
+    SV_CUDA(cudaStreamSynchronize(h->stream));
+    for (int q = 0; q < 64; q++) h->phys[q] = q;
+    return SV_OK;
+}
+
+const char *sv_last_error(void) { return last_error_cstr(); }
+
+const char *sv_version(void) { return "libsv 0.1 (sm_103a)"; }
+
+}  // extern "C"

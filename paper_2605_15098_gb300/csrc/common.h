@@ -1,0 +1,118 @@
+// Internal declarations shared by the translation units of libsv.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sv.h"
+
+namespace sv {
+
+// ---- errors ---------------------------------------------------------------
+sv_status fail(sv_status code, const char *fmt, ...);
+void clear_error();
+
+#define SV_CUDA(call)                                                          \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess)                                                 \
+            return ::sv::fail(SV_ERR_CUDA, "%s failed: %s (%s:%d)", #call,     \
+                              cudaGetErrorString(e_), __FILE__, __LINE__);     \
+    } while (0)
+
+#define SV_TRY(expr)                                                           \
+    do {                                                                       \
+        sv_status s_ = (expr);                                                 \
+        if (s_ != SV_OK) return s_;                                            \
+    } while (0)
+
+// ---- gate matrices (host, FP64) --------------------------------------------
+struct Mat2 {
+    double re[4], im[4];  // row-major: U11, U12, U21, U22
+};
+
+bool is_diagonal_kind(int kind);
+bool is_controlled_kind(int kind);
+// Validate one gate for an n-qubit state; empty string when valid.
+std::string check_gate(int n, const sv_gate &g);
+// 2x2 matrix of a non-SWAP gate (controls excluded: the matrix on the target).
+Mat2 gate_matrix(const sv_gate &g);
+// Phase of a diagonal gate on |1> (or |11>) as a fraction of a full turn in
+// units of 2^-64, exact for the dyadic kinds.  `exact` tells whether the
+// value is exact (dyadic kinds, CZ) or rounded (P/CP in radians).
+uint64_t diag_turns64(const sv_gate &g, bool *exact);
+
+// ---- handle ---------------------------------------------------------------
+}  // namespace sv
+
+struct sv_state {
+    int n = 0;
+    sv_dtype dt = SV_C64;
+    size_t amp_bytes = 8;
+    void *amps = nullptr;
+    bool owned = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int sm_count = 0;
+    int phys[64];                 // physical bit of each logical qubit
+    void *scratch = nullptr;      // device scratch, grown on demand
+    size_t scratch_cap = 0;
+    double *probs = nullptr;      // device marginal of the last read-out
+    size_t probs_cap = 0;
+    void *small = nullptr;        // 64 KiB device area for reduction partials
+    void *plan_dev = nullptr;     // device copy of the tile-pass programme
+    size_t plan_cap = 0;
+    void *plan_host = nullptr;    // pinned host staging for the programme
+    size_t plan_host_cap = 0;
+    sv_stats stats{};
+    // timing recorder
+    bool profiling = false;
+    struct Pending {
+        sv_launch_record rec;
+        cudaEvent_t e0, e1;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+    int launch_index = 0;  // within the current sv_apply_circuit
+};
+
+namespace sv {
+
+sv_status ensure_scratch(sv_state *h, size_t bytes);
+sv_status ensure_probs(sv_state *h, size_t bytes);
+const char *last_error_cstr();
+inline uint64_t state_bytes(const sv_state *h) { return ((uint64_t)1 << h->n) * h->amp_bytes; }
+
+// ---- timing recorder (prof.cpp) ---------------------------------------------
+void note_launch();
+// Record the start event of a launch; returns a record slot or -1.
+int prof_begin(sv_state *h);
+// Record the end event and the launch's description.
+void prof_end(sv_state *h, int slot, const sv_launch_record &meta);
+
+// ---- per-gate path (pergate.cu) ---------------------------------------------
+// Apply one gate whose qubits are already PHYSICAL positions.
+sv_status pergate_apply(sv_state *h, const sv_gate &g_phys);
+// Exchange physical bits a and b of the whole state (a SWAP sweep).
+sv_status pergate_swap_bits(sv_state *h, int a, int b);
+// Set the state to |0...0>.
+sv_status init_zero_state(sv_state *h);
+
+// ---- read-out (measure.cu) ----------------------------------------------------
+// Marginal over physical positions pos[0..m-1] (output bit j <-> pos[j]),
+// renormalised, into device buffer dev_out (2^m doubles), on h->stream.
+sv_status marginal_device(sv_state *h, const int *pos, int m, double *dev_out);
+sv_status argmax_device(sv_state *h, const double *dev_p, uint64_t len,
+                        uint64_t *host_idx, double *host_p);
+sv_status sample_device(sv_state *h, const double *dev_p, uint64_t len,
+                        const double *host_u, size_t shots, uint64_t *host_out);
+
+// ---- partitioned path (planner.cpp, tile.cu) ----------------------------------
+sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates_logical,
+                            const sv_config &cfg);
+
+}  // namespace sv

@@ -1,0 +1,285 @@
+// Greedy partition planner (host).
+//
+// Follows Sec. III-B of arxiv 2605.15098:
+//  * SWAP gates become relabels of the logical-to-physical qubit map ("the
+//    simulator maintains a logical-to-physical qubit mapping that is updated
+//    after each SWAP"), so they cost no data movement;
+//  * gates are deferred and grouped into passes; every gate of a pass is
+//    applied to one tile before the next tile is touched;
+//  * only the target of a gate has to be local; a global control is decided
+//    per tile from the tile's index;
+//  * diagonal gates (P, CP, CZ and their dyadic forms) never need a local
+//    qubit: every out-of-tile bit is a constant of the tile.
+// Passes are built by list scheduling over the gate dependency graph: two
+// gates depend on each other when they share a qubit that at least one of
+// them acts on non-diagonally.  A pass takes, in program order, every ready
+// gate whose non-diagonal qubits fit in the tile's k slots.
+#include <algorithm>
+#include <map>
+#include <string>
+#include <tuple>
+
+#include "common.h"
+#include "plan.h"
+
+namespace sv {
+namespace {
+
+struct PGate {
+    sv_gate g;       // physical qubits
+    int nd[2], nnd;  // qubits acted on non-diagonally
+    int dq[2], ndq;  // qubits acted on diagonally
+    bool diag;
+    std::vector<int> deps;
+};
+
+void classify(PGate &p) {
+    const sv_gate &g = p.g;
+    p.nnd = p.ndq = 0;
+    p.diag = is_diagonal_kind(g.kind);
+    if (g.kind == SV_SWAP) {
+        p.nd[p.nnd++] = g.target;
+        p.nd[p.nnd++] = g.control;
+    } else if (p.diag) {
+        p.dq[p.ndq++] = g.target;
+        if (is_controlled_kind(g.kind)) p.dq[p.ndq++] = g.control;
+    } else {
+        p.nd[p.nnd++] = g.target;
+        if (is_controlled_kind(g.kind)) p.dq[p.ndq++] = g.control;
+    }
+}
+
+bool commutes_with_gate(const PGate &d, const PGate &g) {
+    // d diagonal; g non-diagonal: they commute unless g acts non-diagonally
+    // on one of d's qubits.
+    for (int i = 0; i < g.nnd; i++)
+        for (int j = 0; j < d.ndq; j++)
+            if (g.nd[i] == d.dq[j]) return false;
+    return true;
+}
+
+}  // namespace
+
+std::string build_plan(const std::vector<sv_gate> &gates, const PlanOptions &opt, int *phys,
+                       Plan *out) {
+    const int n = opt.n;
+    out->passes.clear();
+    out->relabels = 0;
+    int k = std::min(opt.k, n);
+    int c = std::min(opt.c, k);
+    if (n > k && k - c < 2) return "tile must leave at least two free slots (k - c >= 2)";
+
+    // 1. physical gate list, SWAPs absorbed into the map
+    std::vector<PGate> pg;
+    pg.reserve(gates.size());
+    for (const sv_gate &g : gates) {
+        if (g.kind == SV_SWAP && opt.relabel) {
+            std::swap(phys[g.target], phys[g.control]);
+            out->relabels++;
+            continue;
+        }
+        PGate p{};
+        p.g = g;
+        p.g.target = phys[g.target];
+        if (is_controlled_kind(g.kind) || g.kind == SV_SWAP) p.g.control = phys[g.control];
+        classify(p);
+        pg.push_back(p);
+    }
+    const int m = (int)pg.size();
+
+    // 2. dependencies
+    std::vector<int> last_nd(64, -1);
+    std::vector<std::vector<int>> diag_since(64);
+    for (int i = 0; i < m; i++) {
+        PGate &p = pg[i];
+        for (int a = 0; a < p.nnd; a++) {
+            int q = p.nd[a];
+            if (last_nd[q] >= 0) p.deps.push_back(last_nd[q]);
+            for (int d : diag_since[q]) p.deps.push_back(d);
+        }
+        for (int a = 0; a < p.ndq; a++) {
+            int q = p.dq[a];
+            if (last_nd[q] >= 0) p.deps.push_back(last_nd[q]);
+        }
+        for (int a = 0; a < p.nnd; a++) {
+            last_nd[p.nd[a]] = i;
+            diag_since[p.nd[a]].clear();
+        }
+        for (int a = 0; a < p.ndq; a++) diag_since[p.dq[a]].push_back(i);
+    }
+
+    // 3. passes by list scheduling
+    std::vector<char> done(m, 0);
+    int remaining = m;
+    while (remaining > 0) {
+        bool in_l[64] = {};
+        int cnt = 0;
+        if (n <= k) {
+            for (int q = 0; q < n; q++) in_l[q] = true;
+            cnt = n;
+        } else {
+            for (int q = 0; q < c; q++) in_l[q] = true;
+            cnt = c;
+        }
+        std::vector<int> order;
+        for (int i = 0; i < m; i++) {
+            if (done[i]) continue;
+            const PGate &p = pg[i];
+            bool ready = true;
+            for (int d : p.deps)
+                if (!done[d]) {
+                    ready = false;
+                    break;
+                }
+            if (!ready) continue;
+            int need = 0;
+            for (int a = 0; a < p.nnd; a++) need += !in_l[p.nd[a]];
+            if (cnt + need > k) continue;
+            for (int a = 0; a < p.nnd; a++)
+                if (!in_l[p.nd[a]]) {
+                    in_l[p.nd[a]] = true;
+                    cnt++;
+                }
+            order.push_back(i);
+            done[i] = 1;
+            remaining--;
+        }
+        if (order.empty()) return "internal: planner made no progress";
+        // fill unused slots with the lowest free bits (longer contiguous runs)
+        for (int q = 0; q < n && cnt < k; q++)
+            if (!in_l[q]) {
+                in_l[q] = true;
+                cnt++;
+            }
+
+        TilePass tp;
+        tp.k = k;
+        tp.c = c;
+        tp.ngates = (int)order.size();
+        int slot_of[64];
+        for (int q = 0; q < 64; q++) slot_of[q] = -1;
+        int s = 0;
+        for (int q = 0; q < n; q++)
+            if (in_l[q]) {
+                tp.slot_phys[s] = q;
+                slot_of[q] = s++;
+            }
+        tp.gmask = 0;
+        for (int q = 0; q < n; q++)
+            if (!in_l[q]) tp.gmask |= UINT64_C(1) << q;
+
+        // 4. segments: gates in order, diagonal gates merged into runs
+        struct Seg {
+            bool diag;
+            std::vector<int> g;
+        };
+        std::vector<Seg> segs;
+        for (int i : order) {
+            const PGate &p = pg[i];
+            if (!p.diag) {
+                segs.push_back({false, {i}});
+                continue;
+            }
+            if (!opt.merge_diag) {
+                segs.push_back({true, {i}});
+                continue;
+            }
+            int blocker = -1;
+            for (int sgi = (int)segs.size() - 1; sgi >= 0; sgi--) {
+                if (segs[sgi].diag) continue;
+                if (!commutes_with_gate(p, pg[segs[sgi].g[0]])) {
+                    blocker = sgi;
+                    break;
+                }
+            }
+            int target = -1;
+            for (int sgi = blocker + 1; sgi < (int)segs.size(); sgi++)
+                if (segs[sgi].diag) {
+                    target = sgi;
+                    break;
+                }
+            if (target >= 0)
+                segs[target].g.push_back(i);
+            else
+                segs.push_back({true, {i}});
+        }
+
+        for (const Seg &sg : segs) {
+            TileOp op{};
+            if (!sg.diag) {
+                const sv_gate &g = pg[sg.g[0]].g;
+                if (g.kind == SV_SWAP) {
+                    op.type = TOP_SWAP;
+                    op.slot = slot_of[g.target];
+                    op.cslot = slot_of[g.control];
+                } else {
+                    op.slot = slot_of[g.target];
+                    Mat2 mm = gate_matrix(g);
+                    for (int e = 0; e < 4; e++) {
+                        op.m[2 * e] = mm.re[e];
+                        op.m[2 * e + 1] = mm.im[e];
+                    }
+                    if (g.kind == SV_CU) {
+                        if (slot_of[g.control] >= 0) {
+                            op.type = TOP_GATE_CL;
+                            op.cslot = slot_of[g.control];
+                        } else {
+                            op.type = TOP_GATE_CG;
+                            op.cbit = g.control;
+                        }
+                    } else if (g.kind == SV_H) {
+                        op.type = TOP_H;
+                    } else if (g.kind == SV_X) {
+                        op.type = TOP_X;
+                    } else {
+                        op.type = TOP_GATE;
+                    }
+                }
+                tp.ops.push_back(op);
+                continue;
+            }
+            // merged diagonal run -> phase polynomial over local / global bits
+            std::map<std::tuple<int, int, int>, uint64_t> acc;
+            for (int gi : sg.g) {
+                const sv_gate &g = pg[gi].g;
+                bool exact;
+                uint64_t th = diag_turns64(g, &exact);
+                if (!is_controlled_kind(g.kind)) {
+                    int q = g.target;
+                    if (slot_of[q] >= 0)
+                        acc[{TERM_L, slot_of[q], 0}] += th;
+                    else
+                        acc[{TERM_G, q, 0}] += th;
+                } else {
+                    int q1 = g.control, q2 = g.target;
+                    int s1 = slot_of[q1], s2 = slot_of[q2];
+                    if (s1 >= 0 && s2 >= 0)
+                        acc[{TERM_LL, std::min(s1, s2), std::max(s1, s2)}] += th;
+                    else if (s1 >= 0)
+                        acc[{TERM_LG, s1, q2}] += th;
+                    else if (s2 >= 0)
+                        acc[{TERM_LG, s2, q1}] += th;
+                    else
+                        acc[{TERM_GG, std::min(q1, q2), std::max(q1, q2)}] += th;
+                }
+            }
+            op.type = TOP_DIAG;
+            op.tb = (int)tp.terms.size();
+            for (auto &kv : acc) {
+                if (kv.second == 0) continue;
+                PhaseTerm t{};
+                t.kind = std::get<0>(kv.first);
+                t.a = std::get<1>(kv.first);
+                t.b = std::get<2>(kv.first);
+                t.theta = kv.second;
+                tp.terms.push_back(t);
+            }
+            op.te = (int)tp.terms.size();
+            if (op.te > op.tb) tp.ops.push_back(op);
+        }
+        out->passes.push_back(std::move(tp));
+    }
+    return "";
+}
+
+}  // namespace sv

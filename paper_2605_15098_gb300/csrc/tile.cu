@@ -1,0 +1,330 @@
+// Partitioned execution: tile kernels and the pass driver.
+//
+// One launch per pass.  A persistent grid walks the 2^(n-k) tiles of the
+// pass; each CTA gathers its tile (2^(k-c) chunks of 2^c contiguous
+// amplitudes) into shared memory, applies the pass's whole programme there
+// (the deferred block-by-block execution of Sec. III-B, arxiv 2605.15098),
+// and writes the tile back.  Out-of-tile bits are constants of the tile, so
+// a control on a global qubit is a per-tile branch and every diagonal run
+// reduces to a per-tile phase polynomial over the local bits.
+#include <algorithm>
+#include <type_traits>
+
+#include "common.h"
+#include "plan.h"
+
+namespace sv {
+namespace {
+
+constexpr int kTileThreads = 256;
+
+struct PassArgs {
+    int k, c, nops;
+    int slot_phys[kMaxTileQubits];
+    uint64_t gmask;
+    uint64_t ntiles;
+    const TileOp *ops;
+    const PhaseTerm *terms;
+};
+
+__device__ __forceinline__ uint64_t pdep64(uint64_t v, uint64_t mask) {
+    uint64_t r = 0;
+    for (uint64_t b = 1; mask; b <<= 1) {
+        const uint64_t low = mask & (~mask + 1);
+        if (v & b) r |= low;
+        mask &= mask - 1;
+    }
+    return r;
+}
+
+__device__ __forceinline__ uint32_t insert_bit(uint32_t x, int p, uint32_t v) {
+    return ((x >> p) << (p + 1)) | (v << p) | (x & ((1u << p) - 1));
+}
+
+template <typename R>
+struct Cx {
+    R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ void phase_cs(uint64_t phi, R *c, R *s);
+
+template <>
+__device__ __forceinline__ void phase_cs<double>(uint64_t phi, double *c, double *s) {
+    // e^{2 pi i phi / 2^64} = cos/sin(pi x) with x = phi / 2^63 in [-1, 1)
+    const double x = (double)(int64_t)phi * 0x1p-63;
+    sincospi(x, s, c);
+}
+
+template <>
+__device__ __forceinline__ void phase_cs<float>(uint64_t phi, float *c, float *s) {
+    const float x = (float)(int32_t)(uint32_t)(phi >> 32) * 0x1p-31f;
+    sincospif(x, s, c);
+}
+
+// x / sqrt(2); in single precision 1/sqrt(2) is split into two floats so
+// that the product is rounded once (a rounded constant would shrink the norm
+// by the same factor at every H).
+template <typename R>
+__device__ __forceinline__ R hscale(R x) {
+    if constexpr (sizeof(R) == 4)
+        return fmaf(x, 0.70710677f, x * 1.21016175e-08f);
+    else
+        return x * 0.70710678118654752440084436210485;
+}
+
+// Offset (in amplitudes) of local chunk j of the tile.
+__device__ __forceinline__ uint64_t chunk_offset(const PassArgs &a, uint32_t j) {
+    uint64_t off = 0;
+    for (int b = 0; b < a.k - a.c; b++)
+        if ((j >> b) & 1) off |= UINT64_C(1) << a.slot_phys[a.c + b];
+    return off;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kTileThreads)
+k_tile(R *__restrict__ state, const PassArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sm = reinterpret_cast<R *>(smem_raw);
+    __shared__ uint64_t lin[kMaxTileQubits];
+    __shared__ uint64_t cst;
+    using V = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
+    constexpr int APV = 16 / (2 * sizeof(R));  // amplitudes per 16-byte vector
+    const uint32_t tile_amps = 1u << a.k;
+    const uint32_t nvec = tile_amps / APV;
+    const uint32_t cmask = (1u << a.c) - 1;
+    V *gv = reinterpret_cast<V *>(state);
+    V *svec = reinterpret_cast<V *>(sm);
+
+    for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        const uint64_t base = pdep64(tile, a.gmask);
+        for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x) {
+            const uint32_t i = v * APV;
+            const uint64_t g = base + chunk_offset(a, i >> a.c) + (i & cmask);
+            svec[v] = gv[g / APV];
+        }
+        __syncthreads();
+
+        for (int o = 0; o < a.nops; o++) {
+            const TileOp &op = a.ops[o];
+            const int type = op.type;
+            if (type == TOP_DIAG) {
+                if ((int)threadIdx.x < a.k) {
+                    uint64_t acc = 0;
+                    for (int t = op.tb; t < op.te; t++) {
+                        const PhaseTerm &pt = a.terms[t];
+                        if (pt.a != (int)threadIdx.x) continue;
+                        if (pt.kind == TERM_L) acc += pt.theta;
+                        if (pt.kind == TERM_LG && ((base >> pt.b) & 1)) acc += pt.theta;
+                    }
+                    lin[threadIdx.x] = acc;
+                } else if ((int)threadIdx.x == a.k) {
+                    uint64_t acc = 0;
+                    for (int t = op.tb; t < op.te; t++) {
+                        const PhaseTerm &pt = a.terms[t];
+                        if (pt.kind == TERM_G && ((base >> pt.a) & 1)) acc += pt.theta;
+                        if (pt.kind == TERM_GG && ((base >> pt.a) & 1) && ((base >> pt.b) & 1))
+                            acc += pt.theta;
+                    }
+                    cst = acc;
+                }
+                __syncthreads();
+                for (uint32_t i = threadIdx.x; i < tile_amps; i += blockDim.x) {
+                    uint64_t phi = cst;
+                    for (int b = 0; b < a.k; b++)
+                        if ((i >> b) & 1) phi += lin[b];
+                    for (int t = op.tb; t < op.te; t++) {
+                        const PhaseTerm &pt = a.terms[t];
+                        if (pt.kind == TERM_LL && ((i >> pt.a) & 1) && ((i >> pt.b) & 1))
+                            phi += pt.theta;
+                    }
+                    if (phi) {
+                        R c, s;
+                        phase_cs<R>(phi, &c, &s);
+                        const R re = sm[2 * i], im = sm[2 * i + 1];
+                        sm[2 * i] = re * c - im * s;
+                        sm[2 * i + 1] = re * s + im * c;
+                    }
+                }
+            } else if (type == TOP_SWAP) {
+                const int sa = op.slot, sb = op.cslot;
+                const int lo = sa < sb ? sa : sb, hi = sa < sb ? sb : sa;
+                for (uint32_t p = threadIdx.x; p < tile_amps / 4; p += blockDim.x) {
+                    uint32_t i = insert_bit(p, lo, lo == sa ? 1u : 0u);
+                    i = insert_bit(i, hi, hi == sa ? 1u : 0u);
+                    const uint32_t j = i ^ (1u << sa) ^ (1u << sb);
+                    const R r0 = sm[2 * i], i0 = sm[2 * i + 1];
+                    sm[2 * i] = sm[2 * j];
+                    sm[2 * i + 1] = sm[2 * j + 1];
+                    sm[2 * j] = r0;
+                    sm[2 * j + 1] = i0;
+                }
+            } else {
+                if (type == TOP_GATE_CG && !((base >> op.cbit) & 1)) continue;  // uniform
+                const int t = op.slot;
+                const bool lctl = type == TOP_GATE_CL;
+                const uint32_t npairs = lctl ? tile_amps / 4 : tile_amps / 2;
+                const R m0r = (R)op.m[0], m0i = (R)op.m[1], m1r = (R)op.m[2], m1i = (R)op.m[3];
+                const R m2r = (R)op.m[4], m2i = (R)op.m[5], m3r = (R)op.m[6], m3i = (R)op.m[7];
+                for (uint32_t p = threadIdx.x; p < npairs; p += blockDim.x) {
+                    uint32_t i;
+                    if (lctl) {
+                        const int cs = op.cslot;
+                        if (cs < t)
+                            i = insert_bit(insert_bit(p, cs, 1u), t, 0u);
+                        else
+                            i = insert_bit(insert_bit(p, t, 0u), cs, 1u);
+                    } else {
+                        i = insert_bit(p, t, 0u);
+                    }
+                    const uint32_t j = i | (1u << t);
+                    const R ar = sm[2 * i], ai = sm[2 * i + 1];
+                    const R br = sm[2 * j], bi = sm[2 * j + 1];
+                    R xr, xi, yr, yi;
+                    if (type == TOP_X) {
+                        xr = br; xi = bi; yr = ar; yi = ai;
+                    } else if (type == TOP_H) {
+                        xr = hscale<R>(ar + br); xi = hscale<R>(ai + bi);
+                        yr = hscale<R>(ar - br); yi = hscale<R>(ai - bi);
+                    } else {
+                        xr = m0r * ar - m0i * ai + m1r * br - m1i * bi;
+                        xi = m0r * ai + m0i * ar + m1r * bi + m1i * br;
+                        yr = m2r * ar - m2i * ai + m3r * br - m3i * bi;
+                        yi = m2r * ai + m2i * ar + m3r * bi + m3i * br;
+                    }
+                    sm[2 * i] = xr; sm[2 * i + 1] = xi;
+                    sm[2 * j] = yr; sm[2 * j + 1] = yi;
+                }
+            }
+            __syncthreads();
+        }
+
+        for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x) {
+            const uint32_t i = v * APV;
+            const uint64_t g = base + chunk_offset(a, i >> a.c) + (i & cmask);
+            gv[g / APV] = svec[v];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename R>
+sv_status launch_pass(sv_state *h, const PassArgs &a, const sv_launch_record &meta) {
+    const size_t smem = ((size_t)1 << a.k) * 2 * sizeof(R);
+    static bool configured[2] = {false, false};
+    auto kern = k_tile<R>;
+    const int idx = sizeof(R) == 8;
+    if (!configured[idx]) {
+        SV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        configured[idx] = true;
+    }
+    int per_sm = 0;
+    SV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileThreads, smem));
+    if (per_sm < 1) return fail(SV_ERR_UNSUPPORTED, "tile of %zu bytes does not fit on an SM", smem);
+    const uint64_t grid = std::min<uint64_t>(a.ntiles, (uint64_t)per_sm * h->sm_count);
+    const int slot = prof_begin(h);
+    kern<<<(unsigned)grid, kTileThreads, smem, h->stream>>>(reinterpret_cast<R *>(h->amps), a);
+    SV_CUDA(cudaGetLastError());
+    note_launch();
+    prof_end(h, slot, meta);
+    h->stats.kernels++;
+    return SV_OK;
+}
+
+}  // namespace
+
+sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, const sv_config &cfg) {
+    PlanOptions opt;
+    opt.n = h->n;
+    const bool dbl = h->dt == SV_C128;
+    opt.k = cfg.tile_qubits ? cfg.tile_qubits : (dbl ? 12 : 13);
+    opt.c = cfg.chunk_qubits ? cfg.chunk_qubits : (dbl ? 4 : 5);
+    if (dbl && opt.k > 13) return fail(SV_ERR_ARG, "complex128 tiles hold at most 2^13 amplitudes");
+    if (!dbl && opt.c < 1) opt.c = 1;
+    opt.merge_diag = !(cfg.flags & SV_FLAG_NO_DIAG_MERGE);
+    opt.relabel = !(cfg.flags & SV_FLAG_NO_RELABEL);
+    Plan plan;
+    int phys[64];
+    std::copy(h->phys, h->phys + 64, phys);
+    std::string err = build_plan(gates, opt, phys, &plan);
+    if (!err.empty()) return fail(SV_ERR_ARG, "planner: %s", err.c_str());
+
+    // upload the programme: all passes' ops and terms in one buffer
+    size_t nops = 0, nterms = 0;
+    for (const TilePass &p : plan.passes) {
+        nops += p.ops.size();
+        nterms += p.terms.size();
+    }
+    const size_t ops_bytes = nops * sizeof(TileOp);
+    const size_t terms_off = (ops_bytes + 255) & ~(size_t)255;
+    const size_t total = terms_off + nterms * sizeof(PhaseTerm) + 256;
+    if (total > h->plan_cap) {
+        SV_CUDA(cudaStreamSynchronize(h->stream));
+        if (h->plan_dev) cudaFree(h->plan_dev);
+        if (h->plan_host) cudaFreeHost(h->plan_host);
+        h->plan_dev = h->plan_host = nullptr;
+        h->plan_cap = 0;
+        size_t cap = std::max<size_t>(total * 2, (size_t)1 << 16);
+        if (cudaMalloc(&h->plan_dev, cap) != cudaSuccess ||
+            cudaMallocHost(&h->plan_host, cap) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SV_ERR_OOM, "cannot allocate the pass programme (%zu bytes)", cap);
+        }
+        h->plan_cap = cap;
+    } else {
+        // the previous upload must have finished before the staging is reused
+        SV_CUDA(cudaStreamSynchronize(h->stream));
+    }
+    char *hb = reinterpret_cast<char *>(h->plan_host);
+    TileOp *hops = reinterpret_cast<TileOp *>(hb);
+    PhaseTerm *hterms = reinterpret_cast<PhaseTerm *>(hb + terms_off);
+    size_t oi = 0, ti = 0;
+    for (const TilePass &p : plan.passes) {
+        std::copy(p.ops.begin(), p.ops.end(), hops + oi);
+        std::copy(p.terms.begin(), p.terms.end(), hterms + ti);
+        oi += p.ops.size();
+        ti += p.terms.size();
+    }
+    SV_CUDA(cudaMemcpyAsync(h->plan_dev, h->plan_host, total, cudaMemcpyHostToDevice, h->stream));
+    h->stats.h2d_bytes += (double)total;
+    const TileOp *dops = reinterpret_cast<const TileOp *>(h->plan_dev);
+    const PhaseTerm *dterms =
+        reinterpret_cast<const PhaseTerm *>(reinterpret_cast<char *>(h->plan_dev) + terms_off);
+
+    oi = ti = 0;
+    for (const TilePass &p : plan.passes) {
+        if (!p.ops.empty()) {
+            PassArgs a{};
+            a.k = p.k;
+            a.c = p.c;
+            a.nops = (int)p.ops.size();
+            for (int s = 0; s < p.k; s++) a.slot_phys[s] = p.slot_phys[s];
+            a.gmask = p.gmask;
+            a.ntiles = UINT64_C(1) << (h->n - p.k);
+            a.ops = dops + oi;
+            a.terms = dterms + ti;
+            sv_launch_record meta{};
+            meta.kind = SV_KERNEL_TILE;
+            meta.pass = h->launch_index++;
+            meta.n = h->n;
+            meta.k = p.k;
+            meta.nops = a.nops;
+            meta.ngates = p.ngates;
+            meta.dtype = (int32_t)h->dt;
+            meta.gate_kind = -1;
+            meta.bytes = 2.0 * (double)state_bytes(h);
+            meta.feat = ~p.gmask & ((h->n == 64) ? ~UINT64_C(0) : ((UINT64_C(1) << h->n) - 1));
+            sv_status st = dbl ? launch_pass<double>(h, a, meta) : launch_pass<float>(h, a, meta);
+            if (st != SV_OK) return st;
+            h->stats.passes++;
+            h->stats.touched_bytes += 2.0 * (double)state_bytes(h);
+        }
+        oi += p.ops.size();
+        ti += p.terms.size();
+    }
+    std::copy(phys, phys + 64, h->phys);
+    h->stats.relabels = plan.relabels;
+    return SV_OK;
+}
+
+}  // namespace sv

@@ -1,0 +1,284 @@
+"""Thin ctypes binding of libsv (include/sv.h): same names, argument marshalling only.
+
+Every step of the simulation runs in the CUDA library; this module converts
+Python / NumPy / PyTorch arguments into pointers and sizes and turns error
+codes into exceptions.  It fails loudly (``LibraryMissing``) when libsv.so has
+not been built: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .circuits import GATE_DTYPE
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsv.so")
+
+SV_C64, SV_C128 = 0, 1
+SV_OK, SV_ERR_ARG, SV_ERR_OOM, SV_ERR_CUDA, SV_ERR_TIMEOUT, SV_ERR_STATE, SV_ERR_UNSUPPORTED = (
+    0, -1, -2, -3, -4, -5, -6)
+SV_MODE_AUTO, SV_MODE_PERGATE, SV_MODE_PARTITIONED, SV_MODE_FUSED = 0, 1, 2, 3
+SV_FLAG_NO_DIAG_MERGE, SV_FLAG_PAPER_SWAP, SV_FLAG_NO_RELABEL = 1, 2, 4
+SV_PLANNER_GREEDY, SV_PLANNER_LEARNED = 0, 1
+
+EXPORTS = (
+    "sv_create", "sv_create_on", "sv_destroy", "sv_reset", "sv_info", "sv_qubit_map",
+    "sv_apply_circuit", "sv_last_stats", "sv_probabilities", "sv_probabilities_device",
+    "sv_argmax", "sv_sample", "sv_copy_out", "sv_copy_in", "sv_last_error", "sv_version",
+    "sv_profile", "sv_profile_read", "sv_launch_count",
+)
+SV_KERNEL_PERGATE, SV_KERNEL_TILE, SV_KERNEL_REMAP, SV_KERNEL_FUSED = 0, 1, 2, 3
+
+
+class LibraryMissing(RuntimeError):
+    pass
+
+
+class SvError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libsv error {code}: {msg}")
+        self.code = code
+
+
+class sv_config(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("tile_qubits", ctypes.c_int32),
+                ("chunk_qubits", ctypes.c_int32), ("fuse_qubits", ctypes.c_int32),
+                ("planner", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 10)]
+
+
+class sv_stats(ctypes.Structure):
+    _fields_ = [("gates", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("remaps", ctypes.c_int32), ("kernels", ctypes.c_int32),
+                ("relabels", ctypes.c_int32), ("fused_blocks", ctypes.c_int32),
+                ("sweep_bytes", ctypes.c_double), ("touched_bytes", ctypes.c_double),
+                ("h2d_bytes", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class sv_launch_record(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pass_", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("nops", ctypes.c_int32), ("ngates", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("gate_kind", ctypes.c_int32),
+                ("bytes", ctypes.c_double), ("ms", ctypes.c_double), ("feat", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise LibraryMissing(f"{LIB_PATH} not built; run paper_2605_15098_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, u64, i32, sz, dp = (ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_size_t,
+                            ctypes.POINTER(ctypes.c_double))
+    sig = {
+        "sv_create": [i32, i32, ctypes.POINTER(vp)],
+        "sv_create_on": [i32, i32, vp, sz, vp, ctypes.POINTER(vp)],
+        "sv_destroy": [vp],
+        "sv_reset": [vp],
+        "sv_info": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(vp)],
+        "sv_qubit_map": [vp, vp],
+        "sv_apply_circuit": [vp, vp, sz, ctypes.POINTER(sv_config)],
+        "sv_last_stats": [vp, ctypes.POINTER(sv_stats)],
+        "sv_probabilities": [vp, u64, vp],
+        "sv_probabilities_device": [vp, u64, vp],
+        "sv_argmax": [vp, u64, ctypes.POINTER(u64), dp],
+        "sv_sample": [vp, u64, vp, sz, vp],
+        "sv_copy_out": [vp, vp],
+        "sv_copy_in": [vp, vp],
+        "sv_profile": [vp, i32],
+        "sv_profile_read": [vp, vp, sz, ctypes.POINTER(sz)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = i32
+    L.sv_last_error.restype = ctypes.c_char_p
+    L.sv_version.restype = ctypes.c_char_p
+    L.sv_launch_count.restype = ctypes.c_uint64
+    L.sv_launch_count.argtypes = []
+    _lib = L
+    return L
+
+
+def _check(code: int) -> None:
+    if code != SV_OK:
+        raise SvError(code, lib().sv_last_error().decode())
+
+
+def sv_version() -> str:
+    return lib().sv_version().decode()
+
+
+def sv_last_error() -> str:
+    return lib().sv_last_error().decode()
+
+
+def make_config(mode=SV_MODE_AUTO, tile_qubits=0, chunk_qubits=0, fuse_qubits=0,
+                planner=SV_PLANNER_GREEDY, flags=0) -> sv_config:
+    return sv_config(mode, tile_qubits, chunk_qubits, fuse_qubits, planner, flags)
+
+
+# ---- handle-level functions (same names as the C ABI) ------------------------
+def sv_create(n: int, dtype: int = SV_C64) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sv_create(n, dtype, ctypes.byref(h)))
+    return h.value
+
+
+def sv_create_on(n: int, dtype: int, dev_ptr: int, nbytes: int, stream: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().sv_create_on(n, dtype, ctypes.c_void_p(dev_ptr), nbytes,
+                              ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h.value
+
+
+def sv_destroy(h: int) -> None:
+    _check(lib().sv_destroy(ctypes.c_void_p(h)))
+
+
+def sv_reset(h: int) -> None:
+    _check(lib().sv_reset(ctypes.c_void_p(h)))
+
+
+def sv_info(h: int) -> tuple[int, int, int]:
+    n, dt, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_void_p()
+    _check(lib().sv_info(ctypes.c_void_p(h), ctypes.byref(n), ctypes.byref(dt), ctypes.byref(p)))
+    return n.value, dt.value, p.value
+
+
+def sv_qubit_map(h: int) -> list[int]:
+    n = sv_info(h)[0]
+    out = np.zeros(n, dtype=np.int32)
+    _check(lib().sv_qubit_map(ctypes.c_void_p(h), out.ctypes.data))
+    return out.tolist()
+
+
+def sv_apply_circuit(h: int, gates: np.ndarray, cfg: sv_config | None = None) -> None:
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    _check(lib().sv_apply_circuit(ctypes.c_void_p(h), g.ctypes.data if g.size else None, g.size,
+                                  ctypes.byref(cfg) if cfg is not None else None))
+
+
+def sv_last_stats(h: int) -> dict:
+    st = sv_stats()
+    _check(lib().sv_last_stats(ctypes.c_void_p(h), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def sv_probabilities(h: int, qubit_mask: int) -> np.ndarray:
+    out = np.empty(1 << bin(qubit_mask).count("1"), dtype=np.float64)
+    _check(lib().sv_probabilities(ctypes.c_void_p(h), qubit_mask, out.ctypes.data))
+    return out
+
+
+def sv_probabilities_device(h: int, qubit_mask: int, dev_ptr: int) -> None:
+    _check(lib().sv_probabilities_device(ctypes.c_void_p(h), qubit_mask, ctypes.c_void_p(dev_ptr)))
+
+
+def sv_argmax(h: int, qubit_mask: int) -> tuple[int, float]:
+    idx, p = ctypes.c_uint64(), ctypes.c_double()
+    _check(lib().sv_argmax(ctypes.c_void_p(h), qubit_mask, ctypes.byref(idx), ctypes.byref(p)))
+    return idx.value, p.value
+
+
+def sv_sample(h: int, qubit_mask: int, u: np.ndarray) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.empty(u.size, dtype=np.uint64)
+    _check(lib().sv_sample(ctypes.c_void_p(h), qubit_mask, u.ctypes.data if u.size else None,
+                           u.size, out.ctypes.data if u.size else None))
+    return out
+
+
+def sv_copy_out(h: int) -> np.ndarray:
+    n, dt, _ = sv_info(h)
+    out = np.empty(1 << n, dtype=np.complex128 if dt == SV_C128 else np.complex64)
+    _check(lib().sv_copy_out(ctypes.c_void_p(h), out.ctypes.data))
+    return out
+
+
+def sv_copy_in(h: int, amps: np.ndarray) -> None:
+    n, dt, _ = sv_info(h)
+    a = np.ascontiguousarray(amps, dtype=np.complex128 if dt == SV_C128 else np.complex64)
+    assert a.size == 1 << n
+    _check(lib().sv_copy_in(ctypes.c_void_p(h), a.ctypes.data))
+
+
+def sv_profile(h: int, enable: bool) -> None:
+    _check(lib().sv_profile(ctypes.c_void_p(h), 1 if enable else 0))
+
+
+def sv_profile_read(h: int, cap: int = 1 << 16) -> list[dict]:
+    buf = (sv_launch_record * cap)()
+    cnt = ctypes.c_size_t()
+    _check(lib().sv_profile_read(ctypes.c_void_p(h), buf, cap, ctypes.byref(cnt)))
+    return [buf[i].as_dict() for i in range(min(cap, cnt.value))]
+
+
+def sv_launch_count() -> int:
+    return int(lib().sv_launch_count())
+
+
+class State:
+    """Owning wrapper: ``with State(n, SV_C128) as s: s.apply(gates)``."""
+
+    def __init__(self, n: int, dtype: int = SV_C64, tensor=None, stream=None):
+        self.n, self.dtype = n, dtype
+        self._tensor = tensor
+        if tensor is not None:  # adopt a torch CUDA buffer and stream
+            nbytes = tensor.numel() * tensor.element_size()
+            sptr = stream.cuda_stream if stream is not None else 0
+            self.h = sv_create_on(n, dtype, tensor.data_ptr(), nbytes, sptr)
+        else:
+            self.h = sv_create(n, dtype)
+
+    def apply(self, gates, cfg=None):
+        sv_apply_circuit(self.h, gates, cfg)
+        return self
+
+    def stats(self):
+        return sv_last_stats(self.h)
+
+    def probabilities(self, mask):
+        return sv_probabilities(self.h, mask)
+
+    def argmax(self, mask):
+        return sv_argmax(self.h, mask)
+
+    def sample(self, mask, u):
+        return sv_sample(self.h, mask, u)
+
+    def amplitudes(self):
+        return sv_copy_out(self.h)
+
+    def reset(self):
+        sv_reset(self.h)
+
+    def close(self):
+        if self.h:
+            sv_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,77 @@
+"""The C ABI library loads and exports every symbol include/sv.h declares.
+
+CPU only: the library is loaded (a CUDA driver is not needed for that) and
+only entry points that reject their arguments on the host are called.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2605_15098_gb300 import build as B
+from paper_2605_15098_gb300 import circuits as C
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def svlib():
+    B.build()
+    from paper_2605_15098_gb300 import sv
+    return sv
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z_0-9]*\s*\**\s*(sv_[a-z_0-9]+)\s*\(",
+                            text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_boundary():
+    names = declared_functions()
+    for required in ("sv_create", "sv_apply_circuit", "sv_probabilities", "sv_sample",
+                     "sv_destroy", "sv_argmax"):
+        assert required in names
+
+
+def test_exports_every_declared_symbol(svlib):
+    lib = svlib.lib()
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} not exported"
+    assert set(svlib.EXPORTS) <= set(declared_functions())
+
+
+def test_version(svlib):
+    assert "sm_103a" in svlib.sv_version()
+
+
+def test_gate_record_layout(svlib):
+    assert C.GATE_DTYPE.itemsize == 96
+    assert ctypes.sizeof(svlib.sv_config) == 64
+
+
+def test_host_validation_rejects_without_device(svlib):
+    lib = svlib.lib()
+    h = ctypes.c_void_p()
+    assert lib.sv_create(0, 0, ctypes.byref(h)) == svlib.SV_ERR_ARG
+    assert "outside" in svlib.sv_last_error()
+    assert lib.sv_create(35, 0, ctypes.byref(h)) == svlib.SV_ERR_ARG
+    assert lib.sv_create(5, 7, ctypes.byref(h)) == svlib.SV_ERR_ARG
+    assert lib.sv_create(5, 0, None) == svlib.SV_ERR_ARG
+    assert lib.sv_destroy(None) == svlib.SV_OK
+    assert lib.sv_apply_circuit(None, None, 0, None) == svlib.SV_ERR_ARG
+    assert lib.sv_create_on(5, 0, None, 0, None, ctypes.byref(h)) == svlib.SV_ERR_ARG
+    g = C.gates([C.h(0)])
+    assert lib.sv_apply_circuit(None, g.ctypes.data, 1, None) == svlib.SV_ERR_ARG
+    # misaligned adopted buffer is refused before any CUDA call
+    assert lib.sv_create_on(5, 0, ctypes.c_void_p(16), 1 << 20, None,
+                            ctypes.byref(h)) == svlib.SV_ERR_ARG
+    assert "aligned" in svlib.sv_last_error()
