@@ -192,6 +192,33 @@ sv_status sv_probabilities(sv_handle h, uint64_t qubit_mask, double *host_out);
  * returns without synchronising. */
 sv_status sv_probabilities_device(sv_handle h, uint64_t qubit_mask, double *dev_out);
 
+/* Allocation-free variant of sv_probabilities_device.  The paper has no
+ * counterpart; it exists for callers that cannot call cudaMalloc when they
+ * read a state out (a runtime that reserves all device memory up front and
+ * forbids further allocation, or code that must not take the device-wide
+ * synchronisation cudaMalloc/cudaFree may cause).
+ *   dev_amps  the state, 2^n amplitudes of dtype dt in physical order
+ *             (e.g. the buffer of sv_info), 16-byte aligned, read only;
+ *   host_phys_of_logical  n ints, the physical bit of each logical qubit
+ *             (sv_qubit_map), or NULL for the identity;
+ *   dev_out   2^popcount(mask) doubles, caller-owned device memory;
+ *   cuda_stream  stream the kernels are enqueued on (NULL = legacy default);
+ *             the call returns without synchronising.
+ * Partial sums live in a fixed 1 MiB + 8 KiB device array compiled into
+ * the library (held by every GPU that loads it until the process exits);
+ * it holds at most 2^17 partial sums, and the reduction is split so that it
+ * fits for every mask of up to 30 qubits.  The first call on each device
+ * looks the array's address up (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the array and leave their partial sums in it; nothing needs clearing, but
+ * calls that overlap on the GPU race on it and must be ordered by the
+ * caller.  Allocates no memory (no cudaMalloc / cudaFree).  Errors:
+ * SV_ERR_ARG (NULL pointer, n outside 1..34, mask empty, beyond n or over
+ * 30 qubits, map not a permutation, misaligned state), SV_ERR_CUDA. */
+sv_status sv_marginal_noalloc(const void *dev_amps, int n, sv_dtype dt,
+                              const int *host_phys_of_logical, uint64_t qubit_mask,
+                              double *dev_out, void *cuda_stream);
+
 /* Most probable outcome of the marginal over `qubit_mask` (lowest index
  * among exact ties) and its probability (p_out may be NULL). */
 sv_status sv_argmax(sv_handle h, uint64_t qubit_mask, uint64_t *host_idx,

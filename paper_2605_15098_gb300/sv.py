@@ -28,7 +28,7 @@ EXPORTS = (
     "sv_create", "sv_create_on", "sv_destroy", "sv_reset", "sv_info", "sv_qubit_map",
     "sv_apply_circuit", "sv_last_stats", "sv_probabilities", "sv_probabilities_device",
     "sv_argmax", "sv_sample", "sv_copy_out", "sv_copy_in", "sv_last_error", "sv_version",
-    "sv_profile", "sv_profile_read", "sv_launch_count",
+    "sv_profile", "sv_profile_read", "sv_launch_count", "sv_marginal_noalloc",
 )
 SV_KERNEL_PERGATE, SV_KERNEL_TILE, SV_KERNEL_REMAP, SV_KERNEL_FUSED = 0, 1, 2, 3
 
@@ -99,6 +99,7 @@ def lib() -> ctypes.CDLL:
         "sv_copy_out": [vp, vp],
         "sv_copy_in": [vp, vp],
         "sv_profile": [vp, i32],
+        "sv_marginal_noalloc": [vp, i32, i32, vp, u64, vp, vp],
         "sv_profile_read": [vp, vp, sz, ctypes.POINTER(sz)],
     }
     for name, args in sig.items():
@@ -186,6 +187,17 @@ def sv_probabilities(h: int, qubit_mask: int) -> np.ndarray:
 
 def sv_probabilities_device(h: int, qubit_mask: int, dev_ptr: int) -> None:
     _check(lib().sv_probabilities_device(ctypes.c_void_p(h), qubit_mask, ctypes.c_void_p(dev_ptr)))
+
+
+def sv_marginal_noalloc(dev_amps: int, n: int, dtype: int, phys: list[int] | None,
+                        qubit_mask: int, dev_out: int, stream: int = 0) -> None:
+    """Allocation-free marginal of a caller-owned state buffer (see include/sv.h)."""
+    pm = None
+    if phys is not None:
+        arr = np.ascontiguousarray(phys, dtype=np.int32)
+        pm = arr.ctypes.data
+    _check(lib().sv_marginal_noalloc(ctypes.c_void_p(dev_amps), n, dtype, pm, qubit_mask,
+                                     ctypes.c_void_p(dev_out), ctypes.c_void_p(stream)))
 
 
 def sv_argmax(h: int, qubit_mask: int) -> tuple[int, float]:
