@@ -281,6 +281,10 @@ def run_ours(args, world, rank, local):
     value = world * args.steps / (max_ms / 1e3)
 
     tile = [r for r in recs if r["kind"] == sv.SV_KERNEL_TILE]
+    t2n = sum(1 for r in tile if r["gate_kind"] == -2)
+    kname, ksrc = (("k_tile2 (register-stage tile pass)", "paper_2605_15098_gb300/csrc/tile2.cu")
+                   if t2n * 2 >= len(tile) else
+                   ("k_tile (generic tile pass)", "paper_2605_15098_gb300/csrc/tile.cu"))
     tile_ms = [r["ms"] for r in tile]
     tile_avg_ms = sum(tile_ms) / len(tile_ms) if tile_ms else float("nan")
     launch_bytes = 2.0 * state_bytes
@@ -310,10 +314,10 @@ def run_ours(args, world, rank, local):
         },
         "hbm_gbs_algorithmic": alg_gbs,
         "roofline": {
-            "kernel": "k_tile (tile pass)", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak,
             "peak_kind": peak_kind, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
-            "traffic": traffic_for("paper_2605_15098_gb300/csrc/tile.cu", f"qpe{n}_{args.dtype}"),
+            "traffic": traffic_for(ksrc, f"qpe{n}_{args.dtype}"),
             "algorithmic_bytes_per_launch": launch_bytes, "launches": len(tile_ms),
             "avg_launch_ms": tile_avg_ms, "share_of_step_time": kern_share,
         },

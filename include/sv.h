@@ -103,7 +103,9 @@ enum {
                                    remap passes with LRU eviction, as the
                                    paper does, instead of gathering them
                                    into the tile                               */
-    SV_FLAG_NO_RELABEL = 4      /* execute SWAP gates as data movement        */
+    SV_FLAG_NO_RELABEL = 4,     /* execute SWAP gates as data movement        */
+    SV_FLAG_GENERIC_TILE = 8    /* use the generic shared-memory tile kernel
+                                   for every pass (no register stages)        */
 };
 
 /* Planner choice for partitioned modes. */
@@ -279,6 +281,18 @@ sv_status sv_profile_read(sv_handle h, sv_launch_record *host_out, size_t cap, s
 uint64_t sv_launch_count(void);
 
 /* ---- diagnostics ------------------------------------------------------ */
+
+/* Describe, as JSON text, the programme sv_apply_circuit would run in a
+ * partitioned mode for n qubits of dtype dt, starting from the qubit map
+ * host_phys_of_logical (NULL = identity): the passes (tile qubits, gathered
+ * physical bits, gate steps, merged diagonal terms) and, per pass, the
+ * register-stage programme or the reason the generic tile kernel is used.
+ * Host only: it plans but calls no CUDA function.  Writes at most cap bytes
+ * (NUL-terminated) to host_buf and the full length to *len.  The planner is
+ * the paper's partitioning (Sec. III-B); the format is this library's. */
+sv_status sv_plan_export(int n, sv_dtype dt, const int *host_phys_of_logical,
+                         const sv_gate *host_gates, size_t m, const sv_config *cfg,
+                         char *host_buf, size_t cap, size_t *len);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *sv_last_error(void);

@@ -69,6 +69,8 @@ struct sv_state {
     void *plan_host = nullptr;    // pinned host staging for the programme
     size_t plan_host_cap = 0;
     sv_stats stats{};
+    void *t2_tables = nullptr;    // FP64-generated phase tables (register-stage kernel)
+    int *t2_err = nullptr;        // device flag: a bounded wait gave up
     // timing recorder
     bool profiling = false;
     struct Pending {
@@ -111,7 +113,14 @@ sv_status argmax_device(sv_state *h, const double *dev_p, uint64_t len,
 sv_status sample_device(sv_state *h, const double *dev_p, uint64_t len,
                         const double *host_u, size_t shots, uint64_t *host_out);
 
-// ---- partitioned path (planner.cpp, tile.cu) ----------------------------------
+// ---- partitioned path (planner.cpp, tile.cu, tile2.cu) -------------------------
+struct T2Pass;
+struct T2Device;
+size_t t2_smem_bytes();
+sv_status t2_prepare(sv_state *h);
+sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta);
+// SV_ERR_TIMEOUT if a kernel of this handle reported a bounded wait that gave up.
+sv_status check_device_flag(sv_state *h);
 sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates_logical,
                             const sv_config &cfg);
 

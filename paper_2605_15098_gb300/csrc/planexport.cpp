@@ -1,0 +1,188 @@
+// sv_plan_export: the programme the partitioned path would run, as JSON.
+// Host only (no CUDA call), for inspection and for host-side tests that
+// execute the exported programme and compare it with the oracle.
+#include <cinttypes>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "common.h"
+#include "plan.h"
+#include "stagecomp.h"
+
+namespace sv {
+namespace {
+
+struct J {
+    std::string s;
+    void raw(const char *t) { s += t; }
+    void num(long long v) { s += std::to_string(v); }
+    void u64(uint64_t v) { s += std::to_string(v); }
+    void dbl(double v) {
+        char b[40];
+        snprintf(b, sizeof b, "%.17g", v);
+        s += b;
+    }
+    template <typename T>
+    void arr(const T *p, int n) {
+        s += "[";
+        for (int i = 0; i < n; i++) {
+            if (i) s += ",";
+            s += std::to_string(p[i]);
+        }
+        s += "]";
+    }
+};
+
+void put_t2(J &j, const T2Pass &t) {
+    j.raw("{\"ins\":[");
+    for (size_t i = 0; i < t.ins.size(); i++) {
+        const T2Ins &in = t.ins[i];
+        if (i) j.raw(",");
+        j.raw("{\"op\":"); j.num(in.op);
+        j.raw(",\"cls\":"); j.num(in.cls);
+        j.raw(",\"idx\":"); j.num(in.idx);
+        j.raw(",\"ccls\":"); j.num(in.ccls);
+        j.raw(",\"cidx\":"); j.num(in.cidx);
+        j.raw(",\"e0\":"); j.num(in.e0);
+        j.raw(",\"e1\":"); j.num(in.e1);
+        j.raw(",\"aux\":"); j.num(in.aux);
+        j.raw("}");
+    }
+    j.raw("],\"stages\":[");
+    for (size_t i = 0; i < t.stages.size(); i++) {
+        if (i) j.raw(",");
+        int tb[13];
+        for (int e = 0; e < 13; e++) tb[e] = t.stages[i].tb[e];
+        j.arr(tb, 13);
+    }
+    j.raw("],\"mats\":[");
+    for (size_t i = 0; i < t.mats.size(); i++) {
+        if (i) j.raw(",");
+        j.raw("[");
+        for (int e = 0; e < 8; e++) {
+            if (e) j.raw(",");
+            j.dbl(t.mats[i].m[e]);
+        }
+        j.raw("]");
+    }
+    j.raw("],\"factors\":[");
+    for (size_t i = 0; i < t.factors.size(); i++) {
+        const T2Factor &f = t.factors[i];
+        uint32_t w0;
+        std::memcpy(&w0, &f.w0, sizeof w0);
+        int32_t row;
+        std::memcpy(&row, &f.c0, sizeof row);
+        if (i) j.raw(",");
+        j.raw("{\"w0\":"); j.u64(w0);
+        j.raw(",\"run\":"); j.num(f.run);
+        j.raw(",\"row\":"); j.num(row);
+        j.raw(",\"c\":["); j.dbl(f.c0); j.raw(","); j.dbl(f.c1); j.raw("]}");
+    }
+    j.raw("],\"stat\":");
+    j.arr(t.stat.data(), (int)t.stat.size());
+    j.raw(",\"tterms\":[");
+    for (size_t i = 0; i < t.tterms.size(); i++) {
+        const T2TileTerm &tt = t.tterms[i];
+        if (i) j.raw(",");
+        j.raw("["); j.num(tt.run); j.raw(","); j.num(tt.tb); j.raw(","); j.num(tt.g0); j.raw(",");
+        j.num(tt.g1); j.raw(","); j.u64(tt.theta); j.raw("]");
+    }
+    j.raw("],\"nruns\":"); j.num(t.nruns);
+    j.raw(",\"n_h\":"); j.num(t.n_h);
+    j.raw("}");
+}
+
+}  // namespace
+}  // namespace sv
+
+using namespace sv;
+
+extern "C" sv_status sv_plan_export(int n, sv_dtype dt, const int *host_phys_of_logical,
+                                    const sv_gate *host_gates, size_t m, const sv_config *cfg,
+                                    char *host_buf, size_t cap, size_t *len) {
+    clear_error();
+    if (!len || (cap && !host_buf) || (m && !host_gates)) return fail(SV_ERR_ARG, "NULL argument");
+    if (n < 1 || n > 34) return fail(SV_ERR_ARG, "n=%d outside 1..34", n);
+    if (dt != SV_C64 && dt != SV_C128) return fail(SV_ERR_ARG, "unknown dtype %d", (int)dt);
+    for (size_t i = 0; i < m; i++) {
+        std::string why = check_gate(n, host_gates[i]);
+        if (!why.empty()) return fail(SV_ERR_ARG, "gate %zu: %s", i, why.c_str());
+    }
+    sv_config c{};
+    if (cfg) c = *cfg;
+    const bool dbl = dt == SV_C128;
+    PlanOptions opt;
+    opt.n = n;
+    opt.k = c.tile_qubits ? c.tile_qubits : (dbl ? 12 : 13);
+    opt.c = c.chunk_qubits ? c.chunk_qubits : (dbl ? 4 : 5);
+    opt.merge_diag = !(c.flags & SV_FLAG_NO_DIAG_MERGE);
+    opt.relabel = !(c.flags & SV_FLAG_NO_RELABEL);
+    int phys[64];
+    for (int q = 0; q < 64; q++) phys[q] = q;
+    if (host_phys_of_logical)
+        for (int q = 0; q < n; q++) phys[q] = host_phys_of_logical[q];
+    Plan plan;
+    std::vector<sv_gate> gl(host_gates, host_gates + m);
+    std::string err = build_plan(gl, opt, phys, &plan);
+    if (!err.empty()) return fail(SV_ERR_ARG, "planner: %s", err.c_str());
+    const bool allow_t2 = !dbl && !(c.flags & SV_FLAG_GENERIC_TILE);
+    J j;
+    j.raw("{\"n\":"); j.num(n);
+    j.raw(",\"relabels\":"); j.num(plan.relabels);
+    j.raw(",\"phys\":"); j.arr(phys, n);
+    j.raw(",\"passes\":[");
+    bool first = true;
+    for (const TilePass &p : plan.passes) {
+        if (!first) j.raw(",");
+        first = false;
+        j.raw("{\"k\":"); j.num(p.k);
+        j.raw(",\"c\":"); j.num(p.c);
+        j.raw(",\"ngates\":"); j.num(p.ngates);
+        j.raw(",\"gmask\":"); j.u64(p.gmask);
+        j.raw(",\"slot_phys\":"); j.arr(p.slot_phys, p.k);
+        j.raw(",\"ops\":[");
+        for (size_t i = 0; i < p.ops.size(); i++) {
+            const TileOp &op = p.ops[i];
+            if (i) j.raw(",");
+            j.raw("{\"type\":"); j.num(op.type);
+            j.raw(",\"slot\":"); j.num(op.slot);
+            j.raw(",\"cslot\":"); j.num(op.cslot);
+            j.raw(",\"cbit\":"); j.num(op.cbit);
+            j.raw(",\"tb\":"); j.num(op.tb);
+            j.raw(",\"te\":"); j.num(op.te);
+            j.raw(",\"m\":[");
+            for (int e = 0; e < 8; e++) {
+                if (e) j.raw(",");
+                j.dbl(op.m[e]);
+            }
+            j.raw("]}");
+        }
+        j.raw("],\"terms\":[");
+        for (size_t i = 0; i < p.terms.size(); i++) {
+            if (i) j.raw(",");
+            j.raw("["); j.num(p.terms[i].kind); j.raw(","); j.num(p.terms[i].a); j.raw(",");
+            j.num(p.terms[i].b); j.raw(","); j.u64(p.terms[i].theta); j.raw("]");
+        }
+        j.raw("]");
+        T2Pass t2;
+        std::string why = allow_t2 && !p.ops.empty() ? compile_t2(p, &t2) : "disabled";
+        if (why.empty()) {
+            j.raw(",\"kernel\":\"t2\",\"t2\":");
+            put_t2(j, t2);
+        } else {
+            j.raw(",\"kernel\":\"generic\",\"why\":\"");
+            j.raw(why.c_str());
+            j.raw("\"");
+        }
+        j.raw("}");
+    }
+    j.raw("]}");
+    *len = j.s.size();
+    if (cap) {
+        size_t k = std::min(cap - 1, j.s.size());
+        std::memcpy(host_buf, j.s.data(), k);
+        host_buf[k] = 0;
+    }
+    return SV_OK;
+}

@@ -1,0 +1,276 @@
+// Stage compiler: tile pass (plan.h) -> register-stage programme (tileprog.h).
+//
+// Layouts are chosen greedily: a stage starts at the first gate that the
+// previous layout cannot execute and takes as register bits the first four
+// new target bits that the following non-diagonal gates need.  Tile bit 0 is
+// always register bit 0 and tile bits 1..3 are always lane bits 0..2 (gates
+// on them use shuffles); every other target must be a register bit.  The
+// remaining tile bits fill lane bits 3..4 and the warp bits.  Diagonal runs
+// are compiled against the layout of the stage that executes them.
+#include <cmath>
+#include <cstring>
+#include <tuple>
+#include <map>
+#include <string>
+
+#include "common.h"
+#include "plan.h"
+#include "stagecomp.h"
+
+namespace sv {
+namespace {
+
+uint32_t turns32(uint64_t t64) { return (uint32_t)((t64 + (UINT64_C(1) << 31)) >> 32); }
+
+struct Layout {
+    int reg[kT2RegBits];  // tile bit of register bit j
+    int lane[5];          // tile bit of lane bit l
+    int warp[3];          // tile bit of warp bit w
+    int cls[kT2Qubits];   // T2C_REG / T2C_LANE / T2C_THREAD (warp)
+    int pos[kT2Qubits];   // register bit, or thread bit (lane l -> l, warp w -> 5 + w)
+
+    void index() {
+        for (int j = 0; j < kT2RegBits; j++) {
+            cls[reg[j]] = T2C_REG;
+            pos[reg[j]] = j;
+        }
+        for (int l = 0; l < 5; l++) {
+            cls[lane[l]] = T2C_LANE;
+            pos[lane[l]] = l;
+        }
+        for (int w = 0; w < 3; w++) {
+            cls[warp[w]] = T2C_THREAD;
+            pos[warp[w]] = 5 + w;
+        }
+    }
+    int thread_tile_bit(int t) const { return t < 5 ? lane[t] : warp[t - 5]; }
+};
+
+bool is_gate_op(int type) {
+    return type == TOP_GATE || type == TOP_GATE_CL || type == TOP_GATE_CG || type == TOP_H ||
+           type == TOP_X;
+}
+
+Layout choose_layout(const TilePass &tp, int from) {
+    Layout L{};
+    bool used[kT2Qubits] = {};
+    L.reg[0] = 0;
+    used[0] = true;
+    for (int l = 0; l < 3; l++) {
+        L.lane[l] = 1 + l;
+        used[1 + l] = true;
+    }
+    int nreg = 1, nlane = 3, nwarp = 0;
+    for (size_t i = from; i < tp.ops.size() && nreg < kT2RegBits; i++) {
+        const TileOp &op = tp.ops[i];
+        if (!is_gate_op(op.type)) continue;
+        const int t = op.slot;
+        if (used[t]) continue;
+        L.reg[nreg++] = t;
+        used[t] = true;
+    }
+    for (int t = 0; t < kT2Qubits; t++) {
+        if (used[t]) continue;
+        if (nreg < kT2RegBits)
+            L.reg[nreg++] = t;
+        else if (nlane < 5)
+            L.lane[nlane++] = t;
+        else
+            L.warp[nwarp++] = t;
+        used[t] = true;
+    }
+    L.index();
+    return L;
+}
+
+bool executable(const Layout &L, const TileOp &op) {
+    if (!is_gate_op(op.type)) return true;
+    return L.cls[op.slot] == T2C_REG || (op.slot >= 1 && op.slot <= 3);
+}
+
+}  // namespace
+
+std::string compile_t2(const TilePass &tp, T2Pass *out) {
+    *out = T2Pass{};
+    if (tp.k != kT2Qubits) return "tile is not 2^13 amplitudes";
+    if (tp.c < 4) return "chunk smaller than 16 amplitudes";
+    for (const TileOp &op : tp.ops)
+        if (op.type == TOP_SWAP) return "in-tile SWAP";
+    int nruns = 0;
+    for (const TileOp &op : tp.ops) nruns += op.type == TOP_DIAG;
+    if (nruns > kT2MaxRuns) return "too many diagonal runs";
+    out->k = tp.k;
+    out->c = tp.c;
+    for (int s = 0; s < tp.k; s++) out->slot_phys[s] = tp.slot_phys[s];
+    out->gmask = tp.gmask;
+    out->ngates = tp.ngates;
+    out->nruns = nruns;
+
+    auto emit_stage = [&](const Layout &L) {
+        T2Stage st{};
+        for (int j = 0; j < kT2RegBits; j++) st.tb[j] = (int8_t)L.reg[j];
+        for (int l = 0; l < 5; l++) st.tb[5 + l] = (int8_t)L.lane[l];
+        for (int w = 0; w < 3; w++) st.tb[10 + w] = (int8_t)L.warp[w];
+        T2Ins in{};
+        in.op = T2_STAGE;
+        in.aux = (int32_t)out->stages.size();
+        out->stages.push_back(st);
+        out->ins.push_back(in);
+    };
+
+    Layout L = choose_layout(tp, 0);
+    emit_stage(L);
+    int run = 0;
+    for (size_t i = 0; i < tp.ops.size(); i++) {
+        const TileOp &op = tp.ops[i];
+        if (!executable(L, op)) {
+            L = choose_layout(tp, (int)i);
+            emit_stage(L);
+        }
+        if (is_gate_op(op.type)) {
+            T2Ins in{};
+            in.op = (int8_t)(op.type == TOP_H ? T2_H : op.type == TOP_X ? T2_X : T2_GATE);
+            in.cls = (int8_t)L.cls[op.slot];
+            in.idx = (int8_t)L.pos[op.slot];
+            in.ccls = T2C_NONE;
+            if (op.type == TOP_GATE_CL) {
+                const int c = op.cslot;
+                in.ccls = (int8_t)(L.cls[c] == T2C_REG ? T2C_REG : T2C_THREAD);
+                in.cidx = (int16_t)L.pos[c];
+            } else if (op.type == TOP_GATE_CG) {
+                in.ccls = T2C_GLOBAL;
+                in.cidx = (int16_t)op.cbit;
+            }
+            if (in.op == T2_GATE) {
+                T2Mat m{};
+                for (int e = 0; e < 8; e++) m.m[e] = (float)op.m[e];
+                in.aux = (int32_t)out->mats.size();
+                out->mats.push_back(m);
+            }
+            if (op.type == TOP_H) out->n_h++;
+            out->ins.push_back(in);
+            continue;
+        }
+        // ---- diagonal run: compile its phase polynomial against layout L
+        const int r = run++;
+        uint32_t sl[kT2Qubits] = {};    // static linear coefficient of each tile bit
+        bool dyn[kT2Qubits] = {};       // tile bit has global-dependent (per-tile) terms
+        bool use_cst = false;
+        uint32_t rt[kT2RegBits][8] = {};
+        std::vector<std::tuple<int, int, uint32_t>> tt;
+        std::map<int, uint32_t> rr;     // register-bit mask -> theta
+        for (int t = op.tb; t < op.te; t++) {
+            const PhaseTerm &pt = tp.terms[t];
+            const uint32_t th = turns32(pt.theta);
+            if (!th) continue;
+            switch (pt.kind) {
+                case TERM_L:
+                    sl[pt.a] += th;
+                    break;
+                case TERM_G:
+                    out->tterms.push_back({r, -1, pt.a, -1, th, 0});
+                    use_cst = true;
+                    break;
+                case TERM_GG:
+                    out->tterms.push_back({r, -1, pt.a, pt.b, th, 0});
+                    use_cst = true;
+                    break;
+                case TERM_LG:
+                    out->tterms.push_back({r, pt.a, pt.b, -1, th, 0});
+                    dyn[pt.a] = true;
+                    break;
+                case TERM_LL: {
+                    const int a = pt.a, b = pt.b;
+                    const bool ra = L.cls[a] == T2C_REG, rb = L.cls[b] == T2C_REG;
+                    if (ra && rb) {
+                        rr[(1 << L.pos[a]) | (1 << L.pos[b])] += th;
+                    } else if (ra || rb) {
+                        const int j = ra ? L.pos[a] : L.pos[b];
+                        const int tbit = ra ? L.pos[b] : L.pos[a];
+                        rt[j][tbit] += th;
+                    } else {
+                        tt.emplace_back(L.pos[a], L.pos[b], th);
+                    }
+                    break;
+                }
+                default:
+                    return "unknown phase term";
+            }
+        }
+        T2Ins in{};
+        in.op = T2_DIAG;
+        in.e0 = (int16_t)out->factors.size();
+        auto add_thread_factor = [&](int mask, bool cst, int lin_reg, int dmask,
+                                     const uint32_t *row) {
+            T2Factor f{};
+            const uint32_t w0 = (uint32_t)mask | (1u << 8) | (cst ? (1u << 9) : 0u) |
+                                ((uint32_t)(lin_reg + 1) << 16) | ((uint32_t)dmask << 24);
+            std::memcpy(&f.w0, &w0, sizeof w0);
+            f.run = r;
+            const int32_t rowi = (int32_t)(out->stat.size() / 256);
+            std::memcpy(&f.c0, &rowi, sizeof rowi);
+            out->stat.insert(out->stat.end(), row, row + 256);
+            out->factors.push_back(f);
+        };
+        // thread factor (all amplitudes of the thread)
+        {
+            uint32_t row[256];
+            bool any = false;
+            int dmask = 0;
+            for (int t = 0; t < 8; t++)
+                if (dyn[L.thread_tile_bit(t)]) dmask |= 1 << t;
+            for (int tau = 0; tau < 256; tau++) {
+                uint32_t u = 0;
+                for (int t = 0; t < 8; t++)
+                    if ((tau >> t) & 1) u += sl[L.thread_tile_bit(t)];
+                for (auto &p : tt)
+                    if (((tau >> std::get<0>(p)) & (tau >> std::get<1>(p))) & 1) u += std::get<2>(p);
+                row[tau] = u;
+                any |= u != 0;
+            }
+            if (any || use_cst || dmask) add_thread_factor(0, use_cst, -1, dmask, row);
+        }
+        // one factor per register bit with a coefficient
+        for (int j = 0; j < kT2RegBits; j++) {
+            const int tb = L.reg[j];
+            uint32_t row[256];
+            bool any = false;
+            for (int tau = 0; tau < 256; tau++) {
+                uint32_t u = sl[tb];
+                for (int t = 0; t < 8; t++)
+                    if ((tau >> t) & 1) u += rt[j][t];
+                row[tau] = u;
+                any |= u != 0;
+            }
+            if (any || dyn[tb]) add_thread_factor(1 << j, false, dyn[tb] ? tb : -1, 0, row);
+        }
+        for (auto &kv : rr) {
+            if (!kv.second) continue;
+            T2Factor f{};
+            f.w0 = kv.first;
+            f.run = r;
+            const double ang = 2.0 * M_PI * ((double)(int32_t)kv.second * 0x1p-32);
+            f.c0 = (float)std::cos(ang);
+            f.c1 = (float)std::sin(ang);
+            out->factors.push_back(f);
+        }
+        in.e1 = (int16_t)out->factors.size();
+        if (out->factors.size() > 32000) return "too many factor applications";
+        if (in.e1 > in.e0) out->ins.push_back(in);
+    }
+    if (out->n_h) {
+        const double s = std::pow(2.0, -0.5 * out->n_h);
+        const float hi = (float)s;
+        T2Mat m{};
+        m.m[0] = hi;
+        m.m[1] = (float)(s - (double)hi);
+        T2Ins in{};
+        in.op = T2_SCALE;
+        in.aux = (int32_t)out->mats.size();
+        out->mats.push_back(m);
+        out->ins.push_back(in);
+    }
+    return "";
+}
+
+}  // namespace sv

@@ -8,10 +8,12 @@
 // a control on a global qubit is a per-tile branch and every diagonal run
 // reduces to a per-tile phase polynomial over the local bits.
 #include <algorithm>
+#include <cstring>
 #include <type_traits>
 
 #include "common.h"
 #include "plan.h"
+#include "stagecomp.h"
 
 namespace sv {
 namespace {
@@ -233,6 +235,43 @@ sv_status launch_pass(sv_state *h, const PassArgs &a, const sv_launch_record &me
 
 }  // namespace
 
+namespace {
+
+// Host staging of everything a call uploads, 256-byte aligned sections.
+struct Blob {
+    std::vector<char> b;
+    size_t put(const void *p, size_t n) {
+        const size_t off = (b.size() + 255) & ~(size_t)255;
+        b.resize(off + n);
+        if (n) std::memcpy(b.data() + off, p, n);
+        return off;
+    }
+    template <typename T>
+    size_t put_vec(const std::vector<T> &v) {
+        return put(v.data(), v.size() * sizeof(T));
+    }
+};
+
+struct PassUpload {
+    bool t2 = false;
+    size_t ops = 0, terms = 0;                                  // generic kernel
+    size_t ins = 0, stages = 0, mats = 0, fac = 0, stat = 0, tterms = 0;  // register-stage kernel
+};
+
+}  // namespace
+
+sv_status check_device_flag(sv_state *h) {
+    if (!h->t2_err) return SV_OK;
+    int flag = 0;
+    SV_CUDA(cudaMemcpyAsync(&flag, h->t2_err, sizeof flag, cudaMemcpyDeviceToHost, h->stream));
+    SV_CUDA(cudaStreamSynchronize(h->stream));
+    if (flag) {
+        SV_CUDA(cudaMemsetAsync(h->t2_err, 0, sizeof(int), h->stream));
+        return fail(SV_ERR_TIMEOUT, "a tile kernel gave up waiting for its bulk copies");
+    }
+    return SV_OK;
+}
+
 sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, const sv_config &cfg) {
     PlanOptions opt;
     opt.n = h->n;
@@ -249,15 +288,29 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
     std::string err = build_plan(gates, opt, phys, &plan);
     if (!err.empty()) return fail(SV_ERR_ARG, "planner: %s", err.c_str());
 
-    // upload the programme: all passes' ops and terms in one buffer
-    size_t nops = 0, nterms = 0;
-    for (const TilePass &p : plan.passes) {
-        nops += p.ops.size();
-        nterms += p.terms.size();
+    // compile every pass; register-stage kernel where it applies
+    const bool allow_t2 = !dbl && !(cfg.flags & SV_FLAG_GENERIC_TILE);
+    std::vector<T2Pass> t2(plan.passes.size());
+    std::vector<PassUpload> up(plan.passes.size());
+    Blob blob;
+    for (size_t i = 0; i < plan.passes.size(); i++) {
+        const TilePass &p = plan.passes[i];
+        if (p.ops.empty()) continue;
+        if (allow_t2 && compile_t2(p, &t2[i]).empty()) {
+            up[i].t2 = true;
+            up[i].ins = blob.put_vec(t2[i].ins);
+            up[i].stages = blob.put_vec(t2[i].stages);
+            up[i].mats = blob.put_vec(t2[i].mats);
+            up[i].fac = blob.put_vec(t2[i].factors);
+            up[i].stat = blob.put_vec(t2[i].stat);
+            up[i].tterms = blob.put_vec(t2[i].tterms);
+        } else {
+            up[i].ops = blob.put_vec(p.ops);
+            up[i].terms = blob.put_vec(p.terms);
+        }
     }
-    const size_t ops_bytes = nops * sizeof(TileOp);
-    const size_t terms_off = (ops_bytes + 255) & ~(size_t)255;
-    const size_t total = terms_off + nterms * sizeof(PhaseTerm) + 256;
+    blob.put(nullptr, 0);
+    const size_t total = blob.b.size() + 256;
     if (total > h->plan_cap) {
         SV_CUDA(cudaStreamSynchronize(h->stream));
         if (h->plan_dev) cudaFree(h->plan_dev);
@@ -275,25 +328,40 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
         // the previous upload must have finished before the staging is reused
         SV_CUDA(cudaStreamSynchronize(h->stream));
     }
-    char *hb = reinterpret_cast<char *>(h->plan_host);
-    TileOp *hops = reinterpret_cast<TileOp *>(hb);
-    PhaseTerm *hterms = reinterpret_cast<PhaseTerm *>(hb + terms_off);
-    size_t oi = 0, ti = 0;
-    for (const TilePass &p : plan.passes) {
-        std::copy(p.ops.begin(), p.ops.end(), hops + oi);
-        std::copy(p.terms.begin(), p.terms.end(), hterms + ti);
-        oi += p.ops.size();
-        ti += p.terms.size();
-    }
-    SV_CUDA(cudaMemcpyAsync(h->plan_dev, h->plan_host, total, cudaMemcpyHostToDevice, h->stream));
-    h->stats.h2d_bytes += (double)total;
-    const TileOp *dops = reinterpret_cast<const TileOp *>(h->plan_dev);
-    const PhaseTerm *dterms =
-        reinterpret_cast<const PhaseTerm *>(reinterpret_cast<char *>(h->plan_dev) + terms_off);
+    std::memcpy(h->plan_host, blob.b.data(), blob.b.size());
+    SV_CUDA(cudaMemcpyAsync(h->plan_dev, h->plan_host, blob.b.size(), cudaMemcpyHostToDevice,
+                            h->stream));
+    h->stats.h2d_bytes += (double)blob.b.size();
+    const char *dev = reinterpret_cast<const char *>(h->plan_dev);
+    bool any_t2 = false;
+    for (auto &u : up) any_t2 |= u.t2;
+    if (any_t2) SV_TRY(t2_prepare(h));
 
-    oi = ti = 0;
-    for (const TilePass &p : plan.passes) {
-        if (!p.ops.empty()) {
+    for (size_t i = 0; i < plan.passes.size(); i++) {
+        const TilePass &p = plan.passes[i];
+        if (p.ops.empty()) continue;
+        sv_launch_record meta{};
+        meta.kind = SV_KERNEL_TILE;
+        meta.pass = h->launch_index++;
+        meta.n = h->n;
+        meta.k = p.k;
+        meta.nops = (int)p.ops.size();
+        meta.ngates = p.ngates;
+        meta.dtype = (int32_t)h->dt;
+        meta.gate_kind = up[i].t2 ? -2 : -1;
+        meta.bytes = 2.0 * (double)state_bytes(h);
+        meta.feat = ~p.gmask & ((UINT64_C(1) << h->n) - 1);
+        sv_status st;
+        if (up[i].t2) {
+            T2Device d;
+            d.ins = reinterpret_cast<const T2Ins *>(dev + up[i].ins);
+            d.stages = reinterpret_cast<const T2Stage *>(dev + up[i].stages);
+            d.mats = reinterpret_cast<const T2Mat *>(dev + up[i].mats);
+            d.fac = reinterpret_cast<const T2Factor *>(dev + up[i].fac);
+            d.stat = reinterpret_cast<const uint32_t *>(dev + up[i].stat);
+            d.tterms = reinterpret_cast<const T2TileTerm *>(dev + up[i].tterms);
+            st = t2_launch(h, t2[i], d, meta);
+        } else {
             PassArgs a{};
             a.k = p.k;
             a.c = p.c;
@@ -301,26 +369,13 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
             for (int s = 0; s < p.k; s++) a.slot_phys[s] = p.slot_phys[s];
             a.gmask = p.gmask;
             a.ntiles = UINT64_C(1) << (h->n - p.k);
-            a.ops = dops + oi;
-            a.terms = dterms + ti;
-            sv_launch_record meta{};
-            meta.kind = SV_KERNEL_TILE;
-            meta.pass = h->launch_index++;
-            meta.n = h->n;
-            meta.k = p.k;
-            meta.nops = a.nops;
-            meta.ngates = p.ngates;
-            meta.dtype = (int32_t)h->dt;
-            meta.gate_kind = -1;
-            meta.bytes = 2.0 * (double)state_bytes(h);
-            meta.feat = ~p.gmask & ((h->n == 64) ? ~UINT64_C(0) : ((UINT64_C(1) << h->n) - 1));
-            sv_status st = dbl ? launch_pass<double>(h, a, meta) : launch_pass<float>(h, a, meta);
-            if (st != SV_OK) return st;
-            h->stats.passes++;
-            h->stats.touched_bytes += 2.0 * (double)state_bytes(h);
+            a.ops = reinterpret_cast<const TileOp *>(dev + up[i].ops);
+            a.terms = reinterpret_cast<const PhaseTerm *>(dev + up[i].terms);
+            st = dbl ? launch_pass<double>(h, a, meta) : launch_pass<float>(h, a, meta);
         }
-        oi += p.ops.size();
-        ti += p.terms.size();
+        if (st != SV_OK) return st;
+        h->stats.passes++;
+        h->stats.touched_bytes += 2.0 * (double)state_bytes(h);
     }
     std::copy(phys, phys + 64, h->phys);
     h->stats.relabels = plan.relabels;

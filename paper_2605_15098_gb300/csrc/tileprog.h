@@ -1,0 +1,90 @@
+// Register-stage tile programme (complex64 tile kernel).
+//
+// A tile pass (see plan.h) is compiled into stages.  In a stage every thread
+// of the CTA holds 2^RB amplitudes of the 2^13-amplitude tile in registers:
+// register bit 0 is always tile bit 0 (two neighbouring amplitudes form one
+// 16-byte shared-memory vector), register bits 1..4 are four tile bits chosen
+// per stage, lane bits 0..2 are tile bits 1..3 (so that the eight lanes of a
+// quarter-warp read one 128-byte row: conflict-free), lane bits 3..4 and the
+// three warp bits are the remaining tile bits.  A gate on a register bit is
+// thread-local arithmetic; a gate on a lane bit exchanges amplitudes with
+// warp shuffles; a stage change stores the tile to shared memory and reloads
+// it in the next stage's layout.
+//
+// A merged diagonal run multiplies amplitude x by e^{2 pi i phi(x) / 2^32}
+// with phi a quadratic polynomial over the bits of x (Sec. III-B's rule that
+// global qubits are constants of a block, applied to every diagonal gate).
+// It is compiled into factor applications: each application multiplies the
+// amplitudes whose register bits include `mask` by one complex factor, which
+// is either a constant (generated in FP64 on the host) or e^{2 pi i u / 2^32}
+// for a per-thread integer phase u, read from FP64-generated tables.  The
+// part of u that does not depend on the tile is tabulated per thread on the
+// host; the kernel adds the tile's global-qubit contributions.
+#pragma once
+
+#include <cstdint>
+
+namespace sv {
+
+constexpr int kT2Qubits = 13;   // tile: 2^13 complex64 amplitudes (64 KiB)
+constexpr int kT2Threads = 256; // 8 warps
+constexpr int kT2RegBits = 5;   // 32 amplitudes per thread
+constexpr int kT2MaxRuns = 64;  // diagonal runs per pass with per-tile data
+
+enum T2Op : int32_t {
+    T2_STAGE = 0,  // switch layout (stage record `aux`), through shared memory
+    T2_GATE = 1,   // general 2x2 (matrix record `aux`) on the target
+    T2_H = 2,      // unnormalised Hadamard [[1,1],[1,-1]] on the target
+    T2_X = 3,      // X on the target
+    T2_DIAG = 4,   // factor applications [e0, e1)
+    T2_SCALE = 5   // multiply every amplitude by hi + lo (matrix record `aux`: m[0], m[1])
+};
+
+enum T2Class : int32_t { T2C_NONE = 0, T2C_REG = 1, T2C_LANE = 2, T2C_THREAD = 3, T2C_GLOBAL = 4 };
+
+// One programme step, 16 bytes (one vector load in the kernel).
+struct T2Ins {
+    int8_t op;
+    int8_t cls;    // target class: T2C_REG (idx = register bit) or T2C_LANE (idx = lane bit)
+    int8_t idx;
+    int8_t ccls;   // control class: NONE, REG (register bit), THREAD (bit of threadIdx.x), GLOBAL
+    int16_t cidx;  // control: register bit, thread bit, or physical bit
+    int16_t pad0;
+    int16_t e0, e1;  // T2_DIAG: factor applications
+    int32_t aux;     // T2_STAGE: stage record; T2_GATE / T2_SCALE: matrix record
+};
+
+// Layout of a stage: tile bit of register bits 0..4, lane bits 0..4 (thread
+// bits 0..4) and warp bits 0..2 (thread bits 5..7).
+struct T2Stage {
+    int8_t tb[16];
+};
+
+struct T2Mat {
+    float m[8];  // U11 re, im, U12 re, im, U21 re, im, U22 re, im
+};
+
+// One factor application, 16 bytes.
+//   w0 bits 0..7:   register-bit mask the amplitude must have set (popcount <= 2)
+//   w0 bit 8:       1 = per-thread phase, 0 = constant (c0, c1)
+//   w0 bit 9:       phase += cst[run] (the tile's global-only part)
+//   w0 bits 16..23: 1 + tile bit whose per-tile coefficient lin[run][tb] is added, 0 = none
+//   w0 bits 24..31: thread bits t whose per-tile coefficient lin[run][tile bit of t] is added
+//                   when thread bit t is set
+// A per-thread phase starts from stat[e * 256 + threadIdx.x] (host table).
+struct T2Factor {
+    int32_t w0;
+    int32_t run;
+    float c0, c1;
+};
+
+// Global-dependent term, applied once per tile: adds theta to lin[run][tb]
+// (tb >= 0) or to cst[run] (tb < 0) when physical bits g0 (and g1, if >= 0)
+// of the tile are set.
+struct T2TileTerm {
+    int32_t run, tb, g0, g1;
+    uint32_t theta;
+    int32_t pad;
+};
+
+}  // namespace sv

@@ -21,14 +21,14 @@ SV_C64, SV_C128 = 0, 1
 SV_OK, SV_ERR_ARG, SV_ERR_OOM, SV_ERR_CUDA, SV_ERR_TIMEOUT, SV_ERR_STATE, SV_ERR_UNSUPPORTED = (
     0, -1, -2, -3, -4, -5, -6)
 SV_MODE_AUTO, SV_MODE_PERGATE, SV_MODE_PARTITIONED, SV_MODE_FUSED = 0, 1, 2, 3
-SV_FLAG_NO_DIAG_MERGE, SV_FLAG_PAPER_SWAP, SV_FLAG_NO_RELABEL = 1, 2, 4
+SV_FLAG_NO_DIAG_MERGE, SV_FLAG_PAPER_SWAP, SV_FLAG_NO_RELABEL, SV_FLAG_GENERIC_TILE = 1, 2, 4, 8
 SV_PLANNER_GREEDY, SV_PLANNER_LEARNED = 0, 1
 
 EXPORTS = (
     "sv_create", "sv_create_on", "sv_destroy", "sv_reset", "sv_info", "sv_qubit_map",
     "sv_apply_circuit", "sv_last_stats", "sv_probabilities", "sv_probabilities_device",
     "sv_argmax", "sv_sample", "sv_copy_out", "sv_copy_in", "sv_last_error", "sv_version",
-    "sv_profile", "sv_profile_read", "sv_launch_count", "sv_marginal_noalloc",
+    "sv_profile", "sv_profile_read", "sv_launch_count", "sv_marginal_noalloc", "sv_plan_export",
 )
 SV_KERNEL_PERGATE, SV_KERNEL_TILE, SV_KERNEL_REMAP, SV_KERNEL_FUSED = 0, 1, 2, 3
 
@@ -100,6 +100,8 @@ def lib() -> ctypes.CDLL:
         "sv_copy_in": [vp, vp],
         "sv_profile": [vp, i32],
         "sv_marginal_noalloc": [vp, i32, i32, vp, u64, vp, vp],
+        "sv_plan_export": [i32, i32, vp, vp, sz, ctypes.POINTER(sv_config), vp, sz,
+                           ctypes.POINTER(sz)],
         "sv_profile_read": [vp, vp, sz, ctypes.POINTER(sz)],
     }
     for name, args in sig.items():
@@ -237,6 +239,23 @@ def sv_profile_read(h: int, cap: int = 1 << 16) -> list[dict]:
     cnt = ctypes.c_size_t()
     _check(lib().sv_profile_read(ctypes.c_void_p(h), buf, cap, ctypes.byref(cnt)))
     return [buf[i].as_dict() for i in range(min(cap, cnt.value))]
+
+
+def sv_plan_export(n: int, dtype: int, gates: np.ndarray, cfg: sv_config | None = None,
+                   phys: list[int] | None = None) -> dict:
+    """The partitioned programme for a gate list, parsed from the library's JSON."""
+    import json
+
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    pm = np.ascontiguousarray(phys, dtype=np.int32) if phys is not None else None
+    ln = ctypes.c_size_t()
+    args = (n, dtype, pm.ctypes.data if pm is not None else None,
+            g.ctypes.data if g.size else None, g.size,
+            ctypes.byref(cfg) if cfg is not None else None)
+    _check(lib().sv_plan_export(*args, None, 0, ctypes.byref(ln)))
+    buf = ctypes.create_string_buffer(ln.value + 1)
+    _check(lib().sv_plan_export(*args, buf, ln.value + 1, ctypes.byref(ln)))
+    return json.loads(buf.value.decode())
 
 
 def sv_launch_count() -> int:

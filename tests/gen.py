@@ -1,0 +1,42 @@
+"""Seeded test inputs shared by the test modules."""
+import numpy as np
+
+from paper_2605_15098_gb300 import circuits as C
+
+
+def mixed_circuit(n, m, seed):
+    """Random circuit over every gate kind (test input)."""
+    rng = np.random.default_rng(seed)
+    recs = []
+    for _ in range(m):
+        kind = int(rng.integers(0, 11))
+        t = int(rng.integers(0, n))
+        o = int(rng.integers(0, n - 1)) if n > 1 else 0
+        o = o + 1 if o >= t else o
+        if n == 1 and kind in (C.CP, C.CZ, C.SWAP, C.CU, C.CPK):
+            kind = C.U3
+        if kind == C.X:
+            recs.append(C.x(t))
+        elif kind == C.H:
+            recs.append(C.h(t))
+        elif kind == C.P:
+            recs.append(C.p(t, float(rng.uniform(-7, 7))))
+        elif kind == C.CP:
+            recs.append(C.cp(o, t, float(rng.uniform(-7, 7))))
+        elif kind == C.CZ:
+            recs.append(C.cz(o, t))
+        elif kind == C.SWAP:
+            recs.append(C.swap(t, o))
+        elif kind == C.U3:
+            recs.append(C.u3(t, *(float(v) for v in rng.uniform(0, 2 * np.pi, 3))))
+        elif kind == C.U:
+            recs.append(C.u(t, C.random_unitary(rng)))
+        elif kind == C.CU:
+            recs.append(C.cu(o, t, C.random_unitary(rng)))
+        elif kind == C.PK:
+            j = int(rng.integers(0, 40))
+            recs.append(C.pk(t, int(rng.integers(-(1 << 40), 1 << 40)), j))
+        else:
+            j = int(rng.integers(0, 40))
+            recs.append(C.cpk(o, t, int(rng.integers(-(1 << 40), 1 << 40)), j))
+    return C.gates(recs)

@@ -1,0 +1,217 @@
+"""Host-side executor of exported tile programmes (test code).
+
+Runs the programme that ``sv_plan_export`` describes on a NumPy state, step
+by step, following the documented meaning of each step (plan.h, tileprog.h),
+in complex128.  Used to check the planner and the stage compiler against the
+FP64 oracle without a GPU.  It shares no code with the oracle or the library.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+TWO32 = 1 << 32
+MASK32 = TWO32 - 1
+
+# generic tile ops (plan.h)
+TOP_GATE, TOP_GATE_CL, TOP_GATE_CG, TOP_DIAG, TOP_SWAP, TOP_H, TOP_X = range(7)
+TERM_L, TERM_LL, TERM_G, TERM_LG, TERM_GG = range(5)
+# register-stage ops (tileprog.h)
+T2_STAGE, T2_GATE, T2_H, T2_X, T2_DIAG, T2_SCALE = range(6)
+C_NONE, C_REG, C_LANE, C_THREAD, C_GLOBAL = range(5)
+
+
+def pdep(v: int, mask: int) -> int:
+    r, b = 0, 0
+    while mask:
+        low = mask & -mask
+        if (v >> b) & 1:
+            r |= low
+        mask &= mask - 1
+        b += 1
+    return r
+
+
+def tile_index(p, base):
+    k = p["k"]
+    idx = np.full(1 << k, base, dtype=np.int64)
+    loc = np.arange(1 << k)
+    for s, q in enumerate(p["slot_phys"]):
+        idx |= ((loc >> s) & 1) << q
+    return idx
+
+
+def mat_of(m):
+    m = np.asarray(m, dtype=np.float64)
+    return (m[0::2] + 1j * m[1::2]).reshape(2, 2)
+
+
+def apply_pairs(t, bit, u, cond=None):
+    loc = np.arange(t.size)
+    sel = ((loc >> bit) & 1) == 0
+    if cond is not None:
+        sel &= cond
+    i0 = loc[sel]
+    i1 = i0 | (1 << bit)
+    a, b = t[i0].copy(), t[i1].copy()
+    t[i0] = u[0, 0] * a + u[0, 1] * b
+    t[i1] = u[1, 0] * a + u[1, 1] * b
+
+
+def phase_of(theta64):
+    return np.exp(2j * np.pi * (theta64 / 2.0 ** 64))
+
+
+def run_generic_pass(state, p):
+    k = p["k"]
+    ntiles = 1 << (int(np.log2(state.size)) - k)
+    loc = np.arange(1 << k)
+    for tile in range(ntiles):
+        base = pdep(tile, p["gmask"])
+        idx = tile_index(p, base)
+        t = state[idx].copy()
+        for op in p["ops"]:
+            ty = op["type"]
+            if ty == TOP_DIAG:
+                phi = np.zeros(t.size, dtype=object)
+                acc = np.zeros(t.size, dtype=np.float64)
+                for kind, a, b, th in p["terms"][op["tb"]:op["te"]]:
+                    if kind == TERM_L:
+                        on = (loc >> a) & 1
+                    elif kind == TERM_LL:
+                        on = ((loc >> a) & 1) & ((loc >> b) & 1)
+                    elif kind == TERM_G:
+                        on = np.full(t.size, (base >> a) & 1)
+                    elif kind == TERM_LG:
+                        on = ((loc >> a) & 1) * ((base >> b) & 1)
+                    else:
+                        on = np.full(t.size, ((base >> a) & 1) & ((base >> b) & 1))
+                    acc += on * (th / 2.0 ** 64)
+                t *= np.exp(2j * np.pi * acc)
+                del phi
+            elif ty == TOP_SWAP:
+                a, b = op["slot"], op["cslot"]
+                sel = (((loc >> a) & 1) == 1) & (((loc >> b) & 1) == 0)
+                i = loc[sel]
+                j = i ^ (1 << a) ^ (1 << b)
+                t[i], t[j] = t[j].copy(), t[i].copy()
+            else:
+                if ty == TOP_GATE_CG and not ((base >> op["cbit"]) & 1):
+                    continue
+                cond = None
+                if ty == TOP_GATE_CL:
+                    cond = ((loc >> op["cslot"]) & 1) == 1
+                if ty == TOP_X:
+                    u = np.array([[0, 1], [1, 0]], dtype=complex)
+                elif ty == TOP_H:
+                    u = np.array([[1, 1], [1, -1]], dtype=complex) / np.sqrt(2)
+                else:
+                    u = mat_of(op["m"])
+                apply_pairs(t, op["slot"], u, cond)
+        state[idx] = t
+
+
+def run_t2_pass(state, p):
+    t2 = p["t2"]
+    k = p["k"]
+    ntiles = 1 << (int(np.log2(state.size)) - k)
+    loc = np.arange(1 << k)
+    stat = np.asarray(t2["stat"], dtype=np.int64)
+    for tile in range(ntiles):
+        base = pdep(tile, p["gmask"])
+        idx = tile_index(p, base)
+        t = state[idx].copy()
+        lin = [0] * (16 * max(t2["nruns"], 1))
+        cst = [0] * max(t2["nruns"], 1)
+        for run, tb, g0, g1, th in t2["tterms"]:
+            on = (base >> g0) & 1
+            if g1 >= 0:
+                on &= (base >> g1) & 1
+            if on:
+                if tb >= 0:
+                    lin[run * 16 + tb] = (lin[run * 16 + tb] + th) & MASK32
+                else:
+                    cst[run] = (cst[run] + th) & MASK32
+        st = None
+        for ins in t2["ins"]:
+            op = ins["op"]
+            if op == T2_STAGE:
+                st = t2["stages"][ins["aux"]]
+                reg, lane, warp = st[0:5], st[5:10], st[10:13]
+                assert sorted(reg + lane + warp) == list(range(k))
+                assert reg[0] == 0 and lane[:3] == [1, 2, 3]
+                ttb = lane + warp                   # tile bit of thread bit t
+                tid = np.zeros(t.size, dtype=np.int64)
+                for tt_, b in enumerate(ttb):
+                    tid |= ((loc >> b) & 1) << tt_
+                continue
+            if op == T2_SCALE:
+                m = t2["mats"][ins["aux"]]
+                t *= np.float64(np.float32(m[0])) + np.float64(np.float32(m[1]))
+                continue
+            if op == T2_DIAG:
+                for f in t2["factors"][ins["e0"]:ins["e1"]]:
+                    w0 = f["w0"]
+                    mask = w0 & 0xFF
+                    sel = np.ones(t.size, dtype=bool)
+                    for j in range(5):
+                        if (mask >> j) & 1:
+                            sel &= ((loc >> reg[j]) & 1) == 1
+                    if not (w0 >> 8) & 1:
+                        fac = np.full(t.size, f["c"][0] + 1j * f["c"][1])
+                    else:
+                        run = f["run"]
+                        u = stat[f["row"] * 256 + tid].copy()
+                        if (w0 >> 9) & 1:
+                            u += cst[run]
+                        lr = ((w0 >> 16) & 0xFF) - 1
+                        if lr >= 0:
+                            u += lin[run * 16 + lr]
+                        dm = (w0 >> 24) & 0xFF
+                        for tt_ in range(8):
+                            if (dm >> tt_) & 1:
+                                u += ((tid >> tt_) & 1) * lin[run * 16 + ttb[tt_]]
+                        u &= MASK32
+                        fac = np.exp(2j * np.pi * (u / 2.0 ** 32))
+                    t[sel] *= fac[sel]
+                continue
+            # gates
+            if ins["cls"] == C_REG:
+                bit = reg[ins["idx"]]
+            else:
+                assert ins["cls"] == C_LANE and ins["idx"] < 3
+                bit = lane[ins["idx"]]
+            cond = None
+            if ins["ccls"] == C_GLOBAL:
+                if not ((base >> ins["cidx"]) & 1):
+                    continue
+            elif ins["ccls"] == C_REG:
+                cond = ((loc >> reg[ins["cidx"]]) & 1) == 1
+            elif ins["ccls"] == C_THREAD:
+                cond = ((loc >> ttb[ins["cidx"]]) & 1) == 1
+            if op == T2_H:
+                u = np.array([[1, 1], [1, -1]], dtype=complex)
+            elif op == T2_X:
+                u = np.array([[0, 1], [1, 0]], dtype=complex)
+            else:
+                u = mat_of(t2["mats"][ins["aux"]])
+            apply_pairs(t, bit, u, cond)
+        state[idx] = t
+
+
+def run_plan(n, plan):
+    state = np.zeros(1 << n, dtype=np.complex128)
+    state[0] = 1.0
+    for p in plan["passes"]:
+        if not p["ops"]:
+            continue
+        if p["kernel"] == "t2":
+            run_t2_pass(state, p)
+        else:
+            run_generic_pass(state, p)
+    # back to logical order
+    phys = plan["phys"]
+    x = np.arange(1 << n)
+    y = np.zeros_like(x)
+    for q in range(n):
+        y |= ((x >> q) & 1) << phys[q]
+    return state[y]

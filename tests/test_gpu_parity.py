@@ -13,6 +13,7 @@ Tolerances:
 import numpy as np
 import pytest
 
+from gen import mixed_circuit
 from paper_2605_15098_gb300 import circuits as C
 
 pytestmark = pytest.mark.gpu
@@ -31,44 +32,6 @@ def sv():
     B.build()
     from paper_2605_15098_gb300 import sv as mod
     return mod
-
-
-def mixed_circuit(n, m, seed):
-    """Random circuit over every gate kind (test input)."""
-    rng = np.random.default_rng(seed)
-    recs = []
-    for _ in range(m):
-        kind = int(rng.integers(0, 11))
-        t = int(rng.integers(0, n))
-        o = int(rng.integers(0, n - 1)) if n > 1 else 0
-        o = o + 1 if o >= t else o
-        if n == 1 and kind in (C.CP, C.CZ, C.SWAP, C.CU, C.CPK):
-            kind = C.U3
-        if kind == C.X:
-            recs.append(C.x(t))
-        elif kind == C.H:
-            recs.append(C.h(t))
-        elif kind == C.P:
-            recs.append(C.p(t, float(rng.uniform(-7, 7))))
-        elif kind == C.CP:
-            recs.append(C.cp(o, t, float(rng.uniform(-7, 7))))
-        elif kind == C.CZ:
-            recs.append(C.cz(o, t))
-        elif kind == C.SWAP:
-            recs.append(C.swap(t, o))
-        elif kind == C.U3:
-            recs.append(C.u3(t, *(float(v) for v in rng.uniform(0, 2 * np.pi, 3))))
-        elif kind == C.U:
-            recs.append(C.u(t, C.random_unitary(rng)))
-        elif kind == C.CU:
-            recs.append(C.cu(o, t, C.random_unitary(rng)))
-        elif kind == C.PK:
-            j = int(rng.integers(0, 40))
-            recs.append(C.pk(t, int(rng.integers(-(1 << 40), 1 << 40)), j))
-        else:
-            j = int(rng.integers(0, 40))
-            recs.append(C.cpk(o, t, int(rng.integers(-(1 << 40), 1 << 40)), j))
-    return C.gates(recs)
 
 
 def run_gpu(sv, n, gates, dtype, cfg=None):
@@ -251,3 +214,28 @@ def test_create_on_torch_buffer(sv, orc):
                 y |= ((x >> q) & 1) << phys[q]
             perm[x] = y
         assert np.max(np.abs(dev[perm] - ref)) <= TOL128
+
+
+@pytest.mark.parametrize("n,chunk", [(14, 5), (16, 4), (17, 6), (18, 7), (19, 5)])
+def test_c64_register_stage_kernel(sv, orc, n, chunk):
+    """complex64 passes on the register-stage kernel (tiles of 2^13, bulk copies)."""
+    g = mixed_circuit(n, 160, 500 + n)
+    ref = orc.run(n, g)
+    with sv.State(n, sv.SV_C64) as s:
+        sv.sv_profile(s.h, True)
+        s.apply(g, sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=chunk))
+        recs = sv.sv_profile_read(s.h)
+        got = s.amplitudes()
+    assert any(r["gate_kind"] == -2 for r in recs)  # register-stage launches
+    assert 1.0 - fidelity(ref, got) <= FID64
+    assert np.max(np.abs(got - ref)) <= ERR64
+
+
+def test_c64_register_stage_vs_generic(sv):
+    """Same circuit through both tile kernels: equal up to float32 rounding."""
+    n = 18
+    g = C.random_circuit(n, 6, 77)
+    a, _ = run_gpu(sv, n, g, sv.SV_C64, sv.make_config(sv.SV_MODE_PARTITIONED))
+    b, _ = run_gpu(sv, n, g, sv.SV_C64,
+                   sv.make_config(sv.SV_MODE_PARTITIONED, flags=sv.SV_FLAG_GENERIC_TILE))
+    assert 1.0 - fidelity(a, b) <= FID64

@@ -1,0 +1,69 @@
+"""Planner and stage compiler, checked on the CPU.
+
+The programme the library would run (sv_plan_export, host only) is executed
+by an independent NumPy executor of the documented step semantics and
+compared with the FP64 oracle.  Register-stage programmes carry float32
+gate matrices and 32-bit phases, hence the looser bound there.
+"""
+import numpy as np
+import pytest
+
+import planemu
+from gen import mixed_circuit
+from paper_2605_15098_gb300 import build as B
+from paper_2605_15098_gb300 import circuits as C
+
+
+@pytest.fixture(scope="module")
+def sv():
+    B.build()
+    from paper_2605_15098_gb300 import sv as mod
+    return mod
+
+
+def check(sv, orc, n, g, cfg, dtype, tol):
+    plan = sv.sv_plan_export(n, dtype, g, cfg)
+    got = planemu.run_plan(n, plan)
+    ref = orc.run(n, g)
+    err = float(np.max(np.abs(got - ref)))
+    assert err <= tol, err
+    return plan
+
+
+@pytest.mark.parametrize("n,seed", [(14, 1), (15, 2), (16, 3)])
+def test_t2_mixed(sv, orc, n, seed):
+    g = mixed_circuit(n, 150, seed)
+    plan = check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED), sv.SV_C64, 2e-5)
+    assert any(p["kernel"] == "t2" for p in plan["passes"])
+
+
+@pytest.mark.parametrize("n", [14, 15, 16])
+def test_t2_qpe(sv, orc, n):
+    g, expected, _ = C.qpe(n, seed=n)
+    plan = check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED), sv.SV_C64, 1e-5)
+    assert all(p["kernel"] == "t2" for p in plan["passes"])
+
+
+@pytest.mark.parametrize("chunk", [4, 5, 6, 7])
+def test_t2_random_layers(sv, orc, chunk):
+    n = 15
+    g = C.random_circuit(n, 4, 99 + chunk)
+    check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=chunk), sv.SV_C64, 2e-5)
+
+
+@pytest.mark.parametrize("flags", [0, 1, 4, 5])
+def test_generic_plan(sv, orc, flags):
+    n = 13
+    g = mixed_circuit(n, 120, 40 + flags)
+    cfg = sv.make_config(sv.SV_MODE_PARTITIONED, tile_qubits=8, chunk_qubits=3,
+                         flags=flags | sv.SV_FLAG_GENERIC_TILE)
+    plan = check(sv, orc, n, g, cfg, sv.SV_C128, 1e-12)
+    assert all(p["kernel"] == "generic" for p in plan["passes"])
+
+
+def test_pass_count_qpe28(sv):
+    """QPE n=28 needs a handful of HBM sweeps instead of one per gate."""
+    g, _, _ = C.qpe(28)
+    plan = sv.sv_plan_export(28, sv.SV_C64, g, sv.make_config(sv.SV_MODE_PARTITIONED))
+    assert len(plan["passes"]) <= 6
+    assert sum(p["ngates"] for p in plan["passes"]) + plan["relabels"] == len(g)
