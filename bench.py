@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-pergate", action="store_true")
     ap.add_argument("--no-c128", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fused", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -238,7 +239,8 @@ def run_ours(args, world, rank, local):
     amp_bytes = 8 if dt == sv.SV_C64 else 16
     gates, expected, info = C.qpe(n)
     mask = info["mask"]
-    cfg = sv.make_config(sv.SV_MODE_PARTITIONED, tile_qubits=args.tile, chunk_qubits=args.chunk)
+    mode = sv.SV_MODE_FUSED if (dt == sv.SV_C64 and not args.no_fused) else sv.SV_MODE_PARTITIONED
+    cfg = sv.make_config(mode, tile_qubits=args.tile, chunk_qubits=args.chunk)
     state_bytes = (1 << n) * amp_bytes
 
     stream = torch.cuda.Stream()
@@ -280,11 +282,14 @@ def run_ours(args, world, rank, local):
     max_ms = max_over_ranks(elapsed_ms)
     value = world * args.steps / (max_ms / 1e3)
 
-    tile = [r for r in recs if r["kind"] == sv.SV_KERNEL_TILE]
-    t2n = sum(1 for r in tile if r["gate_kind"] == -2)
-    kname, ksrc = (("k_tile2 (register-stage tile pass)", "paper_2605_15098_gb300/csrc/tile2.cu")
-                   if t2n * 2 >= len(tile) else
-                   ("k_tile (generic tile pass)", "paper_2605_15098_gb300/csrc/tile.cu"))
+    tile = [r for r in recs if r["kind"] in (sv.SV_KERNEL_TILE, sv.SV_KERNEL_FUSED)]
+    kinds = [r["gate_kind"] for r in tile]
+    if kinds.count(-3) * 2 >= len(kinds):
+        kname, ksrc = "k_tile3 (fused tile pass, tcgen05 blocks)", "paper_2605_15098_gb300/csrc/tile3.cu"
+    elif kinds.count(-2) * 2 >= len(kinds):
+        kname, ksrc = "k_tile2 (register-stage tile pass)", "paper_2605_15098_gb300/csrc/tile2.cu"
+    else:
+        kname, ksrc = "k_tile (generic tile pass)", "paper_2605_15098_gb300/csrc/tile.cu"
     tile_ms = [r["ms"] for r in tile]
     tile_avg_ms = sum(tile_ms) / len(tile_ms) if tile_ms else float("nan")
     launch_bytes = 2.0 * state_bytes
@@ -303,7 +308,8 @@ def run_ours(args, world, rank, local):
         "config": {
             "workload": f"QPE n={n} ({n - 4} counting + 4 eigenstate qubits, {len(gates)} gates), "
                         f"{'complex64' if dt == sv.SV_C64 else 'complex128'}, partitioned tile passes",
-            "n": n, "gates": len(gates), "mode": "partitioned", "passes": st["passes"],
+            "n": n, "gates": len(gates), "mode": "fused" if mode == sv.SV_MODE_FUSED else "partitioned",
+            "passes": st["passes"], "fused_blocks": st["fused_blocks"],
             "relabels": st["relabels"], "tile_qubits": args.tile or (13 if dt == sv.SV_C64 else 12),
             "chunk_qubits": args.chunk or (5 if dt == sv.SV_C64 else 4),
             "state_bytes": state_bytes,
@@ -324,6 +330,21 @@ def run_ours(args, world, rank, local):
         "gpu_launches": launches,
         "clocks": clk,
     }
+
+    # ---- the CUDA-core partitioned kernel on the same circuit ----
+    if mode == sv.SV_MODE_FUSED:
+        pc = sv.make_config(sv.SV_MODE_PARTITIONED)
+        step(pc)
+        e0.record(stream)
+        for _ in range(3):
+            step(pc)
+        e1.record(stream)
+        stream.synchronize()
+        pms = e0.elapsed_time(e1) / 3
+        pst = sv.sv_last_stats(h)
+        out["partitioned_cuda_cores"] = {
+            "circuit_ms": pms, "passes": pst["passes"],
+            "hbm_gbs_full_sweeps": pst["sweep_bytes"] / (pms / 1e3) / 1e9}
 
     # ---- per-gate comparison (same circuit, one HBM sweep per gate) ----
     if not args.no_pergate:

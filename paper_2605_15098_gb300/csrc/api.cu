@@ -131,6 +131,9 @@ sv_status sv_destroy(sv_handle h) {
     if (h->small) cudaFree(h->small);
     if (h->plan_dev) cudaFree(h->plan_dev);
     if (h->plan_host) cudaFreeHost(h->plan_host);
+    if (h->t2_tables) cudaFree(h->t2_tables);
+    if (h->t3_tables) cudaFree(h->t3_tables);
+    if (h->norm_buf) cudaFree(h->norm_buf);
     for (auto &p : h->pending) {
         cudaEventDestroy(p.e0);
         cudaEventDestroy(p.e1);
@@ -144,6 +147,7 @@ sv_status sv_destroy(sv_handle h) {
 sv_status sv_reset(sv_handle h) {
     clear_error();
     if (!h) return fail(SV_ERR_ARG, "handle is NULL");
+    h->norm_pending = false;
     return init_zero_state(h);
 }
 
@@ -190,6 +194,7 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *host_gates, size_t m, con
     if (mode == SV_MODE_AUTO) mode = h->n >= 16 ? SV_MODE_PARTITIONED : SV_MODE_PERGATE;
     sv_status st = SV_OK;
     if (mode == SV_MODE_PERGATE) {
+        st = resolve_norm(h);
         for (size_t i = 0; i < m && st == SV_OK; i++) {
             sv_gate g = host_gates[i];
             g.target = h->phys[g.target];
@@ -258,6 +263,7 @@ sv_status sv_sample(sv_handle h, uint64_t qubit_mask, const double *host_u, size
 sv_status sv_copy_out(sv_handle h, void *host_amps) {
     clear_error();
     if (!h || !host_amps) return fail(SV_ERR_ARG, "NULL argument");
+    SV_TRY(resolve_norm(h));
     SV_TRY(normalise_layout(h));
     SV_CUDA(cudaMemcpyAsync(host_amps, h->amps, state_bytes(h), cudaMemcpyDeviceToHost, h->stream));
     SV_CUDA(cudaStreamSynchronize(h->stream));
@@ -270,6 +276,7 @@ sv_status sv_copy_in(sv_handle h, const void *host_amps) {
     SV_CUDA(cudaMemcpyAsync(h->amps, host_amps, state_bytes(h), cudaMemcpyHostToDevice, h->stream));
     SV_CUDA(cudaStreamSynchronize(h->stream));
     for (int q = 0; q < 64; q++) h->phys[q] = q;
+    h->norm_pending = false;
     return SV_OK;
 }
 

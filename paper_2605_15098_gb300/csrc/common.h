@@ -71,6 +71,10 @@ struct sv_state {
     sv_stats stats{};
     void *t2_tables = nullptr;    // FP64-generated phase tables (register-stage kernel)
     int *t2_err = nullptr;        // device flag: a bounded wait gave up
+    void *t3_tables = nullptr;    // FP64-generated 8-bit phase tables (fused kernel)
+    double *norm_buf = nullptr;   // per-CTA squared norms of fused passes (2 x 256)
+    bool norm_pending = false;    // the state still needs the last fused pass's norm correction
+    int norm_idx = 0, norm_cnt = 0;
     // timing recorder
     bool profiling = false;
     struct Pending {
@@ -119,6 +123,10 @@ struct T2Device;
 size_t t2_smem_bytes();
 sv_status t2_prepare(sv_state *h);
 sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta);
+sv_status t3_prepare(sv_state *h);
+sv_status t3_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta);
+// Multiply the state by the pending norm correction of the last fused pass.
+sv_status resolve_norm(sv_state *h);
 // SV_ERR_TIMEOUT if a kernel of this handle reported a bounded wait that gave up.
 sv_status check_device_flag(sv_state *h);
 sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates_logical,

@@ -88,6 +88,16 @@ void put_t2(J &j, const T2Pass &t) {
         j.raw("["); j.num(tt.run); j.raw(","); j.num(tt.tb); j.raw(","); j.num(tt.g0); j.raw(",");
         j.num(tt.g1); j.raw(","); j.u64(tt.theta); j.raw("]");
     }
+    j.raw("],\"blocks\":[");
+    for (int b = 0; b < t.nblocks; b++) {
+        if (b) j.raw(",");
+        j.raw("[");
+        for (int e = 0; e < 2048; e++) {
+            if (e) j.raw(",");
+            j.dbl(t.blocks64[(size_t)b * 2048 + e]);
+        }
+        j.raw("]");
+    }
     j.raw("],\"nruns\":"); j.num(t.nruns);
     j.raw(",\"n_h\":"); j.num(t.n_h);
     j.raw("}");
@@ -166,9 +176,26 @@ extern "C" sv_status sv_plan_export(int n, sv_dtype dt, const int *host_phys_of_
         }
         j.raw("]");
         T2Pass t2;
-        std::string why = allow_t2 && !p.ops.empty() ? compile_t2(p, &t2) : "disabled";
+        const bool fused = c.mode == SV_MODE_FUSED;
+        std::string why = "disabled";
+        const char *kname = "t2";
+        if (allow_t2 && !p.ops.empty()) {
+            why = fused ? compile_t2(p, &t2, true) : "not fused";
+            kname = "t3";
+            if (!why.empty()) {
+                if (fused) {
+                    j.raw(",\"fused_why\":\"");
+                    j.raw(why.c_str());
+                    j.raw("\"");
+                }
+                why = compile_t2(p, &t2, false);
+                kname = "t2";
+            }
+        }
         if (why.empty()) {
-            j.raw(",\"kernel\":\"t2\",\"t2\":");
+            j.raw(",\"kernel\":\"");
+            j.raw(kname);
+            j.raw("\",\"t2\":");
             put_t2(j, t2);
         } else {
             j.raw(",\"kernel\":\"generic\",\"why\":\"");

@@ -173,8 +173,13 @@ std::string build_plan(const std::vector<sv_gate> &gates, const PlanOptions &opt
             bool diag;
             std::vector<int> g;
         };
+        // Each diagonal gate moves as late as it can: into the diagonal run just
+        // before the next gate that does not commute with it (built on the
+        // reversed order, then flipped).  A run then collects the phases that
+        // feed one non-diagonal gate, as the inverse QFT writes them.
         std::vector<Seg> segs;
-        for (int i : order) {
+        for (auto it = order.rbegin(); it != order.rend(); ++it) {
+            const int i = *it;
             const PGate &p = pg[i];
             if (!p.diag) {
                 segs.push_back({false, {i}});
@@ -203,6 +208,7 @@ std::string build_plan(const std::vector<sv_gate> &gates, const PlanOptions &opt
             else
                 segs.push_back({true, {i}});
         }
+        std::reverse(segs.begin(), segs.end());
 
         for (const Seg &sg : segs) {
             TileOp op{};

@@ -8,6 +8,7 @@
 // remaining tile bits fill lane bits 3..4 and the warp bits.  Diagonal runs
 // are compiled against the layout of the stage that executes them.
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <tuple>
 #include <map>
@@ -83,6 +84,59 @@ Layout choose_layout(const TilePass &tp, int from) {
     return L;
 }
 
+using cplx = std::complex<double>;
+
+struct Block {
+    cplx m[32][32];
+    void identity() {
+        for (int r = 0; r < 32; r++)
+            for (int c = 0; c < 32; c++) m[r][c] = r == c ? 1.0 : 0.0;
+    }
+    // m <- G m, G = u on register bit j (controlled on register bit c when c >= 0)
+    void gate(int j, const cplx u[4], int c) {
+        for (int k = 0; k < 32; k++)
+            for (int r = 0; r < 32; r++) {
+                if ((r >> j) & 1) continue;
+                if (c >= 0 && !((r >> c) & 1)) continue;
+                const int r1 = r | (1 << j);
+                const cplx a = m[r][k], b = m[r1][k];
+                m[r][k] = u[0] * a + u[1] * b;
+                m[r1][k] = u[2] * a + u[3] * b;
+            }
+    }
+    // m <- diag(e^{2 pi i ph[r] / 2^64}) m
+    void phase(const uint64_t ph[32]) {
+        for (int r = 0; r < 32; r++) {
+            if (!ph[r]) continue;
+            const double ang = 2.0 * M_PI * ((double)(int64_t)ph[r] * 0x1p-64);
+            const cplx f(std::cos(ang), std::sin(ang));
+            for (int k = 0; k < 32; k++) m[r][k] *= f;
+        }
+    }
+};
+
+float tf32_round(float x) {
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    b = (b + 0x1000u) & ~0x1FFFu;  // nearest, ties away from zero (magnitude)
+    float r;
+    std::memcpy(&r, &b, 4);
+    return r;
+}
+
+void block_device_layout(const Block &B, float *dst) {
+    for (int part = 0; part < 2; part++)  // 0: hi, 1: lo
+        for (int ri = 0; ri < 2; ri++)    // 0: re, 1: im
+            for (int n = 0; n < 32; n++)
+                for (int k = 0; k < 32; k++) {
+                    const double v = ri ? B.m[n][k].imag() : B.m[n][k].real();
+                    const float hi = tf32_round((float)v);
+                    const float val = part ? (float)(v - (double)hi) : hi;
+                    const int off = (n / 8) * 256 + (k / 4) * 32 + (n % 8) * 4 + (k % 4);
+                    dst[(part * 2 + ri) * 1024 + off] = val;
+                }
+}
+
 bool executable(const Layout &L, const TileOp &op) {
     if (!is_gate_op(op.type)) return true;
     return L.cls[op.slot] == T2C_REG || (op.slot >= 1 && op.slot <= 3);
@@ -90,8 +144,20 @@ bool executable(const Layout &L, const TileOp &op) {
 
 }  // namespace
 
-std::string compile_t2(const TilePass &tp, T2Pass *out) {
+bool unitary2(const double *m) {
+    const cplx a(m[0], m[1]), b(m[2], m[3]), c(m[4], m[5]), d(m[6], m[7]);
+    const cplx p00 = std::conj(a) * a + std::conj(c) * c, p11 = std::conj(b) * b + std::conj(d) * d;
+    const cplx p01 = std::conj(a) * b + std::conj(c) * d;
+    return std::abs(p00 - 1.0) < 1e-9 && std::abs(p11 - 1.0) < 1e-9 && std::abs(p01) < 1e-9;
+}
+
+std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
     *out = T2Pass{};
+    if (fused)
+        for (const TileOp &op : tp.ops)
+            if ((op.type == TOP_GATE || op.type == TOP_GATE_CL || op.type == TOP_GATE_CG) &&
+                !unitary2(op.m))
+                return "non-unitary gate matrix (fused passes renormalise)";
     if (tp.k != kT2Qubits) return "tile is not 2^13 amplitudes";
     if (tp.c < 4) return "chunk smaller than 16 amplitudes";
     for (const TileOp &op : tp.ops)
@@ -121,11 +187,73 @@ std::string compile_t2(const TilePass &tp, T2Pass *out) {
     Layout L = choose_layout(tp, 0);
     emit_stage(L);
     int run = 0;
+    // fused mode: register-bit gates accumulate into a block; thread-dependent
+    // diagonal factors that commute with it wait in `pre` (applied before it)
+    Block blk;
+    blk.identity();
+    bool dirty = false;
+    int nd = 0;  // register bits the block acts on non-diagonally
+    std::vector<T2Factor> pre;
+    auto flush = [&]() -> std::string {
+        if (!pre.empty()) {
+            T2Ins in{};
+            in.op = T2_DIAG;
+            in.e0 = (int16_t)out->factors.size();
+            out->factors.insert(out->factors.end(), pre.begin(), pre.end());
+            in.e1 = (int16_t)out->factors.size();
+            out->ins.push_back(in);
+            pre.clear();
+        }
+        if (dirty) {
+            if (out->nblocks >= 256) return "more than 256 fused blocks in one pass";
+            T2Ins in{};
+            in.op = T2_BLOCK;
+            in.aux = out->nblocks++;
+            for (int r = 0; r < 32; r++)
+                for (int c = 0; c < 32; c++) out->blocks64.push_back(blk.m[r][c].real());
+            for (int r = 0; r < 32; r++)
+                for (int c = 0; c < 32; c++) out->blocks64.push_back(blk.m[r][c].imag());
+            const size_t off = out->blocks_dev.size();
+            out->blocks_dev.resize(off + kBlockFloats);
+            block_device_layout(blk, out->blocks_dev.data() + off);
+            out->ins.push_back(in);
+            blk.identity();
+            dirty = false;
+            nd = 0;
+        }
+        return "";
+    };
     for (size_t i = 0; i < tp.ops.size(); i++) {
         const TileOp &op = tp.ops[i];
         if (!executable(L, op)) {
+            if (fused) {
+                std::string e = flush();
+                if (!e.empty()) return e;
+            }
             L = choose_layout(tp, (int)i);
             emit_stage(L);
+        }
+        if (fused && is_gate_op(op.type) && L.cls[op.slot] == T2C_REG &&
+            (op.type != TOP_GATE_CL || L.cls[op.cslot] == T2C_REG) && op.type != TOP_GATE_CG) {
+            cplx u[4];
+            if (op.type == TOP_H) {
+                const double r = 0.70710678118654752440084436210485;
+                u[0] = r; u[1] = r; u[2] = r; u[3] = -r;
+            } else if (op.type == TOP_X) {
+                u[0] = 0; u[1] = 1; u[2] = 1; u[3] = 0;
+            } else {
+                for (int e = 0; e < 4; e++) u[e] = cplx(op.m[2 * e], op.m[2 * e + 1]);
+            }
+            const int j = L.pos[op.slot];
+            const int c = op.type == TOP_GATE_CL ? L.pos[op.cslot] : -1;
+            blk.gate(j, u, c);
+            nd |= 1 << j;
+            dirty = true;
+            continue;
+        }
+        if (fused && is_gate_op(op.type)) {  // shuffle gate, or a control the block cannot hold
+            std::string e = flush();
+            if (!e.empty()) return e;
         }
         if (is_gate_op(op.type)) {
             T2Ins in{};
@@ -197,9 +325,33 @@ std::string compile_t2(const TilePass &tp, T2Pass *out) {
                     return "unknown phase term";
             }
         }
+        if (fused) {
+            // register-only part (linear terms on register bits, pairs of register bits)
+            // folds into the block at this position, in full 64-bit phase precision
+            uint64_t ph[32] = {};
+            for (int t = op.tb; t < op.te; t++) {
+                const PhaseTerm &pt = tp.terms[t];
+                if (pt.kind == TERM_L && L.cls[pt.a] == T2C_REG) {
+                    for (int rr_ = 0; rr_ < 32; rr_++)
+                        if ((rr_ >> L.pos[pt.a]) & 1) ph[rr_] += pt.theta;
+                    sl[pt.a] = 0;
+                } else if (pt.kind == TERM_LL && L.cls[pt.a] == T2C_REG && L.cls[pt.b] == T2C_REG) {
+                    for (int rr_ = 0; rr_ < 32; rr_++)
+                        if (((rr_ >> L.pos[pt.a]) & (rr_ >> L.pos[pt.b])) & 1) ph[rr_] += pt.theta;
+                }
+            }
+            rr.clear();
+            bool any_ph = false;
+            for (int rr_ = 0; rr_ < 32; rr_++) any_ph |= ph[rr_] != 0;
+            if (any_ph) {
+                blk.phase(ph);
+                dirty = true;
+            }
+        }
         T2Ins in{};
         in.op = T2_DIAG;
         in.e0 = (int16_t)out->factors.size();
+        const size_t nfac0 = out->factors.size();
         auto add_thread_factor = [&](int mask, bool cst, int lin_reg, int dmask,
                                      const uint32_t *row) {
             T2Factor f{};
@@ -254,11 +406,30 @@ std::string compile_t2(const TilePass &tp, T2Pass *out) {
             f.c1 = (float)std::sin(ang);
             out->factors.push_back(f);
         }
+        if (fused) {
+            // move this run's thread-dependent factors into `pre` (before the
+            // block) when they commute with it, else close the block first
+            std::vector<T2Factor> fs(out->factors.begin() + nfac0, out->factors.end());
+            out->factors.resize(nfac0);
+            int jt = 0;
+            for (const T2Factor &f : fs) jt |= f.w0 & 0xff;
+            if (jt & nd) {
+                std::string e = flush();
+                if (!e.empty()) return e;
+            }
+            pre.insert(pre.end(), fs.begin(), fs.end());
+            continue;
+        }
         in.e1 = (int16_t)out->factors.size();
         if (out->factors.size() > 32000) return "too many factor applications";
         if (in.e1 > in.e0) out->ins.push_back(in);
     }
-    if (out->n_h) {
+    if (fused) {
+        std::string e = flush();
+        if (!e.empty()) return e;
+        if (out->factors.size() > 32000) return "too many factor applications";
+    }
+    if (out->n_h || fused) {  // fused passes always end with a scale (norm correction)
         const double s = std::pow(2.0, -0.5 * out->n_h);
         const float hi = (float)s;
         T2Mat m{};

@@ -22,6 +22,9 @@ struct T2Pass {
     std::vector<T2Factor> factors;
     std::vector<uint32_t> stat;     // per-thread static phases: row r is stat[r*256 .. r*256+255]
     std::vector<T2TileTerm> tterms;
+    int nblocks = 0;
+    std::vector<double> blocks64;   // fused: per block 2 x 32 x 32 (re, im), row = output index
+    std::vector<float> blocks_dev;  // fused: per block kBlockFloats in the device layout
 };
 
 // Device copies of a compiled pass (inside the handle's programme buffer).
@@ -32,10 +35,11 @@ struct T2Device {
     const T2Factor *fac;
     const uint32_t *stat;
     const T2TileTerm *tterms;
+    const float *blocks;
 };
 
 // Compile a tile pass; returns "" on success or the reason the pass cannot
 // use the register-stage kernel (it then runs on the generic tile kernel).
-std::string compile_t2(const TilePass &tp, T2Pass *out);
+std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused = false);
 
 }  // namespace sv

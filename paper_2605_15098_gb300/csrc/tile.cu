@@ -254,6 +254,8 @@ struct Blob {
 
 struct PassUpload {
     bool t2 = false;
+    bool t3 = false;
+    size_t blocks = 0;
     size_t ops = 0, terms = 0;                                  // generic kernel
     size_t ins = 0, stages = 0, mats = 0, fac = 0, stat = 0, tterms = 0;  // register-stage kernel
 };
@@ -290,13 +292,22 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
 
     // compile every pass; register-stage kernel where it applies
     const bool allow_t2 = !dbl && !(cfg.flags & SV_FLAG_GENERIC_TILE);
+    const bool fused = cfg.mode == SV_MODE_FUSED;
     std::vector<T2Pass> t2(plan.passes.size());
     std::vector<PassUpload> up(plan.passes.size());
     Blob blob;
     for (size_t i = 0; i < plan.passes.size(); i++) {
         const TilePass &p = plan.passes[i];
         if (p.ops.empty()) continue;
-        if (allow_t2 && compile_t2(p, &t2[i]).empty()) {
+        bool ok = false;
+        if (allow_t2 && fused && compile_t2(p, &t2[i], true).empty()) {
+            ok = true;
+            up[i].t3 = true;
+            up[i].blocks = blob.put_vec(t2[i].blocks_dev);
+        } else if (allow_t2 && compile_t2(p, &t2[i], false).empty()) {
+            ok = true;
+        }
+        if (ok) {
             up[i].t2 = true;
             up[i].ins = blob.put_vec(t2[i].ins);
             up[i].stages = blob.put_vec(t2[i].stages);
@@ -333,9 +344,13 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
                             h->stream));
     h->stats.h2d_bytes += (double)blob.b.size();
     const char *dev = reinterpret_cast<const char *>(h->plan_dev);
-    bool any_t2 = false;
-    for (auto &u : up) any_t2 |= u.t2;
+    bool any_t2 = false, any_t3 = false;
+    for (auto &u : up) {
+        any_t2 |= u.t2;
+        any_t3 |= u.t3;
+    }
     if (any_t2) SV_TRY(t2_prepare(h));
+    if (any_t3) SV_TRY(t3_prepare(h));
 
     for (size_t i = 0; i < plan.passes.size(); i++) {
         const TilePass &p = plan.passes[i];
@@ -348,10 +363,12 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
         meta.nops = (int)p.ops.size();
         meta.ngates = p.ngates;
         meta.dtype = (int32_t)h->dt;
-        meta.gate_kind = up[i].t2 ? -2 : -1;
+        meta.gate_kind = up[i].t3 ? -3 : up[i].t2 ? -2 : -1;
+        if (up[i].t3) meta.kind = SV_KERNEL_FUSED;
         meta.bytes = 2.0 * (double)state_bytes(h);
         meta.feat = ~p.gmask & ((UINT64_C(1) << h->n) - 1);
         sv_status st;
+        if (!up[i].t3) SV_TRY(resolve_norm(h));
         if (up[i].t2) {
             T2Device d;
             d.ins = reinterpret_cast<const T2Ins *>(dev + up[i].ins);
@@ -360,7 +377,8 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
             d.fac = reinterpret_cast<const T2Factor *>(dev + up[i].fac);
             d.stat = reinterpret_cast<const uint32_t *>(dev + up[i].stat);
             d.tterms = reinterpret_cast<const T2TileTerm *>(dev + up[i].tterms);
-            st = t2_launch(h, t2[i], d, meta);
+            d.blocks = up[i].t3 ? reinterpret_cast<const float *>(dev + up[i].blocks) : nullptr;
+            st = up[i].t3 ? t3_launch(h, t2[i], d, meta) : t2_launch(h, t2[i], d, meta);
         } else {
             PassArgs a{};
             a.k = p.k;

@@ -37,8 +37,18 @@ enum T2Op : int32_t {
     T2_H = 2,      // unnormalised Hadamard [[1,1],[1,-1]] on the target
     T2_X = 3,      // X on the target
     T2_DIAG = 4,   // factor applications [e0, e1)
-    T2_SCALE = 5   // multiply every amplitude by hi + lo (matrix record `aux`: m[0], m[1])
+    T2_SCALE = 5,  // multiply every amplitude by hi + lo (matrix record `aux`: m[0], m[1])
+    T2_BLOCK = 6   // fused kernel: 32x32 block `aux` on the register bits (tensor cores)
 };
+
+// Fused blocks: a 32x32 complex matrix U on the register index (bit j of the
+// index = register bit j) multiplies each thread's 32 amplitudes.  On the
+// device a block is 4 x 32 x 32 floats: Re U and Im U rounded to TF32 (hi),
+// then the remainders (lo), each in the K-major, no-swizzle operand layout of
+// the tensor-core B operand: element (n, k) at byte
+//   (n / 8) * 1024 + (k / 4) * 128 + (n % 8) * 16 + (k % 4) * 4.
+constexpr int kBlockFloats = 4 * 32 * 32;
+constexpr int kMaxBlocks = 4;  // shared-memory block slots; more blocks stream through them
 
 enum T2Class : int32_t { T2C_NONE = 0, T2C_REG = 1, T2C_LANE = 2, T2C_THREAD = 3, T2C_GLOBAL = 4 };
 

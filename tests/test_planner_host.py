@@ -67,3 +67,25 @@ def test_pass_count_qpe28(sv):
     plan = sv.sv_plan_export(28, sv.SV_C64, g, sv.make_config(sv.SV_MODE_PARTITIONED))
     assert len(plan["passes"]) <= 6
     assert sum(p["ngates"] for p in plan["passes"]) + plan["relabels"] == len(g)
+
+
+@pytest.mark.parametrize("n,seed", [(14, 11), (16, 12)])
+def test_fused_mixed(sv, orc, n, seed):
+    g = mixed_circuit(n, 150, seed)
+    plan = check(sv, orc, n, g, sv.make_config(sv.SV_MODE_FUSED), sv.SV_C64, 2e-5)
+    assert any(p["kernel"] == "t3" for p in plan["passes"])
+
+
+@pytest.mark.parametrize("n", [14, 16, 17])
+def test_fused_qpe(sv, orc, n):
+    g, _, _ = C.qpe(n, seed=n + 1)
+    plan = check(sv, orc, n, g, sv.make_config(sv.SV_MODE_FUSED), sv.SV_C64, 1e-5)
+    assert all(p["kernel"] == "t3" for p in plan["passes"])
+
+
+@pytest.mark.parametrize("depth", [2, 5])
+def test_fused_random_layers(sv, orc, depth):
+    n = 15
+    g = C.random_circuit(n, depth, 300 + depth)
+    plan = check(sv, orc, n, g, sv.make_config(sv.SV_MODE_FUSED), sv.SV_C64, 2e-5)
+    assert sum(len(p["t2"]["blocks"]) for p in plan["passes"] if p["kernel"] == "t3") >= 1
