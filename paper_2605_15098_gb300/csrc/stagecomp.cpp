@@ -263,7 +263,8 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
             in.ccls = T2C_NONE;
             if (op.type == TOP_GATE_CL) {
                 const int c = op.cslot;
-                in.ccls = (int8_t)(L.cls[c] == T2C_REG ? T2C_REG : T2C_THREAD);
+                if (L.cls[c] == T2C_REG) return "gate controlled by a register bit";
+                in.ccls = (int8_t)T2C_THREAD;
                 in.cidx = (int16_t)L.pos[c];
             } else if (op.type == TOP_GATE_CG) {
                 in.ccls = T2C_GLOBAL;

@@ -39,7 +39,8 @@ constexpr size_t kOffTab = kOffBlk + (size_t)kMaxBlocks * kBlockBytes;
 constexpr size_t kOffLin = kOffTab + 4 * kTabN * 8;
 constexpr size_t kOffCst = kOffLin + (size_t)kT2MaxRuns * 16 * 4;
 constexpr size_t kOffBar = kOffCst + (size_t)kT2MaxRuns * 4;
-constexpr size_t kSmemBytes = kOffBar + 128;
+constexpr size_t kOffChunk = kOffBar + 128;  // chunk offsets >> c (<= 512)
+constexpr size_t kSmemBytes = kOffChunk + 2048;
 constexpr uint32_t kTmemCols = 512;
 
 struct T3Args {
@@ -133,7 +134,8 @@ __device__ __forceinline__ float2 phase_factor(const float2 *tab, uint32_t u) {
 }
 
 __device__ __forceinline__ void issue_tile_load(unsigned char *buf, const float *state, uint64_t base,
-                                                const T3Args &a, uint64_t *bar, int lane) {
+                                                const T3Args &a, uint64_t *bar, int lane,
+                                                const uint32_t *choff) {
     const int nchunks = 1 << (kT2Qubits - a.c);
     const uint32_t chunk_bytes = 8u << a.c;
     if (lane == 0) {
@@ -142,21 +144,18 @@ __device__ __forceinline__ void issue_tile_load(unsigned char *buf, const float 
     }
     __syncwarp();
     for (int j = lane; j < nchunks; j += 32) {
-        uint64_t off = 0;
-        for (int b = 0; b < kT2Qubits - a.c; b++)
-            if ((j >> b) & 1) off |= UINT64_C(1) << a.slot_phys[a.c + b];
+        const uint64_t off = (uint64_t)choff[j] << a.c;
         bulk_g2s(buf + (size_t)j * chunk_bytes, state + 2 * (base + off), chunk_bytes, bar);
     }
 }
 
 __device__ __forceinline__ void issue_tile_store(float *state, const unsigned char *buf,
-                                                 uint64_t base, const T3Args &a, int lane) {
+                                                 uint64_t base, const T3Args &a, int lane,
+                                                 const uint32_t *choff) {
     const int nchunks = 1 << (kT2Qubits - a.c);
     const uint32_t chunk_bytes = 8u << a.c;
     for (int j = lane; j < nchunks; j += 32) {
-        uint64_t off = 0;
-        for (int b = 0; b < kT2Qubits - a.c; b++)
-            if ((j >> b) & 1) off |= UINT64_C(1) << a.slot_phys[a.c + b];
+        const uint64_t off = (uint64_t)choff[j] << a.c;
         bulk_s2g(state + 2 * (base + off), buf + (size_t)j * chunk_bytes, chunk_bytes);
     }
     bulk_commit();
@@ -171,9 +170,16 @@ __global__ void __launch_bounds__(kT2Threads, 1) k_tile3(float *__restrict__ sta
     uint64_t *mma_bar = reinterpret_cast<uint64_t *>(sm + kOffBar + 16);
     uint64_t *slot_bar = reinterpret_cast<uint64_t *>(sm + kOffBar + 24);  // [kMaxBlocks]
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + kOffBar + 24 + 8 * kMaxBlocks);
+    uint32_t *choff = reinterpret_cast<uint32_t *>(sm + kOffChunk);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     for (int i = tid; i < 4 * kTabN; i += blockDim.x) tab[i] = a.tables[i];
+    for (int j = tid; j < (1 << (kT2Qubits - a.c)); j += blockDim.x) {
+        uint64_t off = 0;
+        for (int b = 0; b < kT2Qubits - a.c; b++)
+            if ((j >> b) & 1) off |= UINT64_C(1) << a.slot_phys[a.c + b];
+        choff[j] = (uint32_t)(off >> a.c);
+    }
     if (tid == 0) {
         mbar_init(&full[0], 1);
         mbar_init(&full[1], 1);
@@ -234,7 +240,7 @@ __global__ void __launch_bounds__(kT2Threads, 1) k_tile3(float *__restrict__ sta
     uint32_t mma_phase = 0;
     uint64_t tile = blockIdx.x;
     if (!failed && warp == 0 && tile < a.ntiles)
-        issue_tile_load(sm, state, pdep(tile, a.gmask), a, &full[0], lane);
+        issue_tile_load(sm, state, pdep(tile, a.gmask), a, &full[0], lane, choff);
 
     for (int it = 0; !failed && tile < a.ntiles; it++, tile += gridDim.x) {
         const int b = it & 1;
@@ -247,7 +253,7 @@ __global__ void __launch_bounds__(kT2Threads, 1) k_tile3(float *__restrict__ sta
             bulk_wait_read();
             __syncwarp();
             issue_tile_load(sm + (b ? 0 : kOffBuf1), state, pdep(next, a.gmask), a, &full[b ^ 1],
-                            lane);
+                            lane, choff);
         }
         for (int i = tid; i < a.nruns * 16; i += blockDim.x) lin[i] = 0u;
         for (int i = tid; i < a.nruns; i += blockDim.x) cst[i] = 0u;
@@ -295,13 +301,17 @@ __global__ void __launch_bounds__(kT2Threads, 1) k_tile3(float *__restrict__ sta
                 s2 = 1 << tbyte(2);
                 s3 = 1 << tbyte(3);
                 s4 = 1 << tbyte(4);
+                if (live) {
 #pragma unroll
-                for (int q = 0; q < kNP; q++) {
-                    const float4 v = tile4[sidx(q)];
-                    if (live) {
+                    for (int q = 0; q < kNP; q++) {
+                        const float4 v = tile4[sidx(q)];
                         r.re[q] = make_float2(v.x, v.y);
                         r.im[q] = make_float2(v.z, v.w);
-                    } else {
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < kNP; q++) {
+                        const float4 v = tile4[sidx(q)];
                         r.re[q] = make_float2(v.x, v.z);
                         r.im[q] = make_float2(v.y, v.w);
                     }
@@ -352,29 +362,26 @@ __global__ void __launch_bounds__(kT2Threads, 1) k_tile3(float *__restrict__ sta
                     const uint32_t idesc =
                         (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
                     const uint32_t bblk = saddr(sm + kOffBlk) + (uint32_t)slot * kBlockBytes;
-#pragma unroll 1
+                    const uint64_t d0 = smem_desc(bblk, 128, 1024);
+#pragma unroll
                     for (int hh = 0; hh < 2; hh++) {
-#pragma unroll 1
+#pragma unroll
                         for (int out = 0; out < 2; out++) {  // 0: Re y, 1: Im y
                             const uint32_t dtm = tbase + 256 + hh * 64 + out * 32;
-                            uint32_t acc = 0;
-#pragma unroll 1
+#pragma unroll
                             for (int prod = 0; prod < 3; prod++) {  // hi*hi, hi*lo, lo*hi
-                                const uint32_t acol = (prod == 2 ? 128u : 0u) + hh * 64;
-                                const uint32_t bpart = prod == 1 ? 2u * 4096u : 0u;
-#pragma unroll 1
+#pragma unroll
                                 for (int src = 0; src < 2; src++) {  // 0: Re x, 1: Im x
                                     // Re y: Re x * Re U - Im x * Im U ; Im y: Re x * Im U + Im x * Re U
                                     const bool use_im = (out == 0) ? (src == 1) : (src == 0);
-                                    const bool neg = out == 0 && src == 1;
-                                    const uint32_t bm = bblk + bpart + (use_im ? 4096u : 0u);
-                                    const uint32_t id = idesc | (neg ? (1u << 14) : 0u);
+                                    const uint32_t id = idesc | ((out == 0 && src == 1) ? (1u << 14) : 0u);
+                                    const uint32_t acol = (prod == 2 ? 128u : 0u) + hh * 64 + src * 32;
+                                    const uint32_t boff =
+                                        (prod == 1 ? 2u * 4096u : 0u) + (use_im ? 4096u : 0u);
 #pragma unroll
-                                    for (int s = 0; s < 4; s++) {
-                                        mma_tf32(dtm, tbase + acol + src * 32 + s * 8,
-                                                 smem_desc(bm + s * 256, 128, 1024), id, acc);
-                                        acc = 1;
-                                    }
+                                    for (int s = 0; s < 4; s++)
+                                        mma_tf32(dtm, tbase + acol + s * 8, d0 + ((boff + s * 256) >> 4),
+                                                 id, (prod | src | s) ? 1u : 0u);
                                 }
                             }
                         }
@@ -457,53 +464,30 @@ __global__ void __launch_bounds__(kT2Threads, 1) k_tile3(float *__restrict__ sta
             const int ccls = (w.x >> 24) & 0xff;
             const int cidx = (int16_t)(w.y & 0xffff);
             bool pred = true;
-            int jc = -1;
+            const int jc = -1;  // register-bit controls are not compiled for these kernels
             if (ccls == T2C_GLOBAL) {
                 if (!((base >> cidx) & 1)) continue;
             } else if (ccls == T2C_THREAD) {
                 pred = (tid >> cidx) & 1;
-            } else if (ccls == T2C_REG) {
-                jc = cidx;
             }
-            float m[8];
             if (op == T2_GATE) {
+                float m[8];
                 const float4 m0 = __ldg(a.mats + 2 * w.w), m1 = __ldg(a.mats + 2 * w.w + 1);
                 m[0] = m0.x; m[1] = m0.y; m[2] = m0.z; m[3] = m0.w;
                 m[4] = m1.x; m[5] = m1.y; m[6] = m1.z; m[7] = m1.w;
-            } else {
-#pragma unroll
-                for (int e = 0; e < 8; e++) m[e] = 0.f;
+                if (cls == T2C_LANE)
+                    lane_gate(r, T2_GATE, j, jc, pred, m);
+                else if (pred)
+                    reg_gate(r, T2_GATE, j, jc, m);
+                continue;
             }
+            const float mz[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (cls == T2C_LANE) {
-                lane_gate(r, op, j, jc, pred, m);
+                lane_gate(r, op, j, jc, pred, mz);
                 continue;
             }
             if (!pred) continue;
-            if (op == T2_H) {
-                switch (j) {
-                    case 0: reg_h<0>(r, jc); break;
-                    case 1: reg_h<1>(r, jc); break;
-                    case 2: reg_h<2>(r, jc); break;
-                    case 3: reg_h<3>(r, jc); break;
-                    default: reg_h<4>(r, jc); break;
-                }
-            } else if (op == T2_X) {
-                switch (j) {
-                    case 0: reg_x<0>(r, jc); break;
-                    case 1: reg_x<1>(r, jc); break;
-                    case 2: reg_x<2>(r, jc); break;
-                    case 3: reg_x<3>(r, jc); break;
-                    default: reg_x<4>(r, jc); break;
-                }
-            } else {
-                switch (j) {
-                    case 0: reg_u<0>(r, jc, m); break;
-                    case 1: reg_u<1>(r, jc, m); break;
-                    case 2: reg_u<2>(r, jc, m); break;
-                    case 3: reg_u<3>(r, jc, m); break;
-                    default: reg_u<4>(r, jc, m); break;
-                }
-            }
+            reg_gate(r, op, j, jc, mz);
         }
         if (failed) break;
         if (live) {
@@ -518,7 +502,7 @@ __global__ void __launch_bounds__(kT2Threads, 1) k_tile3(float *__restrict__ sta
         }
         fence_async_smem();
         __syncthreads();
-        if (warp == 0) issue_tile_store(state, buf, base, a, lane);
+        if (warp == 0) issue_tile_store(state, buf, base, a, lane, choff);
     }
     if (failed && tid == 0) atomicExch(a.err, 1);
     if (warp == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");

@@ -200,6 +200,35 @@ __device__ __forceinline__ void reg_u(Regs &r, int jc, const float *m) {
     }
 }
 
+// Gate on register bit j (runtime).
+__device__ __forceinline__ void reg_gate(Regs &r, int op, int j, int jc, const float *m) {
+    if (op == T2_H) {
+        switch (j) {
+            case 0: reg_h<0>(r, jc); break;
+            case 1: reg_h<1>(r, jc); break;
+            case 2: reg_h<2>(r, jc); break;
+            case 3: reg_h<3>(r, jc); break;
+            default: reg_h<4>(r, jc); break;
+        }
+    } else if (op == T2_X) {
+        switch (j) {
+            case 0: reg_x<0>(r, jc); break;
+            case 1: reg_x<1>(r, jc); break;
+            case 2: reg_x<2>(r, jc); break;
+            case 3: reg_x<3>(r, jc); break;
+            default: reg_x<4>(r, jc); break;
+        }
+    } else {
+        switch (j) {
+            case 0: reg_u<0>(r, jc, m); break;
+            case 1: reg_u<1>(r, jc, m); break;
+            case 2: reg_u<2>(r, jc, m); break;
+            case 3: reg_u<3>(r, jc, m); break;
+            default: reg_u<4>(r, jc, m); break;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- lane-bit gates (shuffles)
 __device__ __forceinline__ void lane_gate(Regs &r, int op, int l, int jc, bool pred,
                                           const float *m) {

@@ -4,12 +4,12 @@ import numpy as np
 from paper_2605_15098_gb300 import circuits as C
 
 
-def mixed_circuit(n, m, seed):
+def mixed_circuit(n, m, seed, kinds=tuple(range(11))):
     """Random circuit over every gate kind (test input)."""
     rng = np.random.default_rng(seed)
     recs = []
     for _ in range(m):
-        kind = int(rng.integers(0, 11))
+        kind = int(kinds[int(rng.integers(0, len(kinds)))])
         t = int(rng.integers(0, n))
         o = int(rng.integers(0, n - 1)) if n > 1 else 0
         o = o + 1 if o >= t else o

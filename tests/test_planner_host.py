@@ -33,8 +33,10 @@ def check(sv, orc, n, g, cfg, dtype, tol):
 @pytest.mark.parametrize("n,seed", [(14, 1), (15, 2), (16, 3)])
 def test_t2_mixed(sv, orc, n, seed):
     g = mixed_circuit(n, 150, seed)
+    check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED), sv.SV_C64, 2e-5)
+    g = mixed_circuit(n, 150, seed, kinds=(0, 1, 2, 3, 4, 5, 6, 7, 9, 10))  # no CU
     plan = check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED), sv.SV_C64, 2e-5)
-    assert any(p["kernel"] == "t2" for p in plan["passes"])
+    assert all(p["kernel"] == "t2" for p in plan["passes"])
 
 
 @pytest.mark.parametrize("n", [14, 15, 16])
