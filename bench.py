@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-c128", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fused", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -393,6 +395,25 @@ def run_ours(args, world, rank, local):
         out["c128"] = res
         sv.sv_destroy(h2)
         del buf2
+
+    # ---- batched QPE (4096 instances, n uniform in 10..20): one graph launch ----
+    if not args.no_batch:
+        work = C.qpe_batch(args.batch)
+        t0 = time.perf_counter()
+        bh = sv.sv_batch_create([(nn, gg, mm) for nn, gg, mm, _ in work])
+        t_create = time.perf_counter() - t0
+        sv.sv_batch_run(bh, len(work))
+        runs = [sv.sv_batch_run(bh, len(work)) for _ in range(3)]
+        binfo = sv.sv_batch_info(bh)
+        sv.sv_batch_destroy(bh)
+        bidx = runs[-1][0]
+        bms = statistics.median(r[2] for r in runs)
+        out["batched"] = {
+            "instances": len(work), "n_range": [10, 20], "launch_ms": bms,
+            "instances_per_s": len(work) / (bms / 1e3), "passes": binfo["passes"],
+            "l2_gbs_algorithmic": binfo["sweep_bytes"] / (bms / 1e3) / 1e9,
+            "host_plan_s": t_create,
+            "outcomes_ok": bool(all(int(bidx[i]) == w[3] for i, w in enumerate(work)))}
 
     # ---- end to end through the public API with host buffers ----
     he = sv.sv_create(n, dt)

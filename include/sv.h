@@ -181,6 +181,48 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *host_gates, size_t m,
 /* Counters of the last sv_apply_circuit. */
 sv_status sv_last_stats(sv_handle h, sv_stats *out);
 
+/* ---- batches: many independent circuits in one launch ------------------ */
+
+/* One circuit of a batch: n qubits (1..24) starting from |0...0>, its gate
+ * list (caller-owned, read during sv_batch_create only) and the logical
+ * qubits whose marginal is read out. */
+typedef struct sv_batch_item {
+    int32_t n;
+    int32_t reserved;
+    const sv_gate *gates;
+    size_t m;
+    uint64_t qubit_mask;
+} sv_batch_item;
+
+typedef struct sv_batch_state *sv_batch;
+
+/* Plan every item (tiles of 2^13 complex64 amplitudes; smaller circuits are
+ * padded with untouched qubits), allocate all states, and capture one CUDA
+ * graph that runs the whole batch as a single persistent launch: CTAs take
+ * items from a queue ordered by decreasing cost, apply all their passes and
+ * reduce the FP64 marginal of the read-out qubits to its most probable
+ * outcome.  cfg may be NULL; cfg->chunk_qubits (4..11) sets the bulk-copy
+ * unit.  Errors: SV_ERR_ARG (bad item), SV_ERR_UNSUPPORTED (a pass the
+ * register-stage kernel cannot run), SV_ERR_OOM, SV_ERR_CUDA. */
+sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_config *cfg,
+                          sv_batch *out);
+
+/* Replay the batch (every state restarts from |0...0>) and wait for it.
+ * host_idx[i] / host_p[i] (either may be NULL) receive item i's most probable
+ * outcome (lowest index among exact ties; bit j = j-th lowest qubit of its
+ * mask) and that outcome's probability; *ms (may be NULL) the launch's device
+ * time measured with CUDA events. */
+sv_status sv_batch_run(sv_batch b, uint64_t *host_idx, double *host_p, double *ms);
+
+/* Items, HBM/L2 sweeps and their algorithmic bytes (2 x 2^n x 8 per sweep). */
+sv_status sv_batch_info(sv_batch b, size_t *count, int *passes, double *sweep_bytes);
+
+sv_status sv_batch_destroy(sv_batch b);
+
+/* sv_batch_create + sv_batch_run + sv_batch_destroy. */
+sv_status sv_apply_circuit_batch(const sv_batch_item *items, size_t count, const sv_config *cfg,
+                                 uint64_t *host_idx, double *host_p);
+
 /* ---- reading out (Sec. IV-A: the measured bitstring) ------------------ */
 
 /* Marginal probabilities over the logical qubits in `qubit_mask`, computed

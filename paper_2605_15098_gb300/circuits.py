@@ -227,6 +227,15 @@ def batch_specs(count: int, seed: int = DEFAULT_SEED, n_lo: int = 10, n_hi: int 
     return [(n_lo + g.next() % span, seed + 1 + i) for i in range(count)]
 
 
+def qpe_batch(count: int, seed: int = DEFAULT_SEED, n_lo: int = 10, n_hi: int = 20):
+    """The batched QPE workload: (n_i, gates_i, counting mask_i, expected y_i) per instance."""
+    out = []
+    for n, s in batch_specs(count, seed, n_lo, n_hi):
+        g, _, info = qpe(n, s)
+        out.append((n, g, info["mask"], info["y"]))
+    return out
+
+
 def random_unitary(rng: np.random.Generator) -> np.ndarray:
     """Haar-ish random 2x2 unitary from a QR decomposition (test input)."""
     z = rng.normal(size=(2, 2)) + 1j * rng.normal(size=(2, 2))

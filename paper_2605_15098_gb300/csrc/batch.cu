@@ -1,0 +1,336 @@
+// Batched circuits: many independent states in one persistent, graph-captured launch.
+//
+// Every instance is planned on the host like sv_apply_circuit's partitioned
+// mode (tiles of 2^13 amplitudes; an instance of fewer than 13 qubits is
+// padded with untouched qubits, which stay |0>), compiled to register-stage
+// programmes, and packed with all other instances into one device buffer.
+// One launch then runs them all: CTAs take instances from a queue ordered by
+// decreasing cost (longest processing time first), run every pass of an
+// instance themselves and reduce its read-out.  The launch, the queue reset
+// and the copy of the results are captured once in a CUDA graph that
+// sv_batch_run replays.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <thread>
+
+#include "common.h"
+#include "plan.h"
+#include "stagecomp.h"
+
+using namespace sv;
+
+struct sv_batch_state {
+    int device = 0, sm_count = 0;
+    cudaStream_t stream = nullptr;
+    size_t count = 0;
+    void *states = nullptr;
+    size_t state_amps = 0;
+    void *prog = nullptr;  // programme blob + instance table + pass table + order
+    int *queue = nullptr;
+    uint64_t *out_idx = nullptr;
+    double *out_p = nullptr;
+    uint64_t *h_idx = nullptr;  // pinned
+    double *h_p = nullptr;      // pinned
+    void *tables = nullptr;
+    int *err = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int total_passes = 0;
+    double sweep_bytes = 0;
+};
+
+namespace {
+
+struct Blob {
+    std::vector<char> b;
+    size_t put(const void *p, size_t n) {
+        const size_t off = (b.size() + 255) & ~(size_t)255;
+        b.resize(off + n);  // zero-filled
+        if (n && p) std::memcpy(b.data() + off, p, n);
+        return off;
+    }
+};
+
+struct Compiled {
+    std::string err;
+    int nphys = 0;
+    std::vector<T2Pass> passes;
+    int phys[64];
+};
+
+void destroy(sv_batch_state *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->states) cudaFree(b->states);
+    if (b->prog) cudaFree(b->prog);
+    if (b->queue) cudaFree(b->queue);
+    if (b->out_idx) cudaFree(b->out_idx);
+    if (b->out_p) cudaFree(b->out_p);
+    if (b->h_idx) cudaFreeHost(b->h_idx);
+    if (b->h_p) cudaFreeHost(b->h_p);
+    if (b->tables) cudaFree(b->tables);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_config *cfg,
+                          sv_batch *out) {
+    clear_error();
+    if (!out) return fail(SV_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!count || !items) return fail(SV_ERR_ARG, "empty batch");
+    if (count > (1u << 24)) return fail(SV_ERR_ARG, "batch of %zu items is too large", count);
+    sv_config c{};
+    if (cfg) c = *cfg;
+    const int chunk = c.chunk_qubits ? c.chunk_qubits : 5;
+    if (chunk < 4 || chunk > 11) return fail(SV_ERR_ARG, "chunk_qubits must be 4..11 for batches");
+    for (size_t i = 0; i < count; i++) {
+        const sv_batch_item &it = items[i];
+        if (it.n < 1 || it.n > 24) return fail(SV_ERR_ARG, "item %zu: n=%d outside 1..24", i, it.n);
+        if (it.m && !it.gates) return fail(SV_ERR_ARG, "item %zu: gate list is NULL", i);
+        if (!it.qubit_mask || (it.qubit_mask >> it.n))
+            return fail(SV_ERR_ARG, "item %zu: read-out mask empty or beyond n", i);
+        for (size_t g = 0; g < it.m; g++) {
+            std::string why = check_gate(it.n, it.gates[g]);
+            if (!why.empty()) return fail(SV_ERR_ARG, "item %zu gate %zu: %s", i, g, why.c_str());
+        }
+    }
+    // plan and compile every instance (host threads)
+    std::vector<Compiled> comp(count);
+    auto work = [&](size_t lo, size_t hi) {
+        for (size_t i = lo; i < hi; i++) {
+            const sv_batch_item &it = items[i];
+            Compiled &cp = comp[i];
+            cp.nphys = std::max(it.n, kT2Qubits);
+            PlanOptions opt;
+            opt.n = cp.nphys;
+            opt.k = kT2Qubits;
+            opt.c = chunk;
+            opt.merge_diag = !(c.flags & SV_FLAG_NO_DIAG_MERGE);
+            opt.relabel = true;
+            for (int q = 0; q < 64; q++) cp.phys[q] = q;
+            Plan plan;
+            std::vector<sv_gate> gl(it.gates, it.gates + it.m);
+            cp.err = build_plan(gl, opt, cp.phys, &plan);
+            if (!cp.err.empty()) continue;
+            for (const TilePass &tp : plan.passes) {
+                if (tp.ops.empty()) continue;
+                T2Pass t2;
+                std::string why = compile_t2(tp, &t2, false);
+                if (!why.empty()) {
+                    cp.err = "pass cannot run on the register-stage kernel: " + why;
+                    break;
+                }
+                cp.passes.push_back(std::move(t2));
+            }
+        }
+    };
+    {
+        const size_t nth = std::max<size_t>(1, std::min<size_t>(std::thread::hardware_concurrency(), 16));
+        std::vector<std::thread> th;
+        const size_t per = (count + nth - 1) / nth;
+        for (size_t t = 0; t < nth; t++) {
+            const size_t lo = t * per, hi = std::min(count, lo + per);
+            if (lo < hi) th.emplace_back(work, lo, hi);
+        }
+        for (auto &x : th) x.join();
+    }
+    for (size_t i = 0; i < count; i++)
+        if (!comp[i].err.empty()) return fail(SV_ERR_UNSUPPORTED, "item %zu: %s", i, comp[i].err.c_str());
+
+    sv_batch_state *b = new (std::nothrow) sv_batch_state();
+    if (!b) return fail(SV_ERR_OOM, "host allocation failed");
+    b->count = count;
+    auto bail = [&](sv_status st) {
+        destroy(b);
+        return st;
+    };
+
+    // pack programmes; record instance and pass tables with blob offsets
+    Blob blob;
+    std::vector<BatchInst> inst(count);
+    std::vector<T2Args> pass;
+    struct Off { size_t ins, stages, mats, fac, stat, tterms; };
+    std::vector<Off> offs;
+    std::vector<double> cost(count);
+    uint64_t amps = 0;
+    for (size_t i = 0; i < count; i++) {
+        const Compiled &cp = comp[i];
+        BatchInst &bi = inst[i];
+        bi.state_off = amps;
+        amps += UINT64_C(1) << cp.nphys;
+        bi.nphys = cp.nphys;
+        bi.npass = (int)cp.passes.size();
+        bi.pass0 = (int)pass.size();
+        bi.out = (int)i;
+        bi.m = 0;
+        for (int q = 0; q < items[i].n; q++)
+            if ((items[i].qubit_mask >> q) & 1) bi.pos[bi.m++] = cp.phys[q];
+        cost[i] = (double)std::max<size_t>(1, cp.passes.size()) * (double)(UINT64_C(1) << cp.nphys);
+        for (const T2Pass &t2 : cp.passes) {
+            T2Args a{};
+            a.gmask = t2.gmask;
+            a.ntiles = UINT64_C(1) << (cp.nphys - t2.k);
+            a.c = t2.c;
+            a.nins = (int)t2.ins.size();
+            a.nruns = t2.nruns;
+            a.ntterms = (int)t2.tterms.size();
+            for (int s = 0; s < t2.k; s++) a.slot_phys[s] = t2.slot_phys[s];
+            Off o;
+            o.ins = blob.put(t2.ins.data(), t2.ins.size() * sizeof(T2Ins));
+            o.stages = blob.put(t2.stages.data(), t2.stages.size() * sizeof(T2Stage));
+            o.mats = blob.put(t2.mats.data(), t2.mats.size() * sizeof(T2Mat));
+            o.fac = blob.put(t2.factors.data(), t2.factors.size() * sizeof(T2Factor));
+            o.stat = blob.put(t2.stat.data(), t2.stat.size() * sizeof(uint32_t));
+            o.tterms = blob.put(t2.tterms.data(), t2.tterms.size() * sizeof(T2TileTerm));
+            pass.push_back(a);
+            offs.push_back(o);
+            b->total_passes++;
+            b->sweep_bytes += 2.0 * 8.0 * (double)(UINT64_C(1) << cp.nphys);
+        }
+    }
+    std::vector<int> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    const size_t inst_off = blob.put(inst.data(), inst.size() * sizeof(BatchInst));
+    const size_t order_off = blob.put(order.data(), order.size() * sizeof(int));
+    const size_t pass_off = blob.put(nullptr, pass.size() * sizeof(T2Args));
+    blob.put(nullptr, 0);
+    if (cudaGetDevice(&b->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        return bail(fail(SV_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e)));
+    }
+    if (cudaMalloc(&b->prog, blob.b.size() + 256) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(SV_ERR_OOM, "cannot allocate the batch programme (%zu bytes)", blob.b.size()));
+    }
+    const char *dev = reinterpret_cast<const char *>(b->prog);
+    {
+        const sv_status ts = t2_build_tables(&b->tables, &b->err, b->stream);
+        if (ts != SV_OK) return bail(ts);
+    }
+    for (size_t p = 0; p < pass.size(); p++) {
+        pass[p].ins = reinterpret_cast<const int4 *>(dev + offs[p].ins);
+        pass[p].stages = reinterpret_cast<const int4 *>(dev + offs[p].stages);
+        pass[p].mats = reinterpret_cast<const float4 *>(dev + offs[p].mats);
+        pass[p].fac = reinterpret_cast<const int4 *>(dev + offs[p].fac);
+        pass[p].stat = reinterpret_cast<const uint32_t *>(dev + offs[p].stat);
+        pass[p].tterms = reinterpret_cast<const T2TileTerm *>(dev + offs[p].tterms);
+        pass[p].tables = reinterpret_cast<const float2 *>(b->tables);
+        pass[p].err = b->err;
+    }
+    std::memcpy(blob.b.data() + pass_off, pass.data(), pass.size() * sizeof(T2Args));
+    if (cudaMemcpy(b->prog, blob.b.data(), blob.b.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(SV_ERR_CUDA, "programme upload failed"));
+    }
+    b->state_amps = amps;
+    if (cudaMalloc(&b->states, amps * 8) != cudaSuccess || cudaMalloc(&b->queue, 256) != cudaSuccess ||
+        cudaMalloc(&b->out_idx, count * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMalloc(&b->out_p, count * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&b->h_idx, count * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMallocHost(&b->h_p, count * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(SV_ERR_OOM, "cannot allocate batch states (%llu amplitudes)",
+                         (unsigned long long)amps));
+    }
+    BatchArgs args{};
+    args.inst = reinterpret_cast<const BatchInst *>(dev + inst_off);
+    args.passes = reinterpret_cast<const T2Args *>(dev + pass_off);
+    args.order = reinterpret_cast<const int *>(dev + order_off);
+    args.count = (int)count;
+    args.queue = b->queue;
+    args.out_idx = b->out_idx;
+    args.out_p = b->out_p;
+    args.err = b->err;
+    args.tables = reinterpret_cast<const float2 *>(b->tables);
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(SV_ERR_CUDA, "batch set-up failed"));
+    }
+    // capture: queue reset, the persistent launch, results to pinned host memory
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return bail(fail(SV_ERR_CUDA, "stream capture failed to start"));
+    cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream);
+    sv_status lst = t2_batch_launch(reinterpret_cast<float *>(b->states), args, b->sm_count, b->stream);
+    cudaMemcpyAsync(b->h_idx, b->out_idx, count * sizeof(uint64_t), cudaMemcpyDeviceToHost, b->stream);
+    cudaMemcpyAsync(b->h_p, b->out_p, count * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+    if (lst != SV_OK) {
+        if (g) cudaGraphDestroy(g);
+        return bail(lst);
+    }
+    if (ce != cudaSuccess || !g) {
+        cudaGetLastError();
+        return bail(fail(SV_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(ce)));
+    }
+    b->graph = g;
+    if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(SV_ERR_CUDA, "graph instantiation failed"));
+    }
+    cudaEventCreate(&b->ev0);
+    cudaEventCreate(&b->ev1);
+    *out = b;
+    return SV_OK;
+}
+
+sv_status sv_batch_run(sv_batch b, uint64_t *host_idx, double *host_p, double *ms) {
+    clear_error();
+    if (!b) return fail(SV_ERR_ARG, "batch is NULL");
+    SV_CUDA(cudaEventRecord(b->ev0, b->stream));
+    SV_CUDA(cudaGraphLaunch(b->exec, b->stream));
+    SV_CUDA(cudaEventRecord(b->ev1, b->stream));
+    SV_CUDA(cudaStreamSynchronize(b->stream));
+    int flag = 0;
+    SV_CUDA(cudaMemcpy(&flag, b->err, sizeof flag, cudaMemcpyDeviceToHost));
+    if (flag) return fail(SV_ERR_TIMEOUT, "a batched kernel gave up waiting for its bulk copies");
+    if (ms) {
+        float t = 0.f;
+        SV_CUDA(cudaEventElapsedTime(&t, b->ev0, b->ev1));
+        *ms = t;
+    }
+    if (host_idx) std::memcpy(host_idx, b->h_idx, b->count * sizeof(uint64_t));
+    if (host_p) std::memcpy(host_p, b->h_p, b->count * sizeof(double));
+    return SV_OK;
+}
+
+sv_status sv_batch_info(sv_batch b, size_t *count, int *passes, double *sweep_bytes) {
+    clear_error();
+    if (!b) return fail(SV_ERR_ARG, "batch is NULL");
+    if (count) *count = b->count;
+    if (passes) *passes = b->total_passes;
+    if (sweep_bytes) *sweep_bytes = b->sweep_bytes;
+    return SV_OK;
+}
+
+sv_status sv_batch_destroy(sv_batch b) {
+    clear_error();
+    destroy(b);
+    return SV_OK;
+}
+
+sv_status sv_apply_circuit_batch(const sv_batch_item *items, size_t count, const sv_config *cfg,
+                                 uint64_t *host_idx, double *host_p) {
+    sv_batch b = nullptr;
+    SV_TRY(sv_batch_create(items, count, cfg, &b));
+    sv_status st = sv_batch_run(b, host_idx, host_p, nullptr);
+    destroy(b);
+    return st;
+}
+
+}  // extern "C"

@@ -127,6 +127,9 @@ sv_status t3_prepare(sv_state *h);
 sv_status t3_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta);
 // Multiply the state by the pending norm correction of the last fused pass.
 sv_status resolve_norm(sv_state *h);
+struct BatchArgs;
+sv_status t2_build_tables(void **tables, int **err, cudaStream_t stream);
+sv_status t2_batch_launch(float *states, const BatchArgs &b, int sm_count, cudaStream_t stream);
 // SV_ERR_TIMEOUT if a kernel of this handle reported a bounded wait that gave up.
 sv_status check_device_flag(sv_state *h);
 sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates_logical,

@@ -1,6 +1,8 @@
 // Compiled register-stage programme of one tile pass (complex64).
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <string>
 #include <vector>
 
@@ -36,6 +38,43 @@ struct T2Device {
     const uint32_t *stat;
     const T2TileTerm *tterms;
     const float *blocks;
+};
+
+// Launch parameters of one register-stage pass (device pointers).
+struct T2Args {
+    uint64_t gmask, ntiles;
+    int c, nins, nruns, ntterms;
+    int slot_phys[kMaxTileQubits];
+    const int4 *ins;       // T2Ins records
+    const int4 *stages;    // T2Stage records
+    const float4 *mats;    // T2Mat records (two float4 each)
+    const int4 *fac;       // T2Factor records
+    const uint32_t *stat;  // per-thread static phases
+    const T2TileTerm *tterms;
+    const float2 *tables;
+    int *err;
+};
+
+// One instance of a batch: its state, passes and read-out qubits.
+struct BatchInst {
+    uint64_t state_off;  // in amplitudes
+    int npass, pass0;    // passes [pass0, pass0 + npass) of the batch's pass table
+    int nphys;           // qubits of the stored state (>= 13)
+    int m;               // read-out qubits
+    int out;             // result slot
+    int pos[34];         // physical bit of read-out bit j
+};
+
+struct BatchArgs {
+    const BatchInst *inst;
+    const T2Args *passes;
+    const int *order;  // processing order (largest first)
+    int count;
+    int *queue;
+    uint64_t *out_idx;
+    double *out_p;
+    int *err;
+    const float2 *tables;
 };
 
 // Compile a tile pass; returns "" on success or the reason the pass cannot

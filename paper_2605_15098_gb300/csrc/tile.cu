@@ -242,8 +242,8 @@ struct Blob {
     std::vector<char> b;
     size_t put(const void *p, size_t n) {
         const size_t off = (b.size() + 255) & ~(size_t)255;
-        b.resize(off + n);
-        if (n) std::memcpy(b.data() + off, p, n);
+        b.resize(off + n);  // zero-filled
+        if (n && p) std::memcpy(b.data() + off, p, n);
         return off;
     }
     template <typename T>

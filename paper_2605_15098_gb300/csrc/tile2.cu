@@ -38,21 +38,163 @@ constexpr size_t kOffCst = kOffLin + (size_t)kT2MaxRuns * 16 * 4;
 constexpr size_t kOffBar = kOffCst + (size_t)kT2MaxRuns * 4;
 constexpr size_t kSmemBytes = kOffBar + 16;
 
-struct T2Args {
-    uint64_t gmask, ntiles;
-    int c, nins, nruns, ntterms;
-    int slot_phys[kMaxTileQubits];
-    const int4 *ins;      // T2Ins records
-    const int4 *stages;   // T2Stage records
-    const float4 *mats;   // T2Mat records (two float4 each)
-    const int4 *fac;      // T2Factor records
-    const uint32_t *stat; // per-thread static phases
-    const T2TileTerm *tterms;
-    const float2 *tables;
-    int *err;
-};
 
 // ---------------------------------------------------------------- the kernel
+// Run a pass's programme on the tile in shared memory (interleaved complex64,
+// local index order) and leave the result there, interleaved.
+__device__ __forceinline__ void t2_run(const T2Args &a, float4 *tile4, const float2 *tab,
+                                       const uint32_t *lin, const uint32_t *cst, uint64_t base,
+                                       int tid) {
+    Regs r;
+    int bt = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;  // current layout: thread base, register strides
+    int stage = 0;
+    bool live = false;
+    auto sidx = [&](int q) {
+        return (bt + ((q & 1) ? s1 : 0) + ((q & 2) ? s2 : 0) + ((q & 4) ? s3 : 0) +
+                ((q & 8) ? s4 : 0)) >> 1;
+    };
+    for (int pc = 0; pc < a.nins; pc++) {
+        const int4 w = __ldg(a.ins + pc);
+        const int op = w.x & 0xff;
+        if (op == T2_STAGE) {
+            if (live) {
+#pragma unroll
+                for (int q = 0; q < kNP; q++)
+                    tile4[sidx(q)] = make_float4(r.re[q].x, r.re[q].y, r.im[q].x, r.im[q].y);
+                __syncthreads();
+            }
+            stage = w.w;
+            const int4 st = __ldg(a.stages + stage);
+            auto tbyte = [&](int i) {
+                const int word = i < 4 ? st.x : i < 8 ? st.y : i < 12 ? st.z : st.w;
+                return (word >> (8 * (i & 3))) & 0xff;
+            };
+            bt = 0;
+#pragma unroll
+            for (int t = 0; t < 8; t++) bt |= ((tid >> t) & 1) << tbyte(5 + t);
+            s1 = 1 << tbyte(1);
+            s2 = 1 << tbyte(2);
+            s3 = 1 << tbyte(3);
+            s4 = 1 << tbyte(4);
+#pragma unroll
+            for (int q = 0; q < kNP; q++) {
+                const float4 v = tile4[sidx(q)];
+                if (live) {
+                    r.re[q] = make_float2(v.x, v.y);
+                    r.im[q] = make_float2(v.z, v.w);
+                } else {
+                    r.re[q] = make_float2(v.x, v.z);
+                    r.im[q] = make_float2(v.y, v.w);
+                }
+            }
+            live = true;
+            continue;
+        }
+        if (op == T2_SCALE) {
+            const float4 mm = __ldg(a.mats + 2 * w.w);
+            const float hi = mm.x, lo = mm.y;
+#pragma unroll
+            for (int q = 0; q < kNP; q++) {
+                r.re[q] = fma2(r.re[q], f2(hi), mul2(r.re[q], f2(lo)));
+                r.im[q] = fma2(r.im[q], f2(hi), mul2(r.im[q], f2(lo)));
+            }
+            continue;
+        }
+        if (op == T2_DIAG) {
+            const int e0 = (int16_t)(w.z & 0xffff), e1 = (int16_t)(w.z >> 16);
+            for (int e = e0; e < e1; e++) {
+                const int4 fd = __ldg(a.fac + e);
+                const uint32_t w0 = (uint32_t)fd.x;
+                const int run = fd.y;
+                float fr, fi;
+                if (!(w0 & 0x100u)) {
+                    fr = __int_as_float(fd.z);
+                    fi = __int_as_float(fd.w);
+                } else {
+                    uint32_t u = __ldg(a.stat + fd.z * 256 + tid);
+                    if (w0 & 0x200u) u += cst[run];
+                    const int lr = (int)((w0 >> 16) & 0xff) - 1;
+                    if (lr >= 0) u += lin[run * 16 + lr];
+                    uint32_t dm = (w0 >> 24) & (uint32_t)tid;
+                    while (dm) {
+                        const int t = __ffs(dm) - 1;
+                        dm &= dm - 1;
+                        const int8_t *tbp = reinterpret_cast<const int8_t *>(a.stages + stage);
+                        u += lin[run * 16 + tbp[5 + t]];
+                    }
+                    const float2 f0 = tab[u >> 21];
+                    const float2 f1 = tab[kTab0 + ((u >> 10) & 2047u)];
+                    const float2 fz = tab[kTab0 + kTab1 + (u & 1023u)];
+                    const float2 ff = cx(cx(f0, f1), fz);
+                    fr = ff.x;
+                    fi = ff.y;
+                }
+                apply_factor_any(r, (int)(w0 & 0xffu), fr, fi);
+            }
+            continue;
+        }
+        // gates
+        const int cls = (w.x >> 8) & 0xff;
+        const int j = (int8_t)((w.x >> 16) & 0xff);
+        const int ccls = (w.x >> 24) & 0xff;
+        const int cidx = (int16_t)(w.y & 0xffff);
+        bool pred = true;
+        int jc = -1;
+        if (ccls == T2C_GLOBAL) {
+            if (!((base >> cidx) & 1)) continue;  // tile-uniform
+        } else if (ccls == T2C_THREAD) {
+            pred = (tid >> cidx) & 1;
+        } else if (ccls == T2C_REG) {
+            jc = cidx;
+        }
+        float m[8];
+        if (op == T2_GATE) {
+            const float4 m0 = __ldg(a.mats + 2 * w.w), m1 = __ldg(a.mats + 2 * w.w + 1);
+            m[0] = m0.x; m[1] = m0.y; m[2] = m0.z; m[3] = m0.w;
+            m[4] = m1.x; m[5] = m1.y; m[6] = m1.z; m[7] = m1.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; e++) m[e] = 0.f;
+        }
+        if (cls == T2C_LANE) {
+            lane_gate(r, op, j, jc, pred, m);
+            continue;
+        }
+        if (!pred) continue;
+        if (op == T2_H) {
+            switch (j) {
+                case 0: reg_h<0>(r, jc); break;
+                case 1: reg_h<1>(r, jc); break;
+                case 2: reg_h<2>(r, jc); break;
+                case 3: reg_h<3>(r, jc); break;
+                default: reg_h<4>(r, jc); break;
+            }
+        } else if (op == T2_X) {
+            switch (j) {
+                case 0: reg_x<0>(r, jc); break;
+                case 1: reg_x<1>(r, jc); break;
+                case 2: reg_x<2>(r, jc); break;
+                case 3: reg_x<3>(r, jc); break;
+                default: reg_x<4>(r, jc); break;
+            }
+        } else {
+            switch (j) {
+                case 0: reg_u<0>(r, jc, m); break;
+                case 1: reg_u<1>(r, jc, m); break;
+                case 2: reg_u<2>(r, jc, m); break;
+                case 3: reg_u<3>(r, jc, m); break;
+                default: reg_u<4>(r, jc, m); break;
+            }
+        }
+    }
+    // epilogue: interleaved tile back to shared memory, then TMA store
+    if (live) {
+#pragma unroll
+        for (int q = 0; q < kNP; q++)
+            tile4[sidx(q)] = make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y);
+    }
+}
+
 __global__ void __launch_bounds__(kT2Threads, 2) k_tile2(float *__restrict__ state, const T2Args a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     float4 *tile4 = reinterpret_cast<float4 *>(sm);
@@ -104,154 +246,7 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_tile2(float *__restrict__ sta
             return;
         }
 
-        Regs r;
-        int bt = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;  // current layout: thread base, register strides
-        int stage = 0;
-        bool live = false;
-        auto sidx = [&](int q) {
-            return (bt + ((q & 1) ? s1 : 0) + ((q & 2) ? s2 : 0) + ((q & 4) ? s3 : 0) +
-                    ((q & 8) ? s4 : 0)) >> 1;
-        };
-        for (int pc = 0; pc < a.nins; pc++) {
-            const int4 w = __ldg(a.ins + pc);
-            const int op = w.x & 0xff;
-            if (op == T2_STAGE) {
-                if (live) {
-#pragma unroll
-                    for (int q = 0; q < kNP; q++)
-                        tile4[sidx(q)] = make_float4(r.re[q].x, r.re[q].y, r.im[q].x, r.im[q].y);
-                    __syncthreads();
-                }
-                stage = w.w;
-                const int4 st = __ldg(a.stages + stage);
-                auto tbyte = [&](int i) {
-                    const int word = i < 4 ? st.x : i < 8 ? st.y : i < 12 ? st.z : st.w;
-                    return (word >> (8 * (i & 3))) & 0xff;
-                };
-                bt = 0;
-#pragma unroll
-                for (int t = 0; t < 8; t++) bt |= ((tid >> t) & 1) << tbyte(5 + t);
-                s1 = 1 << tbyte(1);
-                s2 = 1 << tbyte(2);
-                s3 = 1 << tbyte(3);
-                s4 = 1 << tbyte(4);
-#pragma unroll
-                for (int q = 0; q < kNP; q++) {
-                    const float4 v = tile4[sidx(q)];
-                    if (live) {
-                        r.re[q] = make_float2(v.x, v.y);
-                        r.im[q] = make_float2(v.z, v.w);
-                    } else {
-                        r.re[q] = make_float2(v.x, v.z);
-                        r.im[q] = make_float2(v.y, v.w);
-                    }
-                }
-                live = true;
-                continue;
-            }
-            if (op == T2_SCALE) {
-                const float4 mm = __ldg(a.mats + 2 * w.w);
-                const float hi = mm.x, lo = mm.y;
-#pragma unroll
-                for (int q = 0; q < kNP; q++) {
-                    r.re[q] = fma2(r.re[q], f2(hi), mul2(r.re[q], f2(lo)));
-                    r.im[q] = fma2(r.im[q], f2(hi), mul2(r.im[q], f2(lo)));
-                }
-                continue;
-            }
-            if (op == T2_DIAG) {
-                const int e0 = (int16_t)(w.z & 0xffff), e1 = (int16_t)(w.z >> 16);
-                for (int e = e0; e < e1; e++) {
-                    const int4 fd = __ldg(a.fac + e);
-                    const uint32_t w0 = (uint32_t)fd.x;
-                    const int run = fd.y;
-                    float fr, fi;
-                    if (!(w0 & 0x100u)) {
-                        fr = __int_as_float(fd.z);
-                        fi = __int_as_float(fd.w);
-                    } else {
-                        uint32_t u = __ldg(a.stat + fd.z * 256 + tid);
-                        if (w0 & 0x200u) u += cst[run];
-                        const int lr = (int)((w0 >> 16) & 0xff) - 1;
-                        if (lr >= 0) u += lin[run * 16 + lr];
-                        uint32_t dm = (w0 >> 24) & (uint32_t)tid;
-                        while (dm) {
-                            const int t = __ffs(dm) - 1;
-                            dm &= dm - 1;
-                            const int8_t *tbp = reinterpret_cast<const int8_t *>(a.stages + stage);
-                            u += lin[run * 16 + tbp[5 + t]];
-                        }
-                        const float2 f0 = tab[u >> 21];
-                        const float2 f1 = tab[kTab0 + ((u >> 10) & 2047u)];
-                        const float2 fz = tab[kTab0 + kTab1 + (u & 1023u)];
-                        const float2 ff = cx(cx(f0, f1), fz);
-                        fr = ff.x;
-                        fi = ff.y;
-                    }
-                    apply_factor_any(r, (int)(w0 & 0xffu), fr, fi);
-                }
-                continue;
-            }
-            // gates
-            const int cls = (w.x >> 8) & 0xff;
-            const int j = (int8_t)((w.x >> 16) & 0xff);
-            const int ccls = (w.x >> 24) & 0xff;
-            const int cidx = (int16_t)(w.y & 0xffff);
-            bool pred = true;
-            int jc = -1;
-            if (ccls == T2C_GLOBAL) {
-                if (!((base >> cidx) & 1)) continue;  // tile-uniform
-            } else if (ccls == T2C_THREAD) {
-                pred = (tid >> cidx) & 1;
-            } else if (ccls == T2C_REG) {
-                jc = cidx;
-            }
-            float m[8];
-            if (op == T2_GATE) {
-                const float4 m0 = __ldg(a.mats + 2 * w.w), m1 = __ldg(a.mats + 2 * w.w + 1);
-                m[0] = m0.x; m[1] = m0.y; m[2] = m0.z; m[3] = m0.w;
-                m[4] = m1.x; m[5] = m1.y; m[6] = m1.z; m[7] = m1.w;
-            } else {
-#pragma unroll
-                for (int e = 0; e < 8; e++) m[e] = 0.f;
-            }
-            if (cls == T2C_LANE) {
-                lane_gate(r, op, j, jc, pred, m);
-                continue;
-            }
-            if (!pred) continue;
-            if (op == T2_H) {
-                switch (j) {
-                    case 0: reg_h<0>(r, jc); break;
-                    case 1: reg_h<1>(r, jc); break;
-                    case 2: reg_h<2>(r, jc); break;
-                    case 3: reg_h<3>(r, jc); break;
-                    default: reg_h<4>(r, jc); break;
-                }
-            } else if (op == T2_X) {
-                switch (j) {
-                    case 0: reg_x<0>(r, jc); break;
-                    case 1: reg_x<1>(r, jc); break;
-                    case 2: reg_x<2>(r, jc); break;
-                    case 3: reg_x<3>(r, jc); break;
-                    default: reg_x<4>(r, jc); break;
-                }
-            } else {
-                switch (j) {
-                    case 0: reg_u<0>(r, jc, m); break;
-                    case 1: reg_u<1>(r, jc, m); break;
-                    case 2: reg_u<2>(r, jc, m); break;
-                    case 3: reg_u<3>(r, jc, m); break;
-                    default: reg_u<4>(r, jc, m); break;
-                }
-            }
-        }
-        // epilogue: interleaved tile back to shared memory, then TMA store
-        if (live) {
-#pragma unroll
-            for (int q = 0; q < kNP; q++)
-                tile4[sidx(q)] = make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y);
-        }
+        t2_run(a, tile4, tab, lin, cst, base, tid);
         fence_async_smem();
         __syncthreads();
         if (tid < 32) {
@@ -266,6 +261,155 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_tile2(float *__restrict__ sta
         }
         __syncthreads();
         parity ^= 1u;
+    }
+}
+
+// ---------------------------------------------------------------- batched instances
+// One CTA runs whole instances taken from a shared queue (largest first): all
+// passes of the instance (the first pass starts from |0...0> in shared memory
+// instead of reading the state), then the FP64 argmax of the marginal over
+// the instance's read-out qubits.  States of up to 2^20 amplitudes stay in L2.
+__global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ states, const BatchArgs B) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    float4 *tile4 = reinterpret_cast<float4 *>(sm);
+    float2 *tab = reinterpret_cast<float2 *>(sm + kOffTab);
+    uint32_t *lin = reinterpret_cast<uint32_t *>(sm + kOffLin);
+    uint32_t *cst = reinterpret_cast<uint32_t *>(sm + kOffCst);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kOffBar);
+    __shared__ int s_item;
+    // read-out reduction scratch lives in the tile buffer (free after the last pass)
+    double *s_val = reinterpret_cast<double *>(sm);
+    uint64_t *s_idx = reinterpret_cast<uint64_t *>(sm + 8 * kT2Threads);
+    double *s_tot = reinterpret_cast<double *>(sm + 16 * kT2Threads);
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kTabEntries; i += blockDim.x) tab[i] = B.tables[i];
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t parity = 0;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(B.queue, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= B.count) break;
+        const BatchInst &I = B.inst[B.order[item]];
+        float *state = states + 2 * I.state_off;
+        if (I.npass == 0) {  // empty circuit: |0...0>
+            float4 *sv4 = reinterpret_cast<float4 *>(state);
+            for (uint64_t v = tid; v < (UINT64_C(1) << I.nphys) / 2; v += blockDim.x)
+                sv4[v] = make_float4(v == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
+            __syncthreads();
+        }
+        for (int p = 0; p < I.npass; p++) {
+            const T2Args &a = B.passes[I.pass0 + p];
+            const int nchunks = 1 << (kT2Qubits - a.c);
+            const uint32_t chunk_bytes = 8u << a.c;
+            for (uint64_t tile = 0; tile < a.ntiles; tile++) {
+                const uint64_t base = pdep(tile, a.gmask);
+                if (p == 0) {
+                    for (int v = tid; v < (1 << kT2Qubits) / 2; v += blockDim.x)
+                        tile4[v] = make_float4((v == 0 && base == 0) ? 1.f : 0.f, 0.f, 0.f, 0.f);
+                } else if (tid < 32) {
+                    if (tid == 0) {
+                        fence_async_smem();
+                        mbar_expect_tx(bar, kTileBytes);
+                    }
+                    __syncwarp();
+                    for (int j = tid; j < nchunks; j += 32) {
+                        uint64_t off = 0;
+                        for (int b = 0; b < kT2Qubits - a.c; b++)
+                            if ((j >> b) & 1) off |= UINT64_C(1) << a.slot_phys[a.c + b];
+                        bulk_g2s(sm + (size_t)j * chunk_bytes, state + 2 * (base + off), chunk_bytes, bar);
+                    }
+                }
+                for (int i = tid; i < a.nruns * 16; i += blockDim.x) lin[i] = 0u;
+                for (int i = tid; i < a.nruns; i += blockDim.x) cst[i] = 0u;
+                __syncthreads();
+                for (int i = tid; i < a.ntterms; i += blockDim.x) {
+                    const T2TileTerm t = a.tterms[i];
+                    bool on = (base >> t.g0) & 1;
+                    if (t.g1 >= 0) on = on && ((base >> t.g1) & 1);
+                    if (on) atomicAdd(t.tb >= 0 ? &lin[t.run * 16 + t.tb] : &cst[t.run], t.theta);
+                }
+                bool timed_out = false;
+                if (p > 0) {
+                    timed_out = !mbar_wait(bar, parity);
+                    parity ^= 1u;
+                }
+                if (__syncthreads_or(timed_out)) {
+                    if (tid == 0) atomicExch(B.err, 1);
+                    mbar_wait(bar, parity ^ 1u);
+                    return;
+                }
+                t2_run(a, tile4, tab, lin, cst, base, tid);
+                fence_async_smem();
+                __syncthreads();
+                if (tid < 32) {
+                    for (int j = tid; j < nchunks; j += 32) {
+                        uint64_t off = 0;
+                        for (int b = 0; b < kT2Qubits - a.c; b++)
+                            if ((j >> b) & 1) off |= UINT64_C(1) << a.slot_phys[a.c + b];
+                        bulk_s2g(state + 2 * (base + off), sm + (size_t)j * chunk_bytes, chunk_bytes);
+                    }
+                    bulk_commit();
+                    bulk_wait_read();
+                }
+                __syncthreads();
+            }
+            // the next pass (or the read-out) reads what this pass wrote
+            if (tid < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+            asm volatile("fence.proxy.async;" ::: "memory");
+            __syncthreads();
+        }
+        // read-out: argmax (lowest index among ties) of the FP64 marginal over I.pos
+        uint64_t mask = 0;
+        for (int j = 0; j < I.m; j++) mask |= UINT64_C(1) << I.pos[j];
+        const uint64_t all = (UINT64_C(1) << I.nphys) - 1;
+        const uint64_t rest = all & ~mask;
+        const uint64_t outcomes = UINT64_C(1) << I.m;
+        double best = -1.0, tot = 0.0;
+        uint64_t bidx = ~UINT64_C(0);
+        for (uint64_t y = tid; y < outcomes; y += blockDim.x) {
+            uint64_t xy = 0;
+            for (int j = 0; j < I.m; j++)
+                if ((y >> j) & 1) xy |= UINT64_C(1) << I.pos[j];
+            double acc = 0.0;
+            uint64_t xr = 0;
+            do {
+                const float2 amp = reinterpret_cast<const float2 *>(state)[xy | xr];
+                acc += (double)amp.x * amp.x + (double)amp.y * amp.y;
+                xr = ((xr | ~rest) + 1) & rest;
+            } while (xr);
+            tot += acc;
+            if (acc > best) {
+                best = acc;
+                bidx = y;
+            }
+        }
+        s_val[tid] = best;
+        s_idx[tid] = bidx;
+        s_tot[tid] = tot;
+        __syncthreads();
+        for (int w = kT2Threads / 2; w; w >>= 1) {
+            if (tid < w) {
+                const double v2 = s_val[tid + w];
+                const uint64_t i2 = s_idx[tid + w];
+                if (v2 > s_val[tid] || (v2 == s_val[tid] && i2 < s_idx[tid])) {
+                    s_val[tid] = v2;
+                    s_idx[tid] = i2;
+                }
+                s_tot[tid] += s_tot[tid + w];
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            B.out_idx[I.out] = s_idx[0];
+            B.out_p[I.out] = s_tot[0] > 0.0 ? s_val[0] / s_tot[0] : 0.0;
+        }
+        __syncthreads();
     }
 }
 
@@ -338,6 +482,38 @@ sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
     note_launch();
     prof_end(h, slot, meta);
     h->stats.kernels++;
+    return SV_OK;
+}
+
+sv_status t2_build_tables(void **tables, int **err, cudaStream_t stream) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, kTabEntries * sizeof(float2) + 64) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SV_ERR_OOM, "cannot allocate phase tables");
+    }
+    *tables = p;
+    *err = reinterpret_cast<int *>(reinterpret_cast<char *>(p) + kTabEntries * sizeof(float2));
+    SV_CUDA(cudaMemsetAsync(*err, 0, sizeof(int), stream));
+    k_phase_tables<<<(kTabEntries + 255) / 256, 256, 0, stream>>>(reinterpret_cast<float2 *>(p));
+    SV_CUDA(cudaGetLastError());
+    note_launch();
+    return SV_OK;
+}
+
+sv_status t2_batch_launch(float *states, const BatchArgs &b, int sm_count, cudaStream_t stream) {
+    static bool configured = false;
+    if (!configured) {
+        SV_CUDA(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kSmemBytes));
+        configured = true;
+    }
+    int per_sm = 0;
+    SV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kT2Threads, kSmemBytes));
+    if (per_sm < 1) return fail(SV_ERR_UNSUPPORTED, "batched kernel does not fit on an SM");
+    const int grid = std::max(1, std::min(b.count, per_sm * sm_count));
+    k_batch<<<grid, kT2Threads, kSmemBytes, stream>>>(states, b);
+    SV_CUDA(cudaGetLastError());
+    note_launch();
     return SV_OK;
 }
 

@@ -29,6 +29,7 @@ EXPORTS = (
     "sv_apply_circuit", "sv_last_stats", "sv_probabilities", "sv_probabilities_device",
     "sv_argmax", "sv_sample", "sv_copy_out", "sv_copy_in", "sv_last_error", "sv_version",
     "sv_profile", "sv_profile_read", "sv_launch_count", "sv_marginal_noalloc", "sv_plan_export",
+    "sv_batch_create", "sv_batch_run", "sv_batch_info", "sv_batch_destroy", "sv_apply_circuit_batch",
 )
 SV_KERNEL_PERGATE, SV_KERNEL_TILE, SV_KERNEL_REMAP, SV_KERNEL_FUSED = 0, 1, 2, 3
 
@@ -71,6 +72,11 @@ class sv_launch_record(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class sv_batch_item(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("reserved", ctypes.c_int32), ("gates", ctypes.c_void_p),
+                ("m", ctypes.c_size_t), ("qubit_mask", ctypes.c_uint64)]
+
+
 _lib = None
 
 
@@ -102,6 +108,11 @@ def lib() -> ctypes.CDLL:
         "sv_marginal_noalloc": [vp, i32, i32, vp, u64, vp, vp],
         "sv_plan_export": [i32, i32, vp, vp, sz, ctypes.POINTER(sv_config), vp, sz,
                            ctypes.POINTER(sz)],
+        "sv_batch_create": [vp, sz, ctypes.POINTER(sv_config), ctypes.POINTER(vp)],
+        "sv_batch_run": [vp, vp, vp, dp],
+        "sv_batch_info": [vp, ctypes.POINTER(sz), ctypes.POINTER(i32), dp],
+        "sv_batch_destroy": [vp],
+        "sv_apply_circuit_batch": [vp, sz, ctypes.POINTER(sv_config), vp, vp],
         "sv_profile_read": [vp, vp, sz, ctypes.POINTER(sz)],
     }
     for name, args in sig.items():
@@ -256,6 +267,56 @@ def sv_plan_export(n: int, dtype: int, gates: np.ndarray, cfg: sv_config | None 
     buf = ctypes.create_string_buffer(ln.value + 1)
     _check(lib().sv_plan_export(*args, buf, ln.value + 1, ctypes.byref(ln)))
     return json.loads(buf.value.decode())
+
+
+def _batch_items(circuits):
+    """circuits: list of (n, gate array, qubit_mask); returns (ctypes array, keep-alive list)."""
+    keep = []
+    arr = (sv_batch_item * len(circuits))()
+    for i, (n, g, mask) in enumerate(circuits):
+        g = np.ascontiguousarray(g, dtype=GATE_DTYPE)
+        keep.append(g)
+        arr[i] = sv_batch_item(n, 0, g.ctypes.data if g.size else None, g.size, mask)
+    return arr, keep
+
+
+def sv_batch_create(circuits, cfg: sv_config | None = None) -> int:
+    arr, keep = _batch_items(circuits)
+    b = ctypes.c_void_p()
+    _check(lib().sv_batch_create(arr, len(circuits), ctypes.byref(cfg) if cfg is not None else None,
+                                 ctypes.byref(b)))
+    del keep
+    return b.value
+
+
+def sv_batch_run(b: int, count: int):
+    idx = np.empty(count, dtype=np.uint64)
+    p = np.empty(count, dtype=np.float64)
+    ms = ctypes.c_double()
+    _check(lib().sv_batch_run(ctypes.c_void_p(b), idx.ctypes.data, p.ctypes.data, ctypes.byref(ms)))
+    return idx, p, ms.value
+
+
+def sv_batch_info(b: int) -> dict:
+    cnt, passes, sb = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().sv_batch_info(ctypes.c_void_p(b), ctypes.byref(cnt), ctypes.byref(passes),
+                               ctypes.byref(sb)))
+    return {"count": cnt.value, "passes": passes.value, "sweep_bytes": sb.value}
+
+
+def sv_batch_destroy(b: int) -> None:
+    _check(lib().sv_batch_destroy(ctypes.c_void_p(b)))
+
+
+def sv_apply_circuit_batch(circuits, cfg: sv_config | None = None):
+    arr, keep = _batch_items(circuits)
+    idx = np.empty(len(circuits), dtype=np.uint64)
+    p = np.empty(len(circuits), dtype=np.float64)
+    _check(lib().sv_apply_circuit_batch(arr, len(circuits),
+                                        ctypes.byref(cfg) if cfg is not None else None,
+                                        idx.ctypes.data, p.ctypes.data))
+    del keep
+    return idx, p
 
 
 def sv_launch_count() -> int:

@@ -75,3 +75,20 @@ def test_host_validation_rejects_without_device(svlib):
     assert lib.sv_create_on(5, 0, ctypes.c_void_p(16), 1 << 20, None,
                             ctypes.byref(h)) == svlib.SV_ERR_ARG
     assert "aligned" in svlib.sv_last_error()
+
+
+def test_batch_host_path_without_device(svlib):
+    """sv_batch_create plans and packs every item on the host before any CUDA
+    call; without a device it must stop with SV_ERR_CUDA, not crash."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("host-only check")
+    work = C.qpe_batch(40, seed=5)
+    with pytest.raises(svlib.SvError) as e:
+        svlib.sv_batch_create([(n, g, m) for n, g, m, _ in work])
+    assert e.value.code == svlib.SV_ERR_CUDA
+    bad = [(5, C.gates([C.h(7)]), 1)]
+    with pytest.raises(svlib.SvError) as e:
+        svlib.sv_batch_create(bad)
+    assert e.value.code == svlib.SV_ERR_ARG

@@ -295,3 +295,44 @@ def test_fused_qpe_full_size(sv, n):
         idx, p = s.argmax(info["mask"])
         assert idx == info["y"] and abs(p - 1.0) <= 1e-5
         assert s.argmax((1 << n) - 1)[0] == expected
+
+
+def test_batch_qpe_outcomes(sv, orc):
+    """Batched QPE instances (n uniform in 10..20) in one graph-captured launch:
+    every outcome equals the oracle's argmax (small n) and the closed form."""
+    work = C.qpe_batch(96, seed=777)
+    b = sv.sv_batch_create([(n, g, m) for n, g, m, _ in work])
+    try:
+        idx, p, ms = sv.sv_batch_run(b, len(work))
+        idx2, p2, _ = sv.sv_batch_run(b, len(work))  # replay gives the same results
+        info = sv.sv_batch_info(b)
+    finally:
+        sv.sv_batch_destroy(b)
+    assert np.array_equal(idx, idx2) and np.array_equal(p, p2)
+    assert info["count"] == len(work) and info["passes"] >= len(work)
+    for i, (n, g, mask, y) in enumerate(work):
+        assert int(idx[i]) == y, (i, n)
+        assert abs(p[i] - 1.0) <= 1e-5
+        if n <= 14:
+            ref = orc.marginal(n, orc.run(n, g), mask)
+            assert int(idx[i]) == orc.argmax(ref)[0]
+
+
+def test_batch_mixed_circuits_match_single(sv):
+    """Batch read-outs equal those of the single-state API on the same circuits."""
+    from gen import mixed_circuit
+    rng = np.random.default_rng(3)
+    circ = []
+    for i in range(24):
+        n = int(rng.integers(5, 17))
+        g = mixed_circuit(n, 40, 60 + i, kinds=(0, 1, 2, 3, 4, 5, 6, 7, 9, 10))
+        circ.append((n, g, (1 << n) - 1))
+    idx, p = sv.sv_apply_circuit_batch(circ)
+    for i, (n, g, mask) in enumerate(circ):
+        with sv.State(n, sv.SV_C128) as s:
+            s.apply(g, sv.make_config(sv.SV_MODE_PERGATE))
+            probs = s.probabilities(mask)
+        top = np.sort(probs)[-2:]
+        if top[1] - top[0] > 1e-5:  # a clear maximum: same index
+            assert int(idx[i]) == int(np.argmax(probs))
+        assert abs(p[i] - probs.max()) <= 1e-5
