@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fused", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -241,14 +242,20 @@ def run_ours(args, world, rank, local):
     amp_bytes = 8 if dt == sv.SV_C64 else 16
     gates, expected, info = C.qpe(n)
     mask = info["mask"]
-    mode = sv.SV_MODE_FUSED if (dt == sv.SV_C64 and not args.no_fused) else sv.SV_MODE_PARTITIONED
-    cfg = sv.make_config(mode, tile_qubits=args.tile, chunk_qubits=args.chunk)
-    state_bytes = (1 << n) * amp_bytes
-
     stream = torch.cuda.Stream()
     buf = torch.empty(1 << n, dtype=torch.complex64 if dt == sv.SV_C64 else torch.complex128,
                       device="cuda")
+    state_bytes = (1 << n) * amp_bytes
     h = sv.sv_create_on(n, dt, buf.data_ptr(), state_bytes, stream.cuda_stream)
+    # configuration chosen by the library's autotuner (mode x chunk width x tile width)
+    if args.tile or args.chunk or args.no_autotune:
+        mode = sv.SV_MODE_FUSED if (dt == sv.SV_C64 and not args.no_fused) else sv.SV_MODE_PARTITIONED
+        cfg = sv.make_config(mode, tile_qubits=args.tile, chunk_qubits=args.chunk)
+        tuned = None
+    else:
+        cfg, tuned_ms = sv.sv_autotune(h, gates)
+        mode = cfg.mode
+        tuned = {"chosen": sv.config_dict(cfg), "median_ms": tuned_ms}
 
     def step(c=cfg):
         sv.sv_reset(h)
@@ -309,11 +316,12 @@ def run_ours(args, world, rank, local):
         "data": f"synthetic: seeded QPE circuit (splitmix64 seed {C.DEFAULT_SEED}, a_i={info['a']})",
         "config": {
             "workload": f"QPE n={n} ({n - 4} counting + 4 eigenstate qubits, {len(gates)} gates), "
-                        f"{'complex64' if dt == sv.SV_C64 else 'complex128'}, partitioned tile passes",
-            "n": n, "gates": len(gates), "mode": "fused" if mode == sv.SV_MODE_FUSED else "partitioned",
+                        f"{'complex64' if dt == sv.SV_C64 else 'complex128'}, {sv.config_dict(cfg)['mode']} tile passes",
+            "n": n, "gates": len(gates), "mode": sv.config_dict(cfg)["mode"],
             "passes": st["passes"], "fused_blocks": st["fused_blocks"],
-            "relabels": st["relabels"], "tile_qubits": args.tile or (13 if dt == sv.SV_C64 else 12),
-            "chunk_qubits": args.chunk or (5 if dt == sv.SV_C64 else 4),
+            "relabels": st["relabels"],
+            "tile_qubits": cfg.tile_qubits or (13 if dt == sv.SV_C64 else 12),
+            "chunk_qubits": cfg.chunk_qubits or (5 if dt == sv.SV_C64 else 4),
             "state_bytes": state_bytes,
             "l2": "state (2^n amplitudes) exceeds the 126 MiB L2; no flush between steps",
             "parallelism": "replicas" if world > 1 else "single GPU",
@@ -321,6 +329,7 @@ def run_ours(args, world, rank, local):
             "outcome_ok": bool(ok),
         },
         "hbm_gbs_algorithmic": alg_gbs,
+        "autotune": tuned,
         "roofline": {
             "kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak,
             "peak_kind": peak_kind, "unit": "GB/s",
@@ -333,9 +342,10 @@ def run_ours(args, world, rank, local):
         "clocks": clk,
     }
 
-    # ---- the CUDA-core partitioned kernel on the same circuit ----
-    if mode == sv.SV_MODE_FUSED:
-        pc = sv.make_config(sv.SV_MODE_PARTITIONED)
+    # ---- the other tile kernel on the same circuit (fused <-> CUDA-core) ----
+    if dt == sv.SV_C64 and mode in (sv.SV_MODE_FUSED, sv.SV_MODE_PARTITIONED):
+        other = sv.SV_MODE_PARTITIONED if mode == sv.SV_MODE_FUSED else sv.SV_MODE_FUSED
+        pc = sv.make_config(other, chunk_qubits=cfg.chunk_qubits)
         step(pc)
         e0.record(stream)
         for _ in range(3):
@@ -344,7 +354,7 @@ def run_ours(args, world, rank, local):
         stream.synchronize()
         pms = e0.elapsed_time(e1) / 3
         pst = sv.sv_last_stats(h)
-        out["partitioned_cuda_cores"] = {
+        out["fused_tensor_cores" if other == sv.SV_MODE_FUSED else "partitioned_cuda_cores"] = {
             "circuit_ms": pms, "passes": pst["passes"],
             "hbm_gbs_full_sweeps": pst["sweep_bytes"] / (pms / 1e3) / 1e9}
 
@@ -399,8 +409,10 @@ def run_ours(args, world, rank, local):
     # ---- batched QPE (4096 instances, n uniform in 10..20): one graph launch ----
     if not args.no_batch:
         work = C.qpe_batch(args.batch)
+        items = [(nn, gg, mm) for nn, gg, mm, _ in work]
+        bcfg, _ = sv.sv_batch_autotune(items)
         t0 = time.perf_counter()
-        bh = sv.sv_batch_create([(nn, gg, mm) for nn, gg, mm, _ in work])
+        bh = sv.sv_batch_create(items, bcfg)
         t_create = time.perf_counter() - t0
         sv.sv_batch_run(bh, len(work))
         runs = [sv.sv_batch_run(bh, len(work)) for _ in range(3)]
@@ -412,7 +424,7 @@ def run_ours(args, world, rank, local):
             "instances": len(work), "n_range": [10, 20], "launch_ms": bms,
             "instances_per_s": len(work) / (bms / 1e3), "passes": binfo["passes"],
             "l2_gbs_algorithmic": binfo["sweep_bytes"] / (bms / 1e3) / 1e9,
-            "host_plan_s": t_create,
+            "host_plan_s": t_create, "chunk_qubits": bcfg.chunk_qubits,
             "outcomes_ok": bool(all(int(bidx[i]) == w[3] for i, w in enumerate(work)))}
 
     # ---- end to end through the public API with host buffers ----

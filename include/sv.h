@@ -223,6 +223,26 @@ sv_status sv_batch_destroy(sv_batch b);
 sv_status sv_apply_circuit_batch(const sv_batch_item *items, size_t count, const sv_config *cfg,
                                  uint64_t *host_idx, double *host_p);
 
+/* Measure the batch for every chunk width c in 4..7 (one warm-up run and
+ * three timed runs each, median) and return the fastest configuration in
+ * *best (and its time in *best_ms, may be NULL). */
+sv_status sv_batch_autotune(const sv_batch_item *items, size_t count, sv_config *best,
+                            double *best_ms);
+
+/* ---- autotuning --------------------------------------------------------- */
+
+/* Run the circuit under each candidate configuration (execution mode:
+ * per-gate for small n, register-stage tiles, tensor-core fused tiles; chunk
+ * width c; for complex128 the tile width k), one warm-up and three timed runs
+ * each from |0...0> (the paper keeps the fastest block size, median of three
+ * runs, Sec. IV-B), and return the fastest in *best and its median device
+ * time in *best_ms (may be NULL).  The handle's state is overwritten and left
+ * at |0...0>.  cache_path (may be NULL) names a text file of earlier results
+ * keyed by the circuit's structure (kinds and qubits, not angles), n and the
+ * dtype: a hit returns without timing; a new result is appended. */
+sv_status sv_autotune(sv_handle h, const sv_gate *host_gates, size_t m, const char *cache_path,
+                      sv_config *best, double *best_ms);
+
 /* ---- reading out (Sec. IV-A: the measured bitstring) ------------------ */
 
 /* Marginal probabilities over the logical qubits in `qubit_mask`, computed

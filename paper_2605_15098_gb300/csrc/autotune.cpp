@@ -1,0 +1,149 @@
+// Autotuner: picks the execution configuration of a circuit by measurement.
+//
+// The paper sweeps the block size and keeps the fastest (median of three
+// runs, Sec. IV-B); here the sweep covers what sets the cost on a GB300: the
+// execution mode (per-gate sweeps, register-stage tiles on the CUDA cores,
+// tiles with tensor-core fused blocks), the chunk width c of the bulk copies
+// (how many low qubits every tile holds contiguously, 2^c amplitudes), and
+// for complex128 the tile width k.  Each candidate runs the circuit from
+// |0...0> once to warm up and three times under CUDA events; the median wins.
+// Results can be cached in a text file keyed by the circuit's structure
+// (gate kinds and qubits, not their angles), n and the dtype.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.h"
+
+using namespace sv;
+
+namespace {
+
+uint64_t structure_hash(int n, sv_dtype dt, const sv_gate *g, size_t m) {
+    uint64_t h = 1469598103934665603ULL;  // FNV-1a
+    auto mix = [&](uint64_t v) {
+        for (int i = 0; i < 8; i++) {
+            h ^= (v >> (8 * i)) & 0xff;
+            h *= 1099511628211ULL;
+        }
+    };
+    mix((uint64_t)n);
+    mix((uint64_t)dt);
+    for (size_t i = 0; i < m; i++) {
+        mix((uint64_t)(uint32_t)g[i].kind | ((uint64_t)(uint32_t)g[i].target << 8) |
+            ((uint64_t)(uint32_t)(g[i].control + 1) << 24));
+    }
+    return h;
+}
+
+bool cache_lookup(const char *path, uint64_t key, sv_config *cfg, double *ms) {
+    if (!path) return false;
+    FILE *f = fopen(path, "r");
+    if (!f) return false;
+    char line[256];
+    bool found = false;
+    while (fgets(line, sizeof line, f)) {
+        unsigned long long k;
+        int mode, tile, chunk;
+        double t;
+        if (sscanf(line, "%llx %d %d %d %lf", &k, &mode, &tile, &chunk, &t) == 5 && k == key) {
+            *cfg = sv_config{};
+            cfg->mode = mode;
+            cfg->tile_qubits = tile;
+            cfg->chunk_qubits = chunk;
+            *ms = t;
+            found = true;  // last entry wins
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void cache_store(const char *path, uint64_t key, const sv_config &cfg, double ms) {
+    if (!path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%016llx %d %d %d %.6f\n", (unsigned long long)key, cfg.mode, cfg.tile_qubits,
+            cfg.chunk_qubits, ms);
+    fclose(f);
+}
+
+}  // namespace
+
+extern "C" sv_status sv_autotune(sv_handle h, const sv_gate *host_gates, size_t m,
+                                 const char *cache_path, sv_config *best, double *best_ms) {
+    clear_error();
+    if (!h || !best || (m && !host_gates)) return fail(SV_ERR_ARG, "NULL argument");
+    for (size_t i = 0; i < m; i++) {
+        std::string why = check_gate(h->n, host_gates[i]);
+        if (!why.empty()) return fail(SV_ERR_ARG, "gate %zu: %s", i, why.c_str());
+    }
+    const uint64_t key = structure_hash(h->n, h->dt, host_gates, m);
+    double ms = 0.0;
+    if (cache_lookup(cache_path, key, best, &ms)) {
+        if (best_ms) *best_ms = ms;
+        return SV_OK;
+    }
+    std::vector<sv_config> cands;
+    auto add = [&](int mode, int tile, int chunk) {
+        sv_config c{};
+        c.mode = mode;
+        c.tile_qubits = tile;
+        c.chunk_qubits = chunk;
+        cands.push_back(c);
+    };
+    if (h->n <= 12) add(SV_MODE_PERGATE, 0, 0);
+    if (h->dt == SV_C64) {
+        for (int c : {4, 5, 6, 7}) add(SV_MODE_PARTITIONED, 0, c);
+        if (h->n > 13)
+            for (int c : {4, 5, 6}) add(SV_MODE_FUSED, 0, c);
+    } else {
+        for (int k : {11, 12, 13})
+            for (int c : {3, 4, 5}) add(SV_MODE_PARTITIONED, k, c);
+    }
+    cudaEvent_t e0, e1;
+    SV_CUDA(cudaEventCreate(&e0));
+    SV_CUDA(cudaEventCreate(&e1));
+    double best_t = 1e300;
+    sv_config best_c = cands.front();
+    sv_status st = SV_OK;
+    for (const sv_config &c : cands) {
+        std::vector<float> t;
+        for (int r = 0; r < 4 && st == SV_OK; r++) {
+            st = sv_reset(h);
+            if (st != SV_OK) break;
+            cudaEventRecord(e0, h->stream);
+            st = sv_apply_circuit(h, host_gates, m, &c);
+            cudaEventRecord(e1, h->stream);
+            if (st != SV_OK) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st = fail(SV_ERR_CUDA, "autotune: kernel failed");
+                break;
+            }
+            float x = 0.f;
+            cudaEventElapsedTime(&x, e0, e1);
+            if (r) t.push_back(x);  // run 0 warms up
+        }
+        if (st == SV_ERR_UNSUPPORTED || st == SV_ERR_ARG) {  // candidate not valid here: skip it
+            st = SV_OK;
+            continue;
+        }
+        if (st != SV_OK) break;
+        std::sort(t.begin(), t.end());
+        const double med = t[t.size() / 2];
+        if (med < best_t) {
+            best_t = med;
+            best_c = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SV_OK) return st;
+    SV_TRY(sv_reset(h));
+    *best = best_c;
+    if (best_ms) *best_ms = best_t;
+    cache_store(cache_path, key, best_c, best_t);
+    return SV_OK;
+}

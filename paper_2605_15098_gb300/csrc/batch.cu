@@ -324,6 +324,33 @@ sv_status sv_batch_destroy(sv_batch b) {
     return SV_OK;
 }
 
+sv_status sv_batch_autotune(const sv_batch_item *items, size_t count, sv_config *best, double *best_ms) {
+    clear_error();
+    if (!best) return fail(SV_ERR_ARG, "best is NULL");
+    double bt = 1e300;
+    int bc = 0;
+    for (int c : {4, 5, 6, 7}) {
+        sv_config cfg{};
+        cfg.chunk_qubits = c;
+        sv_batch b = nullptr;
+        SV_TRY(sv_batch_create(items, count, &cfg, &b));
+        double t[4] = {};
+        sv_status st = SV_OK;
+        for (int r = 0; r < 4 && st == SV_OK; r++) st = sv_batch_run(b, nullptr, nullptr, &t[r]);
+        destroy(b);
+        SV_TRY(st);
+        std::sort(t + 1, t + 4);  // run 0 warms up
+        if (t[2] < bt) {
+            bt = t[2];
+            bc = c;
+        }
+    }
+    *best = sv_config{};
+    best->chunk_qubits = bc;
+    if (best_ms) *best_ms = bt;
+    return SV_OK;
+}
+
 sv_status sv_apply_circuit_batch(const sv_batch_item *items, size_t count, const sv_config *cfg,
                                  uint64_t *host_idx, double *host_p) {
     sv_batch b = nullptr;

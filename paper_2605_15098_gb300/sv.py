@@ -30,6 +30,7 @@ EXPORTS = (
     "sv_argmax", "sv_sample", "sv_copy_out", "sv_copy_in", "sv_last_error", "sv_version",
     "sv_profile", "sv_profile_read", "sv_launch_count", "sv_marginal_noalloc", "sv_plan_export",
     "sv_batch_create", "sv_batch_run", "sv_batch_info", "sv_batch_destroy", "sv_apply_circuit_batch",
+    "sv_autotune", "sv_batch_autotune",
 )
 SV_KERNEL_PERGATE, SV_KERNEL_TILE, SV_KERNEL_REMAP, SV_KERNEL_FUSED = 0, 1, 2, 3
 
@@ -113,6 +114,8 @@ def lib() -> ctypes.CDLL:
         "sv_batch_info": [vp, ctypes.POINTER(sz), ctypes.POINTER(i32), dp],
         "sv_batch_destroy": [vp],
         "sv_apply_circuit_batch": [vp, sz, ctypes.POINTER(sv_config), vp, vp],
+        "sv_autotune": [vp, vp, sz, ctypes.c_char_p, ctypes.POINTER(sv_config), dp],
+        "sv_batch_autotune": [vp, sz, ctypes.POINTER(sv_config), dp],
         "sv_profile_read": [vp, vp, sz, ctypes.POINTER(sz)],
     }
     for name, args in sig.items():
@@ -317,6 +320,33 @@ def sv_apply_circuit_batch(circuits, cfg: sv_config | None = None):
                                         idx.ctypes.data, p.ctypes.data))
     del keep
     return idx, p
+
+
+def sv_autotune(h: int, gates: np.ndarray, cache_path: str | None = None):
+    """Fastest measured configuration for this circuit: (sv_config, median ms)."""
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    best = sv_config()
+    ms = ctypes.c_double()
+    _check(lib().sv_autotune(ctypes.c_void_p(h), g.ctypes.data if g.size else None, g.size,
+                             cache_path.encode() if cache_path else None, ctypes.byref(best),
+                             ctypes.byref(ms)))
+    return best, ms.value
+
+
+def sv_batch_autotune(circuits):
+    arr, keep = _batch_items(circuits)
+    best = sv_config()
+    ms = ctypes.c_double()
+    _check(lib().sv_batch_autotune(arr, len(circuits), ctypes.byref(best), ctypes.byref(ms)))
+    del keep
+    return best, ms.value
+
+
+def config_dict(c: sv_config) -> dict:
+    names = {SV_MODE_AUTO: "auto", SV_MODE_PERGATE: "per-gate", SV_MODE_PARTITIONED: "partitioned",
+             SV_MODE_FUSED: "fused"}
+    return {"mode": names.get(c.mode, c.mode), "tile_qubits": c.tile_qubits,
+            "chunk_qubits": c.chunk_qubits, "planner": c.planner, "flags": c.flags}
 
 
 def sv_launch_count() -> int:

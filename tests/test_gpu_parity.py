@@ -336,3 +336,33 @@ def test_batch_mixed_circuits_match_single(sv):
         if top[1] - top[0] > 1e-5:  # a clear maximum: same index
             assert int(idx[i]) == int(np.argmax(probs))
         assert abs(p[i] - probs.max()) <= 1e-5
+
+
+def test_autotune_picks_a_valid_config(sv, orc, tmp_path):
+    n = 16
+    g, expected, info = C.qpe(n, seed=5)
+    cache = str(tmp_path / "tune.txt")
+    with sv.State(n, sv.SV_C64) as s:
+        best, ms = sv.sv_autotune(s.h, g, cache)
+        assert ms > 0 and best.mode in (sv.SV_MODE_PARTITIONED, sv.SV_MODE_FUSED)
+        best2, ms2 = sv.sv_autotune(s.h, g, cache)  # cache hit: same answer
+        assert (best2.mode, best2.chunk_qubits, best2.tile_qubits) == \
+            (best.mode, best.chunk_qubits, best.tile_qubits)
+        assert abs(ms2 - ms) < 1e-3
+        s.apply(g, best)
+        idx, p = s.argmax(info["mask"])
+        assert idx == info["y"] and abs(p - 1) < 1e-5
+    # another circuit with the same structure (different angles) hits the same entry
+    g2, _, _ = C.qpe(n, seed=6)
+    with sv.State(n, sv.SV_C64) as s:
+        best3, ms3 = sv.sv_autotune(s.h, g2, cache)
+        assert abs(ms3 - ms) < 1e-3
+
+
+def test_batch_autotune(sv):
+    work = C.qpe_batch(64, seed=11)
+    items = [(n, g, m) for n, g, m, _ in work]
+    best, ms = sv.sv_batch_autotune(items)
+    assert best.chunk_qubits in (4, 5, 6, 7) and ms > 0
+    idx, p = sv.sv_apply_circuit_batch(items, best)
+    assert all(int(idx[i]) == w[3] for i, w in enumerate(work))
