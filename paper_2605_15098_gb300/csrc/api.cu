@@ -93,21 +93,6 @@ sv_status read_marginal(sv_state *h, uint64_t mask, uint64_t *len) {
     return marginal_device(h, pos, m, h->probs);
 }
 
-// Physically reorder the state so that logical qubit q sits at bit q.
-sv_status normalise_layout(sv_state *h) {
-    for (int q = 0; q < h->n; q++) {
-        if (h->phys[q] == q) continue;
-        int r = -1;
-        for (int k = 0; k < h->n; k++)
-            if (h->phys[k] == q) r = k;
-        const int p = h->phys[q];
-        SV_TRY(pergate_swap_bits(h, p, q));
-        h->phys[q] = q;
-        h->phys[r] = p;
-    }
-    return SV_OK;
-}
-
 }  // namespace
 
 extern "C" {
@@ -264,7 +249,7 @@ sv_status sv_copy_out(sv_handle h, void *host_amps) {
     clear_error();
     if (!h || !host_amps) return fail(SV_ERR_ARG, "NULL argument");
     SV_TRY(resolve_norm(h));
-    SV_TRY(normalise_layout(h));
+    SV_TRY(remap_to_identity(h));
     SV_CUDA(cudaMemcpyAsync(host_amps, h->amps, state_bytes(h), cudaMemcpyDeviceToHost, h->stream));
     SV_CUDA(cudaStreamSynchronize(h->stream));
     return SV_OK;

@@ -94,6 +94,8 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
     sv_config c{};
     if (cfg) c = *cfg;
     const int chunk = c.chunk_qubits ? c.chunk_qubits : 5;
+    if (c.flags & SV_FLAG_PAPER_SWAP)
+        return fail(SV_ERR_UNSUPPORTED, "batched instances run no remap passes (SV_FLAG_PAPER_SWAP)");
     if (chunk < 4 || chunk > 11) return fail(SV_ERR_ARG, "chunk_qubits must be 4..11 for batches");
     for (size_t i = 0; i < count; i++) {
         const sv_batch_item &it = items[i];

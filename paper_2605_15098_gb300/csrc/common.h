@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "sv.h"
@@ -103,10 +104,14 @@ void prof_end(sv_state *h, int slot, const sv_launch_record &meta);
 // ---- per-gate path (pergate.cu) ---------------------------------------------
 // Apply one gate whose qubits are already PHYSICAL positions.
 sv_status pergate_apply(sv_state *h, const sv_gate &g_phys);
-// Exchange physical bits a and b of the whole state (a SWAP sweep).
-sv_status pergate_swap_bits(sv_state *h, int a, int b);
 // Set the state to |0...0>.
 sv_status init_zero_state(sv_state *h);
+
+// ---- remap passes (remap.cu) --------------------------------------------------
+// Exchange the disjoint physical bit pairs of the whole state, in place.
+sv_status remap_apply(sv_state *h, const std::vector<std::pair<int, int>> &pairs);
+// Move every logical qubit q to physical bit q (at most two remap passes).
+sv_status remap_to_identity(sv_state *h);
 
 // ---- read-out (measure.cu) ----------------------------------------------------
 // Marginal over physical positions pos[0..m-1] (output bit j <-> pos[j]),

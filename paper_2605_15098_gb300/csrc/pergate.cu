@@ -361,12 +361,4 @@ sv_status pergate_apply(sv_state *h, const sv_gate &g) {
     return launch_op<float, 0>(h, op, units, fx, partner, to_coef<float>(m), meta);
 }
 
-sv_status pergate_swap_bits(sv_state *h, int a, int b) {
-    sv_gate g{};
-    g.kind = SV_SWAP;
-    g.target = a;
-    g.control = b;
-    return pergate_apply(h, g);
-}
-
 }  // namespace sv

@@ -10,9 +10,16 @@
 // 2^c amplitudes, the unit of a bulk copy) plus k - c further physical bits
 // chosen per pass, so a global target is brought local by gathering its
 // chunks into the tile instead of moving amplitudes in a separate SWAP sweep.
+//
+// The paper's own scheme is kept as an option (PlanOptions::paper): the
+// local qubits are always the k lowest physical bits (one contiguous block),
+// and a gate whose target is global is preceded by a remap pass that
+// exchanges it with the least recently used local qubit.
 #pragma once
 
 #include <cstdint>
+#include <string>
+#include <utility>
 #include <vector>
 
 #include "sv.h"
@@ -64,6 +71,10 @@ struct TilePass {
     int slot_phys[kMaxTileQubits];  // physical bit of local slot s
     uint64_t gmask = 0;             // physical bits outside the tile
     int ngates = 0;                 // circuit gates the pass applies
+    // Physical bit pairs (local, global) exchanged by a remap pass before
+    // this pass runs: amplitude x moves to x with each pair's bits swapped.
+    // The pairs are disjoint.
+    std::vector<std::pair<int, int>> remap_before;
     std::vector<TileOp> ops;
     std::vector<PhaseTerm> terms;
 };
@@ -73,11 +84,16 @@ struct PlanOptions {
     int k = 0, c = 0;
     bool merge_diag = true;
     bool relabel = true;
+    bool paper = false;  // explicit LRU remaps, tile = the k lowest physical bits
 };
+
+// Planner options of a configuration (library defaults filled in).
+PlanOptions plan_options(int n, sv_dtype dt, const sv_config &cfg);
 
 struct Plan {
     std::vector<TilePass> passes;
     int relabels = 0;
+    int remaps = 0;  // remap passes (pairs exchanged in one sweep count once)
 };
 
 // Build the programme; phys (logical -> physical, n entries) is updated by

@@ -122,12 +122,7 @@ extern "C" sv_status sv_plan_export(int n, sv_dtype dt, const int *host_phys_of_
     sv_config c{};
     if (cfg) c = *cfg;
     const bool dbl = dt == SV_C128;
-    PlanOptions opt;
-    opt.n = n;
-    opt.k = c.tile_qubits ? c.tile_qubits : (dbl ? 12 : 13);
-    opt.c = c.chunk_qubits ? c.chunk_qubits : (dbl ? 4 : 5);
-    opt.merge_diag = !(c.flags & SV_FLAG_NO_DIAG_MERGE);
-    opt.relabel = !(c.flags & SV_FLAG_NO_RELABEL);
+    PlanOptions opt = plan_options(n, dt, c);
     int phys[64];
     for (int q = 0; q < 64; q++) phys[q] = q;
     if (host_phys_of_logical)
@@ -140,6 +135,7 @@ extern "C" sv_status sv_plan_export(int n, sv_dtype dt, const int *host_phys_of_
     J j;
     j.raw("{\"n\":"); j.num(n);
     j.raw(",\"relabels\":"); j.num(plan.relabels);
+    j.raw(",\"remaps\":"); j.num(plan.remaps);
     j.raw(",\"phys\":"); j.arr(phys, n);
     j.raw(",\"passes\":[");
     bool first = true;
@@ -151,6 +147,13 @@ extern "C" sv_status sv_plan_export(int n, sv_dtype dt, const int *host_phys_of_
         j.raw(",\"ngates\":"); j.num(p.ngates);
         j.raw(",\"gmask\":"); j.u64(p.gmask);
         j.raw(",\"slot_phys\":"); j.arr(p.slot_phys, p.k);
+        j.raw(",\"remap_before\":[");
+        for (size_t i = 0; i < p.remap_before.size(); i++) {
+            if (i) j.raw(",");
+            j.raw("["); j.num(p.remap_before[i].first); j.raw(",");
+            j.num(p.remap_before[i].second); j.raw("]");
+        }
+        j.raw("]");
         j.raw(",\"ops\":[");
         for (size_t i = 0; i < p.ops.size(); i++) {
             const TileOp &op = p.ops[i];

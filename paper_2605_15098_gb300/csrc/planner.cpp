@@ -58,13 +58,251 @@ bool commutes_with_gate(const PGate &d, const PGate &g) {
     return true;
 }
 
+// Build one tile pass: the gates pg[order] (dependency order) on the tile
+// whose local qubits are the physical bits with in_l set (k of them, the c
+// lowest first).  Diagonal gates merge into runs; see build_plan.
+std::string emit_pass(const std::vector<PGate> &pg, const std::vector<int> &order,
+                      const bool *in_l, int n, int k, int c, const PlanOptions &opt,
+                      TilePass *out_pass) {
+    TilePass tp;
+    tp.k = k;
+    tp.c = c;
+    tp.ngates = (int)order.size();
+    int slot_of[64];
+    for (int q = 0; q < 64; q++) slot_of[q] = -1;
+    int s = 0;
+    for (int q = 0; q < n; q++)
+        if (in_l[q]) {
+            tp.slot_phys[s] = q;
+            slot_of[q] = s++;
+        }
+    tp.gmask = 0;
+    for (int q = 0; q < n; q++)
+        if (!in_l[q]) tp.gmask |= UINT64_C(1) << q;
+
+    // segments: gates in order, diagonal gates merged into runs
+    struct Seg {
+        bool diag;
+        std::vector<int> g;
+    };
+    // Each diagonal gate moves as late as it can: into the diagonal run just
+    // before the next gate that does not commute with it (built on the
+    // reversed order, then flipped).  A run then collects the phases that
+    // feed one non-diagonal gate, as the inverse QFT writes them.
+    std::vector<Seg> segs;
+    for (auto it = order.rbegin(); it != order.rend(); ++it) {
+        const int i = *it;
+        const PGate &p = pg[i];
+        if (!p.diag) {
+            segs.push_back({false, {i}});
+            continue;
+        }
+        if (!opt.merge_diag) {
+            segs.push_back({true, {i}});
+            continue;
+        }
+        int blocker = -1;
+        for (int sgi = (int)segs.size() - 1; sgi >= 0; sgi--) {
+            if (segs[sgi].diag) continue;
+            if (!commutes_with_gate(p, pg[segs[sgi].g[0]])) {
+                blocker = sgi;
+                break;
+            }
+        }
+        int target = -1;
+        for (int sgi = blocker + 1; sgi < (int)segs.size(); sgi++)
+            if (segs[sgi].diag) {
+                target = sgi;
+                break;
+            }
+        if (target >= 0)
+            segs[target].g.push_back(i);
+        else
+            segs.push_back({true, {i}});
+    }
+    std::reverse(segs.begin(), segs.end());
+
+    for (const Seg &sg : segs) {
+        TileOp op{};
+        if (!sg.diag) {
+            const sv_gate &g = pg[sg.g[0]].g;
+            if (g.kind == SV_SWAP) {
+                op.type = TOP_SWAP;
+                op.slot = slot_of[g.target];
+                op.cslot = slot_of[g.control];
+            } else {
+                op.slot = slot_of[g.target];
+                Mat2 mm = gate_matrix(g);
+                for (int e = 0; e < 4; e++) {
+                    op.m[2 * e] = mm.re[e];
+                    op.m[2 * e + 1] = mm.im[e];
+                }
+                if (g.kind == SV_CU) {
+                    if (slot_of[g.control] >= 0) {
+                        op.type = TOP_GATE_CL;
+                        op.cslot = slot_of[g.control];
+                    } else {
+                        op.type = TOP_GATE_CG;
+                        op.cbit = g.control;
+                    }
+                } else if (g.kind == SV_H) {
+                    op.type = TOP_H;
+                } else if (g.kind == SV_X) {
+                    op.type = TOP_X;
+                } else {
+                    op.type = TOP_GATE;
+                }
+            }
+            tp.ops.push_back(op);
+            continue;
+        }
+        // merged diagonal run -> phase polynomial over local / global bits
+        std::map<std::tuple<int, int, int>, uint64_t> acc;
+        for (int gi : sg.g) {
+            const sv_gate &g = pg[gi].g;
+            bool exact;
+            uint64_t th = diag_turns64(g, &exact);
+            if (!is_controlled_kind(g.kind)) {
+                int q = g.target;
+                if (slot_of[q] >= 0)
+                    acc[{TERM_L, slot_of[q], 0}] += th;
+                else
+                    acc[{TERM_G, q, 0}] += th;
+            } else {
+                int q1 = g.control, q2 = g.target;
+                int s1 = slot_of[q1], s2 = slot_of[q2];
+                if (s1 >= 0 && s2 >= 0)
+                    acc[{TERM_LL, std::min(s1, s2), std::max(s1, s2)}] += th;
+                else if (s1 >= 0)
+                    acc[{TERM_LG, s1, q2}] += th;
+                else if (s2 >= 0)
+                    acc[{TERM_LG, s2, q1}] += th;
+                else
+                    acc[{TERM_GG, std::min(q1, q2), std::max(q1, q2)}] += th;
+            }
+        }
+        op.type = TOP_DIAG;
+        op.tb = (int)tp.terms.size();
+        for (auto &kv : acc) {
+            if (kv.second == 0) continue;
+            PhaseTerm t{};
+            t.kind = std::get<0>(kv.first);
+            t.a = std::get<1>(kv.first);
+            t.b = std::get<2>(kv.first);
+            t.theta = kv.second;
+            tp.terms.push_back(t);
+        }
+        op.te = (int)tp.terms.size();
+        if (op.te > op.tb) tp.ops.push_back(op);
+    }
+    *out_pass = std::move(tp);
+    return "";
+}
+
+// Sec. III-B as the paper states it.  The local qubits are the physical bits
+// 0..k-1, so a tile is one contiguous block of 2^k amplitudes.  Gates are
+// deferred in program order; a gate whose target (both qubits for a SWAP
+// executed as data) is global ends the deferred batch, which becomes one
+// pass, and a remap exchanges that global bit with the local bit that was
+// used least recently (ties: the lowest bit), updating the logical-to-physical
+// map.  A global control needs no remap: it is decided per tile.
+std::string build_plan_paper(const std::vector<sv_gate> &gates, const PlanOptions &opt, int *phys,
+                             Plan *out) {
+    const int n = opt.n;
+    const int k = std::min(opt.k, n);
+    int inv[64];
+    for (int q = 0; q < 64; q++) inv[q] = -1;
+    for (int q = 0; q < n; q++) inv[phys[q]] = q;
+    std::vector<long> lru(k, -1);
+    long clock = 0;
+    bool in_l[64] = {};
+    for (int q = 0; q < k; q++) in_l[q] = true;
+    std::vector<PGate> pending;
+    std::vector<std::pair<int, int>> remaps;
+    auto flush = [&]() -> std::string {
+        if (pending.empty()) return "";
+        std::vector<int> order(pending.size());
+        for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
+        TilePass tp;
+        std::string e = emit_pass(pending, order, in_l, n, k, k, opt, &tp);
+        if (!e.empty()) return e;
+        tp.remap_before.swap(remaps);
+        remaps.clear();
+        out->passes.push_back(std::move(tp));
+        pending.clear();
+        return "";
+    };
+    for (const sv_gate &g : gates) {
+        if (g.kind == SV_SWAP && opt.relabel) {
+            std::swap(phys[g.target], phys[g.control]);
+            inv[phys[g.target]] = g.target;
+            inv[phys[g.control]] = g.control;
+            out->relabels++;
+            continue;
+        }
+        int need[2], nneed = 0;
+        need[nneed++] = g.target;
+        if (g.kind == SV_SWAP) need[nneed++] = g.control;
+        for (int a = 0; a < nneed; a++) {
+            const int t = phys[need[a]];
+            if (t < k) continue;
+            std::string e = flush();
+            if (!e.empty()) return e;
+            // victim: least recently used local bit the gate does not use
+            int v = -1;
+            for (int p = 0; p < k; p++) {
+                bool used = false;
+                for (int b = 0; b < nneed; b++) used |= phys[need[b]] == p;
+                if (is_controlled_kind(g.kind) && phys[g.control] == p) used = true;
+                if (used) continue;
+                if (v < 0 || lru[p] < lru[v]) v = p;
+            }
+            if (v < 0) return "tile too small for a remap";
+            const int lq = inv[v], gq = inv[t];
+            phys[lq] = t;
+            phys[gq] = v;
+            inv[v] = gq;
+            inv[t] = lq;
+            remaps.push_back({v, t});
+            out->remaps++;
+        }
+        PGate p{};
+        p.g = g;
+        p.g.target = phys[g.target];
+        if (is_controlled_kind(g.kind) || g.kind == SV_SWAP) p.g.control = phys[g.control];
+        classify(p);
+        pending.push_back(p);
+        const long now = clock++;
+        if (p.g.target < k) lru[p.g.target] = now;
+        if ((is_controlled_kind(g.kind) || g.kind == SV_SWAP) && p.g.control < k)
+            lru[p.g.control] = now;
+    }
+    return flush();
+}
+
 }  // namespace
+
+PlanOptions plan_options(int n, sv_dtype dt, const sv_config &cfg) {
+    PlanOptions opt;
+    opt.n = n;
+    const bool dbl = dt == SV_C128;
+    opt.k = cfg.tile_qubits ? cfg.tile_qubits : (dbl ? 12 : 13);
+    opt.c = cfg.chunk_qubits ? cfg.chunk_qubits : (dbl ? 4 : 5);
+    if (!dbl && opt.c < 1) opt.c = 1;
+    opt.merge_diag = !(cfg.flags & SV_FLAG_NO_DIAG_MERGE);
+    opt.relabel = !(cfg.flags & SV_FLAG_NO_RELABEL);
+    opt.paper = (cfg.flags & SV_FLAG_PAPER_SWAP) != 0;
+    if (opt.paper) opt.c = opt.k;  // the block is contiguous
+    return opt;
+}
 
 std::string build_plan(const std::vector<sv_gate> &gates, const PlanOptions &opt, int *phys,
                        Plan *out) {
     const int n = opt.n;
     out->passes.clear();
     out->relabels = 0;
+    out->remaps = 0;
+    if (opt.paper && n > opt.k) return build_plan_paper(gates, opt, phys, out);
     int k = std::min(opt.k, n);
     int c = std::min(opt.c, k);
     if (n > k && k - c < 2) return "tile must leave at least two free slots (k - c >= 2)";
@@ -153,136 +391,8 @@ std::string build_plan(const std::vector<sv_gate> &gates, const PlanOptions &opt
             }
 
         TilePass tp;
-        tp.k = k;
-        tp.c = c;
-        tp.ngates = (int)order.size();
-        int slot_of[64];
-        for (int q = 0; q < 64; q++) slot_of[q] = -1;
-        int s = 0;
-        for (int q = 0; q < n; q++)
-            if (in_l[q]) {
-                tp.slot_phys[s] = q;
-                slot_of[q] = s++;
-            }
-        tp.gmask = 0;
-        for (int q = 0; q < n; q++)
-            if (!in_l[q]) tp.gmask |= UINT64_C(1) << q;
-
-        // 4. segments: gates in order, diagonal gates merged into runs
-        struct Seg {
-            bool diag;
-            std::vector<int> g;
-        };
-        // Each diagonal gate moves as late as it can: into the diagonal run just
-        // before the next gate that does not commute with it (built on the
-        // reversed order, then flipped).  A run then collects the phases that
-        // feed one non-diagonal gate, as the inverse QFT writes them.
-        std::vector<Seg> segs;
-        for (auto it = order.rbegin(); it != order.rend(); ++it) {
-            const int i = *it;
-            const PGate &p = pg[i];
-            if (!p.diag) {
-                segs.push_back({false, {i}});
-                continue;
-            }
-            if (!opt.merge_diag) {
-                segs.push_back({true, {i}});
-                continue;
-            }
-            int blocker = -1;
-            for (int sgi = (int)segs.size() - 1; sgi >= 0; sgi--) {
-                if (segs[sgi].diag) continue;
-                if (!commutes_with_gate(p, pg[segs[sgi].g[0]])) {
-                    blocker = sgi;
-                    break;
-                }
-            }
-            int target = -1;
-            for (int sgi = blocker + 1; sgi < (int)segs.size(); sgi++)
-                if (segs[sgi].diag) {
-                    target = sgi;
-                    break;
-                }
-            if (target >= 0)
-                segs[target].g.push_back(i);
-            else
-                segs.push_back({true, {i}});
-        }
-        std::reverse(segs.begin(), segs.end());
-
-        for (const Seg &sg : segs) {
-            TileOp op{};
-            if (!sg.diag) {
-                const sv_gate &g = pg[sg.g[0]].g;
-                if (g.kind == SV_SWAP) {
-                    op.type = TOP_SWAP;
-                    op.slot = slot_of[g.target];
-                    op.cslot = slot_of[g.control];
-                } else {
-                    op.slot = slot_of[g.target];
-                    Mat2 mm = gate_matrix(g);
-                    for (int e = 0; e < 4; e++) {
-                        op.m[2 * e] = mm.re[e];
-                        op.m[2 * e + 1] = mm.im[e];
-                    }
-                    if (g.kind == SV_CU) {
-                        if (slot_of[g.control] >= 0) {
-                            op.type = TOP_GATE_CL;
-                            op.cslot = slot_of[g.control];
-                        } else {
-                            op.type = TOP_GATE_CG;
-                            op.cbit = g.control;
-                        }
-                    } else if (g.kind == SV_H) {
-                        op.type = TOP_H;
-                    } else if (g.kind == SV_X) {
-                        op.type = TOP_X;
-                    } else {
-                        op.type = TOP_GATE;
-                    }
-                }
-                tp.ops.push_back(op);
-                continue;
-            }
-            // merged diagonal run -> phase polynomial over local / global bits
-            std::map<std::tuple<int, int, int>, uint64_t> acc;
-            for (int gi : sg.g) {
-                const sv_gate &g = pg[gi].g;
-                bool exact;
-                uint64_t th = diag_turns64(g, &exact);
-                if (!is_controlled_kind(g.kind)) {
-                    int q = g.target;
-                    if (slot_of[q] >= 0)
-                        acc[{TERM_L, slot_of[q], 0}] += th;
-                    else
-                        acc[{TERM_G, q, 0}] += th;
-                } else {
-                    int q1 = g.control, q2 = g.target;
-                    int s1 = slot_of[q1], s2 = slot_of[q2];
-                    if (s1 >= 0 && s2 >= 0)
-                        acc[{TERM_LL, std::min(s1, s2), std::max(s1, s2)}] += th;
-                    else if (s1 >= 0)
-                        acc[{TERM_LG, s1, q2}] += th;
-                    else if (s2 >= 0)
-                        acc[{TERM_LG, s2, q1}] += th;
-                    else
-                        acc[{TERM_GG, std::min(q1, q2), std::max(q1, q2)}] += th;
-                }
-            }
-            op.type = TOP_DIAG;
-            op.tb = (int)tp.terms.size();
-            for (auto &kv : acc) {
-                if (kv.second == 0) continue;
-                PhaseTerm t{};
-                t.kind = std::get<0>(kv.first);
-                t.a = std::get<1>(kv.first);
-                t.b = std::get<2>(kv.first);
-                t.theta = kv.second;
-                tp.terms.push_back(t);
-            }
-            op.te = (int)tp.terms.size();
-            if (op.te > op.tb) tp.ops.push_back(op);
-        }
+        std::string e = emit_pass(pg, order, in_l, n, k, c, opt, &tp);
+        if (!e.empty()) return e;
         out->passes.push_back(std::move(tp));
     }
     return "";

@@ -275,15 +275,9 @@ sv_status check_device_flag(sv_state *h) {
 }
 
 sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, const sv_config &cfg) {
-    PlanOptions opt;
-    opt.n = h->n;
     const bool dbl = h->dt == SV_C128;
-    opt.k = cfg.tile_qubits ? cfg.tile_qubits : (dbl ? 12 : 13);
-    opt.c = cfg.chunk_qubits ? cfg.chunk_qubits : (dbl ? 4 : 5);
+    PlanOptions opt = plan_options(h->n, h->dt, cfg);
     if (dbl && opt.k > 13) return fail(SV_ERR_ARG, "complex128 tiles hold at most 2^13 amplitudes");
-    if (!dbl && opt.c < 1) opt.c = 1;
-    opt.merge_diag = !(cfg.flags & SV_FLAG_NO_DIAG_MERGE);
-    opt.relabel = !(cfg.flags & SV_FLAG_NO_RELABEL);
     Plan plan;
     int phys[64];
     std::copy(h->phys, h->phys + 64, phys);
@@ -354,6 +348,7 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
 
     for (size_t i = 0; i < plan.passes.size(); i++) {
         const TilePass &p = plan.passes[i];
+        if (!p.remap_before.empty()) SV_TRY(remap_apply(h, p.remap_before));
         if (p.ops.empty()) continue;
         sv_launch_record meta{};
         meta.kind = SV_KERNEL_TILE;

@@ -211,10 +211,24 @@ def run_t2_pass(state, p):
         state[idx] = t
 
 
+def remap(state, pairs):
+    """Exchange the physical bit pairs of every index (a remap pass)."""
+    x = np.arange(state.size)
+    y = x.copy()
+    for a, b in pairs:
+        differ = ((x >> a) & 1) != ((x >> b) & 1)
+        y = np.where(differ, y ^ ((1 << a) | (1 << b)), y)
+    out = np.empty_like(state)
+    out[y] = state
+    return out
+
+
 def run_plan(n, plan):
     state = np.zeros(1 << n, dtype=np.complex128)
     state[0] = 1.0
     for p in plan["passes"]:
+        if p.get("remap_before"):
+            state = remap(state, p["remap_before"])
         if not p["ops"]:
             continue
         if p["kernel"] in ("t2", "t3"):

@@ -91,3 +91,87 @@ def test_fused_random_layers(sv, orc, depth):
     g = C.random_circuit(n, depth, 300 + depth)
     plan = check(sv, orc, n, g, sv.make_config(sv.SV_MODE_FUSED), sv.SV_C64, 2e-5)
     assert sum(len(p["t2"]["blocks"]) for p in plan["passes"] if p["kernel"] == "t3") >= 1
+
+
+def lru_remap_pairs(n, k, g):
+    """Remap pairs under Sec. III-B's rule, restated independently: the local
+    qubits are the k lowest physical bits; a gate whose target is global
+    exchanges it with the least recently used local bit (ties: the lowest)
+    that the gate does not use; circuit SWAPs relabel the map."""
+    phys = list(range(n))
+    last = [-1] * k
+    pairs, clock = [], 0
+    for r in g:
+        kind, t, c = int(r["kind"]), int(r["target"]), int(r["control"])
+        if kind == C.SWAP:
+            phys[t], phys[c] = phys[c], phys[t]
+            continue
+        ctrl = kind in (C.CP, C.CZ, C.CU, C.CPK)
+        busy = {phys[t]} | ({phys[c]} if ctrl else set())
+        if phys[t] >= k:
+            v = min((p for p in range(k) if p not in busy), key=lambda p: (last[p], p))
+            gq = phys[t]
+            lq = phys.index(v)
+            phys[lq], phys[t] = gq, v
+            pairs.append((v, gq))
+        last[phys[t]] = clock
+        if ctrl and phys[c] < k:
+            last[phys[c]] = clock
+        clock += 1
+    return pairs, phys
+
+
+@pytest.mark.parametrize("flags", [0, 1, 4])
+def test_paper_remap_plan_generic(sv, orc, flags):
+    """Explicit remap passes (SV_FLAG_PAPER_SWAP): the block is the k lowest
+    physical bits, every remap exchanges one local and one global bit, and
+    the programme equals the oracle in FP64."""
+    n, k = 13, 8
+    g = mixed_circuit(n, 150, 70 + flags)
+    cfg = sv.make_config(sv.SV_MODE_PARTITIONED, tile_qubits=k,
+                         flags=flags | sv.SV_FLAG_PAPER_SWAP | sv.SV_FLAG_GENERIC_TILE)
+    plan = check(sv, orc, n, g, cfg, sv.SV_C128, 1e-12)
+    assert plan["remaps"] > 0
+    assert plan["remaps"] == sum(len(p["remap_before"]) for p in plan["passes"])
+    for p in plan["passes"]:
+        assert p["slot_phys"] == list(range(k)) and p["c"] == k
+        for a, b in p["remap_before"]:
+            assert a < k <= b
+        bits = [b for pr in p["remap_before"] for b in pr]
+        assert len(bits) == len(set(bits))
+
+
+def test_paper_remap_plan_register_stage(sv, orc):
+    n = 15
+    g, _, _ = C.qpe(n, seed=4)
+    cfg = sv.make_config(sv.SV_MODE_PARTITIONED, flags=sv.SV_FLAG_PAPER_SWAP)
+    plan = check(sv, orc, n, g, cfg, sv.SV_C64, 1e-5)
+    assert plan["remaps"] > 0
+    assert any(p["kernel"] == "t2" for p in plan["passes"])
+
+
+@pytest.mark.parametrize("n,seed", [(16, 1), (24, 2)])
+def test_paper_remaps_follow_lru(sv, n, seed):
+    g, _, _ = C.qpe(n, seed=seed)
+    g2 = mixed_circuit(n, 200, seed, kinds=(0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10))
+    for gates in (g, g2):
+        for k in (8, 11, 13):
+            cfg = sv.make_config(sv.SV_MODE_PARTITIONED, tile_qubits=k, flags=sv.SV_FLAG_PAPER_SWAP)
+            plan = sv.sv_plan_export(n, sv.SV_C128 if k != 13 else sv.SV_C64, gates, cfg)
+            pairs, phys = lru_remap_pairs(n, k, gates)
+            assert [tuple(pr) for p in plan["passes"] for pr in p["remap_before"]] == pairs
+            assert plan["phys"] == phys
+
+
+def test_paper_swap_count_falls_with_block_size(sv):
+    """The trade-off the paper measures: fewer remaps as the block grows, and
+    many more state sweeps than the gathering planner needs."""
+    n = 24
+    g, _, _ = C.qpe(n)
+    counts = []
+    for k in range(8, 15):
+        cfg = sv.make_config(sv.SV_MODE_PARTITIONED, tile_qubits=k, flags=sv.SV_FLAG_PAPER_SWAP)
+        counts.append(sv.sv_plan_export(n, sv.SV_C64, g, cfg)["remaps"])
+    assert all(a >= b for a, b in zip(counts, counts[1:])) and counts[0] > counts[-1]
+    gather = sv.sv_plan_export(n, sv.SV_C64, g, sv.make_config(sv.SV_MODE_PARTITIONED))
+    assert len(gather["passes"]) * 4 < counts[-1]
