@@ -138,6 +138,10 @@ typedef struct sv_stats {
     double touched_bytes;   /* bytes the kernels had to move (diagonal and SWAP
                                per-gate sweeps touch part of the state)         */
     double h2d_bytes;       /* host-to-device bytes copied (the pass programme)  */
+    int32_t planner;        /* sv_planner that produced the executed plan        */
+    int32_t candidates;     /* learned planner: candidate passes it scored        */
+    double predicted_ms;    /* learned planner: the cost model's estimate (0 if
+                               the greedy plan ran)                             */
 } sv_stats;
 
 /* ---- lifetime --------------------------------------------------------- */
@@ -321,12 +325,22 @@ typedef struct sv_launch_record {
     int32_t nops;      /* programme steps of the pass (1 for per-gate)         */
     int32_t ngates;    /* circuit gates the launch applies                     */
     int32_t dtype;     /* sv_dtype                                             */
-    int32_t gate_kind; /* per-gate: the gate kind; tile: -1                    */
+    int32_t gate_kind; /* per-gate: the gate kind; tile kernels: -1 generic,
+                          -2 register-stage, -3 fused (tensor cores);
+                          remap: -4                                            */
     double bytes;      /* algorithmic bytes: 2 * 2^n * sizeof(amp) per sweep,
-                          or the touched share for per-gate diagonal/SWAP      */
-    double ms;         /* measured duration                                    */
+                          the touched share for per-gate diagonal/SWAP, the
+                          moved share for a remap                              */
+    double ms;         /* measured duration (0 in planning descriptors)        */
     uint64_t feat;     /* tile: bit mask of the physical qubits in the tile;
-                          per-gate: bit mask of the gate's qubits              */
+                          per-gate: bit mask of the gate's qubits; remap: bit
+                          mask of the exchanged bits                           */
+    int32_t c;         /* tile: chunk qubits (contiguous low bits)             */
+    int32_t stages;    /* register-stage / fused: stage layouts                */
+    int32_t blocks;    /* fused: 32x32 tensor-core blocks                      */
+    int32_t nins;      /* register-stage / fused: programme instructions       */
+    int32_t nfactors;  /* register-stage / fused: diagonal factor applications */
+    int32_t reserved;
 } sv_launch_record;
 
 /* Start (enable=1) or stop (0) recording launch records on this handle.
@@ -341,6 +355,100 @@ sv_status sv_profile_read(sv_handle h, sv_launch_record *host_out, size_t cap, s
 
 /* Number of kernels this library has launched in the process so far. */
 uint64_t sv_launch_count(void);
+
+/* ---- cost model and learned planner ------------------------------------- */
+
+/* A small MLP predicts the duration of one launch from a feature vector
+ * that sv_cost_features derives from a launch record.  Layers:
+ * SV_COST_FEATURES -> 64 -> ReLU -> 64 -> ReLU -> 1, FP32.  Parameters are one
+ * flat vector (row-major): W1[F][64], b1[64], W2[64][64], b2[64], W3[64], b3,
+ * with z1_j = b1_j + sum_i x_i W1[i][j].  The output estimates
+ * ln(ms / (bytes / 1e9)), the log of the launch time per algorithmic GB.
+ * Training minimises the mean squared error with Adam; forward, backward
+ * and update run in this library's kernels.  The model only ranks schedules,
+ * so it never changes what a plan computes. */
+#define SV_COST_FEATURES 52
+#define SV_COST_HIDDEN 64
+#define SV_COST_PARAMS 7617
+
+typedef struct sv_cost_model_s *sv_cost_model;
+
+typedef struct sv_train_config {
+    int32_t epochs;   /* passes over the data (default 100)                    */
+    int32_t batch;    /* samples per Adam step (default 4096)                  */
+    float lr;         /* default 1e-3                                          */
+    float beta1;      /* default 0.9                                           */
+    float beta2;      /* default 0.999                                         */
+    float eps;        /* default 1e-8                                          */
+    uint64_t seed;    /* shuffling (SplitMix64 Fisher-Yates per epoch)         */
+    int32_t reserved[6];
+} sv_train_config;
+
+/* Feature vector of one launch record (SV_COST_FEATURES floats): physical
+ * qubit mask bits 0..31, stride class of the highest qubit (<5, 5-9,
+ * 10..k-1, >=k), dtype, kernel family, and scaled logs of gates,
+ * instructions, stages, blocks and factors, plus c, n, k and k - c.
+ * Host only. */
+sv_status sv_cost_features(const sv_launch_record *rec, float *host_out);
+
+/* Create a model on the current device with He-uniform weights drawn from
+ * `seed` (SplitMix64), zero biases and zero Adam moments. */
+sv_status sv_cost_model_create(uint64_t seed, sv_cost_model *out);
+sv_status sv_cost_model_destroy(sv_cost_model m);
+/* SV_COST_PARAMS floats, layout above. */
+sv_status sv_cost_model_get_params(sv_cost_model m, float *host_params);
+sv_status sv_cost_model_set_params(sv_cost_model m, const float *host_params);
+/* y[i] = network(x[i]) for `count` rows of SV_COST_FEATURES floats. */
+sv_status sv_cost_model_predict(sv_cost_model m, const float *host_x, size_t count,
+                                float *host_y);
+/* Gradient of the mean squared error over all `count` samples with respect
+ * to the parameters (SV_COST_PARAMS floats) and the loss itself. */
+sv_status sv_cost_model_gradient(sv_cost_model m, const float *host_x, const float *host_t,
+                                 size_t count, float *host_grad, double *host_loss);
+/* Adam training; host_epoch_loss (may be NULL) receives the mean training
+ * loss of each epoch.  cfg NULL or zero fields = defaults. */
+sv_status sv_cost_model_train(sv_cost_model m, const float *host_x, const float *host_t,
+                              size_t count, const sv_train_config *cfg,
+                              float *host_epoch_loss);
+/* Binary file: "SVCM", version, F, hidden, parameter count, parameters. */
+sv_status sv_cost_model_save(sv_cost_model m, const char *path);
+sv_status sv_cost_model_load(const char *path, sv_cost_model *out);
+
+/* Attach a model to a handle (not owned; NULL detaches).  With
+ * sv_config.planner = SV_PLANNER_LEARNED, sv_apply_circuit then scores
+ * candidate schedules (chunk width, tile gathering or the paper's explicit
+ * remaps, and per pass the register-stage or the fused tensor-core kernel)
+ * by the model's predicted time and runs the cheapest.  Without a model, or
+ * when sv_planner_judge found the greedy plan faster for this circuit
+ * structure, the greedy plan of the configuration runs instead. */
+sv_status sv_set_cost_model(sv_handle h, sv_cost_model m);
+
+/* Outcome of a learned-planner decision. */
+typedef struct sv_plan_choice {
+    int32_t chunk_qubits;        /* c of the chosen candidate                  */
+    int32_t paper_swap;          /* 1: explicit remaps (Sec. III-B literal)    */
+    int32_t passes;              /* tile passes of the chosen plan             */
+    int32_t remaps;              /* remap passes of the chosen plan            */
+    int32_t fused_passes;        /* passes given to the fused kernel           */
+    int32_t candidates;          /* candidate passes scored                    */
+    double predicted_ms;         /* predicted time of the chosen plan          */
+    double greedy_predicted_ms;  /* predicted time of the greedy plan          */
+    double learned_ms;           /* measured by sv_planner_judge, else 0       */
+    double greedy_ms;            /* measured by sv_planner_judge, else 0       */
+    int32_t verdict;             /* planner the judge kept (sv_planner)        */
+    int32_t reserved[7];
+} sv_plan_choice;
+
+/* The learned planner's choice for this gate list (no kernel runs). */
+sv_status sv_learned_plan(sv_handle h, const sv_gate *host_gates, size_t m,
+                          const sv_config *cfg, sv_plan_choice *out);
+
+/* Run the greedy plan of cfg and the learned plan from |0...0>, once to warm
+ * up and three times each under CUDA events, and keep the faster (median)
+ * for this circuit structure on this handle.  The state is reset to
+ * |0...0> afterwards. */
+sv_status sv_planner_judge(sv_handle h, const sv_gate *host_gates, size_t m,
+                           const sv_config *cfg, sv_plan_choice *out);
 
 /* ---- diagnostics ------------------------------------------------------ */
 

@@ -189,7 +189,20 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *host_gates, size_t m, con
     } else {
         std::vector<sv_gate> gl(host_gates, host_gates + m);
         c.mode = mode;
-        st = partitioned_apply(h, gl, c);
+        sv_state::Learned *L = nullptr;
+        if (c.planner == SV_PLANNER_LEARNED && h->cost_model) {
+            sv_config key_cfg = c;
+            key_cfg.planner = SV_PLANNER_GREEDY;
+            st = learned_entry(h, gl, key_cfg, &L);
+        }
+        if (st == SV_OK && L && L->verdict != SV_PLANNER_GREEDY) {
+            st = partitioned_apply(h, gl, c, &L->ov);
+            h->stats.planner = SV_PLANNER_LEARNED;
+            h->stats.predicted_ms = L->info.predicted_ms;
+            h->stats.candidates = L->info.candidates;
+        } else if (st == SV_OK) {
+            st = partitioned_apply(h, gl, c);
+        }
     }
     h->stats.sweep_bytes = 2.0 * h->stats.passes * (double)state_bytes(h);
     return st;

@@ -4,10 +4,12 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <string>
 #include <utility>
 #include <vector>
 
+#include "plan.h"
 #include "sv.h"
 
 namespace sv {
@@ -85,6 +87,14 @@ struct sv_state {
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> event_pool;
     int launch_index = 0;  // within the current sv_apply_circuit
+    // learned planner
+    sv_cost_model_s *cost_model = nullptr;  // attached, not owned
+    struct Learned {
+        sv::PlanOverride ov;
+        sv_plan_choice info{};
+        int verdict = -1;  // planner the judge kept; -1 = not judged
+    };
+    std::map<uint64_t, Learned> learned;  // by circuit structure and start layout
 };
 
 namespace sv {
@@ -113,6 +123,10 @@ sv_status remap_apply(sv_state *h, const std::vector<std::pair<int, int>> &pairs
 // Move every logical qubit q to physical bit q (at most two remap passes).
 sv_status remap_to_identity(sv_state *h);
 
+// ---- cost model (costmodel.cu) -------------------------------------------------
+void cost_features(const sv_launch_record &rec, float *out);
+sv_status cost_predict(sv_cost_model_s *m, const float *host_x, size_t count, float *host_y);
+
 // ---- read-out (measure.cu) ----------------------------------------------------
 // Marginal over physical positions pos[0..m-1] (output bit j <-> pos[j]),
 // renormalised, into device buffer dev_out (2^m doubles), on h->stream.
@@ -138,6 +152,15 @@ sv_status t2_batch_launch(float *states, const BatchArgs &b, int sm_count, cudaS
 // SV_ERR_TIMEOUT if a kernel of this handle reported a bounded wait that gave up.
 sv_status check_device_flag(sv_state *h);
 sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates_logical,
-                            const sv_config &cfg);
+                            const sv_config &cfg, const PlanOverride *ov = nullptr);
+// Learned planner (learned.cpp): the cached decision for this gate list,
+// configuration and the handle's current qubit map (computed on first use).
+sv_status learned_entry(sv_state *h, const std::vector<sv_gate> &gates, const sv_config &cfg,
+                        sv_state::Learned **out);
+// Launch descriptors (the cost model's input) of a tile pass on kernel
+// family PK_* (t2 = its compiled programme, may be NULL for the generic
+// kernel) and of a remap pass.
+sv_launch_record describe_pass(int n, sv_dtype dt, const TilePass &p, const T2Pass *t2, int family);
+sv_launch_record describe_remap(int n, sv_dtype dt, const std::vector<std::pair<int, int>> &pairs);
 
 }  // namespace sv

@@ -96,6 +96,16 @@ struct Plan {
     int remaps = 0;  // remap passes (pairs exchanged in one sweep count once)
 };
 
+// Kernel of one tile pass.
+enum PassKernel : int8_t { PK_GENERIC = 0, PK_T2 = 1, PK_T3 = 2 };
+
+// A plan fixed by the learned planner: planner options and, per pass of the
+// resulting plan, the kernel to run it on.
+struct PlanOverride {
+    PlanOptions opt;
+    std::vector<int8_t> kernel;
+};
+
 // Build the programme; phys (logical -> physical, n entries) is updated by
 // SWAP relabelling.  Gates must be valid.  Returns an empty string on success.
 std::string build_plan(const std::vector<sv_gate> &gates, const PlanOptions &opt, int *phys,

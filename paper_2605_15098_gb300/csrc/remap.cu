@@ -148,14 +148,8 @@ sv_status remap_apply(sv_state *h, const std::vector<std::pair<int, int>> &pairs
     const int vb = std::min(low, vb_max);
     const int gb = (int)h->amp_bytes << vb;
 
-    sv_launch_record meta{};
-    meta.kind = SV_KERNEL_REMAP;
+    sv_launch_record meta = describe_remap(h->n, h->dt, pairs);
     meta.pass = h->launch_index++;
-    meta.n = h->n;
-    meta.dtype = (int32_t)h->dt;
-    meta.ngates = np;
-    meta.bytes = 2.0 * (1.0 - std::ldexp(1.0, -np)) * (double)state_bytes(h);
-    meta.feat = used;
     const int slot = prof_begin(h);
     switch (gb) {
         case 8: launch<8>(h, np, lo, hi, vb); break;

@@ -8,6 +8,7 @@
 // a control on a global qubit is a per-tile branch and every diagonal run
 // reduces to a per-tile phase polynomial over the local bits.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <type_traits>
 
@@ -274,9 +275,44 @@ sv_status check_device_flag(sv_state *h) {
     return SV_OK;
 }
 
-sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, const sv_config &cfg) {
+sv_launch_record describe_pass(int n, sv_dtype dt, const TilePass &p, const T2Pass *t2, int family) {
+    sv_launch_record r{};
+    r.kind = family == PK_T3 ? SV_KERNEL_FUSED : SV_KERNEL_TILE;
+    r.n = n;
+    r.k = p.k;
+    r.c = p.c;
+    r.nops = (int)p.ops.size();
+    r.ngates = p.ngates;
+    r.dtype = (int32_t)dt;
+    r.gate_kind = family == PK_T3 ? -3 : family == PK_T2 ? -2 : -1;
+    r.bytes = 2.0 * (double)(UINT64_C(1) << n) * (dt == SV_C128 ? 16.0 : 8.0);
+    r.feat = ~p.gmask & ((UINT64_C(1) << n) - 1);
+    if (t2 && family != PK_GENERIC) {
+        r.stages = (int)t2->stages.size();
+        r.blocks = family == PK_T3 ? t2->nblocks : 0;
+        r.nins = (int)t2->ins.size();
+        r.nfactors = (int)t2->factors.size();
+    }
+    return r;
+}
+
+sv_launch_record describe_remap(int n, sv_dtype dt, const std::vector<std::pair<int, int>> &pairs) {
+    sv_launch_record r{};
+    r.kind = SV_KERNEL_REMAP;
+    r.n = n;
+    r.dtype = (int32_t)dt;
+    r.gate_kind = -4;
+    r.ngates = (int)pairs.size();
+    for (const auto &pr : pairs) r.feat |= (UINT64_C(1) << pr.first) | (UINT64_C(1) << pr.second);
+    const double sb = (double)(UINT64_C(1) << n) * (dt == SV_C128 ? 16.0 : 8.0);
+    r.bytes = 2.0 * (1.0 - std::ldexp(1.0, -(int)pairs.size())) * sb;
+    return r;
+}
+
+sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, const sv_config &cfg,
+                            const PlanOverride *ov) {
     const bool dbl = h->dt == SV_C128;
-    PlanOptions opt = plan_options(h->n, h->dt, cfg);
+    PlanOptions opt = ov ? ov->opt : plan_options(h->n, h->dt, cfg);
     if (dbl && opt.k > 13) return fail(SV_ERR_ARG, "complex128 tiles hold at most 2^13 amplitudes");
     Plan plan;
     int phys[64];
@@ -290,15 +326,18 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
     std::vector<T2Pass> t2(plan.passes.size());
     std::vector<PassUpload> up(plan.passes.size());
     Blob blob;
+    if (ov && ov->kernel.size() != plan.passes.size())
+        return fail(SV_ERR_STATE, "internal: learned plan does not match the planner's passes");
     for (size_t i = 0; i < plan.passes.size(); i++) {
         const TilePass &p = plan.passes[i];
         if (p.ops.empty()) continue;
+        const int want = ov ? ov->kernel[i] : (!allow_t2 ? PK_GENERIC : fused ? PK_T3 : PK_T2);
         bool ok = false;
-        if (allow_t2 && fused && compile_t2(p, &t2[i], true).empty()) {
+        if (want == PK_T3 && compile_t2(p, &t2[i], true).empty()) {
             ok = true;
             up[i].t3 = true;
             up[i].blocks = blob.put_vec(t2[i].blocks_dev);
-        } else if (allow_t2 && compile_t2(p, &t2[i], false).empty()) {
+        } else if ((want == PK_T3 || want == PK_T2) && compile_t2(p, &t2[i], false).empty()) {
             ok = true;
         }
         if (ok) {
@@ -350,18 +389,9 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
         const TilePass &p = plan.passes[i];
         if (!p.remap_before.empty()) SV_TRY(remap_apply(h, p.remap_before));
         if (p.ops.empty()) continue;
-        sv_launch_record meta{};
-        meta.kind = SV_KERNEL_TILE;
+        sv_launch_record meta = describe_pass(h->n, h->dt, p, up[i].t2 ? &t2[i] : nullptr,
+                                              up[i].t3 ? PK_T3 : up[i].t2 ? PK_T2 : PK_GENERIC);
         meta.pass = h->launch_index++;
-        meta.n = h->n;
-        meta.k = p.k;
-        meta.nops = (int)p.ops.size();
-        meta.ngates = p.ngates;
-        meta.dtype = (int32_t)h->dt;
-        meta.gate_kind = up[i].t3 ? -3 : up[i].t2 ? -2 : -1;
-        if (up[i].t3) meta.kind = SV_KERNEL_FUSED;
-        meta.bytes = 2.0 * (double)state_bytes(h);
-        meta.feat = ~p.gmask & ((UINT64_C(1) << h->n) - 1);
         sv_status st;
         if (!up[i].t3) SV_TRY(resolve_norm(h));
         if (up[i].t2) {

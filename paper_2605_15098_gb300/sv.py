@@ -31,7 +31,12 @@ EXPORTS = (
     "sv_profile", "sv_profile_read", "sv_launch_count", "sv_marginal_noalloc", "sv_plan_export",
     "sv_batch_create", "sv_batch_run", "sv_batch_info", "sv_batch_destroy", "sv_apply_circuit_batch",
     "sv_autotune", "sv_batch_autotune",
+    "sv_cost_features", "sv_cost_model_create", "sv_cost_model_destroy", "sv_cost_model_get_params",
+    "sv_cost_model_set_params", "sv_cost_model_predict", "sv_cost_model_gradient",
+    "sv_cost_model_train", "sv_cost_model_save", "sv_cost_model_load", "sv_set_cost_model",
+    "sv_learned_plan", "sv_planner_judge",
 )
+SV_COST_FEATURES, SV_COST_HIDDEN, SV_COST_PARAMS = 52, 64, 7617
 SV_KERNEL_PERGATE, SV_KERNEL_TILE, SV_KERNEL_REMAP, SV_KERNEL_FUSED = 0, 1, 2, 3
 
 
@@ -57,7 +62,8 @@ class sv_stats(ctypes.Structure):
                 ("remaps", ctypes.c_int32), ("kernels", ctypes.c_int32),
                 ("relabels", ctypes.c_int32), ("fused_blocks", ctypes.c_int32),
                 ("sweep_bytes", ctypes.c_double), ("touched_bytes", ctypes.c_double),
-                ("h2d_bytes", ctypes.c_double)]
+                ("h2d_bytes", ctypes.c_double), ("planner", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("predicted_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -67,10 +73,31 @@ class sv_launch_record(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("pass_", ctypes.c_int32), ("n", ctypes.c_int32),
                 ("k", ctypes.c_int32), ("nops", ctypes.c_int32), ("ngates", ctypes.c_int32),
                 ("dtype", ctypes.c_int32), ("gate_kind", ctypes.c_int32),
-                ("bytes", ctypes.c_double), ("ms", ctypes.c_double), ("feat", ctypes.c_uint64)]
+                ("bytes", ctypes.c_double), ("ms", ctypes.c_double), ("feat", ctypes.c_uint64),
+                ("c", ctypes.c_int32), ("stages", ctypes.c_int32), ("blocks", ctypes.c_int32),
+                ("nins", ctypes.c_int32), ("nfactors", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class sv_train_config(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("seed", ctypes.c_uint64), ("reserved", ctypes.c_int32 * 6)]
+
+
+class sv_plan_choice(ctypes.Structure):
+    _fields_ = [("chunk_qubits", ctypes.c_int32), ("paper_swap", ctypes.c_int32),
+                ("passes", ctypes.c_int32), ("remaps", ctypes.c_int32),
+                ("fused_passes", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("predicted_ms", ctypes.c_double), ("greedy_predicted_ms", ctypes.c_double),
+                ("learned_ms", ctypes.c_double), ("greedy_ms", ctypes.c_double),
+                ("verdict", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 class sv_batch_item(ctypes.Structure):
@@ -117,6 +144,20 @@ def lib() -> ctypes.CDLL:
         "sv_autotune": [vp, vp, sz, ctypes.c_char_p, ctypes.POINTER(sv_config), dp],
         "sv_batch_autotune": [vp, sz, ctypes.POINTER(sv_config), dp],
         "sv_profile_read": [vp, vp, sz, ctypes.POINTER(sz)],
+        "sv_cost_features": [ctypes.POINTER(sv_launch_record), vp],
+        "sv_cost_model_create": [u64, ctypes.POINTER(vp)],
+        "sv_cost_model_destroy": [vp],
+        "sv_cost_model_get_params": [vp, vp],
+        "sv_cost_model_set_params": [vp, vp],
+        "sv_cost_model_predict": [vp, vp, sz, vp],
+        "sv_cost_model_gradient": [vp, vp, vp, sz, vp, dp],
+        "sv_cost_model_train": [vp, vp, vp, sz, ctypes.POINTER(sv_train_config), vp],
+        "sv_cost_model_save": [vp, ctypes.c_char_p],
+        "sv_cost_model_load": [ctypes.c_char_p, ctypes.POINTER(vp)],
+        "sv_set_cost_model": [vp, vp],
+        "sv_learned_plan": [vp, vp, sz, ctypes.POINTER(sv_config), ctypes.POINTER(sv_plan_choice)],
+        "sv_planner_judge": [vp, vp, sz, ctypes.POINTER(sv_config),
+                             ctypes.POINTER(sv_plan_choice)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -340,6 +381,107 @@ def sv_batch_autotune(circuits):
     _check(lib().sv_batch_autotune(arr, len(circuits), ctypes.byref(best), ctypes.byref(ms)))
     del keep
     return best, ms.value
+
+
+def _f32(a, cols=None) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if cols is not None:
+        assert a.ndim == 2 and a.shape[1] == cols, a.shape
+    return a
+
+
+def sv_cost_features(rec: dict) -> np.ndarray:
+    """Feature vector of one launch record (dict as returned by sv_profile_read)."""
+    r = sv_launch_record(**{f: rec.get(f, 0) for f, _ in sv_launch_record._fields_})
+    out = np.zeros(SV_COST_FEATURES, dtype=np.float32)
+    _check(lib().sv_cost_features(ctypes.byref(r), out.ctypes.data))
+    return out
+
+
+def cost_target(rec: dict) -> float:
+    """What the cost model predicts for a record: ln(ms per algorithmic GB)."""
+    return float(np.log(rec["ms"]) - np.log(rec["bytes"] * 1e-9))
+
+
+def sv_cost_model_create(seed: int = 0) -> int:
+    m = ctypes.c_void_p()
+    _check(lib().sv_cost_model_create(seed, ctypes.byref(m)))
+    return m.value
+
+
+def sv_cost_model_destroy(m: int) -> None:
+    _check(lib().sv_cost_model_destroy(ctypes.c_void_p(m)))
+
+
+def sv_cost_model_get_params(m: int) -> np.ndarray:
+    p = np.empty(SV_COST_PARAMS, dtype=np.float32)
+    _check(lib().sv_cost_model_get_params(ctypes.c_void_p(m), p.ctypes.data))
+    return p
+
+
+def sv_cost_model_set_params(m: int, p) -> None:
+    p = _f32(p)
+    assert p.size == SV_COST_PARAMS
+    _check(lib().sv_cost_model_set_params(ctypes.c_void_p(m), p.ctypes.data))
+
+
+def sv_cost_model_predict(m: int, X) -> np.ndarray:
+    X = _f32(X, SV_COST_FEATURES)
+    y = np.empty(X.shape[0], dtype=np.float32)
+    _check(lib().sv_cost_model_predict(ctypes.c_void_p(m), X.ctypes.data if X.size else None,
+                                       X.shape[0], y.ctypes.data if y.size else None))
+    return y
+
+
+def sv_cost_model_gradient(m: int, X, T):
+    X, T = _f32(X, SV_COST_FEATURES), _f32(T)
+    g = np.empty(SV_COST_PARAMS, dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(lib().sv_cost_model_gradient(ctypes.c_void_p(m), X.ctypes.data, T.ctypes.data,
+                                        X.shape[0], g.ctypes.data, ctypes.byref(loss)))
+    return g, loss.value
+
+
+def sv_cost_model_train(m: int, X, T, epochs=100, batch=4096, lr=1e-3, seed=0,
+                        beta1=0.9, beta2=0.999, eps=1e-8) -> np.ndarray:
+    X, T = _f32(X, SV_COST_FEATURES), _f32(T)
+    cfg = sv_train_config(epochs, batch, lr, beta1, beta2, eps, seed)
+    losses = np.empty(epochs, dtype=np.float32)
+    _check(lib().sv_cost_model_train(ctypes.c_void_p(m), X.ctypes.data, T.ctypes.data,
+                                     X.shape[0], ctypes.byref(cfg), losses.ctypes.data))
+    return losses
+
+
+def sv_cost_model_save(m: int, path: str) -> None:
+    _check(lib().sv_cost_model_save(ctypes.c_void_p(m), path.encode()))
+
+
+def sv_cost_model_load(path: str) -> int:
+    m = ctypes.c_void_p()
+    _check(lib().sv_cost_model_load(path.encode(), ctypes.byref(m)))
+    return m.value
+
+
+def sv_set_cost_model(h: int, m: int | None) -> None:
+    _check(lib().sv_set_cost_model(ctypes.c_void_p(h), ctypes.c_void_p(m) if m else None))
+
+
+def sv_learned_plan(h: int, gates, cfg: sv_config | None = None) -> dict:
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    out = sv_plan_choice()
+    _check(lib().sv_learned_plan(ctypes.c_void_p(h), g.ctypes.data if g.size else None, g.size,
+                                 ctypes.byref(cfg) if cfg is not None else None,
+                                 ctypes.byref(out)))
+    return out.as_dict()
+
+
+def sv_planner_judge(h: int, gates, cfg: sv_config | None = None) -> dict:
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    out = sv_plan_choice()
+    _check(lib().sv_planner_judge(ctypes.c_void_p(h), g.ctypes.data if g.size else None, g.size,
+                                  ctypes.byref(cfg) if cfg is not None else None,
+                                  ctypes.byref(out)))
+    return out.as_dict()
 
 
 def config_dict(c: sv_config) -> dict:

@@ -92,3 +92,26 @@ def test_batch_host_path_without_device(svlib):
     with pytest.raises(svlib.SvError) as e:
         svlib.sv_batch_create(bad)
     assert e.value.code == svlib.SV_ERR_ARG
+
+
+def test_cost_features_host(svlib):
+    """Feature vector layout of a launch record (host only)."""
+    rec = {"kind": svlib.SV_KERNEL_TILE, "n": 28, "k": 13, "c": 5, "ngates": 15, "dtype": 0,
+           "gate_kind": -2, "bytes": 4.0e9, "feat": (1 << 5) - 1 | (1 << 9) | (1 << 27),
+           "stages": 3, "blocks": 0, "nins": 40, "nfactors": 7}
+    f = svlib.sv_cost_features(rec)
+    assert f.shape == (svlib.SV_COST_FEATURES,)
+    assert list(f[:32]) == [float((rec["feat"] >> q) & 1) for q in range(32)]
+    assert list(f[32:36]) == [0, 0, 0, 1]        # top qubit 27 >= k
+    assert list(f[36:38]) == [1, 0]              # complex64
+    assert list(f[38:43]) == [0, 0, 1, 0, 0]     # register-stage kernel
+    assert abs(f[43] - np.log2(16) / 8) < 1e-6
+    assert abs(f[47] - 5 / 16) < 1e-7 and abs(f[49] - 13 / 16) < 1e-7 and abs(f[51] - 8 / 16) < 1e-7
+    rec.update(kind=svlib.SV_KERNEL_REMAP, gate_kind=-4, feat=(1 << 3) | (1 << 20))
+    f = svlib.sv_cost_features(rec)
+    assert list(f[38:43]) == [0, 0, 0, 0, 1] and list(f[32:36]) == [0, 0, 0, 1]
+    rec.update(kind=svlib.SV_KERNEL_FUSED, gate_kind=-3, feat=0b111, dtype=1)
+    f = svlib.sv_cost_features(rec)
+    assert list(f[38:43]) == [0, 0, 0, 1, 0] and list(f[32:36]) == [1, 0, 0, 0]
+    assert list(f[36:38]) == [0, 1]
+    assert svlib.cost_target({"ms": 2.0, "bytes": 4.0e9}) == pytest.approx(np.log(0.5))
