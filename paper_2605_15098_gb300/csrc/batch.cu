@@ -186,6 +186,7 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
             a.ntiles = UINT64_C(1) << (cp.nphys - t2.k);
             a.c = t2.c;
             a.nins = (int)t2.ins.size();
+            a.last_stage = t2.last_stage;
             a.nruns = t2.nruns;
             a.ntterms = (int)t2.tterms.size();
             for (int s = 0; s < t2.k; s++) a.slot_phys[s] = t2.slot_phys[s];

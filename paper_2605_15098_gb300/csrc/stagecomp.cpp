@@ -430,6 +430,8 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
         if (!e.empty()) return e;
         if (out->factors.size() > 32000) return "too many factor applications";
     }
+    for (size_t i = 0; i < out->ins.size(); i++)
+        if (out->ins[i].op == T2_STAGE) out->last_stage = (int)i;
     if (out->n_h || fused) {  // fused passes always end with a scale (norm correction)
         const double s = std::pow(2.0, -0.5 * out->n_h);
         const float hi = (float)s;

@@ -18,6 +18,7 @@ struct T2Pass {
     int ngates = 0;
     int nruns = 0;
     int n_h = 0;                    // unnormalised Hadamards (2^(-n_h/2) at the end)
+    int last_stage = -1;            // index in `ins` of the last T2_STAGE
     std::vector<T2Ins> ins;
     std::vector<T2Stage> stages;
     std::vector<T2Mat> mats;
@@ -44,6 +45,7 @@ struct T2Device {
 struct T2Args {
     uint64_t gmask, ntiles;
     int c, nins, nruns, ntterms;
+    int last_stage;  // index of the last T2_STAGE instruction
     int slot_phys[kMaxTileQubits];
     const int4 *ins;       // T2Ins records
     const int4 *stages;    // T2Stage records

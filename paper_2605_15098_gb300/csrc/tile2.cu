@@ -40,54 +40,85 @@ constexpr size_t kSmemBytes = kOffBar + 16;
 
 
 // ---------------------------------------------------------------- the kernel
-// Run a pass's programme on the tile in shared memory (interleaved complex64,
-// local index order) and leave the result there, interleaved.
-__device__ __forceinline__ void t2_run(const T2Args &a, float4 *tile4, const float2 *tab,
-                                       const uint32_t *lin, const uint32_t *cst, uint64_t base,
-                                       int tid) {
-    Regs r;
-    int bt = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0;  // current layout: thread base, register strides
-    int stage = 0;
-    bool live = false;
-    auto sidx = [&](int q) {
+// Run a pass's programme on the tile.  The first stage reads the tile from
+// shared memory (interleaved complex64, local index order).  After the last
+// stage change has read shared memory, `hook()` runs (k_tile2 starts the next
+// tile's bulk copies there).  The result goes back to shared memory,
+// interleaved (kDirect = false), or straight from registers to the global
+// state (kDirect = true; `gw` gives the global offset of a single tile bit).
+struct NoHook {
+    __device__ void operator()() const {}
+};
+
+extern __shared__ __align__(1024) unsigned char t2_dyn_smem[];
+__shared__ uint64_t t2_tile_base;  // physical index of the current tile's amplitude 0
+
+// Float4 index (amplitude pair) of packed pair q in the layout of stage
+// record st, for thread tid.
+struct Layout2 {
+    int bt, s1, s2, s3, s4;
+    __device__ Layout2(const int4 &st, int tid) {
+        auto tb = [&](int i) {
+            const int word = i < 4 ? st.x : i < 8 ? st.y : i < 12 ? st.z : st.w;
+            return (word >> (8 * (i & 3))) & 0xff;
+        };
+        bt = 0;
+#pragma unroll
+        for (int t = 0; t < 8; t++) bt |= ((tid >> t) & 1) << tb(5 + t);
+        s1 = 1 << tb(1);
+        s2 = 1 << tb(2);
+        s3 = 1 << tb(3);
+        s4 = 1 << tb(4);
+    }
+    __device__ int idx(int q) const {
         return (bt + ((q & 1) ? s1 : 0) + ((q & 2) ? s2 : 0) + ((q & 4) ? s3 : 0) +
                 ((q & 8) ? s4 : 0)) >> 1;
-    };
+    }
+};
+
+template <bool kDirect, typename Hook>
+__device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hook) {
+    float4 *tile4 = reinterpret_cast<float4 *>(t2_dyn_smem);
+    const float2 *tab = reinterpret_cast<const float2 *>(t2_dyn_smem + kOffTab);
+    const uint32_t *lin = reinterpret_cast<const uint32_t *>(t2_dyn_smem + kOffLin);
+    const uint32_t *cst = reinterpret_cast<const uint32_t *>(t2_dyn_smem + kOffCst);
+    const int tid = threadIdx.x;
+    Regs r;
+    int stage = 0;
+    bool live = false;
+    bool hooked = false;
     for (int pc = 0; pc < a.nins; pc++) {
         const int4 w = __ldg(a.ins + pc);
         const int op = w.x & 0xff;
         if (op == T2_STAGE) {
             if (live) {
+                const Layout2 L(__ldg(a.stages + stage), tid);
 #pragma unroll
                 for (int q = 0; q < kNP; q++)
-                    tile4[sidx(q)] = make_float4(r.re[q].x, r.re[q].y, r.im[q].x, r.im[q].y);
+                    tile4[L.idx(q)] = make_float4(r.re[q].x, r.re[q].y, r.im[q].x, r.im[q].y);
                 __syncthreads();
             }
             stage = w.w;
-            const int4 st = __ldg(a.stages + stage);
-            auto tbyte = [&](int i) {
-                const int word = i < 4 ? st.x : i < 8 ? st.y : i < 12 ? st.z : st.w;
-                return (word >> (8 * (i & 3))) & 0xff;
-            };
-            bt = 0;
+            {
+                const Layout2 L(__ldg(a.stages + stage), tid);
 #pragma unroll
-            for (int t = 0; t < 8; t++) bt |= ((tid >> t) & 1) << tbyte(5 + t);
-            s1 = 1 << tbyte(1);
-            s2 = 1 << tbyte(2);
-            s3 = 1 << tbyte(3);
-            s4 = 1 << tbyte(4);
-#pragma unroll
-            for (int q = 0; q < kNP; q++) {
-                const float4 v = tile4[sidx(q)];
-                if (live) {
-                    r.re[q] = make_float2(v.x, v.y);
-                    r.im[q] = make_float2(v.z, v.w);
-                } else {
-                    r.re[q] = make_float2(v.x, v.z);
-                    r.im[q] = make_float2(v.y, v.w);
+                for (int q = 0; q < kNP; q++) {
+                    const float4 v = tile4[L.idx(q)];
+                    if (live) {
+                        r.re[q] = make_float2(v.x, v.y);
+                        r.im[q] = make_float2(v.z, v.w);
+                    } else {
+                        r.re[q] = make_float2(v.x, v.z);
+                        r.im[q] = make_float2(v.y, v.w);
+                    }
                 }
             }
             live = true;
+            if (pc == a.last_stage) {
+                __syncthreads();  // every thread has read shared memory
+                hook();
+                hooked = true;
+            }
             continue;
         }
         if (op == T2_SCALE) {
@@ -102,8 +133,18 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *tile4, const flo
         }
         if (op == T2_DIAG) {
             const int e0 = (int16_t)(w.z & 0xffff), e1 = (int16_t)(w.z >> 16);
+            if (e0 >= e1) continue;
+            // software pipeline: the next factor's record and static phase
+            // load while this one is applied
+            int4 fd = __ldg(a.fac + e0);
+            uint32_t sv = ((uint32_t)fd.x & 0x100u) ? __ldg(a.stat + fd.z * 256 + tid) : 0u;
             for (int e = e0; e < e1; e++) {
-                const int4 fd = __ldg(a.fac + e);
+                int4 fdn = fd;
+                uint32_t svn = 0u;
+                if (e + 1 < e1) {
+                    fdn = __ldg(a.fac + e + 1);
+                    if ((uint32_t)fdn.x & 0x100u) svn = __ldg(a.stat + fdn.z * 256 + tid);
+                }
                 const uint32_t w0 = (uint32_t)fd.x;
                 const int run = fd.y;
                 float fr, fi;
@@ -111,7 +152,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *tile4, const flo
                     fr = __int_as_float(fd.z);
                     fi = __int_as_float(fd.w);
                 } else {
-                    uint32_t u = __ldg(a.stat + fd.z * 256 + tid);
+                    uint32_t u = sv;
                     if (w0 & 0x200u) u += cst[run];
                     const int lr = (int)((w0 >> 16) & 0xff) - 1;
                     if (lr >= 0) u += lin[run * 16 + lr];
@@ -130,22 +171,21 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *tile4, const flo
                     fi = ff.y;
                 }
                 apply_factor_any(r, (int)(w0 & 0xffu), fr, fi);
+                fd = fdn;
+                sv = svn;
             }
             continue;
         }
-        // gates
+        // gates (no register-bit controls: the stage compiler never emits them)
         const int cls = (w.x >> 8) & 0xff;
         const int j = (int8_t)((w.x >> 16) & 0xff);
         const int ccls = (w.x >> 24) & 0xff;
         const int cidx = (int16_t)(w.y & 0xffff);
         bool pred = true;
-        int jc = -1;
         if (ccls == T2C_GLOBAL) {
-            if (!((base >> cidx) & 1)) continue;  // tile-uniform
+            if (!((t2_tile_base >> cidx) & 1)) continue;  // tile-uniform
         } else if (ccls == T2C_THREAD) {
             pred = (tid >> cidx) & 1;
-        } else if (ccls == T2C_REG) {
-            jc = cidx;
         }
         float m[8];
         if (op == T2_GATE) {
@@ -156,45 +196,98 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *tile4, const flo
 #pragma unroll
             for (int e = 0; e < 8; e++) m[e] = 0.f;
         }
+        // all ones at run time (see reg_h2); the instruction word's pad field is zero
+        const uint32_t qm = ~((uint32_t)w.y >> 16);
         if (cls == T2C_LANE) {
-            lane_gate(r, op, j, jc, pred, m);
+            if (op == T2_H) lane_op2<T2_H>(r, j, pred, qm, m);
+            else if (op == T2_X) lane_op2<T2_X>(r, j, pred, qm, m);
+            else lane_op2<T2_GATE>(r, j, pred, qm, m);
             continue;
         }
         if (!pred) continue;
         if (op == T2_H) {
             switch (j) {
-                case 0: reg_h<0>(r, jc); break;
-                case 1: reg_h<1>(r, jc); break;
-                case 2: reg_h<2>(r, jc); break;
-                case 3: reg_h<3>(r, jc); break;
-                default: reg_h<4>(r, jc); break;
+                case 0: reg_h2<0>(r, qm); break;
+                case 1: reg_h2<1>(r, qm); break;
+                case 2: reg_h2<2>(r, qm); break;
+                case 3: reg_h2<3>(r, qm); break;
+                default: reg_h2<4>(r, qm); break;
             }
         } else if (op == T2_X) {
             switch (j) {
-                case 0: reg_x<0>(r, jc); break;
-                case 1: reg_x<1>(r, jc); break;
-                case 2: reg_x<2>(r, jc); break;
-                case 3: reg_x<3>(r, jc); break;
-                default: reg_x<4>(r, jc); break;
+                case 0: reg_x2<0>(r, qm); break;
+                case 1: reg_x2<1>(r, qm); break;
+                case 2: reg_x2<2>(r, qm); break;
+                case 3: reg_x2<3>(r, qm); break;
+                default: reg_x2<4>(r, qm); break;
             }
         } else {
             switch (j) {
-                case 0: reg_u<0>(r, jc, m); break;
-                case 1: reg_u<1>(r, jc, m); break;
-                case 2: reg_u<2>(r, jc, m); break;
-                case 3: reg_u<3>(r, jc, m); break;
-                default: reg_u<4>(r, jc, m); break;
+                case 0: reg_u2<0>(r, qm, m); break;
+                case 1: reg_u2<1>(r, qm, m); break;
+                case 2: reg_u2<2>(r, qm, m); break;
+                case 3: reg_u2<3>(r, qm, m); break;
+                default: reg_u2<4>(r, qm, m); break;
             }
         }
     }
-    // epilogue: interleaved tile back to shared memory, then TMA store
-    if (live) {
+    if (!hooked) {  // a programme without a stage change still releases the buffer
+        __syncthreads();
+        hook();
+    }
+    if (!live) return;
+    const int4 st = __ldg(a.stages + stage);
+    if constexpr (kDirect) {
+        // global offset (in amplitudes) of the final layout's tile bits
+        auto tb = [&](int i) {
+            const int word = i < 4 ? st.x : i < 8 ? st.y : i < 12 ? st.z : st.w;
+            return (word >> (8 * (i & 3))) & 0xff;
+        };
+        auto gw = [&](int b) -> uint64_t {
+            return b < a.c ? (UINT64_C(1) << b) : (UINT64_C(1) << a.slot_phys[b]);
+        };
+        uint64_t g0 = t2_tile_base;
+#pragma unroll
+        for (int t = 0; t < 8; t++)
+            if ((tid >> t) & 1) g0 += gw(tb(5 + t));
+        const uint64_t g1 = gw(tb(1)), g2 = gw(tb(2)), g3 = gw(tb(3)), g4 = gw(tb(4));
+#pragma unroll
+        for (int q = 0; q < kNP; q++) {
+            const uint64_t g = g0 + ((q & 1) ? g1 : 0) + ((q & 2) ? g2 : 0) + ((q & 4) ? g3 : 0) +
+                               ((q & 8) ? g4 : 0);
+            __stcs(gstate + (g >> 1), make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y));
+        }
+    } else {
+        const Layout2 L(st, tid);
 #pragma unroll
         for (int q = 0; q < kNP; q++)
-            tile4[sidx(q)] = make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y);
+            tile4[L.idx(q)] = make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y);
     }
 }
 
+__device__ __forceinline__ void issue_tile_load(const T2Args &a, unsigned char *sm, const float *state,
+                                                uint64_t tile, uint64_t *bar, int tid) {
+    const int nchunks = 1 << (kT2Qubits - a.c);
+    const uint32_t chunk_bytes = 8u << a.c;
+    const uint64_t base = pdep(tile, a.gmask);
+    if (tid == 0) {
+        fence_async_smem();
+        mbar_expect_tx(bar, kTileBytes);
+    }
+    __syncwarp();
+    for (int j = tid; j < nchunks; j += 32) {
+        uint64_t off = 0;
+        for (int b = 0; b < kT2Qubits - a.c; b++)
+            if ((j >> b) & 1) off |= UINT64_C(1) << a.slot_phys[a.c + b];
+        bulk_g2s(sm + (size_t)j * chunk_bytes, state + 2 * (base + off), chunk_bytes, bar);
+    }
+}
+
+// Persistent CTA over the pass's tiles.  Tile i+1's bulk copies start as
+// soon as tile i's last stage change has read shared memory, so they overlap
+// the rest of tile i's programme and its write-back, which goes from
+// registers straight to the global state (16-byte stores; lanes 0..7 cover
+// tile bits 1..3, so a quarter-warp writes 128 contiguous bytes).
 __global__ void __launch_bounds__(kT2Threads, 2) k_tile2(float *__restrict__ state, const T2Args a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     float4 *tile4 = reinterpret_cast<float4 *>(sm);
@@ -210,28 +303,18 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_tile2(float *__restrict__ sta
         fence_mbar_init();
     }
     __syncthreads();
+    if (tid < 32 && (uint64_t)blockIdx.x < a.ntiles) issue_tile_load(a, sm, state, blockIdx.x, bar, tid);
 
-    const int nchunks = 1 << (kT2Qubits - a.c);
-    const uint32_t chunk_bytes = 8u << a.c;
     uint32_t parity = 0;
     for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         const uint64_t base = pdep(tile, a.gmask);
-        if (tid < 32) {
-            if (tid == 0) {
-                fence_async_smem();
-                mbar_expect_tx(bar, kTileBytes);
-            }
-            __syncwarp();
-            for (int j = tid; j < nchunks; j += 32) {
-                uint64_t off = 0;
-                for (int b = 0; b < kT2Qubits - a.c; b++)
-                    if ((j >> b) & 1) off |= UINT64_C(1) << a.slot_phys[a.c + b];
-                bulk_g2s(sm + (size_t)j * chunk_bytes, state + 2 * (base + off), chunk_bytes, bar);
-            }
-        }
-        // per-tile diagonal data while the copies are in flight
+        const uint64_t next = tile + gridDim.x;
+        // per-tile diagonal data while the copies are in flight (the barrier
+        // first: the previous tile's programme may still read lin / cst)
+        __syncthreads();
         for (int i = tid; i < a.nruns * 16; i += blockDim.x) lin[i] = 0u;
         for (int i = tid; i < a.nruns; i += blockDim.x) cst[i] = 0u;
+        if (tid == 0) t2_tile_base = base;
         __syncthreads();
         for (int i = tid; i < a.ntterms; i += blockDim.x) {
             const T2TileTerm t = a.tterms[i];
@@ -245,21 +328,10 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_tile2(float *__restrict__ sta
             mbar_wait(bar, parity);  // give copies still in flight a second bounded wait
             return;
         }
-
-        t2_run(a, tile4, tab, lin, cst, base, tid);
-        fence_async_smem();
-        __syncthreads();
-        if (tid < 32) {
-            for (int j = tid; j < nchunks; j += 32) {
-                uint64_t off = 0;
-                for (int b = 0; b < kT2Qubits - a.c; b++)
-                    if ((j >> b) & 1) off |= UINT64_C(1) << a.slot_phys[a.c + b];
-                bulk_s2g(state + 2 * (base + off), sm + (size_t)j * chunk_bytes, chunk_bytes);
-            }
-            bulk_commit();
-            bulk_wait_read();
-        }
-        __syncthreads();
+        auto hook = [&]() {
+            if (tid < 32 && next < a.ntiles) issue_tile_load(a, sm, state, next, bar, tid);
+        };
+        t2_run<true>(a, reinterpret_cast<float4 *>(state), hook);
         parity ^= 1u;
     }
 }
@@ -327,6 +399,7 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
                 }
                 for (int i = tid; i < a.nruns * 16; i += blockDim.x) lin[i] = 0u;
                 for (int i = tid; i < a.nruns; i += blockDim.x) cst[i] = 0u;
+                if (tid == 0) t2_tile_base = base;
                 __syncthreads();
                 for (int i = tid; i < a.ntterms; i += blockDim.x) {
                     const T2TileTerm t = a.tterms[i];
@@ -344,7 +417,7 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
                     mbar_wait(bar, parity ^ 1u);
                     return;
                 }
-                t2_run(a, tile4, tab, lin, cst, base, tid);
+                t2_run<false>(a, nullptr, NoHook{});
                 fence_async_smem();
                 __syncthreads();
                 if (tid < 32) {
@@ -461,6 +534,7 @@ sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
     a.ntiles = UINT64_C(1) << (h->n - p.k);
     a.c = p.c;
     a.nins = (int)p.ins.size();
+    a.last_stage = p.last_stage;
     a.nruns = p.nruns;
     a.ntterms = (int)p.tterms.size();
     for (int s = 0; s < p.k; s++) a.slot_phys[s] = p.slot_phys[s];
