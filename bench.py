@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-paper", action="store_true")
+    ap.add_argument("--no-other", action="store_true", help="skip the other tile kernel's timing")
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -109,7 +110,7 @@ class Clocks:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -344,7 +345,7 @@ def run_ours(args, world, rank, local):
     }
 
     # ---- the other tile kernel on the same circuit (fused <-> CUDA-core) ----
-    if dt == sv.SV_C64 and mode in (sv.SV_MODE_FUSED, sv.SV_MODE_PARTITIONED):
+    if dt == sv.SV_C64 and mode in (sv.SV_MODE_FUSED, sv.SV_MODE_PARTITIONED) and not args.no_other:
         other = sv.SV_MODE_PARTITIONED if mode == sv.SV_MODE_FUSED else sv.SV_MODE_FUSED
         pc = sv.make_config(other, chunk_qubits=cfg.chunk_qubits)
         step(pc)

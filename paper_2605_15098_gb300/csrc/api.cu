@@ -240,9 +240,15 @@ sv_status sv_argmax(sv_handle h, uint64_t qubit_mask, uint64_t *host_idx, double
     clear_error();
     if (!h || !host_idx) return fail(SV_ERR_ARG, "NULL argument");
     SV_TRY(check_mask(h, qubit_mask));
-    uint64_t len;
-    SV_TRY(read_marginal(h, qubit_mask, &len));
-    return argmax_device(h, h->probs, len, host_idx, host_p);
+    // the argmax does not need the normalised vector: only max / total
+    int pos[64];
+    const int m = mask_positions(h, qubit_mask, pos);
+    const uint64_t len = UINT64_C(1) << m;
+    SV_TRY(ensure_probs(h, len * sizeof(double)));
+    const double *sums = nullptr;
+    int nsums = 0;
+    SV_TRY(marginal_device(h, pos, m, h->probs, false, &sums, &nsums));
+    return argmax_device(h, h->probs, len, host_idx, host_p, sums, nsums);
 }
 
 sv_status sv_sample(sv_handle h, uint64_t qubit_mask, const double *host_u, size_t shots,

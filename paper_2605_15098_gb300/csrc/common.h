@@ -130,9 +130,16 @@ sv_status cost_predict(sv_cost_model_s *m, const float *host_x, size_t count, fl
 // ---- read-out (measure.cu) ----------------------------------------------------
 // Marginal over physical positions pos[0..m-1] (output bit j <-> pos[j]),
 // renormalised, into device buffer dev_out (2^m doubles), on h->stream.
-sv_status marginal_device(sv_state *h, const int *pos, int m, double *dev_out);
+// normalise = false leaves the sums unnormalised and returns the block sums
+// whose ordered total is the normaliser (sums_out / nsums_out may be NULL).
+sv_status marginal_device(sv_state *h, const int *pos, int m, double *dev_out,
+                          bool normalise = true, const double **sums_out = nullptr,
+                          int *nsums_out = nullptr);
+// Lowest index of the maximum of dev_p; with sums given, dev_p is unnormalised
+// and *host_p is max / total.
 sv_status argmax_device(sv_state *h, const double *dev_p, uint64_t len,
-                        uint64_t *host_idx, double *host_p);
+                        uint64_t *host_idx, double *host_p, const double *sums = nullptr,
+                        int nsums = 0);
 sv_status sample_device(sv_state *h, const double *dev_p, uint64_t len,
                         const double *host_u, size_t shots, uint64_t *host_out);
 

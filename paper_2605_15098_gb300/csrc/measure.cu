@@ -40,11 +40,42 @@ __device__ __forceinline__ uint64_t pdep_mask(uint64_t v, uint64_t mask) {
     return r;
 }
 
+// Running sum of |amp|^2.  complex128: FP64.  complex64: the squares of the
+// FP32 components are formed exactly (product plus fmaf remainder) and added
+// with error-free FP32 sums into a (hi, lo) pair, converted to FP64 once per
+// thread: the result is the FP64-rounded exact sum to within about 2^-44
+// relative, at FP32 instruction cost (GB300 issues FP64 at 1/64 of FP32).
 template <typename R>
-__device__ __forceinline__ double prob_at(const R *s, uint64_t x) {
-    double re = (double)s[2 * x], im = (double)s[2 * x + 1];
-    return re * re + im * im;
-}
+struct ProbAcc;
+
+template <>
+struct ProbAcc<double> {
+    double acc = 0.0;
+    __device__ void add(const double *s, uint64_t x) {
+        const double re = s[2 * x], im = s[2 * x + 1];
+        acc += re * re + im * im;
+    }
+    __device__ double value() const { return acc; }
+};
+
+template <>
+struct ProbAcc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ void two_sum(float b) {
+        const float t = hi + b;
+        const float bb = t - hi;
+        lo += (hi - (t - bb)) + (b - bb);
+        hi = t;
+    }
+    __device__ void add(const float *s, uint64_t x) {
+        const float2 v = reinterpret_cast<const float2 *>(s)[x];
+        const float pr = v.x * v.x, pi = v.y * v.y;
+        lo += fmaf(v.x, v.x, -pr) + fmaf(v.y, v.y, -pi);
+        two_sum(pr);
+        two_sum(pi);
+    }
+    __device__ double value() const { return (double)hi + (double)lo; }
+};
 
 // Layout M: outcome bit 0 is physical bit 0, so consecutive threads (consecutive
 // physical-order outcomes) read neighbouring amplitudes.
@@ -64,12 +95,12 @@ k_marg_m(const R *__restrict__ s, MargArgs a, double *__restrict__ partial) {
         }
     }
     uint64_t xr = pdep_mask(g * a.per_group, a.rest);
-    double acc = 0.0;
+    ProbAcc<R> acc;
     for (uint64_t i = 0; i < a.per_group; i++) {
-        acc += prob_at(s, xm | xr);
+        acc.add(s, xm | xr);
         xr = ((xr | ~a.rest) + 1) & a.rest;
     }
-    partial[g * outcomes + ml] = acc;
+    partial[g * outcomes + ml] = acc.value();
 }
 
 // Layout R: the lowest physical bits are summed over; one warp per
@@ -93,11 +124,12 @@ k_marg_r(const R *__restrict__ s, MargArgs a, double *__restrict__ partial) {
     const uint64_t lane_bits = a.rest & ~a.upper;
     const uint64_t xl = pdep_mask((uint64_t)lane, lane_bits);
     uint64_t xo = pdep_mask(g * a.per_group, a.upper);
-    double acc = 0.0;
+    ProbAcc<R> pa;
     for (uint64_t i = 0; i < a.per_group; i++) {
-        acc += prob_at(s, xm | xo | xl);
+        pa.add(s, xm | xo | xl);
         xo = ((xo | ~a.upper) + 1) & a.upper;
     }
+    double acc = pa.value();
 #pragma unroll
     for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     if (lane == 0) partial[g * outcomes + ml] = acc;
@@ -142,6 +174,13 @@ __global__ void k_normalise(double *__restrict__ p, uint64_t len, const double *
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride)
         p[i] = p[i] / t;
+}
+
+// v[0] /= total, the total summed over the block sums in order (as k_normalise does).
+__global__ void k_div_total(double *v, const double *__restrict__ sums, int nsums) {
+    double t = 0.0;
+    for (int i = 0; i < nsums; i++) t += sums[i];
+    v[0] = v[0] / t;
 }
 
 // argmax: (value, lowest index) per block, then one block over the partials.
@@ -274,7 +313,8 @@ sv_status ensure_probs(sv_state *h, size_t bytes) {
 }
 
 // pos[j]: physical bit of output bit j.
-sv_status marginal_device(sv_state *h, const int *pos, int m, double *dev_out) {
+sv_status marginal_device(sv_state *h, const int *pos, int m, double *dev_out, bool normalise,
+                          const double **sums_out, int *nsums_out) {
     const int n = h->n;
     MargArgs a{};
     a.n = n;
@@ -345,6 +385,9 @@ sv_status marginal_device(sv_state *h, const int *pos, int m, double *dev_out) {
     k_block_sum<<<nsum_blocks, kRedThreads, 0, h->stream>>>(dev_out, outcomes, sums);
     SV_CUDA(cudaGetLastError());
     note_launch();
+    if (sums_out) *sums_out = sums;
+    if (nsums_out) *nsums_out = nsum_blocks;
+    if (!normalise) return SV_OK;
     k_normalise<<<std::min<unsigned>(blocks_for(outcomes, kRedThreads), 4096), kRedThreads, 0,
                   h->stream>>>(dev_out, outcomes, sums, nsum_blocks);
     SV_CUDA(cudaGetLastError());
@@ -353,7 +396,7 @@ sv_status marginal_device(sv_state *h, const int *pos, int m, double *dev_out) {
 }
 
 sv_status argmax_device(sv_state *h, const double *dev_p, uint64_t len, uint64_t *host_idx,
-                        double *host_p) {
+                        double *host_p, const double *sums, int nsums) {
     const int nb = (int)std::min<uint64_t>(1024, blocks_for(len, kRedThreads));
     char *base = reinterpret_cast<char *>(h->small);
     double *bv = reinterpret_cast<double *>(base);
@@ -366,6 +409,11 @@ sv_status argmax_device(sv_state *h, const double *dev_p, uint64_t len, uint64_t
     k_argmax<<<1, kRedThreads, 0, h->stream>>>(bv, bi, (uint64_t)nb, fv, fi);
     SV_CUDA(cudaGetLastError());
     note_launch();
+    if (sums) {  // unnormalised marginal: p = max / total, the total in the normalisation's order
+        k_div_total<<<1, 1, 0, h->stream>>>(fv, sums, nsums);
+        SV_CUDA(cudaGetLastError());
+        note_launch();
+    }
     double v;
     uint64_t i;
     SV_CUDA(cudaMemcpyAsync(&v, fv, sizeof v, cudaMemcpyDeviceToHost, h->stream));
