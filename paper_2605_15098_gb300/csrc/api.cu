@@ -118,6 +118,7 @@ sv_status sv_destroy(sv_handle h) {
     if (h->plan_host) cudaFreeHost(h->plan_host);
     if (h->t2_tables) cudaFree(h->t2_tables);
     if (h->t3_tables) cudaFree(h->t3_tables);
+    if (h->tab64) cudaFree(h->tab64);
     if (h->norm_buf) cudaFree(h->norm_buf);
     for (auto &p : h->pending) {
         cudaEventDestroy(p.e0);

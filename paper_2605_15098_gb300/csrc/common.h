@@ -75,6 +75,7 @@ struct sv_state {
     void *t2_tables = nullptr;    // FP64-generated phase tables (register-stage kernel)
     int *t2_err = nullptr;        // device flag: a bounded wait gave up
     void *t3_tables = nullptr;    // FP64-generated 8-bit phase tables (fused kernel)
+    void *tab64 = nullptr;        // FP64 phase tables of the complex128 tile kernel (12 MiB)
     double *norm_buf = nullptr;   // per-CTA squared norms of fused passes (2 x 256)
     bool norm_pending = false;    // the state still needs the last fused pass's norm correction
     int norm_idx = 0, norm_cnt = 0;

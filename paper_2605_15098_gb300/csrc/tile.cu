@@ -28,7 +28,15 @@ struct PassArgs {
     uint64_t ntiles;
     const TileOp *ops;
     const PhaseTerm *terms;
+    const double2 *tab64;  // complex128: phase tables (see k_phase_tables64)
+    double hscale;         // complex128: 2^(-h/2) for the pass's h unnormalised Hadamards
 };
+
+// complex128 phases: e^{2 pi i phi / 2^64} = T0[phi >> 46] T1[(phi >> 28) & m] T2[(phi >> 10) & m]
+// with T0[j] = e^{2 pi i j / 2^18}, T1[j] = e^{2 pi i j / 2^36}, T2[j] = e^{2 pi i j / 2^54}
+// (the 10 lowest bits, under 2^-54 of a turn, are dropped), each entry from FP64 sincospi.
+constexpr int kTab64Bits = 18;
+constexpr int kTab64 = 1 << kTab64Bits;
 
 __device__ __forceinline__ uint64_t pdep64(uint64_t v, uint64_t mask) {
     uint64_t r = 0;
@@ -57,6 +65,25 @@ __device__ __forceinline__ void phase_cs<double>(uint64_t phi, double *c, double
     // e^{2 pi i phi / 2^64} = cos/sin(pi x) with x = phi / 2^63 in [-1, 1)
     const double x = (double)(int64_t)phi * 0x1p-63;
     sincospi(x, s, c);
+}
+
+__device__ __forceinline__ double2 phase_tab64(const double2 *__restrict__ t, uint64_t phi) {
+    constexpr uint64_t m = kTab64 - 1;
+    const double2 a = __ldg(t + (phi >> 46));
+    const double2 b = __ldg(t + kTab64 + ((phi >> 28) & m));
+    const double2 c = __ldg(t + 2 * kTab64 + ((phi >> 10) & m));
+    const double2 ab = make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return make_double2(ab.x * c.x - ab.y * c.y, ab.x * c.y + ab.y * c.x);
+}
+
+__global__ void k_phase_tables64(double2 *t) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * kTab64) return;
+    const int lvl = i / kTab64, j = i % kTab64;
+    const double x = (double)j * (lvl == 0 ? 0x1p-18 : lvl == 1 ? 0x1p-36 : 0x1p-54);
+    double s, c;
+    sincospi(2.0 * x, &s, &c);
+    t[i] = make_double2(c, s);
 }
 
 template <>
@@ -143,7 +170,13 @@ k_tile(R *__restrict__ state, const PassArgs a) {
                     }
                     if (phi) {
                         R c, s;
-                        phase_cs<R>(phi, &c, &s);
+                        if constexpr (sizeof(R) == 8) {
+                            const double2 f = phase_tab64(a.tab64, phi);
+                            c = f.x;
+                            s = f.y;
+                        } else {
+                            phase_cs<R>(phi, &c, &s);
+                        }
                         const R re = sm[2 * i], im = sm[2 * i + 1];
                         sm[2 * i] = re * c - im * s;
                         sm[2 * i + 1] = re * s + im * c;
@@ -187,8 +220,13 @@ k_tile(R *__restrict__ state, const PassArgs a) {
                     if (type == TOP_X) {
                         xr = br; xi = bi; yr = ar; yi = ai;
                     } else if (type == TOP_H) {
-                        xr = hscale<R>(ar + br); xi = hscale<R>(ai + bi);
-                        yr = hscale<R>(ar - br); yi = hscale<R>(ai - bi);
+                        if constexpr (sizeof(R) == 8) {  // unnormalised; scaled once at the end
+                            xr = ar + br; xi = ai + bi;
+                            yr = ar - br; yi = ai - bi;
+                        } else {
+                            xr = hscale<R>(ar + br); xi = hscale<R>(ai + bi);
+                            yr = hscale<R>(ar - br); yi = hscale<R>(ai - bi);
+                        }
                     } else {
                         xr = m0r * ar - m0i * ai + m1r * br - m1i * bi;
                         xi = m0r * ai + m0i * ar + m1r * bi + m1i * br;
@@ -205,7 +243,14 @@ k_tile(R *__restrict__ state, const PassArgs a) {
         for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x) {
             const uint32_t i = v * APV;
             const uint64_t g = base + chunk_offset(a, i >> a.c) + (i & cmask);
-            gv[g / APV] = svec[v];
+            V val = svec[v];
+            if constexpr (sizeof(R) == 8) {
+                if (a.hscale != 1.0) {
+                    val.x *= a.hscale;
+                    val.y *= a.hscale;
+                }
+            }
+            gv[g / APV] = val;
         }
         __syncthreads();
     }
@@ -262,6 +307,20 @@ struct PassUpload {
 };
 
 }  // namespace
+
+static sv_status tab64_prepare(sv_state *h) {
+    if (h->tab64) return SV_OK;
+    void *p = nullptr;
+    if (cudaMalloc(&p, (size_t)3 * kTab64 * sizeof(double2)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SV_ERR_OOM, "cannot allocate complex128 phase tables");
+    }
+    h->tab64 = p;
+    k_phase_tables64<<<(3 * kTab64 + 255) / 256, 256, 0, h->stream>>>(reinterpret_cast<double2 *>(p));
+    SV_CUDA(cudaGetLastError());
+    note_launch();
+    return SV_OK;
+}
 
 sv_status check_device_flag(sv_state *h) {
     if (!h->t2_err) return SV_OK;
@@ -414,6 +473,14 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
             a.ntiles = UINT64_C(1) << (h->n - p.k);
             a.ops = reinterpret_cast<const TileOp *>(dev + up[i].ops);
             a.terms = reinterpret_cast<const PhaseTerm *>(dev + up[i].terms);
+            a.hscale = 1.0;
+            if (dbl) {
+                int nh = 0;
+                for (const TileOp &op : p.ops) nh += op.type == TOP_H;
+                a.hscale = std::pow(2.0, -0.5 * nh);
+                SV_TRY(tab64_prepare(h));
+                a.tab64 = reinterpret_cast<const double2 *>(h->tab64);
+            }
             st = dbl ? launch_pass<double>(h, a, meta) : launch_pass<float>(h, a, meta);
         }
         if (st != SV_OK) return st;
