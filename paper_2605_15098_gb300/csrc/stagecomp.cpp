@@ -356,6 +356,26 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
         auto add_thread_factor = [&](int mask, bool cst, int lin_reg, int dmask,
                                      const uint32_t *row) {
             T2Factor f{};
+            // a static row theta * (bit t of the thread) is a constant factor
+            // that only the threads with bit t set apply: no table lookups
+            if (!cst && lin_reg < 0 && dmask == 0) {
+                for (int t = 0; t < 8; t++) {
+                    const uint32_t th = row[1 << t];
+                    if (!th) continue;
+                    bool single = true;
+                    for (int tau = 0; tau < 256 && single; tau++)
+                        single = row[tau] == (((tau >> t) & 1) ? th : 0u);
+                    if (!single) break;
+                    const uint32_t w0 = (uint32_t)mask | ((uint32_t)(t + 1) << 10);
+                    std::memcpy(&f.w0, &w0, sizeof w0);
+                    f.run = r;
+                    const double ang = 2.0 * M_PI * ((double)(int32_t)th * 0x1p-32);
+                    f.c0 = (float)std::cos(ang);
+                    f.c1 = (float)std::sin(ang);
+                    out->factors.push_back(f);
+                    return;
+                }
+            }
             const uint32_t w0 = (uint32_t)mask | (1u << 8) | (cst ? (1u << 9) : 0u) |
                                 ((uint32_t)(lin_reg + 1) << 16) | ((uint32_t)dmask << 24);
             std::memcpy(&f.w0, &w0, sizeof w0);

@@ -147,7 +147,13 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
                 }
                 const uint32_t w0 = (uint32_t)fd.x;
                 const int run = fd.y;
+                const int pb = (int)((w0 >> 10) & 0xfu);  // thread-bit predicate of a constant
                 float fr, fi;
+                if (pb && !((tid >> (pb - 1)) & 1)) {  // not this thread's factor
+                    fd = fdn;
+                    sv = svn;
+                    continue;
+                }
                 if (!(w0 & 0x100u)) {
                     fr = __int_as_float(fd.z);
                     fi = __int_as_float(fd.w);

@@ -436,6 +436,8 @@ __global__ void __launch_bounds__(kT2Threads, 1) k_tile3(float *__restrict__ sta
                     const int run = fd.y;
                     float fr, fi;
                     if (!(w0 & 0x100u)) {
+                        const int pb = (int)((w0 >> 10) & 0xfu);  // thread-bit predicate
+                        if (pb && !((tid >> (pb - 1)) & 1)) continue;
                         fr = __int_as_float(fd.z);
                         fi = __int_as_float(fd.w);
                     } else {

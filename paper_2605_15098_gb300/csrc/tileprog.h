@@ -78,6 +78,8 @@ struct T2Mat {
 //   w0 bits 0..7:   register-bit mask the amplitude must have set (popcount <= 2)
 //   w0 bit 8:       1 = per-thread phase, 0 = constant (c0, c1)
 //   w0 bit 9:       phase += cst[run] (the tile's global-only part)
+//   w0 bits 10..13: constant factors only: 1 + thread bit t; only threads with
+//                   bit t set apply the factor (0 = every thread)
 //   w0 bits 16..23: 1 + tile bit whose per-tile coefficient lin[run][tb] is added, 0 = none
 //   w0 bits 24..31: thread bits t whose per-tile coefficient lin[run][tile bit of t] is added
 //                   when thread bit t is set

@@ -171,6 +171,9 @@ def run_t2_pass(state, p):
                             sel &= ((loc >> reg[j]) & 1) == 1
                     if not (w0 >> 8) & 1:
                         fac = np.full(t.size, f["c"][0] + 1j * f["c"][1])
+                        pb = (w0 >> 10) & 0xF
+                        if pb:
+                            sel &= ((tid >> (pb - 1)) & 1) == 1
                     else:
                         run = f["run"]
                         u = stat[f["row"] * 256 + tid].copy()
