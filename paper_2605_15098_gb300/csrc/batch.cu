@@ -163,7 +163,7 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
     Blob blob;
     std::vector<BatchInst> inst(count);
     std::vector<T2Args> pass;
-    struct Off { size_t ins, stages, mats, fac, stat, tterms; };
+    struct Off { size_t ins, stages, mats, fac, stat, tterms, layx, epi; };
     std::vector<Off> offs;
     std::vector<double> cost(count);
     uint64_t amps = 0;
@@ -193,6 +193,8 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
             Off o;
             o.ins = blob.put(t2.ins.data(), t2.ins.size() * sizeof(T2Ins));
             o.stages = blob.put(t2.stages.data(), t2.stages.size() * sizeof(T2Stage));
+            o.layx = blob.put(t2.layx.data(), t2.layx.size() * sizeof(T2LayoutX));
+            o.epi = blob.put(&t2.epi, sizeof(T2Epilogue));
             o.mats = blob.put(t2.mats.data(), t2.mats.size() * sizeof(T2Mat));
             o.fac = blob.put(t2.factors.data(), t2.factors.size() * sizeof(T2Factor));
             o.stat = blob.put(t2.stat.data(), t2.stat.size() * sizeof(uint32_t));
@@ -228,6 +230,8 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
     for (size_t p = 0; p < pass.size(); p++) {
         pass[p].ins = reinterpret_cast<const int4 *>(dev + offs[p].ins);
         pass[p].stages = reinterpret_cast<const int4 *>(dev + offs[p].stages);
+        pass[p].layx = reinterpret_cast<const T2LayoutX *>(dev + offs[p].layx);
+        pass[p].epi = reinterpret_cast<const T2Epilogue *>(dev + offs[p].epi);
         pass[p].mats = reinterpret_cast<const float4 *>(dev + offs[p].mats);
         pass[p].fac = reinterpret_cast<const int4 *>(dev + offs[p].fac);
         pass[p].stat = reinterpret_cast<const uint32_t *>(dev + offs[p].stat);

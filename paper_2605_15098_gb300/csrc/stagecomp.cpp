@@ -452,6 +452,36 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
     }
     for (size_t i = 0; i < out->ins.size(); i++)
         if (out->ins[i].op == T2_STAGE) out->last_stage = (int)i;
+    // kernel-side layouts and the write-back offsets of the final layout
+    out->layx.resize(out->stages.size());
+    for (size_t si = 0; si < out->stages.size(); si++) {
+        const T2Stage &st = out->stages[si];
+        T2LayoutX &x = out->layx[si];
+        for (int v = 0; v < 16; v++) {
+            int lo = 0, hi = 0;
+            for (int t = 0; t < 4; t++) {
+                if ((v >> t) & 1) lo += 1 << st.tb[5 + t];
+                if ((v >> t) & 1) hi += 1 << st.tb[9 + t];
+            }
+            x.lo[v] = (uint16_t)lo;
+            x.hi[v] = (uint16_t)hi;
+        }
+        for (int j = 0; j < 4; j++) x.s[j] = 1 << st.tb[1 + j];
+    }
+    if (out->last_stage >= 0) {
+        const T2Stage &st = out->stages[out->ins[out->last_stage].aux];
+        auto w = [&](int tb) { return UINT64_C(1) << tp.slot_phys[tb]; };
+        for (int v = 0; v < 16; v++) {
+            uint64_t lo = 0, hi = 0;
+            for (int t = 0; t < 4; t++) {
+                if ((v >> t) & 1) lo += w(st.tb[5 + t]);
+                if ((v >> t) & 1) hi += w(st.tb[9 + t]);
+            }
+            out->epi.glo[v] = lo;
+            out->epi.ghi[v] = hi;
+        }
+        for (int j = 0; j < 4; j++) out->epi.g[j] = w(st.tb[1 + j]);
+    }
     if (out->n_h || fused) {  // fused passes always end with a scale (norm correction)
         const double s = std::pow(2.0, -0.5 * out->n_h);
         const float hi = (float)s;

@@ -21,6 +21,8 @@ struct T2Pass {
     int last_stage = -1;            // index in `ins` of the last T2_STAGE
     std::vector<T2Ins> ins;
     std::vector<T2Stage> stages;
+    std::vector<T2LayoutX> layx;    // per stage, the kernel-side layout
+    T2Epilogue epi{};               // write-back offsets of the final layout
     std::vector<T2Mat> mats;
     std::vector<T2Factor> factors;
     std::vector<uint32_t> stat;     // per-thread static phases: row r is stat[r*256 .. r*256+255]
@@ -39,6 +41,8 @@ struct T2Device {
     const uint32_t *stat;
     const T2TileTerm *tterms;
     const float *blocks;
+    const T2LayoutX *layx;
+    const T2Epilogue *epi;
 };
 
 // Launch parameters of one register-stage pass (device pointers).
@@ -55,6 +59,8 @@ struct T2Args {
     const T2TileTerm *tterms;
     const float2 *tables;
     int *err;
+    const T2LayoutX *layx;  // per stage (register-stage kernel)
+    const T2Epilogue *epi;  // write-back offsets (register-stage kernel)
 };
 
 // One instance of a batch: its state, passes and read-out qubits.

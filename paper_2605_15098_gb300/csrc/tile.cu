@@ -304,6 +304,7 @@ struct PassUpload {
     size_t blocks = 0;
     size_t ops = 0, terms = 0;                                  // generic kernel
     size_t ins = 0, stages = 0, mats = 0, fac = 0, stat = 0, tterms = 0;  // register-stage kernel
+    size_t layx = 0, epi = 0;
 };
 
 }  // namespace
@@ -403,6 +404,8 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
             up[i].t2 = true;
             up[i].ins = blob.put_vec(t2[i].ins);
             up[i].stages = blob.put_vec(t2[i].stages);
+            up[i].layx = blob.put_vec(t2[i].layx);
+            up[i].epi = blob.put(&t2[i].epi, sizeof(T2Epilogue));
             up[i].mats = blob.put_vec(t2[i].mats);
             up[i].fac = blob.put_vec(t2[i].factors);
             up[i].stat = blob.put_vec(t2[i].stat);
@@ -457,6 +460,8 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
             T2Device d;
             d.ins = reinterpret_cast<const T2Ins *>(dev + up[i].ins);
             d.stages = reinterpret_cast<const T2Stage *>(dev + up[i].stages);
+            d.layx = reinterpret_cast<const T2LayoutX *>(dev + up[i].layx);
+            d.epi = reinterpret_cast<const T2Epilogue *>(dev + up[i].epi);
             d.mats = reinterpret_cast<const T2Mat *>(dev + up[i].mats);
             d.fac = reinterpret_cast<const T2Factor *>(dev + up[i].fac);
             d.stat = reinterpret_cast<const uint32_t *>(dev + up[i].stat);

@@ -53,22 +53,17 @@ struct NoHook {
 extern __shared__ __align__(1024) unsigned char t2_dyn_smem[];
 __shared__ uint64_t t2_tile_base;  // physical index of the current tile's amplitude 0
 
-// Float4 index (amplitude pair) of packed pair q in the layout of stage
-// record st, for thread tid.
+// Float4 index (amplitude pair) of packed pair q in a stage layout, for
+// thread tid, from the host-computed layout record.
 struct Layout2 {
     int bt, s1, s2, s3, s4;
-    __device__ Layout2(const int4 &st, int tid) {
-        auto tb = [&](int i) {
-            const int word = i < 4 ? st.x : i < 8 ? st.y : i < 12 ? st.z : st.w;
-            return (word >> (8 * (i & 3))) & 0xff;
-        };
-        bt = 0;
-#pragma unroll
-        for (int t = 0; t < 8; t++) bt |= ((tid >> t) & 1) << tb(5 + t);
-        s1 = 1 << tb(1);
-        s2 = 1 << tb(2);
-        s3 = 1 << tb(3);
-        s4 = 1 << tb(4);
+    __device__ Layout2(const T2LayoutX *x, int tid) {
+        bt = (int)__ldg(&x->lo[tid & 15]) + (int)__ldg(&x->hi[tid >> 4]);
+        const int4 sv = __ldg(reinterpret_cast<const int4 *>(x->s));
+        s1 = sv.x;
+        s2 = sv.y;
+        s3 = sv.z;
+        s4 = sv.w;
     }
     __device__ int idx(int q) const {
         return (bt + ((q & 1) ? s1 : 0) + ((q & 2) ? s2 : 0) + ((q & 4) ? s3 : 0) +
@@ -92,7 +87,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
         const int op = w.x & 0xff;
         if (op == T2_STAGE) {
             if (live) {
-                const Layout2 L(__ldg(a.stages + stage), tid);
+                const Layout2 L(a.layx + stage, tid);
 #pragma unroll
                 for (int q = 0; q < kNP; q++)
                     tile4[L.idx(q)] = make_float4(r.re[q].x, r.re[q].y, r.im[q].x, r.im[q].y);
@@ -100,7 +95,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
             }
             stage = w.w;
             {
-                const Layout2 L(__ldg(a.stages + stage), tid);
+                const Layout2 L(a.layx + stage, tid);
 #pragma unroll
                 for (int q = 0; q < kNP; q++) {
                     const float4 v = tile4[L.idx(q)];
@@ -242,21 +237,11 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
         hook();
     }
     if (!live) return;
-    const int4 st = __ldg(a.stages + stage);
     if constexpr (kDirect) {
-        // global offset (in amplitudes) of the final layout's tile bits
-        auto tb = [&](int i) {
-            const int word = i < 4 ? st.x : i < 8 ? st.y : i < 12 ? st.z : st.w;
-            return (word >> (8 * (i & 3))) & 0xff;
-        };
-        auto gw = [&](int b) -> uint64_t {
-            return b < a.c ? (UINT64_C(1) << b) : (UINT64_C(1) << a.slot_phys[b]);
-        };
-        uint64_t g0 = t2_tile_base;
-#pragma unroll
-        for (int t = 0; t < 8; t++)
-            if ((tid >> t) & 1) g0 += gw(tb(5 + t));
-        const uint64_t g1 = gw(tb(1)), g2 = gw(tb(2)), g3 = gw(tb(3)), g4 = gw(tb(4));
+        const T2Epilogue *E = a.epi;
+        const uint64_t g0 = t2_tile_base + __ldg(&E->glo[tid & 15]) + __ldg(&E->ghi[tid >> 4]);
+        const uint64_t g1 = __ldg(&E->g[0]), g2 = __ldg(&E->g[1]), g3 = __ldg(&E->g[2]),
+                       g4 = __ldg(&E->g[3]);
 #pragma unroll
         for (int q = 0; q < kNP; q++) {
             const uint64_t g = g0 + ((q & 1) ? g1 : 0) + ((q & 2) ? g2 : 0) + ((q & 4) ? g3 : 0) +
@@ -264,7 +249,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
             __stcs(gstate + (g >> 1), make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y));
         }
     } else {
-        const Layout2 L(st, tid);
+        const Layout2 L(a.layx + stage, tid);
 #pragma unroll
         for (int q = 0; q < kNP; q++)
             tile4[L.idx(q)] = make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y);
@@ -552,6 +537,8 @@ sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
     a.tterms = d.tterms;
     a.tables = reinterpret_cast<const float2 *>(h->t2_tables);
     a.err = h->t2_err;
+    a.layx = d.layx;
+    a.epi = d.epi;
     int per_sm = 0;
     SV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile2, kT2Threads, kSmemBytes));
     if (per_sm < 1) return fail(SV_ERR_UNSUPPORTED, "register-stage tile kernel does not fit");

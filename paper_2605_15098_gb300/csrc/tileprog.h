@@ -70,6 +70,24 @@ struct T2Stage {
     int8_t tb[16];
 };
 
+// Kernel-side form of a stage layout, computed on the host: the tile offset
+// (in amplitudes) of thread bits 0..3 (lo, indexed by tid & 15) and 4..7 (hi,
+// indexed by tid >> 4), and of register bits 1..4.  A thread's packed pair q
+// sits at tile offset lo + hi + sum over the set bits j of q of s[j].
+struct T2LayoutX {
+    uint16_t lo[16];
+    uint16_t hi[16];
+    int32_t s[4];
+};
+
+// Write-back offsets of the final layout in the global state (amplitudes),
+// relative to the tile's base: thread bits 0..3, 4..7 and register bits 1..4.
+struct T2Epilogue {
+    uint64_t glo[16];
+    uint64_t ghi[16];
+    uint64_t g[4];
+};
+
 struct T2Mat {
     float m[8];  // U11 re, im, U12 re, im, U21 re, im, U22 re, im
 };
