@@ -147,7 +147,7 @@ typedef struct sv_stats {
 /* ---- lifetime --------------------------------------------------------- */
 
 /* Allocate a state of n qubits (1 <= n <= 34) on the current CUDA device and
- * set it to |0...0>.  The library owns the memory; it uses its own stream.
+ * set it to |0...0> (recorded; see sv_reset).  The library owns the memory; it uses its own stream.
  * Errors: SV_ERR_ARG (n, dt, out), SV_ERR_OOM, SV_ERR_CUDA. */
 sv_status sv_create(int n, sv_dtype dt, sv_handle *out);
 
@@ -161,11 +161,19 @@ sv_status sv_create_on(int n, sv_dtype dt, void *dev_buf, size_t bytes,
 /* Free the handle (and the state, if owned).  NULL is accepted. */
 sv_status sv_destroy(sv_handle h);
 
-/* Set the state to |0...0> and the qubit map to the identity. */
+/* Set the state to |0...0> and the qubit map to the identity.  The library
+ * only records the basis state (as it does at creation): the buffer is
+ * written by the first call that needs it.  Until then, sv_apply_circuit
+ * drops X gates whose qubit no earlier gate of the list touches (they only
+ * flip a bit of the recorded basis index) and its first register-stage pass
+ * generates the state instead of reading the buffer.  sv_info with dev_amps,
+ * the read-outs and sv_copy_out write the buffer first, so a caller who
+ * reads an adopted buffer directly calls sv_info before doing so. */
 sv_status sv_reset(sv_handle h);
 
 /* Number of qubits, dtype, and device address of the state buffer.  The
- * buffer holds amplitudes in PHYSICAL order; see sv_qubit_map. */
+ * buffer holds amplitudes in PHYSICAL order; see sv_qubit_map.  Asking for
+ * dev_amps writes a recorded basis state into the buffer (see sv_reset). */
 sv_status sv_info(sv_handle h, int *n, sv_dtype *dt, void **dev_amps);
 
 /* Physical bit position of each logical qubit (array of n ints).  SWAP gates
@@ -459,7 +467,9 @@ sv_status sv_planner_judge(sv_handle h, const sv_gate *host_gates, size_t m,
  * register-stage programme or the reason the generic tile kernel is used.
  * Host only: it plans but calls no CUDA function.  Writes at most cap bytes
  * (NUL-terminated) to host_buf and the full length to *len.  The planner is
- * the paper's partitioning (Sec. III-B); the format is this library's. */
+ * the paper's partitioning (Sec. III-B); the format is this library's.
+ * The list is planned as given: the X gates sv_apply_circuit drops from a
+ * recorded basis state (see sv_reset) are planned like other gates. */
 sv_status sv_plan_export(int n, sv_dtype dt, const int *host_phys_of_logical,
                          const sv_gate *host_gates, size_t m, const sv_config *cfg,
                          char *host_buf, size_t cap, size_t *len);

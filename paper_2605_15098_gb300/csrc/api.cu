@@ -95,6 +95,26 @@ sv_status read_marginal(sv_state *h, uint64_t mask, uint64_t *len) {
 
 }  // namespace
 
+// While the state is a recorded basis state |b>, an X gate whose qubit no
+// earlier gate of the list touches commutes to the front of the list and
+// only flips a bit of b: drop it and update b.
+void sv::fold_basis_prefix(sv_state *h, std::vector<sv_gate> &g) {
+    if (h->basis < 0) return;
+    bool touched[64] = {};
+    std::vector<sv_gate> out;
+    out.reserve(g.size());
+    for (const sv_gate &a : g) {
+        if (a.kind == SV_X && !touched[a.target]) {
+            h->basis ^= (int64_t)1 << h->phys[a.target];
+            continue;
+        }
+        touched[a.target] = true;
+        if (is_controlled_kind(a.kind) || a.kind == SV_SWAP) touched[a.control] = true;
+        out.push_back(a);
+    }
+    g.swap(out);
+}
+
 extern "C" {
 
 sv_status sv_create(int n, sv_dtype dt, sv_handle *out) {
@@ -142,7 +162,10 @@ sv_status sv_info(sv_handle h, int *n, sv_dtype *dt, void **dev_amps) {
     if (!h) return fail(SV_ERR_ARG, "handle is NULL");
     if (n) *n = h->n;
     if (dt) *dt = h->dt;
-    if (dev_amps) *dev_amps = h->amps;
+    if (dev_amps) {  // the caller may read the buffer: it must hold the state
+        SV_TRY(materialize(h));
+        *dev_amps = h->amps;
+    }
     return SV_OK;
 }
 
@@ -189,6 +212,7 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *host_gates, size_t m, con
         }
     } else {
         std::vector<sv_gate> gl(host_gates, host_gates + m);
+        fold_basis_prefix(h, gl);
         c.mode = mode;
         sv_state::Learned *L = nullptr;
         if (c.planner == SV_PLANNER_LEARNED && h->cost_model) {
@@ -205,7 +229,10 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *host_gates, size_t m, con
             st = partitioned_apply(h, gl, c);
         }
     }
-    h->stats.sweep_bytes = 2.0 * h->stats.passes * (double)state_bytes(h);
+    // per-gate: full-sweep convention (2 x passes x state); partitioned: the
+    // bytes each pass moves (a pass that generates the initial state only writes)
+    h->stats.sweep_bytes = mode == SV_MODE_PERGATE ? 2.0 * h->stats.passes * (double)state_bytes(h)
+                                                   : h->stats.touched_bytes;
     return st;
 }
 
@@ -268,6 +295,7 @@ sv_status sv_sample(sv_handle h, uint64_t qubit_mask, const double *host_u, size
 sv_status sv_copy_out(sv_handle h, void *host_amps) {
     clear_error();
     if (!h || !host_amps) return fail(SV_ERR_ARG, "NULL argument");
+    SV_TRY(materialize(h));
     SV_TRY(resolve_norm(h));
     SV_TRY(remap_to_identity(h));
     SV_CUDA(cudaMemcpyAsync(host_amps, h->amps, state_bytes(h), cudaMemcpyDeviceToHost, h->stream));
@@ -282,6 +310,7 @@ sv_status sv_copy_in(sv_handle h, const void *host_amps) {
     SV_CUDA(cudaStreamSynchronize(h->stream));
     for (int q = 0; q < 64; q++) h->phys[q] = q;
     h->norm_pending = false;
+    h->basis = -1;
     return SV_OK;
 }
 

@@ -62,6 +62,9 @@ struct sv_state {
     int device = 0;
     int sm_count = 0;
     int phys[64];                 // physical bit of each logical qubit
+    // >= 0: the state is the basis state |basis> (physical index) and the
+    // buffer may still hold old data; -1: the buffer holds the state
+    int64_t basis = -1;
     void *scratch = nullptr;      // device scratch, grown on demand
     size_t scratch_cap = 0;
     double *probs = nullptr;      // device marginal of the last read-out
@@ -115,8 +118,12 @@ void prof_end(sv_state *h, int slot, const sv_launch_record &meta);
 // ---- per-gate path (pergate.cu) ---------------------------------------------
 // Apply one gate whose qubits are already PHYSICAL positions.
 sv_status pergate_apply(sv_state *h, const sv_gate &g_phys);
-// Set the state to |0...0>.
+// Set the state to |0...0> (recorded only; see sv_state::basis).
 sv_status init_zero_state(sv_state *h);
+// Write a recorded basis state into the buffer (no-op when it holds the state).
+sv_status materialize(sv_state *h);
+// Drop the X gates that only flip a bit of a recorded basis state (see api.cu).
+void fold_basis_prefix(sv_state *h, std::vector<sv_gate> &gates);
 
 // ---- remap passes (remap.cu) --------------------------------------------------
 // Exchange the disjoint physical bit pairs of the whole state, in place.
@@ -149,7 +156,10 @@ struct T2Pass;
 struct T2Device;
 size_t t2_smem_bytes();
 sv_status t2_prepare(sv_state *h);
-sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta);
+// gen_basis >= 0: the state is that basis state and the pass generates it
+// instead of reading the buffer.
+sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta,
+                    int64_t gen_basis = -1);
 sv_status t3_prepare(sv_state *h);
 sv_status t3_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta);
 // Multiply the state by the pending norm correction of the last fused pass.

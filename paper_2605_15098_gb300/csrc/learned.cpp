@@ -226,8 +226,10 @@ sv_status time_plan(sv_handle h, const std::vector<sv_gate> &g, const sv_config 
         st = sv_reset(h);
         if (st != SV_OK) break;
         h->stats = sv_stats{};
+        std::vector<sv_gate> gf = g;
+        fold_basis_prefix(h, gf);
         cudaEventRecord(e0, h->stream);
-        st = partitioned_apply(h, g, cfg, ov);
+        st = partitioned_apply(h, gf, cfg, ov);
         cudaEventRecord(e1, h->stream);
         if (st != SV_OK) break;
         if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -275,6 +277,9 @@ sv_status sv_learned_plan(sv_handle h, const sv_gate *host_gates, size_t m, cons
     if (!out) return fail(SV_ERR_ARG, "NULL argument");
     const sv_config c = partitioned_cfg(h, cfg);
     std::vector<sv_gate> g(host_gates, host_gates + m);
+    const int64_t b0 = h->basis;  // the list sv_apply_circuit would plan from this state
+    fold_basis_prefix(h, g);
+    h->basis = b0;
     sv_state::Learned *L = nullptr;
     SV_TRY(learned_entry(h, g, c, &L));
     *out = L->info;
@@ -288,8 +293,12 @@ sv_status sv_planner_judge(sv_handle h, const sv_gate *host_gates, size_t m, con
     const sv_config c = partitioned_cfg(h, cfg);
     std::vector<sv_gate> g(host_gates, host_gates + m);
     SV_TRY(sv_reset(h));
+    std::vector<sv_gate> gf = g;  // the list sv_apply_circuit plans after a reset
+    const int64_t b0 = h->basis;
+    fold_basis_prefix(h, gf);
+    h->basis = b0;
     sv_state::Learned *L = nullptr;
-    SV_TRY(learned_entry(h, g, c, &L));
+    SV_TRY(learned_entry(h, gf, c, &L));
     double tg = 0.0, tl = 0.0;
     SV_TRY(time_plan(h, g, c, nullptr, &tg));
     SV_TRY(time_plan(h, g, c, &L->ov, &tl));

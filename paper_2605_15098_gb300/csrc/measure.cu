@@ -315,6 +315,7 @@ sv_status ensure_probs(sv_state *h, size_t bytes) {
 // pos[j]: physical bit of output bit j.
 sv_status marginal_device(sv_state *h, const int *pos, int m, double *dev_out, bool normalise,
                           const double **sums_out, int *nsums_out) {
+    SV_TRY(materialize(h));
     const int n = h->n;
     MargArgs a{};
     a.n = n;

@@ -177,11 +177,11 @@ k_pergate_intra(float *__restrict__ s, uint64_t units, Fixed fx, Coef<float> c) 
     }
 }
 
-__global__ void k_set_first(void *amps, int is_double) {
+__global__ void k_set_first(void *amps, int is_double, uint64_t index) {
     if (is_double)
-        reinterpret_cast<double *>(amps)[0] = 1.0;
+        reinterpret_cast<double *>(amps)[2 * index] = 1.0;
     else
-        reinterpret_cast<float *>(amps)[0] = 1.0f;
+        reinterpret_cast<float *>(amps)[2 * index] = 1.0f;
 }
 
 unsigned grid_for(uint64_t units) {
@@ -242,16 +242,24 @@ void add_fixed(Fixed &f, int pos, int val) {
 }  // namespace
 
 sv_status init_zero_state(sv_state *h) {
+    for (int q = 0; q < 64; q++) h->phys[q] = q;
+    h->basis = 0;  // |0...0>, written when something first reads the state
+    return SV_OK;
+}
+
+sv_status materialize(sv_state *h) {
+    if (h->basis < 0) return SV_OK;
     SV_CUDA(cudaMemsetAsync(h->amps, 0, state_bytes(h), h->stream));
-    k_set_first<<<1, 1, 0, h->stream>>>(h->amps, h->dt == SV_C128);
+    k_set_first<<<1, 1, 0, h->stream>>>(h->amps, h->dt == SV_C128, (uint64_t)h->basis);
     SV_CUDA(cudaGetLastError());
     note_launch();
-    for (int q = 0; q < 64; q++) h->phys[q] = q;
+    h->basis = -1;
     return SV_OK;
 }
 
 // Apply one gate given in PHYSICAL qubit positions.
 sv_status pergate_apply(sv_state *h, const sv_gate &g) {
+    SV_TRY(materialize(h));
     const int n = h->n;
     int op;
     Mat2 m{};

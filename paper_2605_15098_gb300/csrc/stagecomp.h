@@ -61,6 +61,11 @@ struct T2Args {
     int *err;
     const T2LayoutX *layx;  // per stage (register-stage kernel)
     const T2Epilogue *epi;  // write-back offsets (register-stage kernel)
+    // gen != 0: the state is the basis state |gen_basis> (physical index) and
+    // is generated in registers instead of read; gen_local is its index inside
+    // the tile that holds it
+    int gen, gen_local;
+    uint64_t gen_basis;
 };
 
 // One instance of a batch: its state, passes and read-out qubits.

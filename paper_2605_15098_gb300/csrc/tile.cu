@@ -456,6 +456,17 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
         meta.pass = h->launch_index++;
         sv_status st;
         if (!up[i].t3) SV_TRY(resolve_norm(h));
+        // a recorded basis state: the register-stage kernel generates it in
+        // its first pass; every other kernel needs it written out first
+        int64_t gen = -1;
+        if (h->basis >= 0) {
+            if (up[i].t2 && !up[i].t3) {
+                gen = h->basis;
+                meta.bytes = (double)state_bytes(h);  // written, not read
+            } else {
+                SV_TRY(materialize(h));
+            }
+        }
         if (up[i].t2) {
             T2Device d;
             d.ins = reinterpret_cast<const T2Ins *>(dev + up[i].ins);
@@ -467,7 +478,8 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
             d.stat = reinterpret_cast<const uint32_t *>(dev + up[i].stat);
             d.tterms = reinterpret_cast<const T2TileTerm *>(dev + up[i].tterms);
             d.blocks = up[i].t3 ? reinterpret_cast<const float *>(dev + up[i].blocks) : nullptr;
-            st = up[i].t3 ? t3_launch(h, t2[i], d, meta) : t2_launch(h, t2[i], d, meta);
+            st = up[i].t3 ? t3_launch(h, t2[i], d, meta) : t2_launch(h, t2[i], d, meta, gen);
+            if (st == SV_OK && gen >= 0) h->basis = -1;
         } else {
             PassArgs a{};
             a.k = p.k;
@@ -490,7 +502,7 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
         }
         if (st != SV_OK) return st;
         h->stats.passes++;
-        h->stats.touched_bytes += 2.0 * (double)state_bytes(h);
+        h->stats.touched_bytes += meta.bytes;
     }
     std::copy(phys, phys + 64, h->phys);
     h->stats.relabels = plan.relabels;

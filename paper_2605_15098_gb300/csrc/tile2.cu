@@ -96,15 +96,31 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
             stage = w.w;
             {
                 const Layout2 L(a.layx + stage, tid);
+                if (!live && a.gen) {  // the basis state, generated instead of read
+                    const bool has = (a.gen_basis & a.gmask) == t2_tile_base;
+                    const int lp = a.gen_local >> 1;
 #pragma unroll
-                for (int q = 0; q < kNP; q++) {
-                    const float4 v = tile4[L.idx(q)];
-                    if (live) {
-                        r.re[q] = make_float2(v.x, v.y);
-                        r.im[q] = make_float2(v.z, v.w);
-                    } else {
-                        r.re[q] = make_float2(v.x, v.z);
-                        r.im[q] = make_float2(v.y, v.w);
+                    for (int q = 0; q < kNP; q++) {
+                        r.re[q] = make_float2(0.f, 0.f);
+                        r.im[q] = make_float2(0.f, 0.f);
+                        if (has && L.idx(q) == lp) {
+                            if (a.gen_local & 1)
+                                r.re[q].y = 1.f;
+                            else
+                                r.re[q].x = 1.f;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < kNP; q++) {
+                        const float4 v = tile4[L.idx(q)];
+                        if (live) {
+                            r.re[q] = make_float2(v.x, v.y);
+                            r.im[q] = make_float2(v.z, v.w);
+                        } else {
+                            r.re[q] = make_float2(v.x, v.z);
+                            r.im[q] = make_float2(v.y, v.w);
+                        }
                     }
                 }
             }
@@ -294,7 +310,8 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_tile2(float *__restrict__ sta
         fence_mbar_init();
     }
     __syncthreads();
-    if (tid < 32 && (uint64_t)blockIdx.x < a.ntiles) issue_tile_load(a, sm, state, blockIdx.x, bar, tid);
+    if (!a.gen && tid < 32 && (uint64_t)blockIdx.x < a.ntiles)
+        issue_tile_load(a, sm, state, blockIdx.x, bar, tid);
 
     uint32_t parity = 0;
     for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
@@ -313,14 +330,14 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_tile2(float *__restrict__ sta
             if (t.g1 >= 0) on = on && ((base >> t.g1) & 1);
             if (on) atomicAdd(t.tb >= 0 ? &lin[t.run * 16 + t.tb] : &cst[t.run], t.theta);
         }
-        const bool timed_out = !mbar_wait(bar, parity);
+        const bool timed_out = a.gen ? false : !mbar_wait(bar, parity);
         if (__syncthreads_or(timed_out)) {
             if (tid == 0) atomicExch(a.err, 1);
             mbar_wait(bar, parity);  // give copies still in flight a second bounded wait
             return;
         }
         auto hook = [&]() {
-            if (tid < 32 && next < a.ntiles) issue_tile_load(a, sm, state, next, bar, tid);
+            if (!a.gen && tid < 32 && next < a.ntiles) issue_tile_load(a, sm, state, next, bar, tid);
         };
         t2_run<true>(a, reinterpret_cast<float4 *>(state), hook);
         parity ^= 1u;
@@ -519,8 +536,15 @@ sv_status t2_prepare(sv_state *h) {
     return SV_OK;
 }
 
-sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta) {
+sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta,
+                    int64_t gen_basis) {
     T2Args a{};
+    if (gen_basis >= 0) {
+        a.gen = 1;
+        a.gen_basis = (uint64_t)gen_basis;
+        for (int s = 0; s < p.k; s++)
+            a.gen_local |= (int)((a.gen_basis >> p.slot_phys[s]) & 1) << s;
+    }
     a.gmask = p.gmask;
     a.ntiles = UINT64_C(1) << (h->n - p.k);
     a.c = p.c;

@@ -40,3 +40,19 @@ def mixed_circuit(n, m, seed, kinds=tuple(range(11))):
             j = int(rng.integers(0, 40))
             recs.append(C.cpk(o, t, int(rng.integers(-(1 << 40), 1 << 40)), j))
     return C.gates(recs)
+
+
+def without_leading_x(g):
+    """The gate list the library plans when the state is a recorded basis
+    state: X gates whose qubit no earlier gate touches only flip the basis
+    index and are dropped."""
+    touched, keep = set(), []
+    for r in g:
+        kind, t, c = int(r["kind"]), int(r["target"]), int(r["control"])
+        if kind == C.X and t not in touched:
+            continue
+        touched.add(t)
+        if c >= 0:
+            touched.add(c)
+        keep.append(r)
+    return C.gates(keep) if keep else C.gates([])

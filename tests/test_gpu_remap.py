@@ -8,7 +8,7 @@ tolerances of the parity suite (complex128 1e-12, complex64 fidelity).
 import numpy as np
 import pytest
 
-from gen import mixed_circuit
+from gen import mixed_circuit, without_leading_x
 from paper_2605_15098_gb300 import circuits as C
 
 pytestmark = pytest.mark.gpu
@@ -68,7 +68,7 @@ def test_paper_mode_c128(sv, orc, n, k):
     g = mixed_circuit(n, 160, 3 * n + k)
     ref = orc.run(n, g)
     cfg = sv.make_config(sv.SV_MODE_PARTITIONED, tile_qubits=k, flags=sv.SV_FLAG_PAPER_SWAP)
-    plan = sv.sv_plan_export(n, sv.SV_C128, g, cfg)
+    plan = sv.sv_plan_export(n, sv.SV_C128, without_leading_x(g), cfg)
     with sv.State(n, sv.SV_C128) as s:
         s.apply(g, cfg)
         st = s.stats()
@@ -104,4 +104,4 @@ def test_paper_mode_full_size_qpe(sv):
         st = s.stats()
         idx, p = s.argmax(info["mask"])
     assert idx == info["y"] and abs(p - 1.0) <= 1e-5
-    assert st["remaps"] == sv.sv_plan_export(n, sv.SV_C64, g, cfg)["remaps"]
+    assert st["remaps"] == sv.sv_plan_export(n, sv.SV_C64, without_leading_x(g), cfg)["remaps"]
