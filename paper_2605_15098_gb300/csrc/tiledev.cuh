@@ -201,25 +201,29 @@ __device__ __forceinline__ void reg_u(Regs &r, int jc, const float *m) {
 }
 
 // Uncontrolled gates on register bit J for the register-stage kernel.  `qm`
-// is all ones at run time; testing its bits keeps each packed pair's update
-// a separate block, which bounds how many pairs the compiler keeps in
-// flight (and so the register pressure).
+// is all ones at run time; testing one of its bits per group of four packed
+// pairs keeps each group a separate block, which bounds how many pairs the
+// compiler keeps in flight (and so the register pressure).
 template <int J>
 __device__ __forceinline__ void reg_h2(Regs &r, uint32_t qm) {
 #pragma unroll
-    for (int q = 0; q < kNP; q++) {
-        if (!((qm >> q) & 1)) continue;
-        if constexpr (J >= 1) {
-            constexpr int S = 1 << (J - 1);
-            if (q & S) continue;
-            const int q1 = q | S;
-            const float2 ar = r.re[q], ai = r.im[q], br = r.re[q1], bi = r.im[q1];
-            r.re[q] = add2(ar, br); r.im[q] = add2(ai, bi);
-            r.re[q1] = sub2(ar, br); r.im[q1] = sub2(ai, bi);
-        } else {
-            const float2 a = r.re[q], b = r.im[q];
-            r.re[q] = make_float2(a.x + a.y, a.x - a.y);
-            r.im[q] = make_float2(b.x + b.y, b.x - b.y);
+    for (int g4 = 0; g4 < 4; g4++) {
+        if (!((qm >> g4) & 1)) continue;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int q = 4 * g4 + i;
+            if constexpr (J >= 1) {
+                constexpr int S = 1 << (J - 1);
+                if (q & S) continue;
+                const int q1 = q | S;
+                const float2 ar = r.re[q], ai = r.im[q], br = r.re[q1], bi = r.im[q1];
+                r.re[q] = add2(ar, br); r.im[q] = add2(ai, bi);
+                r.re[q1] = sub2(ar, br); r.im[q1] = sub2(ai, bi);
+            } else {
+                const float2 a = r.re[q], b = r.im[q];
+                r.re[q] = make_float2(a.x + a.y, a.x - a.y);
+                r.im[q] = make_float2(b.x + b.y, b.x - b.y);
+            }
         }
     }
 }
@@ -227,17 +231,21 @@ __device__ __forceinline__ void reg_h2(Regs &r, uint32_t qm) {
 template <int J>
 __device__ __forceinline__ void reg_x2(Regs &r, uint32_t qm) {
 #pragma unroll
-    for (int q = 0; q < kNP; q++) {
-        if (!((qm >> q) & 1)) continue;
-        if constexpr (J >= 1) {
-            constexpr int S = 1 << (J - 1);
-            if (q & S) continue;
-            const int q1 = q | S;
-            float2 t = r.re[q]; r.re[q] = r.re[q1]; r.re[q1] = t;
-            t = r.im[q]; r.im[q] = r.im[q1]; r.im[q1] = t;
-        } else {
-            r.re[q] = make_float2(r.re[q].y, r.re[q].x);
-            r.im[q] = make_float2(r.im[q].y, r.im[q].x);
+    for (int g4 = 0; g4 < 4; g4++) {
+        if (!((qm >> g4) & 1)) continue;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int q = 4 * g4 + i;
+            if constexpr (J >= 1) {
+                constexpr int S = 1 << (J - 1);
+                if (q & S) continue;
+                const int q1 = q | S;
+                float2 t = r.re[q]; r.re[q] = r.re[q1]; r.re[q1] = t;
+                t = r.im[q]; r.im[q] = r.im[q1]; r.im[q1] = t;
+            } else {
+                r.re[q] = make_float2(r.re[q].y, r.re[q].x);
+                r.im[q] = make_float2(r.im[q].y, r.im[q].x);
+            }
         }
     }
 }
@@ -247,23 +255,27 @@ __device__ __forceinline__ void reg_u2(Regs &r, uint32_t qm, const float *m) {
     const float u0r = m[0], u0i = m[1], u1r = m[2], u1i = m[3];
     const float u2r = m[4], u2i = m[5], u3r = m[6], u3i = m[7];
 #pragma unroll
-    for (int q = 0; q < kNP; q++) {
-        if (!((qm >> q) & 1)) continue;
-        if constexpr (J >= 1) {
-            constexpr int S = 1 << (J - 1);
-            if (q & S) continue;
-            const int q1 = q | S;
-            const float2 ar = r.re[q], ai = r.im[q], br = r.re[q1], bi = r.im[q1];
-            r.re[q] = fma2(bi, f2(-u1i), fma2(br, f2(u1r), fma2(ai, f2(-u0i), mul2(ar, f2(u0r)))));
-            r.im[q] = fma2(br, f2(u1i), fma2(bi, f2(u1r), fma2(ar, f2(u0i), mul2(ai, f2(u0r)))));
-            r.re[q1] = fma2(bi, f2(-u3i), fma2(br, f2(u3r), fma2(ai, f2(-u2i), mul2(ar, f2(u2r)))));
-            r.im[q1] = fma2(br, f2(u3i), fma2(bi, f2(u3r), fma2(ar, f2(u2i), mul2(ai, f2(u2r)))));
-        } else {
-            const float ar = r.re[q].x, ai = r.im[q].x, br = r.re[q].y, bi = r.im[q].y;
-            r.re[q].x = u0r * ar - u0i * ai + u1r * br - u1i * bi;
-            r.im[q].x = u0r * ai + u0i * ar + u1r * bi + u1i * br;
-            r.re[q].y = u2r * ar - u2i * ai + u3r * br - u3i * bi;
-            r.im[q].y = u2r * ai + u2i * ar + u3r * bi + u3i * br;
+    for (int g4 = 0; g4 < 4; g4++) {
+        if (!((qm >> g4) & 1)) continue;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int q = 4 * g4 + i;
+            if constexpr (J >= 1) {
+                constexpr int S = 1 << (J - 1);
+                if (q & S) continue;
+                const int q1 = q | S;
+                const float2 ar = r.re[q], ai = r.im[q], br = r.re[q1], bi = r.im[q1];
+                r.re[q] = fma2(bi, f2(-u1i), fma2(br, f2(u1r), fma2(ai, f2(-u0i), mul2(ar, f2(u0r)))));
+                r.im[q] = fma2(br, f2(u1i), fma2(bi, f2(u1r), fma2(ar, f2(u0i), mul2(ai, f2(u0r)))));
+                r.re[q1] = fma2(bi, f2(-u3i), fma2(br, f2(u3r), fma2(ai, f2(-u2i), mul2(ar, f2(u2r)))));
+                r.im[q1] = fma2(br, f2(u3i), fma2(bi, f2(u3r), fma2(ar, f2(u2i), mul2(ai, f2(u2r)))));
+            } else {
+                const float ar = r.re[q].x, ai = r.im[q].x, br = r.re[q].y, bi = r.im[q].y;
+                r.re[q].x = u0r * ar - u0i * ai + u1r * br - u1i * bi;
+                r.im[q].x = u0r * ai + u0i * ar + u1r * bi + u1i * br;
+                r.re[q].y = u2r * ar - u2i * ai + u3r * br - u3i * bi;
+                r.im[q].y = u2r * ai + u2i * ar + u3r * bi + u3i * br;
+            }
         }
     }
 }
@@ -283,25 +295,29 @@ __device__ __forceinline__ void lane_op2(Regs &r, int l, bool pred, uint32_t qm,
     }
     const float sg = hi ? -1.f : 1.f;
 #pragma unroll
-    for (int q = 0; q < kNP; q++) {
-        if (!((qm >> q) & 1)) continue;
-        float2 pr, pi;
-        pr.x = __shfl_xor_sync(FULL, r.re[q].x, xm);
-        pr.y = __shfl_xor_sync(FULL, r.re[q].y, xm);
-        pi.x = __shfl_xor_sync(FULL, r.im[q].x, xm);
-        pi.y = __shfl_xor_sync(FULL, r.im[q].y, xm);
-        if (!pred) continue;
-        if constexpr (OP == T2_H) {
-            r.re[q] = fma2(r.re[q], f2(sg), pr);
-            r.im[q] = fma2(r.im[q], f2(sg), pi);
-        } else if constexpr (OP == T2_X) {
-            r.re[q] = pr;
-            r.im[q] = pi;
-        } else {
-            const float2 nr = fma2(pi, f2(-coi), fma2(pr, f2(cor), fma2(r.im[q], f2(-csi), mul2(r.re[q], f2(csr)))));
-            const float2 ni = fma2(pr, f2(coi), fma2(pi, f2(cor), fma2(r.re[q], f2(csi), mul2(r.im[q], f2(csr)))));
-            r.re[q] = nr;
-            r.im[q] = ni;
+    for (int g4 = 0; g4 < 4; g4++) {
+        if (!((qm >> g4) & 1)) continue;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int q = 4 * g4 + i;
+            float2 pr, pi;
+            pr.x = __shfl_xor_sync(FULL, r.re[q].x, xm);
+            pr.y = __shfl_xor_sync(FULL, r.re[q].y, xm);
+            pi.x = __shfl_xor_sync(FULL, r.im[q].x, xm);
+            pi.y = __shfl_xor_sync(FULL, r.im[q].y, xm);
+            if (!pred) continue;
+            if constexpr (OP == T2_H) {
+                r.re[q] = fma2(r.re[q], f2(sg), pr);
+                r.im[q] = fma2(r.im[q], f2(sg), pi);
+            } else if constexpr (OP == T2_X) {
+                r.re[q] = pr;
+                r.im[q] = pi;
+            } else {
+                const float2 nr = fma2(pi, f2(-coi), fma2(pr, f2(cor), fma2(r.im[q], f2(-csi), mul2(r.re[q], f2(csr)))));
+                const float2 ni = fma2(pr, f2(coi), fma2(pi, f2(cor), fma2(r.re[q], f2(csi), mul2(r.im[q], f2(csr)))));
+                r.re[q] = nr;
+                r.im[q] = ni;
+            }
         }
     }
 }
