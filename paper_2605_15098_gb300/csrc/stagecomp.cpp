@@ -450,6 +450,8 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
         if (!e.empty()) return e;
         if (out->factors.size() > 32000) return "too many factor applications";
     }
+    if (!fused && (out->ins.size() > (size_t)kT2SmemIns || out->factors.size() > (size_t)kT2SmemFactors))
+        return "programme longer than the kernel's shared-memory copy";
     for (size_t i = 0; i < out->ins.size(); i++)
         if (out->ins[i].op == T2_STAGE) out->last_stage = (int)i;
     // kernel-side layouts and the write-back offsets of the final layout

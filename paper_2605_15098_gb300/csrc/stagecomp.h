@@ -49,6 +49,7 @@ struct T2Device {
 struct T2Args {
     uint64_t gmask, ntiles;
     int c, nins, nruns, ntterms;
+    int nfac, nstat;  // factor records, static phase words
     int last_stage;  // index of the last T2_STAGE instruction
     int slot_phys[kMaxTileQubits];
     const int4 *ins;       // T2Ins records

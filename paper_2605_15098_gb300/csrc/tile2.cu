@@ -30,10 +30,14 @@ using namespace tiledev;
 
 constexpr int kTileAmps = 1 << kT2Qubits;
 constexpr uint32_t kTileBytes = kTileAmps * 8u;
-constexpr int kTab0 = 2048, kTab1 = 2048, kTab2 = 1024;
-constexpr int kTabEntries = kTab0 + kTab1 + kTab2;
+constexpr int kTabN = 256;               // four levels of 2^8 entries
+constexpr int kTabEntries = 4 * kTabN;
 constexpr size_t kOffTab = kTileBytes;
-constexpr size_t kOffLin = kOffTab + (size_t)kTabEntries * 8;
+// k_tile2 copies the pass's programme into shared memory once per CTA
+constexpr size_t kOffStat = kOffTab + (size_t)kTabEntries * 8;
+constexpr size_t kOffFac = kOffStat + (size_t)kT2SmemStatRows * 256 * 4;
+constexpr size_t kOffIns = kOffFac + (size_t)kT2SmemFactors * 16;
+constexpr size_t kOffLin = kOffIns + (size_t)kT2SmemIns * 16;
 constexpr size_t kOffCst = kOffLin + (size_t)kT2MaxRuns * 16 * 4;
 constexpr size_t kOffBar = kOffCst + (size_t)kT2MaxRuns * 4;
 constexpr size_t kSmemBytes = kOffBar + 16;
@@ -71,8 +75,13 @@ struct Layout2 {
     }
 };
 
-template <bool kDirect, typename Hook>
+template <bool kDirect, bool kSmemProg, typename Hook>
 __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hook) {
+    // the programme: copied to shared memory by k_tile2, read from global by k_batch
+    const int4 *ins = kSmemProg ? reinterpret_cast<const int4 *>(t2_dyn_smem + kOffIns) : a.ins;
+    const int4 *fac = kSmemProg ? reinterpret_cast<const int4 *>(t2_dyn_smem + kOffFac) : a.fac;
+    const uint32_t *stat =
+        kSmemProg ? reinterpret_cast<const uint32_t *>(t2_dyn_smem + kOffStat) : a.stat;
     float4 *tile4 = reinterpret_cast<float4 *>(t2_dyn_smem);
     const float2 *tab = reinterpret_cast<const float2 *>(t2_dyn_smem + kOffTab);
     const uint32_t *lin = reinterpret_cast<const uint32_t *>(t2_dyn_smem + kOffLin);
@@ -83,7 +92,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
     bool live = false;
     bool hooked = false;
     for (int pc = 0; pc < a.nins; pc++) {
-        const int4 w = __ldg(a.ins + pc);
+        const int4 w = ins[pc];
         const int op = w.x & 0xff;
         if (op == T2_STAGE) {
             if (live) {
@@ -147,14 +156,19 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
             if (e0 >= e1) continue;
             // software pipeline: the next factor's record and static phase
             // load while this one is applied
-            int4 fd = __ldg(a.fac + e0);
-            uint32_t sv = ((uint32_t)fd.x & 0x100u) ? __ldg(a.stat + fd.z * 256 + tid) : 0u;
+            // static phase rows beyond the shared-memory copy stay in global memory
+            auto stat_at = [&](int row) -> uint32_t {
+                if (kSmemProg && row >= kT2SmemStatRows) return __ldg(a.stat + row * 256 + tid);
+                return stat[row * 256 + tid];
+            };
+            int4 fd = fac[e0];
+            uint32_t sv = ((uint32_t)fd.x & 0x100u) ? stat_at(fd.z) : 0u;
             for (int e = e0; e < e1; e++) {
                 int4 fdn = fd;
                 uint32_t svn = 0u;
                 if (e + 1 < e1) {
-                    fdn = __ldg(a.fac + e + 1);
-                    if ((uint32_t)fdn.x & 0x100u) svn = __ldg(a.stat + fdn.z * 256 + tid);
+                    fdn = fac[e + 1];
+                    if ((uint32_t)fdn.x & 0x100u) svn = stat_at(fdn.z);
                 }
                 const uint32_t w0 = (uint32_t)fd.x;
                 const int run = fd.y;
@@ -180,10 +194,9 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
                         const int8_t *tbp = reinterpret_cast<const int8_t *>(a.stages + stage);
                         u += lin[run * 16 + tbp[5 + t]];
                     }
-                    const float2 f0 = tab[u >> 21];
-                    const float2 f1 = tab[kTab0 + ((u >> 10) & 2047u)];
-                    const float2 fz = tab[kTab0 + kTab1 + (u & 1023u)];
-                    const float2 ff = cx(cx(f0, f1), fz);
+                    const float2 ff = cx(cx(tab[u >> 24], tab[kTabN + ((u >> 16) & 255u)]),
+                                         cx(tab[2 * kTabN + ((u >> 8) & 255u)],
+                                            tab[3 * kTabN + (u & 255u)]));
                     fr = ff.x;
                     fi = ff.y;
                 }
@@ -305,6 +318,15 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_tile2(float *__restrict__ sta
     const int tid = threadIdx.x;
 
     for (int i = tid; i < kTabEntries; i += blockDim.x) tab[i] = a.tables[i];
+    {  // the programme, once per CTA (sizes bounded by the stage compiler)
+        int4 *si = reinterpret_cast<int4 *>(sm + kOffIns);
+        int4 *sf = reinterpret_cast<int4 *>(sm + kOffFac);
+        uint32_t *ss = reinterpret_cast<uint32_t *>(sm + kOffStat);
+        for (int i = tid; i < a.nins; i += blockDim.x) si[i] = __ldg(a.ins + i);
+        for (int i = tid; i < a.nfac; i += blockDim.x) sf[i] = __ldg(a.fac + i);
+        const int nst = min(a.nstat, kT2SmemStatRows * 256);
+        for (int i = tid; i < nst; i += blockDim.x) ss[i] = __ldg(a.stat + i);
+    }
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
@@ -339,7 +361,7 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_tile2(float *__restrict__ sta
         auto hook = [&]() {
             if (!a.gen && tid < 32 && next < a.ntiles) issue_tile_load(a, sm, state, next, bar, tid);
         };
-        t2_run<true>(a, reinterpret_cast<float4 *>(state), hook);
+        t2_run<true, true>(a, reinterpret_cast<float4 *>(state), hook);
         parity ^= 1u;
     }
 }
@@ -425,7 +447,7 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
                     mbar_wait(bar, parity ^ 1u);
                     return;
                 }
-                t2_run<false>(a, nullptr, NoHook{});
+                t2_run<false, false>(a, nullptr, NoHook{});
                 fence_async_smem();
                 __syncthreads();
                 if (tid < 32) {
@@ -494,17 +516,12 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
     }
 }
 
-// e^{2 pi i x} for x = j/2^11, j/2^22 (j < 2048) and j/2^32 (j < 1024), FP64 then rounded.
+// e^{2 pi i x} for x = j/2^8, j/2^16, j/2^24, j/2^32 (j < 256): FP64 sincospi, then rounded.
 __global__ void k_phase_tables(float2 *t) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= kTabEntries) return;
-    double x;
-    if (i < kTab0)
-        x = (double)i * 0x1p-11;
-    else if (i < kTab0 + kTab1)
-        x = (double)(i - kTab0) * 0x1p-22;
-    else
-        x = (double)(i - kTab0 - kTab1) * 0x1p-32;
+    const int l = i / kTabN, j = i % kTabN;
+    const double x = (double)j * ldexp(1.0, -8 * (l + 1));
     double s, c;
     sincospi(2.0 * x, &s, &c);
     t[i] = make_float2((float)c, (float)s);
@@ -549,6 +566,8 @@ sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
     a.ntiles = UINT64_C(1) << (h->n - p.k);
     a.c = p.c;
     a.nins = (int)p.ins.size();
+    a.nfac = (int)p.factors.size();
+    a.nstat = (int)p.stat.size();
     a.last_stage = p.last_stage;
     a.nruns = p.nruns;
     a.ntterms = (int)p.tterms.size();

@@ -30,6 +30,10 @@ constexpr int kT2Qubits = 13;   // tile: 2^13 complex64 amplitudes (64 KiB)
 constexpr int kT2Threads = 256; // 8 warps
 constexpr int kT2RegBits = 5;   // 32 amplitudes per thread
 constexpr int kT2MaxRuns = 64;  // diagonal runs per pass with per-tile data
+// The register-stage kernel keeps a pass's programme in shared memory.
+constexpr int kT2SmemIns = 128;      // instructions
+constexpr int kT2SmemFactors = 128;  // factor applications
+constexpr int kT2SmemStatRows = 16;  // per-thread static phase rows (later rows stay in global memory)
 
 enum T2Op : int32_t {
     T2_STAGE = 0,  // switch layout (stage record `aux`), through shared memory
