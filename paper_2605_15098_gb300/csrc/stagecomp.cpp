@@ -62,12 +62,17 @@ Layout choose_layout(const TilePass &tp, int from) {
         used[1 + l] = true;
     }
     int nreg = 1, nlane = 3, nwarp = 0;
-    for (size_t i = from; i < tp.ops.size() && nreg < kT2RegBits; i++) {
+    // the next gate targets become register bits, then lane bits 3 and 4
+    // (gates there are warp shuffles, cheaper than another stage change)
+    for (size_t i = from; i < tp.ops.size() && (nreg < kT2RegBits || nlane < 5); i++) {
         const TileOp &op = tp.ops[i];
         if (!is_gate_op(op.type)) continue;
         const int t = op.slot;
         if (used[t]) continue;
-        L.reg[nreg++] = t;
+        if (nreg < kT2RegBits)
+            L.reg[nreg++] = t;
+        else
+            L.lane[nlane++] = t;
         used[t] = true;
     }
     for (int t = 0; t < kT2Qubits; t++) {
@@ -139,7 +144,7 @@ void block_device_layout(const Block &B, float *dst) {
 
 bool executable(const Layout &L, const TileOp &op) {
     if (!is_gate_op(op.type)) return true;
-    return L.cls[op.slot] == T2C_REG || (op.slot >= 1 && op.slot <= 3);
+    return L.cls[op.slot] == T2C_REG || L.cls[op.slot] == T2C_LANE;
 }
 
 }  // namespace

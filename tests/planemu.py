@@ -194,7 +194,7 @@ def run_t2_pass(state, p):
             if ins["cls"] == C_REG:
                 bit = reg[ins["idx"]]
             else:
-                assert ins["cls"] == C_LANE and ins["idx"] < 3
+                assert ins["cls"] == C_LANE and ins["idx"] < 5
                 bit = lane[ins["idx"]]
             cond = None
             if ins["ccls"] == C_GLOBAL:
