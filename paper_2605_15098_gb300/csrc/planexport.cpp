@@ -49,12 +49,14 @@ void put_t2(J &j, const T2Pass &t) {
         j.raw(",\"aux\":"); j.num(in.aux);
         j.raw("}");
     }
-    j.raw("],\"stages\":[");
+    j.raw("],\"rb\":"); j.num(t.rb);
+    j.raw(",\"threads\":"); j.num(t.threads);
+    j.raw(",\"stages\":[");
     for (size_t i = 0; i < t.stages.size(); i++) {
         if (i) j.raw(",");
-        int tb[13];
-        for (int e = 0; e < 13; e++) tb[e] = t.stages[i].tb[e];
-        j.arr(tb, 13);
+        int tb[14];
+        for (int e = 0; e < 14; e++) tb[e] = t.stages[i].tb[e];
+        j.arr(tb, 14);
     }
     j.raw("],\"mats\":[");
     for (size_t i = 0; i < t.mats.size(); i++) {

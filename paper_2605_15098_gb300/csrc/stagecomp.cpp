@@ -24,14 +24,15 @@ namespace {
 uint32_t turns32(uint64_t t64) { return (uint32_t)((t64 + (UINT64_C(1) << 31)) >> 32); }
 
 struct Layout {
-    int reg[kT2RegBits];  // tile bit of register bit j
-    int lane[5];          // tile bit of lane bit l
-    int warp[3];          // tile bit of warp bit w
-    int cls[kT2Qubits];   // T2C_REG / T2C_LANE / T2C_THREAD (warp)
-    int pos[kT2Qubits];   // register bit, or thread bit (lane l -> l, warp w -> 5 + w)
+    int rb = kT2RegBits, nwarp = kT2WarpBits;  // geometry
+    int reg[kMaxRegBits];  // tile bit of register bit j
+    int lane[5];           // tile bit of lane bit l
+    int warp[4];           // tile bit of warp bit w
+    int cls[kT2Qubits];    // T2C_REG / T2C_LANE / T2C_THREAD (warp)
+    int pos[kT2Qubits];    // register bit, or thread bit (lane l -> l, warp w -> 5 + w)
 
     void index() {
-        for (int j = 0; j < kT2RegBits; j++) {
+        for (int j = 0; j < rb; j++) {
             cls[reg[j]] = T2C_REG;
             pos[reg[j]] = j;
         }
@@ -39,11 +40,12 @@ struct Layout {
             cls[lane[l]] = T2C_LANE;
             pos[lane[l]] = l;
         }
-        for (int w = 0; w < 3; w++) {
+        for (int w = 0; w < nwarp; w++) {
             cls[warp[w]] = T2C_THREAD;
             pos[warp[w]] = 5 + w;
         }
     }
+    int tbits() const { return 5 + nwarp; }
     int thread_tile_bit(int t) const { return t < 5 ? lane[t] : warp[t - 5]; }
 };
 
@@ -52,8 +54,10 @@ bool is_gate_op(int type) {
            type == TOP_X;
 }
 
-Layout choose_layout(const TilePass &tp, int from) {
+Layout choose_layout(const TilePass &tp, int from, int rb, int nwarp) {
     Layout L{};
+    L.rb = rb;
+    L.nwarp = nwarp;
     bool used[kT2Qubits] = {};
     L.reg[0] = 0;
     used[0] = true;
@@ -61,15 +65,15 @@ Layout choose_layout(const TilePass &tp, int from) {
         L.lane[l] = 1 + l;
         used[1 + l] = true;
     }
-    int nreg = 1, nlane = 3, nwarp = 0;
+    int nreg = 1, nlane = 3, nw = 0;
     // the next gate targets become register bits, then lane bits 3 and 4
     // (gates there are warp shuffles, cheaper than another stage change)
-    for (size_t i = from; i < tp.ops.size() && (nreg < kT2RegBits || nlane < 5); i++) {
+    for (size_t i = from; i < tp.ops.size() && (nreg < rb || nlane < 5); i++) {
         const TileOp &op = tp.ops[i];
         if (!is_gate_op(op.type)) continue;
         const int t = op.slot;
         if (used[t]) continue;
-        if (nreg < kT2RegBits)
+        if (nreg < rb)
             L.reg[nreg++] = t;
         else
             L.lane[nlane++] = t;
@@ -77,12 +81,12 @@ Layout choose_layout(const TilePass &tp, int from) {
     }
     for (int t = 0; t < kT2Qubits; t++) {
         if (used[t]) continue;
-        if (nreg < kT2RegBits)
+        if (nreg < rb)
             L.reg[nreg++] = t;
         else if (nlane < 5)
             L.lane[nlane++] = t;
         else
-            L.warp[nwarp++] = t;
+            L.warp[nw++] = t;
         used[t] = true;
     }
     L.index();
@@ -176,12 +180,19 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
     out->gmask = tp.gmask;
     out->ngates = tp.ngates;
     out->nruns = nruns;
+    // geometry: the fused kernel needs 5 register bits (32x32 blocks)
+    const int RB = fused ? kT3RegBits : kT2RegBits;
+    const int NW = fused ? kT3WarpBits : kT2WarpBits;
+    const int NT = fused ? kT3Threads : kT2Threads;  // threads = rows of a static phase table
+    const int TB = 5 + NW;                           // thread bits
+    out->rb = RB;
+    out->threads = NT;
 
     auto emit_stage = [&](const Layout &L) {
         T2Stage st{};
-        for (int j = 0; j < kT2RegBits; j++) st.tb[j] = (int8_t)L.reg[j];
+        for (int j = 0; j < RB; j++) st.tb[j] = (int8_t)L.reg[j];
         for (int l = 0; l < 5; l++) st.tb[5 + l] = (int8_t)L.lane[l];
-        for (int w = 0; w < 3; w++) st.tb[10 + w] = (int8_t)L.warp[w];
+        for (int w = 0; w < NW; w++) st.tb[10 + w] = (int8_t)L.warp[w];
         T2Ins in{};
         in.op = T2_STAGE;
         in.aux = (int32_t)out->stages.size();
@@ -189,7 +200,7 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
         out->ins.push_back(in);
     };
 
-    Layout L = choose_layout(tp, 0);
+    Layout L = choose_layout(tp, 0, RB, NW);
     emit_stage(L);
     int run = 0;
     // fused mode: register-bit gates accumulate into a block; thread-dependent
@@ -235,7 +246,7 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
                 std::string e = flush();
                 if (!e.empty()) return e;
             }
-            L = choose_layout(tp, (int)i);
+            L = choose_layout(tp, (int)i, RB, NW);
             emit_stage(L);
         }
         if (fused && is_gate_op(op.type) && L.cls[op.slot] == T2C_REG &&
@@ -290,7 +301,7 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
         uint32_t sl[kT2Qubits] = {};    // static linear coefficient of each tile bit
         bool dyn[kT2Qubits] = {};       // tile bit has global-dependent (per-tile) terms
         bool use_cst = false;
-        uint32_t rt[kT2RegBits][8] = {};
+        uint32_t rt[kMaxRegBits][kMaxThreadBits] = {};
         std::vector<std::tuple<int, int, uint32_t>> tt;
         std::map<int, uint32_t> rr;     // register-bit mask -> theta
         for (int t = op.tb; t < op.te; t++) {
@@ -364,11 +375,11 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
             // a static row theta * (bit t of the thread) is a constant factor
             // that only the threads with bit t set apply: no table lookups
             if (!cst && lin_reg < 0 && dmask == 0) {
-                for (int t = 0; t < 8; t++) {
+                for (int t = 0; t < TB; t++) {
                     const uint32_t th = row[1 << t];
                     if (!th) continue;
                     bool single = true;
-                    for (int tau = 0; tau < 256 && single; tau++)
+                    for (int tau = 0; tau < NT && single; tau++)
                         single = row[tau] == (((tau >> t) & 1) ? th : 0u);
                     if (!single) break;
                     const uint32_t w0 = (uint32_t)mask | ((uint32_t)(t + 1) << 10);
@@ -382,24 +393,25 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
                 }
             }
             const uint32_t w0 = (uint32_t)mask | (1u << 8) | (cst ? (1u << 9) : 0u) |
-                                ((uint32_t)(lin_reg + 1) << 16) | ((uint32_t)dmask << 24);
+                                ((uint32_t)(lin_reg + 1) << kFacLinShift) |
+                                ((uint32_t)dmask << kFacDynShift);
             std::memcpy(&f.w0, &w0, sizeof w0);
             f.run = r;
-            const int32_t rowi = (int32_t)(out->stat.size() / 256);
+            const int32_t rowi = (int32_t)(out->stat.size() / NT);
             std::memcpy(&f.c0, &rowi, sizeof rowi);
-            out->stat.insert(out->stat.end(), row, row + 256);
+            out->stat.insert(out->stat.end(), row, row + NT);
             out->factors.push_back(f);
         };
         // thread factor (all amplitudes of the thread)
         {
-            uint32_t row[256];
+            uint32_t row[kT2Threads];
             bool any = false;
             int dmask = 0;
-            for (int t = 0; t < 8; t++)
+            for (int t = 0; t < TB; t++)
                 if (dyn[L.thread_tile_bit(t)]) dmask |= 1 << t;
-            for (int tau = 0; tau < 256; tau++) {
+            for (int tau = 0; tau < NT; tau++) {
                 uint32_t u = 0;
-                for (int t = 0; t < 8; t++)
+                for (int t = 0; t < TB; t++)
                     if ((tau >> t) & 1) u += sl[L.thread_tile_bit(t)];
                 for (auto &p : tt)
                     if (((tau >> std::get<0>(p)) & (tau >> std::get<1>(p))) & 1) u += std::get<2>(p);
@@ -409,13 +421,13 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
             if (any || use_cst || dmask) add_thread_factor(0, use_cst, -1, dmask, row);
         }
         // one factor per register bit with a coefficient
-        for (int j = 0; j < kT2RegBits; j++) {
+        for (int j = 0; j < RB; j++) {
             const int tb = L.reg[j];
-            uint32_t row[256];
+            uint32_t row[kT2Threads];
             bool any = false;
-            for (int tau = 0; tau < 256; tau++) {
+            for (int tau = 0; tau < NT; tau++) {
                 uint32_t u = sl[tb];
-                for (int t = 0; t < 8; t++)
+                for (int t = 0; t < TB; t++)
                     if ((tau >> t) & 1) u += rt[j][t];
                 row[tau] = u;
                 any |= u != 0;
@@ -464,30 +476,36 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
     for (size_t si = 0; si < out->stages.size(); si++) {
         const T2Stage &st = out->stages[si];
         T2LayoutX &x = out->layx[si];
-        for (int v = 0; v < 16; v++) {
-            int lo = 0, hi = 0;
-            for (int t = 0; t < 4; t++) {
+        for (int v = 0; v < 32; v++) {
+            int lo = 0;
+            for (int t = 0; t < 5; t++)
                 if ((v >> t) & 1) lo += 1 << st.tb[5 + t];
-                if ((v >> t) & 1) hi += 1 << st.tb[9 + t];
-            }
             x.lo[v] = (uint16_t)lo;
+        }
+        for (int v = 0; v < 16; v++) {
+            int hi = 0;
+            for (int t = 0; t < NW; t++)
+                if ((v >> t) & 1) hi += 1 << st.tb[10 + t];
             x.hi[v] = (uint16_t)hi;
         }
-        for (int j = 0; j < 4; j++) x.s[j] = 1 << st.tb[1 + j];
+        for (int j = 0; j < 4; j++) x.s[j] = 1 + j < RB ? 1 << st.tb[1 + j] : 0;
     }
     if (out->last_stage >= 0) {
         const T2Stage &st = out->stages[out->ins[out->last_stage].aux];
         auto w = [&](int tb) { return UINT64_C(1) << tp.slot_phys[tb]; };
-        for (int v = 0; v < 16; v++) {
-            uint64_t lo = 0, hi = 0;
-            for (int t = 0; t < 4; t++) {
+        for (int v = 0; v < 32; v++) {
+            uint64_t lo = 0;
+            for (int t = 0; t < 5; t++)
                 if ((v >> t) & 1) lo += w(st.tb[5 + t]);
-                if ((v >> t) & 1) hi += w(st.tb[9 + t]);
-            }
             out->epi.glo[v] = lo;
+        }
+        for (int v = 0; v < 16; v++) {
+            uint64_t hi = 0;
+            for (int t = 0; t < NW; t++)
+                if ((v >> t) & 1) hi += w(st.tb[10 + t]);
             out->epi.ghi[v] = hi;
         }
-        for (int j = 0; j < 4; j++) out->epi.g[j] = w(st.tb[1 + j]);
+        for (int j = 0; j < 4; j++) out->epi.g[j] = 1 + j < RB ? w(st.tb[1 + j]) : 0;
     }
     if (out->n_h || fused) {  // fused passes always end with a scale (norm correction)
         const double s = std::pow(2.0, -0.5 * out->n_h);

@@ -13,6 +13,7 @@ namespace sv {
 
 struct T2Pass {
     int k = 0, c = 0;
+    int rb = kT2RegBits, threads = kT2Threads;  // geometry (see tileprog.h)
     int slot_phys[kMaxTileQubits] = {};
     uint64_t gmask = 0;
     int ngates = 0;

@@ -1,6 +1,6 @@
 // Register-stage tile kernel (complex64, tiles of 2^13 amplitudes).
 //
-// Per tile (persistent grid, two CTAs per SM, 256 threads each):
+// Per tile (persistent grid, two CTAs per SM, 256 threads each, 32 amplitudes per thread):
 //   1. one warp issues 2^(13-c) bulk copies (TMA, cp.async.bulk) of the
 //      tile's contiguous 2^c-amplitude chunks into shared memory, completing
 //      on an mbarrier;
@@ -31,11 +31,12 @@ using namespace tiledev;
 constexpr int kTileAmps = 1 << kT2Qubits;
 constexpr uint32_t kTileBytes = kTileAmps * 8u;
 constexpr int kTabN = 256;               // four levels of 2^8 entries
+constexpr int kNP2 = 1 << (kT2RegBits - 1);  // packed pairs per thread (16 amplitudes)
 constexpr int kTabEntries = 4 * kTabN;
 constexpr size_t kOffTab = kTileBytes;
 // k_tile2 copies the pass's programme into shared memory once per CTA
 constexpr size_t kOffStat = kOffTab + (size_t)kTabEntries * 8;
-constexpr size_t kOffFac = kOffStat + (size_t)kT2SmemStatRows * 256 * 4;
+constexpr size_t kOffFac = kOffStat + (size_t)kT2SmemStatRows * kT2Threads * 4;
 constexpr size_t kOffIns = kOffFac + (size_t)kT2SmemFactors * 16;
 constexpr size_t kOffLin = kOffIns + (size_t)kT2SmemIns * 16;
 constexpr size_t kOffCst = kOffLin + (size_t)kT2MaxRuns * 16 * 4;
@@ -62,7 +63,7 @@ __shared__ uint64_t t2_tile_base;  // physical index of the current tile's ampli
 struct Layout2 {
     int bt, s1, s2, s3, s4;
     __device__ Layout2(const T2LayoutX *x, int tid) {
-        bt = (int)__ldg(&x->lo[tid & 15]) + (int)__ldg(&x->hi[tid >> 4]);
+        bt = (int)__ldg(&x->lo[tid & 31]) + (int)__ldg(&x->hi[tid >> 5]);
         const int4 sv = __ldg(reinterpret_cast<const int4 *>(x->s));
         s1 = sv.x;
         s2 = sv.y;
@@ -87,7 +88,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
     const uint32_t *lin = reinterpret_cast<const uint32_t *>(t2_dyn_smem + kOffLin);
     const uint32_t *cst = reinterpret_cast<const uint32_t *>(t2_dyn_smem + kOffCst);
     const int tid = threadIdx.x;
-    Regs r;
+    RegsN<kNP2> r;
     int stage = 0;
     bool live = false;
     bool hooked = false;
@@ -98,7 +99,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
             if (live) {
                 const Layout2 L(a.layx + stage, tid);
 #pragma unroll
-                for (int q = 0; q < kNP; q++)
+                for (int q = 0; q < kNP2; q++)
                     tile4[L.idx(q)] = make_float4(r.re[q].x, r.re[q].y, r.im[q].x, r.im[q].y);
                 __syncthreads();
             }
@@ -109,7 +110,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
                     const bool has = (a.gen_basis & a.gmask) == t2_tile_base;
                     const int lp = a.gen_local >> 1;
 #pragma unroll
-                    for (int q = 0; q < kNP; q++) {
+                    for (int q = 0; q < kNP2; q++) {
                         r.re[q] = make_float2(0.f, 0.f);
                         r.im[q] = make_float2(0.f, 0.f);
                         if (has && L.idx(q) == lp) {
@@ -121,7 +122,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
                     }
                 } else {
 #pragma unroll
-                    for (int q = 0; q < kNP; q++) {
+                    for (int q = 0; q < kNP2; q++) {
                         const float4 v = tile4[L.idx(q)];
                         if (live) {
                             r.re[q] = make_float2(v.x, v.y);
@@ -145,7 +146,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
             const float4 mm = __ldg(a.mats + 2 * w.w);
             const float hi = mm.x, lo = mm.y;
 #pragma unroll
-            for (int q = 0; q < kNP; q++) {
+            for (int q = 0; q < kNP2; q++) {
                 r.re[q] = fma2(r.re[q], f2(hi), mul2(r.re[q], f2(lo)));
                 r.im[q] = fma2(r.im[q], f2(hi), mul2(r.im[q], f2(lo)));
             }
@@ -158,8 +159,8 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
             // load while this one is applied
             // static phase rows beyond the shared-memory copy stay in global memory
             auto stat_at = [&](int row) -> uint32_t {
-                if (kSmemProg && row >= kT2SmemStatRows) return __ldg(a.stat + row * 256 + tid);
-                return stat[row * 256 + tid];
+                if (kSmemProg && row >= kT2SmemStatRows) return __ldg(a.stat + row * kT2Threads + tid);
+                return stat[row * kT2Threads + tid];
             };
             int4 fd = fac[e0];
             uint32_t sv = ((uint32_t)fd.x & 0x100u) ? stat_at(fd.z) : 0u;
@@ -185,9 +186,9 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
                 } else {
                     uint32_t u = sv;
                     if (w0 & 0x200u) u += cst[run];
-                    const int lr = (int)((w0 >> 16) & 0xff) - 1;
+                    const int lr = (int)((w0 >> kFacLinShift) & 0x1fu) - 1;
                     if (lr >= 0) u += lin[run * 16 + lr];
-                    uint32_t dm = (w0 >> 24) & (uint32_t)tid;
+                    uint32_t dm = (w0 >> kFacDynShift) & 0x1ffu & (uint32_t)tid;
                     while (dm) {
                         const int t = __ffs(dm) - 1;
                         dm &= dm - 1;
@@ -268,11 +269,11 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
     if (!live) return;
     if constexpr (kDirect) {
         const T2Epilogue *E = a.epi;
-        const uint64_t g0 = t2_tile_base + __ldg(&E->glo[tid & 15]) + __ldg(&E->ghi[tid >> 4]);
+        const uint64_t g0 = t2_tile_base + __ldg(&E->glo[tid & 31]) + __ldg(&E->ghi[tid >> 5]);
         const uint64_t g1 = __ldg(&E->g[0]), g2 = __ldg(&E->g[1]), g3 = __ldg(&E->g[2]),
                        g4 = __ldg(&E->g[3]);
 #pragma unroll
-        for (int q = 0; q < kNP; q++) {
+        for (int q = 0; q < kNP2; q++) {
             const uint64_t g = g0 + ((q & 1) ? g1 : 0) + ((q & 2) ? g2 : 0) + ((q & 4) ? g3 : 0) +
                                ((q & 8) ? g4 : 0);
             __stcs(gstate + (g >> 1), make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y));
@@ -280,7 +281,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
     } else {
         const Layout2 L(a.layx + stage, tid);
 #pragma unroll
-        for (int q = 0; q < kNP; q++)
+        for (int q = 0; q < kNP2; q++)
             tile4[L.idx(q)] = make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y);
     }
 }
@@ -324,7 +325,7 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_tile2(float *__restrict__ sta
         uint32_t *ss = reinterpret_cast<uint32_t *>(sm + kOffStat);
         for (int i = tid; i < a.nins; i += blockDim.x) si[i] = __ldg(a.ins + i);
         for (int i = tid; i < a.nfac; i += blockDim.x) sf[i] = __ldg(a.fac + i);
-        const int nst = min(a.nstat, kT2SmemStatRows * 256);
+        const int nst = min(a.nstat, kT2SmemStatRows * kT2Threads);
         for (int i = tid; i < nst; i += blockDim.x) ss[i] = __ldg(a.stat + i);
     }
     if (tid == 0) {

@@ -161,7 +161,7 @@ __device__ __forceinline__ void issue_tile_store(float *state, const unsigned ch
     bulk_commit();
 }
 
-__global__ void __launch_bounds__(kT2Threads, 1) k_tile3(float *__restrict__ state, const T3Args a) {
+__global__ void __launch_bounds__(kT3Threads, 1) k_tile3(float *__restrict__ state, const T3Args a) {
     extern __shared__ __align__(1024) unsigned char sm[];
     float2 *tab = reinterpret_cast<float2 *>(sm + kOffTab);
     uint32_t *lin = reinterpret_cast<uint32_t *>(sm + kOffLin);
@@ -441,11 +441,11 @@ __global__ void __launch_bounds__(kT2Threads, 1) k_tile3(float *__restrict__ sta
                         fr = __int_as_float(fd.z);
                         fi = __int_as_float(fd.w);
                     } else {
-                        uint32_t u = __ldg(a.stat + fd.z * 256 + tid);
+                        uint32_t u = __ldg(a.stat + fd.z * kT3Threads + tid);
                         if (w0 & 0x200u) u += cst[run];
-                        const int lr = (int)((w0 >> 16) & 0xff) - 1;
+                        const int lr = (int)((w0 >> kFacLinShift) & 0x1fu) - 1;
                         if (lr >= 0) u += lin[run * 16 + lr];
-                        uint32_t dm = (w0 >> 24) & (uint32_t)tid;
+                        uint32_t dm = (w0 >> kFacDynShift) & 0x1ffu & (uint32_t)tid;
                         while (dm) {
                             const int t = __ffs(dm) - 1;
                             dm &= dm - 1;
@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(kT2Threads, 1) k_tile3(float *__restrict__ sta
         double *red = reinterpret_cast<double *>(lin);
         red[tid] = nacc;
         __syncthreads();
-        for (int w2 = kT2Threads / 2; w2; w2 >>= 1) {
+        for (int w2 = kT3Threads / 2; w2; w2 >>= 1) {
             if (tid < w2) red[tid] += red[tid + w2];
             __syncthreads();
         }
@@ -595,7 +595,7 @@ sv_status t3_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
     a.err = h->t2_err;
     const uint64_t grid = std::min<uint64_t>(a.ntiles, std::min<uint64_t>((uint64_t)h->sm_count, 256));
     const int slot = prof_begin(h);
-    k_tile3<<<(unsigned)grid, kT2Threads, kSmemBytes, h->stream>>>(reinterpret_cast<float *>(h->amps), a);
+    k_tile3<<<(unsigned)grid, kT3Threads, kSmemBytes, h->stream>>>(reinterpret_cast<float *>(h->amps), a);
     SV_CUDA(cudaGetLastError());
     note_launch();
     prof_end(h, slot, meta);

@@ -107,6 +107,10 @@ __device__ __forceinline__ float2 cx(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+template <int NP>
+struct RegsN {
+    float2 re[NP], im[NP];
+};
 struct Regs {
     float2 re[kNP], im[kNP];
 };
@@ -204,10 +208,10 @@ __device__ __forceinline__ void reg_u(Regs &r, int jc, const float *m) {
 // is all ones at run time; testing one of its bits per group of four packed
 // pairs keeps each group a separate block, which bounds how many pairs the
 // compiler keeps in flight (and so the register pressure).
-template <int J>
-__device__ __forceinline__ void reg_h2(Regs &r, uint32_t qm) {
+template <int J, int NP>
+__device__ __forceinline__ void reg_h2(RegsN<NP> &r, uint32_t qm) {
 #pragma unroll
-    for (int g4 = 0; g4 < 4; g4++) {
+    for (int g4 = 0; g4 < NP / 4; g4++) {
         if (!((qm >> g4) & 1)) continue;
 #pragma unroll
         for (int i = 0; i < 4; i++) {
@@ -228,10 +232,10 @@ __device__ __forceinline__ void reg_h2(Regs &r, uint32_t qm) {
     }
 }
 
-template <int J>
-__device__ __forceinline__ void reg_x2(Regs &r, uint32_t qm) {
+template <int J, int NP>
+__device__ __forceinline__ void reg_x2(RegsN<NP> &r, uint32_t qm) {
 #pragma unroll
-    for (int g4 = 0; g4 < 4; g4++) {
+    for (int g4 = 0; g4 < NP / 4; g4++) {
         if (!((qm >> g4) & 1)) continue;
 #pragma unroll
         for (int i = 0; i < 4; i++) {
@@ -250,12 +254,12 @@ __device__ __forceinline__ void reg_x2(Regs &r, uint32_t qm) {
     }
 }
 
-template <int J>
-__device__ __forceinline__ void reg_u2(Regs &r, uint32_t qm, const float *m) {
+template <int J, int NP>
+__device__ __forceinline__ void reg_u2(RegsN<NP> &r, uint32_t qm, const float *m) {
     const float u0r = m[0], u0i = m[1], u1r = m[2], u1i = m[3];
     const float u2r = m[4], u2i = m[5], u3r = m[6], u3i = m[7];
 #pragma unroll
-    for (int g4 = 0; g4 < 4; g4++) {
+    for (int g4 = 0; g4 < NP / 4; g4++) {
         if (!((qm >> g4) & 1)) continue;
 #pragma unroll
         for (int i = 0; i < 4; i++) {
@@ -281,8 +285,8 @@ __device__ __forceinline__ void reg_u2(Regs &r, uint32_t qm, const float *m) {
 }
 
 // Uncontrolled (or thread-predicated) gate OP on lane bit l (see reg_h2 for qm).
-template <int OP>
-__device__ __forceinline__ void lane_op2(Regs &r, int l, bool pred, uint32_t qm, const float *m) {
+template <int OP, int NP>
+__device__ __forceinline__ void lane_op2(RegsN<NP> &r, int l, bool pred, uint32_t qm, const float *m) {
     const unsigned FULL = 0xffffffffu;
     const int xm = 1 << l;
     const bool hi = (threadIdx.x >> l) & 1;
@@ -295,7 +299,7 @@ __device__ __forceinline__ void lane_op2(Regs &r, int l, bool pred, uint32_t qm,
     }
     const float sg = hi ? -1.f : 1.f;
 #pragma unroll
-    for (int g4 = 0; g4 < 4; g4++) {
+    for (int g4 = 0; g4 < NP / 4; g4++) {
         if (!((qm >> g4) & 1)) continue;
 #pragma unroll
         for (int i = 0; i < 4; i++) {
@@ -430,10 +434,11 @@ __device__ __forceinline__ void lane_op(Regs &r, int l, bool pred, const float *
 }
 
 // ---------------------------------------------------------------- diagonal factors
-template <int M>
-__device__ __forceinline__ void apply_factor(Regs &r, float fr, float fi) {
+template <int M, typename R>
+__device__ __forceinline__ void apply_factor(R &r, float fr, float fi) {
+    constexpr int NP = sizeof(r.re) / sizeof(r.re[0]);
 #pragma unroll
-    for (int q = 0; q < kNP; q++) {
+    for (int q = 0; q < NP; q++) {
         if constexpr ((M & 1) != 0) {
             if (((2 * q + 1) & M) == M) cmul1(r.re[q].y, r.im[q].y, fr, fi);
         } else {
@@ -442,7 +447,8 @@ __device__ __forceinline__ void apply_factor(Regs &r, float fr, float fi) {
     }
 }
 
-__device__ __forceinline__ void apply_factor_any(Regs &r, int mask, float fr, float fi) {
+template <typename R>
+__device__ __forceinline__ void apply_factor_any(R &r, int mask, float fr, float fi) {
     switch (mask) {
 #define SV_FAC(M) \
     case M: apply_factor<M>(r, fr, fi); break;

@@ -3,10 +3,10 @@
 // A tile pass (see plan.h) is compiled into stages.  In a stage every thread
 // of the CTA holds 2^RB amplitudes of the 2^13-amplitude tile in registers:
 // register bit 0 is always tile bit 0 (two neighbouring amplitudes form one
-// 16-byte shared-memory vector), register bits 1..4 are four tile bits chosen
+// 16-byte shared-memory vector), register bits 1..RB-1 are tile bits chosen
 // per stage, lane bits 0..2 are tile bits 1..3 (so that the eight lanes of a
 // quarter-warp read one 128-byte row: conflict-free), lane bits 3..4 and the
-// three warp bits are the remaining tile bits.  A gate on a register bit is
+// warp bits are the remaining tile bits.  A gate on a register bit is
 // thread-local arithmetic; a gate on a lane bit exchanges amplitudes with
 // warp shuffles; a stage change stores the tile to shared memory and reloads
 // it in the next stage's layout.
@@ -27,8 +27,22 @@
 namespace sv {
 
 constexpr int kT2Qubits = 13;   // tile: 2^13 complex64 amplitudes (64 KiB)
-constexpr int kT2Threads = 256; // 8 warps
-constexpr int kT2RegBits = 5;   // 32 amplitudes per thread
+// The programme format is written for a geometry: register bits RB, 5 lane
+// bits and 13 - RB - 5 warp bits.  The CUDA-core kernels (k_tile2, k_batch)
+// and the fused tensor-core kernel (k_tile3) both hold 32 amplitudes per
+// thread in 256 threads (5 register bits, the index of a 32x32 block for the
+// fused kernel).  A 16-amplitude, 512-thread geometry for the CUDA-core
+// kernels was measured slower: the per-thread work of a diagonal factor
+// (its record and its table lookups) is then spread over half as many
+// amplitudes.
+constexpr int kT2Threads = 256;
+constexpr int kT2RegBits = 5;
+constexpr int kT2WarpBits = 3;
+constexpr int kT3Threads = 256;
+constexpr int kT3RegBits = 5;
+constexpr int kT3WarpBits = 3;
+constexpr int kMaxRegBits = 5;
+constexpr int kMaxThreadBits = 9;  // 5 lane bits + up to 4 warp bits
 constexpr int kT2MaxRuns = 64;  // diagonal runs per pass with per-tile data
 // The register-stage kernel keeps a pass's programme in shared memory.
 constexpr int kT2SmemIns = 128;      // instructions
@@ -75,19 +89,19 @@ struct T2Stage {
 };
 
 // Kernel-side form of a stage layout, computed on the host: the tile offset
-// (in amplitudes) of thread bits 0..3 (lo, indexed by tid & 15) and 4..7 (hi,
-// indexed by tid >> 4), and of register bits 1..4.  A thread's packed pair q
+// (in amplitudes) of the lane bits (lo, indexed by tid & 31) and the warp bits
+// (hi, indexed by tid >> 5), and of register bits 1..  A thread's packed pair q
 // sits at tile offset lo + hi + sum over the set bits j of q of s[j].
 struct T2LayoutX {
-    uint16_t lo[16];
-    uint16_t hi[16];
-    int32_t s[4];
+    uint16_t lo[32];  // lane bits (tid & 31)
+    uint16_t hi[16];  // warp bits (tid >> 5)
+    int32_t s[4];     // register bits 1.. (unused ones 0)
 };
 
 // Write-back offsets of the final layout in the global state (amplitudes),
-// relative to the tile's base: thread bits 0..3, 4..7 and register bits 1..4.
+// relative to the tile's base: lane bits, warp bits and register bits 1..
 struct T2Epilogue {
-    uint64_t glo[16];
+    uint64_t glo[32];
     uint64_t ghi[16];
     uint64_t g[4];
 };
@@ -102,10 +116,13 @@ struct T2Mat {
 //   w0 bit 9:       phase += cst[run] (the tile's global-only part)
 //   w0 bits 10..13: constant factors only: 1 + thread bit t; only threads with
 //                   bit t set apply the factor (0 = every thread)
-//   w0 bits 16..23: 1 + tile bit whose per-tile coefficient lin[run][tb] is added, 0 = none
-//   w0 bits 24..31: thread bits t whose per-tile coefficient lin[run][tile bit of t] is added
+//   w0 bits 14..18: 1 + tile bit whose per-tile coefficient lin[run][tb] is added, 0 = none
+//   w0 bits 19..27: thread bits t whose per-tile coefficient lin[run][tile bit of t] is added
 //                   when thread bit t is set
-// A per-thread phase starts from stat[e * 256 + threadIdx.x] (host table).
+// A per-thread phase starts from row c0 of the host table of per-thread
+// static phases (one entry per thread of the geometry).
+constexpr int kFacLinShift = 14;
+constexpr int kFacDynShift = 19;
 struct T2Factor {
     int32_t w0;
     int32_t run;

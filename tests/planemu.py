@@ -116,6 +116,8 @@ def run_t2_pass(state, p):
     ntiles = 1 << (int(np.log2(state.size)) - k)
     loc = np.arange(1 << k)
     stat = np.asarray(t2["stat"], dtype=np.int64)
+    rb, nthreads = t2["rb"], t2["threads"]
+    nw = nthreads.bit_length() - 1 - 5          # warp bits
     for tile in range(ntiles):
         base = pdep(tile, p["gmask"])
         idx = tile_index(p, base)
@@ -136,7 +138,7 @@ def run_t2_pass(state, p):
             op = ins["op"]
             if op == T2_STAGE:
                 st = t2["stages"][ins["aux"]]
-                reg, lane, warp = st[0:5], st[5:10], st[10:13]
+                reg, lane, warp = st[0:rb], st[5:10], st[10:10 + nw]
                 assert sorted(reg + lane + warp) == list(range(k))
                 assert reg[0] == 0 and lane[:3] == [1, 2, 3]
                 ttb = lane + warp                   # tile bit of thread bit t
@@ -166,7 +168,7 @@ def run_t2_pass(state, p):
                     w0 = f["w0"]
                     mask = w0 & 0xFF
                     sel = np.ones(t.size, dtype=bool)
-                    for j in range(5):
+                    for j in range(rb):
                         if (mask >> j) & 1:
                             sel &= ((loc >> reg[j]) & 1) == 1
                     if not (w0 >> 8) & 1:
@@ -176,14 +178,14 @@ def run_t2_pass(state, p):
                             sel &= ((tid >> (pb - 1)) & 1) == 1
                     else:
                         run = f["run"]
-                        u = stat[f["row"] * 256 + tid].copy()
+                        u = stat[f["row"] * nthreads + tid].copy()
                         if (w0 >> 9) & 1:
                             u += cst[run]
-                        lr = ((w0 >> 16) & 0xFF) - 1
+                        lr = ((w0 >> 14) & 0x1F) - 1
                         if lr >= 0:
                             u += lin[run * 16 + lr]
-                        dm = (w0 >> 24) & 0xFF
-                        for tt_ in range(8):
+                        dm = (w0 >> 19) & 0x1FF
+                        for tt_ in range(5 + nw):
                             if (dm >> tt_) & 1:
                                 u += ((tid >> tt_) & 1) * lin[run * 16 + ttb[tt_]]
                         u &= MASK32
