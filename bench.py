@@ -216,6 +216,23 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def replica_max(dist, x: float) -> float:
+    """Max of a per-rank time over the replicas (each rank runs its own
+    independent copy of the step: nothing else crosses ranks)."""
+    if not dist:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: all replicas' steps over the slowest rank's time."""
+    return world * steps / (max_ms / 1e3)
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -236,11 +253,7 @@ def run_ours(args, world, rank, local):
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replica_max(dist, x)
 
     n = args.n
     dt = sv.SV_C64 if args.dtype == "c64" else sv.SV_C128
@@ -294,7 +307,7 @@ def run_ours(args, world, rank, local):
     recs = sv.sv_profile_read(h)
     sv.sv_profile(h, False)
     max_ms = max_over_ranks(elapsed_ms)
-    value = world * args.steps / (max_ms / 1e3)
+    value = replica_value(world, args.steps, max_ms)
 
     tile = [r for r in recs if r["kind"] in (sv.SV_KERNEL_TILE, sv.SV_KERNEL_FUSED)]
     kinds = [r["gate_kind"] for r in tile]
