@@ -161,26 +161,33 @@ k_block_sum(const double *__restrict__ x, uint64_t len, double *__restrict__ sum
     if (threadIdx.x == 0) sums[blockIdx.x] = sh[0];
 }
 
-__global__ void k_normalise(double *__restrict__ p, uint64_t len, const double *__restrict__ sums,
-                            int nsums) {
-    __shared__ double total;
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < nsums; i++) t += sums[i];
-        total = t;
-    }
-    __syncthreads();
-    const double t = total;
+// Total of the block sums in a fixed order (one warp: lane l sums entries
+// l, l + 32, ... in order, then a fixed shuffle tree), so every call gets the
+// same bits.
+__device__ __forceinline__ double ordered_total(const double *__restrict__ sums, int nsums) {
+    double t = 0.0;
+    for (int i = threadIdx.x & 31; i < nsums; i += 32) t += sums[i];
+#pragma unroll
+    for (int off = 16; off; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    return t;
+}
+
+__global__ void k_total(const double *__restrict__ sums, int nsums, double *__restrict__ total) {
+    const double t = ordered_total(sums, nsums);
+    if (threadIdx.x == 0) *total = t;
+}
+
+__global__ void k_normalise(double *__restrict__ p, uint64_t len, const double *__restrict__ total) {
+    const double t = *total;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride)
         p[i] = p[i] / t;
 }
 
-// v[0] /= total, the total summed over the block sums in order (as k_normalise does).
+// v[0] /= total (the same ordered total as the normalisation uses).
 __global__ void k_div_total(double *v, const double *__restrict__ sums, int nsums) {
-    double t = 0.0;
-    for (int i = 0; i < nsums; i++) t += sums[i];
-    v[0] = v[0] / t;
+    const double t = ordered_total(sums, nsums);
+    if (threadIdx.x == 0) v[0] = v[0] / t;
 }
 
 // argmax: (value, lowest index) per block, then one block over the partials.
@@ -355,7 +362,7 @@ sv_status marginal_device(sv_state *h, const int *pos, int m, double *dev_out, b
     if (groups > 1) need += groups * outcomes * sizeof(double);
     const int nsum_blocks = (int)std::min<uint64_t>(1024, blocks_for(outcomes, kRedThreads));
     const size_t sums_off = (need + 255) & ~(size_t)255;
-    need = sums_off + nsum_blocks * sizeof(double);
+    need = sums_off + (nsum_blocks + 1) * sizeof(double);
     SV_TRY(ensure_scratch(h, need));
     if (groups > 1) partial = reinterpret_cast<double *>(h->scratch);
     double *sums = reinterpret_cast<double *>(reinterpret_cast<char *>(h->scratch) + sums_off);
@@ -389,8 +396,12 @@ sv_status marginal_device(sv_state *h, const int *pos, int m, double *dev_out, b
     if (sums_out) *sums_out = sums;
     if (nsums_out) *nsums_out = nsum_blocks;
     if (!normalise) return SV_OK;
+    double *total = sums + nsum_blocks;
+    k_total<<<1, 32, 0, h->stream>>>(sums, nsum_blocks, total);
+    SV_CUDA(cudaGetLastError());
+    note_launch();
     k_normalise<<<std::min<unsigned>(blocks_for(outcomes, kRedThreads), 4096), kRedThreads, 0,
-                  h->stream>>>(dev_out, outcomes, sums, nsum_blocks);
+                  h->stream>>>(dev_out, outcomes, total);
     SV_CUDA(cudaGetLastError());
     note_launch();
     return SV_OK;
@@ -411,7 +422,7 @@ sv_status argmax_device(sv_state *h, const double *dev_p, uint64_t len, uint64_t
     SV_CUDA(cudaGetLastError());
     note_launch();
     if (sums) {  // unnormalised marginal: p = max / total, the total in the normalisation's order
-        k_div_total<<<1, 1, 0, h->stream>>>(fv, sums, nsums);
+        k_div_total<<<1, 32, 0, h->stream>>>(fv, sums, nsums);
         SV_CUDA(cudaGetLastError());
         note_launch();
     }
