@@ -5,7 +5,7 @@
 // execution mode (per-gate sweeps, register-stage tiles on the CUDA cores,
 // tiles with tensor-core fused blocks), the chunk width c of the bulk copies
 // (how many low qubits every tile holds contiguously, 2^c amplitudes), and
-// for complex128 the tile width k.  Each candidate runs the circuit from
+// the tile width k (2^13 or 2^14 amplitudes for complex64).  Each candidate runs the circuit from
 // |0...0> once to warm up and three times under CUDA events; the median wins.
 // Results can be cached in a text file keyed by the circuit's structure
 // (gate kinds and qubits, not their angles), n and the dtype.
@@ -97,6 +97,8 @@ extern "C" sv_status sv_autotune(sv_handle h, const sv_gate *host_gates, size_t 
     if (h->n <= 12) add(SV_MODE_PERGATE, 0, 0);
     if (h->dt == SV_C64) {
         for (int c : {4, 5, 6, 7}) add(SV_MODE_PARTITIONED, 0, c);
+        if (h->n > 14)  // 2^14-amplitude tiles: fewer passes, one CTA per SM
+            for (int c : {4, 5, 7}) add(SV_MODE_PARTITIONED, 14, c);
         if (h->n > 13)
             for (int c : {4, 5, 6}) add(SV_MODE_FUSED, 0, c);
     } else {

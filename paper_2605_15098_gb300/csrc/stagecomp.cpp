@@ -28,8 +28,8 @@ struct Layout {
     int reg[kMaxRegBits];  // tile bit of register bit j
     int lane[5];           // tile bit of lane bit l
     int warp[4];           // tile bit of warp bit w
-    int cls[kT2Qubits];    // T2C_REG / T2C_LANE / T2C_THREAD (warp)
-    int pos[kT2Qubits];    // register bit, or thread bit (lane l -> l, warp w -> 5 + w)
+    int cls[kT2MaxQubits];  // T2C_REG / T2C_LANE / T2C_THREAD (warp)
+    int pos[kT2MaxQubits];  // register bit, or thread bit (lane l -> l, warp w -> 5 + w)
 
     void index() {
         for (int j = 0; j < rb; j++) {
@@ -58,7 +58,7 @@ Layout choose_layout(const TilePass &tp, int from, int rb, int nwarp) {
     Layout L{};
     L.rb = rb;
     L.nwarp = nwarp;
-    bool used[kT2Qubits] = {};
+    bool used[kT2MaxQubits] = {};
     L.reg[0] = 0;
     used[0] = true;
     for (int l = 0; l < 3; l++) {
@@ -79,7 +79,7 @@ Layout choose_layout(const TilePass &tp, int from, int rb, int nwarp) {
             L.lane[nlane++] = t;
         used[t] = true;
     }
-    for (int t = 0; t < kT2Qubits; t++) {
+    for (int t = 0; t < tp.k; t++) {
         if (used[t]) continue;
         if (nreg < rb)
             L.reg[nreg++] = t;
@@ -167,7 +167,8 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
             if ((op.type == TOP_GATE || op.type == TOP_GATE_CL || op.type == TOP_GATE_CG) &&
                 !unitary2(op.m))
                 return "non-unitary gate matrix (fused passes renormalise)";
-    if (tp.k != kT2Qubits) return "tile is not 2^13 amplitudes";
+    if (tp.k != kT2Qubits && !(tp.k == kT2WideQubits && !fused))
+        return "tile is not 2^13 (or, without fused blocks, 2^14) amplitudes";
     if (tp.c < 4) return "chunk smaller than 16 amplitudes";
     for (const TileOp &op : tp.ops)
         if (op.type == TOP_SWAP) return "in-tile SWAP";
@@ -182,8 +183,8 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
     out->nruns = nruns;
     // geometry: the fused kernel needs 5 register bits (32x32 blocks)
     const int RB = fused ? kT3RegBits : kT2RegBits;
-    const int NW = fused ? kT3WarpBits : kT2WarpBits;
-    const int NT = fused ? kT3Threads : kT2Threads;  // threads = rows of a static phase table
+    const int NW = tp.k - RB - 5;                    // warp bits: 3, or 4 for a 2^14 tile
+    const int NT = 1 << (tp.k - RB);                 // threads = rows of a static phase table
     const int TB = 5 + NW;                           // thread bits
     out->rb = RB;
     out->threads = NT;
@@ -298,8 +299,8 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
         }
         // ---- diagonal run: compile its phase polynomial against layout L
         const int r = run++;
-        uint32_t sl[kT2Qubits] = {};    // static linear coefficient of each tile bit
-        bool dyn[kT2Qubits] = {};       // tile bit has global-dependent (per-tile) terms
+        uint32_t sl[kT2MaxQubits] = {};  // static linear coefficient of each tile bit
+        bool dyn[kT2MaxQubits] = {};     // tile bit has global-dependent (per-tile) terms
         bool use_cst = false;
         uint32_t rt[kMaxRegBits][kMaxThreadBits] = {};
         std::vector<std::tuple<int, int, uint32_t>> tt;
@@ -404,7 +405,7 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
         };
         // thread factor (all amplitudes of the thread)
         {
-            uint32_t row[kT2Threads];
+            uint32_t row[1 << (kT2MaxQubits - kT2RegBits)];
             bool any = false;
             int dmask = 0;
             for (int t = 0; t < TB; t++)
@@ -423,7 +424,7 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
         // one factor per register bit with a coefficient
         for (int j = 0; j < RB; j++) {
             const int tb = L.reg[j];
-            uint32_t row[kT2Threads];
+            uint32_t row[1 << (kT2MaxQubits - kT2RegBits)];
             bool any = false;
             for (int tau = 0; tau < NT; tau++) {
                 uint32_t u = sl[tb];

@@ -28,20 +28,34 @@ namespace {
 
 using namespace tiledev;
 
-constexpr int kTileAmps = 1 << kT2Qubits;
-constexpr uint32_t kTileBytes = kTileAmps * 8u;
 constexpr int kTabN = 256;               // four levels of 2^8 entries
-constexpr int kNP2 = 1 << (kT2RegBits - 1);  // packed pairs per thread (16 amplitudes)
+constexpr int kNP2 = 1 << (kT2RegBits - 1);  // packed pairs per thread (32 amplitudes)
 constexpr int kTabEntries = 4 * kTabN;
-constexpr size_t kOffTab = kTileBytes;
-// k_tile2 copies the pass's programme into shared memory once per CTA
-constexpr size_t kOffStat = kOffTab + (size_t)kTabEntries * 8;
-constexpr size_t kOffFac = kOffStat + (size_t)kT2SmemStatRows * kT2Threads * 4;
-constexpr size_t kOffIns = kOffFac + (size_t)kT2SmemFactors * 16;
-constexpr size_t kOffLin = kOffIns + (size_t)kT2SmemIns * 16;
-constexpr size_t kOffCst = kOffLin + (size_t)kT2MaxRuns * 16 * 4;
-constexpr size_t kOffBar = kOffCst + (size_t)kT2MaxRuns * 4;
-constexpr size_t kSmemBytes = kOffBar + 16;
+
+// Shared-memory layout of a CTA for tiles of 2^K amplitudes (K = 13: 256
+// threads, two CTAs per SM; K = 14: 512 threads, one CTA per SM).  The CTA
+// copies the pass's programme into shared memory once.
+template <int K>
+struct Geo {
+    static constexpr int kThreads = 1 << (K - kT2RegBits);
+    static constexpr uint32_t kTileBytes = 8u << K;
+    static constexpr int kStatRows = kT2SmemStatRows;
+    static constexpr size_t kOffTab = kTileBytes;
+    static constexpr size_t kOffStat = kOffTab + (size_t)kTabEntries * 8;
+    static constexpr size_t kOffFac = kOffStat + (size_t)kStatRows * kThreads * 4;
+    static constexpr size_t kOffIns = kOffFac + (size_t)kT2SmemFactors * 16;
+    static constexpr size_t kOffLin = kOffIns + (size_t)kT2SmemIns * 16;
+    static constexpr size_t kOffCst = kOffLin + (size_t)kT2MaxRuns * 16 * 4;
+    static constexpr size_t kOffBar = kOffCst + (size_t)kT2MaxRuns * 4;
+    static constexpr size_t kSmemBytes = kOffBar + 16;
+};
+using G13 = Geo<13>;
+constexpr uint32_t kTileBytes = G13::kTileBytes;
+constexpr size_t kOffTab = G13::kOffTab;
+constexpr size_t kOffLin = G13::kOffLin;
+constexpr size_t kOffCst = G13::kOffCst;
+constexpr size_t kOffBar = G13::kOffBar;
+constexpr size_t kSmemBytes = G13::kSmemBytes;
 
 
 // ---------------------------------------------------------------- the kernel
@@ -76,17 +90,18 @@ struct Layout2 {
     }
 };
 
-template <bool kDirect, bool kSmemProg, typename Hook>
+template <int K, bool kDirect, bool kSmemProg, typename Hook>
 __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hook) {
+    using G = Geo<K>;
     // the programme: copied to shared memory by k_tile2, read from global by k_batch
-    const int4 *ins = kSmemProg ? reinterpret_cast<const int4 *>(t2_dyn_smem + kOffIns) : a.ins;
-    const int4 *fac = kSmemProg ? reinterpret_cast<const int4 *>(t2_dyn_smem + kOffFac) : a.fac;
+    const int4 *ins = kSmemProg ? reinterpret_cast<const int4 *>(t2_dyn_smem + G::kOffIns) : a.ins;
+    const int4 *fac = kSmemProg ? reinterpret_cast<const int4 *>(t2_dyn_smem + G::kOffFac) : a.fac;
     const uint32_t *stat =
-        kSmemProg ? reinterpret_cast<const uint32_t *>(t2_dyn_smem + kOffStat) : a.stat;
+        kSmemProg ? reinterpret_cast<const uint32_t *>(t2_dyn_smem + G::kOffStat) : a.stat;
     float4 *tile4 = reinterpret_cast<float4 *>(t2_dyn_smem);
-    const float2 *tab = reinterpret_cast<const float2 *>(t2_dyn_smem + kOffTab);
-    const uint32_t *lin = reinterpret_cast<const uint32_t *>(t2_dyn_smem + kOffLin);
-    const uint32_t *cst = reinterpret_cast<const uint32_t *>(t2_dyn_smem + kOffCst);
+    const float2 *tab = reinterpret_cast<const float2 *>(t2_dyn_smem + G::kOffTab);
+    const uint32_t *lin = reinterpret_cast<const uint32_t *>(t2_dyn_smem + G::kOffLin);
+    const uint32_t *cst = reinterpret_cast<const uint32_t *>(t2_dyn_smem + G::kOffCst);
     const int tid = threadIdx.x;
     RegsN<kNP2> r;
     int stage = 0;
@@ -159,8 +174,8 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
             // load while this one is applied
             // static phase rows beyond the shared-memory copy stay in global memory
             auto stat_at = [&](int row) -> uint32_t {
-                if (kSmemProg && row >= kT2SmemStatRows) return __ldg(a.stat + row * kT2Threads + tid);
-                return stat[row * kT2Threads + tid];
+                if (kSmemProg && row >= G::kStatRows) return __ldg(a.stat + row * G::kThreads + tid);
+                return stat[row * G::kThreads + tid];
             };
             int4 fd = fac[e0];
             uint32_t sv = ((uint32_t)fd.x & 0x100u) ? stat_at(fd.z) : 0u;
@@ -286,19 +301,20 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
     }
 }
 
+template <int K>
 __device__ __forceinline__ void issue_tile_load(const T2Args &a, unsigned char *sm, const float *state,
                                                 uint64_t tile, uint64_t *bar, int tid) {
-    const int nchunks = 1 << (kT2Qubits - a.c);
+    const int nchunks = 1 << (K - a.c);
     const uint32_t chunk_bytes = 8u << a.c;
     const uint64_t base = pdep(tile, a.gmask);
     if (tid == 0) {
         fence_async_smem();
-        mbar_expect_tx(bar, kTileBytes);
+        mbar_expect_tx(bar, Geo<K>::kTileBytes);
     }
     __syncwarp();
     for (int j = tid; j < nchunks; j += 32) {
         uint64_t off = 0;
-        for (int b = 0; b < kT2Qubits - a.c; b++)
+        for (int b = 0; b < K - a.c; b++)
             if ((j >> b) & 1) off |= UINT64_C(1) << a.slot_phys[a.c + b];
         bulk_g2s(sm + (size_t)j * chunk_bytes, state + 2 * (base + off), chunk_bytes, bar);
     }
@@ -309,23 +325,26 @@ __device__ __forceinline__ void issue_tile_load(const T2Args &a, unsigned char *
 // the rest of tile i's programme and its write-back, which goes from
 // registers straight to the global state (16-byte stores; lanes 0..7 cover
 // tile bits 1..3, so a quarter-warp writes 128 contiguous bytes).
-__global__ void __launch_bounds__(kT2Threads, 2) k_tile2(float *__restrict__ state, const T2Args a) {
+template <int K>
+__global__ void __launch_bounds__(Geo<K>::kThreads, K == kT2Qubits ? 2 : 1)
+    k_tile2(float *__restrict__ state, const T2Args a) {
+    using G = Geo<K>;
     extern __shared__ __align__(1024) unsigned char sm[];
     float4 *tile4 = reinterpret_cast<float4 *>(sm);
-    float2 *tab = reinterpret_cast<float2 *>(sm + kOffTab);
-    uint32_t *lin = reinterpret_cast<uint32_t *>(sm + kOffLin);
-    uint32_t *cst = reinterpret_cast<uint32_t *>(sm + kOffCst);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kOffBar);
+    float2 *tab = reinterpret_cast<float2 *>(sm + G::kOffTab);
+    uint32_t *lin = reinterpret_cast<uint32_t *>(sm + G::kOffLin);
+    uint32_t *cst = reinterpret_cast<uint32_t *>(sm + G::kOffCst);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + G::kOffBar);
     const int tid = threadIdx.x;
 
     for (int i = tid; i < kTabEntries; i += blockDim.x) tab[i] = a.tables[i];
     {  // the programme, once per CTA (sizes bounded by the stage compiler)
-        int4 *si = reinterpret_cast<int4 *>(sm + kOffIns);
-        int4 *sf = reinterpret_cast<int4 *>(sm + kOffFac);
-        uint32_t *ss = reinterpret_cast<uint32_t *>(sm + kOffStat);
+        int4 *si = reinterpret_cast<int4 *>(sm + G::kOffIns);
+        int4 *sf = reinterpret_cast<int4 *>(sm + G::kOffFac);
+        uint32_t *ss = reinterpret_cast<uint32_t *>(sm + G::kOffStat);
         for (int i = tid; i < a.nins; i += blockDim.x) si[i] = __ldg(a.ins + i);
         for (int i = tid; i < a.nfac; i += blockDim.x) sf[i] = __ldg(a.fac + i);
-        const int nst = min(a.nstat, kT2SmemStatRows * kT2Threads);
+        const int nst = min(a.nstat, G::kStatRows * G::kThreads);
         for (int i = tid; i < nst; i += blockDim.x) ss[i] = __ldg(a.stat + i);
     }
     if (tid == 0) {
@@ -334,7 +353,7 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_tile2(float *__restrict__ sta
     }
     __syncthreads();
     if (!a.gen && tid < 32 && (uint64_t)blockIdx.x < a.ntiles)
-        issue_tile_load(a, sm, state, blockIdx.x, bar, tid);
+        issue_tile_load<K>(a, sm, state, blockIdx.x, bar, tid);
 
     uint32_t parity = 0;
     for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
@@ -360,9 +379,9 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_tile2(float *__restrict__ sta
             return;
         }
         auto hook = [&]() {
-            if (!a.gen && tid < 32 && next < a.ntiles) issue_tile_load(a, sm, state, next, bar, tid);
+            if (!a.gen && tid < 32 && next < a.ntiles) issue_tile_load<K>(a, sm, state, next, bar, tid);
         };
-        t2_run<true, true>(a, reinterpret_cast<float4 *>(state), hook);
+        t2_run<K, true, true>(a, reinterpret_cast<float4 *>(state), hook);
         parity ^= 1u;
     }
 }
@@ -448,7 +467,7 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
                     mbar_wait(bar, parity ^ 1u);
                     return;
                 }
-                t2_run<false, false>(a, nullptr, NoHook{});
+                t2_run<kT2Qubits, false, false>(a, nullptr, NoHook{});
                 fence_async_smem();
                 __syncthreads();
                 if (tid < 32) {
@@ -547,8 +566,10 @@ sv_status t2_prepare(sv_state *h) {
     note_launch();
     static bool configured = false;
     if (!configured) {
-        SV_CUDA(cudaFuncSetAttribute(k_tile2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kSmemBytes));
+        SV_CUDA(cudaFuncSetAttribute(k_tile2<13>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)Geo<13>::kSmemBytes));
+        SV_CUDA(cudaFuncSetAttribute(k_tile2<14>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)Geo<14>::kSmemBytes));
         configured = true;
     }
     return SV_OK;
@@ -583,12 +604,16 @@ sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
     a.err = h->t2_err;
     a.layx = d.layx;
     a.epi = d.epi;
+    if (p.k != 13 && p.k != 14) return fail(SV_ERR_ARG, "internal: register-stage tile of 2^%d", p.k);
+    auto kern = p.k == 13 ? k_tile2<13> : k_tile2<14>;
+    const int threads = p.k == 13 ? Geo<13>::kThreads : Geo<14>::kThreads;
+    const size_t smem = p.k == 13 ? Geo<13>::kSmemBytes : Geo<14>::kSmemBytes;
     int per_sm = 0;
-    SV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile2, kT2Threads, kSmemBytes));
+    SV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) return fail(SV_ERR_UNSUPPORTED, "register-stage tile kernel does not fit");
     const uint64_t grid = std::min<uint64_t>(a.ntiles, (uint64_t)per_sm * h->sm_count);
     const int slot = prof_begin(h);
-    k_tile2<<<(unsigned)grid, kT2Threads, kSmemBytes, h->stream>>>(reinterpret_cast<float *>(h->amps), a);
+    kern<<<(unsigned)grid, threads, smem, h->stream>>>(reinterpret_cast<float *>(h->amps), a);
     SV_CUDA(cudaGetLastError());
     note_launch();
     prof_end(h, slot, meta);

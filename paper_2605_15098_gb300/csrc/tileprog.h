@@ -27,6 +27,9 @@
 namespace sv {
 
 constexpr int kT2Qubits = 13;   // tile: 2^13 complex64 amplitudes (64 KiB)
+constexpr int kT2WideQubits = 14;  // wide tile of the CUDA-core kernel: 2^14 amplitudes,
+                                   // 512 threads, one CTA per SM
+constexpr int kT2MaxQubits = 14;
 // The programme format is written for a geometry: register bits RB, 5 lane
 // bits and 13 - RB - 5 warp bits.  The CUDA-core kernels (k_tile2, k_batch)
 // and the fused tensor-core kernel (k_tile3) both hold 32 amplitudes per

@@ -233,6 +233,27 @@ def test_c64_register_stage_kernel(sv, orc, n, chunk):
     assert np.max(np.abs(got - ref)) <= ERR64
 
 
+@pytest.mark.parametrize("n,chunk,kind", [(15, 4, "mixed"), (17, 7, "mixed"), (18, 5, "qpe"),
+                                          (20, 4, "random")])
+def test_c64_wide_tiles(sv, orc, n, chunk, kind):
+    """2^14-amplitude tiles (512 threads, one CTA per SM) on the register-stage kernel."""
+    if kind == "qpe":
+        g = C.qpe(n, seed=n)[0]
+    elif kind == "random":
+        g = C.random_circuit(n, 8, seed=n)
+    else:
+        g = mixed_circuit(n, 150, n + 3, kinds=(0, 1, 2, 3, 4, 5, 6, 7, 9, 10))
+    ref = orc.run(n, g)
+    cfg = sv.make_config(sv.SV_MODE_PARTITIONED, tile_qubits=14, chunk_qubits=chunk)
+    plan = sv.sv_plan_export(n, sv.SV_C64, g, cfg)
+    assert all(p["kernel"] == "t2" and p["t2"]["threads"] == 512 for p in plan["passes"] if p["ops"])
+    with sv.State(n, sv.SV_C64) as s:
+        s.apply(g, cfg)
+        got = s.amplitudes()
+    assert 1.0 - fidelity(ref, got) <= FID64
+    assert np.max(np.abs(got - ref)) <= ERR64
+
+
 def test_c64_register_stage_vs_generic(sv):
     """Same circuit through both tile kernels: equal up to float32 rounding."""
     n = 18
