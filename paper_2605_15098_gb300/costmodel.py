@@ -74,6 +74,8 @@ def workloads(seed: int, n_lo: int = 24, n_hi: int = 30):
 
 CONFIGS = [("t2c%d" % c, sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=c)) for c in (4, 5, 6, 7)]
 CONFIGS += [("t3c%d" % c, sv.make_config(sv.SV_MODE_FUSED, chunk_qubits=c)) for c in (4, 5, 6, 7)]
+CONFIGS += [("t2k14c%d" % c, sv.make_config(sv.SV_MODE_PARTITIONED, tile_qubits=14, chunk_qubits=c))
+            for c in (4, 7)]
 CONFIGS += [("paper", sv.make_config(sv.SV_MODE_PARTITIONED, flags=sv.SV_FLAG_PAPER_SWAP)),
             ("paper_t3", sv.make_config(sv.SV_MODE_FUSED, flags=sv.SV_FLAG_PAPER_SWAP)),
             ("generic", sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=5,
