@@ -121,6 +121,7 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
             opt.c = chunk;
             opt.merge_diag = !(c.flags & SV_FLAG_NO_DIAG_MERGE);
             opt.relabel = true;
+            opt.split_u3 = true;
             for (int q = 0; q < 64; q++) cp.phys[q] = q;
             Plan plan;
             std::vector<sv_gate> gl(it.gates, it.gates + it.m);

@@ -85,6 +85,7 @@ struct PlanOptions {
     bool merge_diag = true;
     bool relabel = true;
     bool paper = false;  // explicit LRU remaps, tile = the k lowest physical bits
+    bool split_u3 = false;  // U3 as P(phi) RY(theta) P(lambda): phases join the diagonal runs
 };
 
 // Planner options of a configuration (library defaults filled in).

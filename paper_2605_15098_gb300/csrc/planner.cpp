@@ -15,6 +15,7 @@
 // them acts on non-diagonally.  A pass takes, in program order, every ready
 // gate whose non-diagonal qubits fit in the tile's k slots.
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <string>
 #include <tuple>
@@ -30,6 +31,7 @@ struct PGate {
     int nd[2], nnd;  // qubits acted on non-diagonally
     int dq[2], ndq;  // qubits acted on diagonally
     bool diag;
+    bool counted;    // a circuit gate (false: a phase split off a U3)
     std::vector<int> deps;
 };
 
@@ -67,7 +69,8 @@ std::string emit_pass(const std::vector<PGate> &pg, const std::vector<int> &orde
     TilePass tp;
     tp.k = k;
     tp.c = c;
-    tp.ngates = (int)order.size();
+    tp.ngates = 0;
+    for (int i : order) tp.ngates += pg[i].counted ? 1 : 0;
     int slot_of[64];
     for (int q = 0; q < 64; q++) slot_of[q] = -1;
     int s = 0;
@@ -85,42 +88,91 @@ std::string emit_pass(const std::vector<PGate> &pg, const std::vector<int> &orde
         bool diag;
         std::vector<int> g;
     };
-    // Each diagonal gate moves as late as it can: into the diagonal run just
-    // before the next gate that does not commute with it (built on the
-    // reversed order, then flipped).  A run then collects the phases that
-    // feed one non-diagonal gate, as the inverse QFT writes them.
-    std::vector<Seg> segs;
-    for (auto it = order.rbegin(); it != order.rend(); ++it) {
-        const int i = *it;
+    // A diagonal gate may move anywhere between the last earlier and the
+    // first later non-diagonal gate it does not commute with (diagonal gates
+    // commute with each other).  Gap j is the place just before the j-th
+    // non-diagonal gate of the pass (gap N: the end).  The fewest runs that
+    // hold every diagonal gate is a minimum stabbing of these gap intervals:
+    // taken in order of their right ends, an interval not yet stabbed puts a
+    // run at its right end, as late as possible, so that a run collects the
+    // phases that feed one non-diagonal gate (as the inverse QFT writes them).
+    std::vector<int> nd_gates;  // non-diagonal gates of the pass, in order
+    struct Win {
+        int lo, hi, gate;
+    };
+    std::vector<Win> wins;
+    for (int i : order) {
         const PGate &p = pg[i];
         if (!p.diag) {
-            segs.push_back({false, {i}});
+            nd_gates.push_back(i);
             continue;
         }
+        const int here = (int)nd_gates.size();
         if (!opt.merge_diag) {
-            segs.push_back({true, {i}});
+            wins.push_back({here, here, i});
             continue;
         }
-        int blocker = -1;
-        for (int sgi = (int)segs.size() - 1; sgi >= 0; sgi--) {
-            if (segs[sgi].diag) continue;
-            if (!commutes_with_gate(p, pg[segs[sgi].g[0]])) {
-                blocker = sgi;
+        int lo = 0;
+        for (int j = here - 1; j >= 0; j--)
+            if (!commutes_with_gate(p, pg[nd_gates[j]])) {
+                lo = j + 1;
                 break;
+            }
+        wins.push_back({lo, -1, i});
+    }
+    const int N = (int)nd_gates.size();
+    if (opt.merge_diag) {
+        // right ends: the first later non-commuting non-diagonal gate
+        size_t w = 0;
+        int here = 0;
+        for (int i : order) {
+            if (!pg[i].diag) {
+                here++;
+                continue;
+            }
+            Win &wi = wins[w++];
+            wi.hi = N;
+            for (int j = here; j < N; j++)
+                if (!commutes_with_gate(pg[i], pg[nd_gates[j]])) {
+                    wi.hi = j;
+                    break;
+                }
+        }
+    }
+    std::vector<std::vector<int>> run_at(N + 1);
+    if (!opt.merge_diag) {
+        for (const Win &wi : wins) run_at[wi.lo].push_back(wi.gate);
+    } else {
+        std::vector<int> idx(wins.size());
+        for (size_t i = 0; i < idx.size(); i++) idx[i] = (int)i;
+        std::stable_sort(idx.begin(), idx.end(),
+                         [&](int a, int b) { return wins[a].hi < wins[b].hi; });
+        std::vector<char> is_point(N + 1, 0);
+        int point = -1;
+        for (int i : idx)
+            if (wins[i].lo > point) {
+                point = wins[i].hi;
+                is_point[point] = 1;
+            }
+        // each gate joins the latest run inside its window, next to the
+        // gate it feeds, where its phase terms most often share a factor
+        for (const Win &wi : wins) {
+            int j = wi.hi;
+            while (!is_point[j]) j--;
+            run_at[j].push_back(wi.gate);
+        }
+    }
+    std::vector<Seg> segs;
+    for (int j = 0; j <= N; j++) {
+        if (!run_at[j].empty()) {
+            if (opt.merge_diag) {
+                segs.push_back({true, run_at[j]});
+            } else {
+                for (int gi : run_at[j]) segs.push_back({true, {gi}});
             }
         }
-        int target = -1;
-        for (int sgi = blocker + 1; sgi < (int)segs.size(); sgi++)
-            if (segs[sgi].diag) {
-                target = sgi;
-                break;
-            }
-        if (target >= 0)
-            segs[target].g.push_back(i);
-        else
-            segs.push_back({true, {i}});
+        if (j < N) segs.push_back({false, {nd_gates[j]}});
     }
-    std::reverse(segs.begin(), segs.end());
 
     for (const Seg &sg : segs) {
         TileOp op{};
@@ -206,7 +258,8 @@ std::string emit_pass(const std::vector<PGate> &pg, const std::vector<int> &orde
 // pass, and a remap exchanges that global bit with the local bit that was
 // used least recently (ties: the lowest bit), updating the logical-to-physical
 // map.  A global control needs no remap: it is decided per tile.
-std::string build_plan_paper(const std::vector<sv_gate> &gates, const PlanOptions &opt, int *phys,
+std::string build_plan_paper(const std::vector<sv_gate> &gates, const std::vector<char> &counted,
+                             const PlanOptions &opt, int *phys,
                              Plan *out) {
     const int n = opt.n;
     const int k = std::min(opt.k, n);
@@ -232,7 +285,8 @@ std::string build_plan_paper(const std::vector<sv_gate> &gates, const PlanOption
         pending.clear();
         return "";
     };
-    for (const sv_gate &g : gates) {
+    for (size_t gi = 0; gi < gates.size(); gi++) {
+        const sv_gate &g = gates[gi];
         if (g.kind == SV_SWAP && opt.relabel) {
             std::swap(phys[g.target], phys[g.control]);
             inv[phys[g.target]] = g.target;
@@ -267,6 +321,7 @@ std::string build_plan_paper(const std::vector<sv_gate> &gates, const PlanOption
             out->remaps++;
         }
         PGate p{};
+        p.counted = counted[gi] != 0;
         p.g = g;
         p.g.target = phys[g.target];
         if (is_controlled_kind(g.kind) || g.kind == SV_SWAP) p.g.control = phys[g.control];
@@ -293,16 +348,68 @@ PlanOptions plan_options(int n, sv_dtype dt, const sv_config &cfg) {
     opt.relabel = !(cfg.flags & SV_FLAG_NO_RELABEL);
     opt.paper = (cfg.flags & SV_FLAG_PAPER_SWAP) != 0;
     if (opt.paper) opt.c = opt.k;  // the block is contiguous
+    opt.split_u3 = !dbl;
     return opt;
 }
 
-std::string build_plan(const std::vector<sv_gate> &gates, const PlanOptions &opt, int *phys,
+namespace {
+
+// U3(theta, phi, lambda) = P(phi) RY(theta) P(lambda) exactly, with
+// RY(theta) = [[cos(theta/2), -sin(theta/2)], [sin(theta/2), cos(theta/2)]]
+// (multiply out the definition of U3 in sv.h).  The two phases are diagonal
+// gates that merge into the neighbouring diagonal runs, and the rotation is
+// a real matrix, half the arithmetic of a general complex 2x2.
+// counted[i] is 0 for the phases, which are not gates of the circuit.
+std::vector<sv_gate> split_u3(const std::vector<sv_gate> &gates, std::vector<char> *counted) {
+    std::vector<sv_gate> out;
+    out.reserve(gates.size() + gates.size() / 2);
+    counted->clear();
+    for (const sv_gate &g : gates) {
+        if (g.kind != SV_U3) {
+            out.push_back(g);
+            counted->push_back(1);
+            continue;
+        }
+        const double c = std::cos(0.5 * g.p[0]), s = std::sin(0.5 * g.p[0]);
+        sv_gate p{};
+        p.kind = SV_P;
+        p.target = g.target;
+        p.p[0] = g.p[2];
+        if (p.p[0] != 0.0) {
+            out.push_back(p);
+            counted->push_back(0);
+        }
+        sv_gate ry{};
+        ry.kind = SV_U;
+        ry.target = g.target;
+        ry.p[0] = c;
+        ry.p[2] = -s;
+        ry.p[4] = s;
+        ry.p[6] = c;
+        out.push_back(ry);
+        counted->push_back(1);
+        p.p[0] = g.p[1];
+        if (p.p[0] != 0.0) {
+            out.push_back(p);
+            counted->push_back(0);
+        }
+    }
+    return out;
+}
+
+}  // namespace
+
+std::string build_plan(const std::vector<sv_gate> &gates_in, const PlanOptions &opt, int *phys,
                        Plan *out) {
     const int n = opt.n;
     out->passes.clear();
     out->relabels = 0;
     out->remaps = 0;
-    if (opt.paper && n > opt.k) return build_plan_paper(gates, opt, phys, out);
+    std::vector<sv_gate> split;
+    std::vector<char> counted(gates_in.size(), 1);
+    if (opt.split_u3) split = split_u3(gates_in, &counted);
+    const std::vector<sv_gate> &gates = opt.split_u3 ? split : gates_in;
+    if (opt.paper && n > opt.k) return build_plan_paper(gates, counted, opt, phys, out);
     int k = std::min(opt.k, n);
     int c = std::min(opt.c, k);
     if (n > k && k - c < 2) return "tile must leave at least two free slots (k - c >= 2)";
@@ -310,13 +417,15 @@ std::string build_plan(const std::vector<sv_gate> &gates, const PlanOptions &opt
     // 1. physical gate list, SWAPs absorbed into the map
     std::vector<PGate> pg;
     pg.reserve(gates.size());
-    for (const sv_gate &g : gates) {
+    for (size_t gi = 0; gi < gates.size(); gi++) {
+        const sv_gate &g = gates[gi];
         if (g.kind == SV_SWAP && opt.relabel) {
             std::swap(phys[g.target], phys[g.control]);
             out->relabels++;
             continue;
         }
         PGate p{};
+        p.counted = counted[gi] != 0;
         p.g = g;
         p.g.target = phys[g.target];
         if (is_controlled_kind(g.kind) || g.kind == SV_SWAP) p.g.control = phys[g.control];

@@ -275,6 +275,9 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
         if (is_gate_op(op.type)) {
             T2Ins in{};
             in.op = (int8_t)(op.type == TOP_H ? T2_H : op.type == TOP_X ? T2_X : T2_GATE);
+            if (in.op == T2_GATE && (float)op.m[1] == 0.f && (float)op.m[3] == 0.f &&
+                (float)op.m[5] == 0.f && (float)op.m[7] == 0.f)
+                in.op = T2_RGATE;  // a real matrix (a rotation RY, for one)
             in.cls = (int8_t)L.cls[op.slot];
             in.idx = (int8_t)L.pos[op.slot];
             in.ccls = T2C_NONE;
@@ -287,7 +290,7 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
                 in.ccls = T2C_GLOBAL;
                 in.cidx = (int16_t)op.cbit;
             }
-            if (in.op == T2_GATE) {
+            if (in.op == T2_GATE || in.op == T2_RGATE) {
                 T2Mat m{};
                 for (int e = 0; e < 8; e++) m.m[e] = (float)op.m[e];
                 in.aux = (int32_t)out->mats.size();
@@ -376,6 +379,18 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
             // a static row theta * (bit t of the thread) is a constant factor
             // that only the threads with bit t set apply: no table lookups
             if (!cst && lin_reg < 0 && dmask == 0) {
+                bool uniform = true;  // the same phase in every thread: a constant
+                for (int tau = 1; tau < NT && uniform; tau++) uniform = row[tau] == row[0];
+                if (uniform) {
+                    const uint32_t w0 = (uint32_t)mask;
+                    std::memcpy(&f.w0, &w0, sizeof w0);
+                    f.run = r;
+                    const double ang = 2.0 * M_PI * ((double)(int32_t)row[0] * 0x1p-32);
+                    f.c0 = (float)std::cos(ang);
+                    f.c1 = (float)std::sin(ang);
+                    out->factors.push_back(f);
+                    return;
+                }
                 for (int t = 0; t < TB; t++) {
                     const uint32_t th = row[1 << t];
                     if (!th) continue;

@@ -234,7 +234,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
             pred = (tid >> cidx) & 1;
         }
         float m[8];
-        if (op == T2_GATE) {
+        if (op == T2_GATE || op == T2_RGATE) {
             const float4 m0 = __ldg(a.mats + 2 * w.w), m1 = __ldg(a.mats + 2 * w.w + 1);
             m[0] = m0.x; m[1] = m0.y; m[2] = m0.z; m[3] = m0.w;
             m[4] = m1.x; m[5] = m1.y; m[6] = m1.z; m[7] = m1.w;
@@ -247,6 +247,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
         if (cls == T2C_LANE) {
             if (op == T2_H) lane_op2<T2_H>(r, j, pred, qm, m);
             else if (op == T2_X) lane_op2<T2_X>(r, j, pred, qm, m);
+            else if (op == T2_RGATE) lane_op2<T2_RGATE>(r, j, pred, qm, m);
             else lane_op2<T2_GATE>(r, j, pred, qm, m);
             continue;
         }
@@ -266,6 +267,14 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
                 case 2: reg_x2<2>(r, qm); break;
                 case 3: reg_x2<3>(r, qm); break;
                 default: reg_x2<4>(r, qm); break;
+            }
+        } else if (op == T2_RGATE) {
+            switch (j) {
+                case 0: reg_r2<0>(r, qm, m); break;
+                case 1: reg_r2<1>(r, qm, m); break;
+                case 2: reg_r2<2>(r, qm, m); break;
+                case 3: reg_r2<3>(r, qm, m); break;
+                default: reg_r2<4>(r, qm, m); break;
             }
         } else {
             switch (j) {

@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(kT3Threads, 1) k_tile3(float *__restrict__ sta
             } else if (ccls == T2C_THREAD) {
                 pred = (tid >> cidx) & 1;
             }
-            if (op == T2_GATE) {
+            if (op == T2_GATE || op == T2_RGATE) {  // a real matrix runs as a general one here
                 float m[8];
                 const float4 m0 = __ldg(a.mats + 2 * w.w), m1 = __ldg(a.mats + 2 * w.w + 1);
                 m[0] = m0.x; m[1] = m0.y; m[2] = m0.z; m[3] = m0.w;

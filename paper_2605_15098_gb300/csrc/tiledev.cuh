@@ -284,6 +284,35 @@ __device__ __forceinline__ void reg_u2(RegsN<NP> &r, uint32_t qm, const float *m
     }
 }
 
+// Real 2x2 [[a, b], [c, d]] = (m[0], m[2], m[4], m[6]) on register bit J: the
+// real and imaginary planes transform alike, two multiply-adds per output.
+template <int J, int NP>
+__device__ __forceinline__ void reg_r2(RegsN<NP> &r, uint32_t qm, const float *m) {
+    const float a = m[0], b = m[2], c = m[4], d = m[6];
+#pragma unroll
+    for (int g4 = 0; g4 < NP / 4; g4++) {
+        if (!((qm >> g4) & 1)) continue;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int q = 4 * g4 + i;
+            if constexpr (J >= 1) {
+                constexpr int S = 1 << (J - 1);
+                if (q & S) continue;
+                const int q1 = q | S;
+                const float2 ar = r.re[q], ai = r.im[q], br = r.re[q1], bi = r.im[q1];
+                r.re[q] = fma2(br, f2(b), mul2(ar, f2(a)));
+                r.im[q] = fma2(bi, f2(b), mul2(ai, f2(a)));
+                r.re[q1] = fma2(br, f2(d), mul2(ar, f2(c)));
+                r.im[q1] = fma2(bi, f2(d), mul2(ai, f2(c)));
+            } else {
+                const float ar = r.re[q].x, ai = r.im[q].x, br = r.re[q].y, bi = r.im[q].y;
+                r.re[q] = make_float2(a * ar + b * br, c * ar + d * br);
+                r.im[q] = make_float2(a * ai + b * bi, c * ai + d * bi);
+            }
+        }
+    }
+}
+
 // Uncontrolled (or thread-predicated) gate OP on lane bit l (see reg_h2 for qm).
 template <int OP, int NP>
 __device__ __forceinline__ void lane_op2(RegsN<NP> &r, int l, bool pred, uint32_t qm, const float *m) {
@@ -296,6 +325,9 @@ __device__ __forceinline__ void lane_op2(RegsN<NP> &r, int l, bool pred, uint32_
         csi = hi ? m[7] : m[1];
         cor = hi ? m[4] : m[2];
         coi = hi ? m[5] : m[3];
+    } else if constexpr (OP == T2_RGATE) {
+        csr = hi ? m[6] : m[0];
+        cor = hi ? m[4] : m[2];
     }
     const float sg = hi ? -1.f : 1.f;
 #pragma unroll
@@ -316,6 +348,9 @@ __device__ __forceinline__ void lane_op2(RegsN<NP> &r, int l, bool pred, uint32_
             } else if constexpr (OP == T2_X) {
                 r.re[q] = pr;
                 r.im[q] = pi;
+            } else if constexpr (OP == T2_RGATE) {
+                r.re[q] = fma2(pr, f2(cor), mul2(r.re[q], f2(csr)));
+                r.im[q] = fma2(pi, f2(cor), mul2(r.im[q], f2(csr)));
             } else {
                 const float2 nr = fma2(pi, f2(-coi), fma2(pr, f2(cor), fma2(r.im[q], f2(-csi), mul2(r.re[q], f2(csr)))));
                 const float2 ni = fma2(pr, f2(coi), fma2(pi, f2(cor), fma2(r.re[q], f2(csi), mul2(r.im[q], f2(csr)))));

@@ -16,7 +16,7 @@ MASK32 = TWO32 - 1
 TOP_GATE, TOP_GATE_CL, TOP_GATE_CG, TOP_DIAG, TOP_SWAP, TOP_H, TOP_X = range(7)
 TERM_L, TERM_LL, TERM_G, TERM_LG, TERM_GG = range(5)
 # register-stage ops (tileprog.h)
-T2_STAGE, T2_GATE, T2_H, T2_X, T2_DIAG, T2_SCALE, T2_BLOCK = range(7)
+T2_STAGE, T2_GATE, T2_H, T2_X, T2_DIAG, T2_SCALE, T2_BLOCK, T2_RGATE = range(8)
 C_NONE, C_REG, C_LANE, C_THREAD, C_GLOBAL = range(5)
 
 

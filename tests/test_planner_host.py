@@ -53,6 +53,54 @@ def test_t2_random_layers(sv, orc, chunk):
     check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=chunk), sv.SV_C64, 2e-5)
 
 
+def t2_ops(plan):
+    ops = []
+    for p in plan["passes"]:
+        if p.get("t2"):
+            ops += [ins["op"] for ins in p["t2"]["ins"]]
+    return ops
+
+
+@pytest.mark.parametrize("n,depth", [(14, 3), (16, 4)])
+def test_u3_split_real_rotations(sv, orc, n, depth):
+    """In complex64 a U3 runs as P(phi) RY(theta) P(lambda): every
+    non-diagonal step is a real rotation (planemu.T2_RGATE), the phases join
+    diagonal runs, the amplitudes still match the oracle and the pass gate
+    counts still add up to the circuit's gates."""
+    g = C.random_circuit(n, depth, 5 + n)
+    plan = check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED), sv.SV_C64, 2e-5)
+    ops = t2_ops(plan)
+    assert ops.count(planemu.T2_RGATE) == n * depth
+    assert planemu.T2_GATE not in ops
+    assert sum(p["ngates"] for p in plan["passes"]) + plan["relabels"] == len(g)
+    # complex128 keeps the general matrices
+    plan128 = check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED, tile_qubits=10,
+                                                  chunk_qubits=3), sv.SV_C128, 1e-12)
+    assert sum(p["ngates"] for p in plan128["passes"]) + plan128["relabels"] == len(g)
+
+
+def test_diagonal_runs_are_fewest():
+    """Diagonal gates go to the fewest runs their windows allow: a layer of
+    U3 on every qubit of one tile needs one run before the rotations (the
+    lambda phases) and one after them (the phi phases), not one per qubit."""
+    B.build()
+    from paper_2605_15098_gb300 import sv as S
+    def kinds(plan):
+        return [op["type"] for p in plan["passes"] for op in p["ops"]]
+
+    n = 12
+    g = C.gates([C.u3(q, 0.3 + q, 1.1, 2.2) for q in range(n)])
+    plan = S.sv_plan_export(n, S.SV_C64, g, S.make_config(S.SV_MODE_PARTITIONED))
+    assert len(plan["passes"]) == 1
+    assert kinds(plan).count(planemu.TOP_DIAG) == 2
+    assert kinds(plan).count(planemu.TOP_GATE) == n
+    # QFT: one run feeds each Hadamard after the first
+    t = 10
+    g = C.gates(C.qft(t))
+    plan = S.sv_plan_export(t, S.SV_C64, g, S.make_config(S.SV_MODE_PARTITIONED))
+    assert kinds(plan).count(planemu.TOP_DIAG) == t - 1
+
+
 @pytest.mark.parametrize("flags", [0, 1, 4, 5])
 def test_generic_plan(sv, orc, flags):
     n = 13
