@@ -373,6 +373,7 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
         in.op = T2_DIAG;
         in.e0 = (int16_t)out->factors.size();
         const size_t nfac0 = out->factors.size();
+        std::map<size_t, uint32_t> cturn;  // phase (turns / 2^32) of each constant factor
         auto add_thread_factor = [&](int mask, bool cst, int lin_reg, int dmask,
                                      const uint32_t *row) {
             T2Factor f{};
@@ -388,6 +389,7 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
                     const double ang = 2.0 * M_PI * ((double)(int32_t)row[0] * 0x1p-32);
                     f.c0 = (float)std::cos(ang);
                     f.c1 = (float)std::sin(ang);
+                    cturn[out->factors.size()] = row[0];
                     out->factors.push_back(f);
                     return;
                 }
@@ -404,6 +406,7 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
                     const double ang = 2.0 * M_PI * ((double)(int32_t)th * 0x1p-32);
                     f.c0 = (float)std::cos(ang);
                     f.c1 = (float)std::sin(ang);
+                    cturn[out->factors.size()] = th;
                     out->factors.push_back(f);
                     return;
                 }
@@ -458,7 +461,60 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
             const double ang = 2.0 * M_PI * ((double)(int32_t)kv.second * 0x1p-32);
             f.c0 = (float)std::cos(ang);
             f.c1 = (float)std::sin(ang);
+            cturn[out->factors.size()] = kv.second;
             out->factors.push_back(f);
+        }
+        if (!fused) {
+            // Constant factors with the same thread predicate (or none) merge
+            // into one 32-entry phase table over the register index: one
+            // sweep over the thread's amplitudes instead of one per factor.
+            // Each entry is formed from the summed 32-bit phase in FP64 and
+            // rounded once.
+            std::map<int, std::vector<size_t>> group;  // predicate -> factors
+            for (size_t i = nfac0; i < out->factors.size(); i++) {
+                const uint32_t w0 = (uint32_t)out->factors[i].w0;
+                if (!(w0 & 0x100u)) group[(int)((w0 >> 10) & 0xfu)].push_back(i);
+            }
+            std::vector<char> merged(out->factors.size() - nfac0, 0);
+            std::vector<std::pair<size_t, T2Factor>> tables;  // position, table factor
+            for (auto &g : group) {
+                if (g.second.size() < 2) continue;
+                uint32_t u[32] = {};
+                for (size_t i : g.second) {
+                    const int mask = (int)((uint32_t)out->factors[i].w0 & 0xffu);
+                    for (int x = 0; x < 32; x++)
+                        if ((x & mask) == mask) u[x] += cturn.at(i);
+                    merged[i - nfac0] = 1;
+                }
+                const int32_t m0 = (int32_t)out->mats.size();
+                float tab[64];
+                for (int x = 0; x < 32; x++) {
+                    const double ang = 2.0 * M_PI * ((double)(int32_t)u[x] * 0x1p-32);
+                    tab[4 * (x >> 1) + (x & 1)] = (float)std::cos(ang);
+                    tab[4 * (x >> 1) + 2 + (x & 1)] = (float)std::sin(ang);
+                }
+                for (int m = 0; m < 8; m++) {
+                    T2Mat tm{};
+                    for (int e = 0; e < 8; e++) tm.m[e] = tab[8 * m + e];
+                    out->mats.push_back(tm);
+                }
+                T2Factor f{};
+                const uint32_t w0 = kFacTable | ((uint32_t)g.first << 10);
+                std::memcpy(&f.w0, &w0, sizeof w0);
+                f.run = r;
+                std::memcpy(&f.c0, &m0, sizeof m0);
+                tables.push_back({g.second.front(), f});
+            }
+            if (!tables.empty()) {
+                std::vector<T2Factor> keep;
+                for (size_t i = nfac0; i < out->factors.size(); i++) {
+                    for (auto &t : tables)
+                        if (t.first == i) keep.push_back(t.second);
+                    if (!merged[i - nfac0]) keep.push_back(out->factors[i]);
+                }
+                out->factors.resize(nfac0);
+                out->factors.insert(out->factors.end(), keep.begin(), keep.end());
+            }
         }
         if (fused) {
             // move this run's thread-dependent factors into `pre` (before the

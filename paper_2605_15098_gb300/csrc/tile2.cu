@@ -90,7 +90,12 @@ struct Layout2 {
     }
 };
 
-template <int K, bool kDirect, bool kSmemProg, typename Hook>
+// Gate kinds an instantiation carries besides H and the diagonal runs (the
+// host launches the smallest one that covers a pass's programme: every gate
+// path in the loop costs registers and instructions in all the others).
+constexpr int kFeatX = 1, kFeatR = 2, kFeatU = 4, kFeatAll = 7;
+
+template <int K, bool kDirect, bool kSmemProg, int F, typename Hook>
 __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hook) {
     using G = Geo<K>;
     // the programme: copied to shared memory by k_tile2, read from global by k_batch
@@ -170,36 +175,27 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
         if (op == T2_DIAG) {
             const int e0 = (int16_t)(w.z & 0xffff), e1 = (int16_t)(w.z >> 16);
             if (e0 >= e1) continue;
-            // software pipeline: the next factor's record and static phase
-            // load while this one is applied
             // static phase rows beyond the shared-memory copy stay in global memory
             auto stat_at = [&](int row) -> uint32_t {
                 if (kSmemProg && row >= G::kStatRows) return __ldg(a.stat + row * G::kThreads + tid);
                 return stat[row * G::kThreads + tid];
             };
-            int4 fd = fac[e0];
-            uint32_t sv = ((uint32_t)fd.x & 0x100u) ? stat_at(fd.z) : 0u;
             for (int e = e0; e < e1; e++) {
-                int4 fdn = fd;
-                uint32_t svn = 0u;
-                if (e + 1 < e1) {
-                    fdn = fac[e + 1];
-                    if ((uint32_t)fdn.x & 0x100u) svn = stat_at(fdn.z);
-                }
+                const int4 fd = fac[e];
                 const uint32_t w0 = (uint32_t)fd.x;
                 const int run = fd.y;
                 const int pb = (int)((w0 >> 10) & 0xfu);  // thread-bit predicate of a constant
-                float fr, fi;
-                if (pb && !((tid >> (pb - 1)) & 1)) {  // not this thread's factor
-                    fd = fdn;
-                    sv = svn;
+                if (pb && !((tid >> (pb - 1)) & 1)) continue;  // not this thread's factor
+                if (w0 & kFacTable) {
+                    apply_table(r, a.mats + 2 * fd.z, ~((uint32_t)w.y >> 16));
                     continue;
                 }
+                float fr, fi;
                 if (!(w0 & 0x100u)) {
                     fr = __int_as_float(fd.z);
                     fi = __int_as_float(fd.w);
                 } else {
-                    uint32_t u = sv;
+                    uint32_t u = stat_at(fd.z);
                     if (w0 & 0x200u) u += cst[run];
                     const int lr = (int)((w0 >> kFacLinShift) & 0x1fu) - 1;
                     if (lr >= 0) u += lin[run * 16 + lr];
@@ -217,8 +213,6 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
                     fi = ff.y;
                 }
                 apply_factor_any(r, (int)(w0 & 0xffu), fr, fi);
-                fd = fdn;
-                sv = svn;
             }
             continue;
         }
@@ -233,26 +227,14 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
         } else if (ccls == T2C_THREAD) {
             pred = (tid >> cidx) & 1;
         }
-        float m[8];
-        if (op == T2_GATE || op == T2_RGATE) {
-            const float4 m0 = __ldg(a.mats + 2 * w.w), m1 = __ldg(a.mats + 2 * w.w + 1);
-            m[0] = m0.x; m[1] = m0.y; m[2] = m0.z; m[3] = m0.w;
-            m[4] = m1.x; m[5] = m1.y; m[6] = m1.z; m[7] = m1.w;
-        } else {
-#pragma unroll
-            for (int e = 0; e < 8; e++) m[e] = 0.f;
-        }
         // all ones at run time (see reg_h2); the instruction word's pad field is zero
         const uint32_t qm = ~((uint32_t)w.y >> 16);
-        if (cls == T2C_LANE) {
-            if (op == T2_H) lane_op2<T2_H>(r, j, pred, qm, m);
-            else if (op == T2_X) lane_op2<T2_X>(r, j, pred, qm, m);
-            else if (op == T2_RGATE) lane_op2<T2_RGATE>(r, j, pred, qm, m);
-            else lane_op2<T2_GATE>(r, j, pred, qm, m);
-            continue;
-        }
-        if (!pred) continue;
         if (op == T2_H) {
+            if (cls == T2C_LANE) {
+                lane_op2<T2_H>(r, j, pred, qm, nullptr);
+                continue;
+            }
+            if (!pred) continue;
             switch (j) {
                 case 0: reg_h2<0>(r, qm); break;
                 case 1: reg_h2<1>(r, qm); break;
@@ -260,29 +242,65 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
                 case 3: reg_h2<3>(r, qm); break;
                 default: reg_h2<4>(r, qm); break;
             }
-        } else if (op == T2_X) {
-            switch (j) {
-                case 0: reg_x2<0>(r, qm); break;
-                case 1: reg_x2<1>(r, qm); break;
-                case 2: reg_x2<2>(r, qm); break;
-                case 3: reg_x2<3>(r, qm); break;
-                default: reg_x2<4>(r, qm); break;
+            continue;
+        }
+        if constexpr ((F & kFeatX) != 0) {
+            if (op == T2_X) {
+                if (cls == T2C_LANE) {
+                    lane_op2<T2_X>(r, j, pred, qm, nullptr);
+                    continue;
+                }
+                if (!pred) continue;
+                switch (j) {
+                    case 0: reg_x2<0>(r, qm); break;
+                    case 1: reg_x2<1>(r, qm); break;
+                    case 2: reg_x2<2>(r, qm); break;
+                    case 3: reg_x2<3>(r, qm); break;
+                    default: reg_x2<4>(r, qm); break;
+                }
+                continue;
             }
-        } else if (op == T2_RGATE) {
-            switch (j) {
-                case 0: reg_r2<0>(r, qm, m); break;
-                case 1: reg_r2<1>(r, qm, m); break;
-                case 2: reg_r2<2>(r, qm, m); break;
-                case 3: reg_r2<3>(r, qm, m); break;
-                default: reg_r2<4>(r, qm, m); break;
+        }
+        if constexpr ((F & (kFeatR | kFeatU)) != 0) {
+            float m[8];
+            {
+                const float4 m0 = __ldg(a.mats + 2 * w.w), m1 = __ldg(a.mats + 2 * w.w + 1);
+                m[0] = m0.x; m[1] = m0.y; m[2] = m0.z; m[3] = m0.w;
+                m[4] = m1.x; m[5] = m1.y; m[6] = m1.z; m[7] = m1.w;
             }
-        } else {
-            switch (j) {
-                case 0: reg_u2<0>(r, qm, m); break;
-                case 1: reg_u2<1>(r, qm, m); break;
-                case 2: reg_u2<2>(r, qm, m); break;
-                case 3: reg_u2<3>(r, qm, m); break;
-                default: reg_u2<4>(r, qm, m); break;
+            if constexpr ((F & kFeatR) != 0) {
+                if (op == T2_RGATE) {
+                    if (cls == T2C_LANE) {
+                        lane_op2<T2_RGATE>(r, j, pred, qm, m);
+                        continue;
+                    }
+                    if (!pred) continue;
+                    switch (j) {
+                        case 0: reg_r2<0>(r, qm, m); break;
+                        case 1: reg_r2<1>(r, qm, m); break;
+                        case 2: reg_r2<2>(r, qm, m); break;
+                        case 3: reg_r2<3>(r, qm, m); break;
+                        default: reg_r2<4>(r, qm, m); break;
+                    }
+                    continue;
+                }
+            }
+            if constexpr ((F & kFeatU) != 0) {
+                if (op == T2_GATE) {
+                    if (cls == T2C_LANE) {
+                        lane_op2<T2_GATE>(r, j, pred, qm, m);
+                        continue;
+                    }
+                    if (!pred) continue;
+                    switch (j) {
+                        case 0: reg_u2<0>(r, qm, m); break;
+                        case 1: reg_u2<1>(r, qm, m); break;
+                        case 2: reg_u2<2>(r, qm, m); break;
+                        case 3: reg_u2<3>(r, qm, m); break;
+                        default: reg_u2<4>(r, qm, m); break;
+                    }
+                    continue;
+                }
             }
         }
     }
@@ -334,7 +352,7 @@ __device__ __forceinline__ void issue_tile_load(const T2Args &a, unsigned char *
 // the rest of tile i's programme and its write-back, which goes from
 // registers straight to the global state (16-byte stores; lanes 0..7 cover
 // tile bits 1..3, so a quarter-warp writes 128 contiguous bytes).
-template <int K>
+template <int K, int F>
 __global__ void __launch_bounds__(Geo<K>::kThreads, K == kT2Qubits ? 2 : 1)
     k_tile2(float *__restrict__ state, const T2Args a) {
     using G = Geo<K>;
@@ -390,7 +408,7 @@ __global__ void __launch_bounds__(Geo<K>::kThreads, K == kT2Qubits ? 2 : 1)
         auto hook = [&]() {
             if (!a.gen && tid < 32 && next < a.ntiles) issue_tile_load<K>(a, sm, state, next, bar, tid);
         };
-        t2_run<K, true, true>(a, reinterpret_cast<float4 *>(state), hook);
+        t2_run<K, true, true, F>(a, reinterpret_cast<float4 *>(state), hook);
         parity ^= 1u;
     }
 }
@@ -476,7 +494,7 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
                     mbar_wait(bar, parity ^ 1u);
                     return;
                 }
-                t2_run<kT2Qubits, false, false>(a, nullptr, NoHook{});
+                t2_run<kT2Qubits, false, false, kFeatAll>(a, nullptr, NoHook{});
                 fence_async_smem();
                 __syncthreads();
                 if (tid < 32) {
@@ -575,9 +593,10 @@ sv_status t2_prepare(sv_state *h) {
     note_launch();
     static bool configured = false;
     if (!configured) {
-        SV_CUDA(cudaFuncSetAttribute(k_tile2<13>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)Geo<13>::kSmemBytes));
-        SV_CUDA(cudaFuncSetAttribute(k_tile2<14>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        for (auto kern : {k_tile2<13, 0>, k_tile2<13, kFeatX>, k_tile2<13, kFeatR>, k_tile2<13, kFeatAll>})
+            SV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Geo<13>::kSmemBytes));
+        SV_CUDA(cudaFuncSetAttribute(k_tile2<14, kFeatAll>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)Geo<14>::kSmemBytes));
         configured = true;
     }
@@ -614,7 +633,16 @@ sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
     a.layx = d.layx;
     a.epi = d.epi;
     if (p.k != 13 && p.k != 14) return fail(SV_ERR_ARG, "internal: register-stage tile of 2^%d", p.k);
-    auto kern = p.k == 13 ? k_tile2<13> : k_tile2<14>;
+    // the smallest instantiation whose gate kinds cover the programme
+    int need = 0;
+    for (const T2Ins &in : p.ins)
+        need |= in.op == T2_X ? kFeatX : in.op == T2_RGATE ? kFeatR : in.op == T2_GATE ? kFeatU : 0;
+    auto kern = k_tile2<14, kFeatAll>;
+    if (p.k == 13)
+        kern = need == 0 ? k_tile2<13, 0>
+             : need == kFeatX ? k_tile2<13, kFeatX>
+             : need == kFeatR ? k_tile2<13, kFeatR>
+                              : k_tile2<13, kFeatAll>;
     const int threads = p.k == 13 ? Geo<13>::kThreads : Geo<14>::kThreads;
     const size_t smem = p.k == 13 ? Geo<13>::kSmemBytes : Geo<14>::kSmemBytes;
     int per_sm = 0;

@@ -482,6 +482,27 @@ __device__ __forceinline__ void apply_factor(R &r, float fr, float fi) {
     }
 }
 
+// Multiply amplitude x of the register index by entry x of a 32-entry
+// constant phase table: T[q] = (re[2q], re[2q+1], im[2q], im[2q+1]).  `qm` as
+// in reg_h2 (all ones at run time; bounds the loads kept in flight).
+template <int NP>
+__device__ __forceinline__ void apply_table(RegsN<NP> &r, const float4 *__restrict__ T, uint32_t qm) {
+#pragma unroll
+    for (int g4 = 0; g4 < NP / 4; g4++) {
+        if (!((qm >> g4) & 1)) continue;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int q = 4 * g4 + i;
+            const float4 t = __ldg(T + q);
+            const float2 tr = make_float2(t.x, t.y), ti = make_float2(t.z, t.w);
+            const float2 nr = fma2(r.im[q], make_float2(-t.z, -t.w), mul2(r.re[q], tr));
+            const float2 ni = fma2(r.im[q], tr, mul2(r.re[q], ti));
+            r.re[q] = nr;
+            r.im[q] = ni;
+        }
+    }
+}
+
 template <typename R>
 __device__ __forceinline__ void apply_factor_any(R &r, int mask, float fr, float fi) {
     switch (mask) {

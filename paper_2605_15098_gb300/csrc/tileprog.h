@@ -123,10 +123,16 @@ struct T2Mat {
 //   w0 bits 14..18: 1 + tile bit whose per-tile coefficient lin[run][tb] is added, 0 = none
 //   w0 bits 19..27: thread bits t whose per-tile coefficient lin[run][tile bit of t] is added
 //                   when thread bit t is set
+//   w0 bit 28:      phase table: the amplitude with register index x (bits of
+//                   the register bits) is multiplied by entry x of the 32-entry
+//                   constant table starting at matrix record c0 (as an int), which
+//                   holds, per packed pair q, (re[2q], re[2q+1], im[2q], im[2q+1]);
+//                   bits 10..13 as for a constant, mask bits 0
 // A per-thread phase starts from row c0 of the host table of per-thread
 // static phases (one entry per thread of the geometry).
 constexpr int kFacLinShift = 14;
 constexpr int kFacDynShift = 19;
+constexpr uint32_t kFacTable = 1u << 28;
 struct T2Factor {
     int32_t w0;
     int32_t run;

@@ -166,6 +166,19 @@ def run_t2_pass(state, p):
             if op == T2_DIAG:
                 for f in t2["factors"][ins["e0"]:ins["e1"]]:
                     w0 = f["w0"]
+                    if (w0 >> 28) & 1:  # 32-entry constant phase table (tileprog.h)
+                        pb = (w0 >> 10) & 0xF
+                        fl = np.asarray(t2["mats"][f["row"]:f["row"] + 8], dtype=np.float64).reshape(-1)
+                        xs = np.arange(32)
+                        tab = fl[4 * (xs >> 1) + (xs & 1)] + 1j * fl[4 * (xs >> 1) + 2 + (xs & 1)]
+                        xr = np.zeros(t.size, dtype=np.int64)
+                        for j in range(rb):
+                            xr |= ((loc >> reg[j]) & 1) << j
+                        fac = tab[xr]
+                        if pb:
+                            fac = np.where(((tid >> (pb - 1)) & 1) == 1, fac, 1.0)
+                        t *= fac
+                        continue
                     mask = w0 & 0xFF
                     sel = np.ones(t.size, dtype=bool)
                     for j in range(rb):
