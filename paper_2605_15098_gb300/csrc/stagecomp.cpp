@@ -278,6 +278,21 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
             if (in.op == T2_GATE && (float)op.m[1] == 0.f && (float)op.m[3] == 0.f &&
                 (float)op.m[5] == 0.f && (float)op.m[7] == 0.f)
                 in.op = T2_RGATE;  // a real matrix (a rotation RY, for one)
+            // an uncontrolled rotation [[c, -s], [s, c]] on a register bit runs
+            // as three shears; with c < 0 it is -1 times the rotation by c' = -c,
+            // s' = -s, and the sign joins the pass's closing scale
+            double rot_t = 0.0, rot_s = 0.0;
+            if (!fused && in.op == T2_RGATE && op.type == TOP_GATE && L.cls[op.slot] == T2C_REG) {
+                const double c = op.m[0], s = op.m[4];
+                if (op.m[6] == c && op.m[2] == -s && std::fabs(c * c + s * s - 1.0) <= 1e-12) {
+                    const bool flip = c < 0.0;
+                    const double cc = flip ? -c : c, ss = flip ? -s : s;
+                    rot_t = -ss / (1.0 + cc);
+                    rot_s = ss;
+                    if (flip) out->sign_flips++;
+                    in.op = T2_ROT;
+                }
+            }
             in.cls = (int8_t)L.cls[op.slot];
             in.idx = (int8_t)L.pos[op.slot];
             in.ccls = T2C_NONE;
@@ -290,7 +305,13 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
                 in.ccls = T2C_GLOBAL;
                 in.cidx = (int16_t)op.cbit;
             }
-            if (in.op == T2_GATE || in.op == T2_RGATE) {
+            if (in.op == T2_ROT) {
+                T2Mat m{};
+                m.m[0] = (float)rot_t;
+                m.m[1] = (float)rot_s;
+                in.aux = (int32_t)out->mats.size();
+                out->mats.push_back(m);
+            } else if (in.op == T2_GATE || in.op == T2_RGATE) {
                 T2Mat m{};
                 for (int e = 0; e < 8; e++) m.m[e] = (float)op.m[e];
                 in.aux = (int32_t)out->mats.size();
@@ -467,9 +488,10 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
         if (!fused) {
             // Constant factors with the same thread predicate (or none) merge
             // into one 32-entry phase table over the register index: one
-            // sweep over the thread's amplitudes instead of one per factor.
-            // Each entry is formed from the summed 32-bit phase in FP64 and
-            // rounded once.
+            // sweep over the thread's amplitudes instead of one per factor,
+            // and the kernel's per-factor path keeps only per-thread phases
+            // (masks of at most one register bit).  Each entry is formed from
+            // the summed 32-bit phase in FP64 and rounded once.
             std::map<int, std::vector<size_t>> group;  // predicate -> factors
             for (size_t i = nfac0; i < out->factors.size(); i++) {
                 const uint32_t w0 = (uint32_t)out->factors[i].w0;
@@ -478,7 +500,6 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
             std::vector<char> merged(out->factors.size() - nfac0, 0);
             std::vector<std::pair<size_t, T2Factor>> tables;  // position, table factor
             for (auto &g : group) {
-                if (g.second.size() < 2) continue;
                 uint32_t u[32] = {};
                 for (size_t i : g.second) {
                     const int mask = (int)((uint32_t)out->factors[i].w0 & 0xffu);
@@ -579,8 +600,8 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
         }
         for (int j = 0; j < 4; j++) out->epi.g[j] = 1 + j < RB ? w(st.tb[1 + j]) : 0;
     }
-    if (out->n_h || fused) {  // fused passes always end with a scale (norm correction)
-        const double s = std::pow(2.0, -0.5 * out->n_h);
+    if (out->n_h || fused || (out->sign_flips & 1)) {  // fused passes always end with a scale
+        const double s = std::pow(2.0, -0.5 * out->n_h) * ((out->sign_flips & 1) ? -1.0 : 1.0);
         const float hi = (float)s;
         T2Mat m{};
         m.m[0] = hi;

@@ -19,6 +19,7 @@ struct T2Pass {
     int ngates = 0;
     int nruns = 0;
     int n_h = 0;                    // unnormalised Hadamards (2^(-n_h/2) at the end)
+    int sign_flips = 0;             // rotations run as -1 times a shear product (sign at the end)
     int last_stage = -1;            // index in `ins` of the last T2_STAGE
     std::vector<T2Ins> ins;
     std::vector<T2Stage> stages;

@@ -190,11 +190,8 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
                     apply_table(r, a.mats + 2 * fd.z, ~((uint32_t)w.y >> 16));
                     continue;
                 }
-                float fr, fi;
-                if (!(w0 & 0x100u)) {
-                    fr = __int_as_float(fd.z);
-                    fi = __int_as_float(fd.w);
-                } else {
+                // per-thread phase (constants are tables, see the stage compiler)
+                {
                     uint32_t u = stat_at(fd.z);
                     if (w0 & 0x200u) u += cst[run];
                     const int lr = (int)((w0 >> kFacLinShift) & 0x1fu) - 1;
@@ -209,10 +206,8 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
                     const float2 ff = cx(cx(tab[u >> 24], tab[kTabN + ((u >> 16) & 255u)]),
                                          cx(tab[2 * kTabN + ((u >> 8) & 255u)],
                                             tab[3 * kTabN + (u & 255u)]));
-                    fr = ff.x;
-                    fi = ff.y;
+                    apply_factor_bit(r, (int)(w0 & 0xffu), ff.x, ff.y);
                 }
-                apply_factor_any(r, (int)(w0 & 0xffu), fr, fi);
             }
             continue;
         }
@@ -231,7 +226,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
         const uint32_t qm = ~((uint32_t)w.y >> 16);
         if (op == T2_H) {
             if (cls == T2C_LANE) {
-                lane_op2<T2_H>(r, j, pred, qm, nullptr);
+                if (ccls == T2C_THREAD) lane_op3<T2_H, true>(r, j, pred, qm, nullptr); else lane_op3<T2_H, false>(r, j, pred, qm, nullptr);
                 continue;
             }
             if (!pred) continue;
@@ -247,7 +242,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
         if constexpr ((F & kFeatX) != 0) {
             if (op == T2_X) {
                 if (cls == T2C_LANE) {
-                    lane_op2<T2_X>(r, j, pred, qm, nullptr);
+                    if (ccls == T2C_THREAD) lane_op3<T2_X, true>(r, j, pred, qm, nullptr); else lane_op3<T2_X, false>(r, j, pred, qm, nullptr);
                     continue;
                 }
                 if (!pred) continue;
@@ -269,9 +264,19 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
                 m[4] = m1.x; m[5] = m1.y; m[6] = m1.z; m[7] = m1.w;
             }
             if constexpr ((F & kFeatR) != 0) {
+                if (op == T2_ROT) {  // uncontrolled, on a register bit (stage compiler)
+                    switch (j) {
+                        case 0: reg_rot<0>(r, qm, m); break;
+                        case 1: reg_rot<1>(r, qm, m); break;
+                        case 2: reg_rot<2>(r, qm, m); break;
+                        case 3: reg_rot<3>(r, qm, m); break;
+                        default: reg_rot<4>(r, qm, m); break;
+                    }
+                    continue;
+                }
                 if (op == T2_RGATE) {
                     if (cls == T2C_LANE) {
-                        lane_op2<T2_RGATE>(r, j, pred, qm, m);
+                        if (ccls == T2C_THREAD) lane_op3<T2_RGATE, true>(r, j, pred, qm, m); else lane_op3<T2_RGATE, false>(r, j, pred, qm, m);
                         continue;
                     }
                     if (!pred) continue;
@@ -288,7 +293,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
             if constexpr ((F & kFeatU) != 0) {
                 if (op == T2_GATE) {
                     if (cls == T2C_LANE) {
-                        lane_op2<T2_GATE>(r, j, pred, qm, m);
+                        if (ccls == T2C_THREAD) lane_op3<T2_GATE, true>(r, j, pred, qm, m); else lane_op3<T2_GATE, false>(r, j, pred, qm, m);
                         continue;
                     }
                     if (!pred) continue;
@@ -636,7 +641,10 @@ sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
     // the smallest instantiation whose gate kinds cover the programme
     int need = 0;
     for (const T2Ins &in : p.ins)
-        need |= in.op == T2_X ? kFeatX : in.op == T2_RGATE ? kFeatR : in.op == T2_GATE ? kFeatU : 0;
+        need |= in.op == T2_X                             ? kFeatX
+                : (in.op == T2_RGATE || in.op == T2_ROT) ? kFeatR
+                : in.op == T2_GATE                        ? kFeatU
+                                                          : 0;
     auto kern = k_tile2<14, kFeatAll>;
     if (p.k == 13)
         kern = need == 0 ? k_tile2<13, 0>

@@ -208,6 +208,8 @@ __device__ __forceinline__ void reg_u(Regs &r, int jc, const float *m) {
 // is all ones at run time; testing one of its bits per group of four packed
 // pairs keeps each group a separate block, which bounds how many pairs the
 // compiler keeps in flight (and so the register pressure).
+// The butterfly runs in place, b' = a - b then a' = 2a - b', so no register
+// of the pair needs a copy; a' equals a + b up to one extra rounding of a - b.
 template <int J, int NP>
 __device__ __forceinline__ void reg_h2(RegsN<NP> &r, uint32_t qm) {
 #pragma unroll
@@ -220,9 +222,10 @@ __device__ __forceinline__ void reg_h2(RegsN<NP> &r, uint32_t qm) {
                 constexpr int S = 1 << (J - 1);
                 if (q & S) continue;
                 const int q1 = q | S;
-                const float2 ar = r.re[q], ai = r.im[q], br = r.re[q1], bi = r.im[q1];
-                r.re[q] = add2(ar, br); r.im[q] = add2(ai, bi);
-                r.re[q1] = sub2(ar, br); r.im[q1] = sub2(ai, bi);
+                r.re[q1] = sub2(r.re[q], r.re[q1]);
+                r.im[q1] = sub2(r.im[q], r.im[q1]);
+                r.re[q] = fma2(r.re[q], f2(2.f), make_float2(-r.re[q1].x, -r.re[q1].y));
+                r.im[q] = fma2(r.im[q], f2(2.f), make_float2(-r.im[q1].x, -r.im[q1].y));
             } else {
                 const float2 a = r.re[q], b = r.im[q];
                 r.re[q] = make_float2(a.x + a.y, a.x - a.y);
@@ -284,6 +287,42 @@ __device__ __forceinline__ void reg_u2(RegsN<NP> &r, uint32_t qm, const float *m
     }
 }
 
+// Rotation [[c, -s], [s, c]] (c >= 0) on register bit J as three in-place
+// shears: a += t b, b += s a, a += t b with t = -s / (1 + c) = (c - 1) / s
+// (m[0] = t, m[1] = s).  Their product is the rotation exactly; each shear
+// is one multiply-add per plane and no register of the pair is copied.
+template <int J, int NP>
+__device__ __forceinline__ void reg_rot(RegsN<NP> &r, uint32_t qm, const float *m) {
+    const float t = m[0], s = m[1];
+#pragma unroll
+    for (int g4 = 0; g4 < NP / 4; g4++) {
+        if (!((qm >> g4) & 1)) continue;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int q = 4 * g4 + i;
+            if constexpr (J >= 1) {
+                constexpr int S = 1 << (J - 1);
+                if (q & S) continue;
+                const int q1 = q | S;
+                r.re[q] = fma2(r.re[q1], f2(t), r.re[q]);
+                r.im[q] = fma2(r.im[q1], f2(t), r.im[q]);
+                r.re[q1] = fma2(r.re[q], f2(s), r.re[q1]);
+                r.im[q1] = fma2(r.im[q], f2(s), r.im[q1]);
+                r.re[q] = fma2(r.re[q1], f2(t), r.re[q]);
+                r.im[q] = fma2(r.im[q1], f2(t), r.im[q]);
+            } else {
+                float2 &x = r.re[q], &y = r.im[q];
+                x.x = fmaf(x.y, t, x.x);
+                y.x = fmaf(y.y, t, y.x);
+                x.y = fmaf(x.x, s, x.y);
+                y.y = fmaf(y.x, s, y.y);
+                x.x = fmaf(x.y, t, x.x);
+                y.x = fmaf(y.y, t, y.x);
+            }
+        }
+    }
+}
+
 // Real 2x2 [[a, b], [c, d]] = (m[0], m[2], m[4], m[6]) on register bit J: the
 // real and imaginary planes transform alike, two multiply-adds per output.
 template <int J, int NP>
@@ -313,10 +352,18 @@ __device__ __forceinline__ void reg_r2(RegsN<NP> &r, uint32_t qm, const float *m
     }
 }
 
-// Uncontrolled (or thread-predicated) gate OP on lane bit l (see reg_h2 for qm).
-template <int OP, int NP>
-__device__ __forceinline__ void lane_op2(RegsN<NP> &r, int l, bool pred, uint32_t qm, const float *m) {
-    const unsigned FULL = 0xffffffffu;
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int xm) {
+    double d;
+    memcpy(&d, &v, 8);
+    d = __shfl_xor_sync(0xffffffffu, d, xm);
+    float2 o;
+    memcpy(&o, &d, 8);
+    return o;
+}
+
+// Uncontrolled (kPred false) or thread-predicated gate OP on lane bit l (see reg_h2 for qm).
+template <int OP, bool kPred, int NP>
+__device__ __forceinline__ void lane_op3(RegsN<NP> &r, int l, bool pred, uint32_t qm, const float *m) {
     const int xm = 1 << l;
     const bool hi = (threadIdx.x >> l) & 1;
     float csr = 0.f, csi = 0.f, cor = 0.f, coi = 0.f;
@@ -328,27 +375,34 @@ __device__ __forceinline__ void lane_op2(RegsN<NP> &r, int l, bool pred, uint32_
     } else if constexpr (OP == T2_RGATE) {
         csr = hi ? m[6] : m[0];
         cor = hi ? m[4] : m[2];
+    } else if constexpr (OP == T2_H) {
+        csr = hi ? -1.f : 1.f;
+        cor = 1.f;
+    } else {
+        cor = 1.f;
     }
-    const float sg = hi ? -1.f : 1.f;
+    if constexpr (kPred) {  // an unselected thread keeps its value: self 1, partner 0
+        if (!pred) {
+            csr = 1.f;
+            csi = 0.f;
+            cor = 0.f;
+            coi = 0.f;
+        }
+    }
 #pragma unroll
     for (int g4 = 0; g4 < NP / 4; g4++) {
         if (!((qm >> g4) & 1)) continue;
 #pragma unroll
         for (int i = 0; i < 4; i++) {
             const int q = 4 * g4 + i;
-            float2 pr, pi;
-            pr.x = __shfl_xor_sync(FULL, r.re[q].x, xm);
-            pr.y = __shfl_xor_sync(FULL, r.re[q].y, xm);
-            pi.x = __shfl_xor_sync(FULL, r.im[q].x, xm);
-            pi.y = __shfl_xor_sync(FULL, r.im[q].y, xm);
-            if (!pred) continue;
-            if constexpr (OP == T2_H) {
-                r.re[q] = fma2(r.re[q], f2(sg), pr);
-                r.im[q] = fma2(r.im[q], f2(sg), pi);
-            } else if constexpr (OP == T2_X) {
+            const float2 pr = shfl_xor2(r.re[q], xm), pi = shfl_xor2(r.im[q], xm);
+            if constexpr (OP == T2_H && !kPred) {
+                r.re[q] = fma2(r.re[q], f2(csr), pr);
+                r.im[q] = fma2(r.im[q], f2(csr), pi);
+            } else if constexpr (OP == T2_X && !kPred) {
                 r.re[q] = pr;
                 r.im[q] = pi;
-            } else if constexpr (OP == T2_RGATE) {
+            } else if constexpr (OP != T2_GATE) {
                 r.re[q] = fma2(pr, f2(cor), mul2(r.re[q], f2(csr)));
                 r.im[q] = fma2(pi, f2(cor), mul2(r.im[q], f2(csr)));
             } else {
@@ -500,6 +554,19 @@ __device__ __forceinline__ void apply_table(RegsN<NP> &r, const float4 *__restri
             r.re[q] = nr;
             r.im[q] = ni;
         }
+    }
+}
+
+// Masks of at most one register bit (the register-stage kernel's per-thread factors).
+template <typename R>
+__device__ __forceinline__ void apply_factor_bit(R &r, int mask, float fr, float fi) {
+    switch (mask) {
+        case 0: apply_factor<0>(r, fr, fi); break;
+        case 1: apply_factor<1>(r, fr, fi); break;
+        case 2: apply_factor<2>(r, fr, fi); break;
+        case 4: apply_factor<4>(r, fr, fi); break;
+        case 8: apply_factor<8>(r, fr, fi); break;
+        default: apply_factor<16>(r, fr, fi); break;
     }
 }
 

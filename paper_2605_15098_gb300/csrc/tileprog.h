@@ -60,7 +60,8 @@ enum T2Op : int32_t {
     T2_DIAG = 4,   // factor applications [e0, e1)
     T2_SCALE = 5,  // multiply every amplitude by hi + lo (matrix record `aux`: m[0], m[1])
     T2_BLOCK = 6,  // fused kernel: 32x32 block `aux` on the register bits (tensor cores)
-    T2_RGATE = 7   // real 2x2 (matrix record `aux`, imaginary parts zero): half the arithmetic
+    T2_RGATE = 7,  // real 2x2 (matrix record `aux`, imaginary parts zero): half the arithmetic
+    T2_ROT = 8     // uncontrolled register-bit rotation as three shears (record: t, s)
 };
 
 // Fused blocks: a 32x32 complex matrix U on the register index (bit j of the

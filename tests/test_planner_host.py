@@ -64,13 +64,16 @@ def t2_ops(plan):
 @pytest.mark.parametrize("n,depth", [(14, 3), (16, 4)])
 def test_u3_split_real_rotations(sv, orc, n, depth):
     """In complex64 a U3 runs as P(phi) RY(theta) P(lambda): every
-    non-diagonal step is a real rotation (planemu.T2_RGATE), the phases join
+    non-diagonal step is a real rotation (a shear triple on a register bit,
+    a real 2x2 on a lane bit), the phases join
     diagonal runs, the amplitudes still match the oracle and the pass gate
     counts still add up to the circuit's gates."""
     g = C.random_circuit(n, depth, 5 + n)
     plan = check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED), sv.SV_C64, 2e-5)
     ops = t2_ops(plan)
-    assert ops.count(planemu.T2_RGATE) == n * depth
+    # register-bit rotations run as shear triples (planemu.T2_ROT), lane-bit ones as real 2x2
+    assert ops.count(planemu.T2_RGATE) + ops.count(planemu.T2_ROT) == n * depth
+    assert ops.count(planemu.T2_ROT) > 0
     assert planemu.T2_GATE not in ops
     assert sum(p["ngates"] for p in plan["passes"]) + plan["relabels"] == len(g)
     # complex128 keeps the general matrices
