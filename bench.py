@@ -77,17 +77,27 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def sources_sha(paths) -> str:
+    """SHA-256 (16 hex digits) of the concatenated files, in the given order."""
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_for(kernel_src: str, workload: str):
-    """Per-launch DRAM bytes from the committed ncu summary, if the kernel's
-    source is unchanged since the capture (else None)."""
+    """Per-launch DRAM bytes from the committed ncu summary, if the sources
+    the kernel and its programme are built from are unchanged since the
+    capture (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         ent = d[workload]
-        with open(os.path.join(ROOT, kernel_src), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()[:16]
-        if ent.get("source_sha") != sha:
+        if ent.get("source") != kernel_src:
+            return None
+        if ent.get("sources_sha") != sources_sha(ent["sources"]):
             return None
         return float(ent["bytes_per_launch"])
     except Exception:
