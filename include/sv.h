@@ -104,8 +104,10 @@ enum {
                                    paper does, instead of gathering them
                                    into the tile                               */
     SV_FLAG_NO_RELABEL = 4,     /* execute SWAP gates as data movement        */
-    SV_FLAG_GENERIC_TILE = 8    /* use the generic shared-memory tile kernel
+    SV_FLAG_GENERIC_TILE = 8,   /* use the generic shared-memory tile kernel
                                    for every pass (no register stages)        */
+    SV_FLAG_NO_PLAN_CACHE = 16  /* plan, compile and upload the list on this
+                                   call even if the handle holds its programme */
 };
 
 /* Planner choice for partitioned modes. */
@@ -184,6 +186,11 @@ sv_status sv_qubit_map(sv_handle h, int *host_phys_of_logical);
 /* ---- applying gates --------------------------------------------------- */
 
 /* Apply gates g[0..m-1] in order.  cfg may be NULL (defaults).
+ * Partitioned modes keep the compiled programmes (host and device copies) of
+ * the last 8 distinct keys on the handle; a key is the whole gate list, the
+ * configuration and the qubit map at the call.  A repeated key skips the
+ * planning, compilation and upload, never any amplitude arithmetic.  The
+ * programmes are freed with the handle.
  * Errors: SV_ERR_ARG with the index of the first bad gate in the message
  * (qubit out of range, control == target, unknown kind, nonzero reserved,
  * log2den outside 0..62); nothing is applied in that case. */

@@ -5,12 +5,17 @@
 
 #include <cstdint>
 #include <map>
+#include <memory>
 #include <string>
 #include <utility>
 #include <vector>
 
 #include "plan.h"
 #include "sv.h"
+
+namespace sv {
+struct CompiledPlan;  // a planned, compiled and uploaded gate list (tile.cu)
+}
 
 namespace sv {
 
@@ -70,10 +75,11 @@ struct sv_state {
     double *probs = nullptr;      // device marginal of the last read-out
     size_t probs_cap = 0;
     void *small = nullptr;        // 64 KiB device area for reduction partials
-    void *plan_dev = nullptr;     // device copy of the tile-pass programme
-    size_t plan_cap = 0;
-    void *plan_host = nullptr;    // pinned host staging for the programme
+    void *plan_host = nullptr;    // pinned host staging for programme uploads
     size_t plan_host_cap = 0;
+    // compiled programmes of the last few distinct (gate list, configuration,
+    // qubit map) keys, most recent first, each with its own device copy
+    std::vector<std::shared_ptr<sv::CompiledPlan>> plan_cache;
     sv_stats stats{};
     void *t2_tables = nullptr;    // FP64-generated phase tables (register-stage kernel)
     int *t2_err = nullptr;        // device flag: a bounded wait gave up

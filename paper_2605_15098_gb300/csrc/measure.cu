@@ -48,13 +48,19 @@ __device__ __forceinline__ uint64_t pdep_mask(uint64_t v, uint64_t mask) {
 template <typename R>
 struct ProbAcc;
 
+// Amplitude loads a reduction thread keeps in flight before accumulating
+// them (in order): enough bytes in flight per SM to cover HBM latency.
+constexpr int kLoadBatch = 8;
+
 template <>
 struct ProbAcc<double> {
+    using V = double2;
     double acc = 0.0;
-    __device__ void add(const double *s, uint64_t x) {
-        const double re = s[2 * x], im = s[2 * x + 1];
-        acc += re * re + im * im;
+    __device__ static V load(const double *s, uint64_t x) {
+        return reinterpret_cast<const double2 *>(s)[x];
     }
+    __device__ void add(V v) { acc += v.x * v.x + v.y * v.y; }
+    __device__ void add(const double *s, uint64_t x) { add(load(s, x)); }
     __device__ double value() const { return acc; }
 };
 
@@ -67,13 +73,17 @@ struct ProbAcc<float> {
         lo += (hi - (t - bb)) + (b - bb);
         hi = t;
     }
-    __device__ void add(const float *s, uint64_t x) {
-        const float2 v = reinterpret_cast<const float2 *>(s)[x];
+    using V = float2;
+    __device__ static V load(const float *s, uint64_t x) {
+        return reinterpret_cast<const float2 *>(s)[x];
+    }
+    __device__ void add(V v) {
         const float pr = v.x * v.x, pi = v.y * v.y;
         lo += fmaf(v.x, v.x, -pr) + fmaf(v.y, v.y, -pi);
         two_sum(pr);
         two_sum(pi);
     }
+    __device__ void add(const float *s, uint64_t x) { add(load(s, x)); }
     __device__ double value() const { return (double)hi + (double)lo; }
 };
 
@@ -96,7 +106,19 @@ k_marg_m(const R *__restrict__ s, MargArgs a, double *__restrict__ partial) {
     }
     uint64_t xr = pdep_mask(g * a.per_group, a.rest);
     ProbAcc<R> acc;
-    for (uint64_t i = 0; i < a.per_group; i++) {
+    uint64_t i = 0;
+    // kLoadBatch loads in flight per thread, then accumulated in order
+    for (; i + kLoadBatch <= a.per_group; i += kLoadBatch) {
+        typename ProbAcc<R>::V v[kLoadBatch];
+#pragma unroll
+        for (int k = 0; k < kLoadBatch; k++) {
+            v[k] = ProbAcc<R>::load(s, xm | xr);
+            xr = ((xr | ~a.rest) + 1) & a.rest;
+        }
+#pragma unroll
+        for (int k = 0; k < kLoadBatch; k++) acc.add(v[k]);
+    }
+    for (; i < a.per_group; i++) {
         acc.add(s, xm | xr);
         xr = ((xr | ~a.rest) + 1) & a.rest;
     }
@@ -125,7 +147,18 @@ k_marg_r(const R *__restrict__ s, MargArgs a, double *__restrict__ partial) {
     const uint64_t xl = pdep_mask((uint64_t)lane, lane_bits);
     uint64_t xo = pdep_mask(g * a.per_group, a.upper);
     ProbAcc<R> pa;
-    for (uint64_t i = 0; i < a.per_group; i++) {
+    uint64_t i = 0;
+    for (; i + kLoadBatch <= a.per_group; i += kLoadBatch) {
+        typename ProbAcc<R>::V v[kLoadBatch];
+#pragma unroll
+        for (int k = 0; k < kLoadBatch; k++) {
+            v[k] = ProbAcc<R>::load(s, xm | xo | xl);
+            xo = ((xo | ~a.upper) + 1) & a.upper;
+        }
+#pragma unroll
+        for (int k = 0; k < kLoadBatch; k++) pa.add(v[k]);
+    }
+    for (; i < a.per_group; i++) {
         pa.add(s, xm | xo | xl);
         xo = ((xo | ~a.upper) + 1) & a.upper;
     }

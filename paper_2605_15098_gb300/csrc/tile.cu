@@ -307,7 +307,33 @@ struct PassUpload {
     size_t layx = 0, epi = 0;
 };
 
+constexpr size_t kPlanCacheEntries = 8;
+
+// 64-bit FNV-1a
+uint64_t fnv1a(const void *p, size_t n, uint64_t h = 0xcbf29ce484222325ull) {
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; i++) h = (h ^ b[i]) * 0x100000001b3ull;
+    return h;
+}
+
 }  // namespace
+
+// A gate list planned and compiled for one configuration and starting qubit
+// map, with its programme uploaded to its own device buffer.  The key holds
+// every input the plan and the programmes depend on.
+struct CompiledPlan {
+    std::string key;
+    uint64_t hash = 0;
+    Plan plan;
+    std::vector<T2Pass> t2;
+    std::vector<PassUpload> up;
+    int phys_out[64];
+    void *dev = nullptr;
+    size_t bytes = 0;
+    ~CompiledPlan() {
+        if (dev) cudaFree(dev);  // synchronises with work that may still read it
+    }
+};
 
 static sv_status tab64_prepare(sv_state *h) {
     if (h->tab64) return SV_OK;
@@ -369,13 +395,48 @@ sv_launch_record describe_remap(int n, sv_dtype dt, const std::vector<std::pair<
     return r;
 }
 
-sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, const sv_config &cfg,
-                            const PlanOverride *ov) {
+// The cache key: every input of planning and compilation.
+static std::string plan_key(const sv_state *h, const std::vector<sv_gate> &gates, const sv_config &cfg,
+                            const PlanOptions &opt, const PlanOverride *ov) {
+    std::string k;
+    auto put = [&](const void *p, size_t n) { k.append(static_cast<const char *>(p), n); };
+    const int head[] = {h->n, (int)h->dt, cfg.mode, (int)cfg.flags, opt.n, opt.k, opt.c,
+                        opt.merge_diag, opt.relabel, opt.paper, opt.split_u3, ov ? 1 : 0};
+    put(head, sizeof head);
+    put(h->phys, sizeof h->phys);
+    if (ov) {
+        const int n = (int)ov->kernel.size();
+        put(&n, sizeof n);
+        put(ov->kernel.data(), ov->kernel.size());
+    }
+    put(gates.data(), gates.size() * sizeof(sv_gate));
+    return k;
+}
+
+// Plan, compile and upload (or find in the handle's cache) the gate list.
+static sv_status compiled_plan(sv_state *h, const std::vector<sv_gate> &gates, const sv_config &cfg,
+                               const PlanOverride *ov, std::shared_ptr<CompiledPlan> *out) {
     const bool dbl = h->dt == SV_C128;
     PlanOptions opt = ov ? ov->opt : plan_options(h->n, h->dt, cfg);
     if (dbl && opt.k > 13) return fail(SV_ERR_ARG, "complex128 tiles hold at most 2^13 amplitudes");
-    Plan plan;
-    int phys[64];
+    std::string key = plan_key(h, gates, cfg, opt, ov);
+    const uint64_t hash = fnv1a(key.data(), key.size());
+    const bool use_cache = !(cfg.flags & SV_FLAG_NO_PLAN_CACHE);
+    for (size_t i = 0; use_cache && i < h->plan_cache.size(); i++) {
+        const auto &e = h->plan_cache[i];
+        if (e->hash == hash && e->key == key) {
+            std::shared_ptr<CompiledPlan> hit = e;
+            h->plan_cache.erase(h->plan_cache.begin() + (long)i);
+            h->plan_cache.insert(h->plan_cache.begin(), hit);
+            *out = hit;
+            return SV_OK;
+        }
+    }
+    auto cp = std::make_shared<CompiledPlan>();
+    cp->key = std::move(key);
+    cp->hash = hash;
+    Plan &plan = cp->plan;
+    int *phys = cp->phys_out;
     std::copy(h->phys, h->phys + 64, phys);
     std::string err = build_plan(gates, opt, phys, &plan);
     if (!err.empty()) return fail(SV_ERR_ARG, "planner: %s", err.c_str());
@@ -383,8 +444,10 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
     // compile every pass; register-stage kernel where it applies
     const bool allow_t2 = !dbl && !(cfg.flags & SV_FLAG_GENERIC_TILE);
     const bool fused = cfg.mode == SV_MODE_FUSED;
-    std::vector<T2Pass> t2(plan.passes.size());
-    std::vector<PassUpload> up(plan.passes.size());
+    std::vector<T2Pass> &t2 = cp->t2;
+    std::vector<PassUpload> &up = cp->up;
+    t2.resize(plan.passes.size());
+    up.resize(plan.passes.size());
     Blob blob;
     if (ov && ov->kernel.size() != plan.passes.size())
         return fail(SV_ERR_STATE, "internal: learned plan does not match the planner's passes");
@@ -416,29 +479,48 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
         }
     }
     blob.put(nullptr, 0);
-    const size_t total = blob.b.size() + 256;
-    if (total > h->plan_cap) {
+    const size_t total = blob.b.size();
+    if (total > h->plan_host_cap) {
         SV_CUDA(cudaStreamSynchronize(h->stream));
-        if (h->plan_dev) cudaFree(h->plan_dev);
         if (h->plan_host) cudaFreeHost(h->plan_host);
-        h->plan_dev = h->plan_host = nullptr;
-        h->plan_cap = 0;
-        size_t cap = std::max<size_t>(total * 2, (size_t)1 << 16);
-        if (cudaMalloc(&h->plan_dev, cap) != cudaSuccess ||
-            cudaMallocHost(&h->plan_host, cap) != cudaSuccess) {
+        h->plan_host = nullptr;
+        h->plan_host_cap = 0;
+        const size_t cap = std::max<size_t>(total * 2, (size_t)1 << 16);
+        if (cudaMallocHost(&h->plan_host, cap) != cudaSuccess) {
             cudaGetLastError();
-            return fail(SV_ERR_OOM, "cannot allocate the pass programme (%zu bytes)", cap);
+            return fail(SV_ERR_OOM, "cannot allocate the programme staging (%zu bytes)", cap);
         }
-        h->plan_cap = cap;
+        h->plan_host_cap = cap;
     } else {
         // the previous upload must have finished before the staging is reused
         SV_CUDA(cudaStreamSynchronize(h->stream));
     }
-    std::memcpy(h->plan_host, blob.b.data(), blob.b.size());
-    SV_CUDA(cudaMemcpyAsync(h->plan_dev, h->plan_host, blob.b.size(), cudaMemcpyHostToDevice,
-                            h->stream));
-    h->stats.h2d_bytes += (double)blob.b.size();
-    const char *dev = reinterpret_cast<const char *>(h->plan_dev);
+    if (cudaMalloc(&cp->dev, total + 256) != cudaSuccess) {
+        cudaGetLastError();
+        cp->dev = nullptr;
+        return fail(SV_ERR_OOM, "cannot allocate the pass programme (%zu bytes)", total);
+    }
+    cp->bytes = total;
+    std::memcpy(h->plan_host, blob.b.data(), total);
+    SV_CUDA(cudaMemcpyAsync(cp->dev, h->plan_host, total, cudaMemcpyHostToDevice, h->stream));
+    h->stats.h2d_bytes += (double)total;
+    if (use_cache) {
+        h->plan_cache.insert(h->plan_cache.begin(), cp);
+        if (h->plan_cache.size() > kPlanCacheEntries) h->plan_cache.pop_back();
+    }
+    *out = cp;
+    return SV_OK;
+}
+
+sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, const sv_config &cfg,
+                            const PlanOverride *ov) {
+    const bool dbl = h->dt == SV_C128;
+    std::shared_ptr<CompiledPlan> cp;
+    SV_TRY(compiled_plan(h, gates, cfg, ov, &cp));
+    const Plan &plan = cp->plan;
+    const std::vector<T2Pass> &t2 = cp->t2;
+    const std::vector<PassUpload> &up = cp->up;
+    const char *dev = reinterpret_cast<const char *>(cp->dev);
     bool any_t2 = false, any_t3 = false;
     for (auto &u : up) {
         any_t2 |= u.t2;
@@ -504,7 +586,7 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
         h->stats.passes++;
         h->stats.touched_bytes += meta.bytes;
     }
-    std::copy(phys, phys + 64, h->phys);
+    std::copy(cp->phys_out, cp->phys_out + 64, h->phys);
     h->stats.relabels = plan.relabels;
     return SV_OK;
 }
