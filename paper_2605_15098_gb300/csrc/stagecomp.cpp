@@ -317,6 +317,15 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
                 in.aux = (int32_t)out->mats.size();
                 out->mats.push_back(m);
             }
+            {  // dispatch code (tileprog.h)
+                const int kind = in.op == T2_H ? 0 : in.op == T2_X ? 1 : in.op == T2_RGATE ? 2
+                               : in.op == T2_ROT ? 3 : 4;
+                int slot = 7;
+                if (in.ccls == T2C_NONE && in.cls == T2C_REG) slot = in.idx;
+                else if (in.ccls == T2C_NONE && in.cls == T2C_LANE) slot = 5;
+                else if (in.ccls == T2C_THREAD && in.cls == T2C_LANE) slot = 6;
+                in.hd = (int16_t)(kT2Handler + 8 * kind + slot);
+            }
             if (op.type == TOP_H) out->n_h++;
             out->ins.push_back(in);
             continue;

@@ -95,6 +95,35 @@ struct Layout2 {
 // path in the loop costs registers and instructions in all the others).
 constexpr int kFeatX = 1, kFeatR = 2, kFeatU = 4, kFeatAll = 7;
 
+// Gate KIND (0..4: H, X, real 2x2, shear rotation, general 2x2) on register
+// bit SLOT (0..4), or on lane bit l (SLOT 5; SLOT 6 with the thread
+// predicate `pred`).  Kinds outside the instantiation's set F compile to
+// nothing: the host never launches them there.
+template <int F, int KIND, int SLOT, int NP>
+__device__ __forceinline__ void run_gate(RegsN<NP> &r, const float4 *mrec, uint32_t qm, int l, bool pred) {
+    constexpr int need = KIND == 0 ? 0 : KIND == 1 ? kFeatX : KIND == 4 ? kFeatU : kFeatR;
+    if constexpr ((need & F) != need) {
+        return;
+    } else {
+        float m[8] = {};
+        if constexpr (KIND >= 2) {
+            const float4 m0 = __ldg(mrec), m1 = __ldg(mrec + 1);
+            m[0] = m0.x; m[1] = m0.y; m[2] = m0.z; m[3] = m0.w;
+            m[4] = m1.x; m[5] = m1.y; m[6] = m1.z; m[7] = m1.w;
+        }
+        if constexpr (SLOT <= 4) {
+            if constexpr (KIND == 0) reg_h2<SLOT>(r, qm);
+            else if constexpr (KIND == 1) reg_x2<SLOT>(r, qm);
+            else if constexpr (KIND == 2) reg_r2<SLOT>(r, qm, m);
+            else if constexpr (KIND == 3) reg_rot<SLOT>(r, qm, m);
+            else reg_u2<SLOT>(r, qm, m);
+        } else if constexpr (KIND != 3) {
+            constexpr int OP = KIND == 0 ? T2_H : KIND == 1 ? T2_X : KIND == 2 ? T2_RGATE : T2_GATE;
+            lane_op3<OP, SLOT == 6>(r, l, pred, qm, m);
+        }
+    }
+}
+
 template <int K, bool kDirect, bool kSmemProg, int F, typename Hook>
 __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hook) {
     using G = Geo<K>;
@@ -115,6 +144,9 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
     for (int pc = 0; pc < a.nins; pc++) {
         const int4 w = ins[pc];
         const int op = w.x & 0xff;
+        // all ones at run time (the handler code is below 256), opaque to the
+        // compiler (see reg_h2)
+        const uint32_t qm = ~((uint32_t)w.y >> 24);
         if (op == T2_STAGE) {
             if (live) {
                 const Layout2 L(a.layx + stage, tid);
@@ -187,7 +219,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
                 const int pb = (int)((w0 >> 10) & 0xfu);  // thread-bit predicate of a constant
                 if (pb && !((tid >> (pb - 1)) & 1)) continue;  // not this thread's factor
                 if (w0 & kFacTable) {
-                    apply_table(r, a.mats + 2 * fd.z, ~((uint32_t)w.y >> 16));
+                    apply_table(r, a.mats + 2 * fd.z, qm);
                     continue;
                 }
                 // per-thread phase (constants are tables, see the stage compiler)
@@ -211,102 +243,58 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
             }
             continue;
         }
-        // gates (no register-bit controls: the stage compiler never emits them)
-        const int cls = (w.x >> 8) & 0xff;
+        // gates (no register-bit controls: the stage compiler never emits them);
+        // one switch on the handler code the stage compiler set (tileprog.h)
         const int j = (int8_t)((w.x >> 16) & 0xff);
-        const int ccls = (w.x >> 24) & 0xff;
-        const int cidx = (int16_t)(w.y & 0xffff);
-        bool pred = true;
-        if (ccls == T2C_GLOBAL) {
-            if (!((t2_tile_base >> cidx) & 1)) continue;  // tile-uniform
-        } else if (ccls == T2C_THREAD) {
-            pred = (tid >> cidx) & 1;
+        const float4 *mrec = a.mats + 2 * w.w;
+        switch (((uint32_t)w.y >> 16) & 0xffu) {
+#define SV_GATE_CASES(K)                                                                 \
+    case kT2Handler + 8 * K + 0: run_gate<F, K, 0>(r, mrec, qm, j, true); continue;     \
+    case kT2Handler + 8 * K + 1: run_gate<F, K, 1>(r, mrec, qm, j, true); continue;     \
+    case kT2Handler + 8 * K + 2: run_gate<F, K, 2>(r, mrec, qm, j, true); continue;     \
+    case kT2Handler + 8 * K + 3: run_gate<F, K, 3>(r, mrec, qm, j, true); continue;     \
+    case kT2Handler + 8 * K + 4: run_gate<F, K, 4>(r, mrec, qm, j, true); continue;     \
+    case kT2Handler + 8 * K + 5: run_gate<F, K, 5>(r, mrec, qm, j, true); continue;     \
+    case kT2Handler + 8 * K + 6:                                                         \
+        run_gate<F, K, 6>(r, mrec, qm, j, (tid >> (int16_t)(w.y & 0xffff)) & 1); continue;
+            SV_GATE_CASES(0)
+            SV_GATE_CASES(1)
+            SV_GATE_CASES(2)
+            SV_GATE_CASES(3)
+            SV_GATE_CASES(4)
+#undef SV_GATE_CASES
+            default: break;
         }
-        // all ones at run time (see reg_h2); the instruction word's pad field is zero
-        const uint32_t qm = ~((uint32_t)w.y >> 16);
-        if (op == T2_H) {
-            if (cls == T2C_LANE) {
-                if (ccls == T2C_THREAD) lane_op3<T2_H, true>(r, j, pred, qm, nullptr); else lane_op3<T2_H, false>(r, j, pred, qm, nullptr);
-                continue;
+        {  // slot 7: a register-bit gate with a thread or tile control
+            const int ccls = (w.x >> 24) & 0xff;
+            const int cidx = (int16_t)(w.y & 0xffff);
+            if (ccls == T2C_GLOBAL) {
+                if (!((t2_tile_base >> cidx) & 1)) continue;  // tile-uniform
+            } else if (ccls == T2C_THREAD) {
+                if (!((tid >> cidx) & 1)) continue;
             }
-            if (!pred) continue;
-            switch (j) {
-                case 0: reg_h2<0>(r, qm); break;
-                case 1: reg_h2<1>(r, qm); break;
-                case 2: reg_h2<2>(r, qm); break;
-                case 3: reg_h2<3>(r, qm); break;
-                default: reg_h2<4>(r, qm); break;
-            }
-            continue;
-        }
-        if constexpr ((F & kFeatX) != 0) {
-            if (op == T2_X) {
-                if (cls == T2C_LANE) {
-                    if (ccls == T2C_THREAD) lane_op3<T2_X, true>(r, j, pred, qm, nullptr); else lane_op3<T2_X, false>(r, j, pred, qm, nullptr);
-                    continue;
-                }
-                if (!pred) continue;
-                switch (j) {
-                    case 0: reg_x2<0>(r, qm); break;
-                    case 1: reg_x2<1>(r, qm); break;
-                    case 2: reg_x2<2>(r, qm); break;
-                    case 3: reg_x2<3>(r, qm); break;
-                    default: reg_x2<4>(r, qm); break;
-                }
-                continue;
-            }
-        }
-        if constexpr ((F & (kFeatR | kFeatU)) != 0) {
-            float m[8];
-            {
-                const float4 m0 = __ldg(a.mats + 2 * w.w), m1 = __ldg(a.mats + 2 * w.w + 1);
-                m[0] = m0.x; m[1] = m0.y; m[2] = m0.z; m[3] = m0.w;
-                m[4] = m1.x; m[5] = m1.y; m[6] = m1.z; m[7] = m1.w;
-            }
-            if constexpr ((F & kFeatR) != 0) {
-                if (op == T2_ROT) {  // uncontrolled, on a register bit (stage compiler)
-                    switch (j) {
-                        case 0: reg_rot<0>(r, qm, m); break;
-                        case 1: reg_rot<1>(r, qm, m); break;
-                        case 2: reg_rot<2>(r, qm, m); break;
-                        case 3: reg_rot<3>(r, qm, m); break;
-                        default: reg_rot<4>(r, qm, m); break;
-                    }
-                    continue;
-                }
-                if (op == T2_RGATE) {
-                    if (cls == T2C_LANE) {
-                        if (ccls == T2C_THREAD) lane_op3<T2_RGATE, true>(r, j, pred, qm, m); else lane_op3<T2_RGATE, false>(r, j, pred, qm, m);
-                        continue;
-                    }
-                    if (!pred) continue;
-                    switch (j) {
-                        case 0: reg_r2<0>(r, qm, m); break;
-                        case 1: reg_r2<1>(r, qm, m); break;
-                        case 2: reg_r2<2>(r, qm, m); break;
-                        case 3: reg_r2<3>(r, qm, m); break;
-                        default: reg_r2<4>(r, qm, m); break;
-                    }
-                    continue;
-                }
-            }
-            if constexpr ((F & kFeatU) != 0) {
-                if (op == T2_GATE) {
-                    if (cls == T2C_LANE) {
-                        if (ccls == T2C_THREAD) lane_op3<T2_GATE, true>(r, j, pred, qm, m); else lane_op3<T2_GATE, false>(r, j, pred, qm, m);
-                        continue;
-                    }
-                    if (!pred) continue;
-                    switch (j) {
-                        case 0: reg_u2<0>(r, qm, m); break;
-                        case 1: reg_u2<1>(r, qm, m); break;
-                        case 2: reg_u2<2>(r, qm, m); break;
-                        case 3: reg_u2<3>(r, qm, m); break;
-                        default: reg_u2<4>(r, qm, m); break;
-                    }
-                    continue;
-                }
-            }
+            const int kind = ((((uint32_t)w.y >> 16) & 0xffu) - kT2Handler) >> 3;
+            const bool lane = ((w.x >> 8) & 0xff) == T2C_LANE;
+#define SV_CTRL_CASE(K)                                                                  \
+    if (kind == K) {                                                                     \
+        if (lane) {                                                                      \
+            run_gate<F, K, 5>(r, mrec, qm, j, true);                                     \
+        } else {                                                                         \
+            switch (j) {                                                                 \
+                case 0: run_gate<F, K, 0>(r, mrec, qm, j, true); break;                  \
+                case 1: run_gate<F, K, 1>(r, mrec, qm, j, true); break;                  \
+                case 2: run_gate<F, K, 2>(r, mrec, qm, j, true); break;                  \
+                case 3: run_gate<F, K, 3>(r, mrec, qm, j, true); break;                  \
+                default: run_gate<F, K, 4>(r, mrec, qm, j, true); break;                 \
+            }                                                                            \
+        }                                                                                \
+        continue;                                                                        \
+    }
+            SV_CTRL_CASE(0)
+            SV_CTRL_CASE(1)
+            SV_CTRL_CASE(2)
+            SV_CTRL_CASE(4)
+#undef SV_CTRL_CASE
         }
     }
     if (!hooked) {  // a programme without a stage change still releases the buffer

@@ -73,6 +73,15 @@ enum T2Op : int32_t {
 constexpr int kBlockFloats = 4 * 32 * 32;
 constexpr int kMaxBlocks = 4;  // shared-memory block slots; more blocks stream through them
 
+// Handler of a gate instruction, set by the stage compiler so that the
+// register-stage kernel dispatches a gate with one switch:
+// kT2Handler + 8 * kind + slot, kind 0..4 = H, X, real 2x2, shear rotation,
+// general 2x2; slot 0..4 = register bit (uncontrolled), 5 = lane bit
+// (uncontrolled), 6 = lane bit with a thread control, 7 = any other control.
+// Codes stay below 256: the kernel takes the field's high byte, zero, as the
+// opaque all-ones mask of its gate code.
+constexpr int kT2Handler = 16;
+
 enum T2Class : int32_t { T2C_NONE = 0, T2C_REG = 1, T2C_LANE = 2, T2C_THREAD = 3, T2C_GLOBAL = 4 };
 
 // One programme step, 16 bytes (one vector load in the kernel).
@@ -82,7 +91,7 @@ struct T2Ins {
     int8_t idx;
     int8_t ccls;   // control class: NONE, REG (register bit), THREAD (bit of threadIdx.x), GLOBAL
     int16_t cidx;  // control: register bit, thread bit, or physical bit
-    int16_t pad0;
+    int16_t hd;    // gates: handler code (kT2Handler), 0 otherwise
     int16_t e0, e1;  // T2_DIAG: factor applications
     int32_t aux;     // T2_STAGE: stage record; T2_GATE / T2_SCALE: matrix record
 };
