@@ -197,6 +197,14 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
         if (op == T2_SCALE) {
             const float4 mm = __ldg(a.mats + 2 * w.w);
             const float hi = mm.x, lo = mm.y;
+            if (lo == 0.f) {  // an even number of Hadamards: an exact power of two
+#pragma unroll
+                for (int q = 0; q < kNP2; q++) {
+                    r.re[q] = mul2(r.re[q], f2(hi));
+                    r.im[q] = mul2(r.im[q], f2(hi));
+                }
+                continue;
+            }
 #pragma unroll
             for (int q = 0; q < kNP2; q++) {
                 r.re[q] = fma2(r.re[q], f2(hi), mul2(r.re[q], f2(lo)));
@@ -377,15 +385,16 @@ __global__ void __launch_bounds__(Geo<K>::kThreads, K == kT2Qubits ? 2 : 1)
 
     uint32_t parity = 0;
     for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        const uint64_t base = pdep(tile, a.gmask);
         const uint64_t next = tile + gridDim.x;
         // per-tile diagonal data while the copies are in flight (the barrier
-        // first: the previous tile's programme may still read lin / cst)
+        // first: the previous tile's programme may still read lin / cst);
+        // one thread forms the tile's base index, the others read it back
         __syncthreads();
         for (int i = tid; i < a.nruns * 16; i += blockDim.x) lin[i] = 0u;
         for (int i = tid; i < a.nruns; i += blockDim.x) cst[i] = 0u;
-        if (tid == 0) t2_tile_base = base;
+        if (tid == 0) t2_tile_base = pdep(tile, a.gmask);
         __syncthreads();
+        const uint64_t base = t2_tile_base;
         for (int i = tid; i < a.ntterms; i += blockDim.x) {
             const T2TileTerm t = a.tterms[i];
             bool on = (base >> t.g0) & 1;
