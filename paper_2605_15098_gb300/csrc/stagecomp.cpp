@@ -569,6 +569,56 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
         if (!e.empty()) return e;
         if (out->factors.size() > 32000) return "too many factor applications";
     }
+    if (!fused) {
+        // A diagonal run directly followed by an uncontrolled Hadamard on a
+        // register bit j, where the run is the identity on the amplitudes
+        // with bit j = 0 (an inverse-QFT step), becomes one phased butterfly:
+        // b <- M b, then (a + b, a - b), with M the run's per-thread factor
+        // on bit j times its phase table.
+        auto phased_ok = [&](const T2Ins &d, int j) {
+            int ntab = 0, nthr = 0;
+            for (int e = d.e0; e < d.e1; e++) {
+                const T2Factor &f = out->factors[e];
+                const uint32_t w0 = (uint32_t)f.w0;
+                if (w0 & kFacTable) {
+                    if (((w0 >> 10) & 0xfu) || ++ntab > 1) return false;
+                    int32_t m0;
+                    std::memcpy(&m0, &f.c0, sizeof m0);
+                    for (int x = 0; x < 32; x++) {
+                        if ((x >> j) & 1) continue;
+                        // entry x: float 4 (x >> 1) + (x & 1) (re) and + 2 (im) of the table
+                        const float *tf = out->mats[m0 + (x >> 2)].m;
+                        const int o = 4 * ((x >> 1) & 1) + (x & 1);
+                        if (tf[o] != 1.f || tf[o + 2] != 0.f) return false;
+                    }
+                } else if (w0 & 0x100u) {
+                    if ((w0 & 0xffu) != (1u << j) || ++nthr > 1) return false;
+                } else {
+                    return false;
+                }
+            }
+            return d.e1 > d.e0;
+        };
+        std::vector<T2Ins> merged;
+        for (size_t i = 0; i < out->ins.size(); i++) {
+            const T2Ins &d = out->ins[i];
+            if (d.op == T2_DIAG && i + 1 < out->ins.size()) {
+                const T2Ins &hh = out->ins[i + 1];
+                if (hh.op == T2_H && hh.cls == T2C_REG && hh.ccls == T2C_NONE && phased_ok(d, hh.idx)) {
+                    T2Ins f = hh;
+                    f.op = T2_HPH;
+                    f.e0 = d.e0;
+                    f.e1 = d.e1;
+                    f.hd = (int16_t)(kT2Handler + 8 * 5 + hh.idx);
+                    merged.push_back(f);
+                    i++;
+                    continue;
+                }
+            }
+            merged.push_back(d);
+        }
+        out->ins.swap(merged);
+    }
     if (!fused && (out->ins.size() > (size_t)kT2SmemIns || out->factors.size() > (size_t)kT2SmemFactors))
         return "programme longer than the kernel's shared-memory copy";
     for (size_t i = 0; i < out->ins.size(); i++)

@@ -212,14 +212,49 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
             }
             continue;
         }
+        // e^{2 pi i u / 2^32} for this thread's phase u of a per-thread factor
+        auto thread_phase = [&](const int4 fd) -> float2 {
+            const uint32_t w0 = (uint32_t)fd.x;
+            const int run = fd.y;
+            // static phase rows beyond the shared-memory copy stay in global memory
+            uint32_t u = (kSmemProg && fd.z >= G::kStatRows) ? __ldg(a.stat + fd.z * G::kThreads + tid)
+                                                             : stat[fd.z * G::kThreads + tid];
+            if (w0 & 0x200u) u += cst[run];
+            const int lr = (int)((w0 >> kFacLinShift) & 0x1fu) - 1;
+            if (lr >= 0) u += lin[run * 16 + lr];
+            uint32_t dm = (w0 >> kFacDynShift) & 0x1ffu & (uint32_t)tid;
+            while (dm) {
+                const int t = __ffs(dm) - 1;
+                dm &= dm - 1;
+                const int8_t *tbp = reinterpret_cast<const int8_t *>(a.stages + stage);
+                u += lin[run * 16 + tbp[5 + t]];
+            }
+            return cx(cx(tab[u >> 24], tab[kTabN + ((u >> 16) & 255u)]),
+                      cx(tab[2 * kTabN + ((u >> 8) & 255u)], tab[3 * kTabN + (u & 255u)]));
+        };
+        if (op == T2_HPH) {  // diagonal run + H on register bit j in one sweep (stage compiler)
+            const int e0 = (int16_t)(w.z & 0xffff), e1 = (int16_t)(w.z >> 16);
+            const float4 *T = nullptr;
+            float2 ph = make_float2(1.f, 0.f);
+            for (int e = e0; e < e1; e++) {
+                const int4 fd = fac[e];
+                if ((uint32_t)fd.x & kFacTable)
+                    T = a.mats + 2 * fd.z;
+                else
+                    ph = thread_phase(fd);
+            }
+            switch ((w.x >> 16) & 0xff) {
+                case 0: reg_hph<0>(r, qm, T, ph.x, ph.y); break;
+                case 1: reg_hph<1>(r, qm, T, ph.x, ph.y); break;
+                case 2: reg_hph<2>(r, qm, T, ph.x, ph.y); break;
+                case 3: reg_hph<3>(r, qm, T, ph.x, ph.y); break;
+                default: reg_hph<4>(r, qm, T, ph.x, ph.y); break;
+            }
+            continue;
+        }
         if (op == T2_DIAG) {
             const int e0 = (int16_t)(w.z & 0xffff), e1 = (int16_t)(w.z >> 16);
             if (e0 >= e1) continue;
-            // static phase rows beyond the shared-memory copy stay in global memory
-            auto stat_at = [&](int row) -> uint32_t {
-                if (kSmemProg && row >= G::kStatRows) return __ldg(a.stat + row * G::kThreads + tid);
-                return stat[row * G::kThreads + tid];
-            };
             for (int e = e0; e < e1; e++) {
                 const int4 fd = fac[e];
                 const uint32_t w0 = (uint32_t)fd.x;
@@ -231,23 +266,8 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
                     continue;
                 }
                 // per-thread phase (constants are tables, see the stage compiler)
-                {
-                    uint32_t u = stat_at(fd.z);
-                    if (w0 & 0x200u) u += cst[run];
-                    const int lr = (int)((w0 >> kFacLinShift) & 0x1fu) - 1;
-                    if (lr >= 0) u += lin[run * 16 + lr];
-                    uint32_t dm = (w0 >> kFacDynShift) & 0x1ffu & (uint32_t)tid;
-                    while (dm) {
-                        const int t = __ffs(dm) - 1;
-                        dm &= dm - 1;
-                        const int8_t *tbp = reinterpret_cast<const int8_t *>(a.stages + stage);
-                        u += lin[run * 16 + tbp[5 + t]];
-                    }
-                    const float2 ff = cx(cx(tab[u >> 24], tab[kTabN + ((u >> 16) & 255u)]),
-                                         cx(tab[2 * kTabN + ((u >> 8) & 255u)],
-                                            tab[3 * kTabN + (u & 255u)]));
-                    apply_factor_bit(r, (int)(w0 & 0xffu), ff.x, ff.y);
-                }
+                const float2 ff = thread_phase(fd);
+                apply_factor_bit(r, (int)(w0 & 0xffu), ff.x, ff.y);
             }
             continue;
         }

@@ -235,6 +235,54 @@ __device__ __forceinline__ void reg_h2(RegsN<NP> &r, uint32_t qm) {
     }
 }
 
+// Phased Hadamard on register bit J: the amplitude b of each pair (bit J = 1)
+// is multiplied by M = (fr + i fi) T[x] (T: a 32-entry phase table laid out as
+// for apply_table, or none), then the pair takes the butterfly of reg_h2.
+template <int J, int NP>
+__device__ __forceinline__ void reg_hph(RegsN<NP> &r, uint32_t qm, const float4 *__restrict__ T, float fr,
+                                        float fi) {
+#pragma unroll
+    for (int g4 = 0; g4 < NP / 4; g4++) {
+        if (!((qm >> g4) & 1)) continue;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int q = 4 * g4 + i;
+            if constexpr (J >= 1) {
+                constexpr int S = 1 << (J - 1);
+                if (q & S) continue;
+                const int q1 = q | S;
+                float2 mr = f2(fr), mi = f2(fi);
+                if (T) {
+                    const float4 t = __ldg(T + q1);
+                    const float2 tr = make_float2(t.x, t.y), ti = make_float2(t.z, t.w);
+                    mr = fma2(ti, f2(-fi), mul2(tr, f2(fr)));
+                    mi = fma2(ti, f2(fr), mul2(tr, f2(fi)));
+                }
+                const float2 br = r.re[q1], bi = r.im[q1];
+                const float2 pr = fma2(bi, make_float2(-mi.x, -mi.y), mul2(br, mr));
+                const float2 pi = fma2(bi, mr, mul2(br, mi));
+                r.re[q1] = sub2(r.re[q], pr);
+                r.im[q1] = sub2(r.im[q], pi);
+                r.re[q] = fma2(r.re[q], f2(2.f), make_float2(-r.re[q1].x, -r.re[q1].y));
+                r.im[q] = fma2(r.im[q], f2(2.f), make_float2(-r.im[q1].x, -r.im[q1].y));
+            } else {
+                float mr = fr, mi = fi;
+                if (T) {
+                    const float4 t = __ldg(T + q);  // odd entries (bit 0 set): y and w
+                    mr = t.y * fr - t.w * fi;
+                    mi = t.y * fi + t.w * fr;
+                }
+                float2 &x = r.re[q], &y = r.im[q];
+                const float pr = x.y * mr - y.y * mi, pi = x.y * mi + y.y * mr;
+                x.y = x.x - pr;
+                y.y = y.x - pi;
+                x.x = fmaf(x.x, 2.f, -x.y);
+                y.x = fmaf(y.x, 2.f, -y.y);
+            }
+        }
+    }
+}
+
 template <int J, int NP>
 __device__ __forceinline__ void reg_x2(RegsN<NP> &r, uint32_t qm) {
 #pragma unroll

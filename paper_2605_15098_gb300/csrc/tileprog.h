@@ -61,7 +61,10 @@ enum T2Op : int32_t {
     T2_SCALE = 5,  // multiply every amplitude by hi + lo (matrix record `aux`: m[0], m[1])
     T2_BLOCK = 6,  // fused kernel: 32x32 block `aux` on the register bits (tensor cores)
     T2_RGATE = 7,  // real 2x2 (matrix record `aux`, imaginary parts zero): half the arithmetic
-    T2_ROT = 8     // uncontrolled register-bit rotation as three shears (record: t, s)
+    T2_ROT = 8,    // uncontrolled register-bit rotation as three shears (record: t, s)
+    T2_HPH = 9     // diagonal run [e0, e1) then H on register bit idx, in one sweep:
+                   // the run is the identity where bit idx is 0, and holds at
+                   // most one phase table and one per-thread factor on bit idx
 };
 
 // Fused blocks: a 32x32 complex matrix U on the register index (bit j of the
@@ -75,9 +78,10 @@ constexpr int kMaxBlocks = 4;  // shared-memory block slots; more blocks stream 
 
 // Handler of a gate instruction, set by the stage compiler so that the
 // register-stage kernel dispatches a gate with one switch:
-// kT2Handler + 8 * kind + slot, kind 0..4 = H, X, real 2x2, shear rotation,
-// general 2x2; slot 0..4 = register bit (uncontrolled), 5 = lane bit
-// (uncontrolled), 6 = lane bit with a thread control, 7 = any other control.
+// kT2Handler + 8 * kind + slot, kind 0..5 = H, X, real 2x2, shear rotation,
+// general 2x2, phased H (T2_HPH); slot 0..4 = register bit (uncontrolled),
+// 5 = lane bit (uncontrolled), 6 = lane bit with a thread control, 7 = any
+// other control.
 // Codes stay below 256: the kernel takes the field's high byte, zero, as the
 // opaque all-ones mask of its gate code.
 constexpr int kT2Handler = 16;

@@ -16,7 +16,7 @@ MASK32 = TWO32 - 1
 TOP_GATE, TOP_GATE_CL, TOP_GATE_CG, TOP_DIAG, TOP_SWAP, TOP_H, TOP_X = range(7)
 TERM_L, TERM_LL, TERM_G, TERM_LG, TERM_GG = range(5)
 # register-stage ops (tileprog.h)
-T2_STAGE, T2_GATE, T2_H, T2_X, T2_DIAG, T2_SCALE, T2_BLOCK, T2_RGATE, T2_ROT = range(9)
+T2_STAGE, T2_GATE, T2_H, T2_X, T2_DIAG, T2_SCALE, T2_BLOCK, T2_RGATE, T2_ROT, T2_HPH = range(10)
 C_NONE, C_REG, C_LANE, C_THREAD, C_GLOBAL = range(5)
 
 
@@ -163,7 +163,7 @@ def run_t2_pass(state, p):
                 m = t2["mats"][ins["aux"]]
                 t *= np.float64(np.float32(m[0])) + np.float64(np.float32(m[1]))
                 continue
-            if op == T2_DIAG:
+            if op in (T2_DIAG, T2_HPH):  # T2_HPH: the run, then H on register bit idx
                 for f in t2["factors"][ins["e0"]:ins["e1"]]:
                     w0 = f["w0"]
                     if (w0 >> 28) & 1:  # 32-entry constant phase table (tileprog.h)
@@ -204,7 +204,8 @@ def run_t2_pass(state, p):
                         u &= MASK32
                         fac = np.exp(2j * np.pi * (u / 2.0 ** 32))
                     t[sel] *= fac[sel]
-                continue
+                if op == T2_DIAG:
+                    continue
             # gates
             if ins["cls"] == C_REG:
                 bit = reg[ins["idx"]]
@@ -219,7 +220,7 @@ def run_t2_pass(state, p):
                 cond = ((loc >> reg[ins["cidx"]]) & 1) == 1
             elif ins["ccls"] == C_THREAD:
                 cond = ((loc >> ttb[ins["cidx"]]) & 1) == 1
-            if op == T2_H:
+            if op in (T2_H, T2_HPH):
                 u = np.array([[1, 1], [1, -1]], dtype=complex)
             elif op == T2_ROT:  # shears a += t b, b += s a, a += t b (tileprog.h)
                 tt, ss = (float(np.float32(v)) for v in t2["mats"][ins["aux"]][:2])

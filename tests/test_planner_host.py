@@ -44,6 +44,8 @@ def test_t2_qpe(sv, orc, n):
     g, expected, _ = C.qpe(n, seed=n)
     plan = check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED), sv.SV_C64, 1e-5)
     assert all(p["kernel"] == "t2" for p in plan["passes"])
+    # inverse-QFT steps on register bits run as phased butterflies
+    assert planemu.T2_HPH in t2_ops(plan)
 
 
 @pytest.mark.parametrize("chunk", [4, 5, 6, 7])
