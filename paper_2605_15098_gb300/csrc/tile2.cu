@@ -618,8 +618,9 @@ sv_status t2_prepare(sv_state *h) {
         for (auto kern : {k_tile2<13, 0>, k_tile2<13, kFeatX>, k_tile2<13, kFeatR>, k_tile2<13, kFeatAll>})
             SV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Geo<13>::kSmemBytes));
-        SV_CUDA(cudaFuncSetAttribute(k_tile2<14, kFeatAll>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)Geo<14>::kSmemBytes));
+        for (auto kern : {k_tile2<14, 0>, k_tile2<14, kFeatX>, k_tile2<14, kFeatR>, k_tile2<14, kFeatAll>})
+            SV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Geo<14>::kSmemBytes));
         configured = true;
     }
     return SV_OK;
@@ -662,12 +663,15 @@ sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
                 : (in.op == T2_RGATE || in.op == T2_ROT) ? kFeatR
                 : in.op == T2_GATE                        ? kFeatU
                                                           : 0;
-    auto kern = k_tile2<14, kFeatAll>;
-    if (p.k == 13)
-        kern = need == 0 ? k_tile2<13, 0>
-             : need == kFeatX ? k_tile2<13, kFeatX>
-             : need == kFeatR ? k_tile2<13, kFeatR>
-                              : k_tile2<13, kFeatAll>;
+    auto kern = need == 0 ? k_tile2<13, 0>
+              : need == kFeatX ? k_tile2<13, kFeatX>
+              : need == kFeatR ? k_tile2<13, kFeatR>
+                               : k_tile2<13, kFeatAll>;
+    if (p.k == 14)
+        kern = need == 0 ? k_tile2<14, 0>
+             : need == kFeatX ? k_tile2<14, kFeatX>
+             : need == kFeatR ? k_tile2<14, kFeatR>
+                              : k_tile2<14, kFeatAll>;
     const int threads = p.k == 13 ? Geo<13>::kThreads : Geo<14>::kThreads;
     const size_t smem = p.k == 13 ? Geo<13>::kSmemBytes : Geo<14>::kSmemBytes;
     int per_sm = 0;
