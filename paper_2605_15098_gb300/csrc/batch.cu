@@ -183,10 +183,17 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
         cost[i] = (double)std::max<size_t>(1, cp.passes.size()) * (double)(UINT64_C(1) << cp.nphys);
         for (const T2Pass &t2 : cp.passes) {
             T2Args a{};
+            if (pass.size() == (size_t)bi.pass0) {  // the first pass generates |0...0>
+                a.gen = 1;
+                a.gen_basis = 0;
+                a.gen_local = 0;
+            }
             a.gmask = t2.gmask;
             a.ntiles = UINT64_C(1) << (cp.nphys - t2.k);
             a.c = t2.c;
             a.nins = (int)t2.ins.size();
+            a.nfac = (int)t2.factors.size();
+            a.nstat = (int)t2.stat.size();
             a.last_stage = t2.last_stage;
             a.nruns = t2.nruns;
             a.ntterms = (int)t2.tterms.size();
@@ -265,6 +272,9 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
     args.out_p = b->out_p;
     args.err = b->err;
     args.tables = reinterpret_cast<const float2 *>(b->tables);
+    args.need = 0;
+    for (const Compiled &cp : comp)
+        for (const T2Pass &t2 : cp.passes) args.need |= t2_gate_kinds(t2);
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(SV_ERR_CUDA, "batch set-up failed"));

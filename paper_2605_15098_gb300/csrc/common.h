@@ -161,6 +161,9 @@ sv_status sample_device(sv_state *h, const double *dev_p, uint64_t len,
 struct T2Pass;
 struct T2Device;
 size_t t2_smem_bytes();
+// Gate kinds (X, real, general 2x2) a register-stage programme uses: picks the
+// kernel instantiation.
+int t2_gate_kinds(const T2Pass &p);
 sv_status t2_prepare(sv_state *h);
 // gen_basis >= 0: the state is that basis state and the pass generates it
 // instead of reading the buffer.

@@ -91,6 +91,7 @@ struct BatchArgs {
     double *out_p;
     int *err;
     const float2 *tables;
+    int need;  // gate kinds the programmes use (host side: picks the kernel instantiation)
 };
 
 // Compile a tile pass; returns "" on success or the reason the pass cannot

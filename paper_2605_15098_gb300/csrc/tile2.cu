@@ -127,7 +127,8 @@ __device__ __forceinline__ void run_gate(RegsN<NP> &r, const float4 *mrec, uint3
 template <int K, bool kDirect, bool kSmemProg, int F, typename Hook>
 __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hook) {
     using G = Geo<K>;
-    // the programme: copied to shared memory by k_tile2, read from global by k_batch
+    // the programme: copied to shared memory by k_tile2 (once per CTA) and k_batch
+    // (once per pass), or read from global memory
     const int4 *ins = kSmemProg ? reinterpret_cast<const int4 *>(t2_dyn_smem + G::kOffIns) : a.ins;
     const int4 *fac = kSmemProg ? reinterpret_cast<const int4 *>(t2_dyn_smem + G::kOffFac) : a.fac;
     const uint32_t *stat =
@@ -440,6 +441,7 @@ __global__ void __launch_bounds__(Geo<K>::kThreads, K == kT2Qubits ? 2 : 1)
 // passes of the instance (the first pass starts from |0...0> in shared memory
 // instead of reading the state), then the FP64 argmax of the marginal over
 // the instance's read-out qubits.  States of up to 2^20 amplitudes stay in L2.
+template <int F>
 __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ states, const BatchArgs B) {
     extern __shared__ __align__(1024) unsigned char sm[];
     float4 *tile4 = reinterpret_cast<float4 *>(sm);
@@ -476,30 +478,27 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
         }
         for (int p = 0; p < I.npass; p++) {
             const T2Args &a = B.passes[I.pass0 + p];
-            const int nchunks = 1 << (kT2Qubits - a.c);
-            const uint32_t chunk_bytes = 8u << a.c;
+            // the first pass generates |0...0> in registers; later passes read
+            // the state with bulk copies, the next tile's issued as soon as
+            // the current one's last stage change has read shared memory, and
+            // write it straight from registers
+            if (!a.gen && tid < 32) issue_tile_load<kT2Qubits>(a, sm, state, 0, bar, tid);
+            {  // the pass's programme into shared memory (sizes bounded by the stage compiler)
+                int4 *si = reinterpret_cast<int4 *>(sm + G13::kOffIns);
+                int4 *sf = reinterpret_cast<int4 *>(sm + G13::kOffFac);
+                uint32_t *ss = reinterpret_cast<uint32_t *>(sm + G13::kOffStat);
+                for (int i = tid; i < a.nins; i += blockDim.x) si[i] = __ldg(a.ins + i);
+                for (int i = tid; i < a.nfac; i += blockDim.x) sf[i] = __ldg(a.fac + i);
+                const int nst = min(a.nstat, G13::kStatRows * G13::kThreads);
+                for (int i = tid; i < nst; i += blockDim.x) ss[i] = __ldg(a.stat + i);
+            }
             for (uint64_t tile = 0; tile < a.ntiles; tile++) {
-                const uint64_t base = pdep(tile, a.gmask);
-                if (p == 0) {
-                    for (int v = tid; v < (1 << kT2Qubits) / 2; v += blockDim.x)
-                        tile4[v] = make_float4((v == 0 && base == 0) ? 1.f : 0.f, 0.f, 0.f, 0.f);
-                } else if (tid < 32) {
-                    if (tid == 0) {
-                        fence_async_smem();
-                        mbar_expect_tx(bar, kTileBytes);
-                    }
-                    __syncwarp();
-                    for (int j = tid; j < nchunks; j += 32) {
-                        uint64_t off = 0;
-                        for (int b = 0; b < kT2Qubits - a.c; b++)
-                            if ((j >> b) & 1) off |= UINT64_C(1) << a.slot_phys[a.c + b];
-                        bulk_g2s(sm + (size_t)j * chunk_bytes, state + 2 * (base + off), chunk_bytes, bar);
-                    }
-                }
+                __syncthreads();  // the previous tile's programme may still read lin / cst
                 for (int i = tid; i < a.nruns * 16; i += blockDim.x) lin[i] = 0u;
                 for (int i = tid; i < a.nruns; i += blockDim.x) cst[i] = 0u;
-                if (tid == 0) t2_tile_base = base;
+                if (tid == 0) t2_tile_base = pdep(tile, a.gmask);
                 __syncthreads();
+                const uint64_t base = t2_tile_base;
                 for (int i = tid; i < a.ntterms; i += blockDim.x) {
                     const T2TileTerm t = a.tterms[i];
                     bool on = (base >> t.g0) & 1;
@@ -507,32 +506,22 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
                     if (on) atomicAdd(t.tb >= 0 ? &lin[t.run * 16 + t.tb] : &cst[t.run], t.theta);
                 }
                 bool timed_out = false;
-                if (p > 0) {
+                if (!a.gen) {
                     timed_out = !mbar_wait(bar, parity);
                     parity ^= 1u;
                 }
                 if (__syncthreads_or(timed_out)) {
                     if (tid == 0) atomicExch(B.err, 1);
-                    mbar_wait(bar, parity ^ 1u);
+                    mbar_wait(bar, parity ^ 1u);  // a second bounded wait for copies in flight
                     return;
                 }
-                t2_run<kT2Qubits, false, false, kFeatAll>(a, nullptr, NoHook{});
-                fence_async_smem();
-                __syncthreads();
-                if (tid < 32) {
-                    for (int j = tid; j < nchunks; j += 32) {
-                        uint64_t off = 0;
-                        for (int b = 0; b < kT2Qubits - a.c; b++)
-                            if ((j >> b) & 1) off |= UINT64_C(1) << a.slot_phys[a.c + b];
-                        bulk_s2g(state + 2 * (base + off), sm + (size_t)j * chunk_bytes, chunk_bytes);
-                    }
-                    bulk_commit();
-                    bulk_wait_read();
-                }
-                __syncthreads();
+                auto hook = [&]() {
+                    if (!a.gen && tid < 32 && tile + 1 < a.ntiles)
+                        issue_tile_load<kT2Qubits>(a, sm, state, tile + 1, bar, tid);
+                };
+                t2_run<kT2Qubits, true, true, F>(a, reinterpret_cast<float4 *>(state), hook);
             }
-            // the next pass (or the read-out) reads what this pass wrote
-            if (tid < 32) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+            // the next pass's bulk copies (and the read-out) see this pass's stores
             asm volatile("fence.proxy.async;" ::: "memory");
             __syncthreads();
         }
@@ -548,13 +537,25 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
             uint64_t xy = 0;
             for (int j = 0; j < I.m; j++)
                 if ((y >> j) & 1) xy |= UINT64_C(1) << I.pos[j];
-            double acc = 0.0;
+            // exact FP32 squares (product + fmaf remainder) summed as a
+            // double-float pair: FP64-accurate without FP64 arithmetic
+            float hi = 0.f, lo = 0.f;
+            auto two_sum = [&](float b) {
+                const float t = hi + b;
+                const float bb = t - hi;
+                lo += (hi - (t - bb)) + (b - bb);
+                hi = t;
+            };
             uint64_t xr = 0;
             do {
                 const float2 amp = reinterpret_cast<const float2 *>(state)[xy | xr];
-                acc += (double)amp.x * amp.x + (double)amp.y * amp.y;
+                const float pr = amp.x * amp.x, pi = amp.y * amp.y;
+                lo += fmaf(amp.x, amp.x, -pr) + fmaf(amp.y, amp.y, -pi);
+                two_sum(pr);
+                two_sum(pi);
                 xr = ((xr | ~rest) + 1) & rest;
             } while (xr);
+            const double acc = (double)hi + (double)lo;
             tot += acc;
             if (acc > best) {
                 best = acc;
@@ -599,6 +600,16 @@ __global__ void k_phase_tables(float2 *t) {
 }  // namespace
 
 size_t t2_smem_bytes() { return kSmemBytes; }
+
+int t2_gate_kinds(const T2Pass &p) {
+    int need = 0;
+    for (const T2Ins &in : p.ins)
+        need |= in.op == T2_X                             ? kFeatX
+                : (in.op == T2_RGATE || in.op == T2_ROT) ? kFeatR
+                : in.op == T2_GATE                        ? kFeatU
+                                                          : 0;
+    return need;
+}
 
 sv_status t2_prepare(sv_state *h) {
     if (h->t2_tables) return SV_OK;
@@ -657,12 +668,7 @@ sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
     a.epi = d.epi;
     if (p.k != 13 && p.k != 14) return fail(SV_ERR_ARG, "internal: register-stage tile of 2^%d", p.k);
     // the smallest instantiation whose gate kinds cover the programme
-    int need = 0;
-    for (const T2Ins &in : p.ins)
-        need |= in.op == T2_X                             ? kFeatX
-                : (in.op == T2_RGATE || in.op == T2_ROT) ? kFeatR
-                : in.op == T2_GATE                        ? kFeatU
-                                                          : 0;
+    const int need = t2_gate_kinds(p);
     auto kern = need == 0 ? k_tile2<13, 0>
               : need == kFeatX ? k_tile2<13, kFeatX>
               : need == kFeatR ? k_tile2<13, kFeatR>
@@ -705,15 +711,20 @@ sv_status t2_build_tables(void **tables, int **err, cudaStream_t stream) {
 sv_status t2_batch_launch(float *states, const BatchArgs &b, int sm_count, cudaStream_t stream) {
     static bool configured = false;
     if (!configured) {
-        SV_CUDA(cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kSmemBytes));
+        for (auto kern : {k_batch<0>, k_batch<kFeatX>, k_batch<kFeatR>, k_batch<kFeatAll>})
+            SV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
         configured = true;
     }
+    // the smallest instantiation whose gate kinds cover every programme
+    auto kern = b.need == 0 ? k_batch<0>
+              : b.need == kFeatX ? k_batch<kFeatX>
+              : b.need == kFeatR ? k_batch<kFeatR>
+                                 : k_batch<kFeatAll>;
     int per_sm = 0;
-    SV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kT2Threads, kSmemBytes));
+    SV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kT2Threads, kSmemBytes));
     if (per_sm < 1) return fail(SV_ERR_UNSUPPORTED, "batched kernel does not fit on an SM");
     const int grid = std::max(1, std::min(b.count, per_sm * sm_count));
-    k_batch<<<grid, kT2Threads, kSmemBytes, stream>>>(states, b);
+    kern<<<grid, kT2Threads, kSmemBytes, stream>>>(states, b);
     SV_CUDA(cudaGetLastError());
     note_launch();
     return SV_OK;
