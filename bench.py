@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-paper", action="store_true")
     ap.add_argument("--no-other", action="store_true", help="skip the other tile kernel's timing")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-planner comparison")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the QPE n = 20..32 sweep")
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -241,6 +242,62 @@ def replica_max(dist, x: float) -> float:
 def replica_value(world: int, steps: int, max_ms: float) -> float:
     """Whole-job throughput: all replicas' steps over the slowest rank's time."""
     return world * steps / (max_ms / 1e3)
+
+
+SWEEP_N = (20, 24, 28, 30, 32)
+
+
+def qpe_sweep(sv, C, stream, peak: float, no_pergate: bool) -> dict:
+    """QPE circuit time at n = 20 .. 32 in complex64 and complex128, on the
+    partitioned path (the autotuner's measured choice; library defaults for
+    complex128 above n = 28, where each candidate takes seconds) and the
+    per-gate path.  HBM bytes follow the full-sweep convention
+    2 x passes x 2^n x sizeof(amplitude)."""
+    import torch
+
+    res = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for nn in SWEEP_N:
+        g, _, info = C.qpe(nn)
+        for dname, dcode, tdt, ab in (("c64", sv.SV_C64, torch.complex64, 8),
+                                      ("c128", sv.SV_C128, torch.complex128, 16)):
+            buf = torch.empty(1 << nn, dtype=tdt, device="cuda")
+            h = sv.sv_create_on(nn, dcode, buf.data_ptr(), (1 << nn) * ab, stream.cuda_stream)
+            row = {}
+            for mname, mode in (("partitioned", sv.SV_MODE_PARTITIONED), ("per_gate", sv.SV_MODE_PERGATE)):
+                if mname == "per_gate" and no_pergate:
+                    continue
+                cfg, tuned = sv.make_config(mode), False
+                if mname == "partitioned" and (dname == "c64" or nn <= 28):
+                    cfg, _ = sv.sv_autotune(h, g)  # measured choice of tile, chunk and kernel
+                    tuned = True
+                reps = 3 if nn <= 28 else 1
+                if mname == "partitioned" or nn <= 28:  # warm-up (plan, compile, upload)
+                    sv.sv_reset(h)
+                    sv.sv_apply_circuit(h, g, cfg)
+                e0.record(stream)
+                for _ in range(reps):
+                    sv.sv_reset(h)
+                    sv.sv_apply_circuit(h, g, cfg)
+                    idx, p = sv.sv_argmax(h, info["mask"])
+                e1.record(stream)
+                stream.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                st = sv.sv_last_stats(h)
+                gbs = st["sweep_bytes"] / (ms / 1e3) / 1e9
+                row[mname] = {"circuit_ms": round(ms, 3), "passes": st["passes"],
+                              "hbm_gbs_full_sweeps": round(gbs, 1),
+                              "frac_of_measured_hbm": round(gbs / peak, 4),
+                              "outcome_ok": bool(idx == info["y"] and abs(p - 1) < 1e-5),
+                              "config": sv.config_dict(cfg) if tuned else "library defaults"}
+            if "per_gate" in row:
+                row["speedup_partitioned"] = round(row["per_gate"]["circuit_ms"] /
+                                                   row["partitioned"]["circuit_ms"], 2)
+            res[f"n{nn}_{dname}"] = row
+            sv.sv_destroy(h)
+            del buf
+            torch.cuda.empty_cache()
+    return res
 
 
 def run_ours(args, world, rank, local):
@@ -461,6 +518,10 @@ def run_ours(args, world, rank, local):
         out["c128"] = res
         sv.sv_destroy(h2)
         del buf2
+
+    # ---- QPE sweep: n = 20 .. 32, complex64 and complex128, partitioned vs per-gate ----
+    if not args.no_sweep and dt == sv.SV_C64:
+        out["qpe_sweep"] = qpe_sweep(sv, C, stream, peak, args.no_pergate)
 
     # ---- batched QPE (4096 instances, n uniform in 10..20): one graph launch ----
     if not args.no_batch:
