@@ -10,8 +10,10 @@
 //   3. the stage programme runs: each thread holds 32 amplitudes as 16
 //      packed pairs (re and im of two neighbouring amplitudes), gates on
 //      register bits are packed f32x2 arithmetic, gates on lane bits use
-//      warp shuffles, a stage change goes through shared memory;
-//   4. the tile is written back with bulk copies (TMA store).
+//      warp shuffles, a stage change goes through shared memory; once the
+//      last stage change has read shared memory, the next tile's copies start;
+//   4. each thread writes its amplitudes straight from registers to the
+//      global state (16-byte streaming stores).
 // Hadamards are applied unnormalised ([[1,1],[1,-1]]) and the pass ends with
 // one multiplication by 2^(-h/2), exact for even h, so the norm carries no
 // bias from a rounded 1/sqrt(2).
@@ -59,15 +61,12 @@ constexpr size_t kSmemBytes = G13::kSmemBytes;
 
 
 // ---------------------------------------------------------------- the kernel
-// Run a pass's programme on the tile.  The first stage reads the tile from
-// shared memory (interleaved complex64, local index order).  After the last
-// stage change has read shared memory, `hook()` runs (k_tile2 starts the next
-// tile's bulk copies there).  The result goes back to shared memory,
-// interleaved (kDirect = false), or straight from registers to the global
-// state (kDirect = true; `gw` gives the global offset of a single tile bit).
-struct NoHook {
-    __device__ void operator()() const {}
-};
+// Run a pass's programme (in shared memory) on the tile.  The first stage
+// reads the tile from shared memory (interleaved complex64, local index
+// order), or generates the recorded basis state.  After the last stage change
+// has read shared memory, `hook()` runs (the callers start the next tile's
+// bulk copies there).  The result goes straight from registers to the global
+// state, at the offsets of the final layout's write-back record.
 
 extern __shared__ __align__(1024) unsigned char t2_dyn_smem[];
 __shared__ uint64_t t2_tile_base;  // physical index of the current tile's amplitude 0
@@ -124,15 +123,14 @@ __device__ __forceinline__ void run_gate(RegsN<NP> &r, const float4 *mrec, uint3
     }
 }
 
-template <int K, bool kDirect, bool kSmemProg, int F, typename Hook>
+template <int K, int F, typename Hook>
 __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hook) {
     using G = Geo<K>;
-    // the programme: copied to shared memory by k_tile2 (once per CTA) and k_batch
-    // (once per pass), or read from global memory
-    const int4 *ins = kSmemProg ? reinterpret_cast<const int4 *>(t2_dyn_smem + G::kOffIns) : a.ins;
-    const int4 *fac = kSmemProg ? reinterpret_cast<const int4 *>(t2_dyn_smem + G::kOffFac) : a.fac;
-    const uint32_t *stat =
-        kSmemProg ? reinterpret_cast<const uint32_t *>(t2_dyn_smem + G::kOffStat) : a.stat;
+    // the programme: copied to shared memory by k_tile2 (once per CTA) and
+    // k_batch (once per pass); static phase rows beyond the copy stay in global memory
+    const int4 *ins = reinterpret_cast<const int4 *>(t2_dyn_smem + G::kOffIns);
+    const int4 *fac = reinterpret_cast<const int4 *>(t2_dyn_smem + G::kOffFac);
+    const uint32_t *stat = reinterpret_cast<const uint32_t *>(t2_dyn_smem + G::kOffStat);
     float4 *tile4 = reinterpret_cast<float4 *>(t2_dyn_smem);
     const float2 *tab = reinterpret_cast<const float2 *>(t2_dyn_smem + G::kOffTab);
     const uint32_t *lin = reinterpret_cast<const uint32_t *>(t2_dyn_smem + G::kOffLin);
@@ -217,9 +215,8 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
         auto thread_phase = [&](const int4 fd) -> float2 {
             const uint32_t w0 = (uint32_t)fd.x;
             const int run = fd.y;
-            // static phase rows beyond the shared-memory copy stay in global memory
-            uint32_t u = (kSmemProg && fd.z >= G::kStatRows) ? __ldg(a.stat + fd.z * G::kThreads + tid)
-                                                             : stat[fd.z * G::kThreads + tid];
+            uint32_t u = fd.z >= G::kStatRows ? __ldg(a.stat + fd.z * G::kThreads + tid)
+                                              : stat[fd.z * G::kThreads + tid];
             if (w0 & 0x200u) u += cst[run];
             const int lr = (int)((w0 >> kFacLinShift) & 0x1fu) - 1;
             if (lr >= 0) u += lin[run * 16 + lr];
@@ -331,22 +328,14 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
         hook();
     }
     if (!live) return;
-    if constexpr (kDirect) {
-        const T2Epilogue *E = a.epi;
-        const uint64_t g0 = t2_tile_base + __ldg(&E->glo[tid & 31]) + __ldg(&E->ghi[tid >> 5]);
-        const uint64_t g1 = __ldg(&E->g[0]), g2 = __ldg(&E->g[1]), g3 = __ldg(&E->g[2]),
-                       g4 = __ldg(&E->g[3]);
+    const T2Epilogue *E = a.epi;
+    const uint64_t g0 = t2_tile_base + __ldg(&E->glo[tid & 31]) + __ldg(&E->ghi[tid >> 5]);
+    const uint64_t g1 = __ldg(&E->g[0]), g2 = __ldg(&E->g[1]), g3 = __ldg(&E->g[2]), g4 = __ldg(&E->g[3]);
 #pragma unroll
-        for (int q = 0; q < kNP2; q++) {
-            const uint64_t g = g0 + ((q & 1) ? g1 : 0) + ((q & 2) ? g2 : 0) + ((q & 4) ? g3 : 0) +
-                               ((q & 8) ? g4 : 0);
-            __stcs(gstate + (g >> 1), make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y));
-        }
-    } else {
-        const Layout2 L(a.layx + stage, tid);
-#pragma unroll
-        for (int q = 0; q < kNP2; q++)
-            tile4[L.idx(q)] = make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y);
+    for (int q = 0; q < kNP2; q++) {
+        const uint64_t g = g0 + ((q & 1) ? g1 : 0) + ((q & 2) ? g2 : 0) + ((q & 4) ? g3 : 0) +
+                           ((q & 8) ? g4 : 0);
+        __stcs(gstate + (g >> 1), make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y));
     }
 }
 
@@ -431,7 +420,7 @@ __global__ void __launch_bounds__(Geo<K>::kThreads, K == kT2Qubits ? 2 : 1)
         auto hook = [&]() {
             if (!a.gen && tid < 32 && next < a.ntiles) issue_tile_load<K>(a, sm, state, next, bar, tid);
         };
-        t2_run<K, true, true, F>(a, reinterpret_cast<float4 *>(state), hook);
+        t2_run<K, F>(a, reinterpret_cast<float4 *>(state), hook);
         parity ^= 1u;
     }
 }
@@ -519,7 +508,7 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
                     if (!a.gen && tid < 32 && tile + 1 < a.ntiles)
                         issue_tile_load<kT2Qubits>(a, sm, state, tile + 1, bar, tid);
                 };
-                t2_run<kT2Qubits, true, true, F>(a, reinterpret_cast<float4 *>(state), hook);
+                t2_run<kT2Qubits, F>(a, reinterpret_cast<float4 *>(state), hook);
             }
             // the next pass's bulk copies (and the read-out) see this pass's stores
             asm volatile("fence.proxy.async;" ::: "memory");
