@@ -187,6 +187,7 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
                 a.gen = 1;
                 a.gen_basis = 0;
                 a.gen_local = 0;
+                a.gen_hmask = t2.gen_hmask;
             }
             a.gmask = t2.gmask;
             a.ntiles = UINT64_C(1) << (cp.nphys - t2.k);

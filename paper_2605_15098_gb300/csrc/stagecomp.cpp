@@ -619,6 +619,25 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
         }
         out->ins.swap(merged);
     }
+    if (!fused) {
+        // The leading Hadamards: uncontrolled, on distinct tile bits, before
+        // any step other than a stage change.  On a basis state |b> they give
+        // +-1 on the indices that agree with b off those bits (sign: the
+        // parity of b on them), 0 elsewhere, up to the closing scale.
+        int cur = -1;
+        for (T2Ins &in : out->ins) {
+            if (in.op == T2_STAGE) {
+                cur = in.aux;
+                continue;
+            }
+            if (in.op != T2_H || in.ccls != T2C_NONE || cur < 0) break;
+            const T2Stage &st = out->stages[cur];
+            const int tb = in.cls == T2C_REG ? st.tb[in.idx] : st.tb[5 + in.idx];
+            if ((out->gen_hmask >> tb) & 1u) break;
+            out->gen_hmask |= 1u << tb;
+            in.op = T2_HG;
+        }
+    }
     if (!fused && (out->ins.size() > (size_t)kT2SmemIns || out->factors.size() > (size_t)kT2SmemFactors))
         return "programme longer than the kernel's shared-memory copy";
     for (size_t i = 0; i < out->ins.size(); i++)

@@ -20,6 +20,7 @@ struct T2Pass {
     int nruns = 0;
     int n_h = 0;                    // unnormalised Hadamards (2^(-n_h/2) at the end)
     int sign_flips = 0;             // rotations run as -1 times a shear product (sign at the end)
+    uint32_t gen_hmask = 0;         // tile bits of the leading Hadamards (T2_HG)
     int last_stage = -1;            // index in `ins` of the last T2_STAGE
     std::vector<T2Ins> ins;
     std::vector<T2Stage> stages;
@@ -66,9 +67,11 @@ struct T2Args {
     const T2Epilogue *epi;  // write-back offsets (register-stage kernel)
     // gen != 0: the state is the basis state |gen_basis> (physical index) and
     // is generated in registers instead of read; gen_local is its index inside
-    // the tile that holds it
+    // the tile that holds it; gen_hmask: tile bits whose leading Hadamards
+    // (T2_HG) the generation includes
     int gen, gen_local;
     uint64_t gen_basis;
+    uint32_t gen_hmask;
 };
 
 // One instance of a batch: its state, passes and read-out qubits.

@@ -157,19 +157,23 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
             stage = w.w;
             {
                 const Layout2 L(a.layx + stage, tid);
-                if (!live && a.gen) {  // the basis state, generated instead of read
+                if (!live && a.gen) {
+                    // the basis state |b>, after the leading Hadamards on the
+                    // tile bits in gen_hmask (unnormalised: the closing scale
+                    // holds their 2^(-1/2)), generated instead of read:
+                    // +-1 where the index agrees with b off those bits, with
+                    // the sign of the parity of b on them, 0 elsewhere
                     const bool has = (a.gen_basis & a.gmask) == t2_tile_base;
-                    const int lp = a.gen_local >> 1;
+                    const uint32_t gl = (uint32_t)a.gen_local, hm = a.gen_hmask;
+                    auto amp = [&](uint32_t i) -> float {
+                        if (!has || ((i ^ gl) & ~hm)) return 0.f;
+                        return (__popc(i & gl & hm) & 1) ? -1.f : 1.f;
+                    };
 #pragma unroll
                     for (int q = 0; q < kNP2; q++) {
-                        r.re[q] = make_float2(0.f, 0.f);
+                        const uint32_t i0 = 2u * (uint32_t)L.idx(q);
+                        r.re[q] = make_float2(amp(i0), amp(i0 + 1));
                         r.im[q] = make_float2(0.f, 0.f);
-                        if (has && L.idx(q) == lp) {
-                            if (a.gen_local & 1)
-                                r.re[q].y = 1.f;
-                            else
-                                r.re[q].x = 1.f;
-                        }
                     }
                 } else {
 #pragma unroll
@@ -269,6 +273,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
             }
             continue;
         }
+        if (op == T2_HG && a.gen) continue;  // included in the generated state
         // gates (no register-bit controls: the stage compiler never emits them);
         // one switch on the handler code the stage compiler set (tileprog.h)
         const int j = (int8_t)((w.x >> 16) & 0xff);
@@ -634,6 +639,7 @@ sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
         a.gen_basis = (uint64_t)gen_basis;
         for (int s = 0; s < p.k; s++)
             a.gen_local |= (int)((a.gen_basis >> p.slot_phys[s]) & 1) << s;
+        a.gen_hmask = p.gen_hmask;
     }
     a.gmask = p.gmask;
     a.ntiles = UINT64_C(1) << (h->n - p.k);

@@ -62,9 +62,12 @@ enum T2Op : int32_t {
     T2_BLOCK = 6,  // fused kernel: 32x32 block `aux` on the register bits (tensor cores)
     T2_RGATE = 7,  // real 2x2 (matrix record `aux`, imaginary parts zero): half the arithmetic
     T2_ROT = 8,    // uncontrolled register-bit rotation as three shears (record: t, s)
-    T2_HPH = 9     // diagonal run [e0, e1) then H on register bit idx, in one sweep:
+    T2_HPH = 9,    // diagonal run [e0, e1) then H on register bit idx, in one sweep:
                    // the run is the identity where bit idx is 0, and holds at
                    // most one phase table and one per-thread factor on bit idx
+    T2_HG = 10     // H of the programme's leading Hadamards (distinct tile bits, before
+                   // any other step): a pass that generates a basis state generates
+                   // the state after them and skips them; otherwise an H
 };
 
 // Fused blocks: a 32x32 complex matrix U on the register index (bit j of the

@@ -16,7 +16,7 @@ MASK32 = TWO32 - 1
 TOP_GATE, TOP_GATE_CL, TOP_GATE_CG, TOP_DIAG, TOP_SWAP, TOP_H, TOP_X = range(7)
 TERM_L, TERM_LL, TERM_G, TERM_LG, TERM_GG = range(5)
 # register-stage ops (tileprog.h)
-T2_STAGE, T2_GATE, T2_H, T2_X, T2_DIAG, T2_SCALE, T2_BLOCK, T2_RGATE, T2_ROT, T2_HPH = range(10)
+T2_STAGE, T2_GATE, T2_H, T2_X, T2_DIAG, T2_SCALE, T2_BLOCK, T2_RGATE, T2_ROT, T2_HPH, T2_HG = range(11)
 C_NONE, C_REG, C_LANE, C_THREAD, C_GLOBAL = range(5)
 
 
@@ -220,7 +220,7 @@ def run_t2_pass(state, p):
                 cond = ((loc >> reg[ins["cidx"]]) & 1) == 1
             elif ins["ccls"] == C_THREAD:
                 cond = ((loc >> ttb[ins["cidx"]]) & 1) == 1
-            if op in (T2_H, T2_HPH):
+            if op in (T2_H, T2_HPH, T2_HG):  # T2_HG runs as H when the pass reads its state
                 u = np.array([[1, 1], [1, -1]], dtype=complex)
             elif op == T2_ROT:  # shears a += t b, b += s a, a += t b (tileprog.h)
                 tt, ss = (float(np.float32(v)) for v in t2["mats"][ins["aux"]][:2])

@@ -5,7 +5,7 @@ FP64 oracle, including what the adopted device buffer holds."""
 import numpy as np
 import pytest
 
-from gen import mixed_circuit
+from gen import mixed_circuit, without_leading_x
 from paper_2605_15098_gb300 import circuits as C
 
 pytestmark = pytest.mark.gpu
@@ -85,3 +85,31 @@ def test_qpe_first_pass_generates(sv, orc):
     assert st["sweep_bytes"] == sum(r["bytes"] for r in tiles)
     fid = abs(np.vdot(ref, got.astype(np.complex128))) ** 2
     assert 1 - fid <= 1e-6
+
+
+@pytest.mark.parametrize("n,seed", [(14, 1), (16, 2), (19, 3)])
+def test_leading_hadamards_are_generated(sv, orc, n, seed):
+    """The first register-stage pass generates |b> after the programme's
+    leading Hadamards (signs where b has a 1 under an H) instead of applying
+    them; a later pass with the same leading Hadamards applies them."""
+    rng = np.random.default_rng(seed)
+    xs = [int(q) for q in rng.choice(n, size=n // 2, replace=False)]
+    hs = [int(q) for q in rng.choice(n, size=n - 3, replace=False)]
+    body = mixed_circuit(n, 60, seed + 40, kinds=(0, 1, 2, 3, 4, 5, 6, 7, 9, 10))  # no CU
+    g = C.gates([C.x(q) for q in xs] + [C.h(q) for q in hs] + list(body) + [C.h(q) for q in hs])
+    ref = orc.run(n, g)
+    plan = sv.sv_plan_export(n, sv.SV_C64, without_leading_x(g), sv.make_config(sv.SV_MODE_PARTITIONED))
+    first = plan["passes"][0]
+    assert first["kernel"] == "t2"
+    assert sum(1 for i in first["t2"]["ins"] if i["op"] == 10) >= 4  # T2_HG (tileprog.h)
+    with sv.State(n, sv.SV_C64) as s:
+        s.apply(g, sv.make_config(sv.SV_MODE_PARTITIONED))
+        got = s.amplitudes()
+    assert abs(np.vdot(ref, got.astype(np.complex128))) ** 2 >= 1.0 - 1e-6
+    # the same list on a state that is not a basis state: the Hadamards run
+    with sv.State(n, sv.SV_C64) as s:
+        s.apply(C.gates([C.h(0)]), sv.make_config(sv.SV_MODE_PERGATE))
+        s.apply(g, sv.make_config(sv.SV_MODE_PARTITIONED))
+        got2 = s.amplitudes()
+    ref2 = orc.run(n, np.concatenate([C.gates([C.h(0)]), g]))
+    assert abs(np.vdot(ref2, got2.astype(np.complex128))) ** 2 >= 1.0 - 1e-6
