@@ -106,8 +106,11 @@ enum {
     SV_FLAG_NO_RELABEL = 4,     /* execute SWAP gates as data movement        */
     SV_FLAG_GENERIC_TILE = 8,   /* use the generic shared-memory tile kernel
                                    for every pass (no register stages)        */
-    SV_FLAG_NO_PLAN_CACHE = 16  /* plan, compile and upload the list on this
+    SV_FLAG_NO_PLAN_CACHE = 16, /* plan, compile and upload the list on this
                                    call even if the handle holds its programme */
+    SV_FLAG_EARLY_DIAG = 32     /* keep each diagonal gate in the first pass
+                                   where it is ready (default: the pass of the
+                                   first later gate it does not commute with)  */
 };
 
 /* Planner choice for partitioned modes. */
@@ -451,7 +454,9 @@ typedef struct sv_plan_choice {
     double learned_ms;           /* measured by sv_planner_judge, else 0       */
     double greedy_ms;            /* measured by sv_planner_judge, else 0       */
     int32_t verdict;             /* planner the judge kept (sv_planner)        */
-    int32_t reserved[7];
+    int32_t early_diag;          /* 1: the chosen plan keeps diagonal gates in
+                                    the first pass where they are ready       */
+    int32_t reserved[6];
 } sv_plan_choice;
 
 /* The learned planner's choice for this gate list (no kernel runs). */

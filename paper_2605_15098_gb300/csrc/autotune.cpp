@@ -97,6 +97,10 @@ extern "C" sv_status sv_autotune(sv_handle h, const sv_gate *host_gates, size_t 
     if (h->n <= 12) add(SV_MODE_PERGATE, 0, 0);
     if (h->dt == SV_C64) {
         for (int c : {4, 5, 6, 7}) add(SV_MODE_PARTITIONED, 0, c);
+        for (int c : {5, 7}) {  // diagonal gates kept in their first ready pass
+            add(SV_MODE_PARTITIONED, 0, c);
+            cands.back().flags = SV_FLAG_EARLY_DIAG;
+        }
         if (h->n > 14)  // 2^14-amplitude tiles: fewer passes, one CTA per SM
             for (int c : {4, 5, 7}) add(SV_MODE_PARTITIONED, 14, c);
         if (h->n > 13)

@@ -88,14 +88,21 @@ sv_status learned_entry(sv_state *h, const std::vector<sv_gate> &gates, const sv
 
     // candidate planner options; the configuration's own options come first
     std::vector<PlanOptions> opts{base};
-    auto add = [&](int k, int c, bool paper) {
+    auto add1 = [&](int k, int c, bool paper, bool late) {
         PlanOptions o = base;
         o.k = k;
         o.c = paper ? k : c;
         o.paper = paper;
+        o.late_diag = late;
         for (const PlanOptions &e : opts)
-            if (e.k == o.k && e.c == o.c && e.paper == o.paper) return;
+            if (e.k == o.k && e.c == o.c && e.paper == o.paper && e.late_diag == o.late_diag) return;
         opts.push_back(o);
+    };
+    // every (k, c) with diagonal gates in their successors' passes and in
+    // the first pass where they are ready
+    auto add = [&](int k, int c, bool paper) {
+        add1(k, c, paper, true);
+        if (!paper) add1(k, c, paper, false);
     };
     if (!dbl) {
         for (int c : {4, 5, 6, 7}) add(13, c, false);
@@ -187,6 +194,7 @@ sv_status learned_entry(sv_state *h, const std::vector<sv_gate> &gates, const sv
             L.ov.kernel = kern;
             L.info.chunk_qubits = cd.opt.c;
             L.info.paper_swap = cd.opt.paper ? 1 : 0;
+            L.info.early_diag = cd.opt.late_diag ? 0 : 1;
             L.info.passes = cd.passes;
             L.info.remaps = cd.remaps;
             L.info.fused_passes = nfused;

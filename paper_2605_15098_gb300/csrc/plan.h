@@ -86,6 +86,7 @@ struct PlanOptions {
     bool relabel = true;
     bool paper = false;  // explicit LRU remaps, tile = the k lowest physical bits
     bool split_u3 = false;  // U3 as P(phi) RY(theta) P(lambda): phases join the diagonal runs
+    bool late_diag = true;  // diagonal gates move to the pass of their first successor
 };
 
 // Planner options of a configuration (library defaults filled in).

@@ -347,6 +347,7 @@ PlanOptions plan_options(int n, sv_dtype dt, const sv_config &cfg) {
     opt.merge_diag = !(cfg.flags & SV_FLAG_NO_DIAG_MERGE);
     opt.relabel = !(cfg.flags & SV_FLAG_NO_RELABEL);
     opt.paper = (cfg.flags & SV_FLAG_PAPER_SWAP) != 0;
+    opt.late_diag = !(cfg.flags & SV_FLAG_EARLY_DIAG);
     if (opt.paper) opt.c = opt.k;  // the block is contiguous
     opt.split_u3 = !dbl;
     return opt;
@@ -457,6 +458,8 @@ std::string build_plan(const std::vector<sv_gate> &gates_in, const PlanOptions &
 
     // 3. passes by list scheduling
     std::vector<char> done(m, 0);
+    std::vector<std::vector<int>> orders;
+    std::vector<std::vector<char>> locals;
     int remaining = m;
     while (remaining > 0) {
         bool in_l[64] = {};
@@ -499,8 +502,44 @@ std::string build_plan(const std::vector<sv_gate> &gates_in, const PlanOptions &
                 cnt++;
             }
 
+        orders.push_back(std::move(order));
+        locals.emplace_back(in_l, in_l + 64);
+    }
+
+    // 4. A diagonal gate is ready as soon as the gates before it on its
+    // qubits are done, but it only has to run before the next gate that acts
+    // non-diagonally on one of them.  It moves to the pass of its first such
+    // successor, at the front of that pass's order: there its phase terms
+    // join the run that feeds that gate instead of forming a run at the end
+    // of an earlier pass.  Gates without a successor stay where they are.
+    std::vector<int> pass_of(m, 0);
+    for (size_t p = 0; p < orders.size(); p++)
+        for (int i : orders[p]) pass_of[i] = (int)p;
+    std::vector<int> first_succ(m, -1);
+    for (int j = 0; j < m; j++)
+        for (int d : pg[j].deps)
+            if (first_succ[d] < 0 || pass_of[j] < first_succ[d]) first_succ[d] = pass_of[j];
+    if (opt.merge_diag && opt.late_diag) {
+        std::vector<std::vector<int>> moved(orders.size());
+        for (size_t p = 0; p < orders.size(); p++) {
+            std::vector<int> keep;
+            for (int i : orders[p]) {
+                if (pg[i].diag && first_succ[i] > (int)p)
+                    moved[first_succ[i]].push_back(i);
+                else
+                    keep.push_back(i);
+            }
+            orders[p].swap(keep);
+        }
+        for (size_t p = 0; p < orders.size(); p++)
+            if (!moved[p].empty()) orders[p].insert(orders[p].begin(), moved[p].begin(), moved[p].end());
+    }
+    for (size_t p = 0; p < orders.size(); p++) {
+        if (orders[p].empty()) continue;
+        bool in_l[64];
+        for (int q = 0; q < 64; q++) in_l[q] = locals[p][q] != 0;
         TilePass tp;
-        std::string e = emit_pass(pg, order, in_l, n, k, c, opt, &tp);
+        std::string e = emit_pass(pg, orders[p], in_l, n, k, c, opt, &tp);
         if (!e.empty()) return e;
         out->passes.push_back(std::move(tp));
     }

@@ -23,6 +23,7 @@ SV_OK, SV_ERR_ARG, SV_ERR_OOM, SV_ERR_CUDA, SV_ERR_TIMEOUT, SV_ERR_STATE, SV_ERR
 SV_MODE_AUTO, SV_MODE_PERGATE, SV_MODE_PARTITIONED, SV_MODE_FUSED = 0, 1, 2, 3
 SV_FLAG_NO_DIAG_MERGE, SV_FLAG_PAPER_SWAP, SV_FLAG_NO_RELABEL, SV_FLAG_GENERIC_TILE = 1, 2, 4, 8
 SV_FLAG_NO_PLAN_CACHE = 16
+SV_FLAG_EARLY_DIAG = 32
 SV_PLANNER_GREEDY, SV_PLANNER_LEARNED = 0, 1
 
 EXPORTS = (
@@ -95,7 +96,8 @@ class sv_plan_choice(ctypes.Structure):
                 ("fused_passes", ctypes.c_int32), ("candidates", ctypes.c_int32),
                 ("predicted_ms", ctypes.c_double), ("greedy_predicted_ms", ctypes.c_double),
                 ("learned_ms", ctypes.c_double), ("greedy_ms", ctypes.c_double),
-                ("verdict", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("verdict", ctypes.c_int32), ("early_diag", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

@@ -106,6 +106,26 @@ def test_diagonal_runs_are_fewest():
     assert kinds(plan).count(planemu.TOP_DIAG) == t - 1
 
 
+@pytest.mark.parametrize("n", [15, 17])
+def test_diagonal_gates_move_to_their_successors_pass(sv, orc, n):
+    """By default a diagonal gate runs in the pass of the first later gate it
+    does not commute with (SV_FLAG_EARLY_DIAG keeps it in its first ready
+    pass).  Both plans match the oracle; QPE's controlled powers then leave
+    the early passes without diagonal runs and the whole plan has fewer."""
+    g, _, _ = C.qpe(n, seed=n + 2)
+    late = check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=5), sv.SV_C64, 1e-5)
+    early = check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=5,
+                                                flags=sv.SV_FLAG_EARLY_DIAG), sv.SV_C64, 1e-5)
+    runs = lambda plan: sum(1 for op in t2_ops(plan) if op in (planemu.T2_DIAG, planemu.T2_HPH))
+    assert len(late["passes"]) == len(early["passes"]) > 1
+    assert runs(late) < runs(early)
+    first = [ins["op"] for ins in late["passes"][0]["t2"]["ins"]]
+    assert planemu.T2_DIAG not in first and planemu.T2_HPH not in first
+    g = C.random_circuit(n, 4, n)
+    for flags in (0, sv.SV_FLAG_EARLY_DIAG):
+        check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED, flags=flags), sv.SV_C64, 2e-5)
+
+
 @pytest.mark.parametrize("flags", [0, 1, 4, 5])
 def test_generic_plan(sv, orc, flags):
     n = 13
