@@ -303,6 +303,13 @@ def qpe_sweep(sv, C, stream, peak: float, no_pergate: bool) -> dict:
 def run_ours(args, world, rank, local):
     import torch
 
+    if world > 1:
+        # the single-GPU side measurements (other kernel, per-gate, paper
+        # scheme, complex128, sweep, batch) run at N = 1 only, so that an
+        # N-GPU run holds its GPUs for the replicated step and e2e alone
+        args.no_other = args.no_pergate = args.no_paper = True
+        args.no_c128 = args.no_sweep = args.no_batch = True
+
     from paper_2605_15098_gb300 import build as B
     from paper_2605_15098_gb300 import circuits as C
 
