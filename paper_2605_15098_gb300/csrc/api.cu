@@ -275,8 +275,10 @@ sv_status sv_argmax(sv_handle h, uint64_t qubit_mask, uint64_t *host_idx, double
     SV_TRY(ensure_probs(h, len * sizeof(double)));
     const double *sums = nullptr;
     int nsums = 0;
-    SV_TRY(marginal_device(h, pos, m, h->probs, false, &sums, &nsums));
-    return argmax_device(h, h->probs, len, host_idx, host_p, sums, nsums);
+    // the marginal stays in physical order (coalesced stores whatever the qubit map)
+    OutPerm perm{};
+    SV_TRY(marginal_device(h, pos, m, h->probs, false, &sums, &nsums, &perm));
+    return argmax_device(h, h->probs, len, host_idx, host_p, sums, nsums, &perm);
 }
 
 sv_status sv_sample(sv_handle h, uint64_t qubit_mask, const double *host_u, size_t shots,

@@ -142,18 +142,27 @@ void cost_features(const sv_launch_record &rec, float *out);
 sv_status cost_predict(sv_cost_model_s *m, const float *host_x, size_t count, float *host_y);
 
 // ---- read-out (measure.cu) ----------------------------------------------------
+// Order of a marginal held in physical order: bit k of an entry's position
+// is output bit bit[k] (m = 0: the entries are in output order).
+struct OutPerm {
+    int m;
+    int8_t bit[34];
+};
+
 // Marginal over physical positions pos[0..m-1] (output bit j <-> pos[j]),
 // renormalised, into device buffer dev_out (2^m doubles), on h->stream.
 // normalise = false leaves the sums unnormalised and returns the block sums
 // whose ordered total is the normaliser (sums_out / nsums_out may be NULL).
+// With perm_out given, the entries stay in physical order (coalesced stores
+// whatever the qubit map) and *perm_out says how to read them.
 sv_status marginal_device(sv_state *h, const int *pos, int m, double *dev_out,
                           bool normalise = true, const double **sums_out = nullptr,
-                          int *nsums_out = nullptr);
-// Lowest index of the maximum of dev_p; with sums given, dev_p is unnormalised
-// and *host_p is max / total.
+                          int *nsums_out = nullptr, OutPerm *perm_out = nullptr);
+// Lowest output index of the maximum of dev_p (entries ordered as `perm`
+// says); with sums given, dev_p is unnormalised and *host_p is max / total.
 sv_status argmax_device(sv_state *h, const double *dev_p, uint64_t len,
                         uint64_t *host_idx, double *host_p, const double *sums = nullptr,
-                        int nsums = 0);
+                        int nsums = 0, const OutPerm *perm = nullptr);
 sv_status sample_device(sv_state *h, const double *dev_p, uint64_t len,
                         const double *host_u, size_t shots, uint64_t *host_out);
 

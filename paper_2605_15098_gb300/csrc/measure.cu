@@ -231,16 +231,27 @@ __device__ __forceinline__ void better(double &v, uint64_t &i, double v2, uint64
     }
 }
 
+// Output index of the entry at position i of a marginal ordered as p says.
+__device__ __forceinline__ uint64_t output_index(uint64_t i, const OutPerm &p) {
+    if (!p.m) return i;
+    uint64_t r = 0;
+    for (int k = 0; k < p.m; k++) r |= ((i >> k) & 1) << p.bit[k];
+    return r;
+}
+
 __global__ void __launch_bounds__(kRedThreads)
 k_argmax(const double *__restrict__ x, const uint64_t *__restrict__ xi, uint64_t len,
-         double *__restrict__ ov, uint64_t *__restrict__ oi) {
+         double *__restrict__ ov, uint64_t *__restrict__ oi, const OutPerm perm) {
     __shared__ double sv_[kRedThreads];
     __shared__ uint64_t si[kRedThreads];
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     double v = -1.0;
     uint64_t idx = ~UINT64_C(0);
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride)
-        better(v, idx, x[i], xi ? xi[i] : i);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
+        const double xv = x[i];
+        // the output index (for ties: the lowest wins) only for a candidate
+        if (xv >= v) better(v, idx, xv, xi ? xi[i] : output_index(i, perm));
+    }
     sv_[threadIdx.x] = v;
     si[threadIdx.x] = idx;
     __syncthreads();
@@ -354,7 +365,7 @@ sv_status ensure_probs(sv_state *h, size_t bytes) {
 
 // pos[j]: physical bit of output bit j.
 sv_status marginal_device(sv_state *h, const int *pos, int m, double *dev_out, bool normalise,
-                          const double **sums_out, int *nsums_out) {
+                          const double **sums_out, int *nsums_out, OutPerm *perm_out) {
     SV_TRY(materialize(h));
     const int n = h->n;
     MargArgs a{};
@@ -366,8 +377,12 @@ sv_status marginal_device(sv_state *h, const int *pos, int m, double *dev_out, b
     std::sort(order, order + m, [&](int x, int y) { return pos[x] < pos[y]; });
     for (int k = 0; k < m; k++) {
         a.spos[k] = pos[order[k]];
-        a.out_bit[k] = order[k];
+        a.out_bit[k] = perm_out ? k : order[k];
         a.mask |= UINT64_C(1) << pos[order[k]];
+    }
+    if (perm_out) {
+        perm_out->m = m;
+        for (int k = 0; k < m; k++) perm_out->bit[k] = (int8_t)order[k];
     }
     const uint64_t all = (n == 64) ? ~UINT64_C(0) : ((UINT64_C(1) << n) - 1);
     a.rest = all & ~a.mask;
@@ -441,17 +456,19 @@ sv_status marginal_device(sv_state *h, const int *pos, int m, double *dev_out, b
 }
 
 sv_status argmax_device(sv_state *h, const double *dev_p, uint64_t len, uint64_t *host_idx,
-                        double *host_p, const double *sums, int nsums) {
+                        double *host_p, const double *sums, int nsums, const OutPerm *perm) {
+    OutPerm ident{};
+    const OutPerm pm = perm ? *perm : ident;
     const int nb = (int)std::min<uint64_t>(1024, blocks_for(len, kRedThreads));
     char *base = reinterpret_cast<char *>(h->small);
     double *bv = reinterpret_cast<double *>(base);
     uint64_t *bi = reinterpret_cast<uint64_t *>(base + 8192);
     double *fv = reinterpret_cast<double *>(base + 16384);
     uint64_t *fi = reinterpret_cast<uint64_t *>(base + 16384 + 64);
-    k_argmax<<<nb, kRedThreads, 0, h->stream>>>(dev_p, nullptr, len, bv, bi);
+    k_argmax<<<nb, kRedThreads, 0, h->stream>>>(dev_p, nullptr, len, bv, bi, pm);
     SV_CUDA(cudaGetLastError());
     note_launch();
-    k_argmax<<<1, kRedThreads, 0, h->stream>>>(bv, bi, (uint64_t)nb, fv, fi);
+    k_argmax<<<1, kRedThreads, 0, h->stream>>>(bv, bi, (uint64_t)nb, fv, fi, ident);
     SV_CUDA(cudaGetLastError());
     note_launch();
     if (sums) {  // unnormalised marginal: p = max / total, the total in the normalisation's order
