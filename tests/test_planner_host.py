@@ -126,6 +126,25 @@ def test_diagonal_gates_move_to_their_successors_pass(sv, orc, n):
         check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED, flags=flags), sv.SV_C64, 2e-5)
 
 
+def test_fusion_and_prefix_rules(sv, orc):
+    """A diagonal run that also acts off the Hadamard's bit stays a separate
+    run (no phased butterfly); a repeated Hadamard ends the generated prefix.
+    Both programmes still match the oracle."""
+    n = 14
+    cfg = sv.make_config(sv.SV_MODE_PARTITIONED)
+    # the run before H(8) holds CP(8, 9) and CP(10, 11): not the identity where bit 8 is 0
+    g = C.gates([C.h(q) for q in range(n)] + [C.cpk(8, 9, 1, 3), C.cpk(10, 11, 1, 4), C.h(8), C.h(10)])
+    plan = check(sv, orc, n, g, cfg, sv.SV_C64, 1e-5)
+    ops = t2_ops(plan)
+    assert planemu.T2_HPH not in ops and planemu.T2_DIAG in ops
+    # 14 leading Hadamards, then H(3) again: the prefix stops there
+    g = C.gates([C.h(q) for q in range(n)] + [C.h(3), C.cpk(3, 4, 1, 2)])
+    plan = check(sv, orc, n, g, cfg, sv.SV_C64, 1e-5)
+    first = [i["op"] for i in plan["passes"][0]["t2"]["ins"] if i["op"] != planemu.T2_STAGE]
+    k = first.index(planemu.T2_H)
+    assert all(op == planemu.T2_HG for op in first[:k]) and planemu.T2_HG not in first[k:]
+
+
 @pytest.mark.parametrize("flags", [0, 1, 4, 5])
 def test_generic_plan(sv, orc, flags):
     n = 13
