@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-other", action="store_true", help="skip the other tile kernel's timing")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-planner comparison")
     ap.add_argument("--no-sweep", action="store_true", help="skip the QPE n = 20..32 sweep")
+    ap.add_argument("--no-random", action="store_true", help="skip the random-circuit n = 30, 32 timing")
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -244,6 +245,48 @@ def replica_value(world: int, steps: int, max_ms: float) -> float:
     return world * steps / (max_ms / 1e3)
 
 
+RANDOM_N = (30, 32)
+
+
+def random_circuits(sv, C, stream, peak: float) -> dict:
+    """Random circuits (layers of U3 on every qubit, then CZ on a random
+    matching) at n = 30 and 32, depth 40, complex64: the register-stage passes
+    (library defaults) and the fused tensor-core passes (SV_MODE_FUSED), one
+    warm-up and one timed run each.  Every step ends with the argmax of the
+    lowest 10 qubits, and both paths must agree on it."""
+    import torch
+
+    res = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for nn in RANDOM_N:
+        g = C.random_circuit(nn, 40)
+        buf = torch.empty(1 << nn, dtype=torch.complex64, device="cuda")
+        h = sv.sv_create_on(nn, sv.SV_C64, buf.data_ptr(), (1 << nn) * 8, stream.cuda_stream)
+        row = {"gates": int(len(g))}
+        for mname, mode in (("partitioned", sv.SV_MODE_PARTITIONED), ("fused_tensor_cores", sv.SV_MODE_FUSED)):
+            cfg = sv.make_config(mode)
+            sv.sv_reset(h)
+            sv.sv_apply_circuit(h, g, cfg)
+            e0.record(stream)
+            sv.sv_reset(h)
+            sv.sv_apply_circuit(h, g, cfg)
+            idx, p = sv.sv_argmax(h, (1 << 10) - 1)
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1)
+            st = sv.sv_last_stats(h)
+            gbs = st["sweep_bytes"] / (ms / 1e3) / 1e9
+            row[mname] = {"circuit_ms": round(ms, 2), "passes": st["passes"],
+                          "fused_blocks": st["fused_blocks"], "hbm_gbs_full_sweeps": round(gbs, 1),
+                          "frac_of_measured_hbm": round(gbs / peak, 4), "argmax_low10": int(idx)}
+        row["same_argmax"] = row["partitioned"]["argmax_low10"] == row["fused_tensor_cores"]["argmax_low10"]
+        res[f"n{nn}_depth40"] = row
+        sv.sv_destroy(h)
+        del buf
+        torch.cuda.empty_cache()
+    return res
+
+
 SWEEP_N = (20, 24, 28, 30, 32)
 
 
@@ -308,7 +351,7 @@ def run_ours(args, world, rank, local):
         # scheme, complex128, sweep, batch) run at N = 1 only, so that an
         # N-GPU run holds its GPUs for the replicated step and e2e alone
         args.no_other = args.no_pergate = args.no_paper = True
-        args.no_c128 = args.no_sweep = args.no_batch = True
+        args.no_c128 = args.no_sweep = args.no_batch = args.no_random = True
 
     from paper_2605_15098_gb300 import build as B
     from paper_2605_15098_gb300 import circuits as C
@@ -525,6 +568,10 @@ def run_ours(args, world, rank, local):
         out["c128"] = res
         sv.sv_destroy(h2)
         del buf2
+
+    # ---- random circuits, n = 30 and 32, depth 40, complex64: CUDA-core vs tensor-core passes ----
+    if not args.no_random and dt == sv.SV_C64:
+        out["random_circuits"] = random_circuits(sv, C, stream, peak)
 
     # ---- QPE sweep: n = 20 .. 32, complex64 and complex128, partitioned vs per-gate ----
     if not args.no_sweep and dt == sv.SV_C64:
