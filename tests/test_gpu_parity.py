@@ -291,9 +291,24 @@ def test_fused_random_streamed_blocks(sv, orc):
     g = C.random_circuit(n, 8, 4321)
     ref = orc.run(n, g)
     got, st = run_gpu(sv, n, g, sv.SV_C64, sv.make_config(sv.SV_MODE_FUSED))
-    assert st["fused_blocks"] > 4 * st["passes"] * 0  # blocks were used
+    assert st["fused_blocks"] > 0  # blocks were used
     assert 1.0 - fidelity(ref, got) <= FUSED_FID
     assert np.max(np.abs(got - ref)) <= ERR64
+
+
+def test_random_depth40_both_paths(sv, orc):
+    """The random-circuit workload at depth 40 (U3 layers and CZ matchings),
+    n = 24: register-stage passes and fused tensor-core passes both within
+    the complex64 tolerances of the FP64 oracle."""
+    n = 24
+    g = C.random_circuit(n, 40, 2605)
+    ref = orc.run(n, g)
+    for mode in (sv.SV_MODE_PARTITIONED, sv.SV_MODE_FUSED):
+        got, st = run_gpu(sv, n, g, sv.SV_C64, sv.make_config(mode))
+        if mode == sv.SV_MODE_FUSED:
+            assert st["fused_blocks"] > 0
+        assert 1.0 - fidelity(ref, got) <= FUSED_FID
+        assert np.max(np.abs(got - ref)) <= ERR64
 
 
 @pytest.mark.parametrize("n", [16, 20])
