@@ -458,12 +458,21 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
             int dmask = 0;
             for (int t = 0; t < TB; t++)
                 if (dyn[L.thread_tile_bit(t)]) dmask |= 1 << t;
-            for (int tau = 0; tau < NT; tau++) {
-                uint32_t u = 0;
-                for (int t = 0; t < TB; t++)
-                    if ((tau >> t) & 1) u += sl[L.thread_tile_bit(t)];
-                for (auto &p : tt)
-                    if (((tau >> std::get<0>(p)) & (tau >> std::get<1>(p))) & 1) u += std::get<2>(p);
+            // row[tau] = sum of the linear terms of tau's bits and of the pair
+            // terms inside tau, built from tau without its lowest bit b: add
+            // b's linear term and its pairs with the bits already there
+            uint32_t lin_t[kMaxThreadBits] = {}, pair[kMaxThreadBits][kMaxThreadBits] = {};
+            for (int t = 0; t < TB; t++) lin_t[t] = sl[L.thread_tile_bit(t)];
+            for (auto &p : tt) {
+                pair[std::get<0>(p)][std::get<1>(p)] += std::get<2>(p);
+                pair[std::get<1>(p)][std::get<0>(p)] += std::get<2>(p);
+            }
+            row[0] = 0;
+            for (int tau = 1; tau < NT; tau++) {
+                const int b = __builtin_ctz((unsigned)tau);
+                const int prev = tau & (tau - 1);
+                uint32_t u = row[prev] + lin_t[b];
+                for (int rest = prev; rest; rest &= rest - 1) u += pair[b][__builtin_ctz((unsigned)rest)];
                 row[tau] = u;
                 any |= u != 0;
             }
@@ -474,12 +483,11 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
             const int tb = L.reg[j];
             uint32_t row[1 << (kT2MaxQubits - kT2RegBits)];
             bool any = false;
-            for (int tau = 0; tau < NT; tau++) {
-                uint32_t u = sl[tb];
-                for (int t = 0; t < TB; t++)
-                    if ((tau >> t) & 1) u += rt[j][t];
-                row[tau] = u;
-                any |= u != 0;
+            row[0] = sl[tb];  // then row[tau] = row[tau without its lowest bit b] + rt[j][b]
+            any = row[0] != 0;
+            for (int tau = 1; tau < NT; tau++) {
+                row[tau] = row[tau & (tau - 1)] + rt[j][__builtin_ctz((unsigned)tau)];
+                any |= row[tau] != 0;
             }
             if (any || dyn[tb]) add_thread_factor(1 << j, false, dyn[tb] ? tb : -1, 0, row);
         }
