@@ -135,6 +135,7 @@ sv_status sv_destroy(sv_handle h) {
     if (h->probs) cudaFree(h->probs);
     if (h->small) cudaFree(h->small);
     h->plan_cache.clear();  // frees each entry's device copy
+    if (h->plan_dev) cudaFree(h->plan_dev);
     if (h->plan_host) cudaFreeHost(h->plan_host);
     if (h->t2_tables) cudaFree(h->t2_tables);
     if (h->t3_tables) cudaFree(h->t3_tables);

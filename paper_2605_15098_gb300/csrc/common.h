@@ -80,6 +80,8 @@ struct sv_state {
     // compiled programmes of the last few distinct (gate list, configuration,
     // qubit map) keys, most recent first, each with its own device copy
     std::vector<std::shared_ptr<sv::CompiledPlan>> plan_cache;
+    void *plan_dev = nullptr;     // device programme of a call that bypasses the cache
+    size_t plan_cap = 0;
     sv_stats stats{};
     void *t2_tables = nullptr;    // FP64-generated phase tables (register-stage kernel)
     int *t2_err = nullptr;        // device flag: a bounded wait gave up

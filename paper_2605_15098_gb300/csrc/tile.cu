@@ -330,8 +330,9 @@ struct CompiledPlan {
     int phys_out[64];
     void *dev = nullptr;
     size_t bytes = 0;
+    bool owns_dev = false;  // false: the handle's buffer for uncached calls
     ~CompiledPlan() {
-        if (dev) cudaFree(dev);  // synchronises with work that may still read it
+        if (owns_dev && dev) cudaFree(dev);  // synchronises with work that may still read it
     }
 };
 
@@ -496,10 +497,27 @@ static sv_status compiled_plan(sv_state *h, const std::vector<sv_gate> &gates, c
         // the previous upload must have finished before the staging is reused
         SV_CUDA(cudaStreamSynchronize(h->stream));
     }
-    if (cudaMalloc(&cp->dev, total + 256) != cudaSuccess) {
-        cudaGetLastError();
-        cp->dev = nullptr;
-        return fail(SV_ERR_OOM, "cannot allocate the pass programme (%zu bytes)", total);
+    if (use_cache) {
+        if (cudaMalloc(&cp->dev, total + 256) != cudaSuccess) {
+            cudaGetLastError();
+            cp->dev = nullptr;
+            return fail(SV_ERR_OOM, "cannot allocate the pass programme (%zu bytes)", total);
+        }
+        cp->owns_dev = true;
+    } else {  // one buffer per handle, reused (the stream was synchronised above)
+        if (total + 256 > h->plan_cap) {
+            if (h->plan_dev) cudaFree(h->plan_dev);
+            h->plan_dev = nullptr;
+            h->plan_cap = 0;
+            const size_t cap = std::max<size_t>(2 * (total + 256), (size_t)1 << 16);
+            if (cudaMalloc(&h->plan_dev, cap) != cudaSuccess) {
+                cudaGetLastError();
+                h->plan_dev = nullptr;
+                return fail(SV_ERR_OOM, "cannot allocate the pass programme (%zu bytes)", cap);
+            }
+            h->plan_cap = cap;
+        }
+        cp->dev = h->plan_dev;
     }
     cp->bytes = total;
     std::memcpy(h->plan_host, blob.b.data(), total);
