@@ -108,9 +108,12 @@ enum {
                                    for every pass (no register stages)        */
     SV_FLAG_NO_PLAN_CACHE = 16, /* plan, compile and upload the list on this
                                    call even if the handle holds its programme */
-    SV_FLAG_EARLY_DIAG = 32     /* keep each diagonal gate in the first pass
+    SV_FLAG_EARLY_DIAG = 32,    /* keep each diagonal gate in the first pass
                                    where it is ready (default: the pass of the
                                    first later gate it does not commute with)  */
+    SV_FLAG_GREEDY_ONLY = 64    /* take each pass's local qubits as the greedy
+                                   list scheduling picks them, without the
+                                   local search that refines the set          */
 };
 
 /* Planner choice for partitioned modes. */

@@ -87,6 +87,7 @@ struct PlanOptions {
     bool paper = false;  // explicit LRU remaps, tile = the k lowest physical bits
     bool split_u3 = false;  // U3 as P(phi) RY(theta) P(lambda): phases join the diagonal runs
     bool late_diag = true;  // diagonal gates move to the pass of their first successor
+    bool search = true;     // refine each pass's local qubits by local search
 };
 
 // Planner options of a configuration (library defaults filled in).

@@ -348,12 +348,19 @@ PlanOptions plan_options(int n, sv_dtype dt, const sv_config &cfg) {
     opt.relabel = !(cfg.flags & SV_FLAG_NO_RELABEL);
     opt.paper = (cfg.flags & SV_FLAG_PAPER_SWAP) != 0;
     opt.late_diag = !(cfg.flags & SV_FLAG_EARLY_DIAG);
+    opt.search = !(cfg.flags & SV_FLAG_GREEDY_ONLY);
     if (opt.paper) opt.c = opt.k;  // the block is contiguous
     opt.split_u3 = !dbl;
     return opt;
 }
 
 namespace {
+
+// Local-qubit search of one pass: hill-climbing steps, and how many blocked
+// outside qubits (those of the earliest gates only locality holds back) a
+// step tries to bring in.
+constexpr int kSearchSteps = 16;
+constexpr int kSearchWant = 32;
 
 // U3(theta, phi, lambda) = P(phi) RY(theta) P(lambda) exactly, with
 // RY(theta) = [[cos(theta/2), -sin(theta/2)], [sin(theta/2), cos(theta/2)]]
@@ -495,6 +502,91 @@ std::string build_plan(const std::vector<sv_gate> &gates_in, const PlanOptions &
             remaining--;
         }
         if (order.empty()) return "internal: planner made no progress";
+        if (opt.search && n > k) {
+            // The greedy set is the qubits of the earliest ready gates.  Refine
+            // it by hill climbing: swap one of its free qubits for an outside
+            // one (or add one while a slot is free) when the pass then runs
+            // more gates, with the set fixed and the gates taken in list order.
+            for (int i : order) done[i] = 0;
+            int first = 0;
+            while (first < m && done[first]) first++;
+            // Gates run in list order with the set fixed; `want` collects the
+            // outside qubits of the earliest gates that only locality blocks.
+            auto run_pass = [&](const bool *S, std::vector<int> *ord, std::vector<int> *want) {
+                std::vector<int> taken;
+                int cntg = 0;
+                for (int i = first; i < m; i++) {
+                    if (done[i]) continue;
+                    const PGate &p = pg[i];
+                    bool ok = true;
+                    for (int d : p.deps)
+                        if (!done[d]) {
+                            ok = false;
+                            break;
+                        }
+                    if (!ok) continue;
+                    for (int a = 0; ok && a < p.nnd; a++) ok = S[p.nd[a]];
+                    if (!ok) {
+                        if (want && (int)want->size() < kSearchWant)
+                            for (int a = 0; a < p.nnd; a++)
+                                if (!S[p.nd[a]] &&
+                                    std::find(want->begin(), want->end(), p.nd[a]) == want->end())
+                                    want->push_back(p.nd[a]);
+                        continue;
+                    }
+                    done[i] = 1;
+                    taken.push_back(i);
+                    cntg++;
+                }
+                for (int i : taken) done[i] = 0;
+                if (ord) ord->swap(taken);
+                return cntg;
+            };
+            bool S[64];
+            for (int q = 0; q < 64; q++) S[q] = in_l[q];
+            std::vector<int> want;
+            int best = run_pass(S, nullptr, &want);
+            for (int it = 0; it < kSearchSteps && !want.empty(); it++) {
+                int bv = best, bin = -1, bout = -1;
+                for (int qo : want) {
+                    S[qo] = true;
+                    if (cnt < k) {  // a free slot: try adding qo
+                        const int v = run_pass(S, nullptr, nullptr);
+                        if (v > bv) {
+                            bv = v;
+                            bin = -1;
+                            bout = qo;
+                        }
+                    }
+                    for (int qi = c; qi < n; qi++) {
+                        if (!S[qi] || qi == qo) continue;
+                        S[qi] = false;
+                        const int v = run_pass(S, nullptr, nullptr);
+                        S[qi] = true;
+                        if (v > bv) {
+                            bv = v;
+                            bin = qi;
+                            bout = qo;
+                        }
+                    }
+                    S[qo] = false;
+                }
+                if (bout < 0) break;
+                S[bout] = true;
+                if (bin >= 0)
+                    S[bin] = false;
+                else
+                    cnt++;
+                want.clear();
+                best = run_pass(S, nullptr, &want);
+            }
+            order.clear();
+            run_pass(S, &order, nullptr);
+            for (int i : order) done[i] = 1;
+            for (int q = 0; q < 64; q++) in_l[q] = S[q];
+            remaining = 0;
+            for (int i = 0; i < m; i++) remaining += !done[i];
+        }
         // fill unused slots with the lowest free bits (longer contiguous runs)
         for (int q = 0; q < n && cnt < k; q++)
             if (!in_l[q]) {

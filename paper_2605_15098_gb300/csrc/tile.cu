@@ -403,7 +403,7 @@ static std::string plan_key(const sv_state *h, const std::vector<sv_gate> &gates
     auto put = [&](const void *p, size_t n) { k.append(static_cast<const char *>(p), n); };
     const int head[] = {h->n, (int)h->dt, cfg.mode, (int)cfg.flags, opt.n, opt.k, opt.c,
                         opt.merge_diag, opt.relabel, opt.paper, opt.split_u3, opt.late_diag,
-                        ov ? 1 : 0};
+                        opt.search, ov ? 1 : 0};
     put(head, sizeof head);
     put(h->phys, sizeof h->phys);
     if (ov) {

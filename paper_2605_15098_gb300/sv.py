@@ -24,6 +24,7 @@ SV_MODE_AUTO, SV_MODE_PERGATE, SV_MODE_PARTITIONED, SV_MODE_FUSED = 0, 1, 2, 3
 SV_FLAG_NO_DIAG_MERGE, SV_FLAG_PAPER_SWAP, SV_FLAG_NO_RELABEL, SV_FLAG_GENERIC_TILE = 1, 2, 4, 8
 SV_FLAG_NO_PLAN_CACHE = 16
 SV_FLAG_EARLY_DIAG = 32
+SV_FLAG_GREEDY_ONLY = 64
 SV_PLANNER_GREEDY, SV_PLANNER_LEARNED = 0, 1
 
 EXPORTS = (

@@ -113,9 +113,11 @@ def test_diagonal_gates_move_to_their_successors_pass(sv, orc, n):
     pass).  Both plans match the oracle; QPE's controlled powers then leave
     the early passes without diagonal runs and the whole plan has fewer."""
     g, _, _ = C.qpe(n, seed=n + 2)
-    late = check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=5), sv.SV_C64, 1e-5)
+    greedy = sv.SV_FLAG_GREEDY_ONLY  # the pass structure of the plain list scheduling
+    late = check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=5, flags=greedy),
+                 sv.SV_C64, 1e-5)
     early = check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=5,
-                                                flags=sv.SV_FLAG_EARLY_DIAG), sv.SV_C64, 1e-5)
+                                                flags=greedy | sv.SV_FLAG_EARLY_DIAG), sv.SV_C64, 1e-5)
     runs = lambda plan: sum(1 for op in t2_ops(plan) if op in (planemu.T2_DIAG, planemu.T2_HPH))
     assert len(late["passes"]) == len(early["passes"]) > 1
     assert runs(late) < runs(early)
@@ -124,6 +126,35 @@ def test_diagonal_gates_move_to_their_successors_pass(sv, orc, n):
     g = C.random_circuit(n, 4, n)
     for flags in (0, sv.SV_FLAG_EARLY_DIAG):
         check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED, flags=flags), sv.SV_C64, 2e-5)
+
+
+@pytest.mark.parametrize("n,kind", [(16, "qpe"), (18, "qpe"), (16, "random"), (17, "mixed")])
+def test_local_qubit_search(sv, orc, n, kind):
+    """The search that refines each pass's local qubits never needs more
+    passes than the greedy list scheduling, and its plans match the oracle."""
+    if kind == "qpe":
+        g = C.qpe(n, seed=n)[0]
+    elif kind == "random":
+        g = C.random_circuit(n, 12, n)
+    else:
+        g = mixed_circuit(n, 200, n, kinds=(0, 1, 2, 3, 4, 5, 6, 7, 9, 10))
+    for c in (4, 5):
+        searched = check(sv, orc, n, g, sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=c),
+                         sv.SV_C64, 2e-5)
+        greedy = sv.sv_plan_export(n, sv.SV_C64, g, sv.make_config(
+            sv.SV_MODE_PARTITIONED, chunk_qubits=c, flags=sv.SV_FLAG_GREEDY_ONLY))
+        assert len(searched["passes"]) <= len(greedy["passes"])
+
+
+def test_search_shortens_qpe28():
+    """QPE n=28: 3 passes with the search against 5 for the greedy scheduling (c = 7)."""
+    B.build()
+    from paper_2605_15098_gb300 import sv as S
+    g, _, _ = C.qpe(28)
+    n_s = len(S.sv_plan_export(28, S.SV_C64, g, S.make_config(S.SV_MODE_PARTITIONED, chunk_qubits=7))["passes"])
+    n_g = len(S.sv_plan_export(28, S.SV_C64, g, S.make_config(
+        S.SV_MODE_PARTITIONED, chunk_qubits=7, flags=S.SV_FLAG_GREEDY_ONLY))["passes"])
+    assert n_s < n_g
 
 
 def test_fusion_and_prefix_rules(sv, orc):
