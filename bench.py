@@ -314,10 +314,11 @@ def qpe_sweep(sv, C, stream, peak: float, no_pergate: bool) -> dict:
                 if mname == "partitioned" and (dname == "c64" or nn <= 28):
                     cfg, _ = sv.sv_autotune(h, g)  # measured choice of tile, chunk and kernel
                     tuned = True
-                reps = 3 if nn <= 28 else 1
-                if mname == "partitioned" or nn <= 28:  # warm-up (plan, compile, upload)
+                reps = 10 if nn <= 24 else 3 if nn <= 28 else 1
+                if mname == "partitioned" or nn <= 28:  # warm-up: plan, compile, upload, read-out
                     sv.sv_reset(h)
                     sv.sv_apply_circuit(h, g, cfg)
+                    sv.sv_argmax(h, info["mask"])
                 e0.record(stream)
                 for _ in range(reps):
                     sv.sv_reset(h)

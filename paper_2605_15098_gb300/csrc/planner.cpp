@@ -463,10 +463,19 @@ std::string build_plan(const std::vector<sv_gate> &gates_in, const PlanOptions &
         for (int a = 0; a < p.ndq; a++) diag_since[p.dq[a]].push_back(i);
     }
 
-    // 3. passes by list scheduling
+    // 3. passes by list scheduling.  A gate left out of a pass blocks its
+    // non-diagonal qubits: every later gate on one of them depends on it.
+    // Once every qubit is blocked no later gate can run, and a scan stops.
+    const uint64_t all_q = n >= 64 ? ~UINT64_C(0) : (UINT64_C(1) << n) - 1;
+    auto nd_mask = [&](const PGate &p) {
+        uint64_t b = 0;
+        for (int a = 0; a < p.nnd; a++) b |= UINT64_C(1) << p.nd[a];
+        return b;
+    };
     std::vector<char> done(m, 0);
     std::vector<std::vector<int>> orders;
     std::vector<std::vector<char>> locals;
+    std::vector<int> taken, rem;
     int remaining = m;
     while (remaining > 0) {
         bool in_l[64] = {};
@@ -479,7 +488,8 @@ std::string build_plan(const std::vector<sv_gate> &gates_in, const PlanOptions &
             cnt = c;
         }
         std::vector<int> order;
-        for (int i = 0; i < m; i++) {
+        uint64_t blocked = 0;
+        for (int i = 0; i < m && blocked != all_q; i++) {
             if (done[i]) continue;
             const PGate &p = pg[i];
             bool ready = true;
@@ -488,10 +498,16 @@ std::string build_plan(const std::vector<sv_gate> &gates_in, const PlanOptions &
                     ready = false;
                     break;
                 }
-            if (!ready) continue;
+            if (!ready) {
+                blocked |= nd_mask(p);
+                continue;
+            }
             int need = 0;
             for (int a = 0; a < p.nnd; a++) need += !in_l[p.nd[a]];
-            if (cnt + need > k) continue;
+            if (cnt + need > k) {
+                blocked |= nd_mask(p);
+                continue;
+            }
             for (int a = 0; a < p.nnd; a++)
                 if (!in_l[p.nd[a]]) {
                     in_l[p.nd[a]] = true;
@@ -508,15 +524,17 @@ std::string build_plan(const std::vector<sv_gate> &gates_in, const PlanOptions &
             // one (or add one while a slot is free) when the pass then runs
             // more gates, with the set fixed and the gates taken in list order.
             for (int i : order) done[i] = 0;
-            int first = 0;
-            while (first < m && done[first]) first++;
+            rem.clear();
+            for (int i = 0; i < m; i++)
+                if (!done[i]) rem.push_back(i);
             // Gates run in list order with the set fixed; `want` collects the
             // outside qubits of the earliest gates that only locality blocks.
             auto run_pass = [&](const bool *S, std::vector<int> *ord, std::vector<int> *want) {
-                std::vector<int> taken;
+                taken.clear();
                 int cntg = 0;
-                for (int i = first; i < m; i++) {
-                    if (done[i]) continue;
+                uint64_t blk = 0;
+                for (size_t r = 0; r < rem.size() && blk != all_q; r++) {
+                    const int i = rem[r];
                     const PGate &p = pg[i];
                     bool ok = true;
                     for (int d : p.deps)
@@ -524,9 +542,13 @@ std::string build_plan(const std::vector<sv_gate> &gates_in, const PlanOptions &
                             ok = false;
                             break;
                         }
-                    if (!ok) continue;
+                    if (!ok) {
+                        blk |= nd_mask(p);
+                        continue;
+                    }
                     for (int a = 0; ok && a < p.nnd; a++) ok = S[p.nd[a]];
                     if (!ok) {
+                        blk |= nd_mask(p);
                         if (want && (int)want->size() < kSearchWant)
                             for (int a = 0; a < p.nnd; a++)
                                 if (!S[p.nd[a]] &&
@@ -539,7 +561,7 @@ std::string build_plan(const std::vector<sv_gate> &gates_in, const PlanOptions &
                     cntg++;
                 }
                 for (int i : taken) done[i] = 0;
-                if (ord) ord->swap(taken);
+                if (ord) *ord = taken;
                 return cntg;
             };
             bool S[64];
