@@ -227,7 +227,9 @@ typedef struct sv_batch_state *sv_batch;
  * items from a queue ordered by decreasing cost, apply all their passes and
  * reduce the FP64 marginal of the read-out qubits to its most probable
  * outcome.  cfg may be NULL; cfg->chunk_qubits (4..11) sets the bulk-copy
- * unit.  Errors: SV_ERR_ARG (bad item), SV_ERR_UNSUPPORTED (a pass the
+ * unit, and SV_FLAG_NO_DIAG_MERGE, SV_FLAG_EARLY_DIAG and SV_FLAG_GREEDY_ONLY
+ * act as for sv_apply_circuit (SV_FLAG_PAPER_SWAP is refused with
+ * SV_ERR_UNSUPPORTED).  Errors: SV_ERR_ARG (bad item), SV_ERR_UNSUPPORTED (a pass the
  * register-stage kernel cannot run), SV_ERR_OOM, SV_ERR_CUDA. */
 sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_config *cfg,
                           sv_batch *out);

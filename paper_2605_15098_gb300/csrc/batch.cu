@@ -120,6 +120,8 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
             opt.k = kT2Qubits;
             opt.c = chunk;
             opt.merge_diag = !(c.flags & SV_FLAG_NO_DIAG_MERGE);
+            opt.late_diag = !(c.flags & SV_FLAG_EARLY_DIAG);
+            opt.search = !(c.flags & SV_FLAG_GREEDY_ONLY);
             opt.relabel = true;
             opt.split_u3 = true;
             for (int q = 0; q < 64; q++) cp.phys[q] = q;

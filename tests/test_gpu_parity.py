@@ -333,11 +333,14 @@ def test_fused_qpe_full_size(sv, n):
         assert s.argmax((1 << n) - 1)[0] == expected
 
 
-def test_batch_qpe_outcomes(sv, orc):
+@pytest.mark.parametrize("flags", [0, 32, 64, 96])
+def test_batch_qpe_outcomes(sv, orc, flags):
     """Batched QPE instances (n uniform in 10..20) in one graph-captured launch:
-    every outcome equals the oracle's argmax (small n) and the closed form."""
+    every outcome equals the oracle's argmax (small n) and the closed form,
+    with each planner option (diagonal placement, local search)."""
     work = C.qpe_batch(96, seed=777)
-    b = sv.sv_batch_create([(n, g, m) for n, g, m, _ in work])
+    b = sv.sv_batch_create([(n, g, m) for n, g, m, _ in work],
+                           sv.make_config(sv.SV_MODE_PARTITIONED, flags=flags) if flags else None)
     try:
         idx, p, ms = sv.sv_batch_run(b, len(work))
         idx2, p2, _ = sv.sv_batch_run(b, len(work))  # replay gives the same results
