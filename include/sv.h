@@ -458,7 +458,7 @@ typedef struct sv_plan_choice {
     double greedy_predicted_ms;  /* predicted time of the greedy plan          */
     double learned_ms;           /* measured by sv_planner_judge, else 0       */
     double greedy_ms;            /* measured by sv_planner_judge, else 0       */
-    int32_t verdict;             /* planner the judge kept (sv_planner)        */
+    int32_t verdict;             /* planner sv_planner_judge kept (sv_planner) */
     int32_t early_diag;          /* 1: the chosen plan keeps diagonal gates in
                                     the first pass where they are ready       */
     int32_t reserved[6];

@@ -104,7 +104,7 @@ struct sv_state {
     struct Learned {
         sv::PlanOverride ov;
         sv_plan_choice info{};
-        int verdict = -1;  // planner the judge kept; -1 = not judged
+        int verdict = -1;  // planner sv_planner_judge kept; -1 = not judged
     };
     std::map<uint64_t, Learned> learned;  // by circuit structure and start layout
 };

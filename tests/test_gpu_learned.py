@@ -1,6 +1,6 @@
 """Learned planner (GPU): the cost model only chooses among plans of the
 same gate list, so amplitudes agree with the greedy plan's (within the
-complex64 tolerance, reading A12) and outcomes are identical; the judge
+complex64 tolerance, reading A12) and outcomes are identical; sv_planner_judge
 keeps whichever plan measured faster."""
 import os
 
