@@ -87,7 +87,8 @@ struct PlanOptions {
     bool paper = false;  // explicit LRU remaps, tile = the k lowest physical bits
     bool split_u3 = false;  // U3 as P(phi) RY(theta) P(lambda): phases join the diagonal runs
     bool late_diag = true;  // diagonal gates move to the pass of their first successor
-    bool search = true;     // refine each pass's local qubits by local search
+    bool search = true;     // refine each pass's local qubits by local search (the greedy
+                            // plan is kept when it has fewer passes)
 };
 
 // Planner options of a configuration (library defaults filled in).

@@ -407,8 +407,8 @@ std::vector<sv_gate> split_u3(const std::vector<sv_gate> &gates, std::vector<cha
 
 }  // namespace
 
-std::string build_plan(const std::vector<sv_gate> &gates_in, const PlanOptions &opt, int *phys,
-                       Plan *out) {
+static std::string build_plan_once(const std::vector<sv_gate> &gates_in, const PlanOptions &opt,
+                                   int *phys, Plan *out) {
     const int n = opt.n;
     out->passes.clear();
     out->relabels = 0;
@@ -656,6 +656,28 @@ std::string build_plan(const std::vector<sv_gate> &gates_in, const PlanOptions &
         std::string e = emit_pass(pg, orders[p], in_l, n, k, c, opt, &tp);
         if (!e.empty()) return e;
         out->passes.push_back(std::move(tp));
+    }
+    return "";
+}
+
+// The local search makes each pass run at least the gates the greedy
+// scheduling puts there, but a fuller pass can leave a remainder that needs
+// more passes.  The greedy plan is built as well (a small fraction of the
+// search's cost) and kept when it has strictly fewer passes.
+std::string build_plan(const std::vector<sv_gate> &gates, const PlanOptions &opt, int *phys,
+                       Plan *out) {
+    if (!opt.search || opt.paper || opt.n <= opt.k) return build_plan_once(gates, opt, phys, out);
+    int phys_g[64];
+    std::copy(phys, phys + 64, phys_g);
+    std::string err = build_plan_once(gates, opt, phys, out);
+    if (!err.empty()) return err;
+    PlanOptions og = opt;
+    og.search = false;
+    Plan greedy;
+    if (build_plan_once(gates, og, phys_g, &greedy).empty() &&
+        greedy.passes.size() < out->passes.size()) {
+        *out = std::move(greedy);
+        std::copy(phys_g, phys_g + 64, phys);
     }
     return "";
 }

@@ -130,8 +130,9 @@ def test_diagonal_gates_move_to_their_successors_pass(sv, orc, n):
 
 @pytest.mark.parametrize("n,kind", [(16, "qpe"), (18, "qpe"), (16, "random"), (17, "mixed")])
 def test_local_qubit_search(sv, orc, n, kind):
-    """The search that refines each pass's local qubits never needs more
-    passes than the greedy list scheduling, and its plans match the oracle."""
+    """The default planner (local search of each pass's local qubits, the
+    greedy plan kept when it has fewer passes) never needs more passes than
+    the greedy list scheduling alone, and its plans match the oracle."""
     if kind == "qpe":
         g = C.qpe(n, seed=n)[0]
     elif kind == "random":
