@@ -147,6 +147,24 @@ def test_local_qubit_search(sv, orc, n, kind):
         assert len(searched["passes"]) <= len(greedy["passes"])
 
 
+def test_default_plan_never_has_more_passes_than_greedy(sv):
+    """On seeded mixed circuits the default planner (search, greedy plan kept
+    when shorter) never needs more passes than the greedy scheduling alone."""
+    better = 0
+    for seed in range(120):
+        n = 9 + seed % 10
+        kinds = (0, 1, 2, 3, 4, 5, 6, 7, 9, 10) if seed % 2 else (1, 2, 3, 4, 6)
+        g = mixed_circuit(n, 40 + (seed * 7) % 200, seed, kinds=kinds)
+        for c in (3, 4, 5):
+            cfg = dict(tile_qubits=8, chunk_qubits=c)
+            a = len(sv.sv_plan_export(n, sv.SV_C64, g, sv.make_config(sv.SV_MODE_PARTITIONED, **cfg))["passes"])
+            b = len(sv.sv_plan_export(n, sv.SV_C64, g, sv.make_config(
+                sv.SV_MODE_PARTITIONED, flags=sv.SV_FLAG_GREEDY_ONLY, **cfg))["passes"])
+            assert a <= b, (seed, n, c, a, b)
+            better += a < b
+    assert better > 0
+
+
 def test_search_shortens_qpe28():
     """QPE n=28: 3 passes with the search against 5 for the greedy scheduling (c = 7)."""
     B.build()
