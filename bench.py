@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-planner comparison")
     ap.add_argument("--no-sweep", action="store_true", help="skip the QPE n = 20..32 sweep")
     ap.add_argument("--no-random", action="store_true", help="skip the random-circuit n = 30, 32 timing")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the errors against the oracle")
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -163,25 +164,57 @@ class Clocks:
                 "power_w_max": max((num(r[3]) or 0) for r in rows), "reasons": reasons}
 
 
-def oracle_sample(n: int, gates, seconds: float):
-    """Time the FP64 oracle on a prefix of the circuit; returns (s/circuit, gates, threads)."""
+REF_STRIDE = 8  # strata of the circuit for the reference arm: one step = 1/8 of its gates
+
+
+def oracle_strata(gates, stride: int):
+    """Systematic sample of a circuit for timing the FP64 oracle: stratum s
+    holds gates s, s + stride, s + 2 stride, ...  Consecutive strata cover every
+    gate of the circuit exactly once after `stride` steps, so the time of a
+    stratum is a sample of the whole circuit (every gate kind, every qubit), not
+    of its prefix.  The oracle's cost per gate does not depend on the
+    amplitudes, so the order in which strata are applied does not change it."""
+    return [gates[s::stride] for s in range(stride)]
+
+
+def oracle_time(n: int, gates, seconds: float):
+    """Time the FP64 oracle on the circuit: the whole circuit once, in order,
+    when n <= 28; above that, strata (oracle_strata, stride 8) until the time
+    budget is spent.  Returns (seconds per circuit, gates applied, threads,
+    description)."""
     from oracle import oracle
 
     oracle.build()
     threads = oracle.num_threads()
     psi = oracle.init(n)
-    done, t0 = 0, time.perf_counter()
-    while done < len(gates):
-        oracle.apply(n, psi, gates[done:done + 1])
-        done += 1
-        if time.perf_counter() - t0 >= seconds:
+    if n <= 28:
+        t0 = time.perf_counter()
+        oracle.apply(n, psi, gates)
+        el = time.perf_counter() - t0
+        del psi
+        return el, len(gates), threads, (f"the whole {len(gates)}-gate circuit once, in order, "
+                                         f"on the FP64 complex128 oracle")
+    strata = oracle_strata(gates, REF_STRIDE)
+    done, el = 0, 0.0
+    for i in range(REF_STRIDE):
+        t0 = time.perf_counter()
+        oracle.apply(n, psi, strata[i])
+        el += time.perf_counter() - t0
+        done += len(strata[i])
+        if el >= seconds:
             break
-    el = time.perf_counter() - t0
     del psi
-    return el / done * len(gates), done, threads
+    return el / done * len(gates), done, threads, (
+        f"{done} of {len(gates)} gates (strata of every {REF_STRIDE}th gate) on the FP64 "
+        f"complex128 oracle, scaled by gate count")
 
 
 def run_reference(args, world, rank):
+    """The oracle as the reference arm: each step applies one stratum of the
+    QPE circuit (every 8th gate, a different offset each step), so 8
+    consecutive steps apply the whole circuit once.  ms_per_step is the
+    measured time of one such step; value converts it to circuits/s by the
+    fraction of the circuit's gates the timed steps applied."""
     if rank != 0:
         return
     from paper_2605_15098_gb300 import circuits as C
@@ -193,11 +226,10 @@ def run_reference(args, world, rank):
     oracle.build()
     threads = oracle.num_threads()
     psi = oracle.init(n)
-    per = max(1, min(len(gates), 4))
+    strata = oracle_strata(gates, REF_STRIDE)
 
     def step(i):
-        lo = (i * per) % len(gates)
-        sl = gates[lo:lo + per]
+        sl = strata[i % REF_STRIDE]
         t0 = time.perf_counter()
         oracle.apply(n, psi, sl)
         return time.perf_counter() - t0, len(sl)
@@ -209,17 +241,20 @@ def run_reference(args, world, rank):
         dt, g = step(args.warmup + i)
         tot += dt
         ng += g
-    circuit_s = tot / ng * len(gates)
-    value = 1.0 / circuit_s
-    sample = (f"{ng} of {len(gates)} gates of the QPE n={n} circuit (FP64 complex128 oracle, "
-              f"{per} gates per step), extrapolated by gate count")
+    circuits = ng / len(gates)
+    value = circuits / tot
+    sample = (f"each step one stratum of the QPE n={n} circuit (every {REF_STRIDE}th gate, offset "
+              f"advancing by one per step, so {REF_STRIDE} steps apply all {len(gates)} gates); "
+              f"{args.steps} timed steps applied {ng} gates = {circuits:.3f} circuits on the FP64 "
+              f"complex128 oracle")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": f"QPE-{n} circuits/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": circuit_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": tot / max(args.steps, 1) * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded QPE circuit)",
         "config": {"workload": f"QPE n={n}, t={n - 4} counting + 4 eigenstate qubits, "
-                               f"{len(gates)} gates", "n": n},
+                               f"{len(gates)} gates", "n": n,
+                   "circuit_fraction_per_step": 1.0 / REF_STRIDE},
         "cpu_baseline": {"value": value, "unit": f"QPE-{n} circuits/s", "cores": threads,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": f"QPE-{n} circuits/s", "h2d_bytes_per_step": 0,
@@ -290,12 +325,15 @@ def random_circuits(sv, C, stream, peak: float) -> dict:
 SWEEP_N = (20, 24, 28, 30, 32)
 
 
-def qpe_sweep(sv, C, stream, peak: float, no_pergate: bool) -> dict:
+def qpe_sweep(sv, C, stream, peak: float, no_pergate: bool, cfgs: dict) -> dict:
     """QPE circuit time at n = 20 .. 32 in complex64 and complex128, on the
     partitioned path (the autotuner's measured choice; library defaults for
     complex128 above n = 28, where each candidate takes seconds) and the
     per-gate path.  HBM bytes follow the full-sweep convention
-    2 x passes x 2^n x sizeof(amplitude)."""
+    2 x passes x 2^n x sizeof(amplitude) for the partitioned path; a per-gate
+    row's fraction counts the bytes each gate touches (a CP moves a quarter of
+    the state, a SWAP half), its full-sweep rate is printed beside it.  Each
+    chosen configuration is stored in `cfgs` under (n, dtype)."""
     import torch
 
     res = {}
@@ -314,6 +352,7 @@ def qpe_sweep(sv, C, stream, peak: float, no_pergate: bool) -> dict:
                 if mname == "partitioned" and (dname == "c64" or nn <= 28):
                     cfg, _ = sv.sv_autotune(h, g)  # measured choice of tile, chunk and kernel
                     tuned = True
+                    cfgs[(nn, dname)] = cfg
                 reps = 10 if nn <= 24 else 3 if nn <= 28 else 1
                 if mname == "partitioned" or nn <= 28:  # warm-up: plan, compile, upload, read-out
                     sv.sv_reset(h)
@@ -331,9 +370,16 @@ def qpe_sweep(sv, C, stream, peak: float, no_pergate: bool) -> dict:
                 gbs = st["sweep_bytes"] / (ms / 1e3) / 1e9
                 row[mname] = {"circuit_ms": round(ms, 3), "passes": st["passes"],
                               "hbm_gbs_full_sweeps": round(gbs, 1),
-                              "frac_of_measured_hbm": round(gbs / peak, 4),
                               "outcome_ok": bool(idx == info["y"] and abs(p - 1) < 1e-5),
+                              "qpe_outcome_prob_err": float(abs(1.0 - p)),
                               "config": sv.config_dict(cfg) if tuned else "library defaults"}
+                if mname == "per_gate":
+                    tgbs = st["touched_bytes"] / (ms / 1e3) / 1e9
+                    row[mname]["hbm_gbs_touched"] = round(tgbs, 1)
+                    row[mname]["frac_of_measured_hbm"] = round(tgbs / peak, 4)
+                    row[mname]["frac_basis"] = "bytes each gate touches"
+                else:
+                    row[mname]["frac_of_measured_hbm"] = round(gbs / peak, 4)
             if "per_gate" in row:
                 row["speedup_partitioned"] = round(row["per_gate"]["circuit_ms"] /
                                                    row["partitioned"]["circuit_ms"], 2)
@@ -342,6 +388,85 @@ def qpe_sweep(sv, C, stream, peak: float, no_pergate: bool) -> dict:
             del buf
             torch.cuda.empty_cache()
     return res
+
+
+ACC_QPE_N = (20, 24)
+ACC_RANDOM_N = (20, 22, 24, 26)
+ACC_BATCH_SAMPLE = 32
+
+
+def accuracy_rows(sv, C, sweep_cfgs, batch_res) -> dict:
+    """Error of each result against the FP64 oracle, at the sizes the oracle
+    finishes in seconds: QPE n = 20 and 24 (complex64 and complex128, each
+    timed path), random circuits n = 20..26 at depth 40 (complex64,
+    register-stage and fused tensor-core passes), and a sample of the batched
+    instances.  Per row: max |amp - amp_oracle|, fidelity |<psi_oracle|psi>|^2
+    and, for QPE, |p(y) - p_oracle(y)| of the expected outcome y.  Part of the
+    CPU-baseline leg: the oracle runs on the host cores."""
+    from oracle import oracle as orc
+
+    def compare(ref, got):
+        d = np.abs(got.astype(np.complex128) - ref)
+        fid = abs(np.vdot(ref, got.astype(np.complex128))) ** 2
+        return {"max_abs_err": float(d.max()), "fidelity": float(fid),
+                "one_minus_fidelity": float(1.0 - fid)}
+
+    rows = {}
+    for nn in ACC_QPE_N:
+        g, _, info = C.qpe(nn)
+        ref = orc.run(nn, g)
+        p_ref = float(orc.marginal(nn, ref, info["mask"])[info["y"]])
+        for dname, dt, modes in (
+                ("c64", sv.SV_C64, (("partitioned", sv.SV_MODE_PARTITIONED),
+                                    ("fused_tensor_cores", sv.SV_MODE_FUSED),
+                                    ("per_gate", sv.SV_MODE_PERGATE))),
+                ("c128", sv.SV_C128, (("partitioned", sv.SV_MODE_PARTITIONED),
+                                      ("per_gate", sv.SV_MODE_PERGATE)))):
+            for mname, mode in modes:
+                cfg = sweep_cfgs.get((nn, dname)) if mname == "partitioned" else None
+                cfg = cfg or sv.make_config(mode)
+                with sv.State(nn, dt) as s:
+                    s.apply(g, cfg)
+                    got = s.amplitudes()
+                    idx, p = s.argmax(info["mask"])
+                r = compare(ref, got)
+                r["qpe_outcome_prob_err"] = float(abs(p - p_ref))
+                r["outcome_ok"] = bool(idx == info["y"])
+                r["config"] = sv.config_dict(cfg)
+                rows[f"qpe_n{nn}_{dname}_{mname}"] = r
+        del ref
+    for nn in ACC_RANDOM_N:
+        g = C.random_circuit(nn, 40)
+        ref = orc.run(nn, g)
+        for mname, mode in (("partitioned", sv.SV_MODE_PARTITIONED),
+                            ("fused_tensor_cores", sv.SV_MODE_FUSED)):
+            with sv.State(nn, sv.SV_C64) as s:
+                s.apply(g, sv.make_config(mode))
+                got = s.amplitudes()
+            r = compare(ref, got)
+            r["gates"] = int(len(g))
+            rows[f"random_n{nn}_depth40_c64_{mname}"] = r
+            del got
+        del ref
+    if batch_res is not None:
+        work, bidx, bp = batch_res
+        step = max(1, len(work) // ACC_BATCH_SAMPLE)
+        errs, same, sampled = [], 0, 0
+        for i in range(0, len(work), step):
+            nn, g, mask, y = work[i]
+            ref = orc.run(nn, g)
+            pm = orc.marginal(nn, ref, mask)
+            oi, op = orc.argmax(pm)
+            same += int(int(bidx[i]) == oi)
+            errs.append(abs(float(bp[i]) - op))
+            sampled += 1
+        rows["batched_sample"] = {
+            "instances_sampled": sampled, "of": len(work),
+            "outcomes_equal_oracle": same == sampled,
+            "max_qpe_outcome_prob_err": float(max(errs)) if errs else None}
+    return {"tolerance": {"c128_max_abs_err": 1e-12, "c64_max_abs_err": 2e-5,
+                          "c64_min_fidelity": 1 - 1e-6},
+            "rows": rows}
 
 
 def run_ours(args, world, rank, local):
@@ -465,6 +590,7 @@ def run_ours(args, world, rank, local):
             "parallelism": "replicas" if world > 1 else "single GPU",
             "step": "reset + sv_apply_circuit + sv_argmax(counting register)",
             "outcome_ok": bool(ok),
+            "qpe_outcome_prob_err": float(abs(1.0 - p)),
         },
         "hbm_gbs_algorithmic": alg_gbs,
         "autotune": tuned,
@@ -512,6 +638,7 @@ def run_ours(args, world, rank, local):
             "circuit_ms": pms, "passes": pst["passes"],
             "hbm_gbs_full_sweeps": pst["sweep_bytes"] / (pms / 1e3) / 1e9,
             "hbm_gbs_touched": pst["touched_bytes"] / (pms / 1e3) / 1e9,
+            "frac_touched_of_measured_hbm": pst["touched_bytes"] / (pms / 1e3) / 1e9 / peak,
             "speedup_partitioned_over_pergate": pms / circuit_ms,
         }
     # ---- the paper's own scheme: contiguous 2^13 blocks + explicit LRU remaps ----
@@ -574,9 +701,10 @@ def run_ours(args, world, rank, local):
     if not args.no_random and dt == sv.SV_C64:
         out["random_circuits"] = random_circuits(sv, C, stream, peak)
 
+    sweep_cfgs, batch_res = {}, None
     # ---- QPE sweep: n = 20 .. 32, complex64 and complex128, partitioned vs per-gate ----
     if not args.no_sweep and dt == sv.SV_C64:
-        out["qpe_sweep"] = qpe_sweep(sv, C, stream, peak, args.no_pergate)
+        out["qpe_sweep"] = qpe_sweep(sv, C, stream, peak, args.no_pergate, sweep_cfgs)
 
     # ---- batched QPE (4096 instances, n uniform in 10..20): one graph launch ----
     if not args.no_batch:
@@ -591,6 +719,7 @@ def run_ours(args, world, rank, local):
         binfo = sv.sv_batch_info(bh)
         sv.sv_batch_destroy(bh)
         bidx = runs[-1][0]
+        batch_res = (work, runs[-1][0], runs[-1][1])
         bms = statistics.median(r[2] for r in runs)
         out["batched"] = {
             "instances": len(work), "n_range": [10, 20], "launch_ms": bms,
@@ -654,13 +783,15 @@ def run_ours(args, world, rank, local):
                   "step": "sv_create'd handle: reset + sv_apply_circuit(host gate list; planned, "
                           "compiled and its programme uploaded every step) + sv_argmax (host result)"}
 
-    # ---- CPU baseline: the FP64 oracle on the host cores (rank 0, N = 1) ----
+    # ---- CPU-baseline leg (rank 0, N = 1): the FP64 oracle on the host cores,
+    # timed on the same circuit, then the error of each small result against it ----
     if rank == 0 and world == 1 and not args.no_cpu:
-        cs, done, threads = oracle_sample(n, gates, args.cpu_seconds)
+        cs, done, threads, sample = oracle_time(n, gates, args.cpu_seconds)
         out["cpu_baseline"] = {
             "value": 1.0 / cs, "unit": f"QPE-{n} circuits/s", "cores": threads, "kind": "oracle",
-            "sample": f"first {done} of {len(gates)} gates of the same QPE n={n} circuit in the "
-                      f"FP64 complex128 oracle, extrapolated by gate count"}
+            "sample": sample}
+        if dt == sv.SV_C64 and not args.no_accuracy:
+            out["accuracy"] = accuracy_rows(sv, C, sweep_cfgs, batch_res)
     if dist:
         dist.destroy_process_group()
     if rank == 0:

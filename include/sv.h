@@ -155,18 +155,23 @@ typedef struct sv_stats {
 /* ---- lifetime --------------------------------------------------------- */
 
 /* Allocate a state of n qubits (1 <= n <= 34) on the current CUDA device and
- * set it to |0...0> (recorded; see sv_reset).  The library owns the memory; it uses its own stream.
+ * set it to |0...0> (recorded; see sv_reset).  Defining passage: Sec. III-A,
+ * an n-qubit state is a vector of 2^n complex amplitudes; Sec. IV-A starts
+ * every circuit from the all-zero basis state.  The library owns the memory; it uses its own stream.
  * Errors: SV_ERR_ARG (n, dt, out), SV_ERR_OOM, SV_ERR_CUDA. */
 sv_status sv_create(int n, sv_dtype dt, sv_handle *out);
 
-/* Same, on a caller-owned device buffer of `bytes` >= 2^n * sizeof(amp),
+/* Same (Sec. III-A state, Sec. IV-A initial |0...0>), on a caller-owned
+ * device buffer of `bytes` >= 2^n * sizeof(amp),
  * 256-byte aligned, and the caller's stream (NULL = legacy default stream).
  * The buffer must outlive the handle; sv_destroy does not free it.
  * The state is set to |0...0>. */
 sv_status sv_create_on(int n, sv_dtype dt, void *dev_buf, size_t bytes,
                        void *cuda_stream, sv_handle *out);
 
-/* Free the handle (and the state, if owned).  NULL is accepted. */
+/* Free the handle (and the state, if owned).  NULL is accepted.  Ends the
+ * lifetime of the Sec. III-A state vector that sv_create made; the paper's
+ * simulator has no call of its own for this. */
 sv_status sv_destroy(sv_handle h);
 
 /* Set the state to |0...0> and the qubit map to the identity.  The library
@@ -191,7 +196,13 @@ sv_status sv_qubit_map(sv_handle h, int *host_phys_of_logical);
 
 /* ---- applying gates --------------------------------------------------- */
 
-/* Apply gates g[0..m-1] in order.  cfg may be NULL (defaults).
+/* Apply gates g[0..m-1] in order.  cfg may be NULL (defaults).  Defining
+ * passage: Algorithm 1 (Sec. III-A) applied gate by gate, each gate's 2x2
+ * matrix on the amplitude pairs (j, j + 2^t) and a controlled gate only where
+ * bit c of j is 1; Eq. 1 states that this equals multiplying the state by
+ * I x .. x U x .. x I.  The partitioned modes follow Sec. III-B (deferred
+ * local gates applied block by block, global qubits made local) and give the
+ * same result up to floating-point rounding.
  * Partitioned modes keep the compiled programmes (host and device copies) of
  * the last 8 distinct keys on the handle; a key is the whole gate list, the
  * configuration and the qubit map at the call.  A repeated key skips the
@@ -287,7 +298,9 @@ sv_status sv_probabilities_device(sv_handle h, uint64_t qubit_mask, double *dev_
  * counterpart; it exists for callers that cannot call cudaMalloc when they
  * read a state out (a runtime that reserves all device memory up front and
  * forbids further allocation, or code that must not take the device-wide
- * synchronisation cudaMalloc/cudaFree may cause).
+ * synchronisation cudaMalloc/cudaFree may cause).  Its result agrees with
+ * sv_probabilities_device to about 1e-13 (another summation order and, for
+ * SV_C64, squares formed in FP64), not bit for bit.
  *   dev_amps  the state, 2^n amplitudes of dtype dt in physical order
  *             (e.g. the buffer of sv_info), 16-byte aligned, read only;
  *   host_phys_of_logical  n ints, the physical bit of each logical qubit
@@ -303,7 +316,9 @@ sv_status sv_probabilities_device(sv_handle h, uint64_t qubit_mask, double *dev_
  * current; make that first call before any stream capture.  All calls share
  * the array and leave their partial sums in it; nothing needs clearing, but
  * calls that overlap on the GPU race on it and must be ordered by the
- * caller.  Allocates no memory (no cudaMalloc / cudaFree).  Errors:
+ * caller.  The array's address stays valid until the device is reset: do
+ * not call this after a cudaDeviceReset of that device in the same process.
+ * Allocates no memory (no cudaMalloc / cudaFree).  Errors:
  * SV_ERR_ARG (NULL pointer, n outside 1..34, mask empty, beyond n or over
  * 30 qubits, map not a permutation, misaligned state), SV_ERR_CUDA. */
 sv_status sv_marginal_noalloc(const void *dev_amps, int n, sv_dtype dt,
@@ -323,7 +338,9 @@ sv_status sv_sample(sv_handle h, uint64_t qubit_mask, const double *host_u,
                     size_t shots, uint64_t *host_out);
 
 /* Copy the amplitudes, in LOGICAL qubit order, to / from host memory of
- * 2^n * sizeof(amp) bytes.  sv_copy_out may physically reorder the state
+ * 2^n * sizeof(amp) bytes.  Amplitude j belongs to the basis state whose bit
+ * q is qubit q (Algorithm 1's stride 2^t, Sec. III-A); the logical order is
+ * the one Sec. III-B restores by undoing its logical-to-physical qubit map.  sv_copy_out may physically reorder the state
  * to make the qubit map the identity first (results are unchanged). */
 sv_status sv_copy_out(sv_handle h, void *host_amps);
 sv_status sv_copy_in(sv_handle h, const void *host_amps);

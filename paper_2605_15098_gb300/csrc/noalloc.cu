@@ -4,10 +4,17 @@
 // read-out: a serving runtime that reserves all device memory up front and
 // forbids further allocation, or host code that must not take the implicit
 // device-wide synchronisation a cudaMalloc / cudaFree may cause.  For them
-// this entry point computes the same renormalised FP64 marginal as
-// sv_probabilities_device, but takes the state buffer, the qubit map and the
-// output buffer from the caller and keeps its partial sums in a fixed
-// device array that lives in this file, so it allocates nothing.
+// this entry point computes the renormalised FP64 marginal that
+// sv_probabilities_device computes, but takes the state buffer, the qubit map
+// and the output buffer from the caller and keeps its partial sums in a fixed
+// device array that lives in this file, so it allocates nothing.  The two
+// agree to about 1e-13, not bit for bit: this file squares complex64
+// components in FP64 and adds its groups in another order than measure.cu.
+//
+// The array's device address is looked up once per device and kept for the
+// life of the process.  A cudaDeviceReset of that device unloads the module
+// and ends the array's life, so the kept address is then stale: do not call
+// this entry point on a device after resetting it.
 //
 // The array is shared by every call in the process on a given device and
 // keeps the last call's contents.  Every slot a call reads has been written

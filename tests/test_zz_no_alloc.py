@@ -64,6 +64,51 @@ def test_noalloc_matches_allocating_readout(sv, dtype):
                 assert np.max(np.abs(got - ref_h)) <= TOL, (mask, call)
 
 
+def test_noalloc_large_masks_and_no_allocation(sv):
+    """n = 22 complex64 under a permuted qubit map: a 10-qubit mask that
+    holds physical bit 0 (outcome bits low), a 6-qubit mask of high physical
+    bits (outcome bits high, the warp-per-outcome kernel) and an 18-qubit
+    mask (one group: the caller's buffer takes the sums directly), each
+    against sv_probabilities_device on two calls in a row.  After a warm-up
+    call, further calls leave the device's free memory unchanged."""
+    import torch
+
+    n = 22
+    with sv.State(n, sv.SV_C64) as s:
+        s.apply(circuit(n), sv.make_config(sv.SV_MODE_PARTITIONED))
+        _, dt_, dev = sv.sv_info(s.h)
+        phys = sv.sv_qubit_map(s.h)
+        logical_of = {p: q for q, p in enumerate(phys)}
+
+        def mask_of_phys(bits):
+            return sum(1 << logical_of[b] for b in bits)
+
+        masks = [mask_of_phys(range(10)), mask_of_phys(range(n - 6, n)),
+                 mask_of_phys([b for b in range(n) if b not in (3, 7, 11, 19)])]
+        outs = {}
+        for mask in masks:
+            m = bin(mask).count("1")
+            ref = torch.empty(1 << m, dtype=torch.float64, device="cuda")
+            sv.sv_probabilities_device(s.h, mask, ref.data_ptr())
+            torch.cuda.synchronize()
+            ref_h = ref.cpu().numpy()
+            outs[mask] = torch.empty(1 << m, dtype=torch.float64, device="cuda")
+            for call in range(2):
+                outs[mask].fill_(float("nan"))
+                sv.sv_marginal_noalloc(dev, n, dt_, phys, mask, outs[mask].data_ptr(), 0)
+                torch.cuda.synchronize()
+                got = outs[mask].cpu().numpy()
+                assert np.all(np.isfinite(got)), (m, call)
+                assert np.max(np.abs(got - ref_h)) <= TOL, (m, call)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(3):
+            for mask in masks:
+                sv.sv_marginal_noalloc(dev, n, dt_, phys, mask, outs[mask].data_ptr(), 0)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+
+
 def test_noalloc_rejects_bad_arguments(sv):
     import torch
 
