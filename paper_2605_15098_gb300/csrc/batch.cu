@@ -132,7 +132,8 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
             for (const TilePass &tp : plan.passes) {
                 if (tp.ops.empty()) continue;
                 T2Pass t2;
-                std::string why = compile_t2(tp, &t2, false);
+                // the first pass generates |0...0> (and the leading Hadamards) in registers
+                std::string why = compile_t2v2(tp, &t2, cp.passes.empty());
                 if (!why.empty()) {
                     cp.err = "pass cannot run on the register-stage kernel: " + why;
                     break;
@@ -166,7 +167,7 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
     Blob blob;
     std::vector<BatchInst> inst(count);
     std::vector<T2Args> pass;
-    struct Off { size_t ins, stages, mats, fac, stat, tterms, layx, epi; };
+    struct Off { size_t ins, stages, mats, fac, statc, soff, sterms, layx, epi; };
     std::vector<Off> offs;
     std::vector<double> cost(count);
     uint64_t amps = 0;
@@ -191,25 +192,20 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
                 a.gen_local = 0;
                 a.gen_hmask = t2.gen_hmask;
             }
-            a.gmask = t2.gmask;
-            a.ntiles = UINT64_C(1) << (cp.nphys - t2.k);
-            a.c = t2.c;
-            a.nins = (int)t2.ins.size();
-            a.nfac = (int)t2.factors.size();
-            a.nstat = (int)t2.stat.size();
-            a.last_stage = t2.last_stage;
-            a.nruns = t2.nruns;
-            a.ntterms = (int)t2.tterms.size();
-            for (int s = 0; s < t2.k; s++) a.slot_phys[s] = t2.slot_phys[s];
+            {  // counts and geometry; the pointers are set once the blob is on the device
+                const T2Device none{};
+                t2_fill_args(t2, none, cp.nphys, &a);
+            }
             Off o;
             o.ins = blob.put(t2.ins.data(), t2.ins.size() * sizeof(T2Ins));
             o.stages = blob.put(t2.stages.data(), t2.stages.size() * sizeof(T2Stage));
             o.layx = blob.put(t2.layx.data(), t2.layx.size() * sizeof(T2LayoutX));
             o.epi = blob.put(&t2.epi, sizeof(T2Epilogue));
             o.mats = blob.put(t2.mats.data(), t2.mats.size() * sizeof(T2Mat));
-            o.fac = blob.put(t2.factors.data(), t2.factors.size() * sizeof(T2Factor));
-            o.stat = blob.put(t2.stat.data(), t2.stat.size() * sizeof(uint32_t));
-            o.tterms = blob.put(t2.tterms.data(), t2.tterms.size() * sizeof(T2TileTerm));
+            o.fac = blob.put(t2.fac2.data(), t2.fac2.size() * sizeof(T2Fac));
+            o.statc = blob.put(t2.statc.data(), t2.statc.size() * sizeof(float));
+            o.soff = blob.put(t2.soff.data(), t2.soff.size() * sizeof(int32_t));
+            o.sterms = blob.put(t2.sterms.data(), t2.sterms.size() * sizeof(T2SlotTerm));
             pass.push_back(a);
             offs.push_back(o);
             b->total_passes++;
@@ -245,8 +241,9 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
         pass[p].epi = reinterpret_cast<const T2Epilogue *>(dev + offs[p].epi);
         pass[p].mats = reinterpret_cast<const float4 *>(dev + offs[p].mats);
         pass[p].fac = reinterpret_cast<const int4 *>(dev + offs[p].fac);
-        pass[p].stat = reinterpret_cast<const uint32_t *>(dev + offs[p].stat);
-        pass[p].tterms = reinterpret_cast<const T2TileTerm *>(dev + offs[p].tterms);
+        pass[p].statc = reinterpret_cast<const float2 *>(dev + offs[p].statc);
+        pass[p].soff = reinterpret_cast<const int32_t *>(dev + offs[p].soff);
+        pass[p].sterms = reinterpret_cast<const T2SlotTerm *>(dev + offs[p].sterms);
         pass[p].tables = reinterpret_cast<const float2 *>(b->tables);
         pass[p].err = b->err;
     }

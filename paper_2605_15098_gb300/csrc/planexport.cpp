@@ -83,6 +83,29 @@ void put_t2(J &j, const T2Pass &t) {
     }
     j.raw("],\"stat\":");
     j.arr(t.stat.data(), (int)t.stat.size());
+    j.raw(",\"format\":"); j.num(t.format);
+    j.raw(",\"gen_hmask\":"); j.num(t.gen_hmask);
+    j.raw(",\"fac2\":[");
+    for (size_t i = 0; i < t.fac2.size(); i++) {
+        const T2Fac &f = t.fac2[i];
+        if (i) j.raw(",");
+        j.raw("{\"w0\":"); j.u64(f.w0);
+        j.raw(",\"slot\":"); j.num(f.slot);
+        j.raw(",\"dslot\":"); j.num(f.dslot);
+        j.raw(",\"row\":"); j.num(f.row);
+        j.raw("}");
+    }
+    j.raw("],\"statc\":[");
+    for (size_t i = 0; i < t.statc.size(); i++) {
+        if (i) j.raw(",");
+        j.dbl(t.statc[i]);
+    }
+    j.raw("],\"slots\":[");
+    for (size_t i = 0; i < t.slots.size(); i++) {
+        if (i) j.raw(",");
+        j.raw("["); j.num(t.slots[i].i0); j.raw(","); j.num(t.slots[i].i1); j.raw("]");
+    }
+    j.raw("]");
     j.raw(",\"tterms\":[");
     for (size_t i = 0; i < t.tterms.size(); i++) {
         const T2TileTerm &tt = t.tterms[i];
@@ -140,10 +163,12 @@ extern "C" sv_status sv_plan_export(int n, sv_dtype dt, const int *host_phys_of_
     j.raw(",\"remaps\":"); j.num(plan.remaps);
     j.raw(",\"phys\":"); j.arr(phys, n);
     j.raw(",\"passes\":[");
-    bool first = true;
+    bool first = true, first_pass = true;
     for (const TilePass &p : plan.passes) {
         if (!first) j.raw(",");
         first = false;
+        const bool first_ops = first_pass && !p.ops.empty() && p.remap_before.empty();
+        if (!p.ops.empty()) first_pass = false;
         j.raw("{\"k\":"); j.num(p.k);
         j.raw(",\"c\":"); j.num(p.c);
         j.raw(",\"ngates\":"); j.num(p.ngates);
@@ -202,6 +227,14 @@ extern "C" sv_status sv_plan_export(int n, sv_dtype dt, const int *host_phys_of_
             j.raw(kname);
             j.raw("\",\"t2\":");
             put_t2(j, t2);
+            // the variant the first pass runs when it starts from a recorded basis state
+            if (t2.format == 2 && first_ops) {
+                T2Pass g;
+                if (compile_t2v2(p, &g, true).empty()) {
+                    j.raw(",\"t2gen\":");
+                    put_t2(j, g);
+                }
+            }
         } else {
             j.raw(",\"kernel\":\"generic\",\"why\":\"");
             j.raw(why.c_str());

@@ -1,4 +1,6 @@
-// Stage compiler: tile pass (plan.h) -> register-stage programme (tileprog.h).
+// Stage compiler, format 1: tile pass (plan.h) -> register-stage programme of
+// the fused tensor-core kernel (k_tile3; tileprog.h).  Passes without fused
+// blocks compile to format 2 (stagecomp2.cpp).
 //
 // Layouts are chosen greedily: a stage starts at the first gate that the
 // previous layout cannot execute and takes as register bits the first four
@@ -6,7 +8,9 @@
 // always register bit 0 and tile bits 1..3 are always lane bits 0..2 (gates
 // on them use shuffles); every other target must be a register bit.  The
 // remaining tile bits fill lane bits 3..4 and the warp bits.  Diagonal runs
-// are compiled against the layout of the stage that executes them.
+// are compiled against the layout of the stage that executes them; register-
+// bit gates between two shuffle gates or stage changes fold into one 32x32
+// block.
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -161,14 +165,14 @@ bool unitary2(const double *m) {
 }
 
 std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
+    if (!fused) return compile_t2v2(tp, out, false);
     *out = T2Pass{};
     if (fused)
         for (const TileOp &op : tp.ops)
             if ((op.type == TOP_GATE || op.type == TOP_GATE_CL || op.type == TOP_GATE_CG) &&
                 !unitary2(op.m))
                 return "non-unitary gate matrix (fused passes renormalise)";
-    if (tp.k != kT2Qubits && !(tp.k == kT2WideQubits && !fused))
-        return "tile is not 2^13 (or, without fused blocks, 2^14) amplitudes";
+    if (tp.k != kT2Qubits) return "tile is not 2^13 amplitudes";
     if (tp.c < 4) return "chunk smaller than 16 amplitudes";
     for (const TileOp &op : tp.ops)
         if (op.type == TOP_SWAP) return "in-tile SWAP";
@@ -278,21 +282,6 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
             if (in.op == T2_GATE && (float)op.m[1] == 0.f && (float)op.m[3] == 0.f &&
                 (float)op.m[5] == 0.f && (float)op.m[7] == 0.f)
                 in.op = T2_RGATE;  // a real matrix (a rotation RY, for one)
-            // an uncontrolled rotation [[c, -s], [s, c]] on a register bit runs
-            // as three shears; with c < 0 it is -1 times the rotation by c' = -c,
-            // s' = -s, and the sign joins the pass's closing scale
-            double rot_t = 0.0, rot_s = 0.0;
-            if (!fused && in.op == T2_RGATE && op.type == TOP_GATE && L.cls[op.slot] == T2C_REG) {
-                const double c = op.m[0], s = op.m[4];
-                if (op.m[6] == c && op.m[2] == -s && std::fabs(c * c + s * s - 1.0) <= 1e-12) {
-                    const bool flip = c < 0.0;
-                    const double cc = flip ? -c : c, ss = flip ? -s : s;
-                    rot_t = -ss / (1.0 + cc);
-                    rot_s = ss;
-                    if (flip) out->sign_flips++;
-                    in.op = T2_ROT;
-                }
-            }
             in.cls = (int8_t)L.cls[op.slot];
             in.idx = (int8_t)L.pos[op.slot];
             in.ccls = T2C_NONE;
@@ -305,21 +294,14 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
                 in.ccls = T2C_GLOBAL;
                 in.cidx = (int16_t)op.cbit;
             }
-            if (in.op == T2_ROT) {
-                T2Mat m{};
-                m.m[0] = (float)rot_t;
-                m.m[1] = (float)rot_s;
-                in.aux = (int32_t)out->mats.size();
-                out->mats.push_back(m);
-            } else if (in.op == T2_GATE || in.op == T2_RGATE) {
+            if (in.op == T2_GATE || in.op == T2_RGATE) {
                 T2Mat m{};
                 for (int e = 0; e < 8; e++) m.m[e] = (float)op.m[e];
                 in.aux = (int32_t)out->mats.size();
                 out->mats.push_back(m);
             }
             {  // dispatch code (tileprog.h)
-                const int kind = in.op == T2_H ? 0 : in.op == T2_X ? 1 : in.op == T2_RGATE ? 2
-                               : in.op == T2_ROT ? 3 : 4;
+                const int kind = in.op == T2_H ? 0 : in.op == T2_X ? 1 : in.op == T2_RGATE ? 2 : 4;
                 int slot = 7;
                 if (in.ccls == T2C_NONE && in.cls == T2C_REG) slot = in.idx;
                 else if (in.ccls == T2C_NONE && in.cls == T2C_LANE) slot = 5;
@@ -502,58 +484,6 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
             cturn[out->factors.size()] = kv.second;
             out->factors.push_back(f);
         }
-        if (!fused) {
-            // Constant factors with the same thread predicate (or none) merge
-            // into one 32-entry phase table over the register index: one
-            // sweep over the thread's amplitudes instead of one per factor,
-            // and the kernel's per-factor path keeps only per-thread phases
-            // (masks of at most one register bit).  Each entry is formed from
-            // the summed 32-bit phase in FP64 and rounded once.
-            std::map<int, std::vector<size_t>> group;  // predicate -> factors
-            for (size_t i = nfac0; i < out->factors.size(); i++) {
-                const uint32_t w0 = (uint32_t)out->factors[i].w0;
-                if (!(w0 & 0x100u)) group[(int)((w0 >> 10) & 0xfu)].push_back(i);
-            }
-            std::vector<char> merged(out->factors.size() - nfac0, 0);
-            std::vector<std::pair<size_t, T2Factor>> tables;  // position, table factor
-            for (auto &g : group) {
-                uint32_t u[32] = {};
-                for (size_t i : g.second) {
-                    const int mask = (int)((uint32_t)out->factors[i].w0 & 0xffu);
-                    for (int x = 0; x < 32; x++)
-                        if ((x & mask) == mask) u[x] += cturn.at(i);
-                    merged[i - nfac0] = 1;
-                }
-                const int32_t m0 = (int32_t)out->mats.size();
-                float tab[64];
-                for (int x = 0; x < 32; x++) {
-                    const double ang = 2.0 * M_PI * ((double)(int32_t)u[x] * 0x1p-32);
-                    tab[4 * (x >> 1) + (x & 1)] = (float)std::cos(ang);
-                    tab[4 * (x >> 1) + 2 + (x & 1)] = (float)std::sin(ang);
-                }
-                for (int m = 0; m < 8; m++) {
-                    T2Mat tm{};
-                    for (int e = 0; e < 8; e++) tm.m[e] = tab[8 * m + e];
-                    out->mats.push_back(tm);
-                }
-                T2Factor f{};
-                const uint32_t w0 = kFacTable | ((uint32_t)g.first << 10);
-                std::memcpy(&f.w0, &w0, sizeof w0);
-                f.run = r;
-                std::memcpy(&f.c0, &m0, sizeof m0);
-                tables.push_back({g.second.front(), f});
-            }
-            if (!tables.empty()) {
-                std::vector<T2Factor> keep;
-                for (size_t i = nfac0; i < out->factors.size(); i++) {
-                    for (auto &t : tables)
-                        if (t.first == i) keep.push_back(t.second);
-                    if (!merged[i - nfac0]) keep.push_back(out->factors[i]);
-                }
-                out->factors.resize(nfac0);
-                out->factors.insert(out->factors.end(), keep.begin(), keep.end());
-            }
-        }
         if (fused) {
             // move this run's thread-dependent factors into `pre` (before the
             // block) when they commute with it, else close the block first
@@ -577,77 +507,6 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused) {
         if (!e.empty()) return e;
         if (out->factors.size() > 32000) return "too many factor applications";
     }
-    if (!fused) {
-        // A diagonal run directly followed by an uncontrolled Hadamard on a
-        // register bit j, where the run is the identity on the amplitudes
-        // with bit j = 0 (an inverse-QFT step), becomes one phased butterfly:
-        // b <- M b, then (a + b, a - b), with M the run's per-thread factor
-        // on bit j times its phase table.
-        auto phased_ok = [&](const T2Ins &d, int j) {
-            int ntab = 0, nthr = 0;
-            for (int e = d.e0; e < d.e1; e++) {
-                const T2Factor &f = out->factors[e];
-                const uint32_t w0 = (uint32_t)f.w0;
-                if (w0 & kFacTable) {
-                    if (((w0 >> 10) & 0xfu) || ++ntab > 1) return false;
-                    int32_t m0;
-                    std::memcpy(&m0, &f.c0, sizeof m0);
-                    for (int x = 0; x < 32; x++) {
-                        if ((x >> j) & 1) continue;
-                        // entry x: float 4 (x >> 1) + (x & 1) (re) and + 2 (im) of the table
-                        const float *tf = out->mats[m0 + (x >> 2)].m;
-                        const int o = 4 * ((x >> 1) & 1) + (x & 1);
-                        if (tf[o] != 1.f || tf[o + 2] != 0.f) return false;
-                    }
-                } else if (w0 & 0x100u) {
-                    if ((w0 & 0xffu) != (1u << j) || ++nthr > 1) return false;
-                } else {
-                    return false;
-                }
-            }
-            return d.e1 > d.e0;
-        };
-        std::vector<T2Ins> merged;
-        for (size_t i = 0; i < out->ins.size(); i++) {
-            const T2Ins &d = out->ins[i];
-            if (d.op == T2_DIAG && i + 1 < out->ins.size()) {
-                const T2Ins &hh = out->ins[i + 1];
-                if (hh.op == T2_H && hh.cls == T2C_REG && hh.ccls == T2C_NONE && phased_ok(d, hh.idx)) {
-                    T2Ins f = hh;
-                    f.op = T2_HPH;
-                    f.e0 = d.e0;
-                    f.e1 = d.e1;
-                    f.hd = (int16_t)(kT2Handler + 8 * 5 + hh.idx);
-                    merged.push_back(f);
-                    i++;
-                    continue;
-                }
-            }
-            merged.push_back(d);
-        }
-        out->ins.swap(merged);
-    }
-    if (!fused) {
-        // The leading Hadamards: uncontrolled, on distinct tile bits, before
-        // any step other than a stage change.  On a basis state |b> they give
-        // +-1 on the indices that agree with b off those bits (sign: the
-        // parity of b on them), 0 elsewhere, up to the closing scale.
-        int cur = -1;
-        for (T2Ins &in : out->ins) {
-            if (in.op == T2_STAGE) {
-                cur = in.aux;
-                continue;
-            }
-            if (in.op != T2_H || in.ccls != T2C_NONE || cur < 0) break;
-            const T2Stage &st = out->stages[cur];
-            const int tb = in.cls == T2C_REG ? st.tb[in.idx] : st.tb[5 + in.idx];
-            if ((out->gen_hmask >> tb) & 1u) break;
-            out->gen_hmask |= 1u << tb;
-            in.op = T2_HG;
-        }
-    }
-    if (!fused && (out->ins.size() > (size_t)kT2SmemIns || out->factors.size() > (size_t)kT2SmemFactors))
-        return "programme longer than the kernel's shared-memory copy";
     for (size_t i = 0; i < out->ins.size(); i++)
         if (out->ins[i].op == T2_STAGE) out->last_stage = (int)i;
     // kernel-side layouts and the write-back offsets of the final layout

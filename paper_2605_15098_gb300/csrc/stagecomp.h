@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -12,6 +13,7 @@
 namespace sv {
 
 struct T2Pass {
+    int format = 1;  // 1: fused kernel (k_tile3); 2: CUDA-core kernels (tileprog.h, format 2)
     int k = 0, c = 0;
     int rb = kT2RegBits, threads = kT2Threads;  // geometry (see tileprog.h)
     int slot_phys[kMaxTileQubits] = {};
@@ -27,8 +29,17 @@ struct T2Pass {
     std::vector<T2LayoutX> layx;    // per stage, the kernel-side layout
     T2Epilogue epi{};               // write-back offsets of the final layout
     std::vector<T2Mat> mats;
-    std::vector<T2Factor> factors;
-    std::vector<uint32_t> stat;     // per-thread static phases: row r is stat[r*256 .. r*256+255]
+    std::vector<T2Factor> factors;  // format 1
+    std::vector<uint32_t> stat;     // format 1: per-thread static phases, row r = stat[r*256 ..]
+    std::vector<T2Fac> fac2;        // format 2 factor applications
+    std::vector<float> statc;       // format 2: static complex rows, (re, im) per thread
+    std::vector<T2Slot> slots;      // format 2: tile-uniform slots
+    std::vector<int32_t> soff;      // format 2: slot s's terms are sterms[soff[s] .. soff[s + 1])
+    std::vector<T2SlotTerm> sterms;
+    // format 2, first pass of a plan: the variant run when the pass starts
+    // from a recorded basis state (generated in registers, leading Hadamards
+    // included); null when not compiled
+    std::shared_ptr<T2Pass> genv;
     std::vector<T2TileTerm> tterms;
     int nblocks = 0;
     std::vector<double> blocks64;   // fused: per block 2 x 32 x 32 (re, im), row = output index
@@ -40,39 +51,52 @@ struct T2Device {
     const T2Ins *ins;
     const T2Stage *stages;
     const T2Mat *mats;
-    const T2Factor *fac;
-    const uint32_t *stat;
+    const void *fac;         // T2Factor (format 1) or T2Fac (format 2) records
+    const uint32_t *stat;    // format 1
+    const float *statc;      // format 2
+    const T2Slot *slots;     // format 2
+    const int32_t *soff;     // format 2
+    const T2SlotTerm *sterms;  // format 2
     const T2TileTerm *tterms;
     const float *blocks;
     const T2LayoutX *layx;
     const T2Epilogue *epi;
 };
 
-// Launch parameters of one register-stage pass (device pointers).
+// Launch parameters of one register-stage pass in format 2 (device pointers).
 struct T2Args {
     uint64_t gmask, ntiles;
-    int c, nins, nruns, ntterms;
-    int nfac, nstat;  // factor records, static phase words
+    int c, nins;
+    int nfac, nrows, nslots, nmats, nstages;  // factor records, static rows, slots, matrix records, stages
     int last_stage;  // index of the last T2_STAGE instruction
     int slot_phys[kMaxTileQubits];
+    // the tile's physical base index: tile index bits [gs[r], gs[r] + gl[r])
+    // go to physical bits gd[r].. (runs of the global bits)
+    int ngr;
+    int8_t gs[32], gd[32], gl[32];
     const int4 *ins;       // T2Ins records
     const int4 *stages;    // T2Stage records
     const float4 *mats;    // T2Mat records (two float4 each)
-    const int4 *fac;       // T2Factor records
-    const uint32_t *stat;  // per-thread static phases
-    const T2TileTerm *tterms;
+    const int4 *fac;       // T2Fac records
+    const float2 *statc;   // static complex rows (threads entries each)
+    const int32_t *soff;   // slot term ranges
+    const T2SlotTerm *sterms;
     const float2 *tables;
     int *err;
-    const T2LayoutX *layx;  // per stage (register-stage kernel)
-    const T2Epilogue *epi;  // write-back offsets (register-stage kernel)
+    const T2LayoutX *layx;  // per stage
+    const T2Epilogue *epi;  // write-back offsets
     // gen != 0: the state is the basis state |gen_basis> (physical index) and
     // is generated in registers instead of read; gen_local is its index inside
-    // the tile that holds it; gen_hmask: tile bits whose leading Hadamards
-    // (T2_HG) the generation includes
+    // the tile that holds it; gen_hmask: tile bits of the leading Hadamards
+    // the generation includes (the programme is the pass's gen variant)
     int gen, gen_local;
     uint64_t gen_basis;
     uint32_t gen_hmask;
 };
+
+// Fill the counts, pointers and geometry of a format-2 pass (not gen,
+// tables or err).
+void t2_fill_args(const T2Pass &p, const T2Device &d, int n, T2Args *a);
 
 // One instance of a batch: its state, passes and read-out qubits.
 struct BatchInst {
@@ -99,6 +123,12 @@ struct BatchArgs {
 
 // Compile a tile pass; returns "" on success or the reason the pass cannot
 // use the register-stage kernel (it then runs on the generic tile kernel).
+// Without fused blocks the programme is in format 2 (compile_t2v2).
 std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused = false);
+
+// Format 2; `gen`: the variant for a pass that starts from a recorded basis
+// state, which it generates in registers (no shared-memory read of its first
+// stage; the leading Hadamards are part of the generated state).
+std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen);
 
 }  // namespace sv

@@ -298,13 +298,54 @@ struct Blob {
     }
 };
 
+// Blob offsets of one compiled register-stage programme.
+struct T2Off {
+    size_t ins = 0, stages = 0, mats = 0, fac = 0, stat = 0, statc = 0, slots = 0, tterms = 0;
+    size_t soff = 0, sterms = 0;
+    size_t layx = 0, epi = 0;
+};
+
+T2Off put_t2(Blob &blob, const T2Pass &t) {
+    T2Off o;
+    o.ins = blob.put_vec(t.ins);
+    o.stages = blob.put_vec(t.stages);
+    o.layx = blob.put_vec(t.layx);
+    o.epi = blob.put(&t.epi, sizeof(T2Epilogue));
+    o.mats = blob.put_vec(t.mats);
+    o.fac = t.format == 2 ? blob.put_vec(t.fac2) : blob.put_vec(t.factors);
+    o.stat = blob.put_vec(t.stat);
+    o.statc = blob.put_vec(t.statc);
+    o.slots = blob.put_vec(t.slots);
+    o.tterms = blob.put_vec(t.tterms);
+    o.soff = blob.put_vec(t.soff);
+    o.sterms = blob.put_vec(t.sterms);
+    return o;
+}
+
+T2Device t2_device(const char *dev, const T2Off &o) {
+    T2Device d{};
+    d.ins = reinterpret_cast<const T2Ins *>(dev + o.ins);
+    d.stages = reinterpret_cast<const T2Stage *>(dev + o.stages);
+    d.layx = reinterpret_cast<const T2LayoutX *>(dev + o.layx);
+    d.epi = reinterpret_cast<const T2Epilogue *>(dev + o.epi);
+    d.mats = reinterpret_cast<const T2Mat *>(dev + o.mats);
+    d.fac = dev + o.fac;
+    d.stat = reinterpret_cast<const uint32_t *>(dev + o.stat);
+    d.statc = reinterpret_cast<const float *>(dev + o.statc);
+    d.slots = reinterpret_cast<const T2Slot *>(dev + o.slots);
+    d.tterms = reinterpret_cast<const T2TileTerm *>(dev + o.tterms);
+    d.soff = reinterpret_cast<const int32_t *>(dev + o.soff);
+    d.sterms = reinterpret_cast<const T2SlotTerm *>(dev + o.sterms);
+    return d;
+}
+
 struct PassUpload {
     bool t2 = false;
     bool t3 = false;
+    bool has_gen = false;  // a format-2 variant for a generated basis state
     size_t blocks = 0;
-    size_t ops = 0, terms = 0;                                  // generic kernel
-    size_t ins = 0, stages = 0, mats = 0, fac = 0, stat = 0, tterms = 0;  // register-stage kernel
-    size_t layx = 0, epi = 0;
+    size_t ops = 0, terms = 0;  // generic kernel
+    T2Off main, gen;            // register-stage kernels
 };
 
 constexpr size_t kPlanCacheEntries = 8;
@@ -378,7 +419,7 @@ sv_launch_record describe_pass(int n, sv_dtype dt, const TilePass &p, const T2Pa
         r.stages = (int)t2->stages.size();
         r.blocks = family == PK_T3 ? t2->nblocks : 0;
         r.nins = (int)t2->ins.size();
-        r.nfactors = (int)t2->factors.size();
+        r.nfactors = (int)(t2->format == 2 ? t2->fac2.size() : t2->factors.size());
     }
     return r;
 }
@@ -453,9 +494,12 @@ static sv_status compiled_plan(sv_state *h, const std::vector<sv_gate> &gates, c
     Blob blob;
     if (ov && ov->kernel.size() != plan.passes.size())
         return fail(SV_ERR_STATE, "internal: learned plan does not match the planner's passes");
+    bool first_pass = true;  // the pass that may start from a recorded basis state
     for (size_t i = 0; i < plan.passes.size(); i++) {
         const TilePass &p = plan.passes[i];
         if (p.ops.empty()) continue;
+        const bool first_ops = first_pass && p.remap_before.empty();
+        first_pass = false;
         const int want = ov ? ov->kernel[i] : (!allow_t2 ? PK_GENERIC : fused ? PK_T3 : PK_T2);
         bool ok = false;
         if (want == PK_T3 && compile_t2(p, &t2[i], true).empty()) {
@@ -464,17 +508,18 @@ static sv_status compiled_plan(sv_state *h, const std::vector<sv_gate> &gates, c
             up[i].blocks = blob.put_vec(t2[i].blocks_dev);
         } else if ((want == PK_T3 || want == PK_T2) && compile_t2(p, &t2[i], false).empty()) {
             ok = true;
+            if (first_ops) {
+                auto g = std::make_shared<T2Pass>();
+                if (compile_t2v2(p, g.get(), true).empty()) {
+                    t2[i].genv = g;
+                    up[i].has_gen = true;
+                    up[i].gen = put_t2(blob, *g);
+                }
+            }
         }
         if (ok) {
             up[i].t2 = true;
-            up[i].ins = blob.put_vec(t2[i].ins);
-            up[i].stages = blob.put_vec(t2[i].stages);
-            up[i].layx = blob.put_vec(t2[i].layx);
-            up[i].epi = blob.put(&t2[i].epi, sizeof(T2Epilogue));
-            up[i].mats = blob.put_vec(t2[i].mats);
-            up[i].fac = blob.put_vec(t2[i].factors);
-            up[i].stat = blob.put_vec(t2[i].stat);
-            up[i].tterms = blob.put_vec(t2[i].tterms);
+            up[i].main = put_t2(blob, t2[i]);
         } else {
             up[i].ops = blob.put_vec(p.ops);
             up[i].terms = blob.put_vec(p.terms);
@@ -561,7 +606,7 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
         // its first pass; every other kernel needs it written out first
         int64_t gen = -1;
         if (h->basis >= 0) {
-            if (up[i].t2 && !up[i].t3) {
+            if (up[i].t2 && !up[i].t3 && up[i].has_gen) {
                 gen = h->basis;
                 meta.bytes = (double)state_bytes(h);  // written, not read
             } else {
@@ -569,17 +614,11 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
             }
         }
         if (up[i].t2) {
-            T2Device d;
-            d.ins = reinterpret_cast<const T2Ins *>(dev + up[i].ins);
-            d.stages = reinterpret_cast<const T2Stage *>(dev + up[i].stages);
-            d.layx = reinterpret_cast<const T2LayoutX *>(dev + up[i].layx);
-            d.epi = reinterpret_cast<const T2Epilogue *>(dev + up[i].epi);
-            d.mats = reinterpret_cast<const T2Mat *>(dev + up[i].mats);
-            d.fac = reinterpret_cast<const T2Factor *>(dev + up[i].fac);
-            d.stat = reinterpret_cast<const uint32_t *>(dev + up[i].stat);
-            d.tterms = reinterpret_cast<const T2TileTerm *>(dev + up[i].tterms);
+            const bool g = gen >= 0;
+            T2Device d = t2_device(dev, g ? up[i].gen : up[i].main);
             d.blocks = up[i].t3 ? reinterpret_cast<const float *>(dev + up[i].blocks) : nullptr;
-            st = up[i].t3 ? t3_launch(h, t2[i], d, meta) : t2_launch(h, t2[i], d, meta, gen);
+            st = up[i].t3 ? t3_launch(h, t2[i], d, meta)
+                          : t2_launch(h, g ? *t2[i].genv : t2[i], d, meta, gen);
             if (st == SV_OK && gen >= 0) h->basis = -1;
         } else {
             PassArgs a{};

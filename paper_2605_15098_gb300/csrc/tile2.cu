@@ -1,17 +1,19 @@
-// Register-stage tile kernel (complex64, tiles of 2^13 amplitudes).
+// Register-stage tile kernel (complex64, tiles of 2^13 amplitudes), running
+// programmes in format 2 (tileprog.h).
 //
 // Per tile (persistent grid, two CTAs per SM, 256 threads each, 32 amplitudes per thread):
 //   1. one warp issues 2^(13-c) bulk copies (TMA, cp.async.bulk) of the
 //      tile's contiguous 2^c-amplitude chunks into shared memory, completing
 //      on an mbarrier;
 //   2. the pass's per-tile diagonal data (global-qubit contributions, which
-//      are constants of the tile: Sec. III-B of arxiv 2605.15098) is formed
-//      while the copies are in flight;
+//      are constants of the tile: Sec. III-B of arxiv 2605.15098) is summed
+//      as integer phases while the copies are in flight, then turned into the
+//      tile's complex slot values;
 //   3. the stage programme runs: each thread holds 32 amplitudes as 16
-//      packed pairs (re and im of two neighbouring amplitudes), gates on
-//      register bits are packed f32x2 arithmetic, gates on lane bits use
-//      warp shuffles, a stage change goes through shared memory; once the
-//      last stage change has read shared memory, the next tile's copies start;
+//      packed pairs (re and im of two neighbouring amplitudes); every gate
+//      targets a register bit (packed f32x2 arithmetic); a stage change goes
+//      through shared memory in the swizzled order; once the last stage
+//      change has read shared memory, the next tile's copies start;
 //   4. each thread writes its amplitudes straight from registers to the
 //      global state (16-byte streaming stores).
 // Hadamards are applied unnormalised ([[1,1],[1,-1]]) and the pass ends with
@@ -40,44 +42,43 @@ constexpr int kTabEntries = 4 * kTabN;
 template <int K>
 struct Geo {
     static constexpr int kThreads = 1 << (K - kT2RegBits);
+    static constexpr int kWarps = kThreads / 32;
     static constexpr uint32_t kTileBytes = 8u << K;
-    static constexpr int kStatRows = kT2SmemStatRows;
     static constexpr size_t kOffTab = kTileBytes;
-    static constexpr size_t kOffStat = kOffTab + (size_t)kTabEntries * 8;
-    static constexpr size_t kOffFac = kOffStat + (size_t)kStatRows * kThreads * 4;
+    static constexpr size_t kOffRows = kOffTab + (size_t)kTabEntries * 8;
+    static constexpr size_t kOffMats = kOffRows + (size_t)kT2SmemRows * kThreads * 8;
+    static constexpr size_t kOffFac = kOffMats + (size_t)kT2SmemMats * sizeof(T2Mat);
     static constexpr size_t kOffIns = kOffFac + (size_t)kT2SmemFactors * 16;
-    static constexpr size_t kOffLin = kOffIns + (size_t)kT2SmemIns * 16;
-    static constexpr size_t kOffCst = kOffLin + (size_t)kT2MaxRuns * 16 * 4;
-    static constexpr size_t kOffBar = kOffCst + (size_t)kT2MaxRuns * 4;
+    static constexpr size_t kOffSlotc = kOffIns + (size_t)kT2SmemIns * 16;  // two buffers
+    static constexpr size_t kOffLay = kOffSlotc + 2 * (size_t)kT2MaxSlots * 8;
+    static constexpr size_t kOffEpi = kOffLay + (size_t)kT2SmemStages * sizeof(T2LayoutX);
+    static constexpr size_t kOffOnes = kOffEpi + sizeof(T2Epilogue);  // the identity phase table
+    static constexpr size_t kOffBar = kOffOnes + 16 * 16;
     static constexpr size_t kSmemBytes = kOffBar + 16;
 };
 using G13 = Geo<13>;
-constexpr uint32_t kTileBytes = G13::kTileBytes;
-constexpr size_t kOffTab = G13::kOffTab;
-constexpr size_t kOffLin = G13::kOffLin;
-constexpr size_t kOffCst = G13::kOffCst;
-constexpr size_t kOffBar = G13::kOffBar;
 constexpr size_t kSmemBytes = G13::kSmemBytes;
-
+static_assert(2 * (G13::kSmemBytes + 1024) <= 228 * 1024, "two CTAs per SM");
+static_assert(Geo<14>::kSmemBytes <= 227 * 1024, "one CTA per SM");
+static_assert(sizeof(T2LayoutX) % 16 == 0 && sizeof(T2Epilogue) % 16 == 0, "16-byte records");
 
 // ---------------------------------------------------------------- the kernel
 // Run a pass's programme (in shared memory) on the tile.  The first stage
-// reads the tile from shared memory (interleaved complex64, local index
+// reads the tile from shared memory (interleaved complex64, linear tile
 // order), or generates the recorded basis state.  After the last stage change
 // has read shared memory, `hook()` runs (the callers start the next tile's
 // bulk copies there).  The result goes straight from registers to the global
 // state, at the offsets of the final layout's write-back record.
 
 extern __shared__ __align__(1024) unsigned char t2_dyn_smem[];
-__shared__ uint64_t t2_tile_base;  // physical index of the current tile's amplitude 0
 
-// Float4 index (amplitude pair) of packed pair q in a stage layout, for
-// thread tid, from the host-computed layout record.
+// Float4 index (amplitude pair) of packed pair q in a stage layout, linear
+// tile order, for thread tid, from the host-computed layout record.
 struct Layout2 {
     int bt, s1, s2, s3, s4;
     __device__ Layout2(const T2LayoutX *x, int tid) {
-        bt = (int)__ldg(&x->lo[tid & 31]) + (int)__ldg(&x->hi[tid >> 5]);
-        const int4 sv = __ldg(reinterpret_cast<const int4 *>(x->s));
+        bt = (int)x->lo[tid & 31] + (int)x->hi[tid >> 5];
+        const int4 sv = *reinterpret_cast<const int4 *>(x->s);
         s1 = sv.x;
         s2 = sv.y;
         s3 = sv.z;
@@ -89,205 +90,335 @@ struct Layout2 {
     }
 };
 
+// The same positions in the swizzled order of a stage change (tileprog.h).
+struct LayoutS {
+    int b, p1, p2, p3, p4;
+    __device__ LayoutS(const T2LayoutX *x, int tid) {
+        b = (int)x->plo[tid & 31] ^ (int)x->phi[tid >> 5];
+        const int4 pv = *reinterpret_cast<const int4 *>(x->ps);
+        p1 = pv.x;
+        p2 = pv.y;
+        p3 = pv.z;
+        p4 = pv.w;
+    }
+    __device__ int idx(int q) const {
+        return b ^ ((q & 1) ? p1 : 0) ^ ((q & 2) ? p2 : 0) ^ ((q & 4) ? p3 : 0) ^ ((q & 8) ? p4 : 0);
+    }
+};
+
 // Gate kinds an instantiation carries besides H and the diagonal runs (the
 // host launches the smallest one that covers a pass's programme: every gate
 // path in the loop costs registers and instructions in all the others).
 constexpr int kFeatX = 1, kFeatR = 2, kFeatU = 4, kFeatAll = 7;
 
 // Gate KIND (0..4: H, X, real 2x2, shear rotation, general 2x2) on register
-// bit SLOT (0..4), or on lane bit l (SLOT 5; SLOT 6 with the thread
-// predicate `pred`).  Kinds outside the instantiation's set F compile to
+// bit SLOT (0..4).  Kinds outside the instantiation's set F compile to
 // nothing: the host never launches them there.
 template <int F, int KIND, int SLOT, int NP>
-__device__ __forceinline__ void run_gate(RegsN<NP> &r, const float4 *mrec, uint32_t qm, int l, bool pred) {
+__device__ __forceinline__ void run_gate(RegsN<NP> &r, const float4 *mrec, uint32_t qm) {
     constexpr int need = KIND == 0 ? 0 : KIND == 1 ? kFeatX : KIND == 4 ? kFeatU : kFeatR;
     if constexpr ((need & F) != need) {
         return;
     } else {
         float m[8] = {};
         if constexpr (KIND >= 2) {
-            const float4 m0 = __ldg(mrec), m1 = __ldg(mrec + 1);
+            const float4 m0 = mrec[0], m1 = mrec[1];
             m[0] = m0.x; m[1] = m0.y; m[2] = m0.z; m[3] = m0.w;
             m[4] = m1.x; m[5] = m1.y; m[6] = m1.z; m[7] = m1.w;
         }
-        if constexpr (SLOT <= 4) {
-            if constexpr (KIND == 0) reg_h2<SLOT>(r, qm);
-            else if constexpr (KIND == 1) reg_x2<SLOT>(r, qm);
-            else if constexpr (KIND == 2) reg_r2<SLOT>(r, qm, m);
-            else if constexpr (KIND == 3) reg_rot<SLOT>(r, qm, m);
-            else reg_u2<SLOT>(r, qm, m);
-        } else if constexpr (KIND != 3) {
-            constexpr int OP = KIND == 0 ? T2_H : KIND == 1 ? T2_X : KIND == 2 ? T2_RGATE : T2_GATE;
-            lane_op3<OP, SLOT == 6>(r, l, pred, qm, m);
+        if constexpr (KIND == 0) reg_h2<SLOT>(r, qm);
+        else if constexpr (KIND == 1) reg_x2<SLOT>(r, qm);
+        else if constexpr (KIND == 2) reg_r2<SLOT>(r, qm, m);
+        else if constexpr (KIND == 3) reg_rot<SLOT>(r, qm, m);
+        else reg_u2<SLOT>(r, qm, m);
+    }
+}
+
+// General 2x2 on register bit J, applied to the packed pairs in `pm` only (a
+// control on register bit J' >= 1); `odd`: to the odd element of each pair
+// only (a control on register bit 0).  Controlled gates are rare in the
+// workloads: this path favours code size over speed.
+template <int J, int NP>
+__device__ __forceinline__ void reg_u2_ctrl(RegsN<NP> &r, uint32_t pm, bool odd, const float4 *mrec) {
+    const float4 m0 = mrec[0], m1 = mrec[1];
+    const float u0r = m0.x, u0i = m0.y, u1r = m0.z, u1i = m0.w;
+    const float u2r = m1.x, u2i = m1.y, u3r = m1.z, u3i = m1.w;
+#pragma unroll
+    for (int q = 0; q < NP; q++) {
+        if (!((pm >> q) & 1)) continue;
+        if constexpr (J >= 1) {
+            constexpr int S = 1 << (J - 1);
+            if (q & S) continue;
+            const int q1 = q | S;
+            if (odd) {
+                const float ar = r.re[q].y, ai = r.im[q].y, br = r.re[q1].y, bi = r.im[q1].y;
+                r.re[q].y = u0r * ar - u0i * ai + u1r * br - u1i * bi;
+                r.im[q].y = u0r * ai + u0i * ar + u1r * bi + u1i * br;
+                r.re[q1].y = u2r * ar - u2i * ai + u3r * br - u3i * bi;
+                r.im[q1].y = u2r * ai + u2i * ar + u3r * bi + u3i * br;
+            } else {
+                const float2 ar = r.re[q], ai = r.im[q], br = r.re[q1], bi = r.im[q1];
+                r.re[q] = fma2(bi, f2(-u1i), fma2(br, f2(u1r), fma2(ai, f2(-u0i), mul2(ar, f2(u0r)))));
+                r.im[q] = fma2(br, f2(u1i), fma2(bi, f2(u1r), fma2(ar, f2(u0i), mul2(ai, f2(u0r)))));
+                r.re[q1] = fma2(bi, f2(-u3i), fma2(br, f2(u3r), fma2(ai, f2(-u2i), mul2(ar, f2(u2r)))));
+                r.im[q1] = fma2(br, f2(u3i), fma2(bi, f2(u3r), fma2(ar, f2(u2i), mul2(ai, f2(u2r)))));
+            }
+        } else {
+            const float ar = r.re[q].x, ai = r.im[q].x, br = r.re[q].y, bi = r.im[q].y;
+            r.re[q].x = u0r * ar - u0i * ai + u1r * br - u1i * bi;
+            r.im[q].x = u0r * ai + u0i * ar + u1r * bi + u1i * br;
+            r.re[q].y = u2r * ar - u2i * ai + u3r * br - u3i * bi;
+            r.im[q].y = u2r * ai + u2i * ar + u3r * bi + u3i * br;
         }
     }
 }
 
+// Multiply amplitude x of the register index by entry x of a 32-entry
+// constant phase table in shared memory: T[q] = (re[2q], re[2q+1], im[2q],
+// im[2q+1]).  `qm` as in reg_h2 (all ones at run time; bounds the loads kept
+// in flight).
+template <int NP>
+__device__ __forceinline__ void apply_table_s(RegsN<NP> &r, const float4 *T, uint32_t qm) {
+#pragma unroll
+    for (int g4 = 0; g4 < NP / 4; g4++) {
+        if (!((qm >> g4) & 1)) continue;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int q = 4 * g4 + i;
+            const float4 t = T[q];
+            const float2 tr = make_float2(t.x, t.y), ti = make_float2(t.z, t.w);
+            const float2 nr = fma2(r.im[q], make_float2(-t.z, -t.w), mul2(r.re[q], tr));
+            const float2 ni = fma2(r.im[q], tr, mul2(r.re[q], ti));
+            r.re[q] = nr;
+            r.im[q] = ni;
+        }
+    }
+}
+
+// Phased Hadamard on register bit J: the amplitude b of each pair (bit J = 1)
+// is multiplied by M = (fr + i fi) T[x] (T: a 32-entry phase table in shared
+// memory laid out as for apply_table_s; the identity table when the run has
+// none), then the pair becomes (a + M b, a - M b).  Butterflies are grouped
+// four at a time as in reg_h2.  M's imaginary part is formed with both signs
+// from the table and (fr, fi), so no operand needs negating.
+template <int J, int NP>
+__device__ __forceinline__ void reg_hph_s(RegsN<NP> &r, uint32_t qm, const float4 *T, float fr, float fi) {
+    const float2 Fr = f2(fr), Fi = f2(fi), Fnr = f2(-fr), Fni = f2(-fi);
+    if constexpr (J >= 1) {
+#pragma unroll
+        for (int g = 0; g < NP / 8; g++) {
+            if (!((qm >> g) & 1)) continue;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const int q = bfly_q<J>(4 * g + i), q1 = q | (1 << (J - 1));
+                const float4 t = T[q1];
+                const float2 tr = make_float2(t.x, t.y), ti = make_float2(t.z, t.w);
+                const float2 mr = fma2(ti, Fni, mul2(tr, Fr));
+                const float2 mi = fma2(ti, Fr, mul2(tr, Fi));
+                const float2 nmi = fma2(ti, Fnr, mul2(tr, Fni));
+                const float2 br = r.re[q1], bi = r.im[q1];
+                const float2 pr = fma2(bi, nmi, mul2(br, mr));
+                const float2 pi = fma2(bi, mr, mul2(br, mi));
+                r.re[q1] = sub2(r.re[q], pr);
+                r.im[q1] = sub2(r.im[q], pi);
+                r.re[q] = add2(r.re[q], pr);
+                r.im[q] = add2(r.im[q], pi);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int g4 = 0; g4 < NP / 4; g4++) {
+            if (!((qm >> g4) & 1)) continue;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const int q = 4 * g4 + i;
+                const float4 t = T[q];  // odd entries (bit 0 set): y and w
+                const float mr = t.y * fr - t.w * fi, mi = t.y * fi + t.w * fr;
+                float2 &x = r.re[q], &y = r.im[q];
+                const float pr = x.y * mr - y.y * mi, pi = x.y * mi + y.y * mr;
+                x.y = x.x - pr;
+                y.y = y.x - pi;
+                x.x = x.x + pr;
+                y.x = y.x + pi;
+            }
+        }
+    }
+}
+
+// `rbar`: mbarrier that every warp arrives at once it has read a stage's
+// layout from shared memory (count: the CTA's warps); `rd` counts this
+// thread's arrivals.  A stage change waits for the phase of the previous read
+// before it overwrites the tile, so no warp overwrites data another warp has
+// not read yet, without a CTA barrier.  `base`: the tile's physical base
+// index; `slotc`: the tile's slot values.  After the last stage change has
+// read shared memory, `hook()` runs (the callers start the next tile's bulk
+// copies there, once rbar shows every warp's reads done).
 template <int K, int F, typename Hook>
-__device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hook) {
+__device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, uint64_t *rbar, uint32_t &rd,
+                                       uint64_t base, const float2 *slotc, Hook hook) {
     using G = Geo<K>;
     // the programme: copied to shared memory by k_tile2 (once per CTA) and
-    // k_batch (once per pass); static phase rows beyond the copy stay in global memory
+    // k_batch (once per pass); static rows and layouts beyond the copy stay
+    // in global memory
     const int4 *ins = reinterpret_cast<const int4 *>(t2_dyn_smem + G::kOffIns);
     const int4 *fac = reinterpret_cast<const int4 *>(t2_dyn_smem + G::kOffFac);
-    const uint32_t *stat = reinterpret_cast<const uint32_t *>(t2_dyn_smem + G::kOffStat);
+    const float2 *rows = reinterpret_cast<const float2 *>(t2_dyn_smem + G::kOffRows);
+    const float4 *M = reinterpret_cast<const float4 *>(t2_dyn_smem + G::kOffMats);
+    const T2LayoutX *lays = reinterpret_cast<const T2LayoutX *>(t2_dyn_smem + G::kOffLay);
+    const float4 *ones = reinterpret_cast<const float4 *>(t2_dyn_smem + G::kOffOnes);
     float4 *tile4 = reinterpret_cast<float4 *>(t2_dyn_smem);
-    const float2 *tab = reinterpret_cast<const float2 *>(t2_dyn_smem + G::kOffTab);
-    const uint32_t *lin = reinterpret_cast<const uint32_t *>(t2_dyn_smem + G::kOffLin);
-    const uint32_t *cst = reinterpret_cast<const uint32_t *>(t2_dyn_smem + G::kOffCst);
     const int tid = threadIdx.x;
+    auto layout = [&](int st) -> const T2LayoutX * { return st < kT2SmemStages ? lays + st : a.layx + st; };
     RegsN<kNP2> r;
     int stage = 0;
     bool live = false;
-    bool hooked = false;
+    // a per-thread factor: static row x tile slot x one slot per dynamic thread bit set
+    auto thread_factor = [&](const int4 fd) -> float2 {
+        const uint32_t w0 = (uint32_t)fd.x;
+        const int sl = (int16_t)(fd.y & 0xffff), dsl = (int16_t)((uint32_t)fd.y >> 16);
+        float2 f = make_float2(1.f, 0.f);
+        if (fd.z >= 0)
+            f = fd.z < kT2SmemRows ? rows[fd.z * G::kThreads + tid]
+                                   : __ldg(a.statc + (size_t)fd.z * G::kThreads + tid);
+        if (sl >= 0) f = cx(f, slotc[sl]);
+        const uint32_t dmask = (w0 >> kFacDynShift) & 0x1ffu;
+        uint32_t dm = dmask & (uint32_t)tid;
+        while (dm) {
+            const int t = __ffs(dm) - 1;
+            dm &= dm - 1;
+            f = cx(f, slotc[dsl + __popc(dmask & ((1u << t) - 1u))]);
+        }
+        return f;
+    };
+    // the run of a phased butterfly: its table (or the identity) and its factor
+    auto hph_run = [&](const int4 w, const float4 *&T, float2 &ph) {
+        const int e0 = (int16_t)(w.z & 0xffff), e1 = (int16_t)(w.z >> 16);
+        T = ones;
+        ph = make_float2(1.f, 0.f);
+        for (int e = e0; e < e1; e++) {
+            const int4 fd = fac[e];
+            if ((uint32_t)fd.x & kFacTable)
+                T = M + 2 * fd.z;
+            else
+                ph = thread_factor(fd);
+        }
+    };
     for (int pc = 0; pc < a.nins; pc++) {
         const int4 w = ins[pc];
-        const int op = w.x & 0xff;
         // all ones at run time (the handler code is below 256), opaque to the
         // compiler (see reg_h2)
         const uint32_t qm = ~((uint32_t)w.y >> 24);
-        if (op == T2_STAGE) {
-            if (live) {
-                const Layout2 L(a.layx + stage, tid);
+        const float4 *mrec = M + 2 * w.w;
+        // one switch on the handler code the stage compiler set (tileprog.h)
+        switch (((uint32_t)w.y >> 16) & 0xffu) {
+            case kT2HdStage: {
+                if (live) {
+                    // every warp has read the previous layout before any overwrites it
+                    if (!mbar_wait(rbar, (rd - 1u) & 1u)) atomicExch(a.err, 1);
+                    const LayoutS L(layout(stage), tid);
 #pragma unroll
-                for (int q = 0; q < kNP2; q++)
-                    tile4[L.idx(q)] = make_float4(r.re[q].x, r.re[q].y, r.im[q].x, r.im[q].y);
-                __syncthreads();
-            }
-            stage = w.w;
-            {
-                const Layout2 L(a.layx + stage, tid);
-                if (!live && a.gen) {
-                    // the basis state |b>, after the leading Hadamards on the
-                    // tile bits in gen_hmask (unnormalised: the closing scale
-                    // holds their 2^(-1/2)), generated instead of read:
-                    // +-1 where the index agrees with b off those bits, with
-                    // the sign of the parity of b on them, 0 elsewhere
-                    const bool has = (a.gen_basis & a.gmask) == t2_tile_base;
-                    const uint32_t gl = (uint32_t)a.gen_local, hm = a.gen_hmask;
-                    auto amp = [&](uint32_t i) -> float {
-                        if (!has || ((i ^ gl) & ~hm)) return 0.f;
-                        return (__popc(i & gl & hm) & 1) ? -1.f : 1.f;
-                    };
+                    for (int q = 0; q < kNP2; q++)
+                        tile4[L.idx(q)] = make_float4(r.re[q].x, r.re[q].y, r.im[q].x, r.im[q].y);
+                    __syncthreads();
+                    stage = w.w;
+                    const LayoutS L2(layout(stage), tid);
 #pragma unroll
                     for (int q = 0; q < kNP2; q++) {
-                        const uint32_t i0 = 2u * (uint32_t)L.idx(q);
-                        r.re[q] = make_float2(amp(i0), amp(i0 + 1));
-                        r.im[q] = make_float2(0.f, 0.f);
+                        const float4 v = tile4[L2.idx(q)];
+                        r.re[q] = make_float2(v.x, v.y);
+                        r.im[q] = make_float2(v.z, v.w);
                     }
                 } else {
+                    stage = w.w;
+                    const Layout2 L(layout(stage), tid);
+                    if (a.gen) {
+                        // the basis state |b>, after the leading Hadamards on the
+                        // tile bits in gen_hmask (unnormalised: the closing scale
+                        // holds their 2^(-1/2)), generated instead of read:
+                        // +-1 where the index agrees with b off those bits, with
+                        // the sign of the parity of b on them, 0 elsewhere
+                        const bool has = (a.gen_basis & a.gmask) == base;
+                        const uint32_t gl = (uint32_t)a.gen_local, hm = a.gen_hmask;
+                        auto amp = [&](uint32_t i) -> float {
+                            if (!has || ((i ^ gl) & ~hm)) return 0.f;
+                            return (__popc(i & gl & hm) & 1) ? -1.f : 1.f;
+                        };
 #pragma unroll
-                    for (int q = 0; q < kNP2; q++) {
-                        const float4 v = tile4[L.idx(q)];
-                        if (live) {
-                            r.re[q] = make_float2(v.x, v.y);
-                            r.im[q] = make_float2(v.z, v.w);
-                        } else {
+                        for (int q = 0; q < kNP2; q++) {
+                            const uint32_t i0 = 2u * (uint32_t)L.idx(q);
+                            r.re[q] = make_float2(amp(i0), amp(i0 + 1));
+                            r.im[q] = make_float2(0.f, 0.f);
+                        }
+                    } else {  // the bulk copies' linear order: lane bits 0..2 are tile bits 1..3
+#pragma unroll
+                        for (int q = 0; q < kNP2; q++) {
+                            const float4 v = tile4[L.idx(q)];
                             r.re[q] = make_float2(v.x, v.z);
                             r.im[q] = make_float2(v.y, v.w);
                         }
                     }
                 }
+                live = true;
+                __syncwarp();
+                if ((tid & 31) == 0) mbar_arrive(rbar);
+                rd++;
+                if (pc == a.last_stage) hook();
+                continue;
             }
-            live = true;
-            if (pc == a.last_stage) {
-                __syncthreads();  // every thread has read shared memory
-                hook();
-                hooked = true;
-            }
-            continue;
-        }
-        if (op == T2_SCALE) {
-            const float4 mm = __ldg(a.mats + 2 * w.w);
-            const float hi = mm.x, lo = mm.y;
-            if (lo == 0.f) {  // an even number of Hadamards: an exact power of two
+            case kT2HdScale: {
+                const float4 mm = mrec[0];
+                const float hi = mm.x, lo = mm.y;
+                if (lo == 0.f) {  // an even number of Hadamards: an exact power of two
+#pragma unroll
+                    for (int q = 0; q < kNP2; q++) {
+                        r.re[q] = mul2(r.re[q], f2(hi));
+                        r.im[q] = mul2(r.im[q], f2(hi));
+                    }
+                    continue;
+                }
 #pragma unroll
                 for (int q = 0; q < kNP2; q++) {
-                    r.re[q] = mul2(r.re[q], f2(hi));
-                    r.im[q] = mul2(r.im[q], f2(hi));
+                    r.re[q] = fma2(r.re[q], f2(hi), mul2(r.re[q], f2(lo)));
+                    r.im[q] = fma2(r.im[q], f2(hi), mul2(r.im[q], f2(lo)));
                 }
                 continue;
             }
-#pragma unroll
-            for (int q = 0; q < kNP2; q++) {
-                r.re[q] = fma2(r.re[q], f2(hi), mul2(r.re[q], f2(lo)));
-                r.im[q] = fma2(r.im[q], f2(hi), mul2(r.im[q], f2(lo)));
-            }
-            continue;
-        }
-        // e^{2 pi i u / 2^32} for this thread's phase u of a per-thread factor
-        auto thread_phase = [&](const int4 fd) -> float2 {
-            const uint32_t w0 = (uint32_t)fd.x;
-            const int run = fd.y;
-            uint32_t u = fd.z >= G::kStatRows ? __ldg(a.stat + fd.z * G::kThreads + tid)
-                                              : stat[fd.z * G::kThreads + tid];
-            if (w0 & 0x200u) u += cst[run];
-            const int lr = (int)((w0 >> kFacLinShift) & 0x1fu) - 1;
-            if (lr >= 0) u += lin[run * 16 + lr];
-            uint32_t dm = (w0 >> kFacDynShift) & 0x1ffu & (uint32_t)tid;
-            while (dm) {
-                const int t = __ffs(dm) - 1;
-                dm &= dm - 1;
-                const int8_t *tbp = reinterpret_cast<const int8_t *>(a.stages + stage);
-                u += lin[run * 16 + tbp[5 + t]];
-            }
-            return cx(cx(tab[u >> 24], tab[kTabN + ((u >> 16) & 255u)]),
-                      cx(tab[2 * kTabN + ((u >> 8) & 255u)], tab[3 * kTabN + (u & 255u)]));
-        };
-        if (op == T2_HPH) {  // diagonal run + H on register bit j in one sweep (stage compiler)
-            const int e0 = (int16_t)(w.z & 0xffff), e1 = (int16_t)(w.z >> 16);
-            const float4 *T = nullptr;
-            float2 ph = make_float2(1.f, 0.f);
-            for (int e = e0; e < e1; e++) {
-                const int4 fd = fac[e];
-                if ((uint32_t)fd.x & kFacTable)
-                    T = a.mats + 2 * fd.z;
-                else
-                    ph = thread_phase(fd);
-            }
-            switch ((w.x >> 16) & 0xff) {
-                case 0: reg_hph<0>(r, qm, T, ph.x, ph.y); break;
-                case 1: reg_hph<1>(r, qm, T, ph.x, ph.y); break;
-                case 2: reg_hph<2>(r, qm, T, ph.x, ph.y); break;
-                case 3: reg_hph<3>(r, qm, T, ph.x, ph.y); break;
-                default: reg_hph<4>(r, qm, T, ph.x, ph.y); break;
-            }
-            continue;
-        }
-        if (op == T2_DIAG) {
-            const int e0 = (int16_t)(w.z & 0xffff), e1 = (int16_t)(w.z >> 16);
-            if (e0 >= e1) continue;
-            for (int e = e0; e < e1; e++) {
-                const int4 fd = fac[e];
-                const uint32_t w0 = (uint32_t)fd.x;
-                const int run = fd.y;
-                const int pb = (int)((w0 >> 10) & 0xfu);  // thread-bit predicate of a constant
-                if (pb && !((tid >> (pb - 1)) & 1)) continue;  // not this thread's factor
-                if (w0 & kFacTable) {
-                    apply_table(r, a.mats + 2 * fd.z, qm);
-                    continue;
+            case kT2HdDiag: {
+                const int e0 = (int16_t)(w.z & 0xffff), e1 = (int16_t)(w.z >> 16);
+                for (int e = e0; e < e1; e++) {
+                    const int4 fd = fac[e];
+                    const uint32_t w0 = (uint32_t)fd.x;
+                    if (w0 & kFacTable) {
+                        const int pb = (int)((w0 >> 10) & 0xfu);  // thread-bit predicate
+                        if (pb && !((tid >> (pb - 1)) & 1)) continue;
+                        apply_table_s(r, M + 2 * fd.z, qm);
+                        continue;
+                    }
+                    const float2 ff = thread_factor(fd);
+                    apply_factor_bit(r, (int)(w0 & 0xffu), ff.x, ff.y);
                 }
-                // per-thread phase (constants are tables, see the stage compiler)
-                const float2 ff = thread_phase(fd);
-                apply_factor_bit(r, (int)(w0 & 0xffu), ff.x, ff.y);
+                continue;
             }
-            continue;
-        }
-        if (op == T2_HG && a.gen) continue;  // included in the generated state
-        // gates (no register-bit controls: the stage compiler never emits them);
-        // one switch on the handler code the stage compiler set (tileprog.h)
-        const int j = (int8_t)((w.x >> 16) & 0xff);
-        const float4 *mrec = a.mats + 2 * w.w;
-        switch (((uint32_t)w.y >> 16) & 0xffu) {
-#define SV_GATE_CASES(K)                                                                 \
-    case kT2Handler + 8 * K + 0: run_gate<F, K, 0>(r, mrec, qm, j, true); continue;     \
-    case kT2Handler + 8 * K + 1: run_gate<F, K, 1>(r, mrec, qm, j, true); continue;     \
-    case kT2Handler + 8 * K + 2: run_gate<F, K, 2>(r, mrec, qm, j, true); continue;     \
-    case kT2Handler + 8 * K + 3: run_gate<F, K, 3>(r, mrec, qm, j, true); continue;     \
-    case kT2Handler + 8 * K + 4: run_gate<F, K, 4>(r, mrec, qm, j, true); continue;     \
-    case kT2Handler + 8 * K + 5: run_gate<F, K, 5>(r, mrec, qm, j, true); continue;     \
-    case kT2Handler + 8 * K + 6:                                                         \
-        run_gate<F, K, 6>(r, mrec, qm, j, (tid >> (int16_t)(w.y & 0xffff)) & 1); continue;
+#define SV_HPH_CASE(J)                                       \
+    case kT2Handler + 8 * 5 + J: {                           \
+        const float4 *T;                                     \
+        float2 ph;                                           \
+        hph_run(w, T, ph);                                   \
+        reg_hph_s<J>(r, qm, T, ph.x, ph.y);                  \
+        continue;                                            \
+    }
+            SV_HPH_CASE(0)
+            SV_HPH_CASE(1)
+            SV_HPH_CASE(2)
+            SV_HPH_CASE(3)
+            SV_HPH_CASE(4)
+#undef SV_HPH_CASE
+#define SV_GATE_CASES(K)                                                         \
+    case kT2Handler + 8 * K + 0: run_gate<F, K, 0>(r, mrec, qm); continue;       \
+    case kT2Handler + 8 * K + 1: run_gate<F, K, 1>(r, mrec, qm); continue;       \
+    case kT2Handler + 8 * K + 2: run_gate<F, K, 2>(r, mrec, qm); continue;       \
+    case kT2Handler + 8 * K + 3: run_gate<F, K, 3>(r, mrec, qm); continue;       \
+    case kT2Handler + 8 * K + 4: run_gate<F, K, 4>(r, mrec, qm); continue;
             SV_GATE_CASES(0)
             SV_GATE_CASES(1)
             SV_GATE_CASES(2)
@@ -296,46 +427,50 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
 #undef SV_GATE_CASES
             default: break;
         }
-        {  // slot 7: a register-bit gate with a thread or tile control
+        {  // slot 7: a register-bit gate with a register, thread or tile control
+            const int j = (int8_t)((w.x >> 16) & 0xff);
             const int ccls = (w.x >> 24) & 0xff;
             const int cidx = (int16_t)(w.y & 0xffff);
             if (ccls == T2C_GLOBAL) {
-                if (!((t2_tile_base >> cidx) & 1)) continue;  // tile-uniform
+                if (!((base >> cidx) & 1)) continue;  // tile-uniform
             } else if (ccls == T2C_THREAD) {
                 if (!((tid >> cidx) & 1)) continue;
             }
             const int kind = ((((uint32_t)w.y >> 16) & 0xffu) - kT2Handler) >> 3;
-            const bool lane = ((w.x >> 8) & 0xff) == T2C_LANE;
-#define SV_CTRL_CASE(K)                                                                  \
-    if (kind == K) {                                                                     \
-        if (lane) {                                                                      \
-            run_gate<F, K, 5>(r, mrec, qm, j, true);                                     \
-        } else {                                                                         \
-            switch (j) {                                                                 \
-                case 0: run_gate<F, K, 0>(r, mrec, qm, j, true); break;                  \
-                case 1: run_gate<F, K, 1>(r, mrec, qm, j, true); break;                  \
-                case 2: run_gate<F, K, 2>(r, mrec, qm, j, true); break;                  \
-                case 3: run_gate<F, K, 3>(r, mrec, qm, j, true); break;                  \
-                default: run_gate<F, K, 4>(r, mrec, qm, j, true); break;                 \
-            }                                                                            \
-        }                                                                                \
-        continue;                                                                        \
+            if (ccls == T2C_REG) {  // general 2x2 on the pairs that hold the control
+                if constexpr ((F & (kFeatR | kFeatU)) != 0) {
+                    const uint32_t pm = (uint32_t)w.z & 0xffffu;
+                    const bool odd = ((uint32_t)w.z >> 16) != 0;
+                    switch (j) {
+                        case 0: reg_u2_ctrl<0>(r, pm, odd, mrec); break;
+                        case 1: reg_u2_ctrl<1>(r, pm, odd, mrec); break;
+                        case 2: reg_u2_ctrl<2>(r, pm, odd, mrec); break;
+                        case 3: reg_u2_ctrl<3>(r, pm, odd, mrec); break;
+                        default: reg_u2_ctrl<4>(r, pm, odd, mrec); break;
+                    }
+                }
+                continue;
+            }
+#define SV_CTRL_CASE(K)                                                   \
+    if (kind == K) {                                                      \
+        switch (j) {                                                      \
+            case 0: run_gate<F, K, 0>(r, mrec, qm); break;                \
+            case 1: run_gate<F, K, 1>(r, mrec, qm); break;                \
+            case 2: run_gate<F, K, 2>(r, mrec, qm); break;                \
+            case 3: run_gate<F, K, 3>(r, mrec, qm); break;                \
+            default: run_gate<F, K, 4>(r, mrec, qm); break;               \
+        }                                                                 \
+        continue;                                                         \
     }
-            SV_CTRL_CASE(0)
-            SV_CTRL_CASE(1)
             SV_CTRL_CASE(2)
             SV_CTRL_CASE(4)
 #undef SV_CTRL_CASE
         }
     }
-    if (!hooked) {  // a programme without a stage change still releases the buffer
-        __syncthreads();
-        hook();
-    }
     if (!live) return;
-    const T2Epilogue *E = a.epi;
-    const uint64_t g0 = t2_tile_base + __ldg(&E->glo[tid & 31]) + __ldg(&E->ghi[tid >> 5]);
-    const uint64_t g1 = __ldg(&E->g[0]), g2 = __ldg(&E->g[1]), g3 = __ldg(&E->g[2]), g4 = __ldg(&E->g[3]);
+    const T2Epilogue *E = reinterpret_cast<const T2Epilogue *>(t2_dyn_smem + G::kOffEpi);
+    const uint64_t g0 = base + E->glo[tid & 31] + E->ghi[tid >> 5];
+    const uint64_t g1 = E->g[0], g2 = E->g[1], g3 = E->g[2], g4 = E->g[3];
 #pragma unroll
     for (int q = 0; q < kNP2; q++) {
         const uint64_t g = g0 + ((q & 1) ? g1 : 0) + ((q & 2) ? g2 : 0) + ((q & 4) ? g3 : 0) +
@@ -344,12 +479,21 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, Hook hoo
     }
 }
 
+// Physical base index of tile `tile`: its index bits spread over the runs of
+// the global qubits.
+__device__ __forceinline__ uint64_t tile_base(const T2Args &a, uint64_t tile) {
+    uint64_t b = 0;
+    for (int i = 0; i < a.ngr; i++)
+        b |= ((tile >> a.gs[i]) & ((UINT64_C(1) << a.gl[i]) - 1)) << a.gd[i];
+    return b;
+}
+
 template <int K>
 __device__ __forceinline__ void issue_tile_load(const T2Args &a, unsigned char *sm, const float *state,
                                                 uint64_t tile, uint64_t *bar, int tid) {
     const int nchunks = 1 << (K - a.c);
     const uint32_t chunk_bytes = 8u << a.c;
-    const uint64_t base = pdep(tile, a.gmask);
+    const uint64_t base = tile_base(a, tile);
     if (tid == 0) {
         fence_async_smem();
         mbar_expect_tx(bar, Geo<K>::kTileBytes);
@@ -363,6 +507,54 @@ __device__ __forceinline__ void issue_tile_load(const T2Args &a, unsigned char *
     }
 }
 
+// The pass's programme into shared memory (sizes bounded by the stage compiler).
+template <int K>
+__device__ __forceinline__ void load_programme(const T2Args &a, unsigned char *sm, int tid, int nthreads) {
+    using G = Geo<K>;
+    int4 *si = reinterpret_cast<int4 *>(sm + G::kOffIns);
+    int4 *sf = reinterpret_cast<int4 *>(sm + G::kOffFac);
+    float2 *sr = reinterpret_cast<float2 *>(sm + G::kOffRows);
+    float4 *smat = reinterpret_cast<float4 *>(sm + G::kOffMats);
+    int4 *slay = reinterpret_cast<int4 *>(sm + G::kOffLay);
+    int4 *sepi = reinterpret_cast<int4 *>(sm + G::kOffEpi);
+    for (int i = tid; i < a.nins; i += nthreads) si[i] = __ldg(a.ins + i);
+    for (int i = tid; i < a.nfac; i += nthreads) sf[i] = __ldg(a.fac + i);
+    for (int i = tid; i < 2 * a.nmats; i += nthreads) smat[i] = __ldg(a.mats + i);
+    const int nl = min(a.nstages, kT2SmemStages) * (int)(sizeof(T2LayoutX) / 16);
+    for (int i = tid; i < nl; i += nthreads) slay[i] = __ldg(reinterpret_cast<const int4 *>(a.layx) + i);
+    for (int i = tid; i < (int)(sizeof(T2Epilogue) / 16); i += nthreads)
+        sepi[i] = __ldg(reinterpret_cast<const int4 *>(a.epi) + i);
+    const int nr = min(a.nrows, kT2SmemRows) * G::kThreads;
+    for (int i = tid; i < nr; i += nthreads) sr[i] = __ldg(a.statc + i);
+    float4 *ones = reinterpret_cast<float4 *>(sm + G::kOffOnes);  // the identity phase table
+    for (int i = tid; i < 16; i += nthreads) ones[i] = make_float4(1.f, 1.f, 0.f, 0.f);
+}
+
+// The tile's slot values (Sec. III-B: global qubits are constants of the
+// tile): each warp sums the terms of its slots over its lanes (exact 32-bit
+// phase arithmetic), and one lane forms e^{2 pi i u / 2^32} from the four
+// FP64-generated tables.
+template <int K>
+__device__ __forceinline__ void tile_slots(const T2Args &a, const float2 *tab, float2 *slotc, uint64_t base,
+                                           int tid) {
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int sl = warp; sl < a.nslots; sl += Geo<K>::kWarps) {
+        const int t0 = __ldg(a.soff + sl), t1 = __ldg(a.soff + sl + 1);
+        uint32_t u = 0;
+        for (int t = t0 + lane; t < t1; t += 32) {
+            const T2SlotTerm st = a.sterms[t];
+            bool on = (base >> st.g0) & 1;
+            if (st.g1 >= 0) on = on && ((base >> st.g1) & 1);
+            if (on) u += st.theta;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+        if (lane == 0)
+            slotc[sl] = cx(cx(tab[u >> 24], tab[kTabN + ((u >> 16) & 255u)]),
+                           cx(tab[2 * kTabN + ((u >> 8) & 255u)], tab[3 * kTabN + (u & 255u)]));
+    }
+}
+
 // Persistent CTA over the pass's tiles.  Tile i+1's bulk copies start as
 // soon as tile i's last stage change has read shared memory, so they overlap
 // the rest of tile i's programme and its write-back, which goes from
@@ -373,60 +565,48 @@ __global__ void __launch_bounds__(Geo<K>::kThreads, K == kT2Qubits ? 2 : 1)
     k_tile2(float *__restrict__ state, const T2Args a) {
     using G = Geo<K>;
     extern __shared__ __align__(1024) unsigned char sm[];
-    float4 *tile4 = reinterpret_cast<float4 *>(sm);
     float2 *tab = reinterpret_cast<float2 *>(sm + G::kOffTab);
-    uint32_t *lin = reinterpret_cast<uint32_t *>(sm + G::kOffLin);
-    uint32_t *cst = reinterpret_cast<uint32_t *>(sm + G::kOffCst);
+    float2 *slotc = reinterpret_cast<float2 *>(sm + G::kOffSlotc);
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + G::kOffBar);
+    uint64_t *rbar = bar + 1;
     const int tid = threadIdx.x;
 
     for (int i = tid; i < kTabEntries; i += blockDim.x) tab[i] = a.tables[i];
-    {  // the programme, once per CTA (sizes bounded by the stage compiler)
-        int4 *si = reinterpret_cast<int4 *>(sm + G::kOffIns);
-        int4 *sf = reinterpret_cast<int4 *>(sm + G::kOffFac);
-        uint32_t *ss = reinterpret_cast<uint32_t *>(sm + G::kOffStat);
-        for (int i = tid; i < a.nins; i += blockDim.x) si[i] = __ldg(a.ins + i);
-        for (int i = tid; i < a.nfac; i += blockDim.x) sf[i] = __ldg(a.fac + i);
-        const int nst = min(a.nstat, G::kStatRows * G::kThreads);
-        for (int i = tid; i < nst; i += blockDim.x) ss[i] = __ldg(a.stat + i);
-    }
+    load_programme<K>(a, sm, tid, blockDim.x);
     if (tid == 0) {
         mbar_init(bar, 1);
+        mbar_init(rbar, G::kWarps);
         fence_mbar_init();
     }
     __syncthreads();
     if (!a.gen && tid < 32 && (uint64_t)blockIdx.x < a.ntiles)
         issue_tile_load<K>(a, sm, state, blockIdx.x, bar, tid);
 
-    uint32_t parity = 0;
+    uint32_t parity = 0, rd = 0, buf = 0;
     for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         const uint64_t next = tile + gridDim.x;
-        // per-tile diagonal data while the copies are in flight (the barrier
-        // first: the previous tile's programme may still read lin / cst);
-        // one thread forms the tile's base index, the others read it back
-        __syncthreads();
-        for (int i = tid; i < a.nruns * 16; i += blockDim.x) lin[i] = 0u;
-        for (int i = tid; i < a.nruns; i += blockDim.x) cst[i] = 0u;
-        if (tid == 0) t2_tile_base = pdep(tile, a.gmask);
-        __syncthreads();
-        const uint64_t base = t2_tile_base;
-        for (int i = tid; i < a.ntterms; i += blockDim.x) {
-            const T2TileTerm t = a.tterms[i];
-            bool on = (base >> t.g0) & 1;
-            if (t.g1 >= 0) on = on && ((base >> t.g1) & 1);
-            if (on) atomicAdd(t.tb >= 0 ? &lin[t.run * 16 + t.tb] : &cst[t.run], t.theta);
-        }
+        const uint64_t base = tile_base(a, tile);
+        // the tile's slot values while its copies are in flight, into the
+        // buffer the previous tile did not use (every warp passed that tile's
+        // barrier below, so none still reads the one before)
+        float2 *sc = slotc + buf * kT2MaxSlots;
+        tile_slots<K>(a, tab, sc, base, tid);
         const bool timed_out = a.gen ? false : !mbar_wait(bar, parity);
         if (__syncthreads_or(timed_out)) {
             if (tid == 0) atomicExch(a.err, 1);
             mbar_wait(bar, parity);  // give copies still in flight a second bounded wait
             return;
         }
+        // the next tile's copies, once every warp has read the last layout
         auto hook = [&]() {
-            if (!a.gen && tid < 32 && next < a.ntiles) issue_tile_load<K>(a, sm, state, next, bar, tid);
+            if (!a.gen && tid < 32 && next < a.ntiles) {
+                if (!mbar_wait(rbar, (rd - 1u) & 1u)) atomicExch(a.err, 1);
+                issue_tile_load<K>(a, sm, state, next, bar, tid);
+            }
         };
-        t2_run<K, F>(a, reinterpret_cast<float4 *>(state), hook);
+        t2_run<K, F>(a, reinterpret_cast<float4 *>(state), rbar, rd, base, sc, hook);
         parity ^= 1u;
+        buf ^= 1u;
     }
 }
 
@@ -438,11 +618,10 @@ __global__ void __launch_bounds__(Geo<K>::kThreads, K == kT2Qubits ? 2 : 1)
 template <int F>
 __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ states, const BatchArgs B) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    float4 *tile4 = reinterpret_cast<float4 *>(sm);
-    float2 *tab = reinterpret_cast<float2 *>(sm + kOffTab);
-    uint32_t *lin = reinterpret_cast<uint32_t *>(sm + kOffLin);
-    uint32_t *cst = reinterpret_cast<uint32_t *>(sm + kOffCst);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + kOffBar);
+    float2 *tab = reinterpret_cast<float2 *>(sm + G13::kOffTab);
+    float2 *slotc = reinterpret_cast<float2 *>(sm + G13::kOffSlotc);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + G13::kOffBar);
+    uint64_t *rbar = bar + 1;
     __shared__ int s_item;
     // read-out reduction scratch lives in the tile buffer (free after the last pass)
     double *s_val = reinterpret_cast<double *>(sm);
@@ -452,10 +631,11 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
     for (int i = tid; i < kTabEntries; i += blockDim.x) tab[i] = B.tables[i];
     if (tid == 0) {
         mbar_init(bar, 1);
+        mbar_init(rbar, kT2Threads / 32);
         fence_mbar_init();
     }
     __syncthreads();
-    uint32_t parity = 0;
+    uint32_t parity = 0, rd = 0, buf = 0;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(B.queue, 1);
         __syncthreads();
@@ -477,28 +657,12 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
             // the current one's last stage change has read shared memory, and
             // write it straight from registers
             if (!a.gen && tid < 32) issue_tile_load<kT2Qubits>(a, sm, state, 0, bar, tid);
-            {  // the pass's programme into shared memory (sizes bounded by the stage compiler)
-                int4 *si = reinterpret_cast<int4 *>(sm + G13::kOffIns);
-                int4 *sf = reinterpret_cast<int4 *>(sm + G13::kOffFac);
-                uint32_t *ss = reinterpret_cast<uint32_t *>(sm + G13::kOffStat);
-                for (int i = tid; i < a.nins; i += blockDim.x) si[i] = __ldg(a.ins + i);
-                for (int i = tid; i < a.nfac; i += blockDim.x) sf[i] = __ldg(a.fac + i);
-                const int nst = min(a.nstat, G13::kStatRows * G13::kThreads);
-                for (int i = tid; i < nst; i += blockDim.x) ss[i] = __ldg(a.stat + i);
-            }
+            load_programme<kT2Qubits>(a, sm, tid, blockDim.x);
             for (uint64_t tile = 0; tile < a.ntiles; tile++) {
-                __syncthreads();  // the previous tile's programme may still read lin / cst
-                for (int i = tid; i < a.nruns * 16; i += blockDim.x) lin[i] = 0u;
-                for (int i = tid; i < a.nruns; i += blockDim.x) cst[i] = 0u;
-                if (tid == 0) t2_tile_base = pdep(tile, a.gmask);
-                __syncthreads();
-                const uint64_t base = t2_tile_base;
-                for (int i = tid; i < a.ntterms; i += blockDim.x) {
-                    const T2TileTerm t = a.tterms[i];
-                    bool on = (base >> t.g0) & 1;
-                    if (t.g1 >= 0) on = on && ((base >> t.g1) & 1);
-                    if (on) atomicAdd(t.tb >= 0 ? &lin[t.run * 16 + t.tb] : &cst[t.run], t.theta);
-                }
+                const uint64_t base = tile_base(a, tile);
+                // slot values into the buffer the previous tile did not use
+                float2 *sc = slotc + buf * kT2MaxSlots;
+                tile_slots<kT2Qubits>(a, tab, sc, base, tid);
                 bool timed_out = false;
                 if (!a.gen) {
                     timed_out = !mbar_wait(bar, parity);
@@ -510,10 +674,13 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
                     return;
                 }
                 auto hook = [&]() {
-                    if (!a.gen && tid < 32 && tile + 1 < a.ntiles)
+                    if (!a.gen && tid < 32 && tile + 1 < a.ntiles) {
+                        if (!mbar_wait(rbar, (rd - 1u) & 1u)) atomicExch(B.err, 1);
                         issue_tile_load<kT2Qubits>(a, sm, state, tile + 1, bar, tid);
+                    }
                 };
-                t2_run<kT2Qubits, F>(a, reinterpret_cast<float4 *>(state), hook);
+                t2_run<kT2Qubits, F>(a, reinterpret_cast<float4 *>(state), rbar, rd, base, sc, hook);
+                buf ^= 1u;
             }
             // the next pass's bulk copies (and the read-out) see this pass's stores
             asm volatile("fence.proxy.async;" ::: "memory");
@@ -631,9 +798,52 @@ sv_status t2_prepare(sv_state *h) {
     return SV_OK;
 }
 
+void t2_fill_args(const T2Pass &p, const T2Device &d, int n, T2Args *a) {
+    a->gmask = p.gmask;
+    a->ntiles = UINT64_C(1) << (n - p.k);
+    a->c = p.c;
+    a->nins = (int)p.ins.size();
+    a->nfac = (int)p.fac2.size();
+    a->nrows = (int)(p.statc.size() / (2 * (size_t)p.threads));
+    a->nslots = (int)p.slots.size();
+    a->nmats = (int)p.mats.size();
+    a->nstages = (int)p.stages.size();
+    a->last_stage = p.last_stage;
+    for (int s = 0; s < p.k; s++) a->slot_phys[s] = p.slot_phys[s];
+    // runs of the global bits: tile index bit i is the i-th lowest set bit of gmask
+    a->ngr = 0;
+    int ti = 0;
+    const uint64_t gm = p.gmask & ((n >= 64) ? ~UINT64_C(0) : ((UINT64_C(1) << n) - 1));
+    for (int b = 0; b < n;) {
+        if (!((gm >> b) & 1)) {
+            b++;
+            continue;
+        }
+        int e = b;
+        while (e < n && ((gm >> e) & 1)) e++;
+        a->gs[a->ngr] = (int8_t)ti;
+        a->gd[a->ngr] = (int8_t)b;
+        a->gl[a->ngr] = (int8_t)(e - b);
+        a->ngr++;
+        ti += e - b;
+        b = e;
+    }
+    a->ins = reinterpret_cast<const int4 *>(d.ins);
+    a->stages = reinterpret_cast<const int4 *>(d.stages);
+    a->mats = reinterpret_cast<const float4 *>(d.mats);
+    a->fac = reinterpret_cast<const int4 *>(d.fac);
+    a->statc = reinterpret_cast<const float2 *>(d.statc);
+    a->soff = d.soff;
+    a->sterms = d.sterms;
+    a->layx = d.layx;
+    a->epi = d.epi;
+}
+
 sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta,
                     int64_t gen_basis) {
+    if (p.format != 2) return fail(SV_ERR_ARG, "internal: register-stage pass not in format 2");
     T2Args a{};
+    t2_fill_args(p, d, h->n, &a);
     if (gen_basis >= 0) {
         a.gen = 1;
         a.gen_basis = (uint64_t)gen_basis;
@@ -641,26 +851,8 @@ sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
             a.gen_local |= (int)((a.gen_basis >> p.slot_phys[s]) & 1) << s;
         a.gen_hmask = p.gen_hmask;
     }
-    a.gmask = p.gmask;
-    a.ntiles = UINT64_C(1) << (h->n - p.k);
-    a.c = p.c;
-    a.nins = (int)p.ins.size();
-    a.nfac = (int)p.factors.size();
-    a.nstat = (int)p.stat.size();
-    a.last_stage = p.last_stage;
-    a.nruns = p.nruns;
-    a.ntterms = (int)p.tterms.size();
-    for (int s = 0; s < p.k; s++) a.slot_phys[s] = p.slot_phys[s];
-    a.ins = reinterpret_cast<const int4 *>(d.ins);
-    a.stages = reinterpret_cast<const int4 *>(d.stages);
-    a.mats = reinterpret_cast<const float4 *>(d.mats);
-    a.fac = reinterpret_cast<const int4 *>(d.fac);
-    a.stat = d.stat;
-    a.tterms = d.tterms;
     a.tables = reinterpret_cast<const float2 *>(h->t2_tables);
     a.err = h->t2_err;
-    a.layx = d.layx;
-    a.epi = d.epi;
     if (p.k != 13 && p.k != 14) return fail(SV_ERR_ARG, "internal: register-stage tile of 2^%d", p.k);
     // the smallest instantiation whose gate kinds cover the programme
     const int need = t2_gate_kinds(p);

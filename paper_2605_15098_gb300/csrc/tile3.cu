@@ -283,6 +283,8 @@ __global__ void __launch_bounds__(kT3Threads, 1) k_tile3(float *__restrict__ sta
             const int op = w.x & 0xff;
             if (op == T2_STAGE) {
                 if (live) {
+                    // every warp has read the previous layout before any overwrites it
+                    __syncthreads();
 #pragma unroll
                     for (int q = 0; q < kNP; q++)
                         tile4[sidx(q)] = make_float4(r.re[q].x, r.re[q].y, r.im[q].x, r.im[q].y);

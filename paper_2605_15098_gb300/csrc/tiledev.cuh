@@ -30,6 +30,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                  "r"(bytes)
                  : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -204,29 +207,43 @@ __device__ __forceinline__ void reg_u(Regs &r, int jc, const float *m) {
     }
 }
 
-// Uncontrolled gates on register bit J for the register-stage kernel.  `qm`
-// is all ones at run time; testing one of its bits per group of four packed
-// pairs keeps each group a separate block, which bounds how many pairs the
-// compiler keeps in flight (and so the register pressure).
-// The butterfly runs in place, b' = a - b then a' = 2a - b', so no register
-// of the pair needs a copy; a' equals a + b up to one extra rounding of a - b.
+// Uncontrolled gates on register bit J for the register-stage kernel.  For
+// J >= 1 the 8 butterflies (q, q | 2^(J-1)) are numbered b = 0..7 (q is b with
+// a 0 inserted at bit J-1) and taken in two groups of four; `qm` is all ones
+// at run time, and testing one of its bits per group keeps each group a
+// separate block: four independent butterflies in flight, whatever J, which
+// bounds the registers the compiler keeps live.  J = 0 acts inside each
+// packed pair, in four groups of four pairs.
+template <int J>
+__device__ __forceinline__ constexpr int bfly_q(int b) {
+    return ((b >> (J - 1)) << J) | (b & ((1 << (J - 1)) - 1));
+}
+
+// The butterfly runs in place, a' = a + b then b' = a' - 2b, so no register
+// of the pair needs a copy and no operand needs negating; b' equals a - b up
+// to one extra rounding of a + b.
 template <int J, int NP>
 __device__ __forceinline__ void reg_h2(RegsN<NP> &r, uint32_t qm) {
+    if constexpr (J >= 1) {
 #pragma unroll
-    for (int g4 = 0; g4 < NP / 4; g4++) {
-        if (!((qm >> g4) & 1)) continue;
+        for (int g = 0; g < NP / 8; g++) {
+            if (!((qm >> g) & 1)) continue;
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const int q = 4 * g4 + i;
-            if constexpr (J >= 1) {
-                constexpr int S = 1 << (J - 1);
-                if (q & S) continue;
-                const int q1 = q | S;
-                r.re[q1] = sub2(r.re[q], r.re[q1]);
-                r.im[q1] = sub2(r.im[q], r.im[q1]);
-                r.re[q] = fma2(r.re[q], f2(2.f), make_float2(-r.re[q1].x, -r.re[q1].y));
-                r.im[q] = fma2(r.im[q], f2(2.f), make_float2(-r.im[q1].x, -r.im[q1].y));
-            } else {
+            for (int i = 0; i < 4; i++) {
+                const int q = bfly_q<J>(4 * g + i), q1 = q | (1 << (J - 1));
+                r.re[q] = add2(r.re[q], r.re[q1]);
+                r.im[q] = add2(r.im[q], r.im[q1]);
+                r.re[q1] = fma2(r.re[q1], f2(-2.f), r.re[q]);
+                r.im[q1] = fma2(r.im[q1], f2(-2.f), r.im[q]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int g4 = 0; g4 < NP / 4; g4++) {
+            if (!((qm >> g4) & 1)) continue;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const int q = 4 * g4 + i;
                 const float2 a = r.re[q], b = r.im[q];
                 r.re[q] = make_float2(a.x + a.y, a.x - a.y);
                 r.im[q] = make_float2(b.x + b.y, b.x - b.y);
@@ -235,69 +252,26 @@ __device__ __forceinline__ void reg_h2(RegsN<NP> &r, uint32_t qm) {
     }
 }
 
-// Phased Hadamard on register bit J: the amplitude b of each pair (bit J = 1)
-// is multiplied by M = (fr + i fi) T[x] (T: a 32-entry phase table laid out as
-// for apply_table, or none), then the pair takes the butterfly of reg_h2.
-template <int J, int NP>
-__device__ __forceinline__ void reg_hph(RegsN<NP> &r, uint32_t qm, const float4 *__restrict__ T, float fr,
-                                        float fi) {
-#pragma unroll
-    for (int g4 = 0; g4 < NP / 4; g4++) {
-        if (!((qm >> g4) & 1)) continue;
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const int q = 4 * g4 + i;
-            if constexpr (J >= 1) {
-                constexpr int S = 1 << (J - 1);
-                if (q & S) continue;
-                const int q1 = q | S;
-                float2 mr = f2(fr), mi = f2(fi);
-                if (T) {
-                    const float4 t = __ldg(T + q1);
-                    const float2 tr = make_float2(t.x, t.y), ti = make_float2(t.z, t.w);
-                    mr = fma2(ti, f2(-fi), mul2(tr, f2(fr)));
-                    mi = fma2(ti, f2(fr), mul2(tr, f2(fi)));
-                }
-                const float2 br = r.re[q1], bi = r.im[q1];
-                const float2 pr = fma2(bi, make_float2(-mi.x, -mi.y), mul2(br, mr));
-                const float2 pi = fma2(bi, mr, mul2(br, mi));
-                r.re[q1] = sub2(r.re[q], pr);
-                r.im[q1] = sub2(r.im[q], pi);
-                r.re[q] = fma2(r.re[q], f2(2.f), make_float2(-r.re[q1].x, -r.re[q1].y));
-                r.im[q] = fma2(r.im[q], f2(2.f), make_float2(-r.im[q1].x, -r.im[q1].y));
-            } else {
-                float mr = fr, mi = fi;
-                if (T) {
-                    const float4 t = __ldg(T + q);  // odd entries (bit 0 set): y and w
-                    mr = t.y * fr - t.w * fi;
-                    mi = t.y * fi + t.w * fr;
-                }
-                float2 &x = r.re[q], &y = r.im[q];
-                const float pr = x.y * mr - y.y * mi, pi = x.y * mi + y.y * mr;
-                x.y = x.x - pr;
-                y.y = y.x - pi;
-                x.x = fmaf(x.x, 2.f, -x.y);
-                y.x = fmaf(y.x, 2.f, -y.y);
-            }
-        }
-    }
-}
-
 template <int J, int NP>
 __device__ __forceinline__ void reg_x2(RegsN<NP> &r, uint32_t qm) {
+    if constexpr (J >= 1) {
 #pragma unroll
-    for (int g4 = 0; g4 < NP / 4; g4++) {
-        if (!((qm >> g4) & 1)) continue;
+        for (int g = 0; g < NP / 8; g++) {
+            if (!((qm >> g) & 1)) continue;
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const int q = 4 * g4 + i;
-            if constexpr (J >= 1) {
-                constexpr int S = 1 << (J - 1);
-                if (q & S) continue;
-                const int q1 = q | S;
+            for (int i = 0; i < 4; i++) {
+                const int q = bfly_q<J>(4 * g + i), q1 = q | (1 << (J - 1));
                 float2 t = r.re[q]; r.re[q] = r.re[q1]; r.re[q1] = t;
                 t = r.im[q]; r.im[q] = r.im[q1]; r.im[q1] = t;
-            } else {
+            }
+        }
+    } else {
+#pragma unroll
+        for (int g4 = 0; g4 < NP / 4; g4++) {
+            if (!((qm >> g4) & 1)) continue;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const int q = 4 * g4 + i;
                 r.re[q] = make_float2(r.re[q].y, r.re[q].x);
                 r.im[q] = make_float2(r.im[q].y, r.im[q].x);
             }
@@ -309,22 +283,27 @@ template <int J, int NP>
 __device__ __forceinline__ void reg_u2(RegsN<NP> &r, uint32_t qm, const float *m) {
     const float u0r = m[0], u0i = m[1], u1r = m[2], u1i = m[3];
     const float u2r = m[4], u2i = m[5], u3r = m[6], u3i = m[7];
+    if constexpr (J >= 1) {
 #pragma unroll
-    for (int g4 = 0; g4 < NP / 4; g4++) {
-        if (!((qm >> g4) & 1)) continue;
+        for (int g = 0; g < NP / 8; g++) {
+            if (!((qm >> g) & 1)) continue;
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const int q = 4 * g4 + i;
-            if constexpr (J >= 1) {
-                constexpr int S = 1 << (J - 1);
-                if (q & S) continue;
-                const int q1 = q | S;
+            for (int i = 0; i < 4; i++) {
+                const int q = bfly_q<J>(4 * g + i), q1 = q | (1 << (J - 1));
                 const float2 ar = r.re[q], ai = r.im[q], br = r.re[q1], bi = r.im[q1];
                 r.re[q] = fma2(bi, f2(-u1i), fma2(br, f2(u1r), fma2(ai, f2(-u0i), mul2(ar, f2(u0r)))));
                 r.im[q] = fma2(br, f2(u1i), fma2(bi, f2(u1r), fma2(ar, f2(u0i), mul2(ai, f2(u0r)))));
                 r.re[q1] = fma2(bi, f2(-u3i), fma2(br, f2(u3r), fma2(ai, f2(-u2i), mul2(ar, f2(u2r)))));
                 r.im[q1] = fma2(br, f2(u3i), fma2(bi, f2(u3r), fma2(ar, f2(u2i), mul2(ai, f2(u2r)))));
-            } else {
+            }
+        }
+    } else {
+#pragma unroll
+        for (int g4 = 0; g4 < NP / 4; g4++) {
+            if (!((qm >> g4) & 1)) continue;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const int q = 4 * g4 + i;
                 const float ar = r.re[q].x, ai = r.im[q].x, br = r.re[q].y, bi = r.im[q].y;
                 r.re[q].x = u0r * ar - u0i * ai + u1r * br - u1i * bi;
                 r.im[q].x = u0r * ai + u0i * ar + u1r * bi + u1i * br;
@@ -342,23 +321,28 @@ __device__ __forceinline__ void reg_u2(RegsN<NP> &r, uint32_t qm, const float *m
 template <int J, int NP>
 __device__ __forceinline__ void reg_rot(RegsN<NP> &r, uint32_t qm, const float *m) {
     const float t = m[0], s = m[1];
+    if constexpr (J >= 1) {
 #pragma unroll
-    for (int g4 = 0; g4 < NP / 4; g4++) {
-        if (!((qm >> g4) & 1)) continue;
+        for (int g = 0; g < NP / 8; g++) {
+            if (!((qm >> g) & 1)) continue;
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const int q = 4 * g4 + i;
-            if constexpr (J >= 1) {
-                constexpr int S = 1 << (J - 1);
-                if (q & S) continue;
-                const int q1 = q | S;
+            for (int i = 0; i < 4; i++) {
+                const int q = bfly_q<J>(4 * g + i), q1 = q | (1 << (J - 1));
                 r.re[q] = fma2(r.re[q1], f2(t), r.re[q]);
                 r.im[q] = fma2(r.im[q1], f2(t), r.im[q]);
                 r.re[q1] = fma2(r.re[q], f2(s), r.re[q1]);
                 r.im[q1] = fma2(r.im[q], f2(s), r.im[q1]);
                 r.re[q] = fma2(r.re[q1], f2(t), r.re[q]);
                 r.im[q] = fma2(r.im[q1], f2(t), r.im[q]);
-            } else {
+            }
+        }
+    } else {
+#pragma unroll
+        for (int g4 = 0; g4 < NP / 4; g4++) {
+            if (!((qm >> g4) & 1)) continue;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const int q = 4 * g4 + i;
                 float2 &x = r.re[q], &y = r.im[q];
                 x.x = fmaf(x.y, t, x.x);
                 y.x = fmaf(y.y, t, y.x);
@@ -376,88 +360,30 @@ __device__ __forceinline__ void reg_rot(RegsN<NP> &r, uint32_t qm, const float *
 template <int J, int NP>
 __device__ __forceinline__ void reg_r2(RegsN<NP> &r, uint32_t qm, const float *m) {
     const float a = m[0], b = m[2], c = m[4], d = m[6];
+    if constexpr (J >= 1) {
 #pragma unroll
-    for (int g4 = 0; g4 < NP / 4; g4++) {
-        if (!((qm >> g4) & 1)) continue;
+        for (int g = 0; g < NP / 8; g++) {
+            if (!((qm >> g) & 1)) continue;
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const int q = 4 * g4 + i;
-            if constexpr (J >= 1) {
-                constexpr int S = 1 << (J - 1);
-                if (q & S) continue;
-                const int q1 = q | S;
+            for (int i = 0; i < 4; i++) {
+                const int q = bfly_q<J>(4 * g + i), q1 = q | (1 << (J - 1));
                 const float2 ar = r.re[q], ai = r.im[q], br = r.re[q1], bi = r.im[q1];
                 r.re[q] = fma2(br, f2(b), mul2(ar, f2(a)));
                 r.im[q] = fma2(bi, f2(b), mul2(ai, f2(a)));
                 r.re[q1] = fma2(br, f2(d), mul2(ar, f2(c)));
                 r.im[q1] = fma2(bi, f2(d), mul2(ai, f2(c)));
-            } else {
+            }
+        }
+    } else {
+#pragma unroll
+        for (int g4 = 0; g4 < NP / 4; g4++) {
+            if (!((qm >> g4) & 1)) continue;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                const int q = 4 * g4 + i;
                 const float ar = r.re[q].x, ai = r.im[q].x, br = r.re[q].y, bi = r.im[q].y;
                 r.re[q] = make_float2(a * ar + b * br, c * ar + d * br);
                 r.im[q] = make_float2(a * ai + b * bi, c * ai + d * bi);
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ float2 shfl_xor2(float2 v, int xm) {
-    double d;
-    memcpy(&d, &v, 8);
-    d = __shfl_xor_sync(0xffffffffu, d, xm);
-    float2 o;
-    memcpy(&o, &d, 8);
-    return o;
-}
-
-// Uncontrolled (kPred false) or thread-predicated gate OP on lane bit l (see reg_h2 for qm).
-template <int OP, bool kPred, int NP>
-__device__ __forceinline__ void lane_op3(RegsN<NP> &r, int l, bool pred, uint32_t qm, const float *m) {
-    const int xm = 1 << l;
-    const bool hi = (threadIdx.x >> l) & 1;
-    float csr = 0.f, csi = 0.f, cor = 0.f, coi = 0.f;
-    if constexpr (OP == T2_GATE) {
-        csr = hi ? m[6] : m[0];
-        csi = hi ? m[7] : m[1];
-        cor = hi ? m[4] : m[2];
-        coi = hi ? m[5] : m[3];
-    } else if constexpr (OP == T2_RGATE) {
-        csr = hi ? m[6] : m[0];
-        cor = hi ? m[4] : m[2];
-    } else if constexpr (OP == T2_H) {
-        csr = hi ? -1.f : 1.f;
-        cor = 1.f;
-    } else {
-        cor = 1.f;
-    }
-    if constexpr (kPred) {  // an unselected thread keeps its value: self 1, partner 0
-        if (!pred) {
-            csr = 1.f;
-            csi = 0.f;
-            cor = 0.f;
-            coi = 0.f;
-        }
-    }
-#pragma unroll
-    for (int g4 = 0; g4 < NP / 4; g4++) {
-        if (!((qm >> g4) & 1)) continue;
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const int q = 4 * g4 + i;
-            const float2 pr = shfl_xor2(r.re[q], xm), pi = shfl_xor2(r.im[q], xm);
-            if constexpr (OP == T2_H && !kPred) {
-                r.re[q] = fma2(r.re[q], f2(csr), pr);
-                r.im[q] = fma2(r.im[q], f2(csr), pi);
-            } else if constexpr (OP == T2_X && !kPred) {
-                r.re[q] = pr;
-                r.im[q] = pi;
-            } else if constexpr (OP != T2_GATE) {
-                r.re[q] = fma2(pr, f2(cor), mul2(r.re[q], f2(csr)));
-                r.im[q] = fma2(pi, f2(cor), mul2(r.im[q], f2(csr)));
-            } else {
-                const float2 nr = fma2(pi, f2(-coi), fma2(pr, f2(cor), fma2(r.im[q], f2(-csi), mul2(r.re[q], f2(csr)))));
-                const float2 ni = fma2(pr, f2(coi), fma2(pi, f2(cor), fma2(r.re[q], f2(csi), mul2(r.im[q], f2(csr)))));
-                r.re[q] = nr;
-                r.im[q] = ni;
             }
         }
     }
@@ -532,44 +458,6 @@ __device__ __forceinline__ void lane_gate(Regs &r, int op, int l, int jc, bool p
     }
 }
 
-// Uncontrolled (or thread-predicated) gate OP on lane bit l, OP fixed at
-// compile time: four shuffles per packed pair, then the 2x2 arithmetic.
-template <int OP>
-__device__ __forceinline__ void lane_op(Regs &r, int l, bool pred, const float *m) {
-    const unsigned FULL = 0xffffffffu;
-    const int xm = 1 << l;
-    const bool hi = (threadIdx.x >> l) & 1;
-    float csr = 0.f, csi = 0.f, cor = 0.f, coi = 0.f;
-    if constexpr (OP == T2_GATE) {
-        csr = hi ? m[6] : m[0];
-        csi = hi ? m[7] : m[1];
-        cor = hi ? m[4] : m[2];
-        coi = hi ? m[5] : m[3];
-    }
-    const float sg = hi ? -1.f : 1.f;
-#pragma unroll
-    for (int q = 0; q < kNP; q++) {
-        float2 pr, pi;
-        pr.x = __shfl_xor_sync(FULL, r.re[q].x, xm);
-        pr.y = __shfl_xor_sync(FULL, r.re[q].y, xm);
-        pi.x = __shfl_xor_sync(FULL, r.im[q].x, xm);
-        pi.y = __shfl_xor_sync(FULL, r.im[q].y, xm);
-        if (!pred) continue;
-        if constexpr (OP == T2_H) {
-            r.re[q] = fma2(r.re[q], f2(sg), pr);
-            r.im[q] = fma2(r.im[q], f2(sg), pi);
-        } else if constexpr (OP == T2_X) {
-            r.re[q] = pr;
-            r.im[q] = pi;
-        } else {
-            const float2 nr = fma2(pi, f2(-coi), fma2(pr, f2(cor), fma2(r.im[q], f2(-csi), mul2(r.re[q], f2(csr)))));
-            const float2 ni = fma2(pr, f2(coi), fma2(pi, f2(cor), fma2(r.re[q], f2(csi), mul2(r.im[q], f2(csr)))));
-            r.re[q] = nr;
-            r.im[q] = ni;
-        }
-    }
-}
-
 // ---------------------------------------------------------------- diagonal factors
 template <int M, typename R>
 __device__ __forceinline__ void apply_factor(R &r, float fr, float fi) {
@@ -580,27 +468,6 @@ __device__ __forceinline__ void apply_factor(R &r, float fr, float fi) {
             if (((2 * q + 1) & M) == M) cmul1(r.re[q].y, r.im[q].y, fr, fi);
         } else {
             if (((2 * q) & M) == M) cmul2(r.re[q], r.im[q], fr, fi);
-        }
-    }
-}
-
-// Multiply amplitude x of the register index by entry x of a 32-entry
-// constant phase table: T[q] = (re[2q], re[2q+1], im[2q], im[2q+1]).  `qm` as
-// in reg_h2 (all ones at run time; bounds the loads kept in flight).
-template <int NP>
-__device__ __forceinline__ void apply_table(RegsN<NP> &r, const float4 *__restrict__ T, uint32_t qm) {
-#pragma unroll
-    for (int g4 = 0; g4 < NP / 4; g4++) {
-        if (!((qm >> g4) & 1)) continue;
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-            const int q = 4 * g4 + i;
-            const float4 t = __ldg(T + q);
-            const float2 tr = make_float2(t.x, t.y), ti = make_float2(t.z, t.w);
-            const float2 nr = fma2(r.im[q], make_float2(-t.z, -t.w), mul2(r.re[q], tr));
-            const float2 ni = fma2(r.im[q], tr, mul2(r.re[q], ti));
-            r.re[q] = nr;
-            r.im[q] = ni;
         }
     }
 }

@@ -113,11 +113,81 @@ struct T2Stage {
 // (in amplitudes) of the lane bits (lo, indexed by tid & 31) and the warp bits
 // (hi, indexed by tid >> 5), and of register bits 1..  A thread's packed pair q
 // sits at tile offset lo + hi + sum over the set bits j of q of s[j].
+// The p* fields give the same positions in the swizzled shared-memory order
+// of a stage change (format 2, below): the float4 slot of packed pair q is
+// plo ^ phi ^ (xor over the set bits j of q of ps[j]).
 struct T2LayoutX {
     uint16_t lo[32];  // lane bits (tid & 31)
     uint16_t hi[16];  // warp bits (tid >> 5)
     int32_t s[4];     // register bits 1.. (unused ones 0)
+    uint16_t plo[32];
+    uint16_t phi[16];
+    int32_t ps[4];
 };
+
+// ---------------------------------------------------------------- format 2
+// The complex64 register-stage kernel (k_tile2, k_batch) runs programmes in
+// format 2, compiled by compile_t2 without fused blocks:
+//  * every gate target is a register bit of its stage (no shuffle gates): a
+//    target outside the register bits starts a new stage;
+//  * a stage change stores the tile to shared memory and loads it back in the
+//    new layout, both in a swizzled order: the 16-byte vector of float4 index
+//    f (tile index >> 1) lives at slot swz(f) = f ^ fold(f), where fold(f)
+//    XORs f's bits 3.., three at a time, onto bits 0..2.  A quarter-warp's
+//    eight lanes then hit eight distinct bank groups whenever lane bits 0..2
+//    are tile bits whose float4 bits (tile bit - 1) differ mod 3, which the
+//    stage compiler arranges;
+//  * the first stage of a pass that reads its tile takes it from the bulk
+//    copies' linear order, so its lane bits 0..2 are tile bits 1..3; a pass
+//    that generates a recorded basis state has a variant of its own, without
+//    that rule and without the leading Hadamards (they are part of the
+//    generated state);
+//  * diagonal runs compile to T2Fac records: a per-thread factor is a static
+//    complex row (one FP32 e^{i phi} per thread, formed in FP64 on the host)
+//    times tile-uniform slot values (e^{i phi} of the tile's global-qubit
+//    terms, formed once per tile from FP64-generated tables), times one slot
+//    per dynamic thread bit; constants become 32-entry tables as before.
+inline int swz_fold(int f) { return ((f >> 3) ^ (f >> 6) ^ (f >> 9) ^ (f >> 12)) & 7; }
+inline int swz(int f) { return f ^ swz_fold(f); }
+
+// One factor application of format 2, 16 bytes.
+//   w0: as T2Factor (bits 0..7 register mask, bit 8 per-thread, bits 10..13
+//       thread predicate of a table, bits 19..27 dynamic thread bits, bit 28
+//       table); the other bits 0
+//   slot: tile-uniform slot multiplied into a per-thread factor, -1 = none
+//   dslot: slot of the lowest dynamic thread bit; the k-th lowest set bit of
+//       the dynamic mask uses dslot + k
+//   row: per-thread factor: static complex row (-1 = none); table: first
+//       matrix record of the 32-entry table
+struct T2Fac {
+    uint32_t w0;
+    int16_t slot, dslot;
+    int32_t row;
+    int32_t pad;
+};
+
+// A tile-uniform slot: e^{2 pi i (lin[i0] + lin[i1]) / 2^32} for the per-tile
+// phase words lin[run * 16 + tb] (tb = tile bit; 15 = the run's constant);
+// i1 = -1: lin[i0] alone.
+struct T2Slot {
+    int16_t i0, i1;
+};
+constexpr int kT2MaxSlots = 256;
+constexpr int kT2SmemMats = 384;     // matrix records kept in shared memory
+constexpr int kT2SmemRows = 8;       // static complex rows kept in shared memory
+constexpr int kT2SmemStages = 16;    // stage layouts kept in shared memory
+
+// One global-qubit term of a slot, for the kernel: theta (turns / 2^32) when
+// physical bits g0 (and g1, if >= 0) of the tile are set.  The terms of slot
+// s are sterms[soff[s] .. soff[s + 1]): those of its phase words i0 and i1.
+struct T2SlotTerm {
+    int16_t g0, g1;
+    uint32_t theta;
+};
+
+// Handler codes of the non-gate steps (format 2), in the same field as the
+// gate handlers: the kernel dispatches every step with one switch.
+constexpr int kT2HdStage = 1, kT2HdScale = 2, kT2HdDiag = 3;
 
 // Write-back offsets of the final layout in the global state (amplitudes),
 // relative to the tile's base: lane bits, warp bits and register bits 1..

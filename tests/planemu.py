@@ -110,18 +110,42 @@ def run_generic_pass(state, p):
         state[idx] = t
 
 
-def run_t2_pass(state, p):
-    t2 = p["t2"]
+def _expi32(u):
+    return np.exp(2j * np.pi * ((u & MASK32) / 2.0 ** 32))
+
+
+def run_t2_pass(state, p, t2=None, gen_basis=None):
+    """Execute a register-stage pass.  `t2` defaults to the pass's programme;
+    with `gen_basis` (a physical basis index) the pass starts from that basis
+    state and generates its tiles instead of reading them (the programme is
+    then the pass's generated-state variant, `t2gen`)."""
+    t2 = t2 if t2 is not None else p["t2"]
+    fmt = t2.get("format", 1)
     k = p["k"]
     ntiles = 1 << (int(np.log2(state.size)) - k)
     loc = np.arange(1 << k)
     stat = np.asarray(t2["stat"], dtype=np.int64)
     rb, nthreads = t2["rb"], t2["threads"]
     nw = nthreads.bit_length() - 1 - 5          # warp bits
+    if fmt == 2:
+        sc = np.asarray(t2["statc"], dtype=np.float64).reshape(-1, nthreads, 2)
+        statc = sc[:, :, 0] + 1j * sc[:, :, 1]
+    nstages = sum(1 for ins in t2["ins"] if ins["op"] == T2_STAGE)
     for tile in range(ntiles):
         base = pdep(tile, p["gmask"])
         idx = tile_index(p, base)
-        t = state[idx].copy()
+        if gen_basis is None:
+            t = state[idx].copy()
+        else:  # the basis state after the leading Hadamards, unnormalised
+            hm = t2["gen_hmask"]
+            gl = 0
+            for s_, q in enumerate(p["slot_phys"]):
+                gl |= ((gen_basis >> q) & 1) << s_
+            has = (gen_basis & p["gmask"]) == base
+            par = np.array([bin(int(i) & gl & hm).count("1") & 1 for i in loc])
+            t = np.where(((loc ^ gl) & ~hm) == 0, np.where(par == 1, -1.0, 1.0), 0.0).astype(complex)
+            if not has:
+                t[:] = 0
         lin = [0] * (16 * max(t2["nruns"], 1))
         cst = [0] * max(t2["nruns"], 1)
         for run, tb, g0, g1, th in t2["tterms"]:
@@ -129,18 +153,31 @@ def run_t2_pass(state, p):
             if g1 >= 0:
                 on &= (base >> g1) & 1
             if on:
-                if tb >= 0:
+                if fmt == 2:
+                    i = run * 16 + (tb if tb >= 0 else 15)
+                    lin[i] = (lin[i] + th) & MASK32
+                elif tb >= 0:
                     lin[run * 16 + tb] = (lin[run * 16 + tb] + th) & MASK32
                 else:
                     cst[run] = (cst[run] + th) & MASK32
+        if fmt == 2:
+            slotv = [_expi32(lin[i0] + (lin[i1] if i1 >= 0 else 0)) for i0, i1 in t2["slots"]]
         st = None
+        nst = 0
         for ins in t2["ins"]:
             op = ins["op"]
             if op == T2_STAGE:
                 st = t2["stages"][ins["aux"]]
                 reg, lane, warp = st[0:rb], st[5:10], st[10:10 + nw]
                 assert sorted(reg + lane + warp) == list(range(k))
-                assert reg[0] == 0 and lane[:3] == [1, 2, 3]
+                assert reg[0] == 0
+                if fmt == 1:
+                    assert lane[:3] == [1, 2, 3]
+                elif nst == 0 and gen_basis is None:
+                    assert lane[:3] == [1, 2, 3]  # read in the bulk copies' linear order
+                nst += 1
+                if fmt == 2 and nst == nstages:
+                    assert lane[:3] == [1, 2, 3]  # coalesced write-back
                 ttb = lane + warp                   # tile bit of thread bit t
                 tid = np.zeros(t.size, dtype=np.int64)
                 for tt_, b in enumerate(ttb):
@@ -164,7 +201,8 @@ def run_t2_pass(state, p):
                 t *= np.float64(np.float32(m[0])) + np.float64(np.float32(m[1]))
                 continue
             if op in (T2_DIAG, T2_HPH):  # T2_HPH: the run, then H on register bit idx
-                for f in t2["factors"][ins["e0"]:ins["e1"]]:
+                facs = t2["fac2"] if fmt == 2 else t2["factors"]
+                for f in facs[ins["e0"]:ins["e1"]]:
                     w0 = f["w0"]
                     if (w0 >> 28) & 1:  # 32-entry constant phase table (tileprog.h)
                         pb = (w0 >> 10) & 0xF
@@ -184,7 +222,18 @@ def run_t2_pass(state, p):
                     for j in range(rb):
                         if (mask >> j) & 1:
                             sel &= ((loc >> reg[j]) & 1) == 1
-                    if not (w0 >> 8) & 1:
+                    dm = (w0 >> 19) & 0x1FF
+                    if fmt == 2:  # static complex row x tile slot x one slot per dynamic bit
+                        fac = statc[f["row"]][tid] if f["row"] >= 0 else np.ones(t.size, dtype=complex)
+                        if f["slot"] >= 0:
+                            fac = fac * slotv[f["slot"]]
+                        rank = 0
+                        for tt_ in range(5 + nw):
+                            if (dm >> tt_) & 1:
+                                on = ((tid >> tt_) & 1) == 1
+                                fac = np.where(on, fac * slotv[f["dslot"] + rank], fac)
+                                rank += 1
+                    elif not (w0 >> 8) & 1:
                         fac = np.full(t.size, f["c"][0] + 1j * f["c"][1])
                         pb = (w0 >> 10) & 0xF
                         if pb:
@@ -197,7 +246,6 @@ def run_t2_pass(state, p):
                         lr = ((w0 >> 14) & 0x1F) - 1
                         if lr >= 0:
                             u += lin[run * 16 + lr]
-                        dm = (w0 >> 19) & 0x1FF
                         for tt_ in range(5 + nw):
                             if (dm >> tt_) & 1:
                                 u += ((tid >> tt_) & 1) * lin[run * 16 + ttb[tt_]]
@@ -210,7 +258,7 @@ def run_t2_pass(state, p):
             if ins["cls"] == C_REG:
                 bit = reg[ins["idx"]]
             else:
-                assert ins["cls"] == C_LANE and ins["idx"] < 5
+                assert fmt == 1 and ins["cls"] == C_LANE and ins["idx"] < 5
                 bit = lane[ins["idx"]]
             cond = None
             if ins["ccls"] == C_GLOBAL:
@@ -247,18 +295,26 @@ def remap(state, pairs):
     return out
 
 
-def run_plan(n, plan):
+def run_plan(n, plan, use_gen=True):
+    """Run the exported plan from |0...0>.  With `use_gen` the first pass runs
+    its generated-state variant (`t2gen`, as the library does from a recorded
+    basis state) when it has one; otherwise every pass reads its state."""
     state = np.zeros(1 << n, dtype=np.complex128)
     state[0] = 1.0
+    first = True
     for p in plan["passes"]:
         if p.get("remap_before"):
             state = remap(state, p["remap_before"])
         if not p["ops"]:
             continue
         if p["kernel"] in ("t2", "t3"):
-            run_t2_pass(state, p)
+            if first and use_gen and "t2gen" in p:
+                run_t2_pass(state, p, p["t2gen"], gen_basis=0)
+            else:
+                run_t2_pass(state, p)
         else:
             run_generic_pass(state, p)
+        first = False
     # back to logical order
     phys = plan["phys"]
     x = np.arange(1 << n)

@@ -22,11 +22,15 @@ def sv():
 
 
 def check(sv, orc, n, g, cfg, dtype, tol):
+    """Both variants of the first pass (generating |0...0> in registers, as
+    the library does from a recorded basis state, and reading the state)
+    against the oracle."""
     plan = sv.sv_plan_export(n, dtype, g, cfg)
-    got = planemu.run_plan(n, plan)
     ref = orc.run(n, g)
-    err = float(np.max(np.abs(got - ref)))
-    assert err <= tol, err
+    for use_gen in (True, False):
+        got = planemu.run_plan(n, plan, use_gen=use_gen)
+        err = float(np.max(np.abs(got - ref)))
+        assert err <= tol, (use_gen, err)
     return plan
 
 
@@ -187,12 +191,15 @@ def test_fusion_and_prefix_rules(sv, orc):
     plan = check(sv, orc, n, g, cfg, sv.SV_C64, 1e-5)
     ops = t2_ops(plan)
     assert planemu.T2_HPH not in ops and planemu.T2_DIAG in ops
-    # 14 leading Hadamards, then H(3) again: the prefix stops there
+    # 14 leading Hadamards (13 on the first pass's local qubits), then H(3)
+    # again: the generated prefix stops there, and the generated-state variant
+    # of the first pass keeps exactly that one Hadamard step
     g = C.gates([C.h(q) for q in range(n)] + [C.h(3), C.cpk(3, 4, 1, 2)])
     plan = check(sv, orc, n, g, cfg, sv.SV_C64, 1e-5)
-    first = [i["op"] for i in plan["passes"][0]["t2"]["ins"] if i["op"] != planemu.T2_STAGE]
-    k = first.index(planemu.T2_H)
-    assert all(op == planemu.T2_HG for op in first[:k]) and planemu.T2_HG not in first[k:]
+    gen = plan["passes"][0]["t2gen"]
+    assert bin(gen["gen_hmask"]).count("1") == 13
+    ops = [i["op"] for i in gen["ins"]]
+    assert ops.count(planemu.T2_H) + ops.count(planemu.T2_HPH) == 1
 
 
 @pytest.mark.parametrize("flags", [0, 1, 4, 5])
