@@ -95,17 +95,26 @@ sv_status read_marginal(sv_state *h, uint64_t mask, uint64_t *len) {
 
 }  // namespace
 
-// While the state is a recorded basis state |b>, an X gate whose qubit no
-// earlier gate of the list touches commutes to the front of the list and
-// only flips a bit of b: drop it and update b.
+// While the state is a recorded product state H^{hq}|b> (H on the qubits of
+// the mask hq, applied to the basis state |b>), a gate whose qubit no earlier
+// gate of the list touches commutes to the front of the list.  An X on a
+// qubit outside hq only flips a bit of b; an H toggles the qubit in hq (H H
+// is the identity).  Drop such gates and update the record.  An X on a qubit
+// in hq would add a sign that depends on b; it is kept, and so is every
+// later gate on its qubit.
 void sv::fold_basis_prefix(sv_state *h, std::vector<sv_gate> &g) {
     if (h->basis < 0) return;
     bool touched[64] = {};
     std::vector<sv_gate> out;
     out.reserve(g.size());
     for (const sv_gate &a : g) {
-        if (a.kind == SV_X && !touched[a.target]) {
-            h->basis ^= (int64_t)1 << h->phys[a.target];
+        const uint64_t bit = UINT64_C(1) << h->phys[a.target];
+        if (!touched[a.target] && a.kind == SV_X && !(h->basis_h & bit)) {
+            h->basis ^= (int64_t)bit;
+            continue;
+        }
+        if (!touched[a.target] && a.kind == SV_H) {
+            h->basis_h ^= bit;
             continue;
         }
         touched[a.target] = true;
@@ -314,6 +323,7 @@ sv_status sv_copy_in(sv_handle h, const void *host_amps) {
     for (int q = 0; q < 64; q++) h->phys[q] = q;
     h->norm_pending = false;
     h->basis = -1;
+    h->basis_h = 0;
     return SV_OK;
 }
 

@@ -191,6 +191,8 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
                 a.gen_basis = 0;
                 a.gen_local = 0;
                 a.gen_hmask = t2.gen_hmask;
+                a.gen_ghmask = 0;
+                a.gen_val = 1.f;
             }
             {  // counts and geometry; the pointers are set once the blob is on the device
                 const T2Device none{};

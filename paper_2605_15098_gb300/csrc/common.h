@@ -67,9 +67,11 @@ struct sv_state {
     int device = 0;
     int sm_count = 0;
     int phys[64];                 // physical bit of each logical qubit
-    // >= 0: the state is the basis state |basis> (physical index) and the
-    // buffer may still hold old data; -1: the buffer holds the state
+    // >= 0: the state is H on the physical qubits of basis_h applied to the
+    // basis state |basis> (physical index), recorded only: the buffer may
+    // still hold old data; -1: the buffer holds the state
     int64_t basis = -1;
+    uint64_t basis_h = 0;
     void *scratch = nullptr;      // device scratch, grown on demand
     size_t scratch_cap = 0;
     double *probs = nullptr;      // device marginal of the last read-out
@@ -130,7 +132,7 @@ sv_status pergate_apply(sv_state *h, const sv_gate &g_phys);
 sv_status init_zero_state(sv_state *h);
 // Write a recorded basis state into the buffer (no-op when it holds the state).
 sv_status materialize(sv_state *h);
-// Drop the X gates that only flip a bit of a recorded basis state (see api.cu).
+// Drop the X and H gates that only change a recorded basis state (see api.cu).
 void fold_basis_prefix(sv_state *h, std::vector<sv_gate> &gates);
 
 // ---- remap passes (remap.cu) --------------------------------------------------

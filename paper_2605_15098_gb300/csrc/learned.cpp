@@ -287,8 +287,10 @@ sv_status sv_learned_plan(sv_handle h, const sv_gate *host_gates, size_t m, cons
     const sv_config c = partitioned_cfg(h, cfg);
     std::vector<sv_gate> g(host_gates, host_gates + m);
     const int64_t b0 = h->basis;  // the list sv_apply_circuit would plan from this state
+    const uint64_t bh0 = h->basis_h;
     fold_basis_prefix(h, g);
     h->basis = b0;
+    h->basis_h = bh0;
     sv_state::Learned *L = nullptr;
     SV_TRY(learned_entry(h, g, c, &L));
     *out = L->info;
@@ -304,8 +306,10 @@ sv_status sv_planner_judge(sv_handle h, const sv_gate *host_gates, size_t m, con
     SV_TRY(sv_reset(h));
     std::vector<sv_gate> gf = g;  // the list sv_apply_circuit plans after a reset
     const int64_t b0 = h->basis;
+    const uint64_t bh0 = h->basis_h;
     fold_basis_prefix(h, gf);
     h->basis = b0;
+    h->basis_h = bh0;
     sv_state::Learned *L = nullptr;
     SV_TRY(learned_entry(h, gf, c, &L));
     double tg = 0.0, tl = 0.0;

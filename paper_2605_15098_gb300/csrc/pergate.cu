@@ -15,6 +15,9 @@
 // bit 0 pairs the two halves of one vector.  For complex128 a vector is one
 // amplitude.  Consecutive threads take consecutive vectors, so each warp
 // reads and writes whole 512-byte segments.
+#include <algorithm>
+#include <cmath>
+
 #include "common.h"
 
 namespace sv {
@@ -177,11 +180,25 @@ k_pergate_intra(float *__restrict__ s, uint64_t units, Fixed fx, Coef<float> c) 
     }
 }
 
-__global__ void k_set_first(void *amps, int is_double, uint64_t index) {
-    if (is_double)
-        reinterpret_cast<double *>(amps)[2 * index] = 1.0;
-    else
-        reinterpret_cast<float *>(amps)[2 * index] = 1.0f;
+// The recorded product state H^{hq}|b>: amplitude x is (-1)^{|x & b & hq|} v
+// where x agrees with b off hq (v = 2^{-|hq|/2}), 0 elsewhere; two amplitudes
+// per thread and 16-byte store.
+template <typename R>
+__global__ void k_set_product(R *amps, uint64_t npairs, uint64_t b, uint64_t hq, R v) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += stride) {
+        R a[2];
+        for (int e = 0; e < 2; e++) {
+            const uint64_t x = 2 * p + e;
+            a[e] = ((x ^ b) & ~hq) ? R(0) : ((__popcll(x & b & hq) & 1) ? -v : v);
+        }
+        if constexpr (sizeof(R) == 4)
+            reinterpret_cast<float4 *>(amps)[p] = make_float4(a[0], 0.f, a[1], 0.f);
+        else {
+            reinterpret_cast<double2 *>(amps)[2 * p] = make_double2(a[0], 0.0);
+            reinterpret_cast<double2 *>(amps)[2 * p + 1] = make_double2(a[1], 0.0);
+        }
+    }
 }
 
 unsigned grid_for(uint64_t units) {
@@ -244,16 +261,31 @@ void add_fixed(Fixed &f, int pos, int val) {
 sv_status init_zero_state(sv_state *h) {
     for (int q = 0; q < 64; q++) h->phys[q] = q;
     h->basis = 0;  // |0...0>, written when something first reads the state
+    h->basis_h = 0;
     return SV_OK;
 }
 
 sv_status materialize(sv_state *h) {
     if (h->basis < 0) return SV_OK;
-    SV_CUDA(cudaMemsetAsync(h->amps, 0, state_bytes(h), h->stream));
-    k_set_first<<<1, 1, 0, h->stream>>>(h->amps, h->dt == SV_C128, (uint64_t)h->basis);
+    const uint64_t npairs = (UINT64_C(1) << h->n) / 2;
+    const uint64_t hq = h->basis_h, b = (uint64_t)h->basis;
+    const double v = std::pow(2.0, -0.5 * __builtin_popcountll(hq));
+    if (h->n == 1) {  // one pair: the same kernel, one thread
+        if (h->dt == SV_C128)
+            k_set_product<double><<<1, 1, 0, h->stream>>>((double *)h->amps, 1, b, hq, v);
+        else
+            k_set_product<float><<<1, 1, 0, h->stream>>>((float *)h->amps, 1, b, hq, (float)v);
+    } else {
+        const unsigned grid = (unsigned)std::min<uint64_t>((npairs + 255) / 256, (uint64_t)h->sm_count * 8);
+        if (h->dt == SV_C128)
+            k_set_product<double><<<grid, 256, 0, h->stream>>>((double *)h->amps, npairs, b, hq, v);
+        else
+            k_set_product<float><<<grid, 256, 0, h->stream>>>((float *)h->amps, npairs, b, hq, (float)v);
+    }
     SV_CUDA(cudaGetLastError());
     note_launch();
     h->basis = -1;
+    h->basis_h = 0;
     return SV_OK;
 }
 

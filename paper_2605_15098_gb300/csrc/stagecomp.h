@@ -85,13 +85,17 @@ struct T2Args {
     int *err;
     const T2LayoutX *layx;  // per stage
     const T2Epilogue *epi;  // write-back offsets
-    // gen != 0: the state is the basis state |gen_basis> (physical index) and
-    // is generated in registers instead of read; gen_local is its index inside
-    // the tile that holds it; gen_hmask: tile bits of the leading Hadamards
-    // the generation includes (the programme is the pass's gen variant)
+    // gen != 0: the state is H on the physical qubits gen_ghmask (global
+    // qubits of the pass) and the tile bits gen_hmask applied to the basis
+    // state |gen_basis> (physical index), generated in registers instead of
+    // read; gen_local is the basis index's tile-local part; gen_val the
+    // magnitude of a nonzero amplitude before the pass's closing scale (the
+    // tile-bit Hadamards of the programme's own prefix are unnormalised and
+    // the scale holds their 2^(-1/2); the recorded ones are in gen_val)
     int gen, gen_local;
-    uint64_t gen_basis;
+    uint64_t gen_basis, gen_ghmask;
     uint32_t gen_hmask;
+    float gen_val;
 };
 
 // Fill the counts, pointers and geometry of a format-2 pass (not gen,

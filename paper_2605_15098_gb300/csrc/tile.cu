@@ -619,7 +619,10 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
             d.blocks = up[i].t3 ? reinterpret_cast<const float *>(dev + up[i].blocks) : nullptr;
             st = up[i].t3 ? t3_launch(h, t2[i], d, meta)
                           : t2_launch(h, g ? *t2[i].genv : t2[i], d, meta, gen);
-            if (st == SV_OK && gen >= 0) h->basis = -1;
+            if (st == SV_OK && gen >= 0) {
+                h->basis = -1;
+                h->basis_h = 0;
+            }
         } else {
             PassArgs a{};
             a.k = p.k;

@@ -332,16 +332,17 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, uint64_t
                     stage = w.w;
                     const Layout2 L(layout(stage), tid);
                     if (a.gen) {
-                        // the basis state |b>, after the leading Hadamards on the
-                        // tile bits in gen_hmask (unnormalised: the closing scale
-                        // holds their 2^(-1/2)), generated instead of read:
-                        // +-1 where the index agrees with b off those bits, with
-                        // the sign of the parity of b on them, 0 elsewhere
-                        const bool has = (a.gen_basis & a.gmask) == base;
+                        // the product state H^{hq}|b>, generated instead of
+                        // read: +-v where the index agrees with b off the
+                        // Hadamard qubits (global ones decide the whole tile),
+                        // with the sign of the parity of b on them, 0 elsewhere
+                        const bool has = ((a.gen_basis ^ base) & a.gmask & ~a.gen_ghmask) == 0;
+                        const uint32_t gneg = (uint32_t)__popcll(base & a.gen_basis & a.gen_ghmask) & 1u;
                         const uint32_t gl = (uint32_t)a.gen_local, hm = a.gen_hmask;
+                        const float v = a.gen_val;
                         auto amp = [&](uint32_t i) -> float {
                             if (!has || ((i ^ gl) & ~hm)) return 0.f;
-                            return (__popc(i & gl & hm) & 1) ? -1.f : 1.f;
+                            return ((__popc(i & gl & hm) ^ gneg) & 1) ? -v : v;
                         };
 #pragma unroll
                         for (int q = 0; q < kNP2; q++) {
@@ -845,11 +846,24 @@ sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
     T2Args a{};
     t2_fill_args(p, d, h->n, &a);
     if (gen_basis >= 0) {
+        // the programme's leading Hadamards P (unnormalised, tile bits)
+        // applied to the recorded product state H^{hq}|basis> (normalised
+        // Hadamards on the physical qubits of hq): on a qubit in both they
+        // give sqrt(2) I, so the generated state has Hadamards on P xor hq
+        // (its global ones decide presence and sign per tile) and magnitude
+        // 2^{(|P and hq| - |hq without P|) / 2}
         a.gen = 1;
         a.gen_basis = (uint64_t)gen_basis;
-        for (int s = 0; s < p.k; s++)
+        uint32_t hq_local = 0;
+        for (int s = 0; s < p.k; s++) {
             a.gen_local |= (int)((a.gen_basis >> p.slot_phys[s]) & 1) << s;
-        a.gen_hmask = p.gen_hmask;
+            if ((h->basis_h >> p.slot_phys[s]) & 1) hq_local |= 1u << s;
+        }
+        a.gen_hmask = p.gen_hmask ^ hq_local;
+        a.gen_ghmask = h->basis_h & p.gmask;
+        const int both = __builtin_popcount(p.gen_hmask & hq_local);
+        const int hq_only = __builtin_popcountll(h->basis_h) - both;
+        a.gen_val = (float)std::pow(2.0, 0.5 * (both - hq_only));
     }
     a.tables = reinterpret_cast<const float2 *>(h->t2_tables);
     a.err = h->t2_err;

@@ -42,17 +42,30 @@ def mixed_circuit(n, m, seed, kinds=tuple(range(11))):
     return C.gates(recs)
 
 
-def without_leading_x(g):
-    """The gate list the library plans when the state is a recorded basis
-    state: X gates whose qubit no earlier gate touches only flip the basis
-    index and are dropped."""
-    touched, keep = set(), []
+def fold_leading(g):
+    """The library's fold of a recorded basis state: while a qubit is
+    untouched, X flips its bit of the basis index (when it carries no
+    Hadamard) and H toggles it in the Hadamard mask; every other gate, and an
+    X on a Hadamard qubit, touches its qubits.  Identity qubit map.  Returns
+    (basis index, Hadamard mask, the rest of the list)."""
+    basis, hq, touched, rest = 0, 0, set(), []
     for r in g:
         kind, t, c = int(r["kind"]), int(r["target"]), int(r["control"])
-        if kind == C.X and t not in touched:
+        if t not in touched and kind == C.X and not (hq >> t) & 1:
+            basis ^= 1 << t
+            continue
+        if t not in touched and kind == C.H:
+            hq ^= 1 << t
             continue
         touched.add(t)
         if c >= 0:
             touched.add(c)
-        keep.append(r)
-    return C.gates(keep) if keep else C.gates([])
+        rest.append(r)
+    return basis, hq, (C.gates(rest) if rest else C.gates([]))
+
+
+def without_leading_x(g):
+    """The gate list the library plans when the state is a recorded basis
+    state: the leading X and H gates that only change the recorded state are
+    dropped (fold_leading)."""
+    return fold_leading(g)[2]

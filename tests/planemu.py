@@ -114,11 +114,13 @@ def _expi32(u):
     return np.exp(2j * np.pi * ((u & MASK32) / 2.0 ** 32))
 
 
-def run_t2_pass(state, p, t2=None, gen_basis=None):
+def run_t2_pass(state, p, t2=None, gen_basis=None, gen_h=0):
     """Execute a register-stage pass.  `t2` defaults to the pass's programme;
-    with `gen_basis` (a physical basis index) the pass starts from that basis
-    state and generates its tiles instead of reading them (the programme is
-    then the pass's generated-state variant, `t2gen`)."""
+    with `gen_basis` (a physical basis index) the pass starts from the product
+    state H^{gen_h}|gen_basis> (H on the physical qubits of the mask gen_h)
+    and generates its tiles instead of reading them (the programme is then the
+    pass's generated-state variant, `t2gen`, whose own leading Hadamards on
+    tile bits are unnormalised: its closing scale holds their 2^(-1/2))."""
     t2 = t2 if t2 is not None else p["t2"]
     fmt = t2.get("format", 1)
     k = p["k"]
@@ -136,14 +138,23 @@ def run_t2_pass(state, p, t2=None, gen_basis=None):
         idx = tile_index(p, base)
         if gen_basis is None:
             t = state[idx].copy()
-        else:  # the basis state after the leading Hadamards, unnormalised
-            hm = t2["gen_hmask"]
-            gl = 0
+        else:  # the product state after the leading Hadamards
+            # the programme's unnormalised leading Hadamards P on the recorded
+            # H^{gen_h}|gen_basis>: H_unnorm H_norm = sqrt(2) I on a qubit in both
+            P = t2["gen_hmask"]
+            gl, hq_local = 0, 0
             for s_, q in enumerate(p["slot_phys"]):
                 gl |= ((gen_basis >> q) & 1) << s_
-            has = (gen_basis & p["gmask"]) == base
-            par = np.array([bin(int(i) & gl & hm).count("1") & 1 for i in loc])
-            t = np.where(((loc ^ gl) & ~hm) == 0, np.where(par == 1, -1.0, 1.0), 0.0).astype(complex)
+                if (gen_h >> q) & 1:
+                    hq_local |= 1 << s_
+            hm = P ^ hq_local
+            ghm = gen_h & p["gmask"]
+            has = ((gen_basis ^ base) & p["gmask"] & ~ghm) == 0
+            gneg = bin(base & gen_basis & ghm).count("1") & 1
+            both = bin(P & hq_local).count("1")
+            v = 2.0 ** (0.5 * (both - (bin(gen_h).count("1") - both)))
+            par = np.array([(bin(int(i) & gl & hm).count("1") + gneg) & 1 for i in loc])
+            t = np.where(((loc ^ gl) & ~hm) == 0, np.where(par == 1, -v, v), 0.0).astype(complex)
             if not has:
                 t[:] = 0
         lin = [0] * (16 * max(t2["nruns"], 1))
@@ -295,12 +306,20 @@ def remap(state, pairs):
     return out
 
 
-def run_plan(n, plan, use_gen=True):
-    """Run the exported plan from |0...0>.  With `use_gen` the first pass runs
-    its generated-state variant (`t2gen`, as the library does from a recorded
-    basis state) when it has one; otherwise every pass reads its state."""
-    state = np.zeros(1 << n, dtype=np.complex128)
-    state[0] = 1.0
+def product_state(n, basis, hq):
+    """H^{hq}|basis> (H on the physical qubits of the mask hq)."""
+    x = np.arange(1 << n)
+    par = np.array([bin(int(i) & basis & hq).count("1") & 1 for i in x])
+    v = 2.0 ** (-0.5 * bin(hq).count("1"))
+    return np.where(((x ^ basis) & ~hq) == 0, np.where(par == 1, -v, v), 0.0).astype(complex)
+
+
+def run_plan(n, plan, use_gen=True, basis=0, hq=0):
+    """Run the exported plan from the product state H^{hq}|basis> (default
+    |0...0>).  With `use_gen` the first pass runs its generated-state variant
+    (`t2gen`, as the library does from a recorded state) when it has one;
+    otherwise every pass reads its state."""
+    state = product_state(n, basis, hq)
     first = True
     for p in plan["passes"]:
         if p.get("remap_before"):
@@ -309,7 +328,7 @@ def run_plan(n, plan, use_gen=True):
             continue
         if p["kernel"] in ("t2", "t3"):
             if first and use_gen and "t2gen" in p:
-                run_t2_pass(state, p, p["t2gen"], gen_basis=0)
+                run_t2_pass(state, p, p["t2gen"], gen_basis=basis, gen_h=hq)
             else:
                 run_t2_pass(state, p)
         else:

@@ -1,11 +1,12 @@
-"""A reset records |0...0> without writing it; X gates that come first on
-their qubit only flip the recorded basis index, and the first register-stage
-pass generates the state instead of reading it (GPU).  Checked against the
-FP64 oracle, including what the adopted device buffer holds."""
+"""A reset records |0...0> without writing it; X and H gates that come first
+on their qubit only change the recorded product state H^{hq}|b> (X flips a
+bit of b, H toggles a qubit of hq), and the first register-stage pass
+generates the state instead of reading it (GPU).  Checked against the FP64
+oracle, including what the adopted device buffer holds."""
 import numpy as np
 import pytest
 
-from gen import mixed_circuit, without_leading_x
+from gen import fold_leading, mixed_circuit, without_leading_x
 from paper_2605_15098_gb300 import circuits as C
 
 pytestmark = pytest.mark.gpu
@@ -89,28 +90,25 @@ def test_qpe_first_pass_generates(sv, orc):
 
 @pytest.mark.parametrize("n,seed", [(14, 1), (16, 2), (19, 3)])
 def test_leading_hadamards_are_generated(sv, orc, n, seed):
-    """The first register-stage pass generates |b> after the programme's
-    leading Hadamards (signs where b has a 1 under an H) instead of applying
-    them; a later pass with the same leading Hadamards applies them."""
+    """Leading Hadamards (on local and global qubits alike) fold into the
+    recorded state and the first pass generates H^{hq}|b>; the same list on a
+    state that is not a recorded one applies them."""
     rng = np.random.default_rng(seed)
     xs = [int(q) for q in rng.choice(n, size=n // 2, replace=False)]
     hs = [int(q) for q in rng.choice(n, size=n - 3, replace=False)]
     body = mixed_circuit(n, 60, seed + 40, kinds=(0, 1, 2, 3, 4, 5, 6, 7, 9, 10))  # no CU
     g = C.gates([C.x(q) for q in xs] + [C.h(q) for q in hs] + list(body) + [C.h(q) for q in hs])
     ref = orc.run(n, g)
-    plan = sv.sv_plan_export(n, sv.SV_C64, without_leading_x(g), sv.make_config(sv.SV_MODE_PARTITIONED))
-    first = plan["passes"][0]
-    assert first["kernel"] == "t2"
-    # the generated-state variant of the first pass includes the leading
-    # Hadamards (gen_hmask) and carries fewer Hadamard steps than the variant
-    # that reads its state
-    gen = first["t2gen"]
-    assert bin(gen["gen_hmask"]).count("1") >= 4
-    n_h = lambda t2: sum(1 for i in t2["ins"] if i["op"] in (2, 9))  # T2_H, T2_HPH (tileprog.h)
-    assert n_h(gen) <= n_h(first["t2"]) - bin(gen["gen_hmask"]).count("1")
+    basis, hq, rest = fold_leading(g)
+    hs_mask = sum(1 << q for q in hs)
+    assert hq & hs_mask == hs_mask and len(rest) <= len(g) - len(xs) - len(hs)
     with sv.State(n, sv.SV_C64) as s:
+        sv.sv_profile(s.h, True)
         s.apply(g, sv.make_config(sv.SV_MODE_PARTITIONED))
+        recs = sv.sv_profile_read(s.h)
         got = s.amplitudes()
+    tiles = [r for r in recs if r["kind"] == sv.SV_KERNEL_TILE]
+    assert tiles and tiles[0]["bytes"] == 8 * (1 << n)  # generated: written, not read
     assert abs(np.vdot(ref, got.astype(np.complex128))) ** 2 >= 1.0 - 1e-6
     # the same list on a state that is not a basis state: the Hadamards run
     with sv.State(n, sv.SV_C64) as s:
@@ -119,3 +117,28 @@ def test_leading_hadamards_are_generated(sv, orc, n, seed):
         got2 = s.amplitudes()
     ref2 = orc.run(n, np.concatenate([C.gates([C.h(0)]), g]))
     assert abs(np.vdot(ref2, got2.astype(np.complex128))) ** 2 >= 1.0 - 1e-6
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("n", [5, 15, 18])
+def test_recorded_product_state(sv, orc, n, dt):
+    """Prefixes of X and H only (H on every qubit, H H on one, X then H, H
+    then X, which stays a gate): the recorded state, written by the read-out
+    or generated by a following pass, equals the oracle's; a prefix that
+    folds entirely leaves no pass to run."""
+    pre = [C.h(q) for q in range(n)] + [C.h(2), C.x(3)] + [C.x(1)]
+    g_only = C.gates([C.x(0), C.h(0)] + pre[1:])
+    body = mixed_circuit(n, 40, n + 3 * dt)
+    for g in (g_only, C.gates(list(g_only) + list(body))):
+        ref = orc.run(n, g)
+        for mode in (sv.SV_MODE_PARTITIONED, sv.SV_MODE_FUSED) if dt == 0 else (sv.SV_MODE_PARTITIONED,):
+            with sv.State(n, dt) as s:
+                s.apply(g, sv.make_config(mode))
+                st = s.stats()
+                got = s.amplitudes()
+            assert np.max(np.abs(got - ref)) <= tol(sv, dt)
+            if len(g) == len(g_only):
+                # every gate folds but the X on qubit 3, which follows its H
+                assert st["passes"] >= 1 and st["gates"] == len(g)
+
+

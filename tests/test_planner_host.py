@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import planemu
-from gen import mixed_circuit
+from gen import fold_leading, mixed_circuit
 from paper_2605_15098_gb300 import build as B
 from paper_2605_15098_gb300 import circuits as C
 
@@ -324,3 +324,26 @@ def test_paper_swap_count_falls_with_block_size(sv):
     assert all(a >= b for a, b in zip(counts, counts[1:])) and counts[0] > counts[-1]
     gather = sv.sv_plan_export(n, sv.SV_C64, g, sv.make_config(sv.SV_MODE_PARTITIONED))
     assert len(gather["passes"]) * 4 < counts[-1]
+
+
+@pytest.mark.parametrize("n,seed,tile,chunk", [(16, 5, 0, 5), (16, 5, 14, 7), (18, 1, 0, 7), (20, 3, 0, 4)])
+def test_generated_product_state(sv, orc, n, seed, tile, chunk):
+    """After the fold of leading X and H gates, the first pass generates
+    H^{hq}|b> (Hadamards on global qubits included) and its programme may
+    still begin with Hadamards on qubits that carry a folded one (QPE's first
+    inverse-QFT step after zero-phase controlled phases): those cancel.  The
+    generated-state variant, emulated from the recorded state, matches the
+    oracle on the whole list."""
+    g, _, _ = C.qpe(n, seed=seed)
+    mixed = C.gates([C.h(q) for q in range(0, n, 2)] + [C.x(1), C.h(1), C.x(3)] +
+                    list(mixed_circuit(n, 40, seed, kinds=(0, 1, 2, 3, 4, 5, 6, 7, 9, 10))) +
+                    [C.h(0), C.h(2)])
+    cfg = sv.make_config(sv.SV_MODE_PARTITIONED, tile_qubits=tile, chunk_qubits=chunk)
+    for circ in (g, mixed):
+        ref = orc.run(n, circ)
+        basis, hq, rest = fold_leading(circ)
+        assert hq and len(rest) < len(circ)
+        plan = sv.sv_plan_export(n, sv.SV_C64, rest, cfg)
+        assert "t2gen" in plan["passes"][0]
+        got = planemu.run_plan(n, plan, use_gen=True, basis=basis, hq=hq)
+        assert float(np.max(np.abs(got - ref))) <= 2e-5
