@@ -6,7 +6,9 @@ own shared object, built from ``sv_oracle.c`` with gcc, and never touches the
 CUDA library.
 
 Functions follow the paper's definitions (arxiv 2605.15098):
-``apply`` runs Algorithm 1 gate by gate with the control rule of Sec. III-A,
+``apply`` runs Algorithm 1 gate by gate with the control rule of Sec. III-A
+(taken to a set of controls for MCU), a general two-qubit unitary U2Q and a
+collapsing MEASURE (``apply_measured`` also returns the outcomes),
 ``marginal`` / ``argmax`` / ``sample`` read out the measured outcome of
 Sec. IV-A.  Gate records are NumPy structured arrays with the byte layout of
 the library's gate record (96 bytes, see ``GATE_DTYPE``).
@@ -71,13 +73,14 @@ def load(mutation: int = 0) -> ctypes.CDLL:
         u64, i32, dp = ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p
         lib.or_init.argtypes = [i32, dp]
         lib.or_apply.argtypes = [i32, dp, dp, u64]
+        lib.or_apply_measured.argtypes = [i32, dp, dp, u64, dp]
         lib.or_marginal.argtypes = [i32, dp, u64, dp]
         lib.or_argmax.argtypes = [dp, u64, dp, dp]
         lib.or_cdf.argtypes = [dp, u64, dp]
         lib.or_sample.argtypes = [dp, u64, dp, u64, dp, dp]
         lib.or_num_threads.restype = i32
         lib.or_set_threads.argtypes = [i32]
-        for f in (lib.or_init, lib.or_apply, lib.or_marginal, lib.or_argmax,
+        for f in (lib.or_init, lib.or_apply, lib.or_apply_measured, lib.or_marginal, lib.or_argmax,
                   lib.or_cdf, lib.or_sample):
             f.restype = i32
         _libs[mutation] = lib
@@ -113,6 +116,18 @@ def apply(n: int, psi: np.ndarray, gates: np.ndarray, mutation: int = 0) -> np.n
     if rc:
         raise ValueError(f"oracle rejected gate list (code {rc})")
     return psi
+
+
+def apply_measured(n: int, psi: np.ndarray, gates: np.ndarray, mutation: int = 0) -> np.ndarray:
+    """Apply the list in place; returns the outcomes of its MEASURE gates, in order."""
+    assert psi.dtype == np.complex128 and psi.flags.c_contiguous and psi.size == 1 << n
+    g = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    out = np.zeros(max(1, g.size), dtype=np.uint8)
+    rc = load(mutation).or_apply_measured(n, _ptr(psi), _ptr(g) if g.size else None, g.size, _ptr(out))
+    if rc:
+        raise ValueError(f"oracle rejected gate list (code {rc})")
+    nm = int(np.sum(g["kind"] == 14)) if g.size else 0
+    return out[:nm].copy()
 
 
 def run(n: int, gates: np.ndarray, mutation: int = 0) -> np.ndarray:

@@ -41,6 +41,24 @@
  *    PK/CPK = P/CP with phi = 2*pi*k / 2^j, the integer k reduced mod 2^j
  *             first (Eq. 3: U^a = P(2*pi*2^-n*a)).
  *
+ * The general gate set beyond the paper's circuits (its control rule taken
+ * to a set of controls, a general two-qubit unitary, and a measurement that
+ * collapses the state):
+ *    MCU  = explicit 2x2 U on the target where EVERY qubit of the control
+ *           mask (the record's num field, a bit per qubit) is 1: Algorithm 1's
+ *           inner iteration j runs only when all those bits of j are 1.
+ *    U2Q  = explicit 4x4 unitary on the qubit pair (a = target, b = control):
+ *           the amplitudes of the four indices that agree off bits a and b,
+ *           ordered by k = bit_a + 2 bit_b, are multiplied by the matrix.  Its
+ *           rows 0..3 are the p[0..7] (re/im interleaved) of this record and
+ *           of the next three records, which have kind MAT.
+ *    MEASURE = projective measurement of the target with the caller's
+ *           uniform u = p[0] in [0,1): p0 and p1 are the sums of |amp|^2 over
+ *           the indices with the target bit 0 and 1 (index order); the
+ *           outcome is the smallest i with C_i > u C_last for C = (p0,
+ *           p0 + p1); the amplitudes of the other outcome become 0 and the
+ *           kept ones are divided by sqrt(p_outcome).
+ *
  * Sampling order (the paper is silent): the marginal vector is cut into
  * blocks of 1024 consecutive outcomes; each block is summed in index order,
  * the running total over blocks is kept in block order, and the inclusive
@@ -73,7 +91,8 @@ typedef struct {
 
 enum {
     OR_X = 0, OR_H = 1, OR_P = 2, OR_CP = 3, OR_CZ = 4, OR_SWAP = 5,
-    OR_U3 = 6, OR_U = 7, OR_CU = 8, OR_PK = 9, OR_CPK = 10
+    OR_U3 = 6, OR_U = 7, OR_CU = 8, OR_PK = 9, OR_CPK = 10,
+    OR_MCU = 11, OR_U2Q = 12, OR_MAT = 13, OR_MEASURE = 14
 };
 
 #ifndef OR_MUTATION
@@ -147,6 +166,7 @@ static int build_matrix(const or_gate *g, mat2 *u) {
     }
     case OR_U:
     case OR_CU:
+    case OR_MCU:
         for (int e = 0; e < 4; e++) {
             u->re[e] = g->p[2 * e];
             u->im[e] = g->p[2 * e + 1];
@@ -165,8 +185,9 @@ static int has_control(int kind) {
     return kind == OR_CP || kind == OR_CZ || kind == OR_CU || kind == OR_CPK;
 }
 
-/* Algorithm 1 (ApplyGate) with the control rule of Sec. III-A. */
-static void apply_gate_alg1(int n, double *S, const mat2 *u, int t, int ctrl) {
+/* Algorithm 1 (ApplyGate) with the control rule of Sec. III-A, the controls
+ * given as a mask of qubits that must all be 1 (0: none). */
+static void apply_gate_alg1(int n, double *S, const mat2 *u, int t, uint64_t cmask) {
     const uint64_t N = (uint64_t)1 << n;
     const uint64_t st = (uint64_t)1 << t;
 #if OR_MUTATION == 5
@@ -184,7 +205,11 @@ static void apply_gate_alg1(int n, double *S, const mat2 *u, int t, int ctrl) {
             uint64_t i = (uint64_t)io * st2;
             uint64_t j = i + (uint64_t)jo;
             if (j + st >= N) continue;            /* only reachable with a planted mistake */
-            if (ctrl >= 0 && !((j >> ctrl) & 1u)) continue;
+#if OR_MUTATION == 6
+            if (cmask && !(j & cmask)) continue;        /* planted: any control instead of all */
+#else
+            if ((j & cmask) != cmask) continue;
+#endif
             double ar = S[2 * j], ai = S[2 * j + 1];
             double br = S[2 * (j + st)], bi = S[2 * (j + st) + 1];
             /* S[j] = U11 a + U12 b ; S[j+2^t] = U21 a + U22 b */
@@ -215,6 +240,79 @@ static void apply_swap(int n, double *S, int a, int b) {
     }
 }
 
+/* U2Q on (a, b): for every index x with bits a and b both 0, the four
+ * amplitudes x + k_a 2^a + k_b 2^b (k = k_a + 2 k_b) are replaced by
+ * M times them; M row-major, re/im interleaved, 32 doubles. */
+static void apply_u2q(int n, double *S, const double *M, int a, int b) {
+    const uint64_t N = (uint64_t)1 << n;
+    const uint64_t ma = (uint64_t)1 << a, mb = (uint64_t)1 << b;
+    int64_t x;
+#pragma omp parallel for schedule(static) if (N >= (1u << 16))
+    for (x = 0; x < (int64_t)N; x++) {
+        const uint64_t ux = (uint64_t)x;
+        if (ux & (ma | mb)) continue;
+        uint64_t idx[4];
+        idx[0] = ux;
+        idx[1] = ux | ma;
+        idx[2] = ux | mb;
+        idx[3] = ux | ma | mb;
+        double vr[4], vi[4];
+        for (int k = 0; k < 4; k++) {
+            vr[k] = S[2 * idx[k]];
+            vi[k] = S[2 * idx[k] + 1];
+        }
+        for (int r = 0; r < 4; r++) {
+            double yr = 0.0, yi = 0.0;
+            for (int k = 0; k < 4; k++) {
+#if OR_MUTATION == 7
+                const double mr = M[8 * k + 2 * r], mi = M[8 * k + 2 * r + 1]; /* planted: transposed */
+#else
+                const double mr = M[8 * r + 2 * k], mi = M[8 * r + 2 * k + 1];
+#endif
+                yr += mr * vr[k] - mi * vi[k];
+                yi += mr * vi[k] + mi * vr[k];
+            }
+            S[2 * idx[r]] = yr;
+            S[2 * idx[r] + 1] = yi;
+        }
+    }
+}
+
+/* Projective measurement of qubit t with uniform u (see the header);
+ * returns the outcome (0 or 1), or -1 when the state has zero norm. */
+static int apply_measure(int n, double *S, int t, double u) {
+    const uint64_t N = (uint64_t)1 << n;
+    const uint64_t mt = (uint64_t)1 << t;
+    double p0 = 0.0, p1 = 0.0;
+    for (uint64_t x = 0; x < N; x++) {
+        const double q = S[2 * x] * S[2 * x] + S[2 * x + 1] * S[2 * x + 1];
+        if (x & mt) p1 += q;
+        else p0 += q;
+    }
+    const double last = p0 + p1;
+    if (!(last > 0.0)) return -1;
+    const int out = (p0 > u * last) ? 0 : 1;
+    const double keep = out ? p1 : p0;
+#if OR_MUTATION == 8
+    const double sc = 1.0;                  /* planted: no renormalisation */
+#else
+    const double sc = 1.0 / sqrt(keep);
+#endif
+    int64_t x;
+#pragma omp parallel for schedule(static) if (N >= (1u << 16))
+    for (x = 0; x < (int64_t)N; x++) {
+        const int bit = ((uint64_t)x & mt) ? 1 : 0;
+        if (bit == out) {
+            S[2 * x] *= sc;
+            S[2 * x + 1] *= sc;
+        } else {
+            S[2 * x] = 0.0;
+            S[2 * x + 1] = 0.0;
+        }
+    }
+    return out;
+}
+
 int or_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();
@@ -240,34 +338,73 @@ int or_init(int n, double *psi) {
     return 0;
 }
 
-/* Validate one gate against n; 0 if fine. */
+/* Validate one gate against n; 0 if fine.  A U2Q must be followed by three
+ * MAT records and a MAT record may appear only there (checked by the list
+ * walk in or_apply_measured). */
 static int check_gate(int n, const or_gate *g) {
-    if (g->kind < OR_X || g->kind > OR_CPK) return -1;
+    if (g->kind < OR_X || g->kind > OR_MEASURE) return -1;
     if (g->target < 0 || g->target >= n) return -1;
-    if (has_control(g->kind) || g->kind == OR_SWAP) {
+    if (has_control(g->kind) || g->kind == OR_SWAP || g->kind == OR_U2Q) {
         if (g->control < 0 || g->control >= n || g->control == g->target) return -1;
     }
     if ((g->kind == OR_PK || g->kind == OR_CPK) && (g->log2den < 0 || g->log2den > 64)) return -1;
+    if (g->kind == OR_MCU) {
+        const uint64_t cm = (uint64_t)g->num;
+        if (!cm || (n < 64 && (cm >> n)) || ((cm >> g->target) & 1u)) return -1;
+    }
+    if (g->kind == OR_MEASURE && !(g->p[0] >= 0.0 && g->p[0] < 1.0)) return -1;
     return 0;
 }
 
-/* Apply m gates in list order.  Returns 0, or -(index+1) of the first bad gate
- * (nothing is applied when any gate is invalid). */
-int or_apply(int n, double *psi, const or_gate *gates, uint64_t m) {
+/* Apply m gates in list order; the outcome of each MEASURE, in list order,
+ * goes to outcomes[] (optional).  Returns 0, or -(index+1) of the first bad
+ * gate (nothing is applied when any gate is invalid), or -(m+2) when a
+ * measurement meets a state of zero norm. */
+int or_apply_measured(int n, double *psi, const or_gate *gates, uint64_t m, uint8_t *outcomes) {
     if (n < 1 || n > 40 || !psi || (m && !gates)) return -1;
-    for (uint64_t e = 0; e < m; e++)
+    for (uint64_t e = 0; e < m; e++) {
         if (check_gate(n, &gates[e])) return -(int)(e + 1);
+        if (gates[e].kind == OR_MAT) return -(int)(e + 1);
+        if (gates[e].kind == OR_U2Q) {
+            for (uint64_t k = 1; k <= 3; k++)
+                if (e + k >= m || gates[e + k].kind != OR_MAT) return -(int)(e + 1);
+            e += 3;
+        }
+    }
+    uint64_t nm = 0;
     for (uint64_t e = 0; e < m; e++) {
         const or_gate *g = &gates[e];
         if (g->kind == OR_SWAP) {
             apply_swap(n, psi, g->target, g->control);
             continue;
         }
+        if (g->kind == OR_U2Q) {
+            double M[32];
+            for (int r = 0; r < 4; r++)
+                for (int c = 0; c < 8; c++) M[8 * r + c] = gates[e + r].p[c];
+            apply_u2q(n, psi, M, g->target, g->control);
+            e += 3;
+            continue;
+        }
+        if (g->kind == OR_MEASURE) {
+            const int out = apply_measure(n, psi, g->target, g->p[0]);
+            if (out < 0) return -(int)(m + 2);
+            if (outcomes) outcomes[nm] = (uint8_t)out;
+            nm++;
+            continue;
+        }
         mat2 u;
         build_matrix(g, &u);
-        apply_gate_alg1(n, psi, &u, g->target, has_control(g->kind) ? g->control : -1);
+        uint64_t cmask = 0;
+        if (has_control(g->kind)) cmask = (uint64_t)1 << g->control;
+        if (g->kind == OR_MCU) cmask = (uint64_t)g->num;
+        apply_gate_alg1(n, psi, &u, g->target, cmask);
     }
     return 0;
+}
+
+int or_apply(int n, double *psi, const or_gate *gates, uint64_t m) {
+    return or_apply_measured(n, psi, gates, m, NULL);
 }
 
 /* Marginal probabilities over the qubits in mask, renormalised by their total.

@@ -43,8 +43,9 @@ GATE_DTYPE = np.dtype(
 )
 assert GATE_DTYPE.itemsize == 96
 
-X, H, P, CP, CZ, SWAP, U3, U, CU, PK, CPK = range(11)
-KIND_NAMES = ["X", "H", "P", "CP", "CZ", "SWAP", "U3", "U", "CU", "PK", "CPK"]
+X, H, P, CP, CZ, SWAP, U3, U, CU, PK, CPK, MCU, U2Q, MAT, MEASURE = range(15)
+KIND_NAMES = ["X", "H", "P", "CP", "CZ", "SWAP", "U3", "U", "CU", "PK", "CPK", "MCU", "U2Q", "MAT",
+              "MEASURE"]
 DIAGONAL_KINDS = (P, CP, CZ, PK, CPK)
 
 DEFAULT_SEED = 2605150980
@@ -128,6 +129,32 @@ def pk(q, k, j):
 def cpk(c, t, k, j):
     """CP(2*pi*k/2^j) with control c, target t."""
     return _rec(CPK, t, c, num=int(k), log2den=int(j))
+
+
+def mcu(controls, t, m):
+    """U (2x2) on t where every qubit in `controls` is 1: the control mask in num."""
+    r = list(u(t, m))
+    r[0], r[2], r[4] = MCU, -1, int(sum(1 << int(c) for c in controls))
+    return tuple(r)
+
+
+def u2q(a, b, m4):
+    """Four records: a 4x4 unitary on the pair (a, b), basis index k = bit_a +
+    2 bit_b; rows 0..3 of the matrix in the p of this record (kind U2Q) and
+    of three continuation records (kind MAT)."""
+    m4 = np.asarray(m4, dtype=np.complex128).reshape(4, 4)
+    out = []
+    for r in range(4):
+        flat = []
+        for e in m4[r]:
+            flat += [float(e.real), float(e.imag)]
+        out.append(_rec(U2Q if r == 0 else MAT, a, b, p=flat))
+    return out
+
+
+def measure(q, uval):
+    """Projective measurement of q with the caller's uniform uval in [0, 1)."""
+    return _rec(MEASURE, q, p=(float(uval),))
 
 
 # ---- workloads ------------------------------------------------------------

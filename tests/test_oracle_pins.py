@@ -140,7 +140,32 @@ def test_rejects_bad_gates(orc):
         orc.run(3, C.gates([C.swap(0, 0)]))
 
 
-@pytest.mark.parametrize("mutation", [1, 2, 3, 4, 5])
+def test_rejects_bad_general_gates(orc):
+    """A MAT record outside a U2Q, a U2Q without its three rows, a control
+    mask that holds the target or is empty, and u outside [0, 1)."""
+    m4 = np.eye(4)
+    bad_lists = [
+        C.gates(C.u2q(0, 1, m4)[1:2]),
+        C.gates(C.u2q(0, 1, m4)[:3]),
+        C.gates([C.mcu([0, 2], 2, np.eye(2))]),
+        C.gates([C.mcu([], 1, np.eye(2))]),
+        C.gates([C.measure(0, 1.0)]),
+        C.gates([C.measure(0, -0.1)]),
+    ]
+    for g in bad_lists:
+        with pytest.raises(ValueError):
+            orc.run(3, g)
+
+
+def test_measure_outcomes_reported(orc):
+    """Outcomes come back in list order: |1> on qubit 1 always measures 1,
+    |0> on qubit 0 always 0, and H then u = 0.7 gives 1."""
+    g = C.gates([C.x(1), C.measure(1, 0.0), C.measure(0, 0.99), C.h(2), C.measure(2, 0.7)])
+    psi = orc.init(3)
+    assert list(orc.apply_measured(3, psi, g)) == [1, 0, 1]
+
+
+@pytest.mark.parametrize("mutation", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_planted_mistake_is_caught(orc, mutation):
     """A build of the oracle with a planted mistake must fail at least one pin."""
     orc.build(mutation)
