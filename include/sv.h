@@ -69,15 +69,39 @@ typedef enum {
  *           reduced modulo 2^j as an integer, so the phase is exact (Eq. 3,
  *           U^a = P(2 pi 2^-n a))
  *   SV_CPK  SV_PK on `target` when bit `control` is 1
+ *
+ * The general gate set (the control rule of Sec. III-A taken to a set of
+ * controls, a general two-qubit unitary, and a collapsing measurement).  In
+ * the partitioned modes each of them is its own step between tile passes,
+ * run by the per-gate kernels:
+ *   SV_MCU      the explicit 2x2 of p (as SV_U) on `target` where EVERY qubit
+ *               of the mask `num` (bit q = qubit q; nonzero, target not in it)
+ *               is 1; `control` is -1
+ *   SV_U2Q      a 4x4 unitary M on the qubits a = `target`, b = `control`: the
+ *               four amplitudes that agree off a and b, ordered by
+ *               k = bit_a + 2 bit_b, are multiplied by M.  Row r of M (4
+ *               complex entries, re/im interleaved) is the p of record r: this
+ *               record holds row 0 and the next three records, of kind
+ *               SV_MAT with the same target and control, rows 1..3
+ *   SV_MAT      a row of the preceding SV_U2Q (valid only there)
+ *   SV_MEASURE  projective measurement of `target` with the caller's uniform
+ *               u = p[0] in [0,1): p0 and p1 are the FP64 sums of |amp|^2 over
+ *               the amplitudes with that qubit 0 and 1; the outcome is the
+ *               smallest i with C_i > u * C_last for C = (p0, p0 + p1) (as
+ *               sv_sample); the other half of the state becomes 0 and the kept
+ *               half is divided by sqrt(p_outcome).  Outcomes are read with
+ *               sv_last_measurements.
  */
 enum {
     SV_X = 0, SV_H = 1, SV_P = 2, SV_CP = 3, SV_CZ = 4, SV_SWAP = 5,
-    SV_U3 = 6, SV_U = 7, SV_CU = 8, SV_PK = 9, SV_CPK = 10
+    SV_U3 = 6, SV_U = 7, SV_CU = 8, SV_PK = 9, SV_CPK = 10,
+    SV_MCU = 11, SV_U2Q = 12, SV_MAT = 13, SV_MEASURE = 14
 };
 
 /* One gate, 96 bytes.  `control` is the control qubit of CP/CZ/CU/CPK and
- * the second qubit of SWAP; it must differ from `target` and is ignored
- * (set it to -1) for the other kinds.  `reserved` must be 0. */
+ * the second qubit of SWAP, U2Q and MAT; it must differ from `target` and is
+ * ignored (set it to -1) for the other kinds.  `num` is PK/CPK's numerator
+ * and MCU's control mask.  `reserved` must be 0. */
 typedef struct sv_gate {
     int32_t kind;
     int32_t target;
@@ -216,6 +240,14 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *host_gates, size_t m,
 
 /* Counters of the last sv_apply_circuit. */
 sv_status sv_last_stats(sv_handle h, sv_stats *out);
+
+/* Outcomes (0 or 1, in list order) of the SV_MEASURE gates of the last
+ * sv_apply_circuit: the first min(cap, count) go to host_out (may be NULL
+ * when cap is 0) and their number to *count.  Synchronises the handle's
+ * stream.  The outcome rule is the one of Sec. IV-A's measured bitstring
+ * (inverse CDF over the qubit's two values with the caller's u), applied
+ * one qubit at a time with collapse.  Errors: SV_ERR_ARG, SV_ERR_CUDA. */
+sv_status sv_last_measurements(sv_handle h, uint8_t *host_out, size_t cap, size_t *count);
 
 /* ---- batches: many independent circuits in one launch ------------------ */
 

@@ -118,7 +118,11 @@ void sv::fold_basis_prefix(sv_state *h, std::vector<sv_gate> &g) {
             continue;
         }
         touched[a.target] = true;
-        if (is_controlled_kind(a.kind) || a.kind == SV_SWAP) touched[a.control] = true;
+        if (is_controlled_kind(a.kind) || a.kind == SV_SWAP || a.kind == SV_U2Q || a.kind == SV_MAT)
+            touched[a.control] = true;
+        if (a.kind == SV_MCU)
+            for (int q = 0; q < 64; q++)
+                if (((uint64_t)a.num >> q) & 1) touched[q] = true;
         out.push_back(a);
     }
     g.swap(out);
@@ -202,19 +206,38 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *host_gates, size_t m, con
         return fail(SV_ERR_ARG, "tile_qubits / chunk_qubits outside 0..14");
     if (c.fuse_qubits != 0 && c.fuse_qubits != 5)
         return fail(SV_ERR_ARG, "fuse_qubits must be 0 or 5");
-    for (size_t i = 0; i < m; i++) {
-        std::string why = check_gate(h->n, host_gates[i]);
-        if (!why.empty()) return fail(SV_ERR_ARG, "gate %zu: %s", i, why.c_str());
+    {
+        const std::string why = check_list(h->n, host_gates, m);
+        if (!why.empty()) return fail(SV_ERR_ARG, "%s", why.c_str());
     }
     h->stats = sv_stats{};
     h->stats.gates = (int32_t)m;
     h->launch_index = 0;
+    h->nmeas = 0;
     int mode = c.mode;
     if (mode == SV_MODE_AUTO) mode = h->n >= 16 ? SV_MODE_PARTITIONED : SV_MODE_PERGATE;
     sv_status st = SV_OK;
     if (mode == SV_MODE_PERGATE) {
         st = resolve_norm(h);
         for (size_t i = 0; i < m && st == SV_OK; i++) {
+            if (is_general_kind(host_gates[i].kind)) {  // the general gate set, physical qubits
+                const int nr = general_records(host_gates[i].kind);
+                sv_gate g4[4];
+                for (int r = 0; r < nr; r++) {
+                    g4[r] = host_gates[i + r];
+                    g4[r].target = h->phys[g4[r].target];
+                    if (g4[r].control >= 0) g4[r].control = h->phys[g4[r].control];
+                }
+                if (g4[0].kind == SV_MCU) {
+                    uint64_t pm = 0;
+                    for (int q = 0; q < h->n; q++)
+                        if (((uint64_t)g4[0].num >> q) & 1) pm |= UINT64_C(1) << h->phys[q];
+                    g4[0].num = (int64_t)pm;
+                }
+                st = general_apply(h, g4);
+                i += nr - 1;
+                continue;
+            }
             sv_gate g = host_gates[i];
             g.target = h->phys[g.target];
             if (is_controlled_kind(g.kind) || g.kind == SV_SWAP) g.control = h->phys[g.control];
@@ -324,6 +347,16 @@ sv_status sv_copy_in(sv_handle h, const void *host_amps) {
     h->norm_pending = false;
     h->basis = -1;
     h->basis_h = 0;
+    return SV_OK;
+}
+
+sv_status sv_last_measurements(sv_handle h, uint8_t *host_out, size_t cap, size_t *count) {
+    clear_error();
+    if (!h || !count || (cap && !host_out)) return fail(SV_ERR_ARG, "NULL argument");
+    *count = h->nmeas;
+    const size_t k = std::min(cap, h->nmeas);
+    if (k) SV_CUDA(cudaMemcpyAsync(host_out, h->meas_dev, k, cudaMemcpyDeviceToHost, h->stream));
+    SV_CUDA(cudaStreamSynchronize(h->stream));
     return SV_OK;
 }
 

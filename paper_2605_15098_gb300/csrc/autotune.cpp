@@ -76,9 +76,9 @@ extern "C" sv_status sv_autotune(sv_handle h, const sv_gate *host_gates, size_t 
                                  const char *cache_path, sv_config *best, double *best_ms) {
     clear_error();
     if (!h || !best || (m && !host_gates)) return fail(SV_ERR_ARG, "NULL argument");
-    for (size_t i = 0; i < m; i++) {
-        std::string why = check_gate(h->n, host_gates[i]);
-        if (!why.empty()) return fail(SV_ERR_ARG, "gate %zu: %s", i, why.c_str());
+    {
+        const std::string why = check_list(h->n, host_gates, m);
+        if (!why.empty()) return fail(SV_ERR_ARG, "%s", why.c_str());
     }
     const uint64_t key = structure_hash(h->n, h->dt, host_gates, m);
     double ms = 0.0;

@@ -103,10 +103,14 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
         if (it.m && !it.gates) return fail(SV_ERR_ARG, "item %zu: gate list is NULL", i);
         if (!it.qubit_mask || (it.qubit_mask >> it.n))
             return fail(SV_ERR_ARG, "item %zu: read-out mask empty or beyond n", i);
-        for (size_t g = 0; g < it.m; g++) {
-            std::string why = check_gate(it.n, it.gates[g]);
-            if (!why.empty()) return fail(SV_ERR_ARG, "item %zu gate %zu: %s", i, g, why.c_str());
+        {
+            const std::string why = check_list(it.n, it.gates, it.m);
+            if (!why.empty()) return fail(SV_ERR_ARG, "item %zu: %s", i, why.c_str());
         }
+        for (size_t g = 0; g < it.m; g++)
+            if (is_general_kind(it.gates[g].kind))
+                return fail(SV_ERR_UNSUPPORTED, "item %zu gate %zu: the batched launch takes the "
+                            "paper's gate kinds only (no MCU, U2Q or MEASURE)", i, g);
     }
     // plan and compile every instance (host threads)
     std::vector<Compiled> comp(count);

@@ -77,6 +77,9 @@ struct sv_state {
     double *probs = nullptr;      // device marginal of the last read-out
     size_t probs_cap = 0;
     void *small = nullptr;        // 64 KiB device area for reduction partials
+    uint8_t *meas_dev = nullptr;  // outcomes of the last call's measurements
+    size_t meas_cap = 0;
+    size_t nmeas = 0;
     void *plan_host = nullptr;    // pinned host staging for programme uploads
     size_t plan_host_cap = 0;
     // compiled programmes of the last few distinct (gate list, configuration,
@@ -119,7 +122,7 @@ const char *last_error_cstr();
 inline uint64_t state_bytes(const sv_state *h) { return ((uint64_t)1 << h->n) * h->amp_bytes; }
 
 // ---- timing recorder (prof.cpp) ---------------------------------------------
-void note_launch();
+void note_launch(int count = 1);
 // Record the start event of a launch; returns a record slot or -1.
 int prof_begin(sv_state *h);
 // Record the end event and the launch's description.
@@ -132,6 +135,16 @@ sv_status pergate_apply(sv_state *h, const sv_gate &g_phys);
 sv_status init_zero_state(sv_state *h);
 // Write a recorded basis state into the buffer (no-op when it holds the state).
 sv_status materialize(sv_state *h);
+// The general gate set (general.cu): SV_MCU, SV_U2Q (with its three SV_MAT
+// rows) and SV_MEASURE, run by their own per-gate kernels with physical qubit
+// positions; `g` points at the gate's first record.
+bool is_general_kind(int kind);
+int general_records(int kind);
+sv_status general_apply(sv_state *h, const sv_gate *g);
+sv_status ensure_meas(sv_state *h, size_t count);
+// Whole-list validation: every gate (check_gate), a U2Q followed by exactly
+// three MAT rows, no MAT elsewhere; "" or the reason with the gate index.
+std::string check_list(int n, const sv_gate *g, size_t m);
 // Drop the X and H gates that only change a recorded basis state (see api.cu).
 void fold_basis_prefix(sv_state *h, std::vector<sv_gate> &gates);
 

@@ -38,7 +38,7 @@ bool is_controlled_kind(int kind) {
 
 std::string check_gate(int n, const sv_gate &g) {
     char buf[160];
-    if (g.kind < SV_X || g.kind > SV_CPK) {
+    if (g.kind < SV_X || g.kind > SV_MEASURE) {
         snprintf(buf, sizeof buf, "unknown gate kind %d", g.kind);
         return buf;
     }
@@ -46,7 +46,7 @@ std::string check_gate(int n, const sv_gate &g) {
         snprintf(buf, sizeof buf, "target %d outside 0..%d", g.target, n - 1);
         return buf;
     }
-    if (is_controlled_kind(g.kind) || g.kind == SV_SWAP) {
+    if (is_controlled_kind(g.kind) || g.kind == SV_SWAP || g.kind == SV_U2Q || g.kind == SV_MAT) {
         if (g.control < 0 || g.control >= n) {
             snprintf(buf, sizeof buf, "second qubit %d outside 0..%d", g.control, n - 1);
             return buf;
@@ -60,6 +60,35 @@ std::string check_gate(int n, const sv_gate &g) {
     }
     for (int i = 0; i < 8; i++)
         if (!std::isfinite(g.p[i])) return "non-finite parameter";
+    if (g.kind == SV_MCU) {
+        const uint64_t cm = (uint64_t)g.num;
+        if (!cm) return "MCU control mask is empty";
+        if (n < 64 && (cm >> n)) return "MCU control mask has qubits beyond n";
+        if ((cm >> g.target) & 1) return "MCU control mask holds the target";
+    }
+    if (g.kind == SV_MEASURE && !(g.p[0] >= 0.0 && g.p[0] < 1.0)) return "MEASURE u outside [0, 1)";
+    return "";
+}
+
+std::string check_list(int n, const sv_gate *g, size_t m) {
+    char buf[200];
+    for (size_t i = 0; i < m; i++) {
+        std::string why = check_gate(n, g[i]);
+        if (why.empty() && g[i].kind == SV_MAT) why = "a MAT row outside a U2Q";
+        if (why.empty() && g[i].kind == SV_U2Q) {
+            for (size_t r = 1; r <= 3 && why.empty(); r++)
+                if (i + r >= m || g[i + r].kind != SV_MAT || g[i + r].target != g[i].target ||
+                    g[i + r].control != g[i].control)
+                    why = "a U2Q must be followed by three MAT rows on the same qubits";
+            if (why.empty())
+                for (size_t r = 1; r <= 3 && why.empty(); r++) why = check_gate(n, g[i + r]);
+            if (why.empty()) i += 3;
+        }
+        if (!why.empty()) {
+            snprintf(buf, sizeof buf, "gate %zu: %s", i, why.c_str());
+            return buf;
+        }
+    }
     return "";
 }
 
@@ -155,6 +184,7 @@ Mat2 gate_matrix(const sv_gate &g) {
         }
         case SV_U:
         case SV_CU:
+        case SV_MCU:
             for (int e = 0; e < 4; e++) {
                 m.re[e] = g.p[2 * e];
                 m.im[e] = g.p[2 * e + 1];

@@ -216,9 +216,9 @@ namespace {
 sv_status check_args(sv_handle h, const sv_gate *g, size_t m) {
     if (!h) return fail(SV_ERR_ARG, "handle is NULL");
     if (m && !g) return fail(SV_ERR_ARG, "gate list is NULL");
-    for (size_t i = 0; i < m; i++) {
-        std::string why = check_gate(h->n, g[i]);
-        if (!why.empty()) return fail(SV_ERR_ARG, "gate %zu: %s", i, why.c_str());
+    {
+        const std::string why = check_list(h->n, g, m);
+        if (!why.empty()) return fail(SV_ERR_ARG, "%s", why.c_str());
     }
     return SV_OK;
 }

@@ -77,6 +77,9 @@ struct TilePass {
     std::vector<std::pair<int, int>> remap_before;
     std::vector<TileOp> ops;
     std::vector<PhaseTerm> terms;
+    // A gate of the general set (MCU, U2Q with its rows, MEASURE), physical
+    // qubits: the step runs it on the per-gate path; ops and terms are empty.
+    std::vector<sv_gate> general;
 };
 
 struct PlanOptions {
@@ -111,7 +114,10 @@ struct PlanOverride {
 };
 
 // Build the programme; phys (logical -> physical, n entries) is updated by
-// SWAP relabelling.  Gates must be valid.  Returns an empty string on success.
+// SWAP relabelling.  Gates must be valid.  A gate of the general set splits
+// the list: the gates before it are planned, the gate becomes a step of its
+// own (TilePass::general), and the rest is planned from the qubit map then.
+// Returns an empty string on success.
 std::string build_plan(const std::vector<sv_gate> &gates, const PlanOptions &opt, int *phys,
                        Plan *out);
 

@@ -140,9 +140,9 @@ extern "C" sv_status sv_plan_export(int n, sv_dtype dt, const int *host_phys_of_
     if (!len || (cap && !host_buf) || (m && !host_gates)) return fail(SV_ERR_ARG, "NULL argument");
     if (n < 1 || n > 34) return fail(SV_ERR_ARG, "n=%d outside 1..34", n);
     if (dt != SV_C64 && dt != SV_C128) return fail(SV_ERR_ARG, "unknown dtype %d", (int)dt);
-    for (size_t i = 0; i < m; i++) {
-        std::string why = check_gate(n, host_gates[i]);
-        if (!why.empty()) return fail(SV_ERR_ARG, "gate %zu: %s", i, why.c_str());
+    {
+        const std::string why = check_list(n, host_gates, m);
+        if (!why.empty()) return fail(SV_ERR_ARG, "%s", why.c_str());
     }
     sv_config c{};
     if (cfg) c = *cfg;
@@ -168,7 +168,7 @@ extern "C" sv_status sv_plan_export(int n, sv_dtype dt, const int *host_phys_of_
         if (!first) j.raw(",");
         first = false;
         const bool first_ops = first_pass && !p.ops.empty() && p.remap_before.empty();
-        if (!p.ops.empty()) first_pass = false;
+        if (!p.ops.empty() || !p.general.empty()) first_pass = false;
         j.raw("{\"k\":"); j.num(p.k);
         j.raw(",\"c\":"); j.num(p.c);
         j.raw(",\"ngates\":"); j.num(p.ngates);
@@ -205,6 +205,25 @@ extern "C" sv_status sv_plan_export(int n, sv_dtype dt, const int *host_phys_of_
             j.num(p.terms[i].b); j.raw(","); j.u64(p.terms[i].theta); j.raw("]");
         }
         j.raw("]");
+        if (!p.general.empty()) {  // a gate of the general set, run on the per-gate path
+            j.raw(",\"kernel\":\"pergate\",\"general\":[");
+            for (size_t r = 0; r < p.general.size(); r++) {
+                const sv_gate &g = p.general[r];
+                if (r) j.raw(",");
+                j.raw("{\"kind\":"); j.num(g.kind);
+                j.raw(",\"target\":"); j.num(g.target);
+                j.raw(",\"control\":"); j.num(g.control);
+                j.raw(",\"num\":"); j.u64((uint64_t)g.num);
+                j.raw(",\"p\":[");
+                for (int e = 0; e < 8; e++) {
+                    if (e) j.raw(",");
+                    j.dbl(g.p[e]);
+                }
+                j.raw("]}");
+            }
+            j.raw("]}");
+            continue;
+        }
         T2Pass t2;
         const bool fused = c.mode == SV_MODE_FUSED;
         std::string why = "disabled";

@@ -664,8 +664,8 @@ static std::string build_plan_once(const std::vector<sv_gate> &gates_in, const P
 // scheduling puts there, but a fuller pass can leave a remainder that needs
 // more passes.  The greedy plan is built as well (a small fraction of the
 // search's cost) and kept when it has strictly fewer passes.
-std::string build_plan(const std::vector<sv_gate> &gates, const PlanOptions &opt, int *phys,
-                       Plan *out) {
+static std::string build_plan_segment(const std::vector<sv_gate> &gates, const PlanOptions &opt, int *phys,
+                                      Plan *out) {
     if (!opt.search || opt.paper || opt.n <= opt.k) return build_plan_once(gates, opt, phys, out);
     int phys_g[64];
     std::copy(phys, phys + 64, phys_g);
@@ -678,6 +678,49 @@ std::string build_plan(const std::vector<sv_gate> &gates, const PlanOptions &opt
         greedy.passes.size() < out->passes.size()) {
         *out = std::move(greedy);
         std::copy(phys_g, phys_g + 64, phys);
+    }
+    return "";
+}
+
+std::string build_plan(const std::vector<sv_gate> &gates, const PlanOptions &opt, int *phys,
+                       Plan *out) {
+    bool general = false;
+    for (const sv_gate &g : gates) general |= is_general_kind(g.kind);
+    if (!general) return build_plan_segment(gates, opt, phys, out);
+    out->passes.clear();
+    out->relabels = 0;
+    out->remaps = 0;
+    size_t i = 0;
+    for (;;) {
+        size_t j = i;
+        while (j < gates.size() && !is_general_kind(gates[j].kind)) j++;
+        if (j > i) {
+            std::vector<sv_gate> seg(gates.begin() + (long)i, gates.begin() + (long)j);
+            Plan sp;
+            const std::string err = build_plan_segment(seg, opt, phys, &sp);
+            if (!err.empty()) return err;
+            for (TilePass &tp : sp.passes) out->passes.push_back(std::move(tp));
+            out->relabels += sp.relabels;
+            out->remaps += sp.remaps;
+        }
+        if (j == gates.size()) break;
+        const int nr = general_records(gates[j].kind);
+        TilePass step;
+        step.ngates = nr;
+        for (int r = 0; r < nr; r++) {
+            sv_gate g = gates[j + r];
+            g.target = phys[g.target];
+            if (g.control >= 0) g.control = phys[g.control];
+            if (g.kind == SV_MCU) {
+                uint64_t pm = 0;
+                for (int q = 0; q < opt.n; q++)
+                    if (((uint64_t)g.num >> q) & 1) pm |= UINT64_C(1) << phys[q];
+                g.num = (int64_t)pm;
+            }
+            step.general.push_back(g);
+        }
+        out->passes.push_back(std::move(step));
+        i = j + nr;
     }
     return "";
 }

@@ -9,7 +9,7 @@ namespace sv {
 
 static std::atomic<uint64_t> g_launches{0};
 
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launch(int count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
 
 static constexpr size_t kMaxPending = (size_t)1 << 20;
 

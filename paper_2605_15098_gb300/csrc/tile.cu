@@ -497,6 +497,7 @@ static sv_status compiled_plan(sv_state *h, const std::vector<sv_gate> &gates, c
     bool first_pass = true;  // the pass that may start from a recorded basis state
     for (size_t i = 0; i < plan.passes.size(); i++) {
         const TilePass &p = plan.passes[i];
+        if (!p.general.empty()) first_pass = false;  // the step writes the state first
         if (p.ops.empty()) continue;
         const bool first_ops = first_pass && p.remap_before.empty();
         first_pass = false;
@@ -595,6 +596,10 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
 
     for (size_t i = 0; i < plan.passes.size(); i++) {
         const TilePass &p = plan.passes[i];
+        if (!p.general.empty()) {  // a gate of the general set, on the per-gate path
+            SV_TRY(general_apply(h, p.general.data()));
+            continue;
+        }
         if (!p.remap_before.empty()) SV_TRY(remap_apply(h, p.remap_before));
         if (p.ops.empty()) continue;
         sv_launch_record meta = describe_pass(h->n, h->dt, p, up[i].t2 ? &t2[i] : nullptr,

@@ -29,7 +29,8 @@ SV_PLANNER_GREEDY, SV_PLANNER_LEARNED = 0, 1
 
 EXPORTS = (
     "sv_create", "sv_create_on", "sv_destroy", "sv_reset", "sv_info", "sv_qubit_map",
-    "sv_apply_circuit", "sv_last_stats", "sv_probabilities", "sv_probabilities_device",
+    "sv_apply_circuit", "sv_last_stats", "sv_last_measurements", "sv_probabilities",
+    "sv_probabilities_device",
     "sv_argmax", "sv_sample", "sv_copy_out", "sv_copy_in", "sv_last_error", "sv_version",
     "sv_profile", "sv_profile_read", "sv_launch_count", "sv_marginal_noalloc", "sv_plan_export",
     "sv_batch_create", "sv_batch_run", "sv_batch_info", "sv_batch_destroy", "sv_apply_circuit_batch",
@@ -130,6 +131,7 @@ def lib() -> ctypes.CDLL:
         "sv_qubit_map": [vp, vp],
         "sv_apply_circuit": [vp, vp, sz, ctypes.POINTER(sv_config)],
         "sv_last_stats": [vp, ctypes.POINTER(sv_stats)],
+        "sv_last_measurements": [vp, vp, sz, ctypes.POINTER(sz)],
         "sv_probabilities": [vp, u64, vp],
         "sv_probabilities_device": [vp, u64, vp],
         "sv_argmax": [vp, u64, ctypes.POINTER(u64), dp],
@@ -238,6 +240,15 @@ def sv_last_stats(h: int) -> dict:
     st = sv_stats()
     _check(lib().sv_last_stats(ctypes.c_void_p(h), ctypes.byref(st)))
     return st.as_dict()
+
+
+def sv_last_measurements(h: int) -> np.ndarray:
+    """Outcomes (uint8, list order) of the measurements of the last sv_apply_circuit."""
+    cnt = ctypes.c_size_t()
+    _check(lib().sv_last_measurements(ctypes.c_void_p(h), None, 0, ctypes.byref(cnt)))
+    out = np.zeros(max(1, cnt.value), dtype=np.uint8)
+    _check(lib().sv_last_measurements(ctypes.c_void_p(h), out.ctypes.data, cnt.value, ctypes.byref(cnt)))
+    return out[:cnt.value].copy()
 
 
 def sv_probabilities(h: int, qubit_mask: int) -> np.ndarray:
@@ -521,6 +532,9 @@ class State:
 
     def probabilities(self, mask):
         return sv_probabilities(self.h, mask)
+
+    def measurements(self):
+        return sv_last_measurements(self.h)
 
     def argmax(self, mask):
         return sv_argmax(self.h, mask)

@@ -69,3 +69,37 @@ def without_leading_x(g):
     state: the leading X and H gates that only change the recorded state are
     dropped (fold_leading)."""
     return fold_leading(g)[2]
+
+
+def general_circuit(n, m, seed, orc=None):
+    """Seeded circuit mixing the paper's gates with the general set:
+    multi-controlled U (1..3 controls), two-qubit unitaries (four records)
+    and measurements.  Each measurement's u is chosen from the oracle's own
+    probability p0 at that point, half-way inside the outcome it selects, so
+    that no outcome sits on a CDF boundary (input construction only)."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    recs = []
+    for r in mixed_circuit(n, m, seed + 1):
+        recs.append(r)
+        draw = rng.integers(0, 10)
+        if draw < 2:
+            t = int(rng.integers(0, n))
+            others = [q for q in range(n) if q != t]
+            k = int(rng.integers(1, min(3, n - 1) + 1))
+            ctr = [int(c) for c in rng.choice(others, size=k, replace=False)]
+            recs.append(C.mcu(ctr, t, C.random_unitary(rng)))
+        elif draw < 4 and n >= 2:
+            a, b = (int(q) for q in rng.choice(n, size=2, replace=False))
+            z = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))
+            q4, r4 = np.linalg.qr(z)
+            recs += C.u2q(a, b, q4 * (np.diag(r4) / np.abs(np.diag(r4))))
+        elif draw < 5 and orc is not None:
+            t = int(rng.integers(0, n))
+            psi = orc.run(n, C.gates(recs))
+            x = np.arange(1 << n)
+            p0 = float(np.sum(np.abs(psi[((x >> t) & 1) == 0]) ** 2))
+            u = 0.5 * p0 if (rng.random() < 0.5 and p0 > 1e-6) or p0 > 1 - 1e-6 else 0.5 * (1 + p0)
+            recs.append(C.measure(t, u))
+    return C.gates(recs)

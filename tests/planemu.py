@@ -294,6 +294,40 @@ def run_t2_pass(state, p, t2=None, gen_basis=None, gen_h=0):
         state[idx] = t
 
 
+def run_general(state, gates):
+    """A gate of the general set (physical qubits) by its definition: MCU
+    acts where every control bit is 1; U2Q on the four amplitudes ordered by
+    k = bit_a + 2 bit_b; MEASURE picks the smallest i with C_i > u C_last for
+    C = (p0, p0 + p1), zeroes the other half and rescales the kept one.
+    Returns the measurement outcome, or None."""
+    x = np.arange(state.size)
+    g0 = gates[0]
+    if g0["kind"] == 11:  # MCU
+        cm, t = int(g0["num"]), g0["target"]
+        u = mat_of(g0["p"])
+        apply_pairs(state, t, u, (x & cm) == cm)
+        return None
+    if g0["kind"] == 12:  # U2Q
+        a, b = g0["target"], g0["control"]
+        m4 = np.array([[complex(g["p"][2 * k], g["p"][2 * k + 1]) for k in range(4)] for g in gates])
+        base = x[((x >> a) & 1 == 0) & ((x >> b) & 1 == 0)]
+        idx = [base, base | (1 << a), base | (1 << b), base | (1 << a) | (1 << b)]
+        v = np.stack([state[i] for i in idx])
+        w = m4 @ v
+        for k in range(4):
+            state[idx[k]] = w[k]
+        return None
+    t, uval = g0["target"], g0["p"][0]
+    bit = (x >> t) & 1
+    q = np.abs(state) ** 2
+    p0, p1 = float(np.sum(q[bit == 0])), float(np.sum(q[bit == 1]))
+    out = 0 if p0 > uval * (p0 + p1) else 1
+    keep = p0 if out == 0 else p1
+    state[bit != out] = 0
+    state[bit == out] /= np.sqrt(keep)
+    return out
+
+
 def remap(state, pairs):
     """Exchange the physical bit pairs of every index (a remap pass)."""
     x = np.arange(state.size)
@@ -322,6 +356,10 @@ def run_plan(n, plan, use_gen=True, basis=0, hq=0):
     state = product_state(n, basis, hq)
     first = True
     for p in plan["passes"]:
+        if p.get("general"):
+            run_general(state, p["general"])
+            first = False
+            continue
         if p.get("remap_before"):
             state = remap(state, p["remap_before"])
         if not p["ops"]:

@@ -347,3 +347,22 @@ def test_generated_product_state(sv, orc, n, seed, tile, chunk):
         assert "t2gen" in plan["passes"][0]
         got = planemu.run_plan(n, plan, use_gen=True, basis=basis, hq=hq)
         assert float(np.max(np.abs(got - ref))) <= 2e-5
+
+
+@pytest.mark.parametrize("n,seed", [(14, 3), (16, 4)])
+def test_general_gates_split_the_plan(sv, orc, n, seed):
+    """MCU, U2Q and MEASURE become steps of their own between tile passes
+    (run on the per-gate path); the plan around them still matches the
+    oracle, measurement outcomes included."""
+    from gen import general_circuit
+    g = general_circuit(n, 60, seed, orc)
+    kinds = set(int(k) for k in g["kind"])
+    assert {C.MCU, C.U2Q, C.MEASURE} <= kinds
+    plan = sv.sv_plan_export(n, sv.SV_C64, g, sv.make_config(sv.SV_MODE_PARTITIONED))
+    steps = [p for p in plan["passes"] if p.get("general")]
+    assert len(steps) == sum(1 for k in g["kind"] if int(k) in (C.MCU, C.U2Q, C.MEASURE))
+    assert sum(p["ngates"] for p in plan["passes"]) + plan["relabels"] == len(g)
+    psi = orc.init(n)
+    orc.apply_measured(n, psi, g)
+    got = planemu.run_plan(n, plan, use_gen=False)
+    assert float(np.max(np.abs(got - psi))) <= 2e-5
