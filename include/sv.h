@@ -541,6 +541,30 @@ sv_status sv_plan_export(int n, sv_dtype dt, const int *host_phys_of_logical,
                          char *host_buf, size_t cap, size_t *len);
 
 /* Message of the last failed call on this thread ("" if none). */
+/* ---- failure paths, exercised from the host ------------------------------ */
+
+/* Host-side fault injection for tests of the error paths (the paper has no
+ * counterpart).  After `after` further calls at `site` (0: the next one), one
+ * call fails as if the CUDA runtime had refused it, then the site is off
+ * again; after < 0 turns the site off at once.  Sites:
+ *   SV_FAULT_ALLOC   a device allocation: the call returns SV_ERR_OOM
+ *   SV_FAULT_UPLOAD  a programme upload to the device: SV_ERR_CUDA
+ *   SV_FAULT_LAUNCH  a kernel launch, refused before it starts: SV_ERR_CUDA
+ * A call that fails before any kernel wrote the state leaves the state as it
+ * was; one that fails after some of its kernels ran leaves it undefined (as a
+ * real CUDA failure would), and sv_reset or sv_copy_in make it usable again.
+ * The setting is process-wide.  Errors: SV_ERR_ARG (unknown site). */
+enum { SV_FAULT_ALLOC = 0, SV_FAULT_UPLOAD = 1, SV_FAULT_LAUNCH = 2 };
+sv_status sv_fault_inject(int site, int after);
+
+/* Set the handle's device error word from the host, as a tile kernel does
+ * when one of its bounded waits gives up.  The next call that returns data
+ * to the host (sv_probabilities, sv_argmax, sv_sample, sv_copy_out,
+ * sv_last_measurements) reports SV_ERR_TIMEOUT and clears the word; the
+ * state is then undefined.  Lets tests reach the timeout reporting without a
+ * device wait running out.  Errors: SV_ERR_ARG, SV_ERR_OOM, SV_ERR_CUDA. */
+sv_status sv_fault_raise_device_flag(sv_handle h);
+
 const char *sv_last_error(void);
 
 /* Library version string. */

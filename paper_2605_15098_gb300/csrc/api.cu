@@ -49,7 +49,7 @@ sv_status make_handle(int n, sv_dtype dt, void *buf, size_t bytes, void *stream,
             return bail(fail(SV_ERR_CUDA, "cudaStreamCreate failed"));
         }
         h->own_stream = true;
-        if (cudaMalloc(&h->amps, need) != cudaSuccess) {
+        if (dev_malloc(&h->amps, need) != cudaSuccess) {
             cudaGetLastError();
             return bail(fail(SV_ERR_OOM, "cannot allocate %zu bytes for the state", need));
         }
@@ -58,7 +58,7 @@ sv_status make_handle(int n, sv_dtype dt, void *buf, size_t bytes, void *stream,
         h->amps = buf;
         h->stream = reinterpret_cast<cudaStream_t>(stream);
     }
-    if (cudaMalloc(&h->small, 65536) != cudaSuccess) {
+    if (dev_malloc(&h->small, 65536) != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(SV_ERR_OOM, "cannot allocate reduction buffer"));
     }
@@ -150,6 +150,7 @@ sv_status sv_destroy(sv_handle h) {
     h->plan_cache.clear();  // frees each entry's device copy
     if (h->plan_dev) cudaFree(h->plan_dev);
     if (h->plan_host) cudaFreeHost(h->plan_host);
+    if (h->flag_host) cudaFreeHost(h->flag_host);
     if (h->t2_tables) cudaFree(h->t2_tables);
     if (h->t3_tables) cudaFree(h->t3_tables);
     if (h->tab64) cudaFree(h->tab64);
@@ -245,6 +246,8 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *host_gates, size_t m, con
         }
     } else {
         std::vector<sv_gate> gl(host_gates, host_gates + m);
+        const int64_t basis0 = h->basis;
+        const uint64_t basis_h0 = h->basis_h;
         fold_basis_prefix(h, gl);
         c.mode = mode;
         sv_state::Learned *L = nullptr;
@@ -260,6 +263,12 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *host_gates, size_t m, con
             h->stats.candidates = L->info.candidates;
         } else if (st == SV_OK) {
             st = partitioned_apply(h, gl, c);
+        }
+        // a call that fails before any kernel wrote the state leaves it as it
+        // was, the recorded state included (materialising it changes nothing)
+        if (st != SV_OK && h->stats.kernels == 0 && basis0 >= 0) {
+            h->basis = basis0;
+            h->basis_h = basis_h0;
         }
     }
     // per-gate: full-sweep convention (2 x passes x state); partitioned: the
@@ -284,8 +293,7 @@ sv_status sv_probabilities(sv_handle h, uint64_t qubit_mask, double *host_out) {
     SV_TRY(read_marginal(h, qubit_mask, &len));
     SV_CUDA(cudaMemcpyAsync(host_out, h->probs, len * sizeof(double), cudaMemcpyDeviceToHost,
                             h->stream));
-    SV_CUDA(cudaStreamSynchronize(h->stream));
-    return SV_OK;
+    return finish_sync(h);
 }
 
 sv_status sv_probabilities_device(sv_handle h, uint64_t qubit_mask, double *dev_out) {
@@ -334,8 +342,7 @@ sv_status sv_copy_out(sv_handle h, void *host_amps) {
     SV_TRY(resolve_norm(h));
     SV_TRY(remap_to_identity(h));
     SV_CUDA(cudaMemcpyAsync(host_amps, h->amps, state_bytes(h), cudaMemcpyDeviceToHost, h->stream));
-    SV_CUDA(cudaStreamSynchronize(h->stream));
-    return SV_OK;
+    return finish_sync(h);
 }
 
 sv_status sv_copy_in(sv_handle h, const void *host_amps) {
@@ -356,7 +363,21 @@ sv_status sv_last_measurements(sv_handle h, uint8_t *host_out, size_t cap, size_
     *count = h->nmeas;
     const size_t k = std::min(cap, h->nmeas);
     if (k) SV_CUDA(cudaMemcpyAsync(host_out, h->meas_dev, k, cudaMemcpyDeviceToHost, h->stream));
-    SV_CUDA(cudaStreamSynchronize(h->stream));
+    return finish_sync(h);
+}
+
+sv_status sv_fault_inject(int site, int after) {
+    clear_error();
+    if (site < 0 || site >= kFaultSites) return fail(SV_ERR_ARG, "unknown fault site %d", site);
+    g_fault_set(site, after);
+    return SV_OK;
+}
+
+sv_status sv_fault_raise_device_flag(sv_handle h) {
+    clear_error();
+    if (!h) return fail(SV_ERR_ARG, "handle is NULL");
+    SV_TRY(t2_prepare(h));  // the error word lives with the register-stage tables
+    SV_CUDA(cudaMemsetAsync(h->t2_err, 0xff, sizeof(int), h->stream));
     return SV_OK;
 }
 

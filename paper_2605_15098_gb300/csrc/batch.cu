@@ -231,7 +231,7 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
         cudaError_t e = cudaGetLastError();
         return bail(fail(SV_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e)));
     }
-    if (cudaMalloc(&b->prog, blob.b.size() + 256) != cudaSuccess) {
+    if (dev_malloc(&b->prog, blob.b.size() + 256) != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(SV_ERR_OOM, "cannot allocate the batch programme (%zu bytes)", blob.b.size()));
     }
@@ -259,9 +259,9 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
         return bail(fail(SV_ERR_CUDA, "programme upload failed"));
     }
     b->state_amps = amps;
-    if (cudaMalloc(&b->states, amps * 8) != cudaSuccess || cudaMalloc(&b->queue, 256) != cudaSuccess ||
-        cudaMalloc(&b->out_idx, count * sizeof(uint64_t)) != cudaSuccess ||
-        cudaMalloc(&b->out_p, count * sizeof(double)) != cudaSuccess ||
+    if (dev_malloc(&b->states, amps * 8) != cudaSuccess || dev_malloc(&b->queue, 256) != cudaSuccess ||
+        dev_malloc(&b->out_idx, count * sizeof(uint64_t)) != cudaSuccess ||
+        dev_malloc(&b->out_p, count * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&b->h_idx, count * sizeof(uint64_t)) != cudaSuccess ||
         cudaMallocHost(&b->h_p, count * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();

@@ -90,6 +90,7 @@ struct sv_state {
     sv_stats stats{};
     void *t2_tables = nullptr;    // FP64-generated phase tables (register-stage kernel)
     int *t2_err = nullptr;        // device flag: a bounded wait gave up
+    int *flag_host = nullptr;     // pinned host copy of t2_err, read by finish_sync
     void *t3_tables = nullptr;    // FP64-generated 8-bit phase tables (fused kernel)
     void *tab64 = nullptr;        // FP64 phase tables of the complex128 tile kernel (12 MiB)
     double *norm_buf = nullptr;   // per-CTA squared norms of fused passes (2 x 256)
@@ -123,6 +124,24 @@ inline uint64_t state_bytes(const sv_state *h) { return ((uint64_t)1 << h->n) * 
 
 // ---- timing recorder (prof.cpp) ---------------------------------------------
 void note_launch(int count = 1);
+
+// Host-side fault injection (sv_fault_inject): the sites a test can make
+// fail, and the check each site makes before it acts.
+enum FaultSite { kFaultAlloc = 0, kFaultUpload = 1, kFaultLaunch = 2, kFaultSites = 3 };
+bool fault_fire(int site);
+void g_fault_set(int site, int after);
+// cudaMalloc, or cudaErrorMemoryAllocation when an injected fault fires.
+template <typename T>
+cudaError_t dev_malloc(T **p, size_t bytes) {
+    if (fault_fire(kFaultAlloc)) return cudaErrorMemoryAllocation;
+    return cudaMalloc(reinterpret_cast<void **>(p), bytes);
+}
+// The launch-site check: SV_ERR_CUDA, before the launch, when a fault fires.
+sv_status launch_check();
+// End of a call that returns data to the host: synchronise the stream and
+// report (and clear) the handle's device error word, which a bounded device
+// wait sets when it gives up, as SV_ERR_TIMEOUT.
+sv_status finish_sync(sv_state *h);
 // Record the start event of a launch; returns a record slot or -1.
 int prof_begin(sv_state *h);
 // Record the end event and the launch's description.

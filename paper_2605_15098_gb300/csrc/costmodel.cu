@@ -315,10 +315,10 @@ sv_status ensure_rows(sv_cost_model_s *m, size_t count) {
     m->idx = nullptr;
     m->x_cap = 0;
     const size_t cap = std::max<size_t>(count, 1024);
-    if (cudaMalloc(&m->X, cap * NF * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&m->T, cap * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&m->Y, cap * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&m->idx, cap * sizeof(int)) != cudaSuccess) {
+    if (dev_malloc(&m->X, cap * NF * sizeof(float)) != cudaSuccess ||
+        dev_malloc(&m->T, cap * sizeof(float)) != cudaSuccess ||
+        dev_malloc(&m->Y, cap * sizeof(float)) != cudaSuccess ||
+        dev_malloc(&m->idx, cap * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         return fail(SV_ERR_OOM, "cost model: cannot allocate %zu sample rows", cap);
     }
@@ -332,8 +332,8 @@ sv_status ensure_partials(sv_cost_model_s *m, size_t blocks) {
     cudaFree(m->L);
     m->G = m->L = nullptr;
     m->g_cap = 0;
-    if (cudaMalloc(&m->G, blocks * NP * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&m->L, blocks * sizeof(float)) != cudaSuccess) {
+    if (dev_malloc(&m->G, blocks * NP * sizeof(float)) != cudaSuccess ||
+        dev_malloc(&m->L, blocks * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         return fail(SV_ERR_OOM, "cost model: cannot allocate gradient partials");
     }
@@ -469,11 +469,11 @@ sv_status sv_cost_model_create(uint64_t seed, sv_cost_model *out) {
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, m->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(&m->P, NP * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->M, NP * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->V, NP * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->gout, NP * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->loss, sizeof(double));
+    if (e == cudaSuccess) e = dev_malloc(&m->P, NP * sizeof(float));
+    if (e == cudaSuccess) e = dev_malloc(&m->M, NP * sizeof(float));
+    if (e == cudaSuccess) e = dev_malloc(&m->V, NP * sizeof(float));
+    if (e == cudaSuccess) e = dev_malloc(&m->gout, NP * sizeof(float));
+    if (e == cudaSuccess) e = dev_malloc(&m->loss, sizeof(double));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_train());

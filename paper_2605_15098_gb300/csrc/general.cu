@@ -228,6 +228,7 @@ sv_status general_apply(sv_state *h, const sv_gate *g) {
     static_assert(2 * kMeasBlocks * sizeof(double) + 64 <= 64 * 1024, "measurement scratch fits the small area");
     SV_TRY(materialize(h));
     SV_TRY(resolve_norm(h));
+    SV_TRY(launch_check());
     sv_launch_record meta{};
     meta.kind = SV_KERNEL_PERGATE;
     meta.pass = h->launch_index++;
@@ -251,7 +252,7 @@ sv_status ensure_meas(sv_state *h, size_t count) {
     if (count <= h->meas_cap) return SV_OK;
     const size_t cap = std::max<size_t>(2 * count, 256);
     uint8_t *p = nullptr;
-    if (cudaMalloc(&p, cap) != cudaSuccess) {
+    if (dev_malloc(&p, cap) != cudaSuccess) {
         cudaGetLastError();
         return fail(SV_ERR_OOM, "cannot allocate the measurement outcomes (%zu bytes)", cap);
     }

@@ -336,7 +336,7 @@ sv_status ensure_scratch(sv_state *h, size_t bytes) {
         h->scratch_cap = 0;
     }
     size_t cap = std::max<size_t>(bytes, (size_t)1 << 20);
-    if (cudaMalloc(&h->scratch, cap) != cudaSuccess) {
+    if (dev_malloc(&h->scratch, cap) != cudaSuccess) {
         cudaGetLastError();
         h->scratch = nullptr;
         return fail(SV_ERR_OOM, "cannot allocate %zu bytes of device scratch", cap);
@@ -354,7 +354,7 @@ sv_status ensure_probs(sv_state *h, size_t bytes) {
         h->probs_cap = 0;
     }
     size_t cap = std::max<size_t>(bytes, (size_t)1 << 16);
-    if (cudaMalloc(&h->probs, cap) != cudaSuccess) {
+    if (dev_malloc(&h->probs, cap) != cudaSuccess) {
         cudaGetLastError();
         h->probs = nullptr;
         return fail(SV_ERR_OOM, "cannot allocate %zu bytes for probabilities", cap);
@@ -480,7 +480,7 @@ sv_status argmax_device(sv_state *h, const double *dev_p, uint64_t len, uint64_t
     uint64_t i;
     SV_CUDA(cudaMemcpyAsync(&v, fv, sizeof v, cudaMemcpyDeviceToHost, h->stream));
     SV_CUDA(cudaMemcpyAsync(&i, fi, sizeof i, cudaMemcpyDeviceToHost, h->stream));
-    SV_CUDA(cudaStreamSynchronize(h->stream));
+    SV_TRY(finish_sync(h));
     *host_idx = i;
     if (host_p) *host_p = v;
     return SV_OK;
@@ -518,8 +518,7 @@ sv_status sample_device(sv_state *h, const double *dev_p, uint64_t len, const do
         SV_CUDA(cudaMemcpyAsync(host_out, dout, shots * sizeof(uint64_t), cudaMemcpyDeviceToHost,
                                 h->stream));
     }
-    SV_CUDA(cudaStreamSynchronize(h->stream));
-    return SV_OK;
+    return finish_sync(h);
 }
 
 }  // namespace sv

@@ -292,6 +292,7 @@ sv_status materialize(sv_state *h) {
 // Apply one gate given in PHYSICAL qubit positions.
 sv_status pergate_apply(sv_state *h, const sv_gate &g) {
     SV_TRY(materialize(h));
+    SV_TRY(launch_check());
     const int n = h->n;
     int op;
     Mat2 m{};

@@ -11,6 +11,38 @@ static std::atomic<uint64_t> g_launches{0};
 
 void note_launch(int count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
 
+namespace {
+// Countdown per fault site: the call that takes it from 0 to -1 fails; < 0: off.
+std::atomic<int> g_fault[kFaultSites] = {{-1}, {-1}, {-1}};
+}  // namespace
+
+void g_fault_set(int site, int after) { g_fault[site].store(after < 0 ? -1 : after); }
+
+bool fault_fire(int site) {
+    int v = g_fault[site].load(std::memory_order_relaxed);
+    while (v >= 0)
+        if (g_fault[site].compare_exchange_weak(v, v - 1, std::memory_order_relaxed)) return v == 0;
+    return false;
+}
+
+sv_status launch_check() {
+    if (fault_fire(kFaultLaunch)) return fail(SV_ERR_CUDA, "kernel launch failed (injected fault)");
+    return SV_OK;
+}
+
+sv_status finish_sync(sv_state *h) {
+    if (h->t2_err && h->flag_host)
+        SV_CUDA(cudaMemcpyAsync(h->flag_host, h->t2_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    SV_CUDA(cudaStreamSynchronize(h->stream));
+    if (h->t2_err && h->flag_host && *h->flag_host) {
+        *h->flag_host = 0;
+        SV_CUDA(cudaMemsetAsync(h->t2_err, 0, sizeof(int), h->stream));
+        SV_CUDA(cudaStreamSynchronize(h->stream));
+        return fail(SV_ERR_TIMEOUT, "a tile kernel gave up waiting (bounded device wait); the state is undefined");
+    }
+    return SV_OK;
+}
+
 static constexpr size_t kMaxPending = (size_t)1 << 20;
 
 static cudaEvent_t take_event(sv_state *h) {

@@ -127,6 +127,7 @@ void launch(sv_state *h, int np, const int *lo, const int *hi, int vb) {
 
 sv_status remap_apply(sv_state *h, const std::vector<std::pair<int, int>> &pairs) {
     SV_TRY(materialize(h));
+    SV_TRY(launch_check());
     int lo[kMaxPairs], hi[kMaxPairs];
     int np = 0;
     uint64_t used = 0;

@@ -258,6 +258,7 @@ k_tile(R *__restrict__ state, const PassArgs a) {
 
 template <typename R>
 sv_status launch_pass(sv_state *h, const PassArgs &a, const sv_launch_record &meta) {
+    SV_TRY(launch_check());
     const size_t smem = ((size_t)1 << a.k) * 2 * sizeof(R);
     static bool configured[2] = {false, false};
     auto kern = k_tile<R>;
@@ -380,7 +381,7 @@ struct CompiledPlan {
 static sv_status tab64_prepare(sv_state *h) {
     if (h->tab64) return SV_OK;
     void *p = nullptr;
-    if (cudaMalloc(&p, (size_t)3 * kTab64 * sizeof(double2)) != cudaSuccess) {
+    if (dev_malloc(&p, (size_t)3 * kTab64 * sizeof(double2)) != cudaSuccess) {
         cudaGetLastError();
         return fail(SV_ERR_OOM, "cannot allocate complex128 phase tables");
     }
@@ -544,7 +545,7 @@ static sv_status compiled_plan(sv_state *h, const std::vector<sv_gate> &gates, c
         SV_CUDA(cudaStreamSynchronize(h->stream));
     }
     if (use_cache) {
-        if (cudaMalloc(&cp->dev, total + 256) != cudaSuccess) {
+        if (dev_malloc(&cp->dev, total + 256) != cudaSuccess) {
             cudaGetLastError();
             cp->dev = nullptr;
             return fail(SV_ERR_OOM, "cannot allocate the pass programme (%zu bytes)", total);
@@ -556,7 +557,7 @@ static sv_status compiled_plan(sv_state *h, const std::vector<sv_gate> &gates, c
             h->plan_dev = nullptr;
             h->plan_cap = 0;
             const size_t cap = std::max<size_t>(2 * (total + 256), (size_t)1 << 16);
-            if (cudaMalloc(&h->plan_dev, cap) != cudaSuccess) {
+            if (dev_malloc(&h->plan_dev, cap) != cudaSuccess) {
                 cudaGetLastError();
                 h->plan_dev = nullptr;
                 return fail(SV_ERR_OOM, "cannot allocate the pass programme (%zu bytes)", cap);
@@ -566,6 +567,7 @@ static sv_status compiled_plan(sv_state *h, const std::vector<sv_gate> &gates, c
         cp->dev = h->plan_dev;
     }
     cp->bytes = total;
+    if (fault_fire(kFaultUpload)) return fail(SV_ERR_CUDA, "programme upload failed (injected fault)");
     std::memcpy(h->plan_host, blob.b.data(), total);
     SV_CUDA(cudaMemcpyAsync(cp->dev, h->plan_host, total, cudaMemcpyHostToDevice, h->stream));
     h->stats.h2d_bytes += (double)total;

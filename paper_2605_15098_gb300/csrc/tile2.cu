@@ -776,12 +776,18 @@ int t2_gate_kinds(const T2Pass &p) {
 sv_status t2_prepare(sv_state *h) {
     if (h->t2_tables) return SV_OK;
     void *p = nullptr;
-    if (cudaMalloc(&p, kTabEntries * sizeof(float2) + 64) != cudaSuccess) {
+    if (dev_malloc(&p, kTabEntries * sizeof(float2) + 64) != cudaSuccess) {
         cudaGetLastError();
         return fail(SV_ERR_OOM, "cannot allocate phase tables");
     }
     h->t2_tables = p;
     h->t2_err = reinterpret_cast<int *>(reinterpret_cast<char *>(p) + kTabEntries * sizeof(float2));
+    if (cudaMallocHost(&h->flag_host, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        h->flag_host = nullptr;
+        return fail(SV_ERR_OOM, "cannot allocate the pinned error word");
+    }
+    *h->flag_host = 0;
     SV_CUDA(cudaMemsetAsync(h->t2_err, 0, sizeof(int), h->stream));
     k_phase_tables<<<(kTabEntries + 255) / 256, 256, 0, h->stream>>>(reinterpret_cast<float2 *>(p));
     SV_CUDA(cudaGetLastError());
@@ -843,6 +849,7 @@ void t2_fill_args(const T2Pass &p, const T2Device &d, int n, T2Args *a) {
 sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta,
                     int64_t gen_basis) {
     if (p.format != 2) return fail(SV_ERR_ARG, "internal: register-stage pass not in format 2");
+    SV_TRY(launch_check());
     T2Args a{};
     t2_fill_args(p, d, h->n, &a);
     if (gen_basis >= 0) {
@@ -896,7 +903,7 @@ sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
 
 sv_status t2_build_tables(void **tables, int **err, cudaStream_t stream) {
     void *p = nullptr;
-    if (cudaMalloc(&p, kTabEntries * sizeof(float2) + 64) != cudaSuccess) {
+    if (dev_malloc(&p, kTabEntries * sizeof(float2) + 64) != cudaSuccess) {
         cudaGetLastError();
         return fail(SV_ERR_OOM, "cannot allocate phase tables");
     }

@@ -546,7 +546,7 @@ sv_status t3_prepare(sv_state *h) {
     if (h->t3_tables) return SV_OK;
     SV_TRY(t2_prepare(h));  // error flag lives with the register-stage tables
     void *p = nullptr;
-    if (cudaMalloc(&p, 4 * kTabN * sizeof(float2)) != cudaSuccess) {
+    if (dev_malloc(&p, 4 * kTabN * sizeof(float2)) != cudaSuccess) {
         cudaGetLastError();
         return fail(SV_ERR_OOM, "cannot allocate phase tables");
     }
@@ -564,10 +564,11 @@ sv_status t3_prepare(sv_state *h) {
 }
 
 sv_status t3_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta) {
+    SV_TRY(launch_check());
     T3Args a{};
     if (!h->norm_buf) {
         void *nb = nullptr;
-        if (cudaMalloc(&nb, 2 * 256 * sizeof(double)) != cudaSuccess) {
+        if (dev_malloc(&nb, 2 * 256 * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             return fail(SV_ERR_OOM, "cannot allocate the norm buffer");
         }

@@ -38,8 +38,9 @@ EXPORTS = (
     "sv_cost_features", "sv_cost_model_create", "sv_cost_model_destroy", "sv_cost_model_get_params",
     "sv_cost_model_set_params", "sv_cost_model_predict", "sv_cost_model_gradient",
     "sv_cost_model_train", "sv_cost_model_save", "sv_cost_model_load", "sv_set_cost_model",
-    "sv_learned_plan", "sv_planner_judge",
+    "sv_learned_plan", "sv_planner_judge", "sv_fault_inject", "sv_fault_raise_device_flag",
 )
+SV_FAULT_ALLOC, SV_FAULT_UPLOAD, SV_FAULT_LAUNCH = 0, 1, 2
 SV_COST_FEATURES, SV_COST_HIDDEN, SV_COST_PARAMS = 52, 64, 7617
 SV_KERNEL_PERGATE, SV_KERNEL_TILE, SV_KERNEL_REMAP, SV_KERNEL_FUSED = 0, 1, 2, 3
 
@@ -132,6 +133,8 @@ def lib() -> ctypes.CDLL:
         "sv_apply_circuit": [vp, vp, sz, ctypes.POINTER(sv_config)],
         "sv_last_stats": [vp, ctypes.POINTER(sv_stats)],
         "sv_last_measurements": [vp, vp, sz, ctypes.POINTER(sz)],
+        "sv_fault_inject": [i32, i32],
+        "sv_fault_raise_device_flag": [vp],
         "sv_probabilities": [vp, u64, vp],
         "sv_probabilities_device": [vp, u64, vp],
         "sv_argmax": [vp, u64, ctypes.POINTER(u64), dp],
@@ -249,6 +252,14 @@ def sv_last_measurements(h: int) -> np.ndarray:
     out = np.zeros(max(1, cnt.value), dtype=np.uint8)
     _check(lib().sv_last_measurements(ctypes.c_void_p(h), out.ctypes.data, cnt.value, ctypes.byref(cnt)))
     return out[:cnt.value].copy()
+
+
+def sv_fault_inject(site: int, after: int = 0) -> None:
+    _check(lib().sv_fault_inject(site, after))
+
+
+def sv_fault_raise_device_flag(h: int) -> None:
+    _check(lib().sv_fault_raise_device_flag(ctypes.c_void_p(h)))
 
 
 def sv_probabilities(h: int, qubit_mask: int) -> np.ndarray:
