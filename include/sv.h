@@ -135,9 +135,15 @@ enum {
     SV_FLAG_EARLY_DIAG = 32,    /* keep each diagonal gate in the first pass
                                    where it is ready (default: the pass of the
                                    first later gate it does not commute with)  */
-    SV_FLAG_GREEDY_ONLY = 64    /* take each pass's local qubits as the greedy
+    SV_FLAG_GREEDY_ONLY = 64,   /* take each pass's local qubits as the greedy
                                    list scheduling picks them, without the
                                    local search that refines the set          */
+    SV_FLAG_L2_BLOCKS = 128     /* two-level blocking (Sec. III-B's block sized
+                                   to the last-level cache): consecutive
+                                   register-stage passes whose tile qubits
+                                   together span at most l2_qubits qubits run
+                                   as one launch, block by block, so that the
+                                   state moves between them through L2        */
 };
 
 /* Planner choice for partitioned modes. */
@@ -154,7 +160,15 @@ typedef struct sv_config {
     int32_t fuse_qubits;   /* width of a tensor-core fused block; 0 = 5        */
     int32_t planner;       /* sv_planner                                       */
     int32_t flags;         /* SV_FLAG_*                                        */
-    int32_t reserved[10];  /* must be 0                                        */
+    int32_t l2_qubits;     /* with SV_FLAG_L2_BLOCKS: the widest union of tile
+                              qubits a group of passes may span (its L2 block
+                              holds 2^l2_qubits amplitudes); 0 = from the
+                              device's L2 size (a block of at most 1/8 of it) */
+    int32_t l2_chunk;      /* with SV_FLAG_L2_BLOCKS: consecutive tiles a CTA
+                              takes per claim (1, 2, 4, 8 or 16; 0 = 2).  More
+                              tiles per claim mean fewer programme reloads and
+                              a larger lag between a block's passes           */
+    int32_t reserved[8];   /* must be 0                                        */
 } sv_config;
 
 /* Counters of the last sv_apply_circuit on a handle. */
@@ -174,6 +188,9 @@ typedef struct sv_stats {
     int32_t candidates;     /* learned planner: candidate passes it scored        */
     double predicted_ms;    /* learned planner: the cost model's estimate (0 if
                                the greedy plan ran)                             */
+    int32_t ctas_per_sm;    /* resident CTAs per SM of the call's register-stage
+                               and L2 block launches (the smallest; 0 if none)  */
+    int32_t reserved;
 } sv_stats;
 
 /* ---- lifetime --------------------------------------------------------- */
@@ -384,7 +401,10 @@ enum {
     SV_KERNEL_PERGATE = 0,  /* one gate, one HBM sweep                       */
     SV_KERNEL_TILE = 1,     /* one tile pass (shared-memory programme)        */
     SV_KERNEL_REMAP = 2,    /* explicit qubit-remap permutation pass           */
-    SV_KERNEL_FUSED = 3     /* tile pass with tensor-core fused blocks         */
+    SV_KERNEL_FUSED = 3,    /* tile pass with tensor-core fused blocks         */
+    SV_KERNEL_L2BLOCK = 4   /* several register-stage tile passes run block by
+                               block through L2 (SV_FLAG_L2_BLOCKS): k holds
+                               the block qubits, nops the passes             */
 };
 
 /* One kernel launch of sv_apply_circuit, timed with CUDA events recorded on
@@ -399,10 +419,11 @@ typedef struct sv_launch_record {
     int32_t dtype;     /* sv_dtype                                             */
     int32_t gate_kind; /* per-gate: the gate kind; tile kernels: -1 generic,
                           -2 register-stage, -3 fused (tensor cores);
-                          remap: -4                                            */
+                          remap: -4; L2 block group: -5                       */
     double bytes;      /* algorithmic bytes: 2 * 2^n * sizeof(amp) per sweep,
                           the touched share for per-gate diagonal/SWAP, the
-                          moved share for a remap                              */
+                          moved share for a remap; an L2 block group counts
+                          its first read and last write                       */
     double ms;         /* measured duration (0 in planning descriptors)        */
     uint64_t feat;     /* tile: bit mask of the physical qubits in the tile;
                           per-gate: bit mask of the gate's qubits; remap: bit

@@ -39,7 +39,8 @@ sv_status make_handle(int n, sv_dtype dt, void *buf, size_t bytes, void *stream,
     };
     if (cudaGetDevice(&h->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) !=
-            cudaSuccess) {
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&h->l2_bytes, cudaDevAttrL2CacheSize, h->device) != cudaSuccess) {
         cudaError_t e = cudaGetLastError();
         return bail(fail(SV_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e)));
     }
@@ -147,6 +148,7 @@ sv_status sv_destroy(sv_handle h) {
     if (h->scratch) cudaFree(h->scratch);
     if (h->probs) cudaFree(h->probs);
     if (h->small) cudaFree(h->small);
+    if (h->grp) cudaFree(h->grp);
     h->plan_cache.clear();  // frees each entry's device copy
     if (h->plan_dev) cudaFree(h->plan_dev);
     if (h->plan_host) cudaFreeHost(h->plan_host);
@@ -197,8 +199,12 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *host_gates, size_t m, con
     if (m && !host_gates) return fail(SV_ERR_ARG, "gate list is NULL");
     sv_config c{};
     if (cfg) c = *cfg;
-    for (int i = 0; i < 10; i++)
+    for (int i = 0; i < 8; i++)
         if (c.reserved[i]) return fail(SV_ERR_ARG, "sv_config.reserved must be 0");
+    if (c.l2_qubits != 0 && (c.l2_qubits < 14 || c.l2_qubits > 30))
+        return fail(SV_ERR_ARG, "l2_qubits must be 0 or 14..30");
+    if (c.l2_chunk < 0 || c.l2_chunk > 16 || (c.l2_chunk & (c.l2_chunk - 1)))
+        return fail(SV_ERR_ARG, "l2_chunk must be 0 or a power of two up to 16");
     if (c.mode < SV_MODE_AUTO || c.mode > SV_MODE_FUSED)
         return fail(SV_ERR_ARG, "unknown mode %d", c.mode);
     if (c.planner < SV_PLANNER_GREEDY || c.planner > SV_PLANNER_LEARNED)

@@ -66,6 +66,7 @@ struct sv_state {
     bool own_stream = false;
     int device = 0;
     int sm_count = 0;
+    int l2_bytes = 0;
     int phys[64];                 // physical bit of each logical qubit
     // >= 0: the state is H on the physical qubits of basis_h applied to the
     // basis state |basis> (physical index), recorded only: the buffer may
@@ -77,6 +78,8 @@ struct sv_state {
     double *probs = nullptr;      // device marginal of the last read-out
     size_t probs_cap = 0;
     void *small = nullptr;        // 64 KiB device area for reduction partials
+    void *grp = nullptr;          // L2 block groups: done counters and claim queue
+    size_t grp_cap = 0;
     uint8_t *meas_dev = nullptr;  // outcomes of the last call's measurements
     size_t meas_cap = 0;
     size_t nmeas = 0;
@@ -205,6 +208,8 @@ sv_status sample_device(sv_state *h, const double *dev_p, uint64_t len,
 // ---- partitioned path (planner.cpp, tile.cu, tile2.cu) -------------------------
 struct T2Pass;
 struct T2Device;
+struct T2Args;
+struct GroupArgs;
 size_t t2_smem_bytes();
 // Gate kinds (X, real, general 2x2) a register-stage programme uses: picks the
 // kernel instantiation.
@@ -214,6 +219,12 @@ sv_status t2_prepare(sv_state *h);
 // instead of reading the buffer.
 sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta,
                     int64_t gen_basis = -1);
+// The generated-state fields of a first pass that starts from the recorded
+// product state (h->basis = gen_basis, h->basis_h).
+void t2_set_gen(const sv_state *h, const T2Pass &p, int64_t gen_basis, T2Args *a);
+// One launch running the passes of an L2 block group (complex64, 2^13 tiles);
+// `need`: the gate kinds (t2_gate_kinds) of all its passes.
+sv_status t2_group_launch(sv_state *h, const GroupArgs &g, int need, const sv_launch_record &meta);
 sv_status t3_prepare(sv_state *h);
 sv_status t3_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta);
 // Multiply the state by the pending norm correction of the last fused pass.

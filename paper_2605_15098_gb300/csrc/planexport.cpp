@@ -164,7 +164,9 @@ extern "C" sv_status sv_plan_export(int n, sv_dtype dt, const int *host_phys_of_
     j.raw(",\"phys\":"); j.arr(phys, n);
     j.raw(",\"passes\":[");
     bool first = true, first_pass = true;
+    std::vector<char> eligible;  // register-stage, format 2, 2^13 tiles: may join an L2 block group
     for (const TilePass &p : plan.passes) {
+        eligible.push_back(0);
         if (!first) j.raw(",");
         first = false;
         const bool first_ops = first_pass && !p.ops.empty() && p.remap_before.empty();
@@ -242,6 +244,7 @@ extern "C" sv_status sv_plan_export(int n, sv_dtype dt, const int *host_phys_of_
             }
         }
         if (why.empty()) {
+            eligible.back() = t2.format == 2 && p.k == kT2Qubits;
             j.raw(",\"kernel\":\"");
             j.raw(kname);
             j.raw("\",\"t2\":");
@@ -261,7 +264,29 @@ extern "C" sv_status sv_plan_export(int n, sv_dtype dt, const int *host_phys_of_
         }
         j.raw("}");
     }
-    j.raw("]}");
+    j.raw("]");
+    if ((c.flags & SV_FLAG_L2_BLOCKS) && !dbl) {
+        // the groups of two-level blocking, for GB300's defaults: a 126 MiB
+        // L2 (unless l2_qubits is given) and 2 x 152 resident CTAs
+        const int cap = c.l2_qubits ? c.l2_qubits : l2_default_qubits((size_t)126 << 20, 8);
+        std::vector<L2Group> groups;
+        err = form_l2_groups(plan, eligible, n, kT2Qubits, cap, 2 * 152, c.l2_chunk ? c.l2_chunk : 2, &groups);
+        if (!err.empty()) return fail(SV_ERR_ARG, "L2 blocks: %s", err.c_str());
+        j.raw(",\"l2_groups\":[");
+        for (size_t g = 0; g < groups.size(); g++) {
+            if (g) j.raw(",");
+            j.raw("{\"first\":"); j.num(groups[g].first);
+            j.raw(",\"count\":"); j.num(groups[g].count);
+            j.raw(",\"l\":"); j.num(groups[g].l);
+            j.raw(",\"bmask\":"); j.u64(groups[g].bmask);
+            j.raw(",\"lag\":"); j.num(groups[g].lag);
+            j.raw(",\"chunk\":"); j.num(1 << groups[g].chunk_log);
+            j.raw(",\"segs\":"); j.arr(groups[g].segs.data(), (int)groups[g].segs.size());
+            j.raw("}");
+        }
+        j.raw("]");
+    }
+    j.raw("}");
     *len = j.s.size();
     if (cap) {
         size_t k = std::min(cap - 1, j.s.size());

@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "l2group.h"
 #include "plan.h"
 #include "tileprog.h"
 
@@ -96,11 +97,33 @@ struct T2Args {
     uint64_t gen_basis, gen_ghmask;
     uint32_t gen_hmask;
     float gen_val;
+    // write-back: 0 streams the tile out (evict-first stores, the pass's
+    // result goes to HBM); 1 keeps it in L2 (plain stores: the next pass of
+    // an L2 block reads it)
+    int keep;
 };
 
 // Fill the counts, pointers and geometry of a format-2 pass (not gen,
 // tables or err).
 void t2_fill_args(const T2Pass &p, const T2Device &d, int n, T2Args *a);
+
+// Re-order a pass's tile index for an L2 block of the physical qubits
+// `bmask`: the low bits of the tile index run over the pass's global qubits
+// inside the block, the high bits (the block index) over the qubits outside
+// it.  Returns false if the runs do not fit the argument record.
+bool t2_block_runs(T2Args *a, uint64_t gmask, uint64_t bmask, int n);
+
+// One launch of an L2 block group: its passes' arguments and the claim order.
+struct GroupArgs {
+    T2Args pass[kMaxGroupPasses];
+    const uint32_t *segs;       // (block << 3) | pass, in claim order
+    uint64_t nitems;            // segments x tiles per block
+    int npass, tpb_log;         // passes; log2 of a pass's tiles inside a block
+    int chunk_log;              // a claim takes 2^chunk_log consecutive items
+    unsigned *done;             // per (block, pass): tiles finished (zero at launch)
+    unsigned long long *queue;  // next item to claim (zero at launch)
+    int *err;
+};
 
 // One instance of a batch: its state, passes and read-out qubits.
 struct BatchInst {

@@ -369,6 +369,9 @@ struct CompiledPlan {
     Plan plan;
     std::vector<T2Pass> t2;
     std::vector<PassUpload> up;
+    std::vector<L2Group> groups;       // L2 block groups (SV_FLAG_L2_BLOCKS)
+    std::vector<size_t> group_segs;    // blob offset of each group's claim order
+    std::vector<int> group_at;         // per pass: the group it starts, or -1
     int phys_out[64];
     void *dev = nullptr;
     size_t bytes = 0;
@@ -439,13 +442,18 @@ sv_launch_record describe_remap(int n, sv_dtype dt, const std::vector<std::pair<
 }
 
 // The cache key: every input of planning and compilation.
+static int l2_cap(const sv_state *h, const sv_config &cfg) {
+    if (cfg.l2_qubits) return cfg.l2_qubits;
+    return l2_default_qubits(h->l2_bytes > 0 ? (size_t)h->l2_bytes : ((size_t)126 << 20), h->amp_bytes);
+}
+
 static std::string plan_key(const sv_state *h, const std::vector<sv_gate> &gates, const sv_config &cfg,
                             const PlanOptions &opt, const PlanOverride *ov) {
     std::string k;
     auto put = [&](const void *p, size_t n) { k.append(static_cast<const char *>(p), n); };
     const int head[] = {h->n, (int)h->dt, cfg.mode, (int)cfg.flags, opt.n, opt.k, opt.c,
                         opt.merge_diag, opt.relabel, opt.paper, opt.split_u3, opt.late_diag,
-                        opt.search, ov ? 1 : 0};
+                        opt.search, ov ? 1 : 0, l2_cap(h, cfg), cfg.l2_chunk, h->sm_count};
     put(head, sizeof head);
     put(h->phys, sizeof h->phys);
     if (ov) {
@@ -527,6 +535,22 @@ static sv_status compiled_plan(sv_state *h, const std::vector<sv_gate> &gates, c
             up[i].terms = blob.put_vec(p.terms);
         }
     }
+    cp->group_at.assign(plan.passes.size(), -1);
+    if ((cfg.flags & SV_FLAG_L2_BLOCKS) && !dbl) {
+        // two-level blocking: consecutive register-stage passes that fit one L2 block
+        std::vector<char> eligible(plan.passes.size(), 0);
+        for (size_t i = 0; i < plan.passes.size(); i++)
+            eligible[i] = up[i].t2 && !up[i].t3 && t2[i].format == 2 && plan.passes[i].k == kT2Qubits &&
+                          !plan.passes[i].ops.empty();
+        const std::string why =
+            form_l2_groups(plan, eligible, h->n, kT2Qubits, l2_cap(h, cfg), 2 * std::max(1, h->sm_count),
+                           cfg.l2_chunk ? cfg.l2_chunk : 2, &cp->groups);
+        if (!why.empty()) return fail(SV_ERR_ARG, "L2 blocks: %s", why.c_str());
+        for (size_t g = 0; g < cp->groups.size(); g++) {
+            cp->group_segs.push_back(blob.put_vec(cp->groups[g].segs));
+            cp->group_at[cp->groups[g].first] = (int)g;
+        }
+    }
     blob.put(nullptr, 0);
     const size_t total = blob.b.size();
     if (total > h->plan_host_cap) {
@@ -579,6 +603,95 @@ static sv_status compiled_plan(sv_state *h, const std::vector<sv_gate> &gates, c
     return SV_OK;
 }
 
+// Run L2 block group gi of the plan (its first pass's remap already done).
+static sv_status group_apply(sv_state *h, const CompiledPlan &cp, int gi) {
+    const L2Group &g = cp.groups[gi];
+    const char *dev = reinterpret_cast<const char *>(cp.dev);
+    SV_TRY(resolve_norm(h));
+    // a recorded basis state: generated by the first pass, or written out first
+    int64_t gen = -1;
+    if (h->basis >= 0) {
+        if (cp.up[g.first].has_gen)
+            gen = h->basis;
+        else
+            SV_TRY(materialize(h));
+    }
+    GroupArgs ga{};
+    int need = 0, ngates = 0, nins = 0, nfac = 0, nstages = 0;
+    uint64_t feat = 0;
+    for (int j = 0; j < g.count; j++) {
+        const int i = g.first + j;
+        const bool gj = j == 0 && gen >= 0;
+        const T2Pass &tp = gj ? *cp.t2[i].genv : cp.t2[i];
+        T2Args &a = ga.pass[j];
+        t2_fill_args(tp, t2_device(dev, gj ? cp.up[i].gen : cp.up[i].main), h->n, &a);
+        if (!t2_block_runs(&a, tp.gmask, g.bmask, h->n))
+            return fail(SV_ERR_STATE, "internal: tile index runs of an L2 block do not fit");
+        if (gj) t2_set_gen(h, tp, gen, &a);
+        a.tables = reinterpret_cast<const float2 *>(h->t2_tables);
+        a.err = h->t2_err;
+        a.keep = j + 1 < g.count;
+        need |= t2_gate_kinds(tp);
+        ngates += cp.plan.passes[i].ngates;
+        nins += (int)tp.ins.size();
+        nfac += (int)tp.fac2.size();
+        nstages += (int)tp.stages.size();
+        feat |= ~cp.plan.passes[i].gmask;
+    }
+    const uint64_t nblocks = UINT64_C(1) << (h->n - g.l);
+    const size_t ncnt = (size_t)nblocks * g.count;
+    const size_t need_bytes = 256 + ncnt * sizeof(unsigned);
+    if (need_bytes > h->grp_cap) {
+        if (h->grp) {
+            SV_CUDA(cudaStreamSynchronize(h->stream));
+            cudaFree(h->grp);
+        }
+        h->grp = nullptr;
+        h->grp_cap = 0;
+        const size_t cap = std::max<size_t>(2 * need_bytes, (size_t)1 << 16);
+        if (dev_malloc(&h->grp, cap) != cudaSuccess) {
+            cudaGetLastError();
+            h->grp = nullptr;
+            return fail(SV_ERR_OOM, "cannot allocate the L2 block counters (%zu bytes)", cap);
+        }
+        h->grp_cap = cap;
+    }
+    SV_CUDA(cudaMemsetAsync(h->grp, 0, need_bytes, h->stream));
+    ga.queue = reinterpret_cast<unsigned long long *>(h->grp);
+    ga.done = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(h->grp) + 256);
+    ga.segs = reinterpret_cast<const uint32_t *>(dev + cp.group_segs[gi]);
+    ga.npass = g.count;
+    ga.tpb_log = g.l - kT2Qubits;
+    ga.chunk_log = g.chunk_log;
+    ga.nitems = (uint64_t)g.segs.size() << ga.tpb_log;
+    ga.err = h->t2_err;
+
+    sv_launch_record meta{};
+    meta.kind = SV_KERNEL_L2BLOCK;
+    meta.pass = h->launch_index++;
+    meta.n = h->n;
+    meta.k = g.l;
+    meta.c = cp.plan.passes[g.first].c;
+    meta.nops = g.count;
+    meta.ngates = ngates;
+    meta.dtype = (int32_t)h->dt;
+    meta.gate_kind = -5;
+    // HBM: the group's first read (none for a generated state) and last write
+    meta.bytes = (gen >= 0 ? 1.0 : 2.0) * (double)state_bytes(h);
+    meta.feat = feat & ((h->n >= 64) ? ~UINT64_C(0) : ((UINT64_C(1) << h->n) - 1));
+    meta.stages = nstages;
+    meta.nins = nins;
+    meta.nfactors = nfac;
+    SV_TRY(t2_group_launch(h, ga, need, meta));
+    if (gen >= 0) {
+        h->basis = -1;
+        h->basis_h = 0;
+    }
+    h->stats.passes += g.count;
+    h->stats.touched_bytes += meta.bytes;
+    return SV_OK;
+}
+
 sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, const sv_config &cfg,
                             const PlanOverride *ov) {
     const bool dbl = h->dt == SV_C128;
@@ -604,6 +717,12 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
         }
         if (!p.remap_before.empty()) SV_TRY(remap_apply(h, p.remap_before));
         if (p.ops.empty()) continue;
+        if (cp->group_at[i] >= 0) {  // an L2 block group: its passes in one launch
+            const int gi = cp->group_at[i];
+            SV_TRY(group_apply(h, *cp, gi));
+            i += (size_t)cp->groups[gi].count - 1;
+            continue;
+        }
         sv_launch_record meta = describe_pass(h->n, h->dt, p, up[i].t2 ? &t2[i] : nullptr,
                                               up[i].t3 ? PK_T3 : up[i].t2 ? PK_T2 : PK_GENERIC);
         meta.pass = h->launch_index++;

@@ -54,7 +54,11 @@ struct Geo {
     static constexpr size_t kOffEpi = kOffLay + (size_t)kT2SmemStages * sizeof(T2LayoutX);
     static constexpr size_t kOffOnes = kOffEpi + sizeof(T2Epilogue);  // the identity phase table
     static constexpr size_t kOffBar = kOffOnes + 16 * 16;
-    static constexpr size_t kSmemBytes = kOffBar + 16;
+    // a claimed work item (L2 block and batched kernels).  No kernel here
+    // declares static shared memory: it would sit before the 1024-byte
+    // aligned dynamic area and push two CTAs past the SM's shared memory.
+    static constexpr size_t kOffClaim = kOffBar + 16;
+    static constexpr size_t kSmemBytes = kOffClaim + 16;
 };
 using G13 = Geo<13>;
 constexpr size_t kSmemBytes = G13::kSmemBytes;
@@ -303,7 +307,11 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, uint64_t
                 ph = thread_factor(fd);
         }
     };
-    for (int pc = 0; pc < a.nins; pc++) {
+    // loop bounds in registers: `a` may live in memory the compiler cannot
+    // prove unchanged by the tile's shared-memory stores (the L2 block kernel
+    // indexes its passes' arguments)
+    const int nins = a.nins, last_stage = a.last_stage;
+    for (int pc = 0; pc < nins; pc++) {
         const int4 w = ins[pc];
         // all ones at run time (the handler code is below 256), opaque to the
         // compiler (see reg_h2)
@@ -363,7 +371,7 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, uint64_t
                 __syncwarp();
                 if ((tid & 31) == 0) mbar_arrive(rbar);
                 rd++;
-                if (pc == a.last_stage) hook();
+                if (pc == last_stage) hook();
                 continue;
             }
             case kT2HdScale: {
@@ -472,6 +480,15 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, uint64_t
     const T2Epilogue *E = reinterpret_cast<const T2Epilogue *>(t2_dyn_smem + G::kOffEpi);
     const uint64_t g0 = base + E->glo[tid & 31] + E->ghi[tid >> 5];
     const uint64_t g1 = E->g[0], g2 = E->g[1], g3 = E->g[2], g4 = E->g[3];
+    if (a.keep) {  // the next pass of an L2 block reads it: plain stores
+#pragma unroll
+        for (int q = 0; q < kNP2; q++) {
+            const uint64_t g = g0 + ((q & 1) ? g1 : 0) + ((q & 2) ? g2 : 0) + ((q & 4) ? g3 : 0) +
+                               ((q & 8) ? g4 : 0);
+            gstate[g >> 1] = make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y);
+        }
+        return;
+    }
 #pragma unroll
     for (int q = 0; q < kNP2; q++) {
         const uint64_t g = g0 + ((q & 1) ? g1 : 0) + ((q & 2) ? g2 : 0) + ((q & 4) ? g3 : 0) +
@@ -611,6 +628,134 @@ __global__ void __launch_bounds__(Geo<K>::kThreads, K == kT2Qubits ? 2 : 1)
     }
 }
 
+// ---------------------------------------------------------------- L2 blocks
+// Two-level blocking (Sec. III-B, the block sized by the last-level cache):
+// the passes of a group run in one launch over blocks of 2^l amplitudes.
+// Persistent CTAs claim tiles from one queue in the order of G.segs, where
+// pass p of block b comes G.lag steps after pass p-1 of block b: by the time
+// it is claimed the block's previous pass has almost always finished, and
+// its result is still in L2 (written with plain stores; the group's last
+// pass streams its result out).  A tile of pass p >= 1 starts its bulk copies
+// once the (block, p-1) counter shows all of that pass's tiles done:
+//   - at the hook of the tile before it if the counter is already full
+//     there (the usual case: the copies overlap that tile's end);
+//   - otherwise at the top of its own iteration, after the CTA has finished
+//     and counted its previous tile, with a bounded wait on the counter.
+// Claim order is a topological order of the dependencies and only running
+// CTAs claim, so the wait at the top always ends; a CTA never waits for a
+// tile it holds itself.
+template <int F>
+__global__ void __launch_bounds__(kT2Threads, 2)
+    k_group(float *__restrict__ state, const __grid_constant__ GroupArgs G) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    float2 *tab = reinterpret_cast<float2 *>(sm + G13::kOffTab);
+    float2 *slotc = reinterpret_cast<float2 *>(sm + G13::kOffSlotc);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + G13::kOffBar);
+    uint64_t *rbar = bar + 1;
+    unsigned long long &s_next = *reinterpret_cast<unsigned long long *>(sm + G13::kOffClaim);
+    const int tid = threadIdx.x;
+    const unsigned tpb = 1u << G.tpb_log;
+    for (int i = tid; i < kTabEntries; i += blockDim.x) tab[i] = G.pass[0].tables[i];
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init(rbar, G13::kWarps);
+        fence_mbar_init();
+        s_next = atomicAdd(G.queue, 1ull) << G.chunk_log;
+    }
+    __syncthreads();
+    // item q: tile (q mod tpb) of the (block, pass) segment q / tpb; a claim
+    // takes the 2^chunk_log consecutive items of one chunk
+    const unsigned long long cmask = (1ull << G.chunk_log) - 1ull;
+    auto decode = [&](unsigned long long q, int &p, uint32_t &b, uint32_t &t) -> bool {
+        if (q >= G.nitems) return false;
+        const uint32_t s = __ldg(G.segs + (q >> G.tpb_log));
+        p = (int)(s & 7u);
+        b = s >> 3;
+        t = (uint32_t)q & (tpb - 1u);
+        return true;
+    };
+    auto tile_of = [&](uint32_t b, uint32_t t) { return (uint64_t)t | ((uint64_t)b << G.tpb_log); };
+    int p = 0;
+    uint32_t b = 0, t = 0;
+    unsigned long long q = s_next;
+    bool have = decode(q, p, b, t);
+    bool issued = false;    // warp 0: this item's copies were started at the previous hook
+    bool inflight = false;  // warp 0: this item's copies are in flight
+    int loaded = -1;        // the pass whose programme is in shared memory
+    long long sig = -1;     // the counter the previous item raises (-1: none)
+    uint32_t parity = 0, rd = 0, buf = 0;
+    for (;;) {
+        // the previous item's write-back is complete in every thread, and
+        // no thread reads the programme area any more
+        fence_async_global();
+        __syncthreads();
+        if (tid == 0 && sig >= 0) {
+            __threadfence();
+            atomicAdd(G.done + sig, 1u);
+        }
+        if (!have) break;
+        const T2Args &a = G.pass[p];
+        if (p != loaded) {
+            load_programme<kT2Qubits>(a, sm, tid, blockDim.x);
+            loaded = p;
+        }
+        if (tid < 32) {
+            inflight = issued;
+            if (!issued && !a.gen) {
+                bool ok = true;
+                if (tid == 0 && p > 0)
+                    ok = wait_count(G.done + (size_t)b * G.npass + (p - 1), tpb, G.err);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (ok) {
+                    fence_async_global();
+                    issue_tile_load<kT2Qubits>(a, sm, state, tile_of(b, t), bar, tid);
+                    inflight = true;
+                } else if (tid == 0) {
+                    atomicExch(G.err, 1);
+                }
+            }
+            if (tid == 0) s_next = ((q + 1) & cmask) ? q + 1 : (atomicAdd(G.queue, 1ull) << G.chunk_log);
+        }
+        const uint64_t base = tile_base(a, tile_of(b, t));
+        float2 *sc = slotc + buf * kT2MaxSlots;
+        tile_slots<kT2Qubits>(a, tab, sc, base, tid);
+        const bool timed_out = a.gen ? false : !mbar_wait(bar, parity);
+        if (__syncthreads_or(timed_out)) {
+            if (tid == 0) atomicExch(G.err, 1);
+            if (tid < 32 && inflight) mbar_wait(bar, parity);  // a second bounded wait for copies in flight
+            return;
+        }
+        int np = 0;
+        uint32_t nb = 0, nt = 0;
+        const unsigned long long nq = s_next;
+        const bool nhave = decode(nq, np, nb, nt);
+        bool nissued = false;
+        auto hook = [&]() {
+            if (tid < 32 && nhave && !G.pass[np].gen) {
+                bool ok = true;
+                if (tid == 0 && np > 0) ok = ld_acquire(G.done + (size_t)nb * G.npass + (np - 1)) >= tpb;
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (ok) {
+                    if (!mbar_wait(rbar, (rd - 1u) & 1u)) atomicExch(G.err, 1);
+                    fence_async_global();
+                    issue_tile_load<kT2Qubits>(G.pass[np], sm, state, tile_of(nb, nt), bar, tid);
+                    nissued = true;
+                }
+            }
+        };
+        t2_run<kT2Qubits, F>(a, reinterpret_cast<float4 *>(state), rbar, rd, base, sc, hook);
+        sig = p + 1 < G.npass ? (long long)b * G.npass + p : -1;
+        if (!a.gen) parity ^= 1u;
+        buf ^= 1u;
+        q = nq;
+        p = np;
+        b = nb;
+        t = nt;
+        have = nhave;
+        issued = nissued;
+    }
+}
+
 // ---------------------------------------------------------------- batched instances
 // One CTA runs whole instances taken from a shared queue (largest first): all
 // passes of the instance (the first pass starts from |0...0> in shared memory
@@ -623,7 +768,7 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
     float2 *slotc = reinterpret_cast<float2 *>(sm + G13::kOffSlotc);
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + G13::kOffBar);
     uint64_t *rbar = bar + 1;
-    __shared__ int s_item;
+    int &s_item = *reinterpret_cast<int *>(sm + G13::kOffClaim);
     // read-out reduction scratch lives in the tile buffer (free after the last pass)
     double *s_val = reinterpret_cast<double *>(sm);
     uint64_t *s_idx = reinterpret_cast<uint64_t *>(sm + 8 * kT2Threads);
@@ -800,6 +945,9 @@ sv_status t2_prepare(sv_state *h) {
         for (auto kern : {k_tile2<14, 0>, k_tile2<14, kFeatX>, k_tile2<14, kFeatR>, k_tile2<14, kFeatAll>})
             SV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Geo<14>::kSmemBytes));
+        for (auto kern : {k_group<0>, k_group<kFeatX>, k_group<kFeatR>, k_group<kFeatAll>})
+            SV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Geo<13>::kSmemBytes));
         configured = true;
     }
     return SV_OK;
@@ -846,32 +994,55 @@ void t2_fill_args(const T2Pass &p, const T2Device &d, int n, T2Args *a) {
     a->epi = d.epi;
 }
 
+bool t2_block_runs(T2Args *a, uint64_t gmask, uint64_t bmask, int n) {
+    const uint64_t all = n >= 64 ? ~UINT64_C(0) : ((UINT64_C(1) << n) - 1);
+    int pos[64], np = 0;
+    for (int q = 0; q < n; q++)
+        if (((gmask & bmask & all) >> q) & 1) pos[np++] = q;
+    for (int q = 0; q < n; q++)
+        if (((gmask & ~bmask & all) >> q) & 1) pos[np++] = q;
+    a->ngr = 0;
+    for (int i = 0; i < np;) {
+        int e = i + 1;
+        while (e < np && pos[e] == pos[e - 1] + 1) e++;
+        if (a->ngr == 32) return false;
+        a->gs[a->ngr] = (int8_t)i;
+        a->gd[a->ngr] = (int8_t)pos[i];
+        a->gl[a->ngr] = (int8_t)(e - i);
+        a->ngr++;
+        i = e;
+    }
+    return true;
+}
+
+void t2_set_gen(const sv_state *h, const T2Pass &p, int64_t gen_basis, T2Args *a) {
+    // the programme's leading Hadamards P (unnormalised, tile bits) applied
+    // to the recorded product state H^{hq}|basis> (normalised Hadamards on
+    // the physical qubits of hq): on a qubit in both they give sqrt(2) I, so
+    // the generated state has Hadamards on P xor hq (its global ones decide
+    // presence and sign per tile) and magnitude 2^{(|P and hq| - |hq without P|) / 2}
+    a->gen = 1;
+    a->gen_basis = (uint64_t)gen_basis;
+    a->gen_local = 0;
+    uint32_t hq_local = 0;
+    for (int s = 0; s < p.k; s++) {
+        a->gen_local |= (int)((a->gen_basis >> p.slot_phys[s]) & 1) << s;
+        if ((h->basis_h >> p.slot_phys[s]) & 1) hq_local |= 1u << s;
+    }
+    a->gen_hmask = p.gen_hmask ^ hq_local;
+    a->gen_ghmask = h->basis_h & p.gmask;
+    const int both = __builtin_popcount(p.gen_hmask & hq_local);
+    const int hq_only = __builtin_popcountll(h->basis_h) - both;
+    a->gen_val = (float)std::pow(2.0, 0.5 * (both - hq_only));
+}
+
 sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta,
                     int64_t gen_basis) {
     if (p.format != 2) return fail(SV_ERR_ARG, "internal: register-stage pass not in format 2");
     SV_TRY(launch_check());
     T2Args a{};
     t2_fill_args(p, d, h->n, &a);
-    if (gen_basis >= 0) {
-        // the programme's leading Hadamards P (unnormalised, tile bits)
-        // applied to the recorded product state H^{hq}|basis> (normalised
-        // Hadamards on the physical qubits of hq): on a qubit in both they
-        // give sqrt(2) I, so the generated state has Hadamards on P xor hq
-        // (its global ones decide presence and sign per tile) and magnitude
-        // 2^{(|P and hq| - |hq without P|) / 2}
-        a.gen = 1;
-        a.gen_basis = (uint64_t)gen_basis;
-        uint32_t hq_local = 0;
-        for (int s = 0; s < p.k; s++) {
-            a.gen_local |= (int)((a.gen_basis >> p.slot_phys[s]) & 1) << s;
-            if ((h->basis_h >> p.slot_phys[s]) & 1) hq_local |= 1u << s;
-        }
-        a.gen_hmask = p.gen_hmask ^ hq_local;
-        a.gen_ghmask = h->basis_h & p.gmask;
-        const int both = __builtin_popcount(p.gen_hmask & hq_local);
-        const int hq_only = __builtin_popcountll(h->basis_h) - both;
-        a.gen_val = (float)std::pow(2.0, 0.5 * (both - hq_only));
-    }
+    if (gen_basis >= 0) t2_set_gen(h, p, gen_basis, &a);
     a.tables = reinterpret_cast<const float2 *>(h->t2_tables);
     a.err = h->t2_err;
     if (p.k != 13 && p.k != 14) return fail(SV_ERR_ARG, "internal: register-stage tile of 2^%d", p.k);
@@ -891,9 +1062,30 @@ sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
     int per_sm = 0;
     SV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) return fail(SV_ERR_UNSUPPORTED, "register-stage tile kernel does not fit");
+    h->stats.ctas_per_sm = h->stats.ctas_per_sm ? std::min(h->stats.ctas_per_sm, per_sm) : per_sm;
     const uint64_t grid = std::min<uint64_t>(a.ntiles, (uint64_t)per_sm * h->sm_count);
     const int slot = prof_begin(h);
     kern<<<(unsigned)grid, threads, smem, h->stream>>>(reinterpret_cast<float *>(h->amps), a);
+    SV_CUDA(cudaGetLastError());
+    note_launch();
+    prof_end(h, slot, meta);
+    h->stats.kernels++;
+    return SV_OK;
+}
+
+sv_status t2_group_launch(sv_state *h, const GroupArgs &g, int need, const sv_launch_record &meta) {
+    SV_TRY(launch_check());
+    auto kern = need == 0 ? k_group<0>
+              : need == kFeatX ? k_group<kFeatX>
+              : need == kFeatR ? k_group<kFeatR>
+                               : k_group<kFeatAll>;
+    int per_sm = 0;
+    SV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kT2Threads, kSmemBytes));
+    if (per_sm < 1) return fail(SV_ERR_UNSUPPORTED, "L2 block kernel does not fit on an SM");
+    h->stats.ctas_per_sm = h->stats.ctas_per_sm ? std::min(h->stats.ctas_per_sm, per_sm) : per_sm;
+    const uint64_t grid = std::min<uint64_t>(g.nitems, (uint64_t)per_sm * h->sm_count);
+    const int slot = prof_begin(h);
+    kern<<<(unsigned)grid, kT2Threads, kSmemBytes, h->stream>>>(reinterpret_cast<float *>(h->amps), g);
     SV_CUDA(cudaGetLastError());
     note_launch();
     prof_end(h, slot, meta);

@@ -75,6 +75,28 @@ __device__ __forceinline__ void bulk_wait_read() {
 __device__ __forceinline__ void fence_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// Order this thread's generic-proxy accesses of global memory with the bulk
+// copies (async proxy) that follow.
+__device__ __forceinline__ void fence_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+// Wait until *p >= want, with a time limit (2 s), giving up early once *err
+// is set (another CTA gave up); false if it gave up.
+__device__ __forceinline__ bool wait_count(const unsigned *p, unsigned want, const int *err) {
+    if (ld_acquire(p) >= want) return true;
+    const uint64_t t0 = now_ns();
+    for (;;) {
+        __nanosleep(128);
+        if (ld_acquire(p) >= want) return true;
+        if (*(volatile const int *)err) return false;
+        if (now_ns() - t0 > 2000000000ull) return false;
+    }
+}
 
 __device__ __forceinline__ uint64_t pdep(uint64_t v, uint64_t mask) {
     uint64_t r = 0;

@@ -25,6 +25,7 @@ SV_FLAG_NO_DIAG_MERGE, SV_FLAG_PAPER_SWAP, SV_FLAG_NO_RELABEL, SV_FLAG_GENERIC_T
 SV_FLAG_NO_PLAN_CACHE = 16
 SV_FLAG_EARLY_DIAG = 32
 SV_FLAG_GREEDY_ONLY = 64
+SV_FLAG_L2_BLOCKS = 128
 SV_PLANNER_GREEDY, SV_PLANNER_LEARNED = 0, 1
 
 EXPORTS = (
@@ -42,7 +43,7 @@ EXPORTS = (
 )
 SV_FAULT_ALLOC, SV_FAULT_UPLOAD, SV_FAULT_LAUNCH = 0, 1, 2
 SV_COST_FEATURES, SV_COST_HIDDEN, SV_COST_PARAMS = 52, 64, 7617
-SV_KERNEL_PERGATE, SV_KERNEL_TILE, SV_KERNEL_REMAP, SV_KERNEL_FUSED = 0, 1, 2, 3
+SV_KERNEL_PERGATE, SV_KERNEL_TILE, SV_KERNEL_REMAP, SV_KERNEL_FUSED, SV_KERNEL_L2BLOCK = 0, 1, 2, 3, 4
 
 
 class LibraryMissing(RuntimeError):
@@ -59,7 +60,8 @@ class sv_config(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("tile_qubits", ctypes.c_int32),
                 ("chunk_qubits", ctypes.c_int32), ("fuse_qubits", ctypes.c_int32),
                 ("planner", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 10)]
+                ("l2_qubits", ctypes.c_int32), ("l2_chunk", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 8)]
 
 
 class sv_stats(ctypes.Structure):
@@ -68,7 +70,8 @@ class sv_stats(ctypes.Structure):
                 ("relabels", ctypes.c_int32), ("fused_blocks", ctypes.c_int32),
                 ("sweep_bytes", ctypes.c_double), ("touched_bytes", ctypes.c_double),
                 ("h2d_bytes", ctypes.c_double), ("planner", ctypes.c_int32),
-                ("candidates", ctypes.c_int32), ("predicted_ms", ctypes.c_double)]
+                ("candidates", ctypes.c_int32), ("predicted_ms", ctypes.c_double),
+                ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -194,8 +197,8 @@ def sv_last_error() -> str:
 
 
 def make_config(mode=SV_MODE_AUTO, tile_qubits=0, chunk_qubits=0, fuse_qubits=0,
-                planner=SV_PLANNER_GREEDY, flags=0) -> sv_config:
-    return sv_config(mode, tile_qubits, chunk_qubits, fuse_qubits, planner, flags)
+                planner=SV_PLANNER_GREEDY, flags=0, l2_qubits=0, l2_chunk=0) -> sv_config:
+    return sv_config(mode, tile_qubits, chunk_qubits, fuse_qubits, planner, flags, l2_qubits, l2_chunk)
 
 
 # ---- handle-level functions (same names as the C ABI) ------------------------

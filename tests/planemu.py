@@ -114,13 +114,15 @@ def _expi32(u):
     return np.exp(2j * np.pi * ((u & MASK32) / 2.0 ** 32))
 
 
-def run_t2_pass(state, p, t2=None, gen_basis=None, gen_h=0):
+def run_t2_pass(state, p, t2=None, gen_basis=None, gen_h=0, bases=None):
     """Execute a register-stage pass.  `t2` defaults to the pass's programme;
     with `gen_basis` (a physical basis index) the pass starts from the product
     state H^{gen_h}|gen_basis> (H on the physical qubits of the mask gen_h)
     and generates its tiles instead of reading them (the programme is then the
     pass's generated-state variant, `t2gen`, whose own leading Hadamards on
-    tile bits are unnormalised: its closing scale holds their 2^(-1/2))."""
+    tile bits are unnormalised: its closing scale holds their 2^(-1/2)).
+    `bases`: run only the tiles with these physical base indices, in order
+    (default: every tile, in index order)."""
     t2 = t2 if t2 is not None else p["t2"]
     fmt = t2.get("format", 1)
     k = p["k"]
@@ -133,8 +135,7 @@ def run_t2_pass(state, p, t2=None, gen_basis=None, gen_h=0):
         sc = np.asarray(t2["statc"], dtype=np.float64).reshape(-1, nthreads, 2)
         statc = sc[:, :, 0] + 1j * sc[:, :, 1]
     nstages = sum(1 for ins in t2["ins"] if ins["op"] == T2_STAGE)
-    for tile in range(ntiles):
-        base = pdep(tile, p["gmask"])
+    for base in (bases if bases is not None else (pdep(t_, p["gmask"]) for t_ in range(ntiles))):
         idx = tile_index(p, base)
         if gen_basis is None:
             t = state[idx].copy()
@@ -348,14 +349,46 @@ def product_state(n, basis, hq):
     return np.where(((x ^ basis) & ~hq) == 0, np.where(par == 1, -v, v), 0.0).astype(complex)
 
 
-def run_plan(n, plan, use_gen=True, basis=0, hq=0):
+def group_bases(n, p, group, b, tpb_log):
+    """Physical tile bases of pass `p` inside block `b` of an L2 block group:
+    the tile index's low bits run over the pass's global qubits inside the
+    block, the block index over the qubits outside it."""
+    allm = (1 << n) - 1
+    inner = p["gmask"] & group["bmask"] & allm
+    outer = p["gmask"] & ~group["bmask"] & allm
+    return [pdep(t, inner) | pdep(b, outer) for t in range(1 << tpb_log)]
+
+
+def run_plan(n, plan, use_gen=True, basis=0, hq=0, l2_groups=False):
     """Run the exported plan from the product state H^{hq}|basis> (default
     |0...0>).  With `use_gen` the first pass runs its generated-state variant
     (`t2gen`, as the library does from a recorded state) when it has one;
-    otherwise every pass reads its state."""
+    otherwise every pass reads its state.  With `l2_groups` the passes of
+    each exported L2 block group run (block, pass) segment by segment in the
+    group's claim order."""
     state = product_state(n, basis, hq)
     first = True
-    for p in plan["passes"]:
+    groups = {g["first"]: g for g in plan.get("l2_groups", [])} if l2_groups else {}
+    skip = set()
+    for i, p in enumerate(plan["passes"]):
+        if i in skip:
+            continue
+        if i in groups:
+            g = groups[i]
+            if p.get("remap_before"):
+                state = remap(state, p["remap_before"])
+            tpb_log = g["l"] - p["k"]
+            for s in g["segs"]:
+                b, j = s >> 3, s & 7
+                pj = plan["passes"][i + j]
+                bases = group_bases(n, pj, g, b, tpb_log)
+                if j == 0 and first and use_gen and "t2gen" in pj:
+                    run_t2_pass(state, pj, pj["t2gen"], gen_basis=basis, gen_h=hq, bases=bases)
+                else:
+                    run_t2_pass(state, pj, bases=bases)
+            skip.update(range(i + 1, i + g["count"]))
+            first = False
+            continue
         if p.get("general"):
             run_general(state, p["general"])
             first = False
