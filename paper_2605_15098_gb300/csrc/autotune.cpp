@@ -5,7 +5,9 @@
 // execution mode (per-gate sweeps, register-stage tiles on the CUDA cores,
 // tiles with tensor-core fused blocks), the chunk width c of the bulk copies
 // (how many low qubits every tile holds contiguously, 2^c amplitudes), and
-// the tile width k (2^13 or 2^14 amplitudes for complex64).  Each candidate runs the circuit from
+// the tile width k (2^13 or 2^14 amplitudes for complex64), and, for states
+// larger than L2, the two-level blocking of consecutive passes through L2
+// (SV_FLAG_L2_BLOCKS at the default block size).  Each candidate runs the circuit from
 // |0...0> once to warm up and three times under CUDA events; the median wins.
 // Results can be cached in a text file keyed by the circuit's structure
 // (gate kinds and qubits, not their angles), n and the dtype.
@@ -46,13 +48,17 @@ bool cache_lookup(const char *path, uint64_t key, sv_config *cfg, double *ms) {
     bool found = false;
     while (fgets(line, sizeof line, f)) {
         unsigned long long k;
-        int mode, tile, chunk;
+        int mode, tile, chunk, flags, l2c;
         double t;
-        if (sscanf(line, "%llx %d %d %d %lf", &k, &mode, &tile, &chunk, &t) == 5 && k == key) {
+        // key, mode, tile and chunk qubits, flags, L2 tiles per claim, median ms
+        if (sscanf(line, "%llx %d %d %d %d %d %lf", &k, &mode, &tile, &chunk, &flags, &l2c, &t) == 7 &&
+            k == key) {
             *cfg = sv_config{};
             cfg->mode = mode;
             cfg->tile_qubits = tile;
             cfg->chunk_qubits = chunk;
+            cfg->flags = flags;
+            cfg->l2_chunk = l2c;
             *ms = t;
             found = true;  // last entry wins
         }
@@ -65,8 +71,8 @@ void cache_store(const char *path, uint64_t key, const sv_config &cfg, double ms
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%016llx %d %d %d %.6f\n", (unsigned long long)key, cfg.mode, cfg.tile_qubits,
-            cfg.chunk_qubits, ms);
+    fprintf(f, "%016llx %d %d %d %d %d %.6f\n", (unsigned long long)key, cfg.mode, cfg.tile_qubits,
+            cfg.chunk_qubits, cfg.flags, cfg.l2_chunk, ms);
     fclose(f);
 }
 
@@ -101,6 +107,12 @@ extern "C" sv_status sv_autotune(sv_handle h, const sv_gate *host_gates, size_t 
             add(SV_MODE_PARTITIONED, 0, c);
             cands.back().flags = SV_FLAG_EARLY_DIAG;
         }
+        if ((size_t)state_bytes(h) > (size_t)std::max(h->l2_bytes, 1))
+            for (int c : {5, 7}) {  // consecutive passes block by block through L2
+                add(SV_MODE_PARTITIONED, 0, c);
+                cands.back().flags = SV_FLAG_L2_BLOCKS;
+                cands.back().l2_chunk = 4;
+            }
         if (h->n > 14)  // 2^14-amplitude tiles: fewer passes, one CTA per SM
             for (int c : {4, 5, 7}) add(SV_MODE_PARTITIONED, 14, c);
         if (h->n > 13)

@@ -15,7 +15,7 @@
 
 namespace sv {
 
-constexpr int kMaxGroupPasses = 8;
+constexpr int kMaxGroupPasses = 4;
 
 struct L2Group {
     int first = 0, count = 0;    // passes [first, first + count) of the plan

@@ -58,7 +58,9 @@ struct Geo {
     // declares static shared memory: it would sit before the 1024-byte
     // aligned dynamic area and push two CTAs past the SM's shared memory.
     static constexpr size_t kOffClaim = kOffBar + 16;
-    static constexpr size_t kSmemBytes = kOffClaim + 16;
+    // the current pass's arguments (L2 block kernel)
+    static constexpr size_t kOffArgs = kOffClaim + 16;
+    static constexpr size_t kSmemBytes = kOffArgs + ((sizeof(T2Args) + 15) / 16) * 16;
 };
 using G13 = Geo<13>;
 constexpr size_t kSmemBytes = G13::kSmemBytes;
@@ -685,19 +687,27 @@ __global__ void __launch_bounds__(kT2Threads, 2)
     long long sig = -1;     // the counter the previous item raises (-1: none)
     uint32_t parity = 0, rd = 0, buf = 0;
     for (;;) {
-        // the previous item's write-back is complete in every thread, and
-        // no thread reads the programme area any more
-        fence_async_global();
-        __syncthreads();
-        if (tid == 0 && sig >= 0) {
-            __threadfence();
-            atomicAdd(G.done + sig, 1u);
+        // a previous item that a later pass reads is counted once its
+        // write-back is complete in every thread; a pass change needs every
+        // thread past the previous item's use of the programme area
+        if (sig >= 0 || (have && p != loaded)) {
+            if (sig >= 0) fence_async_global();
+            __syncthreads();
+            if (tid == 0 && sig >= 0) {
+                __threadfence();
+                atomicAdd(G.done + sig, 1u);
+            }
         }
         if (!have) break;
-        const T2Args &a = G.pass[p];
+        // the pass's arguments, copied next to its programme: shared-memory
+        // loads instead of loads from the parameter block at a run-time index
+        T2Args &a = *reinterpret_cast<T2Args *>(sm + G13::kOffArgs);
         if (p != loaded) {
-            load_programme<kT2Qubits>(a, sm, tid, blockDim.x);
+            for (int i = tid; i < (int)(sizeof(T2Args) / 4); i += blockDim.x)
+                reinterpret_cast<int *>(&a)[i] = reinterpret_cast<const int *>(&G.pass[p])[i];
+            load_programme<kT2Qubits>(G.pass[p], sm, tid, blockDim.x);
             loaded = p;
+            __syncthreads();
         }
         if (tid < 32) {
             inflight = issued;
@@ -706,6 +716,8 @@ __global__ void __launch_bounds__(kT2Threads, 2)
                 if (tid == 0 && p > 0)
                     ok = wait_count(G.done + (size_t)b * G.npass + (p - 1), tpb, G.err);
                 ok = __shfl_sync(0xffffffffu, ok, 0);
+                // every warp has read the previous item's last layout
+                if (ok && rd && !mbar_wait(rbar, (rd - 1u) & 1u)) ok = false;
                 if (ok) {
                     fence_async_global();
                     issue_tile_load<kT2Qubits>(a, sm, state, tile_of(b, t), bar, tid);

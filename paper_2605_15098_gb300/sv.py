@@ -517,7 +517,8 @@ def config_dict(c: sv_config) -> dict:
     names = {SV_MODE_AUTO: "auto", SV_MODE_PERGATE: "per-gate", SV_MODE_PARTITIONED: "partitioned",
              SV_MODE_FUSED: "fused"}
     return {"mode": names.get(c.mode, c.mode), "tile_qubits": c.tile_qubits,
-            "chunk_qubits": c.chunk_qubits, "planner": c.planner, "flags": c.flags}
+            "chunk_qubits": c.chunk_qubits, "planner": c.planner, "flags": c.flags,
+            "l2_qubits": c.l2_qubits, "l2_chunk": c.l2_chunk}
 
 
 def sv_launch_count() -> int:

@@ -50,7 +50,7 @@ def test_qpe_parity_and_identical_to_one_level(sv, orc, n, l2):
     grouped = [r for r in recs if r["kind"] == sv.SV_KERNEL_L2BLOCK]
     assert st2["kernels"] == st1["kernels"] - sum(r["nops"] - 1 for r in grouped)
     # the default block size follows the device's L2 size
-    assert all(2 <= r["nops"] <= 8 and r["k"] == (min(l2, n) if l2 else min(r["k"], n)) and r["k"] >= 14
+    assert all(2 <= r["nops"] <= 4 and r["k"] == (min(l2, n) if l2 else min(r["k"], n)) and r["k"] >= 14
                for r in grouped)
 
 
@@ -93,3 +93,19 @@ def test_readout_after_groups(sv, orc):
         recs = sv.sv_profile_read(s.h)
     assert idx == info["y"] and p > 0.99
     assert any(r["kind"] == sv.SV_KERNEL_L2BLOCK for r in recs)
+
+
+def test_autotune_with_l2_candidates(sv, tmp_path):
+    """A state larger than L2: the autotuner also measures L2 block groups;
+    whatever it picks reproduces the QPE outcome and comes back from its
+    cache with the same flags."""
+    n = 24
+    g, _, info = C.qpe(n, seed=2)
+    cache = str(tmp_path / "tune.txt")
+    with sv.State(n, sv.SV_C64) as s:
+        best, ms = sv.sv_autotune(s.h, g, cache)
+        best2, _ = sv.sv_autotune(s.h, g, cache)
+        assert (best2.flags, best2.l2_chunk, best2.chunk_qubits) == (best.flags, best.l2_chunk, best.chunk_qubits)
+        s.apply(g, best)
+        idx, p = s.argmax(info["mask"])
+    assert idx == info["y"] and p > 0.99

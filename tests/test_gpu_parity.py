@@ -385,8 +385,8 @@ def test_autotune_picks_a_valid_config(sv, orc, tmp_path):
         best, ms = sv.sv_autotune(s.h, g, cache)
         assert ms > 0 and best.mode in (sv.SV_MODE_PARTITIONED, sv.SV_MODE_FUSED)
         best2, ms2 = sv.sv_autotune(s.h, g, cache)  # cache hit: same answer
-        assert (best2.mode, best2.chunk_qubits, best2.tile_qubits) == \
-            (best.mode, best.chunk_qubits, best.tile_qubits)
+        assert (best2.mode, best2.chunk_qubits, best2.tile_qubits, best2.flags, best2.l2_chunk) == \
+            (best.mode, best.chunk_qubits, best.tile_qubits, best.flags, best.l2_chunk)
         assert abs(ms2 - ms) < 1e-3
         s.apply(g, best)
         idx, p = s.argmax(info["mask"])

@@ -34,7 +34,7 @@ def bits(qs):
 def check_structure(plan, n):
     for g in plan["l2_groups"]:
         passes = plan["passes"][g["first"]:g["first"] + g["count"]]
-        assert 2 <= g["count"] <= 8
+        assert 2 <= g["count"] <= 4
         assert all(p["kernel"] == "t2" and p["k"] == 13 and p["ops"] for p in passes)
         assert all(not p["remap_before"] and not p.get("general") for p in passes[1:])
         union = 0
