@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the QPE n = 20..32 sweep")
     ap.add_argument("--no-random", action="store_true", help="skip the random-circuit n = 30, 32 timing")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the errors against the oracle")
+    ap.add_argument("--no-l2", action="store_true", help="skip the L2 block group timing")
+    ap.add_argument("--l2-sweep", type=int, default=0, metavar="N",
+                    help="only run QPE-N once per L2 block size (for an ncu capture) and print its launches")
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -322,6 +325,77 @@ def random_circuits(sv, C, stream, peak: float) -> dict:
     return res
 
 
+L2_SWEEP = (0, 16, 18, 20, 22, 24)
+
+
+def l2_sweep(n: int) -> None:
+    """QPE-n, complex64, chunk 7: one run per L2 block size (0 = no groups,
+    the one-level plan) after a reset, printing each run's launch records.
+    Meant to run under ncu, one launch per kernel and block size."""
+    from paper_2605_15098_gb300 import build as B
+    from paper_2605_15098_gb300 import circuits as C
+    B.build()
+    from paper_2605_15098_gb300 import sv
+    g, _, info = C.qpe(n)
+    h = sv.sv_create(n, sv.SV_C64)
+    rows = []
+    for l2 in L2_SWEEP:
+        flags = sv.SV_FLAG_L2_BLOCKS if l2 else 0
+        cfg = sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=7, flags=flags, l2_qubits=l2, l2_chunk=2)
+        sv.sv_profile(h, True)
+        sv.sv_reset(h)
+        sv.sv_apply_circuit(h, g, cfg)
+        idx, _ = sv.sv_argmax(h, info["mask"])
+        recs = sv.sv_profile_read(h)
+        sv.sv_profile(h, False)
+        rows.append({"l2_qubits": l2, "outcome_ok": idx == info["y"],
+                     "launches": [{"kind": r["kind"], "k": r["k"], "passes": r["nops"],
+                                   "ms": round(r["ms"], 4), "bytes": r["bytes"]} for r in recs]})
+    sv.sv_destroy(h)
+    print(json.dumps({"l2_sweep": f"QPE n={n} complex64 chunk 7", "rows": rows}))
+
+
+def l2_blocks(sv, C, stream) -> dict:
+    """Two-level blocking through L2 against the one-level plan: QPE-28
+    (chunk 7) and a random circuit at n = 30, depth 40, complex64.  Each
+    configuration: one warm-up, then the median of three (QPE) or one (random)
+    timed run of reset + apply + argmax under CUDA events."""
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+    for name, nn, g, chunk, mask, reps in (
+            ("qpe28", 28, C.qpe(28)[0], 7, C.qpe(28)[2]["mask"], 3),
+            ("random_n30_depth40", 30, C.random_circuit(30, 40), 0, (1 << 10) - 1, 1)):
+        buf = torch.empty(1 << nn, dtype=torch.complex64, device="cuda")
+        h = sv.sv_create_on(nn, sv.SV_C64, buf.data_ptr(), (1 << nn) * 8, stream.cuda_stream)
+        row = {}
+        for label, l2, l2c in (("one_level", 0, 0), ("l2_20_chunk4", 20, 4), ("l2_22_chunk4", 22, 4)):
+            cfg = sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=chunk,
+                                 flags=sv.SV_FLAG_L2_BLOCKS if l2 else 0, l2_qubits=l2, l2_chunk=l2c)
+            sv.sv_reset(h)
+            sv.sv_apply_circuit(h, g, cfg)
+            times, idxs = [], []
+            for _ in range(reps):
+                e0.record(stream)
+                sv.sv_reset(h)
+                sv.sv_apply_circuit(h, g, cfg)
+                idx, _ = sv.sv_argmax(h, mask)
+                e1.record(stream)
+                stream.synchronize()
+                times.append(e0.elapsed_time(e1))
+                idxs.append(int(idx))
+            st = sv.sv_last_stats(h)
+            row[label] = {"circuit_ms": round(sorted(times)[len(times) // 2], 3), "kernels": st["kernels"],
+                          "passes": st["passes"], "argmax": idxs[0]}
+        row["same_argmax"] = len({v["argmax"] for v in row.values()}) == 1
+        res[name] = row
+        sv.sv_destroy(h)
+        del buf
+        torch.cuda.empty_cache()
+    return res
+
+
 SWEEP_N = (20, 24, 28, 30, 32)
 
 
@@ -477,7 +551,7 @@ def run_ours(args, world, rank, local):
         # scheme, complex128, sweep, batch) run at N = 1 only, so that an
         # N-GPU run holds its GPUs for the replicated step and e2e alone
         args.no_other = args.no_pergate = args.no_paper = True
-        args.no_c128 = args.no_sweep = args.no_batch = args.no_random = True
+        args.no_c128 = args.no_sweep = args.no_batch = args.no_random = args.no_l2 = True
 
     from paper_2605_15098_gb300 import build as B
     from paper_2605_15098_gb300 import circuits as C
@@ -701,6 +775,10 @@ def run_ours(args, world, rank, local):
     if not args.no_random and dt == sv.SV_C64:
         out["random_circuits"] = random_circuits(sv, C, stream, peak)
 
+    # ---- two-level blocking through L2 against the one-level plan ----
+    if not args.no_l2 and dt == sv.SV_C64:
+        out["l2_blocks"] = l2_blocks(sv, C, stream)
+
     sweep_cfgs, batch_res = {}, None
     # ---- QPE sweep: n = 20 .. 32, complex64 and complex128, partitioned vs per-gate ----
     if not args.no_sweep and dt == sv.SV_C64:
@@ -803,6 +881,10 @@ def main():
     world, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.l2_sweep:
+        if rank == 0:
+            l2_sweep(args.l2_sweep)
         return
     run_ours(args, world, rank, local)
 
