@@ -59,7 +59,34 @@ struct Compiled {
     int nphys = 0;
     std::vector<T2Pass> passes;
     int phys[64];
+    int64_t basis = 0;     // the first pass generates H^{basis_h}|basis>
+    uint64_t basis_h = 0;
 };
+
+// X and H gates that come first on their qubit change only the starting
+// product state H^{hq}|b> (an X on a qubit that a folded H holds is kept):
+// the first pass generates that state instead of applying them.
+std::vector<sv_gate> fold_prefix(const sv_gate *g, size_t m, int64_t *basis, uint64_t *hq) {
+    bool touched[64] = {};
+    std::vector<sv_gate> out;
+    out.reserve(m);
+    for (size_t i = 0; i < m; i++) {
+        const sv_gate &a = g[i];
+        const uint64_t bit = UINT64_C(1) << a.target;
+        if (!touched[a.target] && a.kind == SV_X && !(*hq & bit)) {
+            *basis ^= (int64_t)bit;
+            continue;
+        }
+        if (!touched[a.target] && a.kind == SV_H) {
+            *hq ^= bit;
+            continue;
+        }
+        touched[a.target] = true;
+        if (is_controlled_kind(a.kind) || a.kind == SV_SWAP) touched[a.control] = true;
+        out.push_back(a);
+    }
+    return out;
+}
 
 void destroy(sv_batch_state *b) {
     if (!b) return;
@@ -128,21 +155,29 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
             opt.search = !(c.flags & SV_FLAG_GREEDY_ONLY);
             opt.relabel = true;
             opt.split_u3 = true;
-            for (int q = 0; q < 64; q++) cp.phys[q] = q;
-            Plan plan;
-            std::vector<sv_gate> gl(it.gates, it.gates + it.m);
-            cp.err = build_plan(gl, opt, cp.phys, &plan);
-            if (!cp.err.empty()) continue;
-            for (const TilePass &tp : plan.passes) {
-                if (tp.ops.empty()) continue;
-                T2Pass t2;
-                // the first pass generates |0...0> (and the leading Hadamards) in registers
-                std::string why = compile_t2v2(tp, &t2, cp.passes.empty());
-                if (!why.empty()) {
-                    cp.err = "pass cannot run on the register-stage kernel: " + why;
-                    break;
+            for (int fold = 1; fold >= 0; fold--) {
+                Plan plan;
+                cp.basis = 0;
+                cp.basis_h = 0;
+                std::vector<sv_gate> gl = fold ? fold_prefix(it.gates, it.m, &cp.basis, &cp.basis_h)
+                                               : std::vector<sv_gate>(it.gates, it.gates + it.m);
+                for (int q = 0; q < 64; q++) cp.phys[q] = q;
+                cp.passes.clear();
+                cp.err = build_plan(gl, opt, cp.phys, &plan);
+                if (!cp.err.empty()) break;
+                for (const TilePass &tp : plan.passes) {
+                    if (tp.ops.empty()) continue;
+                    T2Pass t2;
+                    // the first pass generates the starting product state in registers
+                    std::string why = compile_t2v2(tp, &t2, cp.passes.empty());
+                    if (!why.empty()) {
+                        cp.err = "pass cannot run on the register-stage kernel: " + why;
+                        break;
+                    }
+                    cp.passes.push_back(std::move(t2));
                 }
-                cp.passes.push_back(std::move(t2));
+                // a folded state with no pass left to generate it: plan the gates as given
+                if (!cp.err.empty() || !cp.passes.empty() || (cp.basis == 0 && cp.basis_h == 0)) break;
             }
         }
     };
@@ -190,18 +225,12 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
         cost[i] = (double)std::max<size_t>(1, cp.passes.size()) * (double)(UINT64_C(1) << cp.nphys);
         for (const T2Pass &t2 : cp.passes) {
             T2Args a{};
-            if (pass.size() == (size_t)bi.pass0) {  // the first pass generates |0...0>
-                a.gen = 1;
-                a.gen_basis = 0;
-                a.gen_local = 0;
-                a.gen_hmask = t2.gen_hmask;
-                a.gen_ghmask = 0;
-                a.gen_val = 1.f;
-            }
             {  // counts and geometry; the pointers are set once the blob is on the device
                 const T2Device none{};
                 t2_fill_args(t2, none, cp.nphys, &a);
             }
+            // the first pass generates the starting product state
+            if (pass.size() == (size_t)bi.pass0) t2_set_gen(t2, cp.basis, cp.basis_h, &a);
             Off o;
             o.ins = blob.put(t2.ins.data(), t2.ins.size() * sizeof(T2Ins));
             o.stages = blob.put(t2.stages.data(), t2.stages.size() * sizeof(T2Stage));

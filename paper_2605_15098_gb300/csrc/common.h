@@ -219,9 +219,9 @@ sv_status t2_prepare(sv_state *h);
 // instead of reading the buffer.
 sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta,
                     int64_t gen_basis = -1);
-// The generated-state fields of a first pass that starts from the recorded
-// product state (h->basis = gen_basis, h->basis_h).
-void t2_set_gen(const sv_state *h, const T2Pass &p, int64_t gen_basis, T2Args *a);
+// The generated-state fields of a first pass that starts from the product
+// state H^{basis_h}|gen_basis> (physical qubit masks).
+void t2_set_gen(const T2Pass &p, int64_t gen_basis, uint64_t basis_h, T2Args *a);
 // One launch running the passes of an L2 block group (complex64, 2^13 tiles);
 // `need`: the gate kinds (t2_gate_kinds) of all its passes.
 sv_status t2_group_launch(sv_state *h, const GroupArgs &g, int need, const sv_launch_record &meta);

@@ -627,7 +627,7 @@ static sv_status group_apply(sv_state *h, const CompiledPlan &cp, int gi) {
         t2_fill_args(tp, t2_device(dev, gj ? cp.up[i].gen : cp.up[i].main), h->n, &a);
         if (!t2_block_runs(&a, tp.gmask, g.bmask, h->n))
             return fail(SV_ERR_STATE, "internal: tile index runs of an L2 block do not fit");
-        if (gj) t2_set_gen(h, tp, gen, &a);
+        if (gj) t2_set_gen(tp, gen, h->basis_h, &a);
         a.tables = reinterpret_cast<const float2 *>(h->t2_tables);
         a.err = h->t2_err;
         a.keep = j + 1 < g.count;

@@ -809,13 +809,21 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
             __syncthreads();
         }
         for (int p = 0; p < I.npass; p++) {
-            const T2Args &a = B.passes[I.pass0 + p];
-            // the first pass generates |0...0> in registers; later passes read
-            // the state with bulk copies, the next tile's issued as soon as
-            // the current one's last stage change has read shared memory, and
-            // write it straight from registers
-            if (!a.gen && tid < 32) issue_tile_load<kT2Qubits>(a, sm, state, 0, bar, tid);
-            load_programme<kT2Qubits>(a, sm, tid, blockDim.x);
+            // the pass's arguments, copied next to its programme (shared
+            // memory instead of global loads inside the programme loop)
+            T2Args &a = *reinterpret_cast<T2Args *>(sm + G13::kOffArgs);
+            {
+                const T2Args &ga = B.passes[I.pass0 + p];
+                for (int i = tid; i < (int)(sizeof(T2Args) / 4); i += blockDim.x)
+                    reinterpret_cast<int *>(&a)[i] = reinterpret_cast<const int *>(&ga)[i];
+                // the first pass generates |0...0> in registers; later passes
+                // read the state with bulk copies, the next tile's issued as
+                // soon as the current one's last stage change has read shared
+                // memory, and write it straight from registers
+                if (!ga.gen && tid < 32) issue_tile_load<kT2Qubits>(ga, sm, state, 0, bar, tid);
+                load_programme<kT2Qubits>(ga, sm, tid, blockDim.x);
+                __syncthreads();
+            }
             for (uint64_t tile = 0; tile < a.ntiles; tile++) {
                 const uint64_t base = tile_base(a, tile);
                 // slot values into the buffer the previous tile did not use
@@ -1027,7 +1035,7 @@ bool t2_block_runs(T2Args *a, uint64_t gmask, uint64_t bmask, int n) {
     return true;
 }
 
-void t2_set_gen(const sv_state *h, const T2Pass &p, int64_t gen_basis, T2Args *a) {
+void t2_set_gen(const T2Pass &p, int64_t gen_basis, uint64_t basis_h, T2Args *a) {
     // the programme's leading Hadamards P (unnormalised, tile bits) applied
     // to the recorded product state H^{hq}|basis> (normalised Hadamards on
     // the physical qubits of hq): on a qubit in both they give sqrt(2) I, so
@@ -1039,12 +1047,12 @@ void t2_set_gen(const sv_state *h, const T2Pass &p, int64_t gen_basis, T2Args *a
     uint32_t hq_local = 0;
     for (int s = 0; s < p.k; s++) {
         a->gen_local |= (int)((a->gen_basis >> p.slot_phys[s]) & 1) << s;
-        if ((h->basis_h >> p.slot_phys[s]) & 1) hq_local |= 1u << s;
+        if ((basis_h >> p.slot_phys[s]) & 1) hq_local |= 1u << s;
     }
     a->gen_hmask = p.gen_hmask ^ hq_local;
-    a->gen_ghmask = h->basis_h & p.gmask;
+    a->gen_ghmask = basis_h & p.gmask;
     const int both = __builtin_popcount(p.gen_hmask & hq_local);
-    const int hq_only = __builtin_popcountll(h->basis_h) - both;
+    const int hq_only = __builtin_popcountll(basis_h) - both;
     a->gen_val = (float)std::pow(2.0, 0.5 * (both - hq_only));
 }
 
@@ -1054,7 +1062,7 @@ sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
     SV_TRY(launch_check());
     T2Args a{};
     t2_fill_args(p, d, h->n, &a);
-    if (gen_basis >= 0) t2_set_gen(h, p, gen_basis, &a);
+    if (gen_basis >= 0) t2_set_gen(p, gen_basis, h->basis_h, &a);
     a.tables = reinterpret_cast<const float2 *>(h->t2_tables);
     a.err = h->t2_err;
     if (p.k != 13 && p.k != 14) return fail(SV_ERR_ARG, "internal: register-stage tile of 2^%d", p.k);

@@ -405,3 +405,26 @@ def test_batch_autotune(sv):
     assert best.chunk_qubits in (4, 5, 6, 7) and ms > 0
     idx, p = sv.sv_apply_circuit_batch(items, best)
     assert all(int(idx[i]) == w[3] for i, w in enumerate(work))
+
+
+def test_batch_product_state_prefixes(sv, orc):
+    """Leading X and H gates of a batched instance fold into the product state
+    that its first pass generates; instances made of such gates only (nothing
+    left to generate the state) are planned as given.  Outcomes and their
+    probabilities against the oracle."""
+    from gen import mixed_circuit
+    circ = [(5, C.gates([C.x(0), C.x(3)]), 31),
+            (14, C.gates([C.h(0), C.h(1)]), 3),
+            (14, C.gates([C.x(2), C.h(2)]), 4),
+            (16, C.gates([C.x(1), C.h(1), C.x(1), C.h(4)] + list(mixed_circuit(16, 30, 9))), (1 << 16) - 1),
+            (17, C.gates([C.h(q) for q in range(17)] + [C.x(16), C.cz(0, 16)] +
+                         list(mixed_circuit(17, 40, 10, kinds=(0, 1, 2, 3, 4, 5, 6, 7, 9, 10)))), (1 << 17) - 1)]
+    idx, p = sv.sv_apply_circuit_batch(circ)
+    for i, (n, g, mask) in enumerate(circ):
+        probs = orc.marginal(n, orc.run(n, g), mask)
+        top = np.sort(probs)[-2:]
+        if top[1] - top[0] > 1e-5:
+            assert int(idx[i]) == int(np.argmax(probs)), i
+        else:  # ties: an index of the maximum
+            assert probs[int(idx[i])] >= top[1] - 1e-5, i
+        assert abs(p[i] - probs.max()) <= 1e-5, i
