@@ -168,7 +168,15 @@ typedef struct sv_config {
                               takes per claim (1, 2, 4, 8 or 16; 0 = 2).  More
                               tiles per claim mean fewer programme reloads and
                               a larger lag between a block's passes           */
-    int32_t reserved[8];   /* must be 0                                        */
+    int32_t batch_split;   /* batched launches: an instance of at least this
+                              many qubits has each pass's tiles shared out
+                              among CTAs (claims of 8 tiles), its read-out
+                              following its last pass; smaller instances run
+                              whole on one CTA.  25 = never split; 0 =
+                              automatic: 16 if the largest instance costs
+                              more than half of an even share of the work
+                              per CTA, else never                            */
+    int32_t reserved[7];   /* must be 0                                        */
 } sv_config;
 
 /* Counters of the last sv_apply_circuit on a handle. */
@@ -310,9 +318,11 @@ sv_status sv_batch_destroy(sv_batch b);
 sv_status sv_apply_circuit_batch(const sv_batch_item *items, size_t count, const sv_config *cfg,
                                  uint64_t *host_idx, double *host_p);
 
-/* Measure the batch for every chunk width c in 4..7 (one warm-up run and
- * three timed runs each, median) and return the fastest configuration in
- * *best (and its time in *best_ms, may be NULL). */
+/* Measure the batch for every chunk width c in 4..7, each with the
+ * automatic and with a forced split of instances of 16 qubits or more
+ * (batch_split 0 and 16; one warm-up run and three timed runs each, median),
+ * and return the fastest configuration in *best (and its time in *best_ms,
+ * may be NULL). */
 sv_status sv_batch_autotune(const sv_batch_item *items, size_t count, sv_config *best,
                             double *best_ms);
 

@@ -199,7 +199,7 @@ sv_status sv_apply_circuit(sv_handle h, const sv_gate *host_gates, size_t m, con
     if (m && !host_gates) return fail(SV_ERR_ARG, "gate list is NULL");
     sv_config c{};
     if (cfg) c = *cfg;
-    for (int i = 0; i < 8; i++)
+    for (int i = 0; i < 7; i++)
         if (c.reserved[i]) return fail(SV_ERR_ARG, "sv_config.reserved must be 0");
     if (c.l2_qubits != 0 && (c.l2_qubits < 14 || c.l2_qubits > 30))
         return fail(SV_ERR_ARG, "l2_qubits must be 0 or 14..30");

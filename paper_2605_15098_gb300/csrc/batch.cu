@@ -4,12 +4,14 @@
 // mode (tiles of 2^13 amplitudes; an instance of fewer than 13 qubits is
 // padded with untouched qubits, which stay |0>), compiled to register-stage
 // programmes, and packed with all other instances into one device buffer.
-// One launch then runs them all: CTAs take instances from a queue ordered by
-// decreasing cost (longest processing time first), run every pass of an
-// instance themselves and reduce its read-out.  The launch, the queue reset
-// and the copy of the results are captured once in a CUDA graph that
-// sv_batch_run replays.
+// One launch then runs them all: CTAs take work items from a queue.  An
+// instance of batch_split qubits or more is shared out (each pass in claims
+// of a few tiles, then its read-out); smaller ones run whole on one CTA,
+// largest first (longest processing time first).  The launch, the queue and
+// counter reset and the copy of the results are captured once in a CUDA
+// graph that sv_batch_run replays.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -27,8 +29,9 @@ struct sv_batch_state {
     size_t count = 0;
     void *states = nullptr;
     size_t state_amps = 0;
-    void *prog = nullptr;  // programme blob + instance table + pass table + order
-    int *queue = nullptr;
+    void *prog = nullptr;  // programme blob + instance table + work items + pass table
+    int *queue = nullptr;  // claim counter, then one tile counter per pass
+    size_t queue_bytes = 0;
     uint64_t *out_idx = nullptr;
     double *out_p = nullptr;
     uint64_t *h_idx = nullptr;  // pinned
@@ -88,6 +91,51 @@ std::vector<sv_gate> fold_prefix(const sv_gate *g, size_t m, int64_t *basis, uin
     return out;
 }
 
+// The launch's work items in claim order.  Instances of at least split_q
+// qubits (largest first) are shared out: each pass in claims of
+// kBatchClaimTiles tiles, then the read-out.  Their levels (pass 0, pass 1,
+// ..., read-out) are lagged: level l of the r-th large instance sits in step
+// r + l * lag, with enough claims between two levels of one instance (about
+// 2.5 grids) that the earlier level is done when the later one is claimed.
+// Smaller instances follow whole, largest first, filling the end.
+std::vector<int4> batch_work(const std::vector<BatchInst> &inst, const std::vector<double> &cost, int split_q,
+                             int grid) {
+    std::vector<int> order(inst.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<int> large, small;
+    for (int i : order) (inst[i].nphys >= split_q && inst[i].npass > 0 ? large : small).push_back(i);
+    auto claims = [&](int i) { return std::max(1, (1 << (inst[i].nphys - kT2Qubits)) / kBatchClaimTiles); };
+    std::vector<int4> work;
+    if (!large.empty()) {
+        double per = 0;
+        for (int i : large) per += (double)claims(i) * inst[i].npass + 1;
+        per /= (double)large.size();
+        const int lag = std::max(1, (int)std::ceil(2.5 * grid / per));
+        struct Seg { long long key; int level, inst; };
+        std::vector<Seg> segs;
+        for (size_t r = 0; r < large.size(); r++)
+            for (int l = 0; l <= inst[large[r]].npass; l++)
+                segs.push_back({(long long)r + (long long)l * lag, l, large[r]});
+        std::stable_sort(segs.begin(), segs.end(), [](const Seg &x, const Seg &y) {
+            return x.key != y.key ? x.key < y.key : x.level < y.level;
+        });
+        for (const Seg &s : segs) {
+            const BatchInst &I = inst[s.inst];
+            if (s.level == I.npass) {
+                work.push_back(make_int4(s.inst, kBatchReadout, 0, 0));
+                continue;
+            }
+            const int ntiles = 1 << (I.nphys - kT2Qubits);
+            const int per_claim = std::min(ntiles, kBatchClaimTiles);
+            for (int t = 0; t < ntiles; t += per_claim)
+                work.push_back(make_int4(s.inst, kBatchTiles | (s.level << 4), t, per_claim));
+        }
+    }
+    for (int i : small) work.push_back(make_int4(i, kBatchWhole, 0, 0));
+    return work;
+}
+
 void destroy(sv_batch_state *b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
@@ -121,6 +169,9 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
     sv_config c{};
     if (cfg) c = *cfg;
     const int chunk = c.chunk_qubits ? c.chunk_qubits : 5;
+    int split_q = c.batch_split;
+    if (split_q && (split_q < kT2Qubits + 1 || split_q > 25))
+        return fail(SV_ERR_ARG, "batch_split must be 0 or 14..25");
     if (c.flags & SV_FLAG_PAPER_SWAP)
         return fail(SV_ERR_UNSUPPORTED, "batched instances run no remap passes (SV_FLAG_PAPER_SWAP)");
     if (chunk < 4 || chunk > 11) return fail(SV_ERR_ARG, "chunk_qubits must be 4..11 for batches");
@@ -247,19 +298,30 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
             b->sweep_bytes += 2.0 * 8.0 * (double)(UINT64_C(1) << cp.nphys);
         }
     }
-    std::vector<int> order(count);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-    const size_t inst_off = blob.put(inst.data(), inst.size() * sizeof(BatchInst));
-    const size_t order_off = blob.put(order.data(), order.size() * sizeof(int));
-    const size_t pass_off = blob.put(nullptr, pass.size() * sizeof(T2Args));
-    blob.put(nullptr, 0);
     if (cudaGetDevice(&b->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaError_t e = cudaGetLastError();
         return bail(fail(SV_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e)));
     }
+    const int grid = 2 * std::max(1, b->sm_count);
+    if (!split_q) {
+        // automatic: whole instances (longest first) unless the largest one
+        // would set the end of the launch, i.e. it costs more than half of
+        // an even share of the work; then instances of 16 qubits and more
+        // are shared out
+        double total = 0, largest = 0;
+        for (double x : cost) {
+            total += x;
+            largest = std::max(largest, x);
+        }
+        split_q = largest > 0.5 * total / grid ? 16 : 25;
+    }
+    const std::vector<int4> items4 = batch_work(inst, cost, split_q, grid);
+    const size_t inst_off = blob.put(inst.data(), inst.size() * sizeof(BatchInst));
+    const size_t work_off = blob.put(items4.data(), items4.size() * sizeof(int4));
+    const size_t pass_off = blob.put(nullptr, pass.size() * sizeof(T2Args));
+    blob.put(nullptr, 0);
     if (dev_malloc(&b->prog, blob.b.size() + 256) != cudaSuccess) {
         cudaGetLastError();
         return bail(fail(SV_ERR_OOM, "cannot allocate the batch programme (%zu bytes)", blob.b.size()));
@@ -288,7 +350,8 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
         return bail(fail(SV_ERR_CUDA, "programme upload failed"));
     }
     b->state_amps = amps;
-    if (dev_malloc(&b->states, amps * 8) != cudaSuccess || dev_malloc(&b->queue, 256) != cudaSuccess ||
+    b->queue_bytes = 256 + pass.size() * sizeof(unsigned);
+    if (dev_malloc(&b->states, amps * 8) != cudaSuccess || dev_malloc(&b->queue, b->queue_bytes) != cudaSuccess ||
         dev_malloc(&b->out_idx, count * sizeof(uint64_t)) != cudaSuccess ||
         dev_malloc(&b->out_p, count * sizeof(double)) != cudaSuccess ||
         cudaMallocHost(&b->h_idx, count * sizeof(uint64_t)) != cudaSuccess ||
@@ -300,9 +363,10 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
     BatchArgs args{};
     args.inst = reinterpret_cast<const BatchInst *>(dev + inst_off);
     args.passes = reinterpret_cast<const T2Args *>(dev + pass_off);
-    args.order = reinterpret_cast<const int *>(dev + order_off);
-    args.count = (int)count;
+    args.work = reinterpret_cast<const int4 *>(dev + work_off);
+    args.nwork = (int)items4.size();
     args.queue = b->queue;
+    args.done = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(b->queue) + 256);
     args.out_idx = b->out_idx;
     args.out_p = b->out_p;
     args.err = b->err;
@@ -317,7 +381,7 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
     // capture: queue reset, the persistent launch, results to pinned host memory
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return bail(fail(SV_ERR_CUDA, "stream capture failed to start"));
-    cudaMemsetAsync(b->queue, 0, sizeof(int), b->stream);
+    cudaMemsetAsync(b->queue, 0, b->queue_bytes, b->stream);  // the claim counter and the pass counters
     sv_status lst = t2_batch_launch(reinterpret_cast<float *>(b->states), args, b->sm_count, b->stream);
     cudaMemcpyAsync(b->h_idx, b->out_idx, count * sizeof(uint64_t), cudaMemcpyDeviceToHost, b->stream);
     cudaMemcpyAsync(b->h_p, b->out_p, count * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
@@ -382,9 +446,12 @@ sv_status sv_batch_autotune(const sv_batch_item *items, size_t count, sv_config 
     if (!best) return fail(SV_ERR_ARG, "best is NULL");
     double bt = 1e300;
     int bc = 0;
-    for (int c : {4, 5, 6, 7}) {
+    int bs = 0;
+    for (int k = 0; k < 8; k++) {
+        const int c = 4 + k % 4, split = k < 4 ? 0 : 16;  // chunk width x (automatic, forced) split
         sv_config cfg{};
         cfg.chunk_qubits = c;
+        cfg.batch_split = split;
         sv_batch b = nullptr;
         SV_TRY(sv_batch_create(items, count, &cfg, &b));
         double t[4] = {};
@@ -396,10 +463,12 @@ sv_status sv_batch_autotune(const sv_batch_item *items, size_t count, sv_config 
         if (t[2] < bt) {
             bt = t[2];
             bc = c;
+            bs = split;
         }
     }
     *best = sv_config{};
     best->chunk_qubits = bc;
+    best->batch_split = bs;
     if (best_ms) *best_ms = bt;
     return SV_OK;
 }

@@ -135,11 +135,17 @@ struct BatchInst {
     int pos[34];         // physical bit of read-out bit j
 };
 
+// Work items of a batched launch, in claim order: x = instance, y = kind |
+// (pass << 4), z = first tile, w = tiles.
+enum { kBatchWhole = 0, kBatchTiles = 1, kBatchReadout = 2 };
+constexpr int kBatchClaimTiles = 8;  // tiles of one claim of a split instance
+
 struct BatchArgs {
     const BatchInst *inst;
     const T2Args *passes;
-    const int *order;  // processing order (largest first)
-    int count;
+    const int4 *work;  // work items in claim order
+    int nwork;
+    unsigned *done;    // per pass (index into passes): tiles finished (zero at launch)
     int *queue;
     uint64_t *out_idx;
     double *out_p;

@@ -769,10 +769,18 @@ __global__ void __launch_bounds__(kT2Threads, 2)
 }
 
 // ---------------------------------------------------------------- batched instances
-// One CTA runs whole instances taken from a shared queue (largest first): all
-// passes of the instance (the first pass starts from |0...0> in shared memory
-// instead of reading the state), then the FP64 argmax of the marginal over
-// the instance's read-out qubits.  States of up to 2^20 amplitudes stay in L2.
+// CTAs take work items from a shared queue, in the claim order the host
+// built:
+//   - a small instance whole: all of its passes (the first generates its
+//     starting product state in registers instead of reading the state),
+//     then the FP64 argmax of the marginal over its read-out qubits;
+//   - kBatchClaimTiles tiles of one pass of a large instance (pass p waits,
+//     bounded, for a per-pass counter to show all tiles of pass p-1 done);
+//   - the read-out of a large instance, after its last pass.
+// Large instances come first, their passes lagged so that a pass's tiles are
+// claimed well after the previous pass's; claim order is a topological order
+// of those waits and a CTA counts its previous item before it waits, so
+// every wait ends.  States of up to 2^20 amplitudes stay in L2.
 template <int F>
 __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ states, const BatchArgs B) {
     extern __shared__ __align__(1024) unsigned char sm[];
@@ -794,76 +802,92 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
     }
     __syncthreads();
     uint32_t parity = 0, rd = 0, buf = 0;
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(B.queue, 1);
-        __syncthreads();
-        const int item = s_item;
-        __syncthreads();
-        if (item >= B.count) break;
-        const BatchInst &I = B.inst[B.order[item]];
-        float *state = states + 2 * I.state_off;
-        if (I.npass == 0) {  // empty circuit: |0...0>
-            float4 *sv4 = reinterpret_cast<float4 *>(state);
-            for (uint64_t v = tid; v < (UINT64_C(1) << I.nphys) / 2; v += blockDim.x)
-                sv4[v] = make_float4(v == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
-            __syncthreads();
+    // tiles [t0, t0 + nt) of one pass; false: a bounded wait ran out
+    auto run_tiles = [&](const T2Args &ga, float *state, uint64_t t0, uint64_t nt) -> bool {
+        // the pass's arguments, copied next to its programme (shared memory
+        // instead of global loads inside the programme loop)
+        T2Args &a = *reinterpret_cast<T2Args *>(sm + G13::kOffArgs);
+        for (int i = tid; i < (int)(sizeof(T2Args) / 4); i += blockDim.x)
+            reinterpret_cast<int *>(&a)[i] = reinterpret_cast<const int *>(&ga)[i];
+        // a generated first pass reads nothing; later passes read the state
+        // with bulk copies, the next tile's issued as soon as the current
+        // one's last stage change has read shared memory, and write it
+        // straight from registers
+        if (!ga.gen && tid < 32) {
+            fence_async_global();
+            issue_tile_load<kT2Qubits>(ga, sm, state, t0, bar, tid);
         }
-        for (int p = 0; p < I.npass; p++) {
-            // the pass's arguments, copied next to its programme (shared
-            // memory instead of global loads inside the programme loop)
-            T2Args &a = *reinterpret_cast<T2Args *>(sm + G13::kOffArgs);
-            {
-                const T2Args &ga = B.passes[I.pass0 + p];
-                for (int i = tid; i < (int)(sizeof(T2Args) / 4); i += blockDim.x)
-                    reinterpret_cast<int *>(&a)[i] = reinterpret_cast<const int *>(&ga)[i];
-                // the first pass generates |0...0> in registers; later passes
-                // read the state with bulk copies, the next tile's issued as
-                // soon as the current one's last stage change has read shared
-                // memory, and write it straight from registers
-                if (!ga.gen && tid < 32) issue_tile_load<kT2Qubits>(ga, sm, state, 0, bar, tid);
-                load_programme<kT2Qubits>(ga, sm, tid, blockDim.x);
-                __syncthreads();
+        load_programme<kT2Qubits>(ga, sm, tid, blockDim.x);
+        __syncthreads();
+        for (uint64_t tile = t0; tile < t0 + nt; tile++) {
+            const uint64_t base = tile_base(a, tile);
+            // slot values into the buffer the previous tile did not use
+            float2 *sc = slotc + buf * kT2MaxSlots;
+            tile_slots<kT2Qubits>(a, tab, sc, base, tid);
+            bool timed_out = false;
+            if (!a.gen) {
+                timed_out = !mbar_wait(bar, parity);
+                parity ^= 1u;
             }
-            for (uint64_t tile = 0; tile < a.ntiles; tile++) {
-                const uint64_t base = tile_base(a, tile);
-                // slot values into the buffer the previous tile did not use
-                float2 *sc = slotc + buf * kT2MaxSlots;
-                tile_slots<kT2Qubits>(a, tab, sc, base, tid);
-                bool timed_out = false;
-                if (!a.gen) {
-                    timed_out = !mbar_wait(bar, parity);
-                    parity ^= 1u;
-                }
-                if (__syncthreads_or(timed_out)) {
-                    if (tid == 0) atomicExch(B.err, 1);
-                    mbar_wait(bar, parity ^ 1u);  // a second bounded wait for copies in flight
-                    return;
-                }
-                auto hook = [&]() {
-                    if (!a.gen && tid < 32 && tile + 1 < a.ntiles) {
-                        if (!mbar_wait(rbar, (rd - 1u) & 1u)) atomicExch(B.err, 1);
-                        issue_tile_load<kT2Qubits>(a, sm, state, tile + 1, bar, tid);
-                    }
-                };
-                t2_run<kT2Qubits, F>(a, reinterpret_cast<float4 *>(state), rbar, rd, base, sc, hook);
-                buf ^= 1u;
+            if (__syncthreads_or(timed_out)) {
+                if (tid == 0) atomicExch(B.err, 1);
+                mbar_wait(bar, parity ^ 1u);  // a second bounded wait for copies in flight
+                return false;
             }
-            // the next pass's bulk copies (and the read-out) see this pass's stores
-            asm volatile("fence.proxy.async;" ::: "memory");
-            __syncthreads();
+            auto hook = [&]() {
+                if (!a.gen && tid < 32 && tile + 1 < t0 + nt) {
+                    if (!mbar_wait(rbar, (rd - 1u) & 1u)) atomicExch(B.err, 1);
+                    issue_tile_load<kT2Qubits>(a, sm, state, tile + 1, bar, tid);
+                }
+            };
+            t2_run<kT2Qubits, F>(a, reinterpret_cast<float4 *>(state), rbar, rd, base, sc, hook);
+            buf ^= 1u;
         }
-        // read-out: argmax (lowest index among ties) of the FP64 marginal over I.pos
+        // the next pass's bulk copies (and the read-out) see this pass's stores
+        fence_async_global();
+        __syncthreads();
+        return true;
+    };
+    // argmax (lowest index among ties) of the FP64 marginal over I.pos
+    auto readout = [&](const BatchInst &I, const float *state) {
+        // Outcomes are visited in the order of their physical index (bit i of
+        // the visit index v is the i-th lowest physical read-out qubit), so
+        // that a warp's loads are contiguous whatever qubit map the passes
+        // left (QPE's inverse QFT ends bit-reversed).  Tables, in the tile
+        // buffer after the reduction scratch: per byte of v, its physical
+        // offset (T) and its outcome bits (Y).
+        uint64_t *T = reinterpret_cast<uint64_t *>(sm + 24 * kT2Threads);
+        uint32_t *Y = reinterpret_cast<uint32_t *>(T + 3 * 256);
         uint64_t mask = 0;
         for (int j = 0; j < I.m; j++) mask |= UINT64_C(1) << I.pos[j];
+        for (int e = tid; e < 3 * 256; e += blockDim.x) {
+            const int lvl = e >> 8, v = e & 255;
+            uint64_t x = 0;
+            uint32_t yb = 0;
+            for (int b = 0; b < 8; b++) {
+                const int i = lvl * 8 + b;  // rank among the read-out qubits' physical bits
+                if (i >= I.m || !((v >> b) & 1)) continue;
+                uint64_t mm = mask;
+                for (int k = 0; k < i; k++) mm &= mm - 1;
+                const int ph = __ffsll((long long)mm) - 1;
+                x |= UINT64_C(1) << ph;
+                for (int j = 0; j < I.m; j++)
+                    if (I.pos[j] == ph) yb |= 1u << j;
+            }
+            T[e] = x;
+            Y[e] = yb;
+        }
+        __syncthreads();
         const uint64_t all = (UINT64_C(1) << I.nphys) - 1;
         const uint64_t rest = all & ~mask;
+        const uint64_t nrest = UINT64_C(1) << (I.nphys - I.m);
         const uint64_t outcomes = UINT64_C(1) << I.m;
+        const float2 *st2 = reinterpret_cast<const float2 *>(state);
         double best = -1.0, tot = 0.0;
         uint64_t bidx = ~UINT64_C(0);
-        for (uint64_t y = tid; y < outcomes; y += blockDim.x) {
-            uint64_t xy = 0;
-            for (int j = 0; j < I.m; j++)
-                if ((y >> j) & 1) xy |= UINT64_C(1) << I.pos[j];
+        for (uint64_t v = tid; v < outcomes; v += blockDim.x) {
+            const uint64_t xy = T[v & 255] | T[256 + ((v >> 8) & 255)] | T[512 + ((v >> 16) & 255)];
+            const uint64_t y = Y[v & 255] | Y[256 + ((v >> 8) & 255)] | Y[512 + ((v >> 16) & 255)];
             // exact FP32 squares (product + fmaf remainder) summed as a
             // double-float pair: FP64-accurate without FP64 arithmetic
             float hi = 0.f, lo = 0.f;
@@ -873,18 +897,33 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
                 lo += (hi - (t - bb)) + (b - bb);
                 hi = t;
             };
+            // the amplitudes of outcome y in increasing index order, four
+            // independent loads in flight at a time
             uint64_t xr = 0;
-            do {
-                const float2 amp = reinterpret_cast<const float2 *>(state)[xy | xr];
-                const float pr = amp.x * amp.x, pi = amp.y * amp.y;
-                lo += fmaf(amp.x, amp.x, -pr) + fmaf(amp.y, amp.y, -pi);
-                two_sum(pr);
-                two_sum(pi);
-                xr = ((xr | ~rest) + 1) & rest;
-            } while (xr);
+            for (uint64_t r = 0; r < nrest; r += 4) {
+                uint64_t xs[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    xs[u] = xr;
+                    xr = ((xr | ~rest) + 1) & rest;
+                }
+                float2 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    v[u] = r + u < nrest ? st2[xy | xs[u]] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    if (r + u >= nrest) break;
+                    const float2 amp = v[u];
+                    const float pr = amp.x * amp.x, pi = amp.y * amp.y;
+                    lo += fmaf(amp.x, amp.x, -pr) + fmaf(amp.y, amp.y, -pi);
+                    two_sum(pr);
+                    two_sum(pi);
+                }
+            }
             const double acc = (double)hi + (double)lo;
             tot += acc;
-            if (acc > best) {
+            if (acc > best || (acc == best && y < bidx)) {
                 best = acc;
                 bidx = y;
             }
@@ -910,6 +949,50 @@ __global__ void __launch_bounds__(kT2Threads, 2) k_batch(float *__restrict__ sta
             B.out_p[I.out] = s_tot[0] > 0.0 ? s_val[0] / s_tot[0] : 0.0;
         }
         __syncthreads();
+    };
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(B.queue, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= B.nwork) break;
+        const int4 wk = __ldg(B.work + item);
+        const BatchInst &I = B.inst[wk.x];
+        float *state = states + 2 * I.state_off;
+        const int kind = wk.y & 15, p = wk.y >> 4;
+        const bool whole = kind == kBatchWhole;
+        if (whole && I.npass == 0) {  // empty circuit: |0...0>
+            float4 *sv4 = reinterpret_cast<float4 *>(state);
+            for (uint64_t v = tid; v < (UINT64_C(1) << I.nphys) / 2; v += blockDim.x)
+                sv4[v] = make_float4(v == 0 ? 1.f : 0.f, 0.f, 0.f, 0.f);
+            __syncthreads();
+        }
+        if (!whole) {  // a large instance: wait for the pass this item reads (all of its tiles)
+            const int dep = kind == kBatchTiles ? (p > 0 ? I.pass0 + p - 1 : -1) : I.pass0 + I.npass - 1;
+            bool ok = true;
+            if (tid == 0 && dep >= 0)
+                ok = wait_count(B.done + dep, (unsigned)B.passes[I.pass0].ntiles, B.err);
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) atomicExch(B.err, 1);
+                return;
+            }
+        }
+        // passes [q0, q1): every pass of a whole instance, one pass's tile
+        // range of a large one (one call site keeps the programme loop
+        // inlined once)
+        const int q0 = whole ? 0 : p, q1 = whole ? I.npass : kind == kBatchTiles ? p + 1 : p;
+        for (int q = q0; q < q1; q++) {
+            const T2Args &ga = B.passes[I.pass0 + q];
+            if (!run_tiles(ga, state, whole ? 0 : (uint64_t)wk.z, whole ? ga.ntiles : (uint64_t)wk.w)) return;
+        }
+        if (kind == kBatchTiles) {
+            if (tid == 0) {  // every thread's stores precede the barrier that ended run_tiles
+                __threadfence();
+                atomicAdd(B.done + I.pass0 + p, (unsigned)wk.w);
+            }
+            continue;
+        }
+        readout(I, state);
     }
 }
 
@@ -1143,7 +1226,7 @@ sv_status t2_batch_launch(float *states, const BatchArgs &b, int sm_count, cudaS
     int per_sm = 0;
     SV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kT2Threads, kSmemBytes));
     if (per_sm < 1) return fail(SV_ERR_UNSUPPORTED, "batched kernel does not fit on an SM");
-    const int grid = std::max(1, std::min(b.count, per_sm * sm_count));
+    const int grid = std::max(1, std::min(b.nwork, per_sm * sm_count));
     kern<<<grid, kT2Threads, kSmemBytes, stream>>>(states, b);
     SV_CUDA(cudaGetLastError());
     note_launch();

@@ -61,7 +61,7 @@ class sv_config(ctypes.Structure):
                 ("chunk_qubits", ctypes.c_int32), ("fuse_qubits", ctypes.c_int32),
                 ("planner", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("l2_qubits", ctypes.c_int32), ("l2_chunk", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("batch_split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 class sv_stats(ctypes.Structure):
@@ -197,8 +197,9 @@ def sv_last_error() -> str:
 
 
 def make_config(mode=SV_MODE_AUTO, tile_qubits=0, chunk_qubits=0, fuse_qubits=0,
-                planner=SV_PLANNER_GREEDY, flags=0, l2_qubits=0, l2_chunk=0) -> sv_config:
-    return sv_config(mode, tile_qubits, chunk_qubits, fuse_qubits, planner, flags, l2_qubits, l2_chunk)
+                planner=SV_PLANNER_GREEDY, flags=0, l2_qubits=0, l2_chunk=0, batch_split=0) -> sv_config:
+    return sv_config(mode, tile_qubits, chunk_qubits, fuse_qubits, planner, flags, l2_qubits, l2_chunk,
+                     batch_split)
 
 
 # ---- handle-level functions (same names as the C ABI) ------------------------
@@ -518,7 +519,7 @@ def config_dict(c: sv_config) -> dict:
              SV_MODE_FUSED: "fused"}
     return {"mode": names.get(c.mode, c.mode), "tile_qubits": c.tile_qubits,
             "chunk_qubits": c.chunk_qubits, "planner": c.planner, "flags": c.flags,
-            "l2_qubits": c.l2_qubits, "l2_chunk": c.l2_chunk}
+            "l2_qubits": c.l2_qubits, "l2_chunk": c.l2_chunk, "batch_split": c.batch_split}
 
 
 def sv_launch_count() -> int:

@@ -402,7 +402,7 @@ def test_batch_autotune(sv):
     work = C.qpe_batch(64, seed=11)
     items = [(n, g, m) for n, g, m, _ in work]
     best, ms = sv.sv_batch_autotune(items)
-    assert best.chunk_qubits in (4, 5, 6, 7) and ms > 0
+    assert best.chunk_qubits in (4, 5, 6, 7) and best.batch_split in (0, 16) and ms > 0
     idx, p = sv.sv_apply_circuit_batch(items, best)
     assert all(int(idx[i]) == w[3] for i, w in enumerate(work))
 
@@ -428,3 +428,18 @@ def test_batch_product_state_prefixes(sv, orc):
         else:  # ties: an index of the maximum
             assert probs[int(idx[i])] >= top[1] - 1e-5, i
         assert abs(p[i] - probs.max()) <= 1e-5, i
+
+
+@pytest.mark.parametrize("split", [0, 14, 16, 19, 25])
+def test_batch_split_instances(sv, split):
+    """Instances of at least `split` qubits are shared out among CTAs pass by
+    pass (25: none is): every outcome equals the closed form, and the
+    probabilities equal those of the unsplit launch."""
+    work = C.qpe_batch(160, seed=4242)
+    items = [(n, g, m) for n, g, m, _ in work]
+    idx, p = sv.sv_apply_circuit_batch(items, sv.make_config(sv.SV_MODE_PARTITIONED, batch_split=split))
+    idx0, p0 = sv.sv_apply_circuit_batch(items, sv.make_config(sv.SV_MODE_PARTITIONED, batch_split=25))
+    for i, (n, g, mask, y) in enumerate(work):
+        assert int(idx[i]) == y, (i, n)
+    assert np.array_equal(idx, idx0)
+    assert np.max(np.abs(p - p0)) == 0.0  # same per-tile arithmetic and summation order
