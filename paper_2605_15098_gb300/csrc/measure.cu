@@ -125,6 +125,52 @@ k_marg_m(const R *__restrict__ s, MargArgs a, double *__restrict__ partial) {
     partial[g * outcomes + ml] = acc.value();
 }
 
+// Layout M, complex64: each thread takes the two outcomes that differ in
+// physical bit 0 (one 16-byte load covers both amplitudes), each summed in
+// the same order as k_marg_m.
+__global__ void __launch_bounds__(kRedThreads)
+k_marg_m2(const float *__restrict__ s, MargArgs a, double *__restrict__ partial) {
+    const uint64_t outcomes = UINT64_C(1) << a.m;
+    const uint64_t half = outcomes >> 1;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (half << a.groups_log2)) return;
+    const uint64_t mp = (tid & (half - 1)) << 1;
+    const uint64_t g = tid >> (a.m - 1);
+    uint64_t xm = 0, ml = 0;
+    for (int k = 1; k < a.m; k++) {
+        if ((mp >> k) & 1) {
+            xm |= UINT64_C(1) << a.spos[k];
+            ml |= UINT64_C(1) << a.out_bit[k];
+        }
+    }
+    const uint64_t ml1 = ml | (UINT64_C(1) << a.out_bit[0]);
+    uint64_t xr = pdep_mask(g * a.per_group, a.rest);
+    ProbAcc<float> acc0, acc1;
+    const float4 *s4 = reinterpret_cast<const float4 *>(s);
+    uint64_t i = 0;
+    for (; i + kLoadBatch <= a.per_group; i += kLoadBatch) {
+        float4 v[kLoadBatch];
+#pragma unroll
+        for (int k = 0; k < kLoadBatch; k++) {
+            v[k] = s4[(xm | xr) >> 1];
+            xr = ((xr | ~a.rest) + 1) & a.rest;
+        }
+#pragma unroll
+        for (int k = 0; k < kLoadBatch; k++) {
+            acc0.add(make_float2(v[k].x, v[k].y));
+            acc1.add(make_float2(v[k].z, v[k].w));
+        }
+    }
+    for (; i < a.per_group; i++) {
+        const float4 v = s4[(xm | xr) >> 1];
+        acc0.add(make_float2(v.x, v.y));
+        acc1.add(make_float2(v.z, v.w));
+        xr = ((xr | ~a.rest) + 1) & a.rest;
+    }
+    partial[g * outcomes + ml] = acc0.value();
+    partial[g * outcomes + ml1] = acc1.value();
+}
+
 // Layout R: the lowest physical bits are summed over; one warp per
 // (group, outcome), lanes take the five lowest rest bits.
 template <typename R>
@@ -415,7 +461,9 @@ sv_status marginal_device(sv_state *h, const int *pos, int m, double *dev_out, b
     if (groups > 1) partial = reinterpret_cast<double *>(h->scratch);
     double *sums = reinterpret_cast<double *>(reinterpret_cast<char *>(h->scratch) + sums_off);
 
-    const uint64_t work = layout_r ? (outcomes << gl) * 32 : (outcomes << gl);
+    // complex64 with physical bit 0 an outcome bit: two outcomes per thread
+    const bool pairs = !layout_r && h->dt == SV_C64 && m >= 1 && a.spos[0] == 0;
+    const uint64_t work = layout_r ? (outcomes << gl) * 32 : pairs ? ((outcomes >> 1) << gl) : (outcomes << gl);
     const unsigned grid = blocks_for(work, kRedThreads);
     if (h->dt == SV_C128) {
         const double *s = reinterpret_cast<const double *>(h->amps);
@@ -427,6 +475,8 @@ sv_status marginal_device(sv_state *h, const int *pos, int m, double *dev_out, b
         const float *s = reinterpret_cast<const float *>(h->amps);
         if (layout_r)
             k_marg_r<float><<<grid, kRedThreads, 0, h->stream>>>(s, a, partial);
+        else if (pairs)
+            k_marg_m2<<<grid, kRedThreads, 0, h->stream>>>(s, a, partial);
         else
             k_marg_m<float><<<grid, kRedThreads, 0, h->stream>>>(s, a, partial);
     }

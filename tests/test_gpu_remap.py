@@ -105,3 +105,54 @@ def test_paper_mode_full_size_qpe(sv):
         idx, p = s.argmax(info["mask"])
     assert idx == info["y"] and abs(p - 1.0) <= 1e-5
     assert st["remaps"] == sv.sv_plan_export(n, sv.SV_C64, without_leading_x(g), cfg)["remaps"]
+
+
+def window_circuit(n, windows, per, seed):
+    """Non-diagonal gates (U, X, controlled U) inside qubit windows, one
+    window after another: each window is one tile pass's local set.  Every
+    gate acts on the qubit the previous gate ended on, so no planner can
+    reorder them: floating-point results depend on the order of gates even
+    where they commute.  No Hadamards: a tile pass scales its unnormalised
+    Hadamards once, by a factor that depends on how many the pass holds."""
+    rng = np.random.default_rng(seed)
+    recs = []
+    cur = 0
+    for w in windows:
+        if cur not in w:
+            cur = w[0]
+        for _ in range(per):
+            r = rng.random()
+            if r < 0.45:  # an explicit 2x2 (complex64 plans split U3 into phases and a rotation)
+                recs.append(C.u(cur, C.random_unitary(rng)))
+            elif r < 0.55:
+                recs.append(C.x(cur))
+            else:
+                b = int(rng.choice([q for q in w if q != cur]))
+                recs.append(C.cu(cur, b, C.random_unitary(rng)))
+                cur = b
+    return C.gates(recs)
+
+
+@pytest.mark.parametrize("dt,flags", [(1, 0), (0, 8)])
+def test_remap_points_do_not_change_amplitudes(sv, orc, dt, flags):
+    """Reading A12: two plans of the same gates, in the same order, whose
+    passes differ only in where the qubits are brought together - explicit
+    remap passes before the passes (the paper's global-local SWAPs,
+    SV_FLAG_PAPER_SWAP) or tiles gathered from the qubits where they lie -
+    apply the same arithmetic to every amplitude, so the amplitudes are
+    identical bit for bit (complex128 and complex64 on the generic tile
+    kernel; no diagonal gates, whose grouping into phase factors may differ
+    between the plans)."""
+    n, k = 16, 12
+    windows = [list(range(0, 11)) + [11 + p] for p in range(5)]
+    g = window_circuit(n, windows, 40, 7 + dt)
+    outs, stats = [], []
+    for extra in (0, sv.SV_FLAG_PAPER_SWAP):
+        with sv.State(n, dt) as s:
+            s.apply(g, sv.make_config(sv.SV_MODE_PARTITIONED, tile_qubits=k, flags=flags | extra))
+            stats.append(s.stats())
+            outs.append(s.amplitudes())
+    assert stats[0]["remaps"] == 0 and stats[1]["remaps"] > 0
+    assert np.array_equal(outs[0], outs[1])
+    ref = orc.run(n, g)
+    assert np.max(np.abs(outs[0] - ref)) <= (1e-12 if dt == 1 else 2e-5)
