@@ -541,7 +541,14 @@ typedef struct sv_plan_choice {
     int32_t verdict;             /* planner sv_planner_judge kept (sv_planner) */
     int32_t early_diag;          /* 1: the chosen plan keeps diagonal gates in
                                     the first pass where they are ready       */
-    int32_t reserved[6];
+    int32_t rule_kernels;        /* 1: sv_planner_judge measured the chosen
+                                    options faster with the greedy rule's
+                                    kernel per pass and kept those            */
+    int32_t reserved0;
+    double rule_ms;              /* measured by sv_planner_judge: the chosen
+                                    options with the rule's kernels (0 if the
+                                    model chose the same kernels)             */
+    int32_t reserved[2];
 } sv_plan_choice;
 
 /* The learned planner's choice for this gate list (no kernel runs). */
@@ -550,8 +557,11 @@ sv_status sv_learned_plan(sv_handle h, const sv_gate *host_gates, size_t m,
 
 /* Run the greedy plan of cfg and the learned plan from |0...0>, once to warm
  * up and three times each under CUDA events, and keep the faster (median)
- * for this circuit structure on this handle.  The state is reset to
- * |0...0> afterwards. */
+ * for this circuit structure on this handle.  Where the model picked a
+ * kernel per pass other than the greedy rule's, the learned plan's options
+ * (tile and chunk widths, remaps, diagonal placement) are also timed with
+ * the rule's kernels, and the faster kernel choice becomes the learned plan.
+ * The state is reset to |0...0> afterwards. */
 sv_status sv_planner_judge(sv_handle h, const sv_gate *host_gates, size_t m,
                            const sv_config *cfg, sv_plan_choice *out);
 

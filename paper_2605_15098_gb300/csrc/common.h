@@ -112,6 +112,7 @@ struct sv_state {
     sv_cost_model_s *cost_model = nullptr;  // attached, not owned
     struct Learned {
         sv::PlanOverride ov;
+        std::vector<int8_t> rule_kernel;  // the greedy rule's kernel per pass of ov's plan
         sv_plan_choice info{};
         int verdict = -1;  // planner sv_planner_judge kept; -1 = not judged
     };

@@ -166,7 +166,7 @@ sv_status learned_entry(sv_state *h, const std::vector<sv_gate> &gates, const sv
     for (size_t ci = 0; ci < cands.size(); ci++) {
         const Candidate &cd = cands[ci];
         double tot = 0.0, tot_rule = 0.0;
-        std::vector<int8_t> kern;
+        std::vector<int8_t> kern, kern_rule;
         int nfused = 0;
         for (int r : cd.remap_recs) {
             tot += ms[r];
@@ -175,6 +175,7 @@ sv_status learned_entry(sv_state *h, const std::vector<sv_gate> &gates, const sv
         for (const std::vector<Option> &po : cd.pass_opts) {
             if (po.empty()) {
                 kern.push_back(PK_GENERIC);
+                kern_rule.push_back(PK_GENERIC);
                 continue;
             }
             const Option *bo = &po[0];
@@ -184,6 +185,7 @@ sv_status learned_entry(sv_state *h, const std::vector<sv_gate> &gates, const sv
             kern.push_back((int8_t)bo->family);
             nfused += bo->family == PK_T3;
             const int rf = rule_family(po, allow_t2, fused);
+            kern_rule.push_back((int8_t)rf);
             for (const Option &o : po)
                 if (o.family == rf) tot_rule += ms[o.rec];
         }
@@ -192,6 +194,7 @@ sv_status learned_entry(sv_state *h, const std::vector<sv_gate> &gates, const sv
             best = tot;
             L.ov.opt = cd.opt;
             L.ov.kernel = kern;
+            L.rule_kernel = kern_rule;
             L.info.chunk_qubits = cd.opt.c;
             L.info.paper_swap = cd.opt.paper ? 1 : 0;
             L.info.early_diag = cd.opt.late_diag ? 0 : 1;
@@ -315,6 +318,20 @@ sv_status sv_planner_judge(sv_handle h, const sv_gate *host_gates, size_t m, con
     double tg = 0.0, tl = 0.0;
     SV_TRY(time_plan(h, g, c, nullptr, &tg));
     SV_TRY(time_plan(h, g, c, &L->ov, &tl));
+    L->info.rule_ms = 0.0;
+    if (L->rule_kernel != L->ov.kernel) {  // the chosen options with the rule's kernels
+        PlanOverride rule = L->ov;
+        rule.kernel = L->rule_kernel;
+        double tr = 0.0;
+        SV_TRY(time_plan(h, g, c, &rule, &tr));
+        L->info.rule_ms = tr;
+        if (tr < tl) {
+            L->ov.kernel = L->rule_kernel;
+            L->info.rule_kernels = 1;
+            L->info.fused_passes = (int)std::count(L->ov.kernel.begin(), L->ov.kernel.end(), (int8_t)PK_T3);
+            tl = tr;
+        }
+    }
     L->info.greedy_ms = tg;
     L->info.learned_ms = tl;
     L->verdict = tl < tg ? SV_PLANNER_LEARNED : SV_PLANNER_GREEDY;

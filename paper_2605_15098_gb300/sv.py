@@ -103,7 +103,8 @@ class sv_plan_choice(ctypes.Structure):
                 ("predicted_ms", ctypes.c_double), ("greedy_predicted_ms", ctypes.c_double),
                 ("learned_ms", ctypes.c_double), ("greedy_ms", ctypes.c_double),
                 ("verdict", ctypes.c_int32), ("early_diag", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("rule_kernels", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("rule_ms", ctypes.c_double), ("reserved", ctypes.c_int32 * 2)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
