@@ -117,9 +117,10 @@ extern "C" sv_status sv_autotune(sv_handle h, const sv_gate *host_gates, size_t 
             for (int c : {4, 5, 7}) add(SV_MODE_PARTITIONED, 14, c);
         if (h->n > 13)
             for (int c : {4, 5, 6}) add(SV_MODE_FUSED, 0, c);
-    } else {
-        for (int k : {11, 12, 13})
+    } else {  // the generic FP64 tile kernel, and the FP64 register-stage kernel on 2^13 tiles
+        for (int k : {11, 12})
             for (int c : {3, 4, 5}) add(SV_MODE_PARTITIONED, k, c);
+        for (int c : {4, 5, 6, 7}) add(SV_MODE_PARTITIONED, 13, c);
     }
     cudaEvent_t e0, e1;
     SV_CUDA(cudaEventCreate(&e0));

@@ -223,6 +223,10 @@ sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
 // The generated-state fields of a first pass that starts from the product
 // state H^{basis_h}|gen_basis> (physical qubit masks).
 void t2_set_gen(const T2Pass &p, int64_t gen_basis, uint64_t basis_h, T2Args *a);
+// The complex128 register-stage kernel (tile2d.cu): a pass compiled by
+// compile_t2v2_c128; gen_basis as for t2_launch.  Needs h->tab64.
+sv_status t2d_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta,
+                     int64_t gen_basis = -1);
 // One launch running the passes of an L2 block group (complex64, 2^13 tiles);
 // `need`: the gate kinds (t2_gate_kinds) of all its passes.
 sv_status t2_group_launch(sv_state *h, const GroupArgs &g, int need, const sv_launch_record &meta);

@@ -341,8 +341,9 @@ PlanOptions plan_options(int n, sv_dtype dt, const sv_config &cfg) {
     PlanOptions opt;
     opt.n = n;
     const bool dbl = dt == SV_C128;
-    opt.k = cfg.tile_qubits ? cfg.tile_qubits : (dbl ? 12 : 13);
-    opt.c = cfg.chunk_qubits ? cfg.chunk_qubits : (dbl ? 4 : 5);
+    // complex128 defaults to the FP64 register-stage kernel's 2^13 tiles
+    opt.k = cfg.tile_qubits ? cfg.tile_qubits : 13;
+    opt.c = cfg.chunk_qubits ? cfg.chunk_qubits : 5;
     if (!dbl && opt.c < 1) opt.c = 1;
     opt.merge_diag = !(cfg.flags & SV_FLAG_NO_DIAG_MERGE);
     opt.relabel = !(cfg.flags & SV_FLAG_NO_RELABEL);

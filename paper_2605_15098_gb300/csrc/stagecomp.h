@@ -37,6 +37,13 @@ struct T2Pass {
     std::vector<T2Slot> slots;      // format 2: tile-uniform slots
     std::vector<int32_t> soff;      // format 2: slot s's terms are sterms[soff[s] .. soff[s + 1])
     std::vector<T2SlotTerm> sterms;
+    // complex128 (compile_t2v2_c128): 64-bit phases and FP64 values in place
+    // of sterms, mats and statc (same record indexing: a matrix record is 8
+    // doubles, a table's entry x is (re, im) at doubles 2x, 2x + 1)
+    int wide = 0;
+    std::vector<T2SlotTerm64> sterms64;
+    std::vector<double> mats64;
+    std::vector<double> statc64;
     // format 2, first pass of a plan: the variant run when the pass starts
     // from a recorded basis state (generated in registers, leading Hadamards
     // included); null when not compiled
@@ -101,6 +108,7 @@ struct T2Args {
     // result goes to HBM); 1 keeps it in L2 (plain stores: the next pass of
     // an L2 block reads it)
     int keep;
+    double gen_val64;  // gen_val in FP64 (complex128 kernel)
 };
 
 // Fill the counts, pointers and geometry of a format-2 pass (not gen,
@@ -163,5 +171,9 @@ std::string compile_t2(const TilePass &tp, T2Pass *out, bool fused = false);
 // state, which it generates in registers (no shared-memory read of its first
 // stage; the leading Hadamards are part of the generated state).
 std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen);
+
+// The same programme for the complex128 register-stage kernel (k_tile2d):
+// 64-bit phases, FP64 matrices, tables and rows; 2^13-amplitude tiles.
+std::string compile_t2v2_c128(const TilePass &tp, T2Pass *out, bool gen);
 
 }  // namespace sv

@@ -143,10 +143,124 @@ void expi(uint32_t u, float *re, float *im) {
     *im = (float)std::sin(ang);
 }
 
-}  // namespace
+// Precision policies of the compiler.  P32 (complex64 kernels): phases as
+// 32-bit fractions of a turn, values rounded to FP32 (T2Pass::mats, statc,
+// sterms).  P64 (complex128 kernel): phases as the planner's 64-bit
+// fractions, values in FP64 (T2Pass::mats64, statc64, sterms64).  The
+// programme structure (instructions, stages, factor records, slots) is the
+// same for both.
+struct P32 {
+    using Ph = uint32_t;
+    using V = float;
+    static Ph ph(uint64_t t64) { return turns32(t64); }
+    static void ex(Ph u, V *re, V *im) { expi(u, re, im); }
+    static bool real(const double *m) {
+        return (float)m[1] == 0.f && (float)m[3] == 0.f && (float)m[5] == 0.f && (float)m[7] == 0.f;
+    }
+    static int32_t push_mat(T2Pass *o, const double *m) {
+        T2Mat t{};
+        for (int e = 0; e < 8; e++) t.m[e] = (float)m[e];
+        o->mats.push_back(t);
+        return (int32_t)o->mats.size() - 1;
+    }
+    static size_t nmats(const T2Pass *o) { return o->mats.size(); }
+    static size_t nrowvals(const T2Pass *o) { return o->statc.size(); }
+    static void push_row(T2Pass *o, V re, V im) {
+        o->statc.push_back(re);
+        o->statc.push_back(im);
+    }
+    // 32-entry table: T[q] = (re[2q], re[2q+1], im[2q], im[2q+1]), eight records
+    static int32_t push_table(T2Pass *o, const Ph *u) {
+        const int32_t m0 = (int32_t)o->mats.size();
+        float tab[64];
+        for (int x = 0; x < 32; x++) {
+            float re, im;
+            expi(u[x], &re, &im);
+            tab[4 * (x >> 1) + (x & 1)] = re;
+            tab[4 * (x >> 1) + 2 + (x & 1)] = im;
+        }
+        for (int m = 0; m < 8; m++) {
+            T2Mat tm{};
+            for (int e = 0; e < 8; e++) tm.m[e] = tab[8 * m + e];
+            o->mats.push_back(tm);
+        }
+        return m0;
+    }
+    static bool table_one(const T2Pass *o, int m0, int x) {
+        const float *tf = o->mats[m0 + (x >> 2)].m;
+        const int off = 4 * ((x >> 1) & 1) + (x & 1);
+        return tf[off] == 1.f && tf[off + 2] == 0.f;
+    }
+    // s as an unevaluated FP32 sum hi + lo
+    static int32_t push_scale(T2Pass *o, double s) {
+        const float hi = (float)s;
+        double m[8] = {};
+        m[0] = hi;
+        m[1] = (float)(s - (double)hi);
+        return push_mat(o, m);
+    }
+    static void push_sterm(T2Pass *o, int g0, int g1, Ph th) {
+        o->sterms.push_back({(int16_t)g0, (int16_t)g1, th});
+    }
+};
 
-std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen) {
+struct P64 {
+    using Ph = uint64_t;
+    using V = double;
+    static Ph ph(uint64_t t64) { return t64; }
+    static void ex(Ph u, V *re, V *im) {
+        const double ang = 2.0 * M_PI * ((double)(int64_t)u * 0x1p-64);
+        *re = std::cos(ang);
+        *im = std::sin(ang);
+    }
+    static bool real(const double *m) { return m[1] == 0.0 && m[3] == 0.0 && m[5] == 0.0 && m[7] == 0.0; }
+    static int32_t push_mat(T2Pass *o, const double *m) {
+        o->mats64.insert(o->mats64.end(), m, m + 8);
+        return (int32_t)(o->mats64.size() / 8) - 1;
+    }
+    static size_t nmats(const T2Pass *o) { return o->mats64.size() / 8; }
+    static size_t nrowvals(const T2Pass *o) { return o->statc64.size(); }
+    static void push_row(T2Pass *o, V re, V im) {
+        o->statc64.push_back(re);
+        o->statc64.push_back(im);
+    }
+    // 32-entry table: entry x = (re, im) at doubles 2x, 2x + 1, eight records
+    static int32_t push_table(T2Pass *o, const Ph *u) {
+        const int32_t m0 = (int32_t)nmats(o);
+        for (int x = 0; x < 32; x++) {
+            double re, im;
+            ex(u[x], &re, &im);
+            o->mats64.push_back(re);
+            o->mats64.push_back(im);
+        }
+        return m0;
+    }
+    static bool table_one(const T2Pass *o, int m0, int x) {
+        const double *t = &o->mats64[8 * (size_t)m0 + 2 * x];
+        return t[0] == 1.0 && t[1] == 0.0;
+    }
+    static int32_t push_scale(T2Pass *o, double s) {
+        double m[8] = {};
+        m[0] = s;
+        return push_mat(o, m);
+    }
+    static void push_sterm(T2Pass *o, int g0, int g1, Ph th) {
+        o->sterms64.push_back({(int16_t)g0, (int16_t)g1, 0, th});
+    }
+};
+
+template <class P>
+std::string compile_fmt2(const TilePass &tp, T2Pass *out, bool gen) {
+    using Ph = typename P::Ph;
+    using V = typename P::V;
+    // a tile term with its phase in the policy's width
+    struct TT {
+        int32_t run, tb, g0, g1;
+        Ph theta;
+    };
+    std::vector<TT> tts;
     *out = T2Pass{};
+    out->wide = sizeof(Ph) == 8;
     if (tp.k != kT2Qubits && tp.k != kT2WideQubits) return "tile is not 2^13 or 2^14 amplitudes";
     if (tp.c < 4) return "chunk smaller than 16 amplitudes";
     for (const TileOp &op : tp.ops)
@@ -182,7 +296,7 @@ std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen) {
     }
 
     std::map<std::pair<int, int>, int> slot_of;
-    std::map<std::vector<uint32_t>, int32_t> table_of;  // table phases -> first matrix record
+    std::map<std::vector<Ph>, int32_t> table_of;  // table phases -> first matrix record
     auto slot = [&](int i0, int i1) -> int {
         auto key = std::make_pair(i0, i1);
         auto it = slot_of.find(key);
@@ -229,9 +343,7 @@ std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen) {
         if (is_gate(op.type)) {
             T2Ins in{};
             in.op = (int8_t)(op.type == TOP_H ? T2_H : op.type == TOP_X ? T2_X : T2_GATE);
-            if (in.op == T2_GATE && (float)op.m[1] == 0.f && (float)op.m[3] == 0.f &&
-                (float)op.m[5] == 0.f && (float)op.m[7] == 0.f)
-                in.op = T2_RGATE;  // a real matrix (a rotation RY, for one)
+            if (in.op == T2_GATE && P::real(op.m)) in.op = T2_RGATE;  // a real matrix (a rotation RY, for one)
             // an uncontrolled rotation [[c, -s], [s, c]] runs as three shears;
             // with c < 0 it is -1 times the rotation by c' = -c, s' = -s, and
             // the sign joins the pass's closing scale
@@ -271,16 +383,12 @@ std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen) {
                 in.cidx = (int16_t)op.cbit;
             }
             if (in.op == T2_ROT) {
-                T2Mat m{};
-                m.m[0] = (float)rot_t;
-                m.m[1] = (float)rot_s;
-                in.aux = (int32_t)out->mats.size();
-                out->mats.push_back(m);
+                double m[8] = {};
+                m[0] = rot_t;
+                m[1] = rot_s;
+                in.aux = P::push_mat(out, m);
             } else if (in.op == T2_GATE || in.op == T2_RGATE) {
-                T2Mat m{};
-                for (int e = 0; e < 8; e++) m.m[e] = (float)op.m[e];
-                in.aux = (int32_t)out->mats.size();
-                out->mats.push_back(m);
+                in.aux = P::push_mat(out, op.m);
             }
             const int kind = in.op == T2_H ? 0 : in.op == T2_X ? 1 : in.op == T2_RGATE ? 2
                            : in.op == T2_ROT ? 3 : 4;
@@ -292,30 +400,30 @@ std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen) {
         }
         // ---- diagonal run against layout L
         const int r = run++;
-        uint32_t sl[kT2MaxQubits] = {};  // static linear coefficient of each tile bit
+        Ph sl[kT2MaxQubits] = {};  // static linear coefficient of each tile bit
         bool dyn[kT2MaxQubits] = {};     // tile bit with a per-tile (global) coefficient
         bool use_cst = false;
-        uint32_t rt[kT2RegBits][kMaxThreadBits] = {};  // register x thread pairs
-        uint32_t tt[kMaxThreadBits][kMaxThreadBits] = {};
-        std::map<int, uint32_t> rr;  // register-bit mask -> theta
+        Ph rt[kT2RegBits][kMaxThreadBits] = {};  // register x thread pairs
+        Ph tt[kMaxThreadBits][kMaxThreadBits] = {};
+        std::map<int, Ph> rr;  // register-bit mask -> theta
         for (int t = op.tb; t < op.te; t++) {
             const PhaseTerm &pt = tp.terms[t];
-            const uint32_t th = turns32(pt.theta);
+            const Ph th = P::ph(pt.theta);
             if (!th) continue;
             switch (pt.kind) {
                 case TERM_L:
                     sl[pt.a] += th;
                     break;
                 case TERM_G:
-                    out->tterms.push_back({r, -1, pt.a, -1, th, 0});
+                    tts.push_back({r, -1, pt.a, -1, th});
                     use_cst = true;
                     break;
                 case TERM_GG:
-                    out->tterms.push_back({r, -1, pt.a, pt.b, th, 0});
+                    tts.push_back({r, -1, pt.a, pt.b, th});
                     use_cst = true;
                     break;
                 case TERM_LG:
-                    out->tterms.push_back({r, pt.a, pt.b, -1, th, 0});
+                    tts.push_back({r, pt.a, pt.b, -1, th});
                     dyn[pt.a] = true;
                     break;
                 case TERM_LL: {
@@ -336,13 +444,13 @@ std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen) {
             }
         }
         // constants: (register mask, thread predicate 0 = all / t + 1) -> phase
-        std::map<std::pair<int, int>, uint32_t> cst;
+        std::map<std::pair<int, int>, Ph> cst;
         std::vector<T2Fac> facs;
         // a static row over the thread index: a constant, a constant on the
         // threads with one bit set (thread factors only: a register-bit
         // factor keeps such a row, so that the run can still become a phased
         // butterfly), or a complex row
-        auto add_factor = [&](int mask, const uint32_t *row, int sl0, int dmask) {
+        auto add_factor = [&](int mask, const Ph *row, int sl0, int dmask) {
             bool any = false;
             for (int tau = 0; tau < NT; tau++) any |= row[tau] != 0;
             int rowi = -1;
@@ -352,7 +460,7 @@ std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen) {
                 int single = -1;
                 if (!uniform && mask == 0)
                     for (int t = 0; t < TB && single < 0; t++) {
-                        const uint32_t th = row[1 << t];
+                        const Ph th = row[1 << t];
                         if (!th) continue;
                         bool ok = true;
                         for (int tau = 0; tau < NT && ok; tau++)
@@ -365,12 +473,11 @@ std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen) {
                 } else if (single >= 0) {
                     cst[{mask, single + 1}] += row[1 << single];
                 } else {
-                    rowi = (int)(out->statc.size() / (2 * (size_t)NT));
+                    rowi = (int)(P::nrowvals(out) / (2 * (size_t)NT));
                     for (int tau = 0; tau < NT; tau++) {
-                        float re, im;
-                        expi(row[tau], &re, &im);
-                        out->statc.push_back(re);
-                        out->statc.push_back(im);
+                        V re, im;
+                        P::ex(row[tau], &re, &im);
+                        P::push_row(out, re, im);
                     }
                 }
             }
@@ -388,12 +495,12 @@ std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen) {
             facs.push_back(f);
         };
         {  // thread factor (every amplitude of the thread)
-            uint32_t row[1 << (kT2MaxQubits - kT2RegBits)];
+            Ph row[1 << (kT2MaxQubits - kT2RegBits)];
             row[0] = 0;
             for (int tau = 1; tau < NT; tau++) {
                 const int b = __builtin_ctz((unsigned)tau);
                 const int prev = tau & (tau - 1);
-                uint32_t u = row[prev] + sl[L.ttb(b)];
+                Ph u = row[prev] + sl[L.ttb(b)];
                 for (int rest = prev; rest; rest &= rest - 1) u += tt[b][__builtin_ctz((unsigned)rest)];
                 row[tau] = u;
             }
@@ -405,7 +512,7 @@ std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen) {
         }
         for (int j = 0; j < kT2RegBits; j++) {  // one factor per register bit with a coefficient
             const int tb = L.reg[j];
-            uint32_t row[1 << (kT2MaxQubits - kT2RegBits)];
+            Ph row[1 << (kT2MaxQubits - kT2RegBits)];
             row[0] = sl[tb];
             for (int tau = 1; tau < NT; tau++)
                 row[tau] = row[tau & (tau - 1)] + rt[j][__builtin_ctz((unsigned)tau)];
@@ -414,7 +521,7 @@ std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen) {
         for (auto &kv : rr)
             if (kv.second) cst[{kv.first, 0}] += kv.second;
         // constants with the same thread predicate merge into one 32-entry table
-        std::map<int, std::vector<std::pair<int, uint32_t>>> group;
+        std::map<int, std::vector<std::pair<int, Ph>>> group;
         for (auto &kv : cst)
             if (kv.second) group[kv.first.second].push_back({kv.first.first, kv.second});
         T2Ins in{};
@@ -422,31 +529,19 @@ std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen) {
         in.hd = kT2HdDiag;
         in.e0 = (int16_t)out->fac2.size();
         for (auto &g : group) {
-            uint32_t u[32] = {};
+            Ph u[32] = {};
             for (auto &mc : g.second)
                 for (int x = 0; x < 32; x++)
                     if ((x & mc.first) == mc.first) u[x] += mc.second;
             // identical tables share their matrix records
-            std::vector<uint32_t> key(u, u + 32);
+            std::vector<Ph> key(u, u + 32);
             auto hit = table_of.find(key);
             int32_t m0;
             if (hit != table_of.end()) {
                 m0 = hit->second;
             } else {
-                m0 = (int32_t)out->mats.size();
+                m0 = P::push_table(out, u);
                 table_of[key] = m0;
-                float tab[64];
-                for (int x = 0; x < 32; x++) {
-                    float re, im;
-                    expi(u[x], &re, &im);
-                    tab[4 * (x >> 1) + (x & 1)] = re;
-                    tab[4 * (x >> 1) + 2 + (x & 1)] = im;
-                }
-                for (int m = 0; m < 8; m++) {
-                    T2Mat tm{};
-                    for (int e = 0; e < 8; e++) tm.m[e] = tab[8 * m + e];
-                    out->mats.push_back(tm);
-                }
             }
             T2Fac f{};
             f.w0 = kFacTable | ((uint32_t)g.first << 10);
@@ -463,13 +558,18 @@ std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen) {
     // each slot's terms (those of its two phase words), for the kernel
     out->soff.push_back(0);
     for (const T2Slot &sl : out->slots) {
-        for (const T2TileTerm &t : out->tterms) {
+        int nterm = 0;
+        for (const TT &t : tts) {
             const int li = t.run * 16 + (t.tb >= 0 ? t.tb : 15);
-            if (li == sl.i0 || (sl.i1 >= 0 && li == sl.i1))
-                out->sterms.push_back({(int16_t)t.g0, (int16_t)t.g1, t.theta});
+            if (li == sl.i0 || (sl.i1 >= 0 && li == sl.i1)) {
+                P::push_sterm(out, t.g0, t.g1, t.theta);
+                nterm++;
+            }
         }
-        out->soff.push_back((int32_t)out->sterms.size());
+        out->soff.push_back(out->soff.back() + nterm);
     }
+    if (!out->wide)  // the 32-bit tile terms, as the format-1 compiler records them
+        for (const TT &t : tts) out->tterms.push_back({t.run, t.tb, t.g0, t.g1, (uint32_t)t.theta, 0});
     // the phased butterfly: a run that is the identity where register bit j
     // is 0 (at most one unpredicated table, one per-thread factor on bit j)
     // directly followed by an uncontrolled H on register bit j
@@ -481,9 +581,7 @@ std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen) {
                 if (((f.w0 >> 10) & 0xfu) || ++ntab > 1) return false;
                 for (int x = 0; x < 32; x++) {
                     if ((x >> j) & 1) continue;
-                    const float *tf = out->mats[f.row + (x >> 2)].m;
-                    const int o = 4 * ((x >> 1) & 1) + (x & 1);
-                    if (tf[o] != 1.f || tf[o + 2] != 0.f) return false;
+                    if (!P::table_one(out, f.row, x)) return false;
                 }
             } else {
                 if ((f.w0 & 0xffu) != (1u << j) || ((f.w0 >> kFacDynShift) & 0x1ffu) || ++nthr > 1)
@@ -527,7 +625,7 @@ std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen) {
     }
     if (out->ins.size() > (size_t)kT2SmemIns || out->fac2.size() > (size_t)kT2SmemFactors)
         return "programme longer than the kernel's shared-memory copy";
-    if (out->mats.size() > (size_t)kT2SmemMats) return "more matrix records than the kernel's shared-memory copy";
+    if (P::nmats(out) > (size_t)kT2SmemMats) return "more matrix records than the kernel's shared-memory copy";
     for (size_t i = 0; i < out->ins.size(); i++)
         if (out->ins[i].op == T2_STAGE) out->last_stage = (int)i;
     // kernel-side layouts (linear and swizzled) and the write-back offsets
@@ -573,19 +671,23 @@ std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen) {
     }
     if (out->n_h || (out->sign_flips & 1)) {
         const double s = std::pow(2.0, -0.5 * out->n_h) * ((out->sign_flips & 1) ? -1.0 : 1.0);
-        const float hi = (float)s;
-        T2Mat m{};
-        m.m[0] = hi;
-        m.m[1] = (float)(s - (double)hi);
         T2Ins in{};
         in.op = T2_SCALE;
         in.hd = kT2HdScale;
-        in.aux = (int32_t)out->mats.size();
-        out->mats.push_back(m);
+        in.aux = P::push_scale(out, s);
         out->ins.push_back(in);
     }
-    if (out->mats.size() > (size_t)kT2SmemMats) return "more matrix records than the kernel's shared-memory copy";
+    if (P::nmats(out) > (size_t)kT2SmemMats) return "more matrix records than the kernel's shared-memory copy";
     return "";
+}
+
+}  // namespace
+
+std::string compile_t2v2(const TilePass &tp, T2Pass *out, bool gen) { return compile_fmt2<P32>(tp, out, gen); }
+
+std::string compile_t2v2_c128(const TilePass &tp, T2Pass *out, bool gen) {
+    if (tp.k != kT2Qubits) return "complex128 register-stage tiles hold 2^13 amplitudes";
+    return compile_fmt2<P64>(tp, out, gen);
 }
 
 }  // namespace sv

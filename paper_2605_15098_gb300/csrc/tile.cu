@@ -312,14 +312,15 @@ T2Off put_t2(Blob &blob, const T2Pass &t) {
     o.stages = blob.put_vec(t.stages);
     o.layx = blob.put_vec(t.layx);
     o.epi = blob.put(&t.epi, sizeof(T2Epilogue));
-    o.mats = blob.put_vec(t.mats);
+    // a complex128 programme's FP64 records take the places of the FP32 ones
+    o.mats = t.wide ? blob.put_vec(t.mats64) : blob.put_vec(t.mats);
     o.fac = t.format == 2 ? blob.put_vec(t.fac2) : blob.put_vec(t.factors);
     o.stat = blob.put_vec(t.stat);
-    o.statc = blob.put_vec(t.statc);
+    o.statc = t.wide ? blob.put_vec(t.statc64) : blob.put_vec(t.statc);
     o.slots = blob.put_vec(t.slots);
     o.tterms = blob.put_vec(t.tterms);
     o.soff = blob.put_vec(t.soff);
-    o.sterms = blob.put_vec(t.sterms);
+    o.sterms = t.wide ? blob.put_vec(t.sterms64) : blob.put_vec(t.sterms);
     return o;
 }
 
@@ -493,8 +494,9 @@ static sv_status compiled_plan(sv_state *h, const std::vector<sv_gate> &gates, c
     std::string err = build_plan(gates, opt, phys, &plan);
     if (!err.empty()) return fail(SV_ERR_ARG, "planner: %s", err.c_str());
 
-    // compile every pass; register-stage kernel where it applies
-    const bool allow_t2 = !dbl && !(cfg.flags & SV_FLAG_GENERIC_TILE);
+    // compile every pass; register-stage kernel where it applies (complex128:
+    // the FP64 variant on 2^13-amplitude tiles)
+    const bool allow_t2 = !(cfg.flags & SV_FLAG_GENERIC_TILE) && (!dbl || opt.k == kT2Qubits);
     const bool fused = cfg.mode == SV_MODE_FUSED;
     std::vector<T2Pass> &t2 = cp->t2;
     std::vector<PassUpload> &up = cp->up;
@@ -510,9 +512,21 @@ static sv_status compiled_plan(sv_state *h, const std::vector<sv_gate> &gates, c
         if (p.ops.empty()) continue;
         const bool first_ops = first_pass && p.remap_before.empty();
         first_pass = false;
-        const int want = ov ? ov->kernel[i] : (!allow_t2 ? PK_GENERIC : fused ? PK_T3 : PK_T2);
+        const int want = ov ? ov->kernel[i] : (!allow_t2 ? PK_GENERIC : fused && !dbl ? PK_T3 : PK_T2);
         bool ok = false;
-        if (want == PK_T3 && compile_t2(p, &t2[i], true).empty()) {
+        if (dbl) {
+            if (want != PK_GENERIC && allow_t2 && compile_t2v2_c128(p, &t2[i], false).empty()) {
+                ok = true;
+                if (first_ops) {
+                    auto g = std::make_shared<T2Pass>();
+                    if (compile_t2v2_c128(p, g.get(), true).empty()) {
+                        t2[i].genv = g;
+                        up[i].has_gen = true;
+                        up[i].gen = put_t2(blob, *g);
+                    }
+                }
+            }
+        } else if (want == PK_T3 && compile_t2(p, &t2[i], true).empty()) {
             ok = true;
             up[i].t3 = true;
             up[i].blocks = blob.put_vec(t2[i].blocks_dev);
@@ -707,6 +721,7 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
         any_t3 |= u.t3;
     }
     if (any_t2) SV_TRY(t2_prepare(h));
+    if (any_t2 && dbl) SV_TRY(tab64_prepare(h));
     if (any_t3) SV_TRY(t3_prepare(h));
 
     for (size_t i = 0; i < plan.passes.size(); i++) {
@@ -744,6 +759,7 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
             T2Device d = t2_device(dev, g ? up[i].gen : up[i].main);
             d.blocks = up[i].t3 ? reinterpret_cast<const float *>(dev + up[i].blocks) : nullptr;
             st = up[i].t3 ? t3_launch(h, t2[i], d, meta)
+                 : dbl    ? t2d_launch(h, g ? *t2[i].genv : t2[i], d, meta, gen)
                           : t2_launch(h, g ? *t2[i].genv : t2[i], d, meta, gen);
             if (st == SV_OK && gen >= 0) {
                 h->basis = -1;

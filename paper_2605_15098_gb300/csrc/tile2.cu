@@ -1062,9 +1062,9 @@ void t2_fill_args(const T2Pass &p, const T2Device &d, int n, T2Args *a) {
     a->c = p.c;
     a->nins = (int)p.ins.size();
     a->nfac = (int)p.fac2.size();
-    a->nrows = (int)(p.statc.size() / (2 * (size_t)p.threads));
+    a->nrows = (int)((p.wide ? p.statc64.size() : p.statc.size()) / (2 * (size_t)p.threads));
     a->nslots = (int)p.slots.size();
-    a->nmats = (int)p.mats.size();
+    a->nmats = (int)(p.wide ? p.mats64.size() / 8 : p.mats.size());
     a->nstages = (int)p.stages.size();
     a->last_stage = p.last_stage;
     for (int s = 0; s < p.k; s++) a->slot_phys[s] = p.slot_phys[s];
@@ -1136,7 +1136,8 @@ void t2_set_gen(const T2Pass &p, int64_t gen_basis, uint64_t basis_h, T2Args *a)
     a->gen_ghmask = basis_h & p.gmask;
     const int both = __builtin_popcount(p.gen_hmask & hq_local);
     const int hq_only = __builtin_popcountll(basis_h) - both;
-    a->gen_val = (float)std::pow(2.0, 0.5 * (both - hq_only));
+    a->gen_val64 = std::pow(2.0, 0.5 * (both - hq_only));
+    a->gen_val = (float)a->gen_val64;
 }
 
 sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_launch_record &meta,

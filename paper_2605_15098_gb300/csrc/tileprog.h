@@ -184,6 +184,12 @@ struct T2SlotTerm {
     int16_t g0, g1;
     uint32_t theta;
 };
+// The same with a 64-bit phase (complex128 kernel).
+struct T2SlotTerm64 {
+    int16_t g0, g1;
+    int32_t pad;
+    uint64_t theta;
+};
 
 // Handler codes of the non-gate steps (format 2), in the same field as the
 // gate handlers: the kernel dispatches every step with one switch.
