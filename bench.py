@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-random", action="store_true", help="skip the random-circuit n = 30, 32 timing")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the errors against the oracle")
     ap.add_argument("--no-l2", action="store_true", help="skip the L2 block group timing")
+    ap.add_argument("--no-cpu-part", action="store_true", help="skip the partitioned CPU baseline")
     ap.add_argument("--l2-sweep", type=int, default=0, metavar="N",
                     help="only run QPE-N once per L2 block size (for an ncu capture) and print its launches")
     ap.add_argument("--batch", type=int, default=4096)
@@ -397,6 +398,32 @@ def l2_blocks(sv, C, stream) -> dict:
 
 
 SWEEP_N = (20, 24, 28, 30, 32)
+
+
+def cpu_partitioned(C) -> dict:
+    """The paper's CPU finding (partitioning does not pay on a CPU), on the
+    host cores: QPE n = 22 (64 MiB in FP64), the whole circuit, with the
+    oracle's plain Algorithm 1 (one sweep per gate) and with the partitioned
+    CPU program at block sizes of 2^12 .. 2^20 amplitudes (cpupart.c).  Both
+    use every host thread; the two states must agree within 1e-12."""
+    from oracle import oracle as orc
+    from paper_2605_15098_gb300 import cpupart
+
+    n = 22
+    g, _, _ = C.qpe(n)
+    t0 = time.perf_counter()
+    ref = orc.run(n, g)
+    t_plain = time.perf_counter() - t0
+    rows = {}
+    for l in (12, 16, 18, 20):
+        t0 = time.perf_counter()
+        got, st = cpupart.run(n, g, l)
+        dt_ = time.perf_counter() - t0
+        rows[f"block_2^{l}"] = {"ms": round(dt_ * 1e3, 2), "flushes": st["passes"], "swaps": st["swaps"],
+                                "max_abs_err_vs_oracle": float(np.max(np.abs(got - ref))),
+                                "speedup_vs_plain": round(t_plain / dt_, 3)}
+    return {"workload": f"QPE n={n} complex128 ({len(g)} gates), host CPU", "threads": cpupart.num_threads(),
+            "plain_algorithm1_ms": round(t_plain * 1e3, 2), "partitioned": rows}
 
 
 def qpe_sweep(sv, C, stream, peak: float, no_pergate: bool, cfgs: dict) -> dict:
@@ -870,6 +897,8 @@ def run_ours(args, world, rank, local):
             "sample": sample}
         if dt == sv.SV_C64 and not args.no_accuracy:
             out["accuracy"] = accuracy_rows(sv, C, sweep_cfgs, batch_res)
+        if not args.no_cpu_part:
+            out["cpu_partitioned"] = cpu_partitioned(C)
     if dist:
         dist.destroy_process_group()
     if rank == 0:
