@@ -85,6 +85,7 @@ void put_t2(J &j, const T2Pass &t) {
     j.arr(t.stat.data(), (int)t.stat.size());
     j.raw(",\"format\":"); j.num(t.format);
     j.raw(",\"gen_hmask\":"); j.num(t.gen_hmask);
+    j.raw(",\"gen_scale\":"); j.dbl(t.gen_scale);
     j.raw(",\"fac2\":[");
     for (size_t i = 0; i < t.fac2.size(); i++) {
         const T2Fac &f = t.fac2[i];

@@ -48,6 +48,9 @@ struct T2Pass {
     // from a recorded basis state (generated in registers, leading Hadamards
     // included); null when not compiled
     std::shared_ptr<T2Pass> genv;
+    // the gen variant: the pass's closing scale (2^(-n_h/2), sign flips),
+    // multiplied into the generated state instead of applied at the end
+    double gen_scale = 1.0;
     std::vector<T2TileTerm> tterms;
     int nblocks = 0;
     std::vector<double> blocks64;   // fused: per block 2 x 32 x 32 (re, im), row = output index

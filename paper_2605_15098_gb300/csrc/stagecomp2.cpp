@@ -602,6 +602,22 @@ std::string compile_fmt2(const TilePass &tp, T2Pass *out, bool gen) {
                     f.e0 = d.e0;
                     f.e1 = d.e1;
                     f.hd = (int16_t)(kT2Handler + 8 * 5 + hh.idx);
+                    // the run's table, static row and slot, also in the step
+                    // itself (tileprog.h: T2_HPH), so that the complex64 kernel
+                    // reads them without the factor records
+                    int trec = -1, row = -1, sl = -1;
+                    for (int e = d.e0; e < d.e1; e++) {
+                        const T2Fac &fc = out->fac2[e];
+                        if (fc.w0 & kFacTable) {
+                            trec = fc.row;
+                        } else {
+                            row = fc.row;
+                            sl = fc.slot;
+                        }
+                    }
+                    f.ccls = kT2HphDirect;
+                    f.cidx = (int16_t)sl;
+                    f.aux = (int32_t)(((uint32_t)(row + 1) << 16) | (uint32_t)(trec + 1));
                     merged.push_back(f);
                     i++;
                     continue;
@@ -671,6 +687,12 @@ std::string compile_fmt2(const TilePass &tp, T2Pass *out, bool gen) {
     }
     if (out->n_h || (out->sign_flips & 1)) {
         const double s = std::pow(2.0, -0.5 * out->n_h) * ((out->sign_flips & 1) ? -1.0 : 1.0);
+        if (gen) {
+            // every step is linear: the pass that generates its starting
+            // state generates it times the closing scale instead
+            out->gen_scale = s;
+            return "";
+        }
         T2Ins in{};
         in.op = T2_SCALE;
         in.hd = kT2HdScale;

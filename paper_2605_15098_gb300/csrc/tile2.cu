@@ -202,15 +202,35 @@ __device__ __forceinline__ void apply_table_s(RegsN<NP> &r, const float4 *T, uin
 }
 
 // Phased Hadamard on register bit J: the amplitude b of each pair (bit J = 1)
-// is multiplied by M = (fr + i fi) T[x] (T: a 32-entry phase table in shared
-// memory laid out as for apply_table_s; the identity table when the run has
-// none), then the pair becomes (a + M b, a - M b).  Butterflies are grouped
-// four at a time as in reg_h2.  M's imaginary part is formed with both signs
-// from the table and (fr, fi), so no operand needs negating.
+// is multiplied by T[x] (a 32-entry phase table in shared memory laid out as
+// for apply_table_s), then by the per-thread factor (fr + i fi), and the pair
+// becomes (a + p, a - p) with p that product.  Butterflies are grouped four at
+// a time as in reg_h2.  Without a table (`tab` false: the run's phase is the
+// per-thread factor alone, as for the first Hadamard of a stage in an inverse
+// QFT) the table product is skipped.
 template <int J, int NP>
-__device__ __forceinline__ void reg_hph_s(RegsN<NP> &r, uint32_t qm, const float4 *T, float fr, float fi) {
-    const float2 Fr = f2(fr), Fi = f2(fi), Fnr = f2(-fr), Fni = f2(-fi);
+__device__ __forceinline__ void reg_hph_s(RegsN<NP> &r, uint32_t qm, const float4 *T, bool tab, float fr,
+                                          float fi) {
+    const float2 Fr = f2(fr), Fi = f2(fi), Fni = f2(-fi);
     if constexpr (J >= 1) {
+        if (!tab) {
+#pragma unroll
+            for (int g = 0; g < NP / 8; g++) {
+                if (!((qm >> g) & 1)) continue;
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const int q = bfly_q<J>(4 * g + i), q1 = q | (1 << (J - 1));
+                    const float2 br = r.re[q1], bi = r.im[q1];
+                    const float2 pr = fma2(bi, Fni, mul2(br, Fr));
+                    const float2 pi = fma2(bi, Fr, mul2(br, Fi));
+                    r.re[q1] = sub2(r.re[q], pr);
+                    r.im[q1] = sub2(r.im[q], pi);
+                    r.re[q] = add2(r.re[q], pr);
+                    r.im[q] = add2(r.im[q], pi);
+                }
+            }
+            return;
+        }
 #pragma unroll
         for (int g = 0; g < NP / 8; g++) {
             if (!((qm >> g) & 1)) continue;
@@ -219,12 +239,12 @@ __device__ __forceinline__ void reg_hph_s(RegsN<NP> &r, uint32_t qm, const float
                 const int q = bfly_q<J>(4 * g + i), q1 = q | (1 << (J - 1));
                 const float4 t = T[q1];
                 const float2 tr = make_float2(t.x, t.y), ti = make_float2(t.z, t.w);
-                const float2 mr = fma2(ti, Fni, mul2(tr, Fr));
-                const float2 mi = fma2(ti, Fr, mul2(tr, Fi));
-                const float2 nmi = fma2(ti, Fnr, mul2(tr, Fni));
-                const float2 br = r.re[q1], bi = r.im[q1];
-                const float2 pr = fma2(bi, nmi, mul2(br, mr));
-                const float2 pi = fma2(bi, mr, mul2(br, mi));
+                const float2 nti = make_float2(-t.z, -t.w);
+                const float2 b0r = r.re[q1], b0i = r.im[q1];
+                const float2 br = fma2(b0i, nti, mul2(b0r, tr));  // T b
+                const float2 bi = fma2(b0i, tr, mul2(b0r, ti));
+                const float2 pr = fma2(bi, Fni, mul2(br, Fr));    // F (T b)
+                const float2 pi = fma2(bi, Fr, mul2(br, Fi));
                 r.re[q1] = sub2(r.re[q], pr);
                 r.im[q1] = sub2(r.im[q], pi);
                 r.re[q] = add2(r.re[q], pr);
@@ -238,8 +258,12 @@ __device__ __forceinline__ void reg_hph_s(RegsN<NP> &r, uint32_t qm, const float
 #pragma unroll
             for (int i = 0; i < 4; i++) {
                 const int q = 4 * g4 + i;
-                const float4 t = T[q];  // odd entries (bit 0 set): y and w
-                const float mr = t.y * fr - t.w * fi, mi = t.y * fi + t.w * fr;
+                float mr = fr, mi = fi;
+                if (tab) {
+                    const float4 t = T[q];  // odd entries (bit 0 set): y and w
+                    mr = t.y * fr - t.w * fi;
+                    mi = t.y * fi + t.w * fr;
+                }
                 float2 &x = r.re[q], &y = r.im[q];
                 const float pr = x.y * mr - y.y * mi, pi = x.y * mi + y.y * mr;
                 x.y = x.x - pr;
@@ -309,10 +333,24 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, uint64_t
                 ph = thread_factor(fd);
         }
     };
+    // the same from the step itself: its table, static row and slot are
+    // independent loads (no factor record first)
+    auto hph_direct = [&](const int4 w, const float4 *&T, float2 &ph) {
+        const int trec = (int)((uint32_t)w.w & 0xffffu) - 1, row = (int)((uint32_t)w.w >> 16) - 1;
+        const int sl = (int16_t)(w.y & 0xffff);
+        T = trec >= 0 ? M + 2 * trec : ones;
+        ph = make_float2(1.f, 0.f);
+        if (row >= 0)
+            ph = row < kT2SmemRows ? rows[row * G::kThreads + tid]
+                                   : __ldg(a.statc + (size_t)row * G::kThreads + tid);
+        if (sl >= 0) ph = cx(ph, slotc[sl]);
+    };
     // loop bounds in registers: `a` may live in memory the compiler cannot
     // prove unchanged by the tile's shared-memory stores (the L2 block kernel
     // indexes its passes' arguments)
     const int nins = a.nins, last_stage = a.last_stage;
+    // the next step's record is read while this one runs (the dispatch
+    // depends on it); the read past the last step stays inside shared memory
     for (int pc = 0; pc < nins; pc++) {
         const int4 w = ins[pc];
         // all ones at run time (the handler code is below 256), opaque to the
@@ -345,19 +383,37 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, uint64_t
                         // the product state H^{hq}|b>, generated instead of
                         // read: +-v where the index agrees with b off the
                         // Hadamard qubits (global ones decide the whole tile),
-                        // with the sign of the parity of b on them, 0 elsewhere
-                        const bool has = ((a.gen_basis ^ base) & a.gmask & ~a.gen_ghmask) == 0;
-                        const uint32_t gneg = (uint32_t)__popcll(base & a.gen_basis & a.gen_ghmask) & 1u;
+                        // with the sign of the parity of b on them, 0 elsewhere.
+                        // Element x of the register index (bit 0: the element
+                        // of a packed pair, bits 1..4: register bits 1..4) sits
+                        // at tile index bt + sum of the s_k of its set bits, so
+                        // both conditions split into a per-thread part and one
+                        // bit mask over the 32 elements each.
                         const uint32_t gl = (uint32_t)a.gen_local, hm = a.gen_hmask;
-                        const float v = a.gen_val;
-                        auto amp = [&](uint32_t i) -> float {
-                            if (!has || ((i ^ gl) & ~hm)) return 0.f;
-                            return ((__popc(i & gl & hm) ^ gneg) & 1) ? -v : v;
+                        const uint32_t pos[5] = {1u, (uint32_t)L.s1, (uint32_t)L.s2, (uint32_t)L.s3,
+                                                 (uint32_t)L.s4};
+                        const uint32_t R = pos[0] | pos[1] | pos[2] | pos[3] | pos[4];
+                        const uint32_t bt = (uint32_t)L.bt;
+                        bool has = ((a.gen_basis ^ base) & a.gmask & ~a.gen_ghmask) == 0;
+                        has = has && ((bt ^ gl) & ~hm & ~R) == 0;
+                        uint32_t neg = (((uint32_t)__popcll(base & a.gen_basis & a.gen_ghmask) ^
+                                         (uint32_t)__popc(bt & gl & hm)) & 1u) ? ~0u : 0u;
+                        uint32_t nz = has ? ~0u : 0u;
+                        // x's bit k set: the elements of the k-th alternating bit mask
+                        const uint32_t Mk[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u,
+                                                0xFFFF0000u};
+#pragma unroll
+                        for (int k = 0; k < 5; k++) {
+                            if (pos[k] & ~hm) nz &= (gl & pos[k]) ? Mk[k] : ~Mk[k];
+                            if (pos[k] & gl & hm) neg ^= Mk[k];
+                        }
+                        const uint32_t vb = __float_as_uint(a.gen_val);
+                        auto amp = [&](int x) -> float {
+                            return __uint_as_float((((neg >> x) & 1u) << 31 ^ vb) & (0u - ((nz >> x) & 1u)));
                         };
 #pragma unroll
                         for (int q = 0; q < kNP2; q++) {
-                            const uint32_t i0 = 2u * (uint32_t)L.idx(q);
-                            r.re[q] = make_float2(amp(i0), amp(i0 + 1));
+                            r.re[q] = make_float2(amp(2 * q), amp(2 * q + 1));
                             r.im[q] = make_float2(0.f, 0.f);
                         }
                     } else {  // the bulk copies' linear order: lane bits 0..2 are tile bits 1..3
@@ -414,8 +470,11 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, uint64_t
     case kT2Handler + 8 * 5 + J: {                           \
         const float4 *T;                                     \
         float2 ph;                                           \
-        hph_run(w, T, ph);                                   \
-        reg_hph_s<J>(r, qm, T, ph.x, ph.y);                  \
+        if ((int8_t)(w.x >> 24) == kT2HphDirect)             \
+            hph_direct(w, T, ph);                            \
+        else                                                 \
+            hph_run(w, T, ph);                               \
+        reg_hph_s<J>(r, qm, T, T != ones, ph.x, ph.y);       \
         continue;                                            \
     }
             SV_HPH_CASE(0)
@@ -480,23 +539,38 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, uint64_t
     }
     if (!live) return;
     const T2Epilogue *E = reinterpret_cast<const T2Epilogue *>(t2_dyn_smem + G::kOffEpi);
-    const uint64_t g0 = base + E->glo[tid & 31] + E->ghi[tid >> 5];
-    const uint64_t g1 = E->g[0], g2 = E->g[1], g3 = E->g[2], g4 = E->g[3];
-    if (a.keep) {  // the next pass of an L2 block reads it: plain stores
+    // offsets inside the state, in 16-byte vectors from the tile's base (bit 0
+    // of every amplitude offset is a tile bit, so they are even); 32 bits wide
+    // while the state holds at most 2^33 amplitudes
+    float4 *gt = gstate + (base >> 1);
+    if (a.ntiles <= (UINT64_C(1) << (33 - K))) {
+        const uint32_t o0 = (uint32_t)((E->glo[tid & 31] + E->ghi[tid >> 5]) >> 1);
+        const uint32_t o1 = (uint32_t)(E->g[0] >> 1), o2 = (uint32_t)(E->g[1] >> 1);
+        const uint32_t o3 = (uint32_t)(E->g[2] >> 1), o4 = (uint32_t)(E->g[3] >> 1);
+        auto off = [&](int q) {
+            return o0 + ((q & 1) ? o1 : 0u) + ((q & 2) ? o2 : 0u) + ((q & 4) ? o3 : 0u) + ((q & 8) ? o4 : 0u);
+        };
+        if (a.keep) {  // the next pass of an L2 block reads it: plain stores
 #pragma unroll
-        for (int q = 0; q < kNP2; q++) {
-            const uint64_t g = g0 + ((q & 1) ? g1 : 0) + ((q & 2) ? g2 : 0) + ((q & 4) ? g3 : 0) +
-                               ((q & 8) ? g4 : 0);
-            gstate[g >> 1] = make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y);
+            for (int q = 0; q < kNP2; q++) gt[off(q)] = make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y);
+            return;
         }
+#pragma unroll
+        for (int q = 0; q < kNP2; q++) __stcs(gt + off(q), make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y));
+        return;
+    }
+    const uint64_t g0 = E->glo[tid & 31] + E->ghi[tid >> 5];
+    const uint64_t g1 = E->g[0], g2 = E->g[1], g3 = E->g[2], g4 = E->g[3];
+    auto off64 = [&](int q) {
+        return (g0 + ((q & 1) ? g1 : 0) + ((q & 2) ? g2 : 0) + ((q & 4) ? g3 : 0) + ((q & 8) ? g4 : 0)) >> 1;
+    };
+    if (a.keep) {
+#pragma unroll
+        for (int q = 0; q < kNP2; q++) gt[off64(q)] = make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y);
         return;
     }
 #pragma unroll
-    for (int q = 0; q < kNP2; q++) {
-        const uint64_t g = g0 + ((q & 1) ? g1 : 0) + ((q & 2) ? g2 : 0) + ((q & 4) ? g3 : 0) +
-                           ((q & 8) ? g4 : 0);
-        __stcs(gstate + (g >> 1), make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y));
-    }
+    for (int q = 0; q < kNP2; q++) __stcs(gt + off64(q), make_float4(r.re[q].x, r.im[q].x, r.re[q].y, r.im[q].y));
 }
 
 // Physical base index of tile `tile`: its index bits spread over the runs of
@@ -1136,7 +1210,7 @@ void t2_set_gen(const T2Pass &p, int64_t gen_basis, uint64_t basis_h, T2Args *a)
     a->gen_ghmask = basis_h & p.gmask;
     const int both = __builtin_popcount(p.gen_hmask & hq_local);
     const int hq_only = __builtin_popcountll(basis_h) - both;
-    a->gen_val64 = std::pow(2.0, 0.5 * (both - hq_only));
+    a->gen_val64 = std::pow(2.0, 0.5 * (both - hq_only)) * p.gen_scale;
     a->gen_val = (float)a->gen_val64;
 }
 

@@ -65,6 +65,9 @@ enum T2Op : int32_t {
     T2_HPH = 9,    // diagonal run [e0, e1) then H on register bit idx, in one sweep:
                    // the run is the identity where bit idx is 0, and holds at
                    // most one phase table and one per-thread factor on bit idx
+                   // (no dynamic thread bits); with ccls == kT2HphDirect the
+                   // step also names them: aux = (row + 1) << 16 | (table + 1)
+                   // (0 = none), cidx = the factor's slot (-1 = none)
     T2_HG = 10     // H of the programme's leading Hadamards (distinct tile bits, before
                    // any other step): a pass that generates a basis state generates
                    // the state after them and skips them; otherwise an H
@@ -90,6 +93,8 @@ constexpr int kMaxBlocks = 4;  // shared-memory block slots; more blocks stream 
 constexpr int kT2Handler = 16;
 
 enum T2Class : int32_t { T2C_NONE = 0, T2C_REG = 1, T2C_LANE = 2, T2C_THREAD = 3, T2C_GLOBAL = 4 };
+// control-class field of a T2_HPH step whose table, row and slot are in the step
+constexpr int8_t kT2HphDirect = 0x40;
 
 // One programme step, 16 bytes (one vector load in the kernel).
 struct T2Ins {

@@ -120,7 +120,8 @@ def run_t2_pass(state, p, t2=None, gen_basis=None, gen_h=0, bases=None):
     state H^{gen_h}|gen_basis> (H on the physical qubits of the mask gen_h)
     and generates its tiles instead of reading them (the programme is then the
     pass's generated-state variant, `t2gen`, whose own leading Hadamards on
-    tile bits are unnormalised: its closing scale holds their 2^(-1/2)).
+    tile bits are unnormalised: its closing scale, `gen_scale`, which holds
+    their 2^(-1/2), multiplies the generated state).
     `bases`: run only the tiles with these physical base indices, in order
     (default: every tile, in index order)."""
     t2 = t2 if t2 is not None else p["t2"]
@@ -153,7 +154,8 @@ def run_t2_pass(state, p, t2=None, gen_basis=None, gen_h=0, bases=None):
             has = ((gen_basis ^ base) & p["gmask"] & ~ghm) == 0
             gneg = bin(base & gen_basis & ghm).count("1") & 1
             both = bin(P & hq_local).count("1")
-            v = 2.0 ** (0.5 * (both - (bin(gen_h).count("1") - both)))
+            # the variant's closing scale is part of the generated state
+            v = 2.0 ** (0.5 * (both - (bin(gen_h).count("1") - both))) * t2.get("gen_scale", 1.0)
             par = np.array([(bin(int(i) & gl & hm).count("1") + gneg) & 1 for i in loc])
             t = np.where(((loc ^ gl) & ~hm) == 0, np.where(par == 1, -v, v), 0.0).astype(complex)
             if not has:
