@@ -149,6 +149,7 @@ sv_status sv_destroy(sv_handle h) {
     if (h->probs) cudaFree(h->probs);
     if (h->small) cudaFree(h->small);
     if (h->grp) cudaFree(h->grp);
+    if (h->slotv) cudaFree(h->slotv);
     h->plan_cache.clear();  // frees each entry's device copy
     if (h->plan_dev) cudaFree(h->plan_dev);
     if (h->plan_host) cudaFreeHost(h->plan_host);

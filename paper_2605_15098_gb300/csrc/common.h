@@ -80,6 +80,8 @@ struct sv_state {
     void *small = nullptr;        // 64 KiB device area for reduction partials
     void *grp = nullptr;          // L2 block groups: done counters and claim queue
     size_t grp_cap = 0;
+    void *slotv = nullptr;        // per-tile slot values of the register-stage passes
+    size_t slotv_cap = 0;
     uint8_t *meas_dev = nullptr;  // outcomes of the last call's measurements
     size_t meas_cap = 0;
     size_t nmeas = 0;

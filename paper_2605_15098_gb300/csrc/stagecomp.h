@@ -112,7 +112,19 @@ struct T2Args {
     // an L2 block reads it)
     int keep;
     double gen_val64;  // gen_val in FP64 (complex128 kernel)
+    // the tile-uniform slot values computed for every tile before the launch
+    // (k_slotv: nsp values per tile, nslots rounded up to even, so that one
+    // tile's values are one 16-byte-multiple bulk copy); NULL: each tile
+    // computes its own
+    const float2 *slotv;
+    int nsp;
 };
+
+// Bytes of the per-tile slot values of a complex64 register-stage pass
+// (T2Args::slotv), 0 when the pass computes them per tile: no slots, or more
+// than kSlotvMaxBytes.
+constexpr size_t kSlotvMaxBytes = (size_t)256 << 20;
+size_t t2_slotv_bytes(const T2Pass &p, int n);
 
 // Fill the counts, pointers and geometry of a format-2 pass (not gen,
 // tables or err).

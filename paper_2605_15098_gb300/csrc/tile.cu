@@ -722,6 +722,28 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
     }
     if (any_t2) SV_TRY(t2_prepare(h));
     if (any_t2 && dbl) SV_TRY(tab64_prepare(h));
+    if (any_t2 && !dbl) {  // the per-tile slot values of the one-level register-stage passes
+        size_t need = 0;
+        for (size_t i = 0; i < up.size(); i++) {
+            if (!up[i].t2 || up[i].t3 || cp->group_at[i] >= 0) continue;
+            need = std::max(need, t2_slotv_bytes(t2[i], h->n));
+            if (t2[i].genv) need = std::max(need, t2_slotv_bytes(*t2[i].genv, h->n));
+        }
+        if (need > h->slotv_cap) {
+            if (h->slotv) {
+                SV_CUDA(cudaStreamSynchronize(h->stream));
+                cudaFree(h->slotv);
+            }
+            h->slotv = nullptr;
+            h->slotv_cap = 0;
+            if (dev_malloc(&h->slotv, need) != cudaSuccess) {
+                cudaGetLastError();
+                h->slotv = nullptr;
+                return fail(SV_ERR_OOM, "cannot allocate the per-tile slot values (%zu bytes)", need);
+            }
+            h->slotv_cap = need;
+        }
+    }
     if (any_t3) SV_TRY(t3_prepare(h));
 
     for (size_t i = 0; i < plan.passes.size(); i++) {

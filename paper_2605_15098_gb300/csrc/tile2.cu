@@ -582,15 +582,20 @@ __device__ __forceinline__ uint64_t tile_base(const T2Args &a, uint64_t tile) {
     return b;
 }
 
+// The tile's bulk copies (warp 0); with `slots` the tile's precomputed slot
+// values come on the same barrier.
 template <int K>
 __device__ __forceinline__ void issue_tile_load(const T2Args &a, unsigned char *sm, const float *state,
-                                                uint64_t tile, uint64_t *bar, int tid) {
+                                                uint64_t tile, uint64_t *bar, int tid,
+                                                float2 *slots = nullptr) {
     const int nchunks = 1 << (K - a.c);
     const uint32_t chunk_bytes = 8u << a.c;
     const uint64_t base = tile_base(a, tile);
     if (tid == 0) {
         fence_async_smem();
-        mbar_expect_tx(bar, Geo<K>::kTileBytes);
+        const uint32_t sb = slots ? (uint32_t)a.nsp * 8u : 0u;
+        mbar_expect_tx(bar, Geo<K>::kTileBytes + sb);
+        if (slots) bulk_g2s(slots, a.slotv + tile * (uint64_t)a.nsp, sb, bar);
     }
     __syncwarp();
     for (int j = tid; j < nchunks; j += 32) {
@@ -649,6 +654,34 @@ __device__ __forceinline__ void tile_slots(const T2Args &a, const float2 *tab, f
     }
 }
 
+// The slot values of every tile of a pass (the same sums and table products
+// as tile_slots, one thread per tile and slot), computed before the pass so
+// that its tiles receive them with their bulk copies.
+__global__ void k_slotv(const T2Args a, float2 *__restrict__ out) {
+    const uint64_t total = a.ntiles * (uint64_t)a.nsp;
+    const float2 *tab = a.tables;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t tile = i / (uint64_t)a.nsp;
+        const int sl = (int)(i - tile * (uint64_t)a.nsp);
+        float2 v = make_float2(1.f, 0.f);
+        if (sl < a.nslots) {
+            const uint64_t base = tile_base(a, tile);
+            uint32_t u = 0;
+            const int t1 = __ldg(a.soff + sl + 1);
+            for (int t = __ldg(a.soff + sl); t < t1; t++) {
+                const T2SlotTerm st = a.sterms[t];
+                bool on = (base >> st.g0) & 1;
+                if (st.g1 >= 0) on = on && ((base >> st.g1) & 1);
+                if (on) u += st.theta;
+            }
+            v = cx(cx(__ldg(tab + (u >> 24)), __ldg(tab + kTabN + ((u >> 16) & 255u))),
+                   cx(__ldg(tab + 2 * kTabN + ((u >> 8) & 255u)), __ldg(tab + 3 * kTabN + (u & 255u))));
+        }
+        out[i] = v;
+    }
+}
+
 // Persistent CTA over the pass's tiles.  Tile i+1's bulk copies start as
 // soon as tile i's last stage change has read shared memory, so they overlap
 // the rest of tile i's programme and its write-back, which goes from
@@ -673,8 +706,21 @@ __global__ void __launch_bounds__(Geo<K>::kThreads, K == kT2Qubits ? 2 : 1)
         fence_mbar_init();
     }
     __syncthreads();
-    if (!a.gen && tid < 32 && (uint64_t)blockIdx.x < a.ntiles)
-        issue_tile_load<K>(a, sm, state, blockIdx.x, bar, tid);
+    // precomputed slot values: tile t's arrive with its copies (a pass that
+    // generates its state copies only them), into the slot buffer the previous
+    // tile did not use
+    const bool pre = a.slotv != nullptr;
+    auto issue_slots_only = [&](uint64_t t, float2 *dst) {
+        fence_async_smem();
+        mbar_expect_tx(bar, (uint32_t)a.nsp * 8u);
+        bulk_g2s(dst, a.slotv + t * (uint64_t)a.nsp, (uint32_t)a.nsp * 8u, bar);
+    };
+    if ((uint64_t)blockIdx.x < a.ntiles) {
+        if (!a.gen && tid < 32)
+            issue_tile_load<K>(a, sm, state, blockIdx.x, bar, tid, pre ? slotc : nullptr);
+        else if (a.gen && pre && tid == 0)
+            issue_slots_only(blockIdx.x, slotc);
+    }
 
     uint32_t parity = 0, rd = 0, buf = 0;
     for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
@@ -684,8 +730,8 @@ __global__ void __launch_bounds__(Geo<K>::kThreads, K == kT2Qubits ? 2 : 1)
         // buffer the previous tile did not use (every warp passed that tile's
         // barrier below, so none still reads the one before)
         float2 *sc = slotc + buf * kT2MaxSlots;
-        tile_slots<K>(a, tab, sc, base, tid);
-        const bool timed_out = a.gen ? false : !mbar_wait(bar, parity);
+        if (!pre) tile_slots<K>(a, tab, sc, base, tid);
+        const bool timed_out = (a.gen && !pre) ? false : !mbar_wait(bar, parity);
         if (__syncthreads_or(timed_out)) {
             if (tid == 0) atomicExch(a.err, 1);
             mbar_wait(bar, parity);  // give copies still in flight a second bounded wait
@@ -693,9 +739,12 @@ __global__ void __launch_bounds__(Geo<K>::kThreads, K == kT2Qubits ? 2 : 1)
         }
         // the next tile's copies, once every warp has read the last layout
         auto hook = [&]() {
+            float2 *nsc = slotc + (buf ^ 1u) * kT2MaxSlots;
             if (!a.gen && tid < 32 && next < a.ntiles) {
                 if (!mbar_wait(rbar, (rd - 1u) & 1u)) atomicExch(a.err, 1);
-                issue_tile_load<K>(a, sm, state, next, bar, tid);
+                issue_tile_load<K>(a, sm, state, next, bar, tid, pre ? nsc : nullptr);
+            } else if (a.gen && pre && tid == 0 && next < a.ntiles) {
+                issue_slots_only(next, nsc);
             }
         };
         t2_run<K, F>(a, reinterpret_cast<float4 *>(state), rbar, rd, base, sc, hook);
@@ -1085,6 +1134,13 @@ __global__ void k_phase_tables(float2 *t) {
 
 size_t t2_smem_bytes() { return kSmemBytes; }
 
+size_t t2_slotv_bytes(const T2Pass &p, int n) {
+    if (p.slots.empty() || p.wide) return 0;
+    const size_t nsp = (p.slots.size() + 1) & ~(size_t)1;
+    const size_t bytes = ((size_t)1 << (n - p.k)) * nsp * sizeof(float2);
+    return bytes <= kSlotvMaxBytes ? bytes : 0;
+}
+
 int t2_gate_kinds(const T2Pass &p) {
     int need = 0;
     for (const T2Ins &in : p.ins)
@@ -1224,6 +1280,18 @@ sv_status t2_launch(sv_state *h, const T2Pass &p, const T2Device &d, const sv_la
     a.tables = reinterpret_cast<const float2 *>(h->t2_tables);
     a.err = h->t2_err;
     if (p.k != 13 && p.k != 14) return fail(SV_ERR_ARG, "internal: register-stage tile of 2^%d", p.k);
+    // the tiles' slot values, computed ahead into the handle's buffer (sized
+    // by t2_slotv_bytes before the first launch of the call)
+    const size_t sbytes = t2_slotv_bytes(p, h->n);
+    if (sbytes && sbytes <= h->slotv_cap) {
+        a.nsp = (int)((p.slots.size() + 1) & ~(size_t)1);
+        a.slotv = reinterpret_cast<const float2 *>(h->slotv);
+        const uint64_t total = a.ntiles * (uint64_t)a.nsp;
+        const unsigned blocks = (unsigned)std::min<uint64_t>((total + 255) / 256, (uint64_t)h->sm_count * 8);
+        k_slotv<<<blocks, 256, 0, h->stream>>>(a, reinterpret_cast<float2 *>(h->slotv));
+        SV_CUDA(cudaGetLastError());
+        note_launch();
+    }
     // the smallest instantiation whose gate kinds cover the programme
     const int need = t2_gate_kinds(p);
     auto kern = need == 0 ? k_tile2<13, 0>

@@ -128,8 +128,11 @@ __device__ __forceinline__ void cmul1(float &re, float &im, float fr, float fi) 
     re = nr;
     im = ni;
 }
+// Complex product with its rounding fixed (one product rounded, then a fused
+// multiply-add), so that every kernel that forms a value with it gets the same
+// bits whatever the compiler's contraction choices.
 __device__ __forceinline__ float2 cx(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return make_float2(__fmaf_rn(a.x, b.x, __fmul_rn(-a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
 }
 
 template <int NP>
