@@ -285,14 +285,16 @@ def replica_value(world: int, steps: int, max_ms: float) -> float:
 
 
 RANDOM_N = (30, 32)
+RANDOM_PERGATE_C128_N = 30  # the per-gate complex128 baseline of the random circuits
 
 
 def random_circuits(sv, C, stream, peak: float) -> dict:
     """Random circuits (layers of U3 on every qubit, then CZ on a random
     matching) at n = 30 and 32, depth 40, complex64: the register-stage passes
     (library defaults) and the fused tensor-core passes (SV_MODE_FUSED), one
-    warm-up and one timed run each.  Every step ends with the argmax of the
-    lowest 10 qubits, and both paths must agree on it."""
+    warm-up and one timed run each; at n = 30 also the per-gate kernel in
+    complex128.  Every step ends with the argmax of the lowest 10 qubits, and
+    all paths must agree on it."""
     import torch
 
     res = {}
@@ -323,6 +325,30 @@ def random_circuits(sv, C, stream, peak: float) -> dict:
         sv.sv_destroy(h)
         del buf
         torch.cuda.empty_cache()
+        if nn == RANDOM_PERGATE_C128_N:
+            # the same circuit on the plain per-gate kernel in complex128 (FP64
+            # arithmetic, one HBM sweep per gate): the baseline the complex64
+            # tile paths are compared with; one run after a 64-gate warm-up
+            buf = torch.empty(1 << nn, dtype=torch.complex128, device="cuda")
+            h = sv.sv_create_on(nn, sv.SV_C128, buf.data_ptr(), (1 << nn) * 16, stream.cuda_stream)
+            cfg = sv.make_config(sv.SV_MODE_PERGATE)
+            sv.sv_apply_circuit(h, g[:64], cfg)
+            sv.sv_reset(h)
+            e0.record(stream)
+            sv.sv_apply_circuit(h, g, cfg)
+            idx, p = sv.sv_argmax(h, (1 << 10) - 1)
+            e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1)
+            st = sv.sv_last_stats(h)
+            row["per_gate_c128"] = {"circuit_ms": round(ms, 2), "passes": st["passes"],
+                                    "argmax_low10": int(idx),
+                                    "same_argmax": int(idx) == row["partitioned"]["argmax_low10"]}
+            for k in ("partitioned", "fused_tensor_cores"):
+                row[f"{k}_speedup_over_per_gate_c128"] = round(ms / row[k]["circuit_ms"], 2)
+            sv.sv_destroy(h)
+            del buf
+            torch.cuda.empty_cache()
     return res
 
 
