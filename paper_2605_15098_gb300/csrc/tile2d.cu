@@ -258,16 +258,16 @@ __device__ __forceinline__ void d_factor_bit(RegsD &r, int mask, double2 f) {
 }
 
 // Phased Hadamard on register bit J: b <- M b with M = f T[x_b], then the
-// pair becomes (a + M b, a - M b).
+// pair becomes (a + M b, a - M b).  Without a table (`tab` false) M = f.
 template <int J>
-__device__ __forceinline__ void d_hph(RegsD &r, uint32_t qm, const double2 *T, double2 f) {
+__device__ __forceinline__ void d_hph(RegsD &r, uint32_t qm, const double2 *T, bool tab, double2 f) {
 #pragma unroll
     for (int g8 = 0; g8 < 2; g8++) {
         if (!((qm >> g8) & 1)) continue;
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             const int a = lo_of<J>(8 * g8 + i), b = a | (1 << J);
-            const double2 m = cxd(f, T[b]);
+            const double2 m = tab ? cxd(f, T[b]) : f;
             const double br = r.re[b], bi = r.im[b];
             const double pr = fma(-bi, m.y, br * m.x), pi = fma(br, m.y, bi * m.x);
             const double ar = r.re[a], ai = r.im[a];
@@ -343,6 +343,15 @@ __device__ __forceinline__ void t2d_run(const T2Args &a, double2 *gstate, uint64
             else
                 ph = thread_factor(fd);
         }
+    };
+    // the same from the step itself (tileprog.h: kT2HphDirect)
+    auto hph_direct = [&](const int4 w, const double2 *&T, double2 &ph) {
+        const int trec = (int)((uint32_t)w.w & 0xffffu) - 1, row = (int)((uint32_t)w.w >> 16) - 1;
+        const int sl = (int16_t)(w.y & 0xffff);
+        T = trec >= 0 ? M + 4 * trec : ones;
+        ph = make_double2(1.0, 0.0);
+        if (row >= 0) ph = row < kT2SmemRows ? rows[row * kDThreads + tid] : statc[(size_t)row * kDThreads + tid];
+        if (sl >= 0) ph = cxd(ph, slotc[sl]);
     };
     const int nins = a.nins, last_stage = a.last_stage;
     for (int pc = 0; pc < nins; pc++) {
@@ -427,8 +436,11 @@ __device__ __forceinline__ void t2d_run(const T2Args &a, double2 *gstate, uint64
     case kT2Handler + 8 * 5 + J: {      \
         const double2 *T;               \
         double2 ph;                     \
-        hph_run(w, T, ph);              \
-        d_hph<J>(r, qm, T, ph);         \
+        if ((int8_t)(w.x >> 24) == kT2HphDirect) \
+            hph_direct(w, T, ph);       \
+        else                            \
+            hph_run(w, T, ph);          \
+        d_hph<J>(r, qm, T, T != ones, ph); \
         continue;                       \
     }
             SV_HPH_CASE(0)

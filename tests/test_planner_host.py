@@ -366,3 +366,36 @@ def test_general_gates_split_the_plan(sv, orc, n, seed):
     orc.apply_measured(n, psi, g)
     got = planemu.run_plan(n, plan, use_gen=False)
     assert float(np.max(np.abs(got - psi))) <= 2e-5
+
+
+@pytest.mark.parametrize("n,kind", [(16, "qpe"), (15, "mixed"), (15, "random")])
+def test_phased_butterfly_fields_match_their_run(sv, n, kind):
+    """A phased butterfly step names its run's table record, static row and
+    slot itself (read by the complex64 and complex128 kernels instead of the
+    run's factor records); they must be exactly those of the records the step
+    also keeps (read by the emulator above)."""
+    K_DIRECT, FAC_TABLE = 0x40, 1 << 28
+    g = (C.qpe(n, seed=n)[0] if kind == "qpe" else mixed_circuit(n, 150, 7) if kind == "mixed"
+         else C.random_circuit(n, 4, 5))
+    found = 0
+    for dtype in (sv.SV_C64, sv.SV_C128):
+        plan = sv.sv_plan_export(n, dtype, g, sv.make_config(sv.SV_MODE_PARTITIONED))
+        for p in plan["passes"]:
+            for t2 in [p[k] for k in ("t2", "t2gen") if k in p]:
+                fac = t2["fac2"]
+                for ins in t2["ins"]:
+                    if ins["op"] != planemu.T2_HPH:
+                        continue
+                    found += 1
+                    trec, row, slot = -1, -1, -1
+                    for f in fac[ins["e0"]:ins["e1"]]:
+                        if f["w0"] & FAC_TABLE:
+                            trec = f["row"]
+                        else:
+                            row, slot = f["row"], f["slot"]
+                    assert ins["ccls"] == K_DIRECT
+                    assert (ins["aux"] & 0xffff) - 1 == trec
+                    assert ((ins["aux"] >> 16) & 0xffff) - 1 == row
+                    assert ins["cidx"] == slot
+    if kind == "qpe":
+        assert found > 0
