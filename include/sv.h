@@ -138,12 +138,18 @@ enum {
     SV_FLAG_GREEDY_ONLY = 64,   /* take each pass's local qubits as the greedy
                                    list scheduling picks them, without the
                                    local search that refines the set          */
-    SV_FLAG_L2_BLOCKS = 128     /* two-level blocking (Sec. III-B's block sized
+    SV_FLAG_L2_BLOCKS = 128,    /* two-level blocking (Sec. III-B's block sized
                                    to the last-level cache): consecutive
                                    register-stage passes whose tile qubits
                                    together span at most l2_qubits qubits run
                                    as one launch, block by block, so that the
                                    state moves between them through L2        */
+    SV_FLAG_NARROW_FIRST = 256  /* the first tile pass of the list gathers
+                                   16-amplitude chunks (4 chunk qubits) whatever
+                                   chunk_qubits says, so that more of its tile
+                                   qubits are free to choose; it pays when that
+                                   pass generates a recorded basis state and
+                                   reads nothing (sv_create, sv_reset)        */
 };
 
 /* Planner choice for partitioned modes. */

@@ -107,6 +107,11 @@ extern "C" sv_status sv_autotune(sv_handle h, const sv_gate *host_gates, size_t 
             add(SV_MODE_PARTITIONED, 0, c);
             cands.back().flags = SV_FLAG_EARLY_DIAG;
         }
+        if (h->n > 13)
+            for (int c : {6, 7}) {  // a first pass of 16-amplitude chunks (it generates the state)
+                add(SV_MODE_PARTITIONED, 0, c);
+                cands.back().flags = SV_FLAG_NARROW_FIRST;
+            }
         if ((size_t)state_bytes(h) > (size_t)std::max(h->l2_bytes, 1))
             for (int c : {5, 7}) {  // consecutive passes block by block through L2
                 add(SV_MODE_PARTITIONED, 0, c);
@@ -121,6 +126,11 @@ extern "C" sv_status sv_autotune(sv_handle h, const sv_gate *host_gates, size_t 
         for (int k : {11, 12})
             for (int c : {3, 4, 5}) add(SV_MODE_PARTITIONED, k, c);
         for (int c : {4, 5, 6, 7}) add(SV_MODE_PARTITIONED, 13, c);
+        if (h->n > 13)
+            for (int c : {6, 7}) {
+                add(SV_MODE_PARTITIONED, 13, c);
+                cands.back().flags = SV_FLAG_NARROW_FIRST;
+            }
     }
     cudaEvent_t e0, e1;
     SV_CUDA(cudaEventCreate(&e0));

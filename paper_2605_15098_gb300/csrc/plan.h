@@ -92,6 +92,7 @@ struct PlanOptions {
     bool late_diag = true;  // diagonal gates move to the pass of their first successor
     bool search = true;     // refine each pass's local qubits by local search (the greedy
                             // plan is kept when it has fewer passes)
+    int first_c = 0;        // chunk qubits of the list's first pass (0: c); SV_FLAG_NARROW_FIRST
 };
 
 // Planner options of a configuration (library defaults filled in).

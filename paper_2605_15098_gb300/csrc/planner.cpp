@@ -351,6 +351,7 @@ PlanOptions plan_options(int n, sv_dtype dt, const sv_config &cfg) {
     opt.late_diag = !(cfg.flags & SV_FLAG_EARLY_DIAG);
     opt.search = !(cfg.flags & SV_FLAG_GREEDY_ONLY);
     if (opt.paper) opt.c = opt.k;  // the block is contiguous
+    if ((cfg.flags & SV_FLAG_NARROW_FIRST) && !opt.paper) opt.first_c = 4;
     opt.split_u3 = !dbl;
     return opt;
 }
@@ -474,6 +475,7 @@ static std::string build_plan_once(const std::vector<sv_gate> &gates_in, const P
         return b;
     };
     std::vector<char> done(m, 0);
+    std::vector<int> pass_c;  // chunk qubits of each pass
     std::vector<std::vector<int>> orders;
     std::vector<std::vector<char>> locals;
     std::vector<int> taken, rem;
@@ -484,9 +486,12 @@ static std::string build_plan_once(const std::vector<sv_gate> &gates_in, const P
         if (n <= k) {
             for (int q = 0; q < n; q++) in_l[q] = true;
             cnt = n;
-        } else {
-            for (int q = 0; q < c; q++) in_l[q] = true;
-            cnt = c;
+        }
+        // the first pass may gather narrower chunks (SV_FLAG_NARROW_FIRST)
+        const int cc = (orders.empty() && opt.first_c > 0) ? std::min(opt.first_c, c) : c;
+        if (n > k) {
+            for (int q = 0; q < cc; q++) in_l[q] = true;
+            cnt = cc;
         }
         std::vector<int> order;
         uint64_t blocked = 0;
@@ -581,7 +586,7 @@ static std::string build_plan_once(const std::vector<sv_gate> &gates_in, const P
                             bout = qo;
                         }
                     }
-                    for (int qi = c; qi < n; qi++) {
+                    for (int qi = cc; qi < n; qi++) {
                         if (!S[qi] || qi == qo) continue;
                         S[qi] = false;
                         const int v = run_pass(S, nullptr, nullptr);
@@ -617,6 +622,7 @@ static std::string build_plan_once(const std::vector<sv_gate> &gates_in, const P
                 cnt++;
             }
 
+        pass_c.push_back(cc);
         orders.push_back(std::move(order));
         locals.emplace_back(in_l, in_l + 64);
     }
@@ -654,7 +660,7 @@ static std::string build_plan_once(const std::vector<sv_gate> &gates_in, const P
         bool in_l[64];
         for (int q = 0; q < 64; q++) in_l[q] = locals[p][q] != 0;
         TilePass tp;
-        std::string e = emit_pass(pg, orders[p], in_l, n, k, c, opt, &tp);
+        std::string e = emit_pass(pg, orders[p], in_l, n, k, pass_c[p], opt, &tp);
         if (!e.empty()) return e;
         out->passes.push_back(std::move(tp));
     }
@@ -698,7 +704,9 @@ std::string build_plan(const std::vector<sv_gate> &gates, const PlanOptions &opt
         if (j > i) {
             std::vector<sv_gate> seg(gates.begin() + (long)i, gates.begin() + (long)j);
             Plan sp;
-            const std::string err = build_plan_segment(seg, opt, phys, &sp);
+            PlanOptions os = opt;  // only the list's first pass may be narrow
+            if (!out->passes.empty()) os.first_c = 0;
+            const std::string err = build_plan_segment(seg, os, phys, &sp);
             if (!err.empty()) return err;
             for (TilePass &tp : sp.passes) out->passes.push_back(std::move(tp));
             out->relabels += sp.relabels;

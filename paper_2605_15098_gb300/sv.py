@@ -26,6 +26,7 @@ SV_FLAG_NO_PLAN_CACHE = 16
 SV_FLAG_EARLY_DIAG = 32
 SV_FLAG_GREEDY_ONLY = 64
 SV_FLAG_L2_BLOCKS = 128
+SV_FLAG_NARROW_FIRST = 256
 SV_PLANNER_GREEDY, SV_PLANNER_LEARNED = 0, 1
 
 EXPORTS = (

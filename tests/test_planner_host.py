@@ -399,3 +399,18 @@ def test_phased_butterfly_fields_match_their_run(sv, n, kind):
                     assert ins["cidx"] == slot
     if kind == "qpe":
         assert found > 0
+
+
+@pytest.mark.parametrize("n,kind,chunk", [(16, "qpe", 7), (17, "qpe", 6), (15, "mixed", 7), (16, "random", 6)])
+def test_narrow_first_pass(sv, orc, n, kind, chunk):
+    """SV_FLAG_NARROW_FIRST: the list's first pass gathers 16-amplitude chunks
+    (4 chunk qubits), the others the configured width; the programme matches
+    the oracle whether the first pass generates |0...0> or reads it."""
+    g = (C.qpe(n, seed=n)[0] if kind == "qpe" else mixed_circuit(n, 150, 11) if kind == "mixed"
+         else C.random_circuit(n, 4, 21))
+    cfg = sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=chunk, flags=sv.SV_FLAG_NARROW_FIRST)
+    plan = check(sv, orc, n, g, cfg, sv.SV_C64, 2e-5)
+    cs = [p["c"] for p in plan["passes"] if "c" in p]
+    assert cs[0] == 4 and all(c == chunk for c in cs[1:]), cs
+    # the first pass's tile holds its 4 chunk qubits and k - 4 free ones
+    assert plan["passes"][0]["slot_phys"][:4] == [0, 1, 2, 3]
