@@ -856,7 +856,7 @@ def run_ours(args, world, rank, local):
             "instances": len(work), "n_range": [10, 20], "launch_ms": bms,
             "instances_per_s": len(work) / (bms / 1e3), "passes": binfo["passes"],
             "l2_gbs_algorithmic": binfo["sweep_bytes"] / (bms / 1e3) / 1e9,
-            "host_plan_s": t_create, "chunk_qubits": bcfg.chunk_qubits,
+            "host_plan_s": t_create, "chunk_qubits": bcfg.chunk_qubits, "config": sv.config_dict(bcfg),
             "outcomes_ok": bool(all(int(bidx[i]) == w[3] for i, w in enumerate(work)))}
 
     # ---- learned planner vs greedy: random circuit and QPE, n = 30, complex64 ----
@@ -883,6 +883,36 @@ def run_ours(args, world, rank, local):
                 r["same_argmax"] = bool(outs[0][0][0] == outs[1][0][0])
                 r["marginal10_max_abs_diff"] = float(np.max(np.abs(outs[0][1] - outs[1][1])))
                 r["gain_over_greedy"] = r["greedy_ms"] / min(r["greedy_ms"], r["learned_ms"])
+
+                # the same step timed the same way for every configuration
+                # (reset + apply + argmax, host clock, median of 3 after a
+                # warm-up that also fills the programme cache): what the
+                # network adds over the greedy rules at the chunk width it
+                # chose, and, for QPE, over the autotuner's measured choice
+                def wall_ms(c_w):
+                    sv.sv_reset(hl)
+                    sv.sv_apply_circuit(hl, g_l, c_w)
+                    sv.sv_argmax(hl, 1)
+                    ts = []
+                    for _ in range(3):
+                        t1 = time.perf_counter()
+                        sv.sv_reset(hl)
+                        sv.sv_apply_circuit(hl, g_l, c_w)
+                        sv.sv_argmax(hl, 1)
+                        ts.append(time.perf_counter() - t1)
+                    return statistics.median(ts) * 1e3
+                wall = {"greedy_default": wall_ms(greedy_cfg),
+                        "greedy_at_learned_chunk": wall_ms(sv.make_config(
+                            sv.SV_MODE_PARTITIONED, chunk_qubits=int(r["chunk_qubits"]))),
+                        "learned": wall_ms(learned_cfg)}
+                if name.startswith("QPE"):
+                    tuned_cfg, _ = sv.sv_autotune(hl, g_l)
+                    wall["autotuned"] = wall_ms(tuned_cfg)
+                    r["autotuned_config"] = sv.config_dict(tuned_cfg)
+                r["wall_ms"] = {k: round(v, 3) for k, v in wall.items()}
+                for k in wall:
+                    if k != "learned":
+                        r[f"learned_gain_over_{k}"] = round(wall[k] / wall["learned"], 3)
                 res[name] = r
             sv.sv_destroy(hl)
             sv.sv_cost_model_destroy(model)

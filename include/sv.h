@@ -301,8 +301,9 @@ typedef struct sv_batch_state *sv_batch;
  * items from a queue ordered by decreasing cost, apply all their passes and
  * reduce the FP64 marginal of the read-out qubits to its most probable
  * outcome.  cfg may be NULL; cfg->chunk_qubits (4..11) sets the bulk-copy
- * unit, and SV_FLAG_NO_DIAG_MERGE, SV_FLAG_EARLY_DIAG and SV_FLAG_GREEDY_ONLY
- * act as for sv_apply_circuit (SV_FLAG_PAPER_SWAP is refused with
+ * unit, and SV_FLAG_NO_DIAG_MERGE, SV_FLAG_EARLY_DIAG, SV_FLAG_GREEDY_ONLY and
+ * SV_FLAG_NARROW_FIRST act as for sv_apply_circuit (each item's first pass
+ * generates its starting state) (SV_FLAG_PAPER_SWAP is refused with
  * SV_ERR_UNSUPPORTED).  Errors: SV_ERR_ARG (bad item), SV_ERR_UNSUPPORTED (a pass the
  * register-stage kernel cannot run), SV_ERR_OOM, SV_ERR_CUDA. */
 sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_config *cfg,
@@ -326,9 +327,9 @@ sv_status sv_apply_circuit_batch(const sv_batch_item *items, size_t count, const
 
 /* Measure the batch for every chunk width c in 4..7, each with the
  * automatic and with a forced split of instances of 16 qubits or more
- * (batch_split 0 and 16; one warm-up run and three timed runs each, median),
- * and return the fastest configuration in *best (and its time in *best_ms,
- * may be NULL). */
+ * (batch_split 0 and 16), and for c in 5..7 also with SV_FLAG_NARROW_FIRST
+ * (one warm-up run and three timed runs each, median), and return the
+ * fastest configuration in *best (and its time in *best_ms, may be NULL). */
 sv_status sv_batch_autotune(const sv_batch_item *items, size_t count, sv_config *best,
                             double *best_ms);
 

@@ -204,6 +204,7 @@ sv_status sv_batch_create(const sv_batch_item *items, size_t count, const sv_con
             opt.merge_diag = !(c.flags & SV_FLAG_NO_DIAG_MERGE);
             opt.late_diag = !(c.flags & SV_FLAG_EARLY_DIAG);
             opt.search = !(c.flags & SV_FLAG_GREEDY_ONLY);
+            opt.first_c = (c.flags & SV_FLAG_NARROW_FIRST) ? 4 : 0;  // the first pass generates its state
             opt.relabel = true;
             opt.split_u3 = true;
             for (int fold = 1; fold >= 0; fold--) {
@@ -446,12 +447,17 @@ sv_status sv_batch_autotune(const sv_batch_item *items, size_t count, sv_config 
     if (!best) return fail(SV_ERR_ARG, "best is NULL");
     double bt = 1e300;
     int bc = 0;
-    int bs = 0;
-    for (int k = 0; k < 8; k++) {
-        const int c = 4 + k % 4, split = k < 4 ? 0 : 16;  // chunk width x (automatic, forced) split
+    int bs = 0, bf = 0;
+    // chunk width x (automatic, forced) split, and with chunks wider than 16
+    // amplitudes a first pass of 16-amplitude chunks (SV_FLAG_NARROW_FIRST)
+    for (int k = 0; k < 14; k++) {
+        const int c = k < 8 ? 4 + k % 4 : 5 + (k - 8) % 3;
+        const int split = (k < 8 ? k < 4 : k < 11) ? 0 : 16;
+        const int flags = k < 8 ? 0 : SV_FLAG_NARROW_FIRST;
         sv_config cfg{};
         cfg.chunk_qubits = c;
         cfg.batch_split = split;
+        cfg.flags = flags;
         sv_batch b = nullptr;
         SV_TRY(sv_batch_create(items, count, &cfg, &b));
         double t[4] = {};
@@ -464,11 +470,13 @@ sv_status sv_batch_autotune(const sv_batch_item *items, size_t count, sv_config 
             bt = t[2];
             bc = c;
             bs = split;
+            bf = flags;
         }
     }
     *best = sv_config{};
     best->chunk_qubits = bc;
     best->batch_split = bs;
+    best->flags = bf;
     if (best_ms) *best_ms = bt;
     return SV_OK;
 }

@@ -333,14 +333,18 @@ def test_fused_qpe_full_size(sv, n):
         assert s.argmax((1 << n) - 1)[0] == expected
 
 
-@pytest.mark.parametrize("flags", [0, 32, 64, 96])
+@pytest.mark.parametrize("flags", [0, 32, 64, 96, 256])
 def test_batch_qpe_outcomes(sv, orc, flags):
     """Batched QPE instances (n uniform in 10..20) in one graph-captured launch:
     every outcome equals the oracle's argmax (small n) and the closed form,
-    with each planner option (diagonal placement, local search)."""
+    with each planner option (diagonal placement, local search, a first pass
+    of 16-amplitude chunks at chunk width 7)."""
     work = C.qpe_batch(96, seed=777)
-    b = sv.sv_batch_create([(n, g, m) for n, g, m, _ in work],
-                           sv.make_config(sv.SV_MODE_PARTITIONED, flags=flags) if flags else None)
+    cfg = None
+    if flags:
+        cfg = sv.make_config(sv.SV_MODE_PARTITIONED, flags=flags,
+                             chunk_qubits=7 if flags & sv.SV_FLAG_NARROW_FIRST else 0)
+    b = sv.sv_batch_create([(n, g, m) for n, g, m, _ in work], cfg)
     try:
         idx, p, ms = sv.sv_batch_run(b, len(work))
         idx2, p2, _ = sv.sv_batch_run(b, len(work))  # replay gives the same results
