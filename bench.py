@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--flags", type=int, default=0, help="SV_FLAG_* bits of the headline configuration "
+                    "when it is given (--tile / --chunk / --no-autotune)")
     ap.add_argument("--no-pergate", action="store_true")
     ap.add_argument("--no-c128", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -636,9 +638,9 @@ def run_ours(args, world, rank, local):
     state_bytes = (1 << n) * amp_bytes
     h = sv.sv_create_on(n, dt, buf.data_ptr(), state_bytes, stream.cuda_stream)
     # configuration chosen by the library's autotuner (mode x chunk width x tile width)
-    if args.tile or args.chunk or args.no_autotune:
+    if args.tile or args.chunk or args.flags or args.no_autotune:
         mode = sv.SV_MODE_FUSED if (dt == sv.SV_C64 and not args.no_fused) else sv.SV_MODE_PARTITIONED
-        cfg = sv.make_config(mode, tile_qubits=args.tile, chunk_qubits=args.chunk)
+        cfg = sv.make_config(mode, tile_qubits=args.tile, chunk_qubits=args.chunk, flags=args.flags)
         tuned = None
     else:
         cfg, tuned_ms = sv.sv_autotune(h, gates)
