@@ -204,8 +204,9 @@ __device__ __forceinline__ void apply_table_s(RegsN<NP> &r, const float4 *T, uin
 // Phased Hadamard on register bit J: the amplitude b of each pair (bit J = 1)
 // is multiplied by T[x] (a 32-entry phase table in shared memory laid out as
 // for apply_table_s), then by the per-thread factor (fr + i fi), and the pair
-// becomes (a + p, a - p) with p that product.  Butterflies are grouped four at
-// a time as in reg_h2.  Without a table (`tab` false: the run's phase is the
+// becomes (a + p, a - p) with p that product.  Butterflies without a table are
+// grouped four at a time as in reg_h2, those with one all eight together.
+// Without a table (`tab` false: the run's phase is the
 // per-thread factor alone, as for the first Hadamard of a stage in an inverse
 // QFT) the table product is skipped.
 template <int J, int NP>
@@ -232,11 +233,11 @@ __device__ __forceinline__ void reg_hph_s(RegsN<NP> &r, uint32_t qm, const float
             return;
         }
 #pragma unroll
-        for (int g = 0; g < NP / 8; g++) {
+        for (int g = 0; g < NP / 16; g++) {  // all eight butterflies in one group (measured faster)
             if (!((qm >> g) & 1)) continue;
 #pragma unroll
-            for (int i = 0; i < 4; i++) {
-                const int q = bfly_q<J>(4 * g + i), q1 = q | (1 << (J - 1));
+            for (int i = 0; i < 8; i++) {
+                const int q = bfly_q<J>(8 * g + i), q1 = q | (1 << (J - 1));
                 const float4 t = T[q1];
                 const float2 tr = make_float2(t.x, t.y), ti = make_float2(t.z, t.w);
                 const float2 nti = make_float2(-t.z, -t.w);
