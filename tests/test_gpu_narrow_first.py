@@ -81,3 +81,22 @@ def test_reading_first_pass(sv, orc):
         idx, p = s.argmax(info["mask"])
     assert idx == info["y"]
     assert np.max(np.abs(got - ref)) <= ERR64
+
+
+def test_with_l2_blocks_identical_to_one_level(sv, orc):
+    """A narrow first pass inside an L2 block group: the group kernel computes
+    the tiles' slot values itself, the one-level kernel receives them from
+    k_slotv; the same sums and products, so the amplitudes are bit-identical."""
+    n = 22
+    g, expected, info = C.qpe(n, seed=5)
+    ref = orc.run(n, g)
+    outs = []
+    for flags, l2 in ((sv.SV_FLAG_NARROW_FIRST, 0), (sv.SV_FLAG_NARROW_FIRST | sv.SV_FLAG_L2_BLOCKS, 18)):
+        cfg = sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=7, flags=flags, l2_qubits=l2, l2_chunk=2)
+        with sv.State(n, sv.SV_C64) as s:
+            s.apply(g, cfg)
+            outs.append(s.amplitudes())
+            idx, p = s.argmax(info["mask"])
+        assert idx == info["y"]
+        assert np.max(np.abs(outs[-1] - ref)) <= ERR64
+    assert np.array_equal(outs[0], outs[1])
