@@ -337,7 +337,9 @@ sv_status sv_batch_autotune(const sv_batch_item *items, size_t count, sv_config 
 
 /* Run the circuit under each candidate configuration (execution mode:
  * per-gate for small n, register-stage tiles, tensor-core fused tiles; chunk
- * width c; for complex128 the tile width k), one warm-up and three timed runs
+ * width c; for complex128 the tile width k; diagonal placement
+ * (SV_FLAG_EARLY_DIAG), a narrow first pass (SV_FLAG_NARROW_FIRST), L2 block
+ * groups (SV_FLAG_L2_BLOCKS) when the state exceeds L2), one warm-up and three timed runs
  * each from |0...0> (the paper keeps the fastest block size, median of three
  * runs, Sec. IV-B), and return the fastest in *best and its median device
  * time in *best_ms (may be NULL).  The handle's state is overwritten and left
