@@ -553,7 +553,8 @@ typedef struct sv_plan_choice {
     int32_t rule_kernels;        /* 1: sv_planner_judge measured the chosen
                                     options faster with the greedy rule's
                                     kernel per pass and kept those            */
-    int32_t reserved0;
+    int32_t narrow_first;        /* 1: the chosen plan's first pass gathers
+                                    16-amplitude chunks (SV_FLAG_NARROW_FIRST) */
     double rule_ms;              /* measured by sv_planner_judge: the chosen
                                     options with the rule's kernels (0 if the
                                     model chose the same kernels)             */

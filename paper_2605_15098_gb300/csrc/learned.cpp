@@ -34,6 +34,7 @@ uint64_t plan_key(const sv_state *h, const std::vector<sv_gate> &g, const sv_con
     };
     mix((uint64_t)h->n);
     mix((uint64_t)h->dt);
+    mix((uint64_t)(h->basis >= 0));  // a recorded basis state: the first pass generates it
     for (int q = 0; q < h->n; q++) mix((uint64_t)h->phys[q]);
     mix((uint64_t)(uint32_t)cfg.mode | ((uint64_t)(uint32_t)cfg.flags << 32));
     mix((uint64_t)(uint32_t)cfg.tile_qubits | ((uint64_t)(uint32_t)cfg.chunk_qubits << 32));
@@ -88,14 +89,17 @@ sv_status learned_entry(sv_state *h, const std::vector<sv_gate> &gates, const sv
 
     // candidate planner options; the configuration's own options come first
     std::vector<PlanOptions> opts{base};
-    auto add1 = [&](int k, int c, bool paper, bool late) {
+    auto add1 = [&](int k, int c, bool paper, bool late, int first_c = 0) {
         PlanOptions o = base;
         o.k = k;
         o.c = paper ? k : c;
         o.paper = paper;
         o.late_diag = late;
+        o.first_c = paper ? 0 : first_c;
         for (const PlanOptions &e : opts)
-            if (e.k == o.k && e.c == o.c && e.paper == o.paper && e.late_diag == o.late_diag) return;
+            if (e.k == o.k && e.c == o.c && e.paper == o.paper && e.late_diag == o.late_diag &&
+                e.first_c == o.first_c)
+                return;
         opts.push_back(o);
     };
     // every (k, c) with diagonal gates in their successors' passes and in
@@ -106,6 +110,7 @@ sv_status learned_entry(sv_state *h, const std::vector<sv_gate> &gates, const sv
     };
     if (!dbl) {
         for (int c : {4, 5, 6, 7}) add(13, c, false);
+        for (int c : {6, 7}) add1(13, c, false, true, 4);  // a narrow first pass
         for (int c : {4, 5, 7}) add(14, c, false);
         add(13, 13, true);
     } else {
@@ -123,8 +128,14 @@ sv_status learned_entry(sv_state *h, const std::vector<sv_gate> &gates, const sv
         std::copy(h->phys, h->phys + 64, phys);
         Plan plan;
         if (!build_plan(gates, o, phys, &plan).empty()) continue;
+        // from a recorded basis state the first pass, on the register-stage
+        // kernel, generates its tiles: it is described by the programme it
+        // then runs and the bytes it writes (as the recorded launches are)
+        bool gen_next = h->basis >= 0;
         for (const TilePass &p : plan.passes) {
+            if (!p.general.empty()) gen_next = false;
             if (!p.remap_before.empty()) {
+                gen_next = false;
                 cd.remap_recs.push_back((int)recs.size());
                 recs.push_back(describe_remap(h->n, h->dt, p.remap_before));
                 cd.remaps++;
@@ -135,10 +146,13 @@ sv_status learned_entry(sv_state *h, const std::vector<sv_gate> &gates, const sv
                 po.push_back({PK_GENERIC, (int)recs.size()});
                 recs.push_back(describe_pass(h->n, h->dt, p, nullptr, PK_GENERIC));
                 if (allow_t2) {
-                    T2Pass a;
+                    T2Pass a, g;
                     if (compile_t2(p, &a, false).empty()) {
+                        const bool gen = gen_next && a.format == 2 && compile_t2v2(p, &g, true).empty();
+                        sv_launch_record rec = describe_pass(h->n, h->dt, p, gen ? &g : &a, PK_T2);
+                        if (gen) rec.bytes *= 0.5;  // written only
                         po.push_back({PK_T2, (int)recs.size()});
-                        recs.push_back(describe_pass(h->n, h->dt, p, &a, PK_T2));
+                        recs.push_back(rec);
                     }
                     T2Pass b;
                     if (compile_t2(p, &b, true).empty()) {
@@ -148,6 +162,7 @@ sv_status learned_entry(sv_state *h, const std::vector<sv_gate> &gates, const sv
                 }
             }
             cd.pass_opts.push_back(std::move(po));
+            if (!p.ops.empty()) gen_next = false;
         }
         cands.push_back(std::move(cd));
     }
@@ -198,6 +213,7 @@ sv_status learned_entry(sv_state *h, const std::vector<sv_gate> &gates, const sv
             L.info.chunk_qubits = cd.opt.c;
             L.info.paper_swap = cd.opt.paper ? 1 : 0;
             L.info.early_diag = cd.opt.late_diag ? 0 : 1;
+            L.info.narrow_first = cd.opt.first_c > 0 ? 1 : 0;
             L.info.passes = cd.passes;
             L.info.remaps = cd.remaps;
             L.info.fused_passes = nfused;

@@ -104,7 +104,7 @@ class sv_plan_choice(ctypes.Structure):
                 ("predicted_ms", ctypes.c_double), ("greedy_predicted_ms", ctypes.c_double),
                 ("learned_ms", ctypes.c_double), ("greedy_ms", ctypes.c_double),
                 ("verdict", ctypes.c_int32), ("early_diag", ctypes.c_int32),
-                ("rule_kernels", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("rule_kernels", ctypes.c_int32), ("narrow_first", ctypes.c_int32),
                 ("rule_ms", ctypes.c_double), ("reserved", ctypes.c_int32 * 2)]
 
     def as_dict(self) -> dict:
