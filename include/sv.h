@@ -452,7 +452,8 @@ typedef struct sv_launch_record {
     int32_t blocks;    /* fused: 32x32 tensor-core blocks                      */
     int32_t nins;      /* register-stage / fused: programme instructions       */
     int32_t nfactors;  /* register-stage / fused: diagonal factor applications */
-    int32_t reserved;
+    int32_t generated; /* 1: a register-stage pass that generated a recorded
+                          basis state (written only: bytes count the write)  */
 } sv_launch_record;
 
 /* Start (enable=1) or stop (0) recording launch records on this handle.
@@ -498,9 +499,9 @@ typedef struct sv_train_config {
 
 /* Feature vector of one launch record (SV_COST_FEATURES floats): physical
  * qubit mask bits 0..31, stride class of the highest qubit (<5, 5-9,
- * 10..k-1, >=k), dtype, kernel family, and scaled logs of gates,
- * instructions, stages, blocks and factors, plus c, n, k and k - c.
- * Host only. */
+ * 10..k-1, >=k), a pass that generates its state, complex128, kernel
+ * family, and scaled logs of gates, instructions, stages, blocks and
+ * factors, plus c, n, k and k - c.  Host only. */
 sv_status sv_cost_features(const sv_launch_record *rec, float *host_out);
 
 /* Create a model on the current device with He-uniform weights drawn from

@@ -384,7 +384,8 @@ void cost_features(const sv_launch_record &r, float *f) {
         }
     const int k = r.k > 0 ? r.k : 13;
     f[32 + (top < 5 ? 0 : top < 10 ? 1 : top < k ? 2 : 3)] = 1.f;
-    f[36 + (r.dtype == SV_C128 ? 1 : 0)] = 1.f;
+    f[36] = r.generated ? 1.f : 0.f;  // generated its state: no reads
+    f[37] = r.dtype == SV_C128 ? 1.f : 0.f;
     int fam = 0;  // per-gate
     if (r.kind == SV_KERNEL_REMAP) fam = 4;
     else if (r.kind == SV_KERNEL_FUSED || r.gate_kind == -3) fam = 3;

@@ -150,7 +150,10 @@ sv_status learned_entry(sv_state *h, const std::vector<sv_gate> &gates, const sv
                     if (compile_t2(p, &a, false).empty()) {
                         const bool gen = gen_next && a.format == 2 && compile_t2v2(p, &g, true).empty();
                         sv_launch_record rec = describe_pass(h->n, h->dt, p, gen ? &g : &a, PK_T2);
-                        if (gen) rec.bytes *= 0.5;  // written only
+                        if (gen) {  // written only
+                            rec.bytes *= 0.5;
+                            rec.generated = 1;
+                        }
                         po.push_back({PK_T2, (int)recs.size()});
                         recs.push_back(rec);
                     }

@@ -772,6 +772,7 @@ sv_status partitioned_apply(sv_state *h, const std::vector<sv_gate> &gates, cons
             if (up[i].t2 && !up[i].t3 && up[i].has_gen) {
                 gen = h->basis;
                 meta.bytes = (double)state_bytes(h);  // written, not read
+                meta.generated = 1;
             } else {
                 SV_TRY(materialize(h));
             }

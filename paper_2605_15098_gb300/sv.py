@@ -85,7 +85,7 @@ class sv_launch_record(ctypes.Structure):
                 ("bytes", ctypes.c_double), ("ms", ctypes.c_double), ("feat", ctypes.c_uint64),
                 ("c", ctypes.c_int32), ("stages", ctypes.c_int32), ("blocks", ctypes.c_int32),
                 ("nins", ctypes.c_int32), ("nfactors", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("generated", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

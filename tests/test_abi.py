@@ -103,7 +103,7 @@ def test_cost_features_host(svlib):
     assert f.shape == (svlib.SV_COST_FEATURES,)
     assert list(f[:32]) == [float((rec["feat"] >> q) & 1) for q in range(32)]
     assert list(f[32:36]) == [0, 0, 0, 1]        # top qubit 27 >= k
-    assert list(f[36:38]) == [1, 0]              # complex64
+    assert list(f[36:38]) == [0, 0]              # reads its tile; complex64
     assert list(f[38:43]) == [0, 0, 1, 0, 0]     # register-stage kernel
     assert abs(f[43] - np.log2(16) / 8) < 1e-6
     assert abs(f[47] - 5 / 16) < 1e-7 and abs(f[49] - 13 / 16) < 1e-7 and abs(f[51] - 8 / 16) < 1e-7
@@ -113,5 +113,8 @@ def test_cost_features_host(svlib):
     rec.update(kind=svlib.SV_KERNEL_FUSED, gate_kind=-3, feat=0b111, dtype=1)
     f = svlib.sv_cost_features(rec)
     assert list(f[38:43]) == [0, 0, 0, 1, 0] and list(f[32:36]) == [1, 0, 0, 0]
-    assert list(f[36:38]) == [0, 1]
+    assert list(f[36:38]) == [0, 1]              # complex128
+    rec.update(kind=svlib.SV_KERNEL_TILE, gate_kind=-2, dtype=0, generated=1)
+    f = svlib.sv_cost_features(rec)
+    assert list(f[36:38]) == [1, 0]              # generates its state
     assert svlib.cost_target({"ms": 2.0, "bytes": 4.0e9}) == pytest.approx(np.log(0.5))
