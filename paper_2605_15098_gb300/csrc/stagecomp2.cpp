@@ -603,8 +603,8 @@ std::string compile_fmt2(const TilePass &tp, T2Pass *out, bool gen) {
                     f.e1 = d.e1;
                     f.hd = (int16_t)(kT2Handler + 8 * 5 + hh.idx);
                     // the run's table, static row and slot, also in the step
-                    // itself (tileprog.h: T2_HPH), so that the complex64 kernel
-                    // reads them without the factor records
+                    // itself (tileprog.h: T2_HPH), so that the register-stage
+                    // kernels read them without the factor records
                     int trec = -1, row = -1, sl = -1;
                     for (int e = d.e0; e < d.e1; e++) {
                         const T2Fac &fc = out->fac2[e];

@@ -350,8 +350,6 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, uint64_t
     // prove unchanged by the tile's shared-memory stores (the L2 block kernel
     // indexes its passes' arguments)
     const int nins = a.nins, last_stage = a.last_stage;
-    // the next step's record is read while this one runs (the dispatch
-    // depends on it); the read past the last step stays inside shared memory
     for (int pc = 0; pc < nins; pc++) {
         const int4 w = ins[pc];
         // all ones at run time (the handler code is below 256), opaque to the
