@@ -108,7 +108,7 @@ extern "C" sv_status sv_autotune(sv_handle h, const sv_gate *host_gates, size_t 
             cands.back().flags = SV_FLAG_EARLY_DIAG;
         }
         if (h->n > 13)
-            for (int c : {6, 7}) {  // a first pass of 16-amplitude chunks (it generates the state)
+            for (int c : {6, 7, 8, 9}) {  // a first pass of 16-amplitude chunks (it generates the state)
                 add(SV_MODE_PARTITIONED, 0, c);
                 cands.back().flags = SV_FLAG_NARROW_FIRST;
             }
