@@ -81,7 +81,7 @@ CONFIGS += [("paper", sv.make_config(sv.SV_MODE_PARTITIONED, flags=sv.SV_FLAG_PA
             ("generic", sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=5,
                                        flags=sv.SV_FLAG_GENERIC_TILE))]
 CONFIGS += [("t2c%dnarrow" % c, sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=c,
-                                               flags=sv.SV_FLAG_NARROW_FIRST)) for c in (6, 7)]
+                                               flags=sv.SV_FLAG_NARROW_FIRST)) for c in (6, 7, 8, 9)]
 # complex128 runs on the generic tile kernel; sampled on smaller states
 CONFIGS128 = [("c128k%dc%d" % (k, c), sv.make_config(sv.SV_MODE_PARTITIONED, tile_qubits=k,
                                                      chunk_qubits=c))

@@ -110,7 +110,7 @@ sv_status learned_entry(sv_state *h, const std::vector<sv_gate> &gates, const sv
     };
     if (!dbl) {
         for (int c : {4, 5, 6, 7}) add(13, c, false);
-        for (int c : {6, 7}) add1(13, c, false, true, 4);  // a narrow first pass
+        for (int c : {6, 7, 8, 9}) add1(13, c, false, true, 4);  // a narrow first pass
         for (int c : {4, 5, 7}) add(14, c, false);
         add(13, 13, true);
     } else {
