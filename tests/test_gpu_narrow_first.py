@@ -30,7 +30,7 @@ def fidelity(a, b):
     return abs(np.vdot(a.astype(np.complex128), b.astype(np.complex128))) ** 2
 
 
-@pytest.mark.parametrize("n,chunk", [(20, 7), (22, 6), (24, 7), (26, 7)])
+@pytest.mark.parametrize("n,chunk", [(20, 7), (22, 6), (22, 8), (24, 7), (26, 7), (26, 9)])
 def test_qpe_c64(sv, orc, n, chunk):
     g, expected, info = C.qpe(n, seed=n)
     ref = orc.run(n, g)
@@ -50,7 +50,7 @@ def test_qpe_c64(sv, orc, n, chunk):
 def test_mixed_c64_and_c128(sv, orc, n, seed):
     g = mixed_circuit(n, 200, 31 * n + seed)
     ref = orc.run(n, g)
-    for dtype, chunk in ((sv.SV_C64, 7), (sv.SV_C128, 6)):
+    for dtype, chunk in ((sv.SV_C64, 7), (sv.SV_C64, 9), (sv.SV_C128, 6)):
         cfg = sv.make_config(sv.SV_MODE_PARTITIONED, tile_qubits=13, chunk_qubits=chunk,
                              flags=sv.SV_FLAG_NARROW_FIRST)
         with sv.State(n, dtype) as s:

@@ -101,13 +101,15 @@ def test_qpe_sweep_c128_parity(sv, orc, n):
         assert np.max(np.abs(got - ref)) <= TOL128
 
 
-@pytest.mark.parametrize("n,dtype", [(28, 0), (28, 1), (30, 0)])
-def test_qpe_full_size_closed_form(sv, n, dtype):
-    """Full-size QPE in the benchmark's launch configuration: the counting
-    register reads y = sum(a_i) mod 2^t with probability 1 (Eq. 2-3)."""
+@pytest.mark.parametrize("n,dtype,chunk,flags", [(28, 0, 0, 0), (28, 1, 0, 0), (30, 0, 0, 0),
+                                                   (28, 0, 9, 256), (30, 0, 9, 256)])
+def test_qpe_full_size_closed_form(sv, n, dtype, chunk, flags):
+    """Full-size QPE in the library's default configuration and in the one the
+    autotuner picks for complex64 QPE-28/30 (chunk 9, narrow first pass): the
+    counting register reads y = sum(a_i) mod 2^t with probability 1 (Eq. 2-3)."""
     g, expected, info = C.qpe(n)
     with sv.State(n, dtype) as s:
-        s.apply(g, sv.make_config(sv.SV_MODE_PARTITIONED))
+        s.apply(g, sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=chunk, flags=flags))
         idx, p = s.argmax(info["mask"])
         assert idx == info["y"]
         assert abs(p - 1.0) <= (1e-12 if dtype == sv.SV_C128 else 1e-5)
