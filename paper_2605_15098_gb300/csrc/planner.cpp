@@ -16,9 +16,7 @@
 // gate whose non-diagonal qubits fit in the tile's k slots.
 #include <algorithm>
 #include <cmath>
-#include <map>
 #include <string>
-#include <tuple>
 
 #include "common.h"
 #include "plan.h"
@@ -32,7 +30,6 @@ struct PGate {
     int dq[2], ndq;  // qubits acted on diagonally
     bool diag;
     bool counted;    // a circuit gate (false: a phase split off a U3)
-    std::vector<int> deps;
 };
 
 void classify(PGate &p) {
@@ -174,6 +171,11 @@ std::string emit_pass(const std::vector<PGate> &pg, const std::vector<int> &orde
         if (j < N) segs.push_back({false, {nd_gates[j]}});
     }
 
+    struct Acc {
+        int kind, a, b;
+        uint64_t th;
+    };
+    std::vector<Acc> acc;
     for (const Seg &sg : segs) {
         TileOp op{};
         if (!sg.diag) {
@@ -208,8 +210,10 @@ std::string emit_pass(const std::vector<PGate> &pg, const std::vector<int> &orde
             tp.ops.push_back(op);
             continue;
         }
-        // merged diagonal run -> phase polynomial over local / global bits
-        std::map<std::tuple<int, int, int>, uint64_t> acc;
+        // merged diagonal run -> phase polynomial over local / global bits:
+        // one term per (kind, a, b), in that order, its phases summed (exact
+        // 64-bit fractions of a turn, so the order of the sum is immaterial)
+        acc.clear();
         for (int gi : sg.g) {
             const sv_gate &g = pg[gi].g;
             bool exact;
@@ -217,32 +221,36 @@ std::string emit_pass(const std::vector<PGate> &pg, const std::vector<int> &orde
             if (!is_controlled_kind(g.kind)) {
                 int q = g.target;
                 if (slot_of[q] >= 0)
-                    acc[{TERM_L, slot_of[q], 0}] += th;
+                    acc.push_back({TERM_L, slot_of[q], 0, th});
                 else
-                    acc[{TERM_G, q, 0}] += th;
+                    acc.push_back({TERM_G, q, 0, th});
             } else {
                 int q1 = g.control, q2 = g.target;
                 int s1 = slot_of[q1], s2 = slot_of[q2];
                 if (s1 >= 0 && s2 >= 0)
-                    acc[{TERM_LL, std::min(s1, s2), std::max(s1, s2)}] += th;
+                    acc.push_back({TERM_LL, std::min(s1, s2), std::max(s1, s2), th});
                 else if (s1 >= 0)
-                    acc[{TERM_LG, s1, q2}] += th;
+                    acc.push_back({TERM_LG, s1, q2, th});
                 else if (s2 >= 0)
-                    acc[{TERM_LG, s2, q1}] += th;
+                    acc.push_back({TERM_LG, s2, q1, th});
                 else
-                    acc[{TERM_GG, std::min(q1, q2), std::max(q1, q2)}] += th;
+                    acc.push_back({TERM_GG, std::min(q1, q2), std::max(q1, q2), th});
             }
         }
+        std::sort(acc.begin(), acc.end(), [](const Acc &x, const Acc &y) {
+            return x.kind != y.kind ? x.kind < y.kind : x.a != y.a ? x.a < y.a : x.b < y.b;
+        });
         op.type = TOP_DIAG;
         op.tb = (int)tp.terms.size();
-        for (auto &kv : acc) {
-            if (kv.second == 0) continue;
+        for (size_t i = 0; i < acc.size();) {
             PhaseTerm t{};
-            t.kind = std::get<0>(kv.first);
-            t.a = std::get<1>(kv.first);
-            t.b = std::get<2>(kv.first);
-            t.theta = kv.second;
-            tp.terms.push_back(t);
+            t.kind = acc[i].kind;
+            t.a = acc[i].a;
+            t.b = acc[i].b;
+            t.theta = 0;
+            for (; i < acc.size() && acc[i].kind == t.kind && acc[i].a == t.a && acc[i].b == t.b; i++)
+                t.theta += acc[i].th;
+            if (t.theta != 0) tp.terms.push_back(t);
         }
         op.te = (int)tp.terms.size();
         if (op.te > op.tb) tp.ops.push_back(op);
@@ -444,19 +452,23 @@ static std::string build_plan_once(const std::vector<sv_gate> &gates_in, const P
     }
     const int m = (int)pg.size();
 
-    // 2. dependencies
+    // 2. dependencies, gate i's in dep_idx[dep_off[i] .. dep_off[i + 1])
     std::vector<int> last_nd(64, -1);
     std::vector<std::vector<int>> diag_since(64);
+    for (int q = 0; q < n; q++) diag_since[q].reserve(16);
+    std::vector<int> dep_off(m + 1, 0), dep_idx;
+    dep_idx.reserve(4 * (size_t)m);
     for (int i = 0; i < m; i++) {
         PGate &p = pg[i];
+        dep_off[i] = (int)dep_idx.size();
         for (int a = 0; a < p.nnd; a++) {
             int q = p.nd[a];
-            if (last_nd[q] >= 0) p.deps.push_back(last_nd[q]);
-            for (int d : diag_since[q]) p.deps.push_back(d);
+            if (last_nd[q] >= 0) dep_idx.push_back(last_nd[q]);
+            for (int d : diag_since[q]) dep_idx.push_back(d);
         }
         for (int a = 0; a < p.ndq; a++) {
             int q = p.dq[a];
-            if (last_nd[q] >= 0) p.deps.push_back(last_nd[q]);
+            if (last_nd[q] >= 0) dep_idx.push_back(last_nd[q]);
         }
         for (int a = 0; a < p.nnd; a++) {
             last_nd[p.nd[a]] = i;
@@ -464,6 +476,7 @@ static std::string build_plan_once(const std::vector<sv_gate> &gates_in, const P
         }
         for (int a = 0; a < p.ndq; a++) diag_since[p.dq[a]].push_back(i);
     }
+    dep_off[m] = (int)dep_idx.size();
 
     // 3. passes by list scheduling.  A gate left out of a pass blocks its
     // non-diagonal qubits: every later gate on one of them depends on it.
@@ -475,10 +488,17 @@ static std::string build_plan_once(const std::vector<sv_gate> &gates_in, const P
         return b;
     };
     std::vector<char> done(m, 0);
+    auto deps_done = [&](int i) {
+        for (int e = dep_off[i]; e < dep_off[i + 1]; e++)
+            if (!done[dep_idx[e]]) return false;
+        return true;
+    };
     std::vector<int> pass_c;  // chunk qubits of each pass
     std::vector<std::vector<int>> orders;
     std::vector<std::vector<char>> locals;
     std::vector<int> taken, rem;
+    taken.reserve((size_t)m);
+    rem.reserve((size_t)m);
     int remaining = m;
     while (remaining > 0) {
         bool in_l[64] = {};
@@ -494,17 +514,12 @@ static std::string build_plan_once(const std::vector<sv_gate> &gates_in, const P
             cnt = cc;
         }
         std::vector<int> order;
+        order.reserve((size_t)remaining);
         uint64_t blocked = 0;
         for (int i = 0; i < m && blocked != all_q; i++) {
             if (done[i]) continue;
             const PGate &p = pg[i];
-            bool ready = true;
-            for (int d : p.deps)
-                if (!done[d]) {
-                    ready = false;
-                    break;
-                }
-            if (!ready) {
+            if (!deps_done(i)) {
                 blocked |= nd_mask(p);
                 continue;
             }
@@ -542,12 +557,7 @@ static std::string build_plan_once(const std::vector<sv_gate> &gates_in, const P
                 for (size_t r = 0; r < rem.size() && blk != all_q; r++) {
                     const int i = rem[r];
                     const PGate &p = pg[i];
-                    bool ok = true;
-                    for (int d : p.deps)
-                        if (!done[d]) {
-                            ok = false;
-                            break;
-                        }
+                    bool ok = deps_done(i);
                     if (!ok) {
                         blk |= nd_mask(p);
                         continue;
@@ -573,6 +583,7 @@ static std::string build_plan_once(const std::vector<sv_gate> &gates_in, const P
             bool S[64];
             for (int q = 0; q < 64; q++) S[q] = in_l[q];
             std::vector<int> want;
+            want.reserve(kSearchWant);
             int best = run_pass(S, nullptr, &want);
             for (int it = 0; it < kSearchSteps && !want.empty(); it++) {
                 int bv = best, bin = -1, bout = -1;
@@ -638,12 +649,15 @@ static std::string build_plan_once(const std::vector<sv_gate> &gates_in, const P
         for (int i : orders[p]) pass_of[i] = (int)p;
     std::vector<int> first_succ(m, -1);
     for (int j = 0; j < m; j++)
-        for (int d : pg[j].deps)
+        for (int e = dep_off[j]; e < dep_off[j + 1]; e++) {
+            const int d = dep_idx[e];
             if (first_succ[d] < 0 || pass_of[j] < first_succ[d]) first_succ[d] = pass_of[j];
+        }
     if (opt.merge_diag && opt.late_diag) {
         std::vector<std::vector<int>> moved(orders.size());
         for (size_t p = 0; p < orders.size(); p++) {
             std::vector<int> keep;
+            keep.reserve(orders[p].size());
             for (int i : orders[p]) {
                 if (pg[i].diag && first_succ[i] > (int)p)
                     moved[first_succ[i]].push_back(i);

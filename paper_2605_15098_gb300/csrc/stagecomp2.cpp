@@ -137,10 +137,27 @@ void pick_regs(const TilePass &tp, size_t from, bool no123, int out[4]) {
 
 uint32_t turns32(uint64_t t64) { return (uint32_t)((t64 + (UINT64_C(1) << 31)) >> 32); }
 
+// cos and sin of 2 pi u / 2^32, evaluated in FP64 and rounded to FP32.  A
+// pass's static rows repeat the same phases across threads and rows, so a
+// small direct-mapped memo per host thread hands back values it has already
+// evaluated; a value is the same whichever way it is obtained.
 void expi(uint32_t u, float *re, float *im) {
-    const double ang = 2.0 * M_PI * ((double)(int32_t)u * 0x1p-32);
-    *re = (float)std::cos(ang);
-    *im = (float)std::sin(ang);
+    struct Memo {
+        uint32_t u;
+        bool ok;
+        float re, im;
+    };
+    static thread_local Memo memo[4096];
+    Memo &e = memo[(u * 2654435761u) >> 20];
+    if (!e.ok || e.u != u) {
+        const double ang = 2.0 * M_PI * ((double)(int32_t)u * 0x1p-32);
+        e.u = u;
+        e.ok = true;
+        e.re = (float)std::cos(ang);
+        e.im = (float)std::sin(ang);
+    }
+    *re = e.re;
+    *im = e.im;
 }
 
 // Precision policies of the compiler.  P32 (complex64 kernels): phases as
