@@ -414,3 +414,22 @@ def test_narrow_first_pass(sv, orc, n, kind, chunk):
     assert cs[0] == 4 and all(c == chunk for c in cs[1:]), cs
     # the first pass's tile holds its 4 chunk qubits and k - 4 free ones
     assert plan["passes"][0]["slot_phys"][:4] == [0, 1, 2, 3]
+
+
+def test_programme_independent_of_earlier_compilations(sv):
+    """The compiler keeps a per-thread memo of FP32 phase exponentials.  A
+    programme must not depend on what was compiled before it: the same
+    circuit exported before and after others (continuous rotation angles
+    and dyadic QPE phases, both dtypes) gives the same bytes."""
+    import json
+
+    n = 16
+    a = C.qpe(n, seed=4)[0]
+    others = [C.random_circuit(n, 12, seed=s) for s in (1, 2, 3)] + [C.qpe(n, seed=9)[0]]
+    cfg = sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=5)
+    first = json.dumps(sv.sv_plan_export(n, sv.SV_C64, a, cfg), sort_keys=True)
+    for g in others:
+        sv.sv_plan_export(n, sv.SV_C64, g, cfg)
+        sv.sv_plan_export(n, sv.SV_C128, g, cfg)
+    again = json.dumps(sv.sv_plan_export(n, sv.SV_C64, a, cfg), sort_keys=True)
+    assert first == again
