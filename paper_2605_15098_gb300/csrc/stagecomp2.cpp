@@ -208,6 +208,20 @@ struct P32 {
         const int off = 4 * ((x >> 1) & 1) + (x & 1);
         return tf[off] == 1.f && tf[off + 2] == 0.f;
     }
+    // the packed entries q1 of a phased butterfly on register bit j (q1 over
+    // register bits 1..4, bit j - 1 of q1 set) depend only on register bits
+    // below j: every entry equals the one with the same low j - 1 bits
+    static constexpr bool kSharedTwiddles = true;
+    static bool table_low_only(const T2Pass *o, int m0, int j) {
+        auto entry = [&](int q) { return o->mats[m0 + (q >> 1)].m + 4 * (q & 1); };
+        const int hb = 1 << (j - 1);
+        for (int q1 = 0; q1 < 16; q1++) {
+            if (!(q1 & hb)) continue;
+            const float *a = entry(q1), *b = entry((q1 & (hb - 1)) | hb);
+            if (std::memcmp(a, b, 4 * sizeof(float)) != 0) return false;
+        }
+        return true;
+    }
     // s as an unevaluated FP32 sum hi + lo
     static int32_t push_scale(T2Pass *o, double s) {
         const float hi = (float)s;
@@ -231,6 +245,8 @@ struct P64 {
         *im = std::sin(ang);
     }
     static bool real(const double *m) { return m[1] == 0.0 && m[3] == 0.0 && m[5] == 0.0 && m[7] == 0.0; }
+    static constexpr bool kSharedTwiddles = false;  // the complex128 kernel keeps one form
+    static bool table_low_only(const T2Pass *, int, int) { return false; }
     static int32_t push_mat(T2Pass *o, const double *m) {
         o->mats64.insert(o->mats64.end(), m, m + 8);
         return (int32_t)(o->mats64.size() / 8) - 1;
@@ -633,6 +649,9 @@ std::string compile_fmt2(const TilePass &tp, T2Pass *out, bool gen) {
                         }
                     }
                     f.ccls = kT2HphDirect;
+                    if (P::kSharedTwiddles && trec >= 0 && hh.idx >= 1 && hh.idx <= 3 &&
+                        P::table_low_only(out, trec, hh.idx))
+                        f.ccls = kT2HphShared;
                     f.cidx = (int16_t)sl;
                     f.aux = (int32_t)(((uint32_t)(row + 1) << 16) | (uint32_t)(trec + 1));
                     merged.push_back(f);

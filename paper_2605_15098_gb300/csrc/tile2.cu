@@ -211,9 +211,43 @@ __device__ __forceinline__ void apply_table_s(RegsN<NP> &r, const float4 *T, uin
 // QFT) the table product is skipped.
 template <int J, int NP>
 __device__ __forceinline__ void reg_hph_s(RegsN<NP> &r, uint32_t qm, const float4 *T, bool tab, float fr,
-                                          float fi) {
+                                          float fi, bool shared) {
     const float2 Fr = f2(fr), Fi = f2(fi), Fni = f2(-fi);
     if constexpr (J >= 1) {
+        if constexpr (J <= 3) {
+            if (tab && shared) {
+                // the table depends only on register bits below J
+                // (kT2HphShared): the 2^(J-1) products u = F T, once, then
+                // b <- u b per pair
+                constexpr int NV = 1 << (J - 1);
+                float2 ur[NV], ui[NV], nui[NV];
+#pragma unroll
+                for (int v = 0; v < NV; v++) {
+                    const float4 t = T[v | NV];
+                    const float2 tr = make_float2(t.x, t.y), ti = make_float2(t.z, t.w);
+                    ur[v] = fma2(ti, Fni, mul2(tr, Fr));
+                    ui[v] = fma2(tr, Fi, mul2(ti, Fr));
+                    nui[v] = make_float2(-ui[v].x, -ui[v].y);
+                }
+#pragma unroll
+                for (int g = 0; g < NP / 16; g++) {
+                    if (!((qm >> g) & 1)) continue;
+#pragma unroll
+                    for (int i = 0; i < 8; i++) {
+                        const int q = bfly_q<J>(8 * g + i), q1 = q | (1 << (J - 1));
+                        const int v = q1 & (NV - 1);
+                        const float2 br = r.re[q1], bi = r.im[q1];
+                        const float2 pr = fma2(bi, nui[v], mul2(br, ur[v]));
+                        const float2 pi = fma2(bi, ur[v], mul2(br, ui[v]));
+                        r.re[q1] = sub2(r.re[q], pr);
+                        r.im[q1] = sub2(r.im[q], pi);
+                        r.re[q] = add2(r.re[q], pr);
+                        r.im[q] = add2(r.im[q], pi);
+                    }
+                }
+                return;
+            }
+        }
         if (!tab) {
 #pragma unroll
             for (int g = 0; g < NP / 8; g++) {
@@ -465,16 +499,17 @@ __device__ __forceinline__ void t2_run(const T2Args &a, float4 *gstate, uint64_t
                 }
                 continue;
             }
-#define SV_HPH_CASE(J)                                       \
-    case kT2Handler + 8 * 5 + J: {                           \
-        const float4 *T;                                     \
-        float2 ph;                                           \
-        if ((int8_t)(w.x >> 24) == kT2HphDirect)             \
-            hph_direct(w, T, ph);                            \
-        else                                                 \
-            hph_run(w, T, ph);                               \
-        reg_hph_s<J>(r, qm, T, T != ones, ph.x, ph.y);       \
-        continue;                                            \
+#define SV_HPH_CASE(J)                                              \
+    case kT2Handler + 8 * 5 + J: {                                  \
+        const float4 *T;                                            \
+        float2 ph;                                                  \
+        const int8_t hc = (int8_t)(w.x >> 24);                      \
+        if (hc == kT2HphDirect || hc == kT2HphShared)               \
+            hph_direct(w, T, ph);                                   \
+        else                                                        \
+            hph_run(w, T, ph);                                      \
+        reg_hph_s<J>(r, qm, T, T != ones, ph.x, ph.y, hc == kT2HphShared); \
+        continue;                                                   \
     }
             SV_HPH_CASE(0)
             SV_HPH_CASE(1)

@@ -433,3 +433,38 @@ def test_programme_independent_of_earlier_compilations(sv):
         sv.sv_plan_export(n, sv.SV_C128, g, cfg)
     again = json.dumps(sv.sv_plan_export(n, sv.SV_C64, a, cfg), sort_keys=True)
     assert first == again
+
+
+@pytest.mark.parametrize("kind", ["qpe", "random"])
+def test_shared_twiddle_flag_holds(sv, kind):
+    """A phased butterfly marked kT2HphShared (control-class 0x41) on register
+    bit j has a table whose packed entries q1 (bit j - 1 of q1 set) depend only
+    on the bits of q1 below j - 1: the kernel then forms the 2^(j-1) products
+    of the thread factor and the table once.  Checked entry by entry on the
+    exported FP32 tables; QPE's inverse QFT has such steps."""
+    if kind == "qpe":
+        n, g = 24, fold_leading(C.qpe(24, seed=2)[0])[2]
+    else:
+        n, g = 18, C.random_circuit(18, 10, seed=3)
+    flagged = 0
+    for chunk in (5, 7, 9):
+        cfg = sv.make_config(sv.SV_MODE_PARTITIONED, chunk_qubits=chunk, flags=sv.SV_FLAG_NARROW_FIRST)
+        plan = sv.sv_plan_export(n, sv.SV_C64, g, cfg)
+        for p in plan["passes"]:
+            for t2 in (p.get("t2"), p.get("t2gen")):
+                if not t2:
+                    continue
+                mats = np.array(t2["mats"], dtype=np.float32).reshape(-1)
+                for ins in t2["ins"]:
+                    if ins["op"] != 9 or ins["ccls"] != 0x41:
+                        continue
+                    flagged += 1
+                    j, trec = ins["idx"], (ins["aux"] & 0xFFFF) - 1
+                    assert 1 <= j <= 3 and trec >= 0
+                    entry = lambda q: mats[8 * trec + 4 * q:8 * trec + 4 * q + 4]
+                    hb = 1 << (j - 1)
+                    for q1 in range(16):
+                        if q1 & hb:
+                            assert np.array_equal(entry(q1), entry((q1 & (hb - 1)) | hb))
+    if kind == "qpe":
+        assert flagged > 0
