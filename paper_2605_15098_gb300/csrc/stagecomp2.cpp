@@ -212,6 +212,7 @@ struct P32 {
     // register bits 1..4, bit j - 1 of q1 set) depend only on register bits
     // below j: every entry equals the one with the same low j - 1 bits
     static constexpr bool kSharedTwiddles = true;
+    static constexpr int kSharedMinJ = 1, kSharedMaxJ = 3;  // bit 0 is the packed element
     static bool table_low_only(const T2Pass *o, int m0, int j) {
         auto entry = [&](int q) { return o->mats[m0 + (q >> 1)].m + 4 * (q & 1); };
         const int hb = 1 << (j - 1);
@@ -245,8 +246,19 @@ struct P64 {
         *im = std::sin(ang);
     }
     static bool real(const double *m) { return m[1] == 0.0 && m[3] == 0.0 && m[5] == 0.0 && m[7] == 0.0; }
-    static constexpr bool kSharedTwiddles = false;  // the complex128 kernel keeps one form
-    static bool table_low_only(const T2Pass *, int, int) { return false; }
+    // entries x of a phased butterfly on register bit j (bit j of x set)
+    // depend only on register bits below j
+    static constexpr bool kSharedTwiddles = true;
+    static constexpr int kSharedMinJ = 0, kSharedMaxJ = 3;
+    static bool table_low_only(const T2Pass *o, int m0, int j) {
+        auto entry = [&](int x) { return &o->mats64[8 * (size_t)m0 + 2 * x]; };
+        const int hb = 1 << j;
+        for (int x = 0; x < 32; x++) {
+            if (!(x & hb)) continue;
+            if (std::memcmp(entry(x), entry((x & (hb - 1)) | hb), 2 * sizeof(double)) != 0) return false;
+        }
+        return true;
+    }
     static int32_t push_mat(T2Pass *o, const double *m) {
         o->mats64.insert(o->mats64.end(), m, m + 8);
         return (int32_t)(o->mats64.size() / 8) - 1;
@@ -649,8 +661,8 @@ std::string compile_fmt2(const TilePass &tp, T2Pass *out, bool gen) {
                         }
                     }
                     f.ccls = kT2HphDirect;
-                    if (P::kSharedTwiddles && trec >= 0 && hh.idx >= 1 && hh.idx <= 3 &&
-                        P::table_low_only(out, trec, hh.idx))
+                    if (P::kSharedTwiddles && trec >= 0 && hh.idx >= P::kSharedMinJ &&
+                        hh.idx <= P::kSharedMaxJ && P::table_low_only(out, trec, hh.idx))
                         f.ccls = kT2HphShared;
                     f.cidx = (int16_t)sl;
                     f.aux = (int32_t)(((uint32_t)(row + 1) << 16) | (uint32_t)(trec + 1));

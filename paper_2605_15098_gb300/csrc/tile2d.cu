@@ -260,7 +260,35 @@ __device__ __forceinline__ void d_factor_bit(RegsD &r, int mask, double2 f) {
 // Phased Hadamard on register bit J: b <- M b with M = f T[x_b], then the
 // pair becomes (a + M b, a - M b).  Without a table (`tab` false) M = f.
 template <int J>
-__device__ __forceinline__ void d_hph(RegsD &r, uint32_t qm, const double2 *T, bool tab, double2 f) {
+__device__ __forceinline__ void d_hph(RegsD &r, uint32_t qm, const double2 *T, bool tab, double2 f,
+                                      bool shared) {
+    if constexpr (J <= 3) {
+        if (tab && shared) {
+            // the table depends only on register bits below J (kT2HphShared):
+            // the 2^J products F T, once, then one product per pair
+            constexpr int NV = 1 << J;
+            double2 u[NV];
+#pragma unroll
+            for (int v = 0; v < NV; v++) u[v] = cxd(f, T[v | NV]);
+#pragma unroll
+            for (int g8 = 0; g8 < 2; g8++) {
+                if (!((qm >> g8) & 1)) continue;
+#pragma unroll
+                for (int i = 0; i < 8; i++) {
+                    const int a = lo_of<J>(8 * g8 + i), b = a | (1 << J);
+                    const double2 m = u[b & (NV - 1)];
+                    const double br = r.re[b], bi = r.im[b];
+                    const double pr = fma(-bi, m.y, br * m.x), pi = fma(br, m.y, bi * m.x);
+                    const double ar = r.re[a], ai = r.im[a];
+                    r.re[a] = ar + pr;
+                    r.im[a] = ai + pi;
+                    r.re[b] = ar - pr;
+                    r.im[b] = ai - pi;
+                }
+            }
+            return;
+        }
+    }
 #pragma unroll
     for (int g8 = 0; g8 < 2; g8++) {
         if (!((qm >> g8) & 1)) continue;
@@ -344,7 +372,7 @@ __device__ __forceinline__ void t2d_run(const T2Args &a, double2 *gstate, uint64
                 ph = thread_factor(fd);
         }
     };
-    // the same from the step itself (tileprog.h: kT2HphDirect)
+    // the same from the step itself (tileprog.h: kT2HphDirect, kT2HphShared)
     auto hph_direct = [&](const int4 w, const double2 *&T, double2 &ph) {
         const int trec = (int)((uint32_t)w.w & 0xffffu) - 1, row = (int)((uint32_t)w.w >> 16) - 1;
         const int sl = (int16_t)(w.y & 0xffff);
@@ -436,11 +464,12 @@ __device__ __forceinline__ void t2d_run(const T2Args &a, double2 *gstate, uint64
     case kT2Handler + 8 * 5 + J: {      \
         const double2 *T;               \
         double2 ph;                     \
-        if ((int8_t)(w.x >> 24) == kT2HphDirect) \
+        const int8_t hc = (int8_t)(w.x >> 24); \
+        if (hc == kT2HphDirect || hc == kT2HphShared) \
             hph_direct(w, T, ph);       \
         else                            \
             hph_run(w, T, ph);          \
-        d_hph<J>(r, qm, T, T != ones, ph); \
+        d_hph<J>(r, qm, T, T != ones, ph, hc == kT2HphShared); \
         continue;                       \
     }
             SV_HPH_CASE(0)

@@ -95,12 +95,14 @@ constexpr int kT2Handler = 16;
 enum T2Class : int32_t { T2C_NONE = 0, T2C_REG = 1, T2C_LANE = 2, T2C_THREAD = 3, T2C_GLOBAL = 4 };
 // control-class field of a T2_HPH step whose table, row and slot are in the step
 constexpr int8_t kT2HphDirect = 0x40;
-// The same, for a step on register bit j = 1..3 whose table depends only on
-// register bits 0..j-1 (complex64 programmes; the inverse QFT's phases on a
-// qubit come from the qubits it transformed before, often register bits of
-// the same stage): the 2^(j-1) distinct products of the thread factor and
-// the table are formed once, and each pair takes one of them.  A kernel that
-// does not know the code reads the run from its factor records.
+// The same, for a step on register bit j whose table depends only on
+// register bits 0..j-1 (j = 1..3 in complex64 programmes, where bit 0 is the
+// element of a packed pair; j = 0..3 in complex128 ones).  The inverse QFT's
+// phases on a qubit come from the qubits it transformed before, often
+// register bits of the same stage.  The distinct products of the thread
+// factor and the table (2^(j-1) packed, 2^j in FP64) are formed once, and
+// each pair takes one of them.  A kernel that does not know the code reads
+// the run from its factor records.
 constexpr int8_t kT2HphShared = 0x41;
 
 // One programme step, 16 bytes (one vector load in the kernel).
