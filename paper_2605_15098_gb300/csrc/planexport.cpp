@@ -58,13 +58,15 @@ void put_t2(J &j, const T2Pass &t) {
         for (int e = 0; e < 14; e++) tb[e] = t.stages[i].tb[e];
         j.arr(tb, 14);
     }
+    // matrix records: FP32 (complex64 programmes) or FP64 (complex128), 8 values each
     j.raw("],\"mats\":[");
-    for (size_t i = 0; i < t.mats.size(); i++) {
+    const size_t nm = t.mats.empty() ? t.mats64.size() / 8 : t.mats.size();
+    for (size_t i = 0; i < nm; i++) {
         if (i) j.raw(",");
         j.raw("[");
         for (int e = 0; e < 8; e++) {
             if (e) j.raw(",");
-            j.dbl(t.mats[i].m[e]);
+            j.dbl(t.mats.empty() ? t.mats64[8 * i + e] : (double)t.mats[i].m[e]);
         }
         j.raw("]");
     }
@@ -97,9 +99,10 @@ void put_t2(J &j, const T2Pass &t) {
         j.raw("}");
     }
     j.raw("],\"statc\":[");
-    for (size_t i = 0; i < t.statc.size(); i++) {
+    const size_t ns = t.statc.empty() ? t.statc64.size() : t.statc.size();
+    for (size_t i = 0; i < ns; i++) {
         if (i) j.raw(",");
-        j.dbl(t.statc[i]);
+        j.dbl(t.statc.empty() ? t.statc64[i] : (double)t.statc[i]);
     }
     j.raw("],\"slots\":[");
     for (size_t i = 0; i < t.slots.size(); i++) {
@@ -242,6 +245,24 @@ extern "C" sv_status sv_plan_export(int n, sv_dtype dt, const int *host_phys_of_
                 }
                 why = compile_t2(p, &t2, false);
                 kname = "t2";
+            }
+        }
+        if (dbl && !(c.flags & SV_FLAG_GENERIC_TILE) && p.k == kT2Qubits && !p.ops.empty()) {
+            // complex128 on 2^13-amplitude tiles: the FP64 register-stage kernel
+            // (its programme is the emulator's business only through the ops)
+            why = compile_t2v2_c128(p, &t2, false);
+            if (why.empty()) {
+                j.raw(",\"kernel\":\"t2d\",\"t2d\":");
+                put_t2(j, t2);
+                if (first_ops) {
+                    T2Pass g;
+                    if (compile_t2v2_c128(p, &g, true).empty()) {
+                        j.raw(",\"t2dgen\":");
+                        put_t2(j, g);
+                    }
+                }
+                j.raw("}");
+                continue;
             }
         }
         if (why.empty()) {

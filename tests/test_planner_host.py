@@ -375,13 +375,14 @@ def test_phased_butterfly_fields_match_their_run(sv, n, kind):
     run's factor records); they must be exactly those of the records the step
     also keeps (read by the emulator above)."""
     K_DIRECT, FAC_TABLE = 0x40, 1 << 28
+    K_SHARED = 0x41  # the same, with shared twiddles (tileprog.h: kT2HphShared)
     g = (C.qpe(n, seed=n)[0] if kind == "qpe" else mixed_circuit(n, 150, 7) if kind == "mixed"
          else C.random_circuit(n, 4, 5))
     found = 0
     for dtype in (sv.SV_C64, sv.SV_C128):
         plan = sv.sv_plan_export(n, dtype, g, sv.make_config(sv.SV_MODE_PARTITIONED))
         for p in plan["passes"]:
-            for t2 in [p[k] for k in ("t2", "t2gen") if k in p]:
+            for t2 in [p[k] for k in ("t2", "t2gen", "t2d", "t2dgen") if k in p]:
                 fac = t2["fac2"]
                 for ins in t2["ins"]:
                     if ins["op"] != planemu.T2_HPH:
@@ -393,7 +394,7 @@ def test_phased_butterfly_fields_match_their_run(sv, n, kind):
                             trec = f["row"]
                         else:
                             row, slot = f["row"], f["slot"]
-                    assert ins["ccls"] == K_DIRECT
+                    assert ins["ccls"] in (K_DIRECT, K_SHARED)
                     assert (ins["aux"] & 0xffff) - 1 == trec
                     assert ((ins["aux"] >> 16) & 0xffff) - 1 == row
                     assert ins["cidx"] == slot
@@ -468,3 +469,33 @@ def test_shared_twiddle_flag_holds(sv, kind):
                             assert np.array_equal(entry(q1), entry((q1 & (hb - 1)) | hb))
     if kind == "qpe":
         assert flagged > 0
+
+
+def test_shared_twiddle_flag_holds_c128(sv):
+    """The complex128 form: a step marked 0x41 on register bit j = 0..3 has a
+    32-entry FP64 table whose entries x (bit j of x set) depend only on the
+    bits of x below j.  QPE's complex128 programmes run on the FP64
+    register-stage kernel (exported as t2d) and have such steps."""
+    n, g = 22, fold_leading(C.qpe(22, seed=5)[0])[2]
+    flagged = 0
+    for chunk in (5, 6, 7):
+        cfg = sv.make_config(sv.SV_MODE_PARTITIONED, tile_qubits=13, chunk_qubits=chunk)
+        plan = sv.sv_plan_export(n, sv.SV_C128, g, cfg)
+        assert all(p["kernel"] == "t2d" for p in plan["passes"] if p["ops"])
+        for p in plan["passes"]:
+            for t2 in (p.get("t2d"), p.get("t2dgen")):
+                if not t2:
+                    continue
+                mats = np.array(t2["mats"], dtype=np.float64).reshape(-1)
+                for ins in t2["ins"]:
+                    if ins["op"] != planemu.T2_HPH or ins["ccls"] != 0x41:
+                        continue
+                    flagged += 1
+                    j, trec = ins["idx"], (ins["aux"] & 0xFFFF) - 1
+                    assert 0 <= j <= 3 and trec >= 0
+                    entry = lambda x: mats[8 * trec + 2 * x:8 * trec + 2 * x + 2]
+                    hb = 1 << j
+                    for x in range(32):
+                        if x & hb:
+                            assert np.array_equal(entry(x), entry((x & (hb - 1)) | hb))
+    assert flagged > 0
